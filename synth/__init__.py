@@ -1,0 +1,12 @@
+"""Seeded synthetic inputs for the map-making solver.
+
+This package only *synthesises* data: scan geometry (pixel index and
+polarisation angle per sample), stationary-interval boundaries, noise
+parameters, a random sky, and the timestream d = A z + n of the data model
+(Section 3, Eqs. 1-2).  It contains none of the solver's arithmetic (no
+pointing operators, no noise filters, no FFT convolution, no PCG).  Both the
+CPU oracle and the GPU library consume what it produces; neither imports the
+other.
+"""
+
+from .flat import Problem, make_config, make_flat_problem, config_spec  # noqa: F401

@@ -1,0 +1,369 @@
+"""Pins for the FP64 oracle: each ties an oracle function to something other than itself
+(a closed form, an invariant, brute force on tiny inputs, or the paper's own algebra).
+
+CPU only (no GPU marker).
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import noise as nz
+from oracle import pointing as pt
+from oracle.solver import System, pcg
+from tests.helpers import lags_for, rel_rms, system_for, tiny_IQU, tiny_T
+
+
+# ----------------------------------------------------------------------------- pointing
+def test_observed_pixels_bruteforce():
+    rng = np.random.default_rng(5)
+    n_pix = 50
+    pix = rng.integers(-1, n_pix, size=300).astype(np.int32)
+    pix[pix == 17] = 3                                      # leave some pixels unobserved
+    o2g, g2o = pt.observed_pixels(pix, n_pix)
+    # Section 5.4 bit array, written as plain Python loops
+    bits = [0] * n_pix
+    for p in pix.tolist():
+        if p >= 0:
+            bits[p] = 1
+    want = [g for g in range(n_pix) if bits[g]]
+    assert o2g.tolist() == want
+    for g in range(n_pix):
+        assert g2o[g] == (want.index(g) if bits[g] else -1)
+
+
+def test_weights_closed_form():
+    psi = np.array([0.0, np.pi / 4, np.pi / 2, 3 * np.pi / 4], dtype=np.float32)
+    w = pt.weights(psi, 3)
+    want = np.array([[1, 1, 0], [1, 0, 1], [1, -1, 0], [1, 0, -1]], dtype=np.float64)
+    assert np.allclose(w, want, atol=1e-7)
+    assert pt.weights(psi, 1) is None
+
+
+def test_point_is_transpose_of_unpoint():
+    p = tiny_IQU()
+    S = system_for(p)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((S.n_obs, 3))
+    y = rng.standard_normal(p.n_samples)
+    lhs = float(np.sum(S.unpoint(x) * y))
+    rhs = float(np.sum(x * S.point(y)))
+    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+    A = pt.dense_pointing(S.pixl, S.w, S.n_obs, 3)
+    assert np.allclose(A @ x.reshape(-1), S.unpoint(x), atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- N^-1
+def _rand_lags(n_c, seed=0):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(n_c) * np.exp(-np.arange(n_c) / 3.0)
+
+
+def test_ninv_impulse_and_constant_closed_forms():
+    n_c = 6
+    f = _rand_lags(n_c, 1)
+    offs = np.array([0, 40, 55])
+    filt = np.array([0, 0])
+    lags = f[None, :]
+    # impulse at t0 inside interval 0: response f(|t - t0|) inside the interval only
+    y = np.zeros(55)
+    y[37] = 1.0
+    w = nz.apply_ninv_direct(y, offs, filt, lags)
+    for t in range(55):
+        want = f[abs(t - 37)] if (t < 40 and abs(t - 37) < n_c) else 0.0
+        assert w[t] == pytest.approx(want, abs=1e-15)
+    # constant input: interior = symbol at zero frequency; first sample = one-sided sum
+    y = np.ones(55)
+    w = nz.apply_ninv_direct(y, offs, filt, lags)
+    assert w[20] == pytest.approx(f[0] + 2 * f[1:].sum(), rel=1e-14)
+    assert w[0] == pytest.approx(f.sum(), rel=1e-14)
+    assert w[40] == pytest.approx(f.sum(), rel=1e-14)     # first sample of interval 1
+
+
+def test_ninv_sinusoid_eigen_interior():
+    n_c = 9
+    f = _rand_lags(n_c, 2)
+    n = 200
+    th = 0.37
+    t = np.arange(n)
+    y = np.cos(th * t)
+    w = nz.apply_ninv_direct(y, np.array([0, n]), np.array([0]), f[None, :])
+    S = f[0] + 2 * np.sum(f[1:] * np.cos(th * np.arange(1, n_c)))
+    inner = slice(n_c, n - n_c)
+    assert np.allclose(w[inner], S * y[inner], atol=1e-12)
+
+
+@pytest.mark.parametrize("n_f", [None, 32, 64, 256])
+def test_ninv_fft_overlap_save_equals_direct(n_f):
+    rng = np.random.default_rng(3)
+    n_c = 11
+    lags = np.stack([_rand_lags(n_c, 4), _rand_lags(n_c, 5)])
+    lens = [1, 7, 30, 31, 100, 333]
+    offs = np.concatenate([[0], np.cumsum(lens)])
+    filt = np.array([0, 1, 0, 1, 1, 0])
+    y = rng.standard_normal(offs[-1])
+    nf = nz.fft_length(n_c, max(lens)) if n_f is None else n_f
+    a = nz.apply_ninv_fft(y, offs, filt, lags, nf)
+    b = nz.apply_ninv_direct(y, offs, filt, lags)
+    assert np.max(np.abs(a - b)) < 1e-12 * np.max(np.abs(b))
+
+
+def test_ninv_direct_equals_dense_matrix():
+    n_c = 5
+    lags = np.stack([_rand_lags(n_c, 6), _rand_lags(n_c, 7)])
+    offs = np.array([0, 3, 20, 33])
+    filt = np.array([1, 0, 1])
+    y = np.random.default_rng(8).standard_normal(33)
+    M = nz.dense_ninv(offs, filt, lags)
+    assert np.allclose(M, M.T)
+    assert np.allclose(M @ y, nz.apply_ninv_direct(y, offs, filt, lags), atol=1e-13)
+
+
+# ----------------------------------------------------------------------------- filter lags
+def test_filter_white_noise_limit():
+    f = nz.filter_lags(64, 100.0, 2.0, 0.0, 1.5)
+    want = np.zeros(64)
+    want[0] = 0.25
+    assert np.allclose(f, want, atol=1e-15)
+
+
+@pytest.mark.parametrize("fk", [0.05, 0.1, 0.2])
+def test_filter_alpha2_lorentzian_closed_form(fk):
+    # 1/p = (1/s^2) [1 - fk^2/(f^2 + fk^2)]; the Lorentzian transforms to
+    # pi fk exp(-2 pi fk |t|), so c_tau = (1/s^2)[delta - (pi fk/fs) exp(-2 pi fk tau/fs)]
+    # up to the band edge at fs/2, the finite-DC bin and aliasing (all < 1e-5 here).
+    n_c, fs, s = 4096, 100.0, 1.7
+    f = nz.filter_lags(n_c, fs, s, fk, 2.0)
+    tau = np.arange(n_c)
+    c = (tau == 0) - (math.pi * fk / fs) * np.exp(-2 * math.pi * fk * tau / fs)
+    want = (1.0 - tau / n_c) * c / s ** 2
+    assert np.max(np.abs(f - want)) < 2e-5 / s ** 2
+
+
+def test_filter_sigma_scaling_and_taper():
+    f1 = nz.filter_lags(128, 100.0, 1.0, 0.1, 1.3)
+    f2 = nz.filter_lags(128, 100.0, 3.0, 0.1, 1.3)
+    assert np.allclose(f2, f1 / 9.0, rtol=1e-12, atol=1e-18)
+
+
+@pytest.mark.parametrize("params", [(1.0, 0.1, 2.0), (1.0, 0.05, 1.0), (1.0, 0.2, 2.0), (0.7, 0.03, 1.7),
+                                    (1.0, 5.0, 1.5)])
+def test_filter_toeplitz_positive_definite(params):
+    n_c = 64
+    f = nz.filter_lags(n_c, 100.0, *params)
+    n = 3 * n_c
+    T = np.array([[f[abs(i - j)] if abs(i - j) < n_c else 0.0 for j in range(n)] for i in range(n)])
+    ev = np.linalg.eigvalsh(T)
+    sym = nz.toeplitz_symbol(f, 8 * n_c)
+    assert sym.min() > 0
+    assert ev.min() > 0
+    assert ev.min() >= sym.min() * (1 - 1e-9) - 1e-14      # Toeplitz spectrum within the symbol's range
+    assert ev.max() <= sym.max() * (1 + 1e-9) + 1e-14
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_filter_gradient_central_difference(k):
+    base = np.array([1.1, 0.12, 1.6])
+    f, g = nz.filter_lags(256, 100.0, *base, with_grad=True)
+    h = 1e-5 * base[k]
+    up, dn = base.copy(), base.copy()
+    up[k] += h
+    dn[k] -= h
+    fd = (nz.filter_lags(256, 100.0, *up) - nz.filter_lags(256, 100.0, *dn)) / (2 * h)
+    assert np.max(np.abs(fd - g[k])) < 1e-6 * np.max(np.abs(g[k]))
+
+
+# ----------------------------------------------------------------------------- FFT length
+@pytest.mark.parametrize("n_c", [2 ** 8, 2 ** 10, 2 ** 12])
+def test_optimal_nf_is_integer_argmin_of_h(n_c):
+    root = nz.optimal_nf(n_c)
+    n = np.arange(2 * n_c + 1, 60 * n_c, dtype=np.float64)
+    hv = n * np.log(n) / (n - 2 * n_c)
+    assert abs(n[np.argmin(hv)] - root) <= 1.0
+    assert nz.hsecond(root, n_c) > 0                        # Appendix A
+
+
+@pytest.mark.parametrize("x", [3000.0, 10000.0, 50000.0, 200000.0])
+def test_hprime_matches_numerical_derivative(x):
+    n_c = 1024
+    e = 1e-5 * x
+    fd = (nz.h(x + e, n_c) - nz.h(x - e, n_c)) / (2 * e)
+    assert nz.hprime(x, n_c) == pytest.approx(fd, rel=1e-5)
+    e2 = 1e-4 * x
+    fd2 = (nz.hprime(x + e2, n_c) - nz.hprime(x - e2, n_c)) / (2 * e2)
+    assert nz.hsecond(x, n_c) == pytest.approx(fd2, rel=1e-3)
+
+
+@pytest.mark.parametrize("n_c,longest", [(2 ** 12, 2 ** 18), (2 ** 14, 2 ** 20), (2 ** 15, 648000),
+                                          (2 ** 12, 5000), (16, 100)])
+def test_fft_length_rule_brackets_optimum(n_c, longest):
+    n_f = nz.fft_length(n_c, longest)
+    assert n_f & (n_f - 1) == 0 and n_f > 2 * n_c
+    opt = nz.optimal_nf(n_c)
+    top = 1 << int(math.ceil(math.log2(longest + 1)))
+    if n_f < top:                                 # the rule halved: optimum sits in (n_f/2, n_f]
+        assert n_f / 2 < opt <= n_f or n_f // 2 <= 2 * n_c
+
+
+# ----------------------------------------------------------------------------- preconditioner
+def test_preconditioner_blocks_inverse_and_excision_closed_form():
+    # pixel 0: angles 0/45/90/135 deg, m hits each -> A^T A = m diag(4,2,2), rcond = 1/2
+    # pixel 1: angles 0/90 only -> U column zero -> singular -> excised
+    m = 5
+    ang = np.deg2rad(np.array([0.0, 45.0, 90.0, 135.0] * m + [0.0, 90.0] * m))
+    pix = np.array([0] * (4 * m) + [1] * (2 * m), dtype=np.int32)
+    offs = np.array([0, pix.size])
+    lags = np.array([[2.0, 0.3]])
+    S = System(pix, ang.astype(np.float32), 2, 3, offs, np.array([0]), lags)
+    assert S.rcond[0] == pytest.approx(0.5, rel=1e-6)
+    assert not S.excised[0] and S.excised[1]
+    assert np.allclose(S.blocks[0], 2.0 * m * np.diag([4.0, 2.0, 2.0]), atol=1e-5)
+    assert np.allclose(S.Pinv[0] @ S.blocks[0], np.eye(3), atol=1e-12)
+    assert np.all(S.pixl[4 * m:] == -1)
+
+
+def test_preconditioner_matches_dense_AtWA():
+    p = tiny_IQU()
+    S = system_for(p)
+    A = pt.dense_pointing(S.pixl, S.w, S.n_obs, 3)
+    f0 = np.repeat(S.lags[S.ivl_filter, 0], np.diff(S.offsets))
+    AtWA = A.T @ (f0[:, None] * A)
+    for q in range(S.n_obs):
+        if S.excised[q]:
+            continue
+        blk = AtWA[3 * q:3 * q + 3, 3 * q:3 * q + 3]
+        assert np.allclose(S.blocks[q], blk, rtol=1e-12, atol=1e-12)
+        assert np.allclose(S.Pinv[q] @ blk, np.eye(3), atol=1e-10)
+
+
+# ----------------------------------------------------------------------------- solve
+@pytest.mark.parametrize("maker,ninv", [(tiny_T, "fft"), (tiny_T, "direct"), (tiny_IQU, "fft")])
+def test_pcg_matches_dense_cholesky(maker, ninv):
+    p = maker()
+    S = system_for(p, ninv=ninv)
+    x, info = S.solve(p.d[0], rel_tol=1e-14, max_iter=500)
+    xd = S.dense_solve(p.d[0])
+    assert rel_rms(x, xd) < 1e-10
+    assert info["best_res"] <= 1e-13
+
+
+def test_finite_termination():
+    p = tiny_T(n=300, ivls=(300,), width=3)
+    S = system_for(p)
+    n_unk = S.n_obs
+    _, info = S.solve(p.d[0], rel_tol=1e-12, max_iter=n_unk + 5)
+    assert info["best_res"] <= 1e-12
+    assert info["iters"] <= n_unk + 5
+
+
+def test_h_norm_error_monotone_and_lowest_residual_rule():
+    p = tiny_IQU(seed=7)
+    S = system_for(p)
+    b = S.rhs(p.d[0])
+    xs = S.dense_solve(p.d[0])
+    x, info = S.pcg(b, rel_tol=1e-30, max_iter=25, keep_history=True)
+    errs = []
+    for xi in info["iterates"]:
+        e = (xi - xs).reshape(-1)
+        errs.append(float(e @ S.H(e.reshape(S.n_obs, 3)).reshape(-1)))
+    assert all(errs[i + 1] <= errs[i] * (1 + 1e-9) + 1e-20 for i in range(len(errs) - 1))
+    k = int(np.argmin(info["history"]))
+    assert info["best_iter"] == k
+    assert np.array_equal(x, info["iterates"][k])
+
+
+def test_lowest_residual_rule_returns_earlier_iterate_when_residual_rises():
+    # 2x2 SPD system where CG's residual goes up at step 1 (non-monotone residual norm)
+    H = np.array([[1.0, 0.0], [0.0, 100.0]])
+    b = np.array([1.0, 0.1])
+    x, info = pcg(lambda v: H @ v, lambda r: r, b, 1e-30, 1, keep_history=True)
+    hist = info["history"]
+    assert hist[1] > hist[0]
+    assert info["best_iter"] == 0 and np.all(x == 0)
+
+
+def test_white_noise_limit_is_binned_average_T():
+    p = tiny_T(seed=11, ivls=(600,))
+    S = system_for(p, lags=np.array([[1.0]]))
+    x, info = S.solve(p.d[0], rel_tol=1e-14, max_iter=10)
+    assert info["iters"] == 1                      # exact block preconditioner: one step
+    for q, g in enumerate(S.obs2glob):
+        sel = p.pix == g
+        assert x[q, 0] == pytest.approx(float(np.mean(p.d[0][sel].astype(np.float64))), rel=1e-12, abs=1e-12)
+
+
+def test_white_noise_limit_is_binned_average_IQU():
+    p = tiny_IQU(seed=12)
+    lags = np.ones((p.n_filters, 1)) * 0.5
+    S = system_for(p, lags=lags)
+    x, info = S.solve(p.d[0], rel_tol=1e-14, max_iter=10)
+    assert info["iters"] == 1
+    two = 2.0 * p.psi.astype(np.float64)
+    for q, g in enumerate(S.obs2glob):
+        if S.excised[q]:
+            continue
+        sel = p.pix == g
+        Ap = np.stack([np.ones(sel.sum()), np.cos(two[sel]), np.sin(two[sel])], 1)
+        want = np.linalg.lstsq(Ap, p.d[0][sel].astype(np.float64), rcond=None)[0]
+        assert np.allclose(x[q], want, rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("maker", [tiny_T, tiny_IQU])
+def test_noiseless_recovery(maker):
+    p = maker(noiseless=True)
+    S = system_for(p)
+    x, _ = S.solve(p.d[0], rel_tol=1e-13, max_iter=500)
+    z = p.sky[S.obs2glob]
+    keep = ~S.excised
+    assert rel_rms(x[keep], z[keep]) < 1e-6            # d is stored in float32
+
+
+def test_operator_symmetric_positive_definite():
+    p = tiny_IQU(seed=3)
+    S = system_for(p)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((S.n_obs, 3))
+    y = rng.standard_normal((S.n_obs, 3))
+    x[S.excised] = 0
+    y[S.excised] = 0
+    a = float(np.sum(x * S.H(y)))
+    b = float(np.sum(y * S.H(x)))
+    assert abs(a - b) <= 1e-12 * abs(a)
+    assert float(np.sum(x * S.H(x))) > 0
+
+
+def test_polarisation_relabelling():
+    """Paper's row (1/2)[i + q sin 2a + u cos 2a] versus (I + Q cos 2psi + U sin 2psi)."""
+    p = tiny_IQU(seed=4)
+    S = system_for(p)
+    xs = S.dense_solve(p.d[0])
+    two = 2.0 * p.psi.astype(np.float64)
+    keep_rows = S.pixl >= 0
+    Ap = np.zeros((p.n_samples, S.n_obs * 3))
+    for t in np.flatnonzero(keep_rows):
+        q = S.pixl[t]
+        Ap[t, 3 * q:3 * q + 3] = 0.5 * np.array([1.0, np.sin(two[t]), np.cos(two[t])])
+    _, N, _ = S.dense_H()
+    keep = np.repeat(~S.excised, 3)
+    Hp = (Ap.T @ N @ Ap)[np.ix_(keep, keep)]
+    bp = (Ap.T @ N @ p.d[0].astype(np.float64))[keep]
+    iqu = np.zeros(S.n_obs * 3)
+    iqu[keep] = np.linalg.solve(Hp, bp)
+    iqu = iqu.reshape(S.n_obs, 3)
+    ours = np.stack([iqu[:, 0] / 2, iqu[:, 2] / 2, iqu[:, 1] / 2], 1)
+    assert rel_rms(xs, ours) < 1e-10
+
+
+def test_flagged_samples_are_zero_rows():
+    p = tiny_T(seed=9, flag_frac=0.2)
+    S = system_for(p)
+    y = np.random.default_rng(2).standard_normal(p.n_samples)
+    y2 = y.copy()
+    y2[p.pix < 0] += 1e6                           # data on flagged rows never reaches the map
+    assert np.allclose(S.point(y), S.point(y2))
+    xs = S.dense_solve(p.d[0])
+    x, _ = S.solve(p.d[0], rel_tol=1e-13, max_iter=300)
+    assert rel_rms(x, xs) < 1e-10
