@@ -1,0 +1,213 @@
+/*
+ * madmap.h -- C ABI of libmadmap, a GB300 (sm_103a) library for the
+ * maximum-likelihood map-making solve of MADmap (Cantalupo et al.,
+ * arXiv:0906.1775).
+ *
+ * The library solves  H m = b,  H = A^T N^-1 A,  b = A^T N^-1 d
+ * (Section 4, Eq. 10; the maximum-likelihood map of Section 3, Eq. 8) with
+ * preconditioned conjugate gradients, where
+ *   A     is the sparse pointing matrix: one unit weight per sample for
+ *         temperature (Section 3, Eq. 3), or the weights (1, cos 2psi, sin 2psi)
+ *         on (I, Q, U) for polarisation (Section 3, Eq. 4, relabelled as
+ *         (I, Q, U) = (i/2, u/2, q/2) of the paper's Stokes vector);
+ *   N^-1  is block diagonal with one banded symmetric Toeplitz block per
+ *         stationary interval, N^-1_{t,t'} = f(|t-t'|) for |t-t'| < n_c
+ *         (Section 5.2, Eq. 15), applied by FFT convolution of circulant
+ *         embeddings over overlapping windows (Section 5.2, Eqs. 16-22).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a madmap_status; nothing aborts or exits.  On an
+ *     error, madmap_last_error() returns a message (thread local).
+ *   - "device" pointers are CUDA device memory owned by the caller; "host"
+ *     pointers are ordinary host memory, read during the call only.
+ *   - Calls that take a cudaStream_t (passed as void*, NULL = legacy default
+ *     stream) are ordered on that stream and may return before the GPU work
+ *     finishes, except where stated.
+ *   - A plan keeps the caller's pix/psi device pointers by reference only
+ *     during madmap_plan_create (it copies what it needs into derived buffers
+ *     it owns); after creation the caller may free them.
+ *   - Maps exchanged with the caller are laid out [n_rhs][n_obs][n_stokes]
+ *     over the plan's observed pixels (ascending global index, Section 5.4).
+ *   - A plan is not thread safe: calls on one plan must be serialised.
+ */
+#ifndef MADMAP_H_
+#define MADMAP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct madmap_plan_s* madmap_plan_t;
+
+typedef enum {
+  MADMAP_OK = 0,
+  MADMAP_WARN_MAXITER = 1,      /* result valid: lowest-residual iterate returned */
+  MADMAP_ERR_INVALID_ARG = -1,  /* bad sizes, pointers, indices, offsets or filters */
+  MADMAP_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+  MADMAP_ERR_OOM = -3,          /* device allocation failed (or was injected to fail) */
+  MADMAP_ERR_NOT_PD = -4,       /* a filter's Toeplitz symbol is not positive, or p^T H p <= 0 */
+  MADMAP_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up */
+  MADMAP_ERR_INTERNAL = -6
+} madmap_status;
+
+typedef enum {
+  MADMAP_FP64 = 0,   /* operator, vectors and scalars in float64 */
+  MADMAP_MIXED = 1,  /* float32 operator and vectors inside float64 iterative refinement */
+  MADMAP_FP32 = 2    /* float32 operator (madmap_apply_ATNA / madmap_apply_ninv / madmap_rhs only) */
+} madmap_precision;
+
+/* Description of the data a plan is built over.  Section 3 (data model),
+ * Section 5.2 (stationary intervals and filters), Section 5.4 (indexing). */
+typedef struct {
+  int32_t n_stokes;                 /* 1 (T) or 3 (IQU) */
+  int64_t n_samples;                /* n_t, all detectors concatenated; 0 allowed (empty plan) */
+  int32_t n_pix;                    /* global pixel count n_z (> 0) */
+  const int32_t* pix;               /* device [n_samples]: global pixel of each sample,
+                                       -1 = flagged sample (zero row of A, Section 4 gap filling);
+                                       any other value outside [0, n_pix) is INVALID_ARG */
+  const float* psi;                 /* device [n_samples]: polarisation angle in radians;
+                                       must be NULL when n_stokes == 1 and non-NULL when 3 */
+  int32_t n_intervals;              /* stationary intervals (Toeplitz blocks of N^-1), >= 0 */
+  const int64_t* interval_offsets;  /* host [n_intervals + 1]: non-decreasing, [0] = 0,
+                                       [n_intervals] = n_samples; interval i = [off[i], off[i+1]) */
+  const int32_t* interval_filter;   /* host [n_intervals]: filter index of each interval */
+  int32_t n_filters;                /* >= 1 */
+  int32_t n_lags;                   /* n_c >= 1: lags tau = 0 .. n_c-1 of Eq. 15 */
+  const double* filter_lags;        /* host [n_filters][n_lags]: f(tau) of each filter; each
+                                       filter's Toeplitz symbol must be > 0 (else NOT_PD) */
+  double rcond_excise;              /* IQU: excise pixels with hits < 3 or
+                                       rcond(A^T A block) < this (<= 0: default 1e-6) */
+  double rcond_fp64;                /* IQU: keep float64 preconditioner blocks for pixels with
+                                       rcond below this in MIXED solves (<= 0: default 1e-2) */
+  int32_t fft_len;                  /* complex FFT length M per window (power of two in
+                                       [256, 2^20], > 2 (n_lags-1)); 0 = chosen by the plan */
+  int32_t tiles_per_chunk;          /* windows pairs per operator launch chunk; 0 = chosen */
+} madmap_plan_desc;
+
+typedef struct {
+  int32_t n_obs;           /* observed pixels */
+  int32_t n_excised;       /* observed pixels excised (IQU, Section 4) */
+  int32_t n_fp64_pixels;   /* pixels keeping float64 preconditioner blocks */
+  int32_t n_stokes;
+  int32_t fft_len;         /* M */
+  int32_t n1, n2;          /* M = n1 * n2 (four-step factorisation) */
+  int32_t n_segments;      /* overlap-save windows over all intervals */
+  int32_t n_tiles;         /* window pairs (two real windows per complex FFT) */
+  int32_t tiles_per_chunk;
+  int32_t n_lags;
+  int32_t n_filters;
+  int64_t n_samples;
+  int64_t device_bytes;    /* device memory owned by the plan */
+} madmap_plan_stats;
+
+typedef struct {
+  int32_t max_iter;        /* PCG iterations (mixed: total inner iterations); default 50 (Section 5) */
+  double rel_tol;          /* stop at ||r_k|| / ||b|| <= rel_tol; default 1e-6 (Section 5) */
+  int32_t precision;       /* madmap_precision: FP64 or MIXED */
+  int32_t max_outer;       /* MIXED: refinement steps, default 10 */
+  double inner_rel_tol;    /* MIXED: inner float32 PCG stops at this reduction of its residual,
+                              default 1e-4 */
+  int32_t use_graph;       /* 1 (default): replay iterations as CUDA graphs */
+  int32_t iters_per_sync;  /* iterations enqueued between host checks, default 8 */
+} madmap_solve_opts;
+
+typedef struct {
+  int32_t status;          /* madmap_status of the solve */
+  int32_t iters;           /* PCG iterations performed (sum of inner iterations for MIXED) */
+  int32_t outer_iters;     /* MIXED refinement steps (FP64: 1) */
+  int32_t best_iter;       /* iteration count at which the returned iterate was produced */
+  int32_t fp64_applies;    /* float64 operator applications, including the right-hand side */
+  int32_t fp32_applies;    /* float32 operator applications */
+  double final_rel_res;    /* last relative residual ||b - H x_k|| / ||b|| (recursive for FP64) */
+  double best_rel_res;     /* relative residual of the returned map */
+  double t_rhs_ms;         /* right-hand side time */
+  double t_solve_ms;       /* total call time (right-hand side included) */
+} madmap_solve_info;
+
+/* ------------------------------------------------------------------ plans */
+
+/* Build a plan: observed-pixel compaction (Section 5.4), pixel classification
+ * and preconditioner blocks (Sections 4-5), overlap-save windows, filter
+ * spectra and work buffers.  Synchronises `stream` before returning.
+ * out: receives the plan (NULL on error). */
+madmap_status madmap_plan_create(const madmap_plan_desc* desc, void* stream, madmap_plan_t* out);
+
+/* Free all device memory of a plan.  NULL is accepted. */
+madmap_status madmap_plan_destroy(madmap_plan_t plan);
+
+madmap_status madmap_plan_get_stats(madmap_plan_t plan, madmap_plan_stats* out);
+
+/* Observed pixels (Section 5.4).  *n_obs receives their count.  When
+ * non-NULL, obs2glob (device int32 [n_obs], caller-owned) receives the global
+ * index of each observed pixel in ascending order, and excised (device uint8
+ * [n_obs]) receives 1 for pixels excised as poorly conditioned (Section 4; their
+ * map value is 0).  Copies are ordered on `stream`.  Call with NULL buffers
+ * first to learn n_obs. */
+madmap_status madmap_plan_observed(madmap_plan_t plan, int32_t* n_obs, int32_t* obs2glob, uint8_t* excised,
+                                   void* stream);
+
+/* Replace the filter lags (host [n_filters][n_lags]) without re-planning:
+ * recomputes spectra and preconditioner blocks.  Synchronises `stream`. */
+madmap_status madmap_plan_set_filters(madmap_plan_t plan, const double* filter_lags, void* stream);
+
+/* ------------------------------------------------------------------ operators */
+
+/* y = H x = A^T N^-1 A x (Eq. 10) for n_rhs maps.  x, y: device
+ * [n_rhs][n_obs][n_stokes], double for MADMAP_FP64, float for MADMAP_FP32.
+ * y is overwritten.  n_rhs >= 1.  Excised pixels give 0. */
+madmap_status madmap_apply_ATNA(madmap_plan_t plan, int32_t precision, int32_t n_rhs,
+                                const void* x, void* y, void* stream);
+
+/* b = A^T N^-1 d (Eq. 10), the right-hand side.  d: device float [n_rhs][n_samples];
+ * b: device [n_rhs][n_obs][n_stokes] (double for FP64, float for FP32). */
+madmap_status madmap_rhs(madmap_plan_t plan, int32_t precision, int32_t n_rhs, const float* d,
+                         void* b, void* stream);
+
+/* w = N^-1 y on timestreams (Section 5.2, Eq. 15), interval by interval.
+ * y, w: device [n_rhs][n_samples], double for FP64, float for FP32. */
+madmap_status madmap_apply_ninv(madmap_plan_t plan, int32_t precision, int32_t n_rhs,
+                                const void* y, void* w, void* stream);
+
+/* ------------------------------------------------------------------ solves */
+
+void madmap_solve_opts_default(madmap_solve_opts* opts);
+
+/* PCG solve of H m = A^T N^-1 d (Section 4, Eq. 10; Section 5: x_0 = 0,
+ * stop at max_iter or relative residual rel_tol, return the iterate with the
+ * lowest relative residual).  d: device float [n_samples]; m: device double
+ * [n_obs][n_stokes].  opts/info may be NULL (defaults / not reported).
+ * Synchronises `stream` before returning.  Returns MADMAP_WARN_MAXITER when
+ * rel_tol was not reached (m is still the best iterate). */
+madmap_status madmap_solve(madmap_plan_t plan, const float* d, double* m, const madmap_solve_opts* opts,
+                           madmap_solve_info* info, void* stream);
+
+/* ------------------------------------------------------------------ host helpers */
+
+/* Inverse-noise filter lags from the PSD p(f) = sigma^2 (1 + (fknee/f)^alpha)
+ * (Section 4, Eq. 13).  The paper leaves the PSD-to-lag map unstated; this
+ * library samples 1/p on L = 4 n_lags frequencies nu_j = min(j, L-j) fs / L
+ * (the j = 0 bin takes the value of j = 1), inverse-DFTs, and applies a
+ * Bartlett taper 1 - tau/n_lags, which keeps every Toeplitz block positive
+ * definite.  lags_out: host [n_lags].  dlags_out: host [3][n_lags]
+ * (d/dsigma, d/dfknee, d/dalpha) or NULL.  Host only, synchronous. */
+madmap_status madmap_noise_filter(int32_t n_lags, double fs, double sigma, double fknee, double alpha,
+                                  double* lags_out, double* dlags_out);
+
+/* FFT length of Section 5.2: the smallest power of two above the longest
+ * interval, halved while h'(n_f) (Eq. 24) stays positive and n_f/2 > 2 n_c. */
+int64_t madmap_paper_fft_length(int64_t n_lags, int64_t longest_interval);
+
+/* Message of the last error on this thread ("" if none). */
+const char* madmap_last_error(void);
+
+/* Library version string. */
+const char* madmap_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MADMAP_H_ */

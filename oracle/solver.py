@@ -124,6 +124,34 @@ class System:
         """b = A^T N^-1 d (Eq. 10)."""
         return self.point(self.ninv(np.asarray(d, dtype=np.float64)))
 
+    def H_sampled(self, x, pixels):
+        """(H x)_p for a few observed pixels p, each computed on its own from Eq. 15.
+
+        For every sample t of pixel p: (N^-1 A x)_t = sum over |tau| < n_c inside
+        t's interval of f(|tau|) (A x)_{t+tau}; then weight and sum into p.  Used
+        to check full-size operator outputs one by one.
+        """
+        x = np.asarray(x, dtype=np.float64).reshape(self.n_obs, self.n_s)
+        out = np.zeros((len(pixels), self.n_s))
+        for k, p in enumerate(pixels):
+            ts = np.flatnonzero(self.pixl == p)
+            for t in ts:
+                i = int(np.searchsorted(self.offsets, t, side="right") - 1)
+                a, b = int(self.offsets[i]), int(self.offsets[i + 1])
+                lo, hi = max(a, t - self.n_c + 1), min(b, t + self.n_c)
+                sl = slice(lo, hi)
+                pl = self.pixl[sl]
+                ok = pl >= 0
+                w = None if self.w is None else self.w[sl]
+                ax = _pt.unpoint(x, pl, w)
+                f = self.lags[self.ivl_filter[i]][np.abs(np.arange(lo, hi) - t)]
+                v = float(np.sum(f[ok] * ax[ok]))
+                if self.w is None:
+                    out[k, 0] += v
+                else:
+                    out[k] += v * self.w[t]
+        return out
+
     def precond(self, r):
         return np.einsum("pab,pb->pa", self.Pinv, r)
 

@@ -1,0 +1,230 @@
+"""Python binding of libmadmap: the MADmap PCG map-making solve on GB300.
+
+Thin marshalling over the C ABI declared in ``include/madmap.h``: tensors are
+passed as device pointers on the caller's current CUDA stream; every step of
+the computation runs in the library's CUDA kernels.  PyTorch is used only for
+device memory and streams.
+
+    plan = Plan(pix, psi, n_pix, interval_offsets, interval_filter, filter_lags)
+    m, info = plan.solve(d, precision="mixed", rel_tol=1e-6)
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (MADMAP_FP32, MADMAP_FP64, MADMAP_MIXED, MadmapError, check, load)  # noqa: F401
+
+__all__ = ["Plan", "noise_filter", "paper_fft_length", "MadmapError", "load", "library_path",
+           "madmap_plan_create", "madmap_plan_destroy", "madmap_plan_get_stats", "madmap_plan_observed",
+           "madmap_plan_set_filters", "madmap_apply_ATNA", "madmap_rhs", "madmap_apply_ninv", "madmap_solve",
+           "madmap_noise_filter", "madmap_paper_fft_length", "madmap_last_error"]
+
+_PREC = {"fp64": MADMAP_FP64, "mixed": MADMAP_MIXED, "fp32": MADMAP_FP32,
+         MADMAP_FP64: MADMAP_FP64, MADMAP_MIXED: MADMAP_MIXED, MADMAP_FP32: MADMAP_FP32}
+
+
+def library_path() -> str:
+    return _lib.LIB_PATH
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+def _dev_ptr(t, dtype, what):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return t.data_ptr()
+
+
+# ----------------------------------------------------------------- C-ABI names
+def madmap_plan_create(desc, stream=None):
+    h = C.c_void_p()
+    check(load().madmap_plan_create(C.byref(desc), C.c_void_p(_stream_ptr(stream)), C.byref(h)),
+          "madmap_plan_create")
+    return h
+
+
+def madmap_plan_destroy(h):
+    check(load().madmap_plan_destroy(h), "madmap_plan_destroy")
+
+
+def madmap_plan_get_stats(h) -> dict:
+    s = _lib.madmap_plan_stats()
+    check(load().madmap_plan_get_stats(h, C.byref(s)), "madmap_plan_get_stats")
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def madmap_plan_observed(h, obs2glob_ptr=None, excised_ptr=None, stream=None) -> int:
+    n = C.c_int32()
+    check(load().madmap_plan_observed(h, C.byref(n), obs2glob_ptr, excised_ptr,
+                                      C.c_void_p(_stream_ptr(stream) if (obs2glob_ptr or excised_ptr) else 0)),
+          "madmap_plan_observed")
+    return n.value
+
+
+def madmap_plan_set_filters(h, lags: np.ndarray, stream=None):
+    lags = np.ascontiguousarray(lags, dtype=np.float64)
+    check(load().madmap_plan_set_filters(h, lags.ctypes.data, C.c_void_p(_stream_ptr(stream))),
+          "madmap_plan_set_filters")
+
+
+def madmap_apply_ATNA(h, precision, n_rhs, x_ptr, y_ptr, stream=None):
+    check(load().madmap_apply_ATNA(h, precision, n_rhs, x_ptr, y_ptr, C.c_void_p(_stream_ptr(stream))),
+          "madmap_apply_ATNA")
+
+
+def madmap_rhs(h, precision, n_rhs, d_ptr, b_ptr, stream=None):
+    check(load().madmap_rhs(h, precision, n_rhs, d_ptr, b_ptr, C.c_void_p(_stream_ptr(stream))), "madmap_rhs")
+
+
+def madmap_apply_ninv(h, precision, n_rhs, y_ptr, w_ptr, stream=None):
+    check(load().madmap_apply_ninv(h, precision, n_rhs, y_ptr, w_ptr, C.c_void_p(_stream_ptr(stream))),
+          "madmap_apply_ninv")
+
+
+def madmap_solve(h, d_ptr, m_ptr, opts, stream=None):
+    info = _lib.madmap_solve_info()
+    st = load().madmap_solve(h, d_ptr, m_ptr, C.byref(opts), C.byref(info), C.c_void_p(_stream_ptr(stream)))
+    check(st, "madmap_solve", allow_warn=True)
+    return info
+
+
+def madmap_noise_filter(n_lags, fs, sigma, fknee, alpha, with_grad=False):
+    lags = np.zeros(n_lags)
+    dl = np.zeros((3, n_lags)) if with_grad else None
+    check(load().madmap_noise_filter(n_lags, fs, sigma, fknee, alpha, lags.ctypes.data,
+                                     dl.ctypes.data if with_grad else None), "madmap_noise_filter")
+    return (lags, dl) if with_grad else lags
+
+
+def madmap_paper_fft_length(n_lags, longest) -> int:
+    return int(load().madmap_paper_fft_length(int(n_lags), int(longest)))
+
+
+def madmap_last_error() -> str:
+    return load().madmap_last_error().decode(errors="replace")
+
+
+noise_filter = madmap_noise_filter
+paper_fft_length = madmap_paper_fft_length
+
+
+# ----------------------------------------------------------------- convenience wrapper
+class Plan:
+    """A libmadmap plan over device-resident pointing.
+
+    pix: int32 CUDA tensor [n_t] (global pixel, -1 flagged); psi: float32 CUDA
+    tensor [n_t] or None (temperature); interval_offsets [n_ivl+1],
+    interval_filter [n_ivl] and filter_lags [n_filters, n_lags] are host arrays.
+    """
+
+    def __init__(self, pix, psi, n_pix, interval_offsets, interval_filter, filter_lags, rcond_excise=0.0,
+                 rcond_fp64=0.0, fft_len=0, tiles_per_chunk=0, stream=None):
+        torch = _torch()
+        self._h = None
+        off = np.ascontiguousarray(interval_offsets, dtype=np.int64)
+        filt = np.ascontiguousarray(interval_filter, dtype=np.int32)
+        lags = np.ascontiguousarray(np.atleast_2d(filter_lags), dtype=np.float64)
+        n_t = int(pix.numel())
+        d = _lib.madmap_plan_desc()
+        d.n_stokes = 1 if psi is None else 3
+        d.n_samples = n_t
+        d.n_pix = int(n_pix)
+        d.pix = _dev_ptr(pix, torch.int32, "pix") if n_t else None
+        d.psi = _dev_ptr(psi, torch.float32, "psi") if (psi is not None and n_t) else None
+        d.n_intervals = int(filt.shape[0])
+        d.interval_offsets = off.ctypes.data
+        d.interval_filter = filt.ctypes.data if filt.size else None
+        d.n_filters, d.n_lags = int(lags.shape[0]), int(lags.shape[1])
+        d.filter_lags = lags.ctypes.data
+        d.rcond_excise, d.rcond_fp64 = float(rcond_excise), float(rcond_fp64)
+        d.fft_len, d.tiles_per_chunk = int(fft_len), int(tiles_per_chunk)
+        self._keep = (off, filt, lags)
+        self._h = madmap_plan_create(d, stream)
+        self.n_stokes = d.n_stokes
+        self.n_samples = n_t
+        self.stats = madmap_plan_get_stats(self._h)
+        self.n_obs = self.stats["n_obs"]
+
+    def close(self):
+        if self._h is not None:
+            madmap_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def observed(self, stream=None):
+        """(obs2glob int32, excised uint8) CUDA tensors over the observed pixels."""
+        torch = _torch()
+        o = torch.empty(max(self.n_obs, 1), dtype=torch.int32, device="cuda")
+        e = torch.empty(max(self.n_obs, 1), dtype=torch.uint8, device="cuda")
+        madmap_plan_observed(self._h, o.data_ptr(), e.data_ptr(), stream)
+        return o[:self.n_obs], e[:self.n_obs]
+
+    def set_filters(self, filter_lags, stream=None):
+        madmap_plan_set_filters(self._h, np.atleast_2d(filter_lags), stream)
+
+    def _map_shape(self, n_rhs):
+        return (n_rhs, self.n_obs, self.n_stokes)
+
+    def apply_ATNA(self, x, precision="fp64", stream=None):
+        torch = _torch()
+        prec = _PREC[precision]
+        dt = torch.float64 if prec == MADMAP_FP64 else torch.float32
+        x = x.reshape(-1, self.n_obs, self.n_stokes)
+        y = torch.empty_like(x)
+        madmap_apply_ATNA(self._h, prec, x.shape[0], _dev_ptr(x, dt, "x"), y.data_ptr(), stream)
+        return y
+
+    def rhs(self, d, precision="fp64", stream=None):
+        torch = _torch()
+        prec = _PREC[precision]
+        d = d.reshape(-1, self.n_samples)
+        b = torch.empty(self._map_shape(d.shape[0]), dtype=torch.float64 if prec == MADMAP_FP64 else torch.float32,
+                        device=d.device)
+        madmap_rhs(self._h, prec, d.shape[0], _dev_ptr(d, torch.float32, "d"), b.data_ptr(), stream)
+        return b
+
+    def apply_ninv(self, y, precision="fp64", stream=None):
+        torch = _torch()
+        prec = _PREC[precision]
+        dt = torch.float64 if prec == MADMAP_FP64 else torch.float32
+        y = y.reshape(-1, self.n_samples)
+        w = torch.empty_like(y)
+        madmap_apply_ninv(self._h, prec, y.shape[0], _dev_ptr(y, dt, "y"), w.data_ptr(), stream)
+        return w
+
+    def solve(self, d, precision="fp64", max_iter=50, rel_tol=1e-6, max_outer=10, inner_rel_tol=1e-4,
+              use_graph=True, iters_per_sync=8, out=None, stream=None):
+        """Maximum-likelihood map [n_obs, n_stokes] (float64) and the solve info dict."""
+        torch = _torch()
+        o = _lib.madmap_solve_opts()
+        o.max_iter, o.rel_tol, o.precision = int(max_iter), float(rel_tol), _PREC[precision]
+        o.max_outer, o.inner_rel_tol = int(max_outer), float(inner_rel_tol)
+        o.use_graph, o.iters_per_sync = int(bool(use_graph)), int(iters_per_sync)
+        m = out if out is not None else torch.empty((self.n_obs, self.n_stokes), dtype=torch.float64,
+                                                    device="cuda")
+        info = madmap_solve(self._h, _dev_ptr(d.reshape(-1), torch.float32, "d"), _dev_ptr(m, torch.float64, "m"),
+                            o, stream)
+        return m, {k: getattr(info, k) for k, _ in info._fields_}

@@ -1,0 +1,754 @@
+// Plan construction: validation, observed-pixel indexing (Section 5.4), pixel
+// classification and block preconditioner (Sections 4-5), overlap-save
+// windows and filter spectra (Section 5.2), and the host-side helpers of the
+// C ABI (errors, noise-filter lags, the paper's FFT-length rule).
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace mm {
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+madmap_status cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string("CUDA error ") + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ") in " + what;
+  if (e == cudaErrorMemoryAllocation) return MADMAP_ERR_OOM;
+  return MADMAP_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- allocation
+// MADMAP_FAULT_ALLOC_FAIL_AT=n makes the n-th device allocation of the process
+// (counting from 1) report out-of-memory, so callers' error paths can be
+// tested on the host without exhausting a shared GPU.
+static long long g_alloc_count = 0;
+
+madmap_status dalloc(Plan* p, void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  ++g_alloc_count;
+  const char* inj = getenv("MADMAP_FAULT_ALLOC_FAIL_AT");
+  if (inj && atoll(inj) == g_alloc_count) {
+    set_error("injected allocation failure (MADMAP_FAULT_ALLOC_FAIL_AT)");
+    return MADMAP_ERR_OOM;
+  }
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return cuda_fail(e, "cudaMalloc");
+  }
+  p->allocs.push_back(*ptr);
+  p->device_bytes += bytes;
+  return MADMAP_OK;
+}
+
+void free_solve_buffers(Plan* p);  // solver.cu
+
+Plan::~Plan() {
+  free_solve_buffers(this);
+  if (solve_event) cudaEventDestroy(solve_event);
+  if (solve_stream) cudaStreamDestroy(solve_stream);
+  for (void* a : allocs) cudaFree(a);
+}
+
+// ---------------------------------------------------------------- host FFT
+// Iterative radix-2 Cooley-Tukey, float64; length must be a power of two.
+void host_fft(std::vector<double>& re, std::vector<double>& im, bool inverse) {
+  const size_t n = re.size();
+  for (size_t i = 1, j = 0; i < n; ++i) {
+    size_t bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) {
+      std::swap(re[i], re[j]);
+      std::swap(im[i], im[j]);
+    }
+  }
+  const double sgn = inverse ? 1.0 : -1.0;
+  for (size_t len = 2; len <= n; len <<= 1) {
+    const size_t half = len >> 1;
+    std::vector<double> wr(half), wi(half);
+    for (size_t k = 0; k < half; ++k) {
+      const double ang = 2.0 * M_PI * (double)k / (double)len;
+      wr[k] = cos(ang);
+      wi[k] = sgn * sin(ang);
+    }
+    for (size_t i = 0; i < n; i += len) {
+      for (size_t k = 0; k < half; ++k) {
+        const size_t a = i + k, b = a + half;
+        const double xr = re[b] * wr[k] - im[b] * wi[k];
+        const double xi = re[b] * wi[k] + im[b] * wr[k];
+        re[b] = re[a] - xr;
+        im[b] = im[a] - xi;
+        re[a] += xr;
+        im[a] += xi;
+      }
+    }
+  }
+}
+
+static bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// ---------------------------------------------------------------- noise filter
+// Inverse DFT of an even real sequence q of length L, first n outputs.
+static void even_idft(const std::vector<double>& q, int n, double* out) {
+  const size_t L = q.size();
+  if (is_pow2((long long)L)) {
+    std::vector<double> re(q), im(L, 0.0);
+    host_fft(re, im, true);
+    for (int t = 0; t < n; ++t) out[t] = re[t] / (double)L;
+  } else {
+    for (int t = 0; t < n; ++t) {
+      double acc = 0.0;
+      for (size_t j = 0; j < L; ++j) acc += q[j] * cos(2.0 * M_PI * (double)((j * (size_t)t) % L) / (double)L);
+      out[t] = acc / (double)L;
+    }
+  }
+}
+
+}  // namespace mm
+
+using namespace mm;
+
+extern "C" madmap_status madmap_noise_filter(int32_t n_lags, double fs, double sigma, double fknee,
+                                             double alpha, double* lags_out, double* dlags_out) {
+  MM_CHECK(n_lags >= 1 && lags_out, MADMAP_ERR_INVALID_ARG, "noise_filter: n_lags >= 1 and lags_out required");
+  MM_CHECK(fs > 0 && sigma > 0 && fknee >= 0 && isfinite(alpha), MADMAP_ERR_INVALID_ARG,
+           "noise_filter: need fs > 0, sigma > 0, fknee >= 0, finite alpha");
+  const int L = 4 * n_lags;
+  std::vector<double> nu(L), q(L);
+  for (int j = 0; j < L; ++j) nu[j] = (double)std::min(j, L - j) * fs / (double)L;
+  nu[0] = nu[1];
+  for (int j = 0; j < L; ++j) q[j] = 1.0 / (sigma * sigma * (1.0 + pow(fknee / nu[j], alpha)));
+  std::vector<double> c(n_lags);
+  even_idft(q, n_lags, c.data());
+  for (int t = 0; t < n_lags; ++t) lags_out[t] = (1.0 - (double)t / n_lags) * c[t];
+  if (dlags_out) {
+    std::vector<double> dq(L);
+    for (int k = 0; k < 3; ++k) {
+      for (int j = 0; j < L; ++j) {
+        const double r = pow(fknee / nu[j], alpha);
+        if (k == 0) dq[j] = -2.0 * q[j] / sigma;
+        else if (k == 1) dq[j] = fknee > 0 ? -q[j] * q[j] * sigma * sigma * alpha * r / fknee : 0.0;
+        else dq[j] = fknee > 0 ? -q[j] * q[j] * sigma * sigma * r * log(fknee / nu[j]) : 0.0;
+      }
+      even_idft(dq, n_lags, c.data());
+      for (int t = 0; t < n_lags; ++t) dlags_out[k * n_lags + t] = (1.0 - (double)t / n_lags) * c[t];
+    }
+  }
+  return MADMAP_OK;
+}
+
+static double hprime(double nf, double nc) {
+  return (1.0 + log(nf)) / (nf - 2 * nc) - nf * log(nf) / ((nf - 2 * nc) * (nf - 2 * nc));
+}
+
+extern "C" int64_t madmap_paper_fft_length(int64_t n_lags, int64_t longest) {
+  int64_t nf = 1;
+  while (nf <= longest) nf *= 2;
+  while (nf <= 2 * n_lags) nf *= 2;
+  if (hprime((double)nf, (double)n_lags) > 0) {
+    while (nf / 2 > 2 * n_lags && hprime((double)(nf / 2), (double)n_lags) >= 0) nf /= 2;
+  }
+  return nf;
+}
+
+extern "C" const char* madmap_last_error(void) { return g_err.c_str(); }
+extern "C" const char* madmap_version(void) { return "madmap-gb300 0.1"; }
+
+namespace mm {
+
+// ---------------------------------------------------------------- plan kernels
+__global__ void k_validate_pix(const int* pix, long long n, int n_pix, int* bad) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int g = pix[t];
+    if (g < -1 || g >= n_pix) atomicOr(bad, 1);
+  }
+}
+
+__global__ void k_validate_psi(const float* psi, long long n, int* bad) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    if (!isfinite(psi[t])) atomicOr(bad, 2);
+  }
+}
+
+// Section 5.4: one bit per global pixel, set when a sample observes it.
+__global__ void k_mark_bits(const int* pix, long long n, int n_pix, unsigned* bits) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int g = pix[t];
+    if (g >= 0 && g < n_pix) atomicOr(bits + (g >> 5), 1u << (g & 31));
+  }
+}
+
+// Exclusive prefix of popcounts over the bit words (single block of 1024).
+__global__ void __launch_bounds__(1024) k_scan_words(const unsigned* bits, int n_words, int* prefix, int* total) {
+  __shared__ int part[1024];
+  const int tid = threadIdx.x;
+  const int chunk = (n_words + 1023) / 1024;
+  const int b = tid * chunk, e = min(n_words, b + chunk);
+  int acc = 0;
+  for (int w = b; w < e; ++w) acc += __popc(bits[w]);
+  part[tid] = acc;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const int v = tid >= off ? part[tid - off] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  int run = part[tid] - acc;
+  for (int w = b; w < e; ++w) {
+    prefix[w] = run;
+    run += __popc(bits[w]);
+  }
+  if (tid == 1023) *total = part[1023];
+}
+
+__device__ __forceinline__ int rank_of(const unsigned* bits, const int* prefix, int g) {
+  const unsigned w = bits[g >> 5];
+  return prefix[g >> 5] + __popc(w & ((1u << (g & 31)) - 1u));
+}
+
+__global__ void k_obs2glob(const unsigned* bits, const int* prefix, int n_pix, int* obs2glob) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_pix; g += gridDim.x * blockDim.x) {
+    if (bits[g >> 5] & (1u << (g & 31))) obs2glob[rank_of(bits, prefix, g)] = g;
+  }
+}
+
+__global__ void k_pix_obs(const int* pix, long long n, int n_pix, const unsigned* bits, const int* prefix,
+                          int* pix_obs) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int g = pix[t];
+    pix_obs[t] = (g < 0 || g >= n_pix) ? -1 : rank_of(bits, prefix, g);
+  }
+}
+
+__device__ __forceinline__ int interval_of(const long long* off, int n_ivl, long long t) {
+  int lo = 0, hi = n_ivl;  // find i with off[i] <= t < off[i+1]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= t) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Per-pixel sums for the preconditioner (Section 5): hits, A^T A and
+// A^T W^-1 A with W^-1 = diag(N^-1), i.e. each sample weighted by f(0) of its
+// interval's filter.  Also stores (cos 2psi, sin 2psi) in float64 for the FP64
+// operator.  acc layout per pixel: T: [wsum]; IQU: [6 AtA | 6 AtWA].
+__global__ void k_accumulate(const int* pix_obs, const float* psi, long long n, const long long* off, int n_ivl,
+                             const int* ivl_filter, const double* f0, int ns, double* acc, int* hits,
+                             double2* cs64) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double c = 1.0, s = 0.0;
+    if (ns == 3) {
+      sincos(2.0 * (double)psi[t], &s, &c);
+      cs64[t] = make_double2(c, s);
+    }
+    const int p = pix_obs[t];
+    if (p < 0) continue;
+    const double w0 = f0[ivl_filter[interval_of(off, n_ivl, t)]];
+    atomicAdd(hits + p, 1);
+    if (ns == 1) {
+      atomicAdd(acc + p, w0);
+    } else {
+      double* a = acc + 12LL * p;
+      const double v[6] = {1.0, c, s, c * c, c * s, s * s};
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        atomicAdd(a + k, v[k]);
+        atomicAdd(a + 6 + k, w0 * v[k]);
+      }
+    }
+  }
+}
+
+// Eigenvalues of a symmetric 3x3 matrix by the trigonometric closed form
+// (O. K. Smith, "Eigenvalues of a symmetric 3x3 matrix", CACM 4, 1961).
+__device__ void sym3_eig(double a00, double a01, double a02, double a11, double a12, double a22, double& lmin,
+                         double& lmax) {
+  const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
+  if (p1 == 0.0) {
+    lmin = fmin(a00, fmin(a11, a22));
+    lmax = fmax(a00, fmax(a11, a22));
+    return;
+  }
+  const double q = (a00 + a11 + a22) / 3.0;
+  const double b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+  const double p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0 * p1;
+  const double p = sqrt(p2 / 6.0);
+  const double ip = 1.0 / p;
+  const double c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip, c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
+  const double det = c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) + c02 * (c01 * c12 - c11 * c02);
+  double r = 0.5 * det;
+  r = fmin(1.0, fmax(-1.0, r));
+  const double phi = acos(r) / 3.0;
+  lmax = q + 2.0 * p * cos(phi);
+  lmin = q + 2.0 * p * cos(phi + 2.0 * M_PI / 3.0);
+}
+
+// Classify observed pixels (IQU: excise when hits < 3 or rcond(A^T A) is
+// below rcond_excise; flag float64 blocks below rcond_fp64) and invert the
+// (A^T W^-1 A) blocks in float64.
+__global__ void k_classify(const double* acc, const int* hits, int n_obs, int ns, double rc_ex, double rc_64,
+                           double* P64, float* P32, unsigned char* excised, unsigned char* fp64flag, int* counts) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_obs; p += gridDim.x * blockDim.x) {
+    if (ns == 1) {
+      const bool ex = hits[p] == 0 || !(acc[p] > 0.0);
+      const double inv = ex ? 0.0 : 1.0 / acc[p];
+      P64[p] = inv;
+      P32[p] = (float)inv;
+      excised[p] = ex;
+      fp64flag[p] = 0;
+      if (ex) atomicAdd(counts, 1);
+      continue;
+    }
+    const double* a = acc + 12LL * p;
+    double lmin = 0.0, lmax = 0.0;
+    sym3_eig(a[0], a[1], a[2], a[3], a[4], a[5], lmin, lmax);
+    const double rc = lmax > 0.0 ? lmin / lmax : 0.0;
+    bool ex = hits[p] < 3 || !(rc >= rc_ex);
+    // inverse of the weighted block by cofactors
+    const double m00 = a[6], m01 = a[7], m02 = a[8], m11 = a[9], m12 = a[10], m22 = a[11];
+    const double A00 = m11 * m22 - m12 * m12, A01 = m02 * m12 - m01 * m22, A02 = m01 * m12 - m02 * m11;
+    const double A11 = m00 * m22 - m02 * m02, A12 = m01 * m02 - m00 * m12, A22 = m00 * m11 - m01 * m01;
+    const double det = m00 * A00 + m01 * A01 + m02 * A02;
+    if (!(det > 0.0)) ex = true;
+    const double id = ex ? 0.0 : 1.0 / det;
+    const double inv[6] = {A00 * id, A01 * id, A02 * id, A11 * id, A12 * id, A22 * id};
+    for (int k = 0; k < 6; ++k) {
+      P64[6LL * p + k] = inv[k];
+      P32[8LL * p + k] = (float)inv[k];
+    }
+    P32[8LL * p + 6] = 0.f;
+    P32[8LL * p + 7] = 0.f;
+    excised[p] = ex;
+    const bool f64 = !ex && rc < rc_64;
+    fp64flag[p] = f64;
+    if (ex) atomicAdd(counts, 1);
+    if (f64) atomicAdd(counts + 1, 1);
+  }
+}
+
+// Rows of A observing excised pixels become zero (Section 4, gap filling).
+__global__ void k_zero_excised_rows(int* pix_obs, long long n, const unsigned char* excised) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int p = pix_obs[t];
+    if (p >= 0 && excised[p]) pix_obs[t] = -1;
+  }
+}
+
+static int grid_for(long long n, int threads = 256) {
+  long long g = (n + threads - 1) / threads;
+  if (g > 152LL * 32) g = 152LL * 32;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// ---------------------------------------------------------------- windows and tiles
+struct Seg {
+  long long ws, lo, hi;
+  int out_lo, out_hi, filter;
+};
+
+static void make_segments(const std::vector<long long>& off, const std::vector<int>& filt, int n_lags, int M,
+                          std::vector<Seg>& segs) {
+  segs.clear();
+  const long long h = n_lags - 1;
+  const long long U = M - 2 * h;
+  for (size_t i = 0; i + 1 < off.size(); ++i) {
+    const long long t0 = off[i], t1 = off[i + 1], n = t1 - t0;
+    if (n <= 0) continue;
+    if (n + h <= M) {
+      segs.push_back({t0, t0, t1, 0, (int)n, filt[i]});
+      continue;
+    }
+    for (long long u0 = t0; u0 < t1; u0 += U) {
+      const long long u1 = std::min(t1, u0 + U);
+      const long long ws = u0 - h;
+      segs.push_back({ws, std::max(t0, ws), std::min(t1, ws + M), (int)h, (int)(h + u1 - u0), filt[i]});
+    }
+  }
+}
+
+static void pair_tiles(const std::vector<Seg>& segs, int n_filters, std::vector<Tile>& tiles) {
+  tiles.clear();
+  for (int f = 0; f < n_filters; ++f) {
+    std::vector<const Seg*> mine;
+    for (const Seg& s : segs)
+      if (s.filter == f) mine.push_back(&s);
+    for (size_t k = 0; k < mine.size(); k += 2) {
+      Tile T;
+      memset(&T, 0, sizeof(T));
+      T.filter = f;
+      for (int l = 0; l < 2; ++l) {
+        Lane& L = T.l[l];
+        if (k + l < mine.size()) {
+          const Seg* s = mine[k + l];
+          L.ws = s->ws;
+          L.lo = s->lo;
+          L.hi = s->hi;
+          L.out_lo = s->out_lo;
+          L.out_hi = s->out_hi;
+        } else {
+          L.ws = 0;
+          L.lo = 0;
+          L.hi = 0;
+          L.out_lo = 0;
+          L.out_hi = 0;
+        }
+        L.rhs = 0;
+      }
+      tiles.push_back(T);
+    }
+  }
+}
+
+// Autotuning model for the FFT length: work ~ tiles * M * (log2 M + c), where
+// c stands for the gather/scatter and memory passes per complex element.
+static int choose_fft_len(const std::vector<long long>& off, const std::vector<int>& filt, int n_filters,
+                          int n_lags) {
+  double best = 1e300;
+  int bestM = 0;
+  std::vector<Seg> segs;
+  std::vector<Tile> tiles;
+  for (int lg = 8; lg <= 20; ++lg) {
+    const int M = 1 << lg;
+    if (M - 2 * (n_lags - 1) < 1) continue;
+    make_segments(off, filt, n_lags, M, segs);
+    pair_tiles(segs, n_filters, tiles);
+    const double cost = (double)tiles.size() * (double)M * (lg + 8.0) + 1.0 * M;
+    if (cost < best) {
+      best = cost;
+      bestM = M;
+    }
+  }
+  return bestM;
+}
+
+static madmap_status build_spectra(Plan* p) {
+  const int M = p->M;
+  std::vector<double> h64((size_t)p->n_filters * M);
+  std::vector<float> h32((size_t)p->n_filters * M);
+  std::vector<double> re(M), im(M);
+  for (int f = 0; f < p->n_filters; ++f) {
+    std::fill(re.begin(), re.end(), 0.0);
+    std::fill(im.begin(), im.end(), 0.0);
+    const double* lg = &p->lags[(size_t)f * p->n_lags];
+    re[0] = lg[0];
+    for (int t = 1; t < p->n_lags; ++t) {
+      re[t] += lg[t];
+      re[M - t] += lg[t];
+    }
+    host_fft(re, im, false);
+    double mn = 1e300;
+    for (int k = 0; k < M; ++k) mn = std::min(mn, re[k]);
+    if (!(mn > 0.0)) {
+      set_error("filter " + std::to_string(f) + " is not positive definite (circulant symbol minimum " +
+                std::to_string(mn) + ")");
+      return MADMAP_ERR_NOT_PD;
+    }
+    for (int pos2 = 0; pos2 < p->N2; ++pos2) {
+      int k2 = 0;
+      for (int b = 0; b < p->logN2; ++b) k2 |= ((pos2 >> b) & 1) << (p->logN2 - 1 - b);
+      for (int pos1 = 0; pos1 < p->N1; ++pos1) {
+        int k1 = 0;
+        for (int b = 0; b < p->logN1; ++b) k1 |= ((pos1 >> b) & 1) << (p->logN1 - 1 - b);
+        const double v = re[k2 + (size_t)p->N2 * k1] / (double)M;
+        h64[(size_t)f * M + (size_t)pos2 * p->N1 + pos1] = v;
+        h32[(size_t)f * M + (size_t)pos2 * p->N1 + pos1] = (float)v;
+      }
+    }
+  }
+  MM_CUDA(cudaMemcpy(p->H64, h64.data(), h64.size() * sizeof(double), cudaMemcpyHostToDevice));
+  MM_CUDA(cudaMemcpy(p->H32, h32.data(), h32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  return MADMAP_OK;
+}
+
+static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
+  const long long n = p->n_t;
+  const int n_obs = p->n_obs;
+  const int ns = p->n_stokes;
+  double* acc = nullptr;
+  int* hits = nullptr;
+  long long* doff = nullptr;
+  int* dfilt = nullptr;
+  double* df0 = nullptr;
+  int* counts = nullptr;
+  // temporaries (freed at the end)
+  MM_CUDA(cudaMalloc(&acc, sizeof(double) * (size_t)std::max(1, n_obs) * (ns == 1 ? 1 : 12)));
+  madmap_status st = MADMAP_OK;
+  auto cleanup = [&]() {
+    cudaFree(acc);
+    cudaFree(hits);
+    cudaFree(doff);
+    cudaFree(dfilt);
+    cudaFree(df0);
+    cudaFree(counts);
+  };
+  cudaError_t e = cudaSuccess;
+  std::vector<double> f0(p->n_filters);
+  for (int f = 0; f < p->n_filters; ++f) f0[f] = p->lags[(size_t)f * p->n_lags];
+  if ((e = cudaMalloc(&hits, sizeof(int) * (size_t)std::max(1, n_obs))) != cudaSuccess ||
+      (e = cudaMalloc(&doff, sizeof(long long) * (p->n_ivl + 1))) != cudaSuccess ||
+      (e = cudaMalloc(&dfilt, sizeof(int) * std::max(1, p->n_ivl))) != cudaSuccess ||
+      (e = cudaMalloc(&df0, sizeof(double) * p->n_filters)) != cudaSuccess ||
+      (e = cudaMalloc(&counts, sizeof(int) * 2)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "cudaMalloc (preconditioner temporaries)");
+  }
+  cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)std::max(1, n_obs) * (ns == 1 ? 1 : 12), s);
+  cudaMemsetAsync(hits, 0, sizeof(int) * (size_t)std::max(1, n_obs), s);
+  cudaMemsetAsync(counts, 0, sizeof(int) * 2, s);
+  cudaMemcpyAsync(doff, p->offsets.data(), sizeof(long long) * (p->n_ivl + 1), cudaMemcpyHostToDevice, s);
+  if (p->n_ivl) cudaMemcpyAsync(dfilt, p->ivl_filter.data(), sizeof(int) * p->n_ivl, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(df0, f0.data(), sizeof(double) * p->n_filters, cudaMemcpyHostToDevice, s);
+  if (n > 0)
+    k_accumulate<<<grid_for(n), 256, 0, s>>>(p->pix_obs, p->psi, n, doff, p->n_ivl, dfilt, df0, ns, acc, hits,
+                                              p->cs64);
+  if (n_obs > 0)
+    k_classify<<<grid_for(n_obs), 256, 0, s>>>(acc, hits, n_obs, ns, p->rcond_excise, p->rcond_fp64, p->P64,
+                                                p->P32, p->excised, p->fp64flag, counts);
+  if (n > 0) k_zero_excised_rows<<<grid_for(n), 256, 0, s>>>(p->pix_obs, n, p->excised);
+  int hc[2] = {0, 0};
+  e = cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "preconditioner build");
+  p->n_excised = hc[0];
+  p->n_fp64 = hc[1];
+  return st;
+}
+
+}  // namespace mm
+
+// ---------------------------------------------------------------- C ABI
+extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* stream, madmap_plan_t* out) {
+  MM_CHECK(out != nullptr, MADMAP_ERR_INVALID_ARG, "plan_create: out is NULL");
+  *out = nullptr;
+  MM_CHECK(d != nullptr, MADMAP_ERR_INVALID_ARG, "plan_create: desc is NULL");
+  MM_CHECK(d->n_stokes == 1 || d->n_stokes == 3, MADMAP_ERR_INVALID_ARG, "n_stokes must be 1 or 3");
+  MM_CHECK(d->n_samples >= 0 && d->n_samples < (1LL << 40), MADMAP_ERR_INVALID_ARG, "bad n_samples");
+  MM_CHECK(d->n_pix > 0, MADMAP_ERR_INVALID_ARG, "n_pix must be > 0");
+  MM_CHECK(d->n_samples == 0 || d->pix != nullptr, MADMAP_ERR_INVALID_ARG, "pix is NULL");
+  MM_CHECK((d->n_stokes == 1) == (d->psi == nullptr) || d->n_samples == 0, MADMAP_ERR_INVALID_ARG,
+           "psi must be NULL for T and non-NULL for IQU");
+  MM_CHECK(d->n_intervals >= 0 && d->interval_offsets != nullptr, MADMAP_ERR_INVALID_ARG, "bad intervals");
+  MM_CHECK(d->n_intervals == 0 || d->interval_filter != nullptr, MADMAP_ERR_INVALID_ARG, "interval_filter NULL");
+  MM_CHECK(d->n_filters >= 1 && d->n_lags >= 1 && d->filter_lags != nullptr, MADMAP_ERR_INVALID_ARG,
+           "need n_filters >= 1, n_lags >= 1 and filter_lags");
+  MM_CHECK(d->n_lags <= (1 << 18), MADMAP_ERR_INVALID_ARG, "n_lags too large (max 2^18)");
+  const int64_t* off = d->interval_offsets;
+  MM_CHECK(off[0] == 0 && off[d->n_intervals] == d->n_samples, MADMAP_ERR_INVALID_ARG,
+           "interval_offsets must start at 0 and end at n_samples");
+  for (int i = 0; i < d->n_intervals; ++i) {
+    MM_CHECK(off[i + 1] >= off[i], MADMAP_ERR_INVALID_ARG, "interval_offsets must be non-decreasing");
+    MM_CHECK(d->interval_filter[i] >= 0 && d->interval_filter[i] < d->n_filters, MADMAP_ERR_INVALID_ARG,
+             "interval_filter out of range");
+  }
+  for (long long k = 0; k < (long long)d->n_filters * d->n_lags; ++k)
+    MM_CHECK(isfinite(d->filter_lags[k]), MADMAP_ERR_INVALID_ARG, "filter_lags must be finite");
+  if (d->fft_len != 0) {
+    MM_CHECK(is_pow2(d->fft_len) && d->fft_len >= 256 && d->fft_len <= (1 << 20) &&
+                 d->fft_len > 2 * (d->n_lags - 1),
+             MADMAP_ERR_INVALID_ARG, "fft_len must be a power of two in [256, 2^20] above 2 (n_lags - 1)");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Plan* p = new Plan();
+  p->n_stokes = d->n_stokes;
+  p->ns_pad = d->n_stokes == 1 ? 1 : 4;
+  p->n_t = d->n_samples;
+  p->n_pix = d->n_pix;
+  p->n_ivl = d->n_intervals;
+  p->n_filters = d->n_filters;
+  p->n_lags = d->n_lags;
+  p->rcond_excise = d->rcond_excise > 0 ? d->rcond_excise : 1e-6;
+  p->rcond_fp64 = d->rcond_fp64 > 0 ? d->rcond_fp64 : 1e-2;
+  p->offsets.assign(off, off + d->n_intervals + 1);
+  p->ivl_filter.assign(d->interval_filter, d->interval_filter + d->n_intervals);
+  p->lags.assign(d->filter_lags, d->filter_lags + (size_t)d->n_filters * d->n_lags);
+  madmap_status st = MADMAP_OK;
+#define MM_TRY(x)                 \
+  do {                            \
+    st = (x);                     \
+    if (st != MADMAP_OK) {        \
+      delete p;                   \
+      return st;                  \
+    }                             \
+  } while (0)
+#define MM_TRYC(x) MM_TRY(((x) == cudaSuccess) ? MADMAP_OK : cuda_fail(cudaGetLastError(), #x))
+  const long long n = p->n_t;
+  const int n_words = (p->n_pix + 31) / 32;
+  unsigned* bits = nullptr;
+  int* prefix = nullptr;
+  int* total = nullptr;
+  MM_TRY(dalloc_t(p, &p->dev_flag, 16));
+  MM_TRY(dalloc_t(p, &bits, n_words));
+  MM_TRY(dalloc_t(p, &prefix, n_words));
+  MM_TRY(dalloc_t(p, &total, 1));
+  MM_TRY(dalloc_t(p, &p->pix_obs, std::max(1LL, n)));
+  if (p->n_stokes == 3) {
+    MM_TRY(dalloc_t(p, &p->psi, std::max(1LL, n)));
+    MM_TRY(dalloc_t(p, &p->cs64, std::max(1LL, n)));
+  }
+  MM_TRYC(cudaMemsetAsync(p->dev_flag, 0, 16 * sizeof(int), s));
+  MM_TRYC(cudaMemsetAsync(bits, 0, sizeof(unsigned) * n_words, s));
+  if (n > 0) {
+    k_validate_pix<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, p->dev_flag);
+    if (p->n_stokes == 3) {
+      MM_TRYC(cudaMemcpyAsync(p->psi, d->psi, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+      k_validate_psi<<<grid_for(n), 256, 0, s>>>(p->psi, n, p->dev_flag);
+    }
+    k_mark_bits<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, bits);
+  }
+  k_scan_words<<<1, 1024, 0, s>>>(bits, n_words, prefix, total);
+  int hv[2] = {0, 0};
+  MM_TRYC(cudaMemcpyAsync(&hv[0], p->dev_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MM_TRYC(cudaMemcpyAsync(&hv[1], total, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MM_TRYC(cudaStreamSynchronize(s));
+  MM_TRYC(cudaGetLastError());
+  if (hv[0] & 1) {
+    delete p;
+    set_error("pix holds values outside [-1, n_pix)");
+    return MADMAP_ERR_INVALID_ARG;
+  }
+  if (hv[0] & 2) {
+    delete p;
+    set_error("psi holds non-finite values");
+    return MADMAP_ERR_INVALID_ARG;
+  }
+  p->n_obs = hv[1];
+  const int n_obs = p->n_obs;
+  MM_TRY(dalloc_t(p, &p->obs2glob, std::max(1, n_obs)));
+  MM_TRY(dalloc_t(p, &p->excised, std::max(1, n_obs)));
+  MM_TRY(dalloc_t(p, &p->fp64flag, std::max(1, n_obs)));
+  MM_TRY(dalloc_t(p, &p->P64, (size_t)std::max(1, n_obs) * (p->n_stokes == 1 ? 1 : 6)));
+  MM_TRY(dalloc_t(p, &p->P32, (size_t)std::max(1, n_obs) * (p->n_stokes == 1 ? 1 : 8)));
+  k_obs2glob<<<grid_for(p->n_pix), 256, 0, s>>>(bits, prefix, p->n_pix, p->obs2glob);
+  if (n > 0) k_pix_obs<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, bits, prefix, p->pix_obs);
+  MM_TRY(build_preconditioner(p, s));
+  // FFT geometry and windows
+  p->M = d->fft_len ? d->fft_len : choose_fft_len(p->offsets, p->ivl_filter, p->n_filters, p->n_lags);
+  if (p->M <= 0) {
+    delete p;
+    set_error("no FFT length up to 2^20 fits n_lags");
+    return MADMAP_ERR_INVALID_ARG;
+  }
+  {
+    const int lg = ilog2((unsigned)p->M);
+    p->logN2 = (lg + 1) / 2;
+    p->logN1 = lg - p->logN2;
+    p->N1 = 1 << p->logN1;
+    p->N2 = 1 << p->logN2;
+  }
+  std::vector<Seg> segs;
+  make_segments(p->offsets, p->ivl_filter, p->n_lags, p->M, segs);
+  pair_tiles(segs, p->n_filters, p->host_tiles);
+  p->n_segments = (int)segs.size();
+  p->n_tiles = (int)p->host_tiles.size();
+  {
+    long long tpc = d->tiles_per_chunk > 0 ? d->tiles_per_chunk : (32LL << 20) / (8LL * p->M);
+    tpc = std::max(1LL, std::min<long long>(tpc, std::max(1, p->n_tiles)));
+    tpc = std::min<long long>(tpc, 65535);
+    p->tiles_per_chunk = (int)tpc;
+  }
+  MM_TRY(dalloc_t(p, &p->tiles, std::max(1, p->n_tiles)));
+  if (p->n_tiles)
+    MM_TRYC(cudaMemcpy(p->tiles, p->host_tiles.data(), sizeof(Tile) * p->n_tiles, cudaMemcpyHostToDevice));
+  MM_TRY(dalloc_t(p, &p->H64, (size_t)p->n_filters * p->M));
+  MM_TRY(dalloc_t(p, &p->H32, (size_t)p->n_filters * p->M));
+  MM_TRY(build_spectra(p));
+  {
+    std::vector<double2> t64(p->M);
+    std::vector<float2> t32(p->M);
+    for (int j = 0; j < p->M; ++j) {
+      const double ang = 2.0 * M_PI * (double)j / (double)p->M;
+      t64[j] = make_double2(cos(ang), -sin(ang));
+      t32[j] = make_float2((float)t64[j].x, (float)t64[j].y);
+    }
+    MM_TRY(dalloc_t(p, &p->tw64, p->M));
+    MM_TRY(dalloc_t(p, &p->tw32, p->M));
+    MM_TRYC(cudaMemcpy(p->tw64, t64.data(), sizeof(double2) * p->M, cudaMemcpyHostToDevice));
+    MM_TRYC(cudaMemcpy(p->tw32, t32.data(), sizeof(float2) * p->M, cudaMemcpyHostToDevice));
+  }
+  MM_TRY(dalloc(p, &p->scratch, (size_t)p->tiles_per_chunk * p->M * sizeof(double2)));
+  MM_TRYC(cudaStreamSynchronize(s));
+  MM_TRYC(cudaGetLastError());
+#undef MM_TRY
+#undef MM_TRYC
+  *out = reinterpret_cast<madmap_plan_t>(p);
+  return MADMAP_OK;
+}
+
+extern "C" madmap_status madmap_plan_destroy(madmap_plan_t plan) {
+  if (!plan) return MADMAP_OK;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  cudaDeviceSynchronize();
+  delete p;
+  return MADMAP_OK;
+}
+
+extern "C" madmap_status madmap_plan_get_stats(madmap_plan_t plan, madmap_plan_stats* o) {
+  MM_CHECK(plan && o, MADMAP_ERR_INVALID_ARG, "plan_get_stats: NULL argument");
+  const Plan* p = reinterpret_cast<const Plan*>(plan);
+  o->n_obs = p->n_obs;
+  o->n_excised = p->n_excised;
+  o->n_fp64_pixels = p->n_fp64;
+  o->n_stokes = p->n_stokes;
+  o->fft_len = p->M;
+  o->n1 = p->N1;
+  o->n2 = p->N2;
+  o->n_segments = p->n_segments;
+  o->n_tiles = p->n_tiles;
+  o->tiles_per_chunk = p->tiles_per_chunk;
+  o->n_lags = p->n_lags;
+  o->n_filters = p->n_filters;
+  o->n_samples = p->n_t;
+  o->device_bytes = (int64_t)p->device_bytes;
+  return MADMAP_OK;
+}
+
+extern "C" madmap_status madmap_plan_observed(madmap_plan_t plan, int32_t* n_obs, int32_t* obs2glob,
+                                              uint8_t* excised, void* stream) {
+  MM_CHECK(plan, MADMAP_ERR_INVALID_ARG, "plan_observed: NULL plan");
+  const Plan* p = reinterpret_cast<const Plan*>(plan);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n_obs) *n_obs = p->n_obs;
+  if (obs2glob && p->n_obs)
+    MM_CUDA(cudaMemcpyAsync(obs2glob, p->obs2glob, sizeof(int) * p->n_obs, cudaMemcpyDeviceToDevice, s));
+  if (excised && p->n_obs)
+    MM_CUDA(cudaMemcpyAsync(excised, p->excised, p->n_obs, cudaMemcpyDeviceToDevice, s));
+  return MADMAP_OK;
+}
+
+extern "C" madmap_status madmap_plan_set_filters(madmap_plan_t plan, const double* lags, void* stream) {
+  MM_CHECK(plan && lags, MADMAP_ERR_INVALID_ARG, "plan_set_filters: NULL argument");
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  for (long long k = 0; k < (long long)p->n_filters * p->n_lags; ++k)
+    MM_CHECK(isfinite(lags[k]), MADMAP_ERR_INVALID_ARG, "filter_lags must be finite");
+  std::vector<double> old = p->lags;
+  p->lags.assign(lags, lags + (size_t)p->n_filters * p->n_lags);
+  madmap_status st = build_spectra(p);
+  if (st != MADMAP_OK) {
+    p->lags = old;
+    build_spectra(p);
+    return st;
+  }
+  // The block preconditioner weighs samples by f(0) of their filter: rebuild it.
+  // Rows of excised pixels are already zero, so those pixels have no hits and
+  // classify as excised again; every other pixel keeps its A^T A block.
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return build_preconditioner(p, s);
+}

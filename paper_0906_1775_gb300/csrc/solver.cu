@@ -1,0 +1,744 @@
+// PCG solve of H x = b (Section 4, Eq. 10) with MADmap's termination and
+// output rule (Section 5): x_0 = 0, stop at max_iter or when the relative
+// residual ||r_k|| / ||b|| reaches rel_tol, return the iterate with the lowest
+// relative residual seen.  The preconditioner is the per-pixel block inverse
+// (A^T W^-1 A)^-1 (Section 5, MADpre).
+//
+// Each iteration is: q = H p (three operator kernels per tile chunk), then
+//   k_cg_alpha      <p,q> -> alpha = <r,z>/<p,q>
+//   k_cg_update     x += alpha p, r -= alpha q, z = P r, <r,z>, <r,r> -> beta,
+//                   residual, best iterate, termination
+//   k_cg_direction  copy x to the best iterate if it improved, p = z + beta p,
+//                   q = 0
+// Dot products are accumulated in float64 in every precision, per block, and
+// the last block to finish (atomic ticket, no waiting) reduces the partials in
+// a fixed order, so results are reproducible run to run.  All scalars live on
+// the device; the host only reads the state every few iterations.  When the
+// solve has finished every kernel returns at once, so chunks of iterations
+// can be enqueued (or replayed from a CUDA graph) ahead of the host check.
+//
+// MIXED precision: float32 operator and vectors inside float64 iterative
+// refinement: b and the residual b - H x are float64 (float64 operator), the
+// correction solve H e = r runs in float32 with float64 dots and scalars, and
+// pixels flagged as poorly conditioned keep float64 preconditioner blocks.
+#include <math.h>
+#include <stdlib.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace mm {
+
+struct CgState {
+  double rz, alpha, beta, bnorm, res, best_res, tol;
+  int k, best_k, dir_k, max_iter, done, status;
+  unsigned counter;
+  int pad;
+};
+
+struct SolveBuffers {
+  bool fp64 = false;
+  long long nvec = 0;  // n_obs * ns_pad
+  void *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *xb = nullptr;
+  double* partials = nullptr;
+  CgState* st = nullptr;
+  CgState* host_st = nullptr;  // pinned, 2 slots
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  // float64 refinement vectors (allocated with the float64 buffers)
+  double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *t64 = nullptr, *xbest64 = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int graph_iters = 0;
+  std::vector<void*> allocs;
+};
+
+static const int NB = 304;  // blocks of the vector kernels (2 per SM)
+static const int NT = 256;
+
+void free_solve_buffers(Plan* p) {
+  for (SolveBuffers* sb : {p->sb64, p->sb32}) {
+    if (!sb) continue;
+    if (sb->exec) cudaGraphExecDestroy(sb->exec);
+    for (int i = 0; i < 2; ++i)
+      if (sb->ev[i]) cudaEventDestroy(sb->ev[i]);
+    if (sb->host_st) cudaFreeHost(sb->host_st);
+    for (void* a : sb->allocs) cudaFree(a);
+    delete sb;
+  }
+  p->sb64 = p->sb32 = nullptr;
+}
+
+static madmap_status sb_alloc(Plan* p, SolveBuffers* sb, void** ptr, size_t bytes) {
+  madmap_status st = dalloc(p, ptr, bytes);
+  if (st != MADMAP_OK) return st;
+  // ownership moves to the solve buffers
+  p->allocs.pop_back();
+  sb->allocs.push_back(*ptr);
+  return MADMAP_OK;
+}
+
+static madmap_status get_buffers(Plan* p, bool fp64, SolveBuffers** out) {
+  SolveBuffers*& slot = fp64 ? p->sb64 : p->sb32;
+  if (slot) {
+    *out = slot;
+    return MADMAP_OK;
+  }
+  SolveBuffers* sb = new SolveBuffers();
+  sb->fp64 = fp64;
+  sb->nvec = (long long)std::max(1, p->n_obs) * p->ns_pad;
+  const size_t vb = (size_t)sb->nvec * (fp64 ? sizeof(double) : sizeof(float));
+  madmap_status st = MADMAP_OK;
+  void** vecs[6] = {&sb->x, &sb->r, &sb->z, &sb->p, &sb->q, &sb->xb};
+  for (void** v : vecs)
+    if ((st = sb_alloc(p, sb, v, vb)) != MADMAP_OK) break;
+  if (st == MADMAP_OK) st = sb_alloc(p, sb, (void**)&sb->partials, sizeof(double) * NB * 4);
+  if (st == MADMAP_OK) st = sb_alloc(p, sb, (void**)&sb->st, sizeof(CgState));
+  if (st == MADMAP_OK && fp64) {
+    double** v64[5] = {&sb->b64, &sb->x64, &sb->r64, &sb->t64, &sb->xbest64};
+    for (double** v : v64)
+      if ((st = sb_alloc(p, sb, (void**)v, sizeof(double) * sb->nvec)) != MADMAP_OK) break;
+  }
+  if (st == MADMAP_OK) {
+    cudaError_t e = cudaMallocHost(&sb->host_st, 2 * sizeof(CgState));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sb->ev[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sb->ev[1], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemset(sb->st, 0, sizeof(CgState));
+    if (e != cudaSuccess) st = cuda_fail(e, "solve buffers");
+  }
+  slot = sb;  // freed with the plan, even when partially built
+  if (st != MADMAP_OK) return st;
+  *out = sb;
+  return MADMAP_OK;
+}
+
+// ---------------------------------------------------------------- small vector helpers
+template <typename Real, int NS> struct V3 {
+  Real a, b, c;
+};
+
+template <typename Real, int NS>
+__device__ __forceinline__ V3<Real, NS> ldv(const Real* v, int p) {
+  V3<Real, NS> o;
+  if (NS == 1) {
+    o.a = v[p];
+    o.b = o.c = 0;
+  } else {
+    o.a = v[4LL * p];
+    o.b = v[4LL * p + 1];
+    o.c = v[4LL * p + 2];
+  }
+  return o;
+}
+template <typename Real, int NS>
+__device__ __forceinline__ void stv(Real* v, int p, const V3<Real, NS>& o) {
+  if (NS == 1) {
+    v[p] = o.a;
+  } else {
+    v[4LL * p] = o.a;
+    v[4LL * p + 1] = o.b;
+    v[4LL * p + 2] = o.c;
+    v[4LL * p + 3] = 0;
+  }
+}
+template <typename Real, int NS>
+__device__ __forceinline__ double dotv(const V3<Real, NS>& u, const V3<Real, NS>& v) {
+  double s = (double)u.a * (double)v.a;
+  if (NS == 3) s += (double)u.b * (double)v.b + (double)u.c * (double)v.c;
+  return s;
+}
+
+// z = P r with the pixel's block inverse
+template <typename Real, int NS>
+__device__ __forceinline__ V3<Real, NS> precond(const V3<Real, NS>& r, int p, const double* P64, const float* P32,
+                                               const unsigned char* f64) {
+  V3<Real, NS> z;
+  if (NS == 1) {
+    if (sizeof(Real) == 8) z.a = (Real)(P64[p] * (double)r.a);
+    else z.a = (Real)(P32[p] * (float)r.a);
+    z.b = z.c = 0;
+    return z;
+  }
+  if (sizeof(Real) == 8 || f64[p]) {
+    const double* m = P64 + 6LL * p;
+    const double a = r.a, b = r.b, c = r.c;
+    z.a = (Real)(m[0] * a + m[1] * b + m[2] * c);
+    z.b = (Real)(m[1] * a + m[3] * b + m[4] * c);
+    z.c = (Real)(m[2] * a + m[4] * b + m[5] * c);
+  } else {
+    const float4 m0 = reinterpret_cast<const float4*>(P32)[2LL * p];
+    const float4 m1 = reinterpret_cast<const float4*>(P32)[2LL * p + 1];
+    const float a = r.a, b = r.b, c = r.c;
+    z.a = (Real)(m0.x * a + m0.y * b + m0.z * c);
+    z.b = (Real)(m0.y * a + m0.w * b + m1.x * c);
+    z.c = (Real)(m0.z * a + m1.x * b + m1.y * c);
+  }
+  return z;
+}
+
+// Block sum of up to 2 doubles; returns true in thread 0 of the block that
+// finishes last (after every block has published its partials).
+template <int K>
+__device__ __forceinline__ bool block_reduce_publish(double (&v)[K], double* partials, unsigned* counter) {
+  __shared__ double sh[32][K];
+  __shared__ bool last;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[wid][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += sh[w][k];
+      partials[blockIdx.x * 4 + k] = s;
+    }
+    __threadfence();
+    const unsigned ticket = atomicAdd(counter, 1u);
+    last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  return last;
+}
+
+template <int K>
+__device__ __forceinline__ void final_sums(const double* partials, double (&out)[K]) {
+  // executed by thread 0 of the last block: fixed order over blocks
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = 0.0;
+  for (unsigned b = 0; b < gridDim.x; ++b)
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] += ((volatile const double*)partials)[b * 4 + k];
+}
+
+// ---------------------------------------------------------------- CG kernels
+template <typename Real, int NS, typename Bt>
+__global__ void __launch_bounds__(NT) k_cg_init(Real* x, Real* r, Real* z, Real* p, Real* q, Real* xb, const Bt* b,
+                                                int n_obs, const double* P64, const float* P32,
+                                                const unsigned char* f64, CgState* st, double* partials,
+                                                double tol, int max_iter) {
+  double acc[2] = {0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_obs; i += gridDim.x * blockDim.x) {
+    V3<Real, NS> rv;
+    if (NS == 1) {
+      rv.a = (Real)b[i];
+      rv.b = rv.c = 0;
+    } else {
+      rv.a = (Real)b[4LL * i];
+      rv.b = (Real)b[4LL * i + 1];
+      rv.c = (Real)b[4LL * i + 2];
+    }
+    const V3<Real, NS> zv = precond<Real, NS>(rv, i, P64, P32, f64);
+    const V3<Real, NS> zero = {0, 0, 0};
+    stv<Real, NS>(r, i, rv);
+    stv<Real, NS>(z, i, zv);
+    stv<Real, NS>(p, i, zv);
+    stv<Real, NS>(x, i, zero);
+    stv<Real, NS>(xb, i, zero);
+    stv<Real, NS>(q, i, zero);
+    acc[0] += dotv(rv, zv);
+    acc[1] += dotv(rv, rv);
+  }
+  if (block_reduce_publish<2>(acc, partials, &st->counter) && threadIdx.x == 0) {
+    double s[2];
+    final_sums<2>(partials, s);
+    st->counter = 0;
+    st->rz = s[0];
+    st->bnorm = sqrt(s[1]);
+    st->res = st->bnorm > 0.0 ? 1.0 : 0.0;
+    st->best_res = st->res;
+    st->tol = tol;
+    st->k = 0;
+    st->best_k = 0;
+    st->dir_k = 0;
+    st->max_iter = max_iter;
+    st->status = 0;
+    st->alpha = st->beta = 0.0;
+    st->done = (st->bnorm == 0.0 || max_iter <= 0 || st->res <= tol) ? 1 : 0;
+  }
+}
+
+template <typename Real, int NS>
+__global__ void __launch_bounds__(NT) k_cg_alpha(const Real* p, const Real* q, int n_obs, CgState* st,
+                                                 double* partials) {
+  if (st->done) return;
+  double acc[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_obs; i += gridDim.x * blockDim.x)
+    acc[0] += dotv(ldv<Real, NS>(p, i), ldv<Real, NS>(q, i));
+  if (block_reduce_publish<1>(acc, partials, &st->counter) && threadIdx.x == 0) {
+    double s[1];
+    final_sums<1>(partials, s);
+    st->counter = 0;
+    if (!(s[0] > 0.0) || !isfinite(s[0])) {
+      st->status = (int)MADMAP_ERR_NOT_PD;
+      st->done = 1;
+    } else {
+      st->alpha = st->rz / s[0];
+    }
+  }
+}
+
+template <typename Real, int NS>
+__global__ void __launch_bounds__(NT) k_cg_update(Real* x, Real* r, Real* z, const Real* p, const Real* q, int n_obs,
+                                                  const double* P64, const float* P32, const unsigned char* f64,
+                                                  CgState* st, double* partials) {
+  if (st->done) return;
+  const Real alpha = (Real)st->alpha;
+  double acc[2] = {0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_obs; i += gridDim.x * blockDim.x) {
+    V3<Real, NS> xv = ldv<Real, NS>(x, i), rv = ldv<Real, NS>(r, i);
+    const V3<Real, NS> pv = ldv<Real, NS>(p, i), qv = ldv<Real, NS>(q, i);
+    xv.a += alpha * pv.a;
+    rv.a -= alpha * qv.a;
+    if (NS == 3) {
+      xv.b += alpha * pv.b;
+      xv.c += alpha * pv.c;
+      rv.b -= alpha * qv.b;
+      rv.c -= alpha * qv.c;
+    }
+    const V3<Real, NS> zv = precond<Real, NS>(rv, i, P64, P32, f64);
+    stv<Real, NS>(x, i, xv);
+    stv<Real, NS>(r, i, rv);
+    stv<Real, NS>(z, i, zv);
+    acc[0] += dotv(rv, zv);
+    acc[1] += dotv(rv, rv);
+  }
+  if (block_reduce_publish<2>(acc, partials, &st->counter) && threadIdx.x == 0) {
+    double s[2];
+    final_sums<2>(partials, s);
+    st->counter = 0;
+    const int k = st->k + 1;
+    st->k = k;
+    const double res = sqrt(s[1]) / st->bnorm;
+    st->res = res;
+    if (res < st->best_res) {
+      st->best_res = res;
+      st->best_k = k;
+    }
+    if (res <= st->tol || k >= st->max_iter || !isfinite(res)) st->done = 1;
+    st->beta = s[0] / st->rz;
+    st->rz = s[0];
+  }
+}
+
+template <typename Real, int NS>
+__global__ void __launch_bounds__(NT) k_cg_direction(const Real* x, const Real* z, Real* p, Real* q, Real* xb,
+                                                     int n_obs, CgState* st) {
+  const int k = st->k;
+  if (st->dir_k >= k) return;
+  const bool copy = st->best_k == k;
+  const bool more = !st->done;
+  const Real beta = (Real)st->beta;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_obs; i += gridDim.x * blockDim.x) {
+    if (copy) stv<Real, NS>(xb, i, ldv<Real, NS>(x, i));
+    if (more) {
+      V3<Real, NS> pv = ldv<Real, NS>(p, i);
+      const V3<Real, NS> zv = ldv<Real, NS>(z, i);
+      pv.a = zv.a + beta * pv.a;
+      if (NS == 3) {
+        pv.b = zv.b + beta * pv.b;
+        pv.c = zv.c + beta * pv.c;
+      }
+      stv<Real, NS>(p, i, pv);
+      const V3<Real, NS> zero = {0, 0, 0};
+      stv<Real, NS>(q, i, zero);
+    }
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&st->counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    st->counter = 0;
+    st->dir_k = k;
+  }
+}
+
+// ---------------------------------------------------------------- layout and refinement kernels
+// user [n][ns] (U) -> padded working layout [n][ns_pad] (Real)
+template <typename U, typename Real>
+__global__ void k_pack(const U* in, Real* out, int n_obs, int ns, int ns_pad) {
+  const long long n = (long long)n_obs * ns_pad;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(i % ns_pad);
+    const long long pp = i / ns_pad;
+    out[i] = s < ns ? (Real)in[pp * ns + s] : (Real)0;
+  }
+}
+template <typename Real, typename U>
+__global__ void k_unpack(const Real* in, U* out, int n_obs, int ns, int ns_pad) {
+  const long long n = (long long)n_obs * ns;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(i % ns);
+    const long long pp = i / ns;
+    out[i] = (U)in[pp * ns_pad + s];
+  }
+}
+
+// x64 += e (float32 correction), t64 = 0
+__global__ void k_refine_add(double* x64, const float* e, double* t64, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    x64[i] += (double)e[i];
+    t64[i] = 0.0;
+  }
+}
+
+// r64 = b64 - t64, ||r64||^2 -> st->res (relative to st->bnorm) by the last block
+__global__ void __launch_bounds__(NT) k_residual(const double* b64, const double* t64, double* r64, long long n,
+                                                 CgState* st, double* partials) {
+  double acc[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = b64[i] - t64[i];
+    r64[i] = v;
+    acc[0] += v * v;
+  }
+  if (block_reduce_publish<1>(acc, partials, &st->counter) && threadIdx.x == 0) {
+    double s[1];
+    final_sums<1>(partials, s);
+    st->counter = 0;
+    st->res = sqrt(s[0]);
+  }
+}
+
+static int grid_vec(long long n) {
+  long long g = (n + NT - 1) / NT;
+  return (int)std::max(1LL, std::min<long long>(g, NB));
+}
+
+// ---------------------------------------------------------------- PCG driver
+template <typename Real, int NS>
+static void enqueue_iteration(Plan* p, SolveBuffers* sb, cudaStream_t s, madmap_status* st) {
+  Real* x = (Real*)sb->x;
+  Real* r = (Real*)sb->r;
+  Real* z = (Real*)sb->z;
+  Real* pp = (Real*)sb->p;
+  Real* q = (Real*)sb->q;
+  Real* xb = (Real*)sb->xb;
+  const int n = p->n_obs;
+  const int g = grid_vec(n);
+  *st = op_launch(p, sizeof(Real) == 8, IN_MAP, OUT_MAP, pp, q, 0, 0, 1, &sb->st->done, s);
+  k_cg_alpha<Real, NS><<<g, NT, 0, s>>>(pp, q, n, sb->st, sb->partials);
+  k_cg_update<Real, NS><<<g, NT, 0, s>>>(x, r, z, pp, q, n, p->P64, p->P32, p->fp64flag, sb->st, sb->partials);
+  k_cg_direction<Real, NS><<<g, NT, 0, s>>>(x, z, pp, q, xb, n, sb->st);
+}
+
+template <typename Real, int NS>
+static madmap_status enqueue_chunk(Plan* p, SolveBuffers* sb, int iters, bool use_graph, cudaStream_t s) {
+  madmap_status st = MADMAP_OK;
+  if (!use_graph) {
+    for (int i = 0; i < iters && st == MADMAP_OK; ++i) enqueue_iteration<Real, NS>(p, sb, s, &st);
+    return st;
+  }
+  if (!sb->exec || sb->graph_iters != iters) {
+    // kernel attributes are set before capture begins
+    st = op_launch(p, sizeof(Real) == 8, IN_MAP, OUT_MAP, nullptr, nullptr, 0, 0, 0, nullptr, s);
+    if (st != MADMAP_OK) return st;
+    if (sb->exec) {
+      cudaGraphExecDestroy(sb->exec);
+      sb->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    MM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    for (int i = 0; i < iters && st == MADMAP_OK; ++i) enqueue_iteration<Real, NS>(p, sb, s, &st);
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (st != MADMAP_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    MM_CUDA(e);
+    e = cudaGraphInstantiate(&sb->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    MM_CUDA(e);
+    sb->graph_iters = iters;
+  }
+  MM_CUDA(cudaGraphLaunch(sb->exec, s));
+  return MADMAP_OK;
+}
+
+struct PcgResult {
+  int iters = 0, best_iter = 0, status = 0;
+  double best_res = 0.0, final_res = 0.0;
+};
+
+// Runs PCG on H e = b for the plan in the buffers' precision.  b: Bt vector in
+// the padded working layout.  Result: best iterate in sb->xb.
+template <typename Real, int NS, typename Bt>
+static madmap_status run_pcg(Plan* p, SolveBuffers* sb, const Bt* b, double tol, int max_iter, int per_sync,
+                             bool use_graph, cudaStream_t s, PcgResult* out) {
+  const int n = p->n_obs;
+  k_cg_init<Real, NS, Bt><<<grid_vec(n), NT, 0, s>>>((Real*)sb->x, (Real*)sb->r, (Real*)sb->z, (Real*)sb->p,
+                                                     (Real*)sb->q, (Real*)sb->xb, b, n, p->P64, p->P32,
+                                                     p->fp64flag, sb->st, sb->partials, tol, max_iter);
+  MM_CUDA(cudaGetLastError());
+  int launched = 0, slot = 0;
+  bool pending = false;
+  const int G = std::max(1, per_sync);
+  // one chunk in flight ahead of the host check
+  while (true) {
+    if (launched < max_iter) {
+      madmap_status st = enqueue_chunk<Real, NS>(p, sb, G, use_graph, s);
+      if (st != MADMAP_OK) return st;
+      launched += G;
+    }
+    MM_CUDA(cudaMemcpyAsync(&sb->host_st[slot], sb->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    MM_CUDA(cudaEventRecord(sb->ev[slot], s));
+    if (pending) {
+      const int prev = slot ^ 1;
+      MM_CUDA(cudaEventSynchronize(sb->ev[prev]));
+      if (sb->host_st[prev].done) break;
+    }
+    if (launched >= max_iter && pending) {
+      MM_CUDA(cudaEventSynchronize(sb->ev[slot]));
+      break;
+    }
+    pending = true;
+    slot ^= 1;
+  }
+  MM_CUDA(cudaStreamSynchronize(s));
+  CgState h;
+  MM_CUDA(cudaMemcpy(&h, sb->st, sizeof(CgState), cudaMemcpyDeviceToHost));
+  out->iters = h.k;
+  out->best_iter = h.best_k;
+  out->best_res = h.best_res;
+  out->final_res = h.res;
+  out->status = h.status;
+  return MADMAP_OK;
+}
+
+template <int NS>
+static madmap_status solve_impl(Plan* p, const float* d, double* m, const madmap_solve_opts& o,
+                                madmap_solve_info* info, cudaStream_t s) {
+  auto t_start = std::chrono::steady_clock::now();
+  SolveBuffers* sb64 = nullptr;
+  madmap_status st = get_buffers(p, true, &sb64);
+  if (st != MADMAP_OK) return st;
+  const long long nv = sb64->nvec;
+  const int n = p->n_obs;
+  madmap_solve_info I;
+  memset(&I, 0, sizeof(I));
+  // right-hand side b = A^T N^-1 d in float64
+  MM_CUDA(cudaMemsetAsync(sb64->b64, 0, sizeof(double) * nv, s));
+  st = op_launch(p, true, IN_TOD, OUT_MAP, d, sb64->b64, 0, 0, 1, nullptr, s);
+  if (st != MADMAP_OK) return st;
+  I.fp64_applies = 1;
+  MM_CUDA(cudaStreamSynchronize(s));
+  I.t_rhs_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  const bool graph = o.use_graph != 0;
+  if (o.precision == MADMAP_FP64) {
+    PcgResult R;
+    st = run_pcg<double, NS, double>(p, sb64, sb64->b64, o.rel_tol, o.max_iter, o.iters_per_sync, graph, s, &R);
+    if (st != MADMAP_OK) return st;
+    k_unpack<double, double><<<grid_vec((long long)n * p->n_stokes), NT, 0, s>>>((const double*)sb64->xb, m, n,
+                                                                                p->n_stokes, p->ns_pad);
+    I.iters = R.iters;
+    I.outer_iters = 1;
+    I.best_iter = R.best_iter;
+    I.fp64_applies += R.iters;
+    I.final_rel_res = R.final_res;
+    I.best_rel_res = R.best_res;
+    I.status = R.status != 0 ? R.status : (R.best_res <= o.rel_tol ? MADMAP_OK : MADMAP_WARN_MAXITER);
+  } else {
+    SolveBuffers* sb32 = nullptr;
+    st = get_buffers(p, false, &sb32);
+    if (st != MADMAP_OK) return st;
+    // r64 = b64 and ||b||
+    MM_CUDA(cudaMemsetAsync(sb64->t64, 0, sizeof(double) * nv, s));
+    k_residual<<<grid_vec(nv), NT, 0, s>>>(sb64->b64, sb64->t64, sb64->r64, nv, sb64->st, sb64->partials);
+    CgState h;
+    MM_CUDA(cudaMemcpyAsync(&h, sb64->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    MM_CUDA(cudaStreamSynchronize(s));
+    const double bnorm = h.res;
+    MM_CUDA(cudaMemsetAsync(sb64->x64, 0, sizeof(double) * nv, s));
+    MM_CUDA(cudaMemsetAsync(sb64->xbest64, 0, sizeof(double) * nv, s));
+    double best = bnorm > 0 ? 1.0 : 0.0, res = best;
+    int best_iter = 0, total = 0, outer = 0, inner_status = 0;
+    while (bnorm > 0 && res > o.rel_tol && total < o.max_iter && outer < o.max_outer) {
+      PcgResult R;
+      const int budget = o.max_iter - total;
+      st = run_pcg<float, NS, double>(p, sb32, sb64->r64, o.inner_rel_tol, budget, o.iters_per_sync, graph, s, &R);
+      if (st != MADMAP_OK) return st;
+      total += R.iters;
+      I.fp32_applies += R.iters;
+      ++outer;
+      if (R.status != 0) inner_status = R.status;
+      k_refine_add<<<grid_vec(nv), NT, 0, s>>>(sb64->x64, (const float*)sb32->xb, sb64->t64, nv);
+      st = op_launch(p, true, IN_MAP, OUT_MAP, sb64->x64, sb64->t64, 0, 0, 1, nullptr, s);
+      if (st != MADMAP_OK) return st;
+      ++I.fp64_applies;
+      k_residual<<<grid_vec(nv), NT, 0, s>>>(sb64->b64, sb64->t64, sb64->r64, nv, sb64->st, sb64->partials);
+      MM_CUDA(cudaMemcpyAsync(&h, sb64->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+      MM_CUDA(cudaStreamSynchronize(s));
+      res = h.res / bnorm;
+      if (res < best) {
+        best = res;
+        best_iter = total;
+        MM_CUDA(cudaMemcpyAsync(sb64->xbest64, sb64->x64, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+      }
+      if (R.iters == 0) break;
+    }
+    k_unpack<double, double><<<grid_vec((long long)n * p->n_stokes), NT, 0, s>>>(sb64->xbest64, m, n, p->n_stokes,
+                                                                                p->ns_pad);
+    I.iters = total;
+    I.outer_iters = outer;
+    I.best_iter = best_iter;
+    I.final_rel_res = res;
+    I.best_rel_res = best;
+    I.status = best <= o.rel_tol ? MADMAP_OK : (inner_status != 0 ? inner_status : MADMAP_WARN_MAXITER);
+  }
+  MM_CUDA(cudaStreamSynchronize(s));
+  MM_CUDA(cudaGetLastError());
+  I.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  if (info) *info = I;
+  return (madmap_status)I.status;
+}
+
+// ---------------------------------------------------------------- operator entry points
+template <typename Real>
+static madmap_status apply_impl(Plan* p, bool fp64, int n_rhs, const void* x, void* y, cudaStream_t s) {
+  SolveBuffers* sb = nullptr;
+  madmap_status st = get_buffers(p, fp64, &sb);
+  if (st != MADMAP_OK) return st;
+  const int n = p->n_obs, ns = p->n_stokes, np = p->ns_pad;
+  const long long user = (long long)n * ns;
+  for (int r = 0; r < n_rhs; ++r) {
+    const Real* xr = static_cast<const Real*>(x) + r * user;
+    Real* yr = static_cast<Real*>(y) + r * user;
+    k_pack<Real, Real><<<grid_vec((long long)n * np), NT, 0, s>>>(xr, (Real*)sb->p, n, ns, np);
+    MM_CUDA(cudaMemsetAsync(sb->q, 0, sizeof(Real) * sb->nvec, s));
+    st = op_launch(p, fp64, IN_MAP, OUT_MAP, sb->p, sb->q, 0, 0, 1, nullptr, s);
+    if (st != MADMAP_OK) return st;
+    k_unpack<Real, Real><<<grid_vec(user), NT, 0, s>>>((const Real*)sb->q, yr, n, ns, np);
+  }
+  MM_CUDA(cudaGetLastError());
+  return MADMAP_OK;
+}
+
+template <typename Real>
+static madmap_status rhs_impl(Plan* p, bool fp64, int n_rhs, const float* d, void* b, cudaStream_t s) {
+  SolveBuffers* sb = nullptr;
+  madmap_status st = get_buffers(p, fp64, &sb);
+  if (st != MADMAP_OK) return st;
+  const int n = p->n_obs, ns = p->n_stokes, np = p->ns_pad;
+  const long long user = (long long)n * ns;
+  for (int r = 0; r < n_rhs; ++r) {
+    MM_CUDA(cudaMemsetAsync(sb->q, 0, sizeof(Real) * sb->nvec, s));
+    st = op_launch(p, fp64, IN_TOD, OUT_MAP, d + (long long)r * p->n_t, sb->q, 0, 0, 1, nullptr, s);
+    if (st != MADMAP_OK) return st;
+    k_unpack<Real, Real><<<grid_vec(user), NT, 0, s>>>((const Real*)sb->q, static_cast<Real*>(b) + r * user, n, ns,
+                                                       np);
+  }
+  MM_CUDA(cudaGetLastError());
+  return MADMAP_OK;
+}
+
+}  // namespace mm
+
+using namespace mm;
+
+static madmap_status check_prec(int precision, bool allow_mixed) {
+  if (precision == MADMAP_FP64 || precision == MADMAP_FP32) return MADMAP_OK;
+  if (allow_mixed && precision == MADMAP_MIXED) return MADMAP_OK;
+  set_error("unsupported precision");
+  return MADMAP_ERR_INVALID_ARG;
+}
+
+extern "C" madmap_status madmap_apply_ATNA(madmap_plan_t plan, int32_t precision, int32_t n_rhs, const void* x,
+                                           void* y, void* stream) {
+  MM_CHECK(plan && n_rhs >= 1, MADMAP_ERR_INVALID_ARG, "apply_ATNA: bad arguments");
+  madmap_status st = check_prec(precision, false);
+  if (st != MADMAP_OK) return st;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  MM_CHECK((x && y) || p->n_obs == 0, MADMAP_ERR_INVALID_ARG, "apply_ATNA: NULL map");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->n_obs == 0) return MADMAP_OK;
+  return precision == MADMAP_FP64 ? apply_impl<double>(p, true, n_rhs, x, y, s)
+                                  : apply_impl<float>(p, false, n_rhs, x, y, s);
+}
+
+extern "C" madmap_status madmap_rhs(madmap_plan_t plan, int32_t precision, int32_t n_rhs, const float* d, void* b,
+                                    void* stream) {
+  MM_CHECK(plan && n_rhs >= 1, MADMAP_ERR_INVALID_ARG, "rhs: bad arguments");
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  MM_CHECK(b || p->n_obs == 0, MADMAP_ERR_INVALID_ARG, "rhs: b is NULL");
+  MM_CHECK(d || p->n_t == 0, MADMAP_ERR_INVALID_ARG, "rhs: d is NULL");
+  madmap_status st = check_prec(precision, false);
+  if (st != MADMAP_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->n_obs == 0) return MADMAP_OK;
+  return precision == MADMAP_FP64 ? rhs_impl<double>(p, true, n_rhs, d, b, s)
+                                  : rhs_impl<float>(p, false, n_rhs, d, b, s);
+}
+
+extern "C" madmap_status madmap_apply_ninv(madmap_plan_t plan, int32_t precision, int32_t n_rhs, const void* y,
+                                           void* w, void* stream) {
+  MM_CHECK(plan && n_rhs >= 1, MADMAP_ERR_INVALID_ARG, "apply_ninv: bad arguments");
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  MM_CHECK((y && w) || p->n_t == 0, MADMAP_ERR_INVALID_ARG, "apply_ninv: NULL timestream");
+  madmap_status st = check_prec(precision, false);
+  if (st != MADMAP_OK) return st;
+  const bool fp64 = precision == MADMAP_FP64;
+  const size_t es = fp64 ? sizeof(double) : sizeof(float);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int r = 0; r < n_rhs; ++r) {
+    st = op_launch(p, fp64, IN_TOD_REAL, OUT_TOD, static_cast<const char*>(y) + (size_t)r * p->n_t * es,
+                   static_cast<char*>(w) + (size_t)r * p->n_t * es, 0, 0, 1, nullptr, s);
+    if (st != MADMAP_OK) return st;
+  }
+  return MADMAP_OK;
+}
+
+extern "C" void madmap_solve_opts_default(madmap_solve_opts* o) {
+  if (!o) return;
+  o->max_iter = 50;
+  o->rel_tol = 1e-6;
+  o->precision = MADMAP_FP64;
+  o->max_outer = 10;
+  o->inner_rel_tol = 1e-4;
+  o->use_graph = 1;
+  o->iters_per_sync = 8;
+}
+
+extern "C" madmap_status madmap_solve(madmap_plan_t plan, const float* d, double* m, const madmap_solve_opts* opts,
+                                      madmap_solve_info* info, void* stream) {
+  MM_CHECK(plan, MADMAP_ERR_INVALID_ARG, "solve: NULL plan");
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  MM_CHECK(m || p->n_obs == 0, MADMAP_ERR_INVALID_ARG, "solve: m is NULL");
+  MM_CHECK(d || p->n_t == 0, MADMAP_ERR_INVALID_ARG, "solve: d is NULL");
+  madmap_solve_opts o;
+  madmap_solve_opts_default(&o);
+  if (opts) o = *opts;
+  MM_CHECK(o.precision == MADMAP_FP64 || o.precision == MADMAP_MIXED, MADMAP_ERR_INVALID_ARG,
+           "solve: precision must be FP64 or MIXED");
+  MM_CHECK(o.max_iter >= 0 && o.rel_tol >= 0 && o.iters_per_sync >= 1 && o.max_outer >= 1 &&
+               o.inner_rel_tol > 0 && o.inner_rel_tol < 1,
+           MADMAP_ERR_INVALID_ARG, "solve: bad options");
+  cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  if (p->n_obs == 0) {
+    if (info) {
+      memset(info, 0, sizeof(*info));
+    }
+    return MADMAP_OK;
+  }
+  if (!p->solve_stream) {
+    MM_CUDA(cudaStreamCreateWithFlags(&p->solve_stream, cudaStreamNonBlocking));
+    MM_CUDA(cudaEventCreateWithFlags(&p->solve_event, cudaEventDisableTiming));
+  }
+  cudaStream_t s = p->solve_stream;
+  MM_CUDA(cudaEventRecord(p->solve_event, caller));
+  MM_CUDA(cudaStreamWaitEvent(s, p->solve_event, 0));
+  madmap_status st = p->n_stokes == 1 ? solve_impl<1>(p, d, m, o, info, s) : solve_impl<3>(p, d, m, o, info, s);
+  cudaStreamSynchronize(s);
+  return st;
+}

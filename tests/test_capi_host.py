@@ -1,0 +1,71 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, and its host-only helpers agree with the oracle."""
+
+from __future__ import annotations
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    import paper_0906_1775_gb300 as mm
+    from paper_0906_1775_gb300 import build
+    if not os.path.exists(mm.library_path()):
+        build.build()
+    return mm
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "madmap.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(madmap_[a-z_A-Z0-9]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    mm = _lib()
+    lib = mm.load()
+    names = _declared()
+    assert "madmap_solve" in names and "madmap_apply_ATNA" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    bound = {p[0] for p in mm._lib.PROTOTYPES}
+    assert set(names) == bound, set(names) ^ bound
+
+
+def test_version_and_error_strings():
+    mm = _lib()
+    assert mm.load().madmap_version().startswith(b"madmap")
+    assert isinstance(mm.madmap_last_error(), str)
+
+
+@pytest.mark.parametrize("params", [(64, 100.0, 1.0, 0.1, 2.0), (128, 100.0, 1.3, 0.05, 1.2),
+                                    (8, 100.0, 0.9, 5.0, 1.5), (4096, 100.0, 1.0, 0.1, 2.0), (12, 180.0, 1.0, 0.03, 1.7)])
+def test_noise_filter_matches_oracle(params):
+    from oracle.noise import filter_lags
+    mm = _lib()
+    n, fs, s, fk, a = params
+    lib_f, lib_g = mm.noise_filter(n, fs, s, fk, a, with_grad=True)
+    ora_f, ora_g = filter_lags(n, fs, s, fk, a, with_grad=True)
+    assert np.max(np.abs(lib_f - ora_f)) <= 1e-13 * np.max(np.abs(ora_f))
+    assert np.max(np.abs(lib_g - ora_g)) <= 1e-12 * np.max(np.abs(ora_g))
+
+
+def test_noise_filter_rejects_bad_args():
+    mm = _lib()
+    with pytest.raises(mm.MadmapError):
+        mm.noise_filter(0, 100.0, 1.0, 0.1, 2.0)
+    with pytest.raises(mm.MadmapError):
+        mm.noise_filter(8, 100.0, -1.0, 0.1, 2.0)
+
+
+@pytest.mark.parametrize("n_c,longest", [(2 ** 12, 2 ** 18), (2 ** 14, 2 ** 20), (2 ** 15, 648000), (16, 100),
+                                          (2 ** 12, 5000), (1, 10)])
+def test_paper_fft_length_matches_oracle(n_c, longest):
+    from oracle.noise import fft_length
+    mm = _lib()
+    assert mm.paper_fft_length(n_c, longest) == fft_length(n_c, longest)

@@ -1,0 +1,338 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances.  FP64 path: relative RMS <= 1e-10 for maps (the stated target)
+and <= 1e-11 for single operator applications (an FFT of length M = 2^k has
+relative error ~ k * 2^-53; a four-step transform and a few hundred summed
+terms stay far below 1e-12).  FP32 operator: relative RMS <= 2e-5 (k * 2^-24
+~ 1e-6 for the transforms, plus float32 accumulation of the scatter; 2e-5
+leaves a 10x margin).  Pixel indexing is compared bit for bit.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from tests.gpu_helpers import cuda, dominant_lags, host, lib_lags, make_plan
+from tests.helpers import lags_for, rel_rms, system_for, tiny_IQU, tiny_T
+
+pytestmark = pytest.mark.gpu
+
+FP64_OP_TOL = 1e-11
+FP32_OP_TOL = 2e-5
+FP64_MAP_TOL = 1e-10
+MIXED_MAP_TOL = 1e-6
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ragged(seed=0, n_stokes=1, lens=(1, 7, 300, 1000, 0, 2500, 77, 4096), width=8, n_lags=33, flag_frac=0.05):
+    from synth import make_flat_problem
+
+    def ivl(_rng, tot):
+        return list(lens)
+
+    n = sum(lens)
+    return make_flat_problem("ragged", seed, width, 1 if n_stokes == 1 else 1, n, n_stokes, n_lags,
+                             interval_lengths=ivl, noise=(1.0, 5.0, 1.5), flag_frac=flag_frac,
+                             det_angles_deg=[10.0], hwp_step_deg=22.5)
+
+
+# ------------------------------------------------------------------ indexing
+@pytest.mark.parametrize("maker", [lambda: tiny_T(flag_frac=0.1), lambda: tiny_IQU(flag_frac=0.05),
+                                   lambda: _ragged(3, 3)])
+def test_observed_pixels_bit_exact(maker):
+    p = maker()
+    S = system_for(p)
+    plan = make_plan(p)
+    o2g, exc = plan.observed()
+    assert plan.n_obs == S.n_obs
+    assert np.array_equal(host(o2g).astype(np.int64), S.obs2glob)
+    assert np.array_equal(host(exc).astype(bool), S.excised)
+
+
+# ------------------------------------------------------------------ N^-1
+@pytest.mark.parametrize("fft_len,tpc", [(0, 0), (256, 0), (256, 3), (1024, 1)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_apply_ninv_vs_direct_sum(fft_len, tpc, prec):
+    from oracle.noise import apply_ninv_direct
+    torch = _torch()
+    p = _ragged(1)
+    lags = dominant_lags(1, p.n_lags, seed=5)
+    plan = make_plan(p, lags=lags, fft_len=fft_len, tiles_per_chunk=tpc)
+    y = np.random.default_rng(7).standard_normal(p.n_samples)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    w = host(plan.apply_ninv(cuda(y, dt), precision=prec))[0]
+    ref = apply_ninv_direct(y.astype(np.float32).astype(np.float64) if prec == "fp32" else y, p.interval_offsets,
+                            p.interval_filter, lags)
+    assert rel_rms(w, ref) < (FP64_OP_TOL if prec == "fp64" else FP32_OP_TOL)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_apply_ninv_multifilter_intervals(prec):
+    from oracle.noise import apply_ninv_direct
+    torch = _torch()
+    p = tiny_IQU(n_per_det=700, n_lags=21, n_ivl_lo=20, n_ivl_hi=300)
+    lags = dominant_lags(p.n_filters, p.n_lags, seed=9)
+    plan = make_plan(p, lags=lags, fft_len=256)
+    y = np.random.default_rng(3).standard_normal(p.n_samples)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    w = host(plan.apply_ninv(cuda(y, dt), precision=prec))[0]
+    ref = apply_ninv_direct(y.astype(np.float32).astype(np.float64) if prec == "fp32" else y, p.interval_offsets,
+                            p.interval_filter, lags)
+    assert rel_rms(w, ref) < (FP64_OP_TOL if prec == "fp64" else FP32_OP_TOL)
+
+
+# ------------------------------------------------------------------ H and b
+CASES = {
+    "tinyT": lambda: tiny_T(flag_frac=0.05),
+    "tinyIQU": lambda: tiny_IQU(flag_frac=0.03),
+    "raggedT": lambda: _ragged(2, 1),
+    "raggedIQU": lambda: _ragged(4, 3, width=6),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("fft_len", [0, 512])
+def test_apply_ATNA_vs_oracle(case, prec, fft_len):
+    torch = _torch()
+    p = CASES[case]()
+    S = system_for(p)
+    plan = make_plan(p, fft_len=fft_len)
+    x = np.random.default_rng(11).standard_normal((S.n_obs, p.n_stokes))
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    y = host(plan.apply_ATNA(cuda(x, dt), precision=prec))[0]
+    xin = x.astype(np.float32).astype(np.float64) if prec == "fp32" else x
+    ref = S.H(xin)
+    assert rel_rms(y, ref) < (FP64_OP_TOL if prec == "fp64" else FP32_OP_TOL)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_rhs_vs_oracle(case, prec):
+    p = CASES[case]()
+    S = system_for(p)
+    plan = make_plan(p)
+    b = host(plan.rhs(cuda(p.d), precision=prec))[0]
+    ref = S.rhs(p.d[0])
+    assert rel_rms(b, ref) < (FP64_OP_TOL if prec == "fp64" else FP32_OP_TOL)
+
+
+def test_operator_symmetric_positive_definite_on_gpu():
+    torch = _torch()
+    p = tiny_IQU(seed=31)
+    plan = make_plan(p)
+    rng = np.random.default_rng(0)
+    o2g, exc = plan.observed()
+    keep = ~host(exc).astype(bool)
+    x = rng.standard_normal((plan.n_obs, 3)) * keep[:, None]
+    y = rng.standard_normal((plan.n_obs, 3)) * keep[:, None]
+    Hx = host(plan.apply_ATNA(cuda(x, torch.float64)))[0]
+    Hy = host(plan.apply_ATNA(cuda(y, torch.float64)))[0]
+    a, b = float(np.sum(y * Hx)), float(np.sum(x * Hy))
+    assert abs(a - b) <= 1e-12 * abs(a)
+    assert float(np.sum(x * Hx)) > 0
+
+
+# ------------------------------------------------------------------ solves
+@pytest.mark.parametrize("case", list(CASES))
+def test_solve_fp64_matches_oracle(case):
+    p = CASES[case]()
+    S = system_for(p)
+    plan = make_plan(p)
+    d = cuda(p.d[0])
+    for tol, maxit in [(1e-13, 400), (1e-5, 400), (1e-30, 7)]:
+        m, info = plan.solve(d, precision="fp64", rel_tol=tol, max_iter=maxit)
+        x, oi = S.solve(p.d[0], rel_tol=tol, max_iter=maxit)
+        assert abs(info["iters"] - oi["iters"]) <= 1
+        if info["iters"] == oi["iters"]:
+            assert info["best_iter"] == oi["best_iter"]
+        assert rel_rms(host(m), x) < (FP64_MAP_TOL if tol < 1e-10 else 1e-6)
+        assert info["best_rel_res"] == pytest.approx(oi["best_res"], rel=1e-6, abs=1e-14)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_solve_mixed_reaches_fp64_map(case):
+    p = CASES[case]()
+    S = system_for(p)
+    plan = make_plan(p)
+    m, info = plan.solve(cuda(p.d[0]), precision="mixed", rel_tol=1e-12, max_iter=600, max_outer=20)
+    x, _ = S.solve(p.d[0], rel_tol=1e-13, max_iter=600)
+    keep = ~S.excised
+    for s in range(p.n_stokes):
+        assert rel_rms(host(m)[keep, s], x[keep, s]) < MIXED_MAP_TOL
+    assert info["outer_iters"] >= 1 and info["fp64_applies"] == info["outer_iters"] + 1
+
+
+def test_solve_without_graphs_is_identical():
+    p = tiny_IQU(seed=5)
+    plan = make_plan(p)
+    d = cuda(p.d[0])
+    m1, i1 = plan.solve(d, rel_tol=1e-10, max_iter=200, use_graph=True)
+    m2, i2 = plan.solve(d, rel_tol=1e-10, max_iter=200, use_graph=False, iters_per_sync=3)
+    assert i1["iters"] == i2["iters"]
+    # dot products reduce in a fixed order, but the scatter's float atomics do not
+    assert rel_rms(host(m1), host(m2)) < 1e-12
+
+
+def test_white_noise_solve_is_binned_average():
+    p = tiny_T(seed=8, ivls=(600,))
+    plan = make_plan(p, lags=np.array([[1.0]]))
+    m, info = plan.solve(cuda(p.d[0]), rel_tol=1e-14, max_iter=10)
+    assert info["iters"] == 1
+    o2g, _ = plan.observed()
+    for q, g in enumerate(host(o2g)):
+        assert host(m)[q, 0] == pytest.approx(float(np.mean(p.d[0][p.pix == g].astype(np.float64))), rel=1e-12)
+
+
+def test_noiseless_recovery_on_gpu():
+    p = tiny_IQU(seed=6, noiseless=True)
+    plan = make_plan(p)
+    m, _ = plan.solve(cuda(p.d[0]), rel_tol=1e-13, max_iter=500)
+    o2g, exc = plan.observed()
+    keep = ~host(exc).astype(bool)
+    z = p.sky[host(o2g)]
+    assert rel_rms(host(m)[keep], z[keep]) < 1e-6
+
+
+# ------------------------------------------------------------------ full-size workloads
+def test_config1_full_size_fp64():
+    from synth import make_config
+    p = make_config(1)
+    S = system_for(p)
+    plan = make_plan(p)
+    d = cuda(p.d[0])
+    m, info = plan.solve(d, precision="fp64", rel_tol=1e-8, max_iter=300)
+    x, oi = S.solve(p.d[0], rel_tol=1e-8, max_iter=300)
+    assert info["iters"] == oi["iters"]
+    assert rel_rms(host(m), x) < FP64_MAP_TOL
+    m2, _ = plan.solve(d, precision="fp64", rel_tol=1e-13, max_iter=300)
+    x2, _ = S.solve(p.d[0], rel_tol=1e-13, max_iter=300)
+    assert rel_rms(host(m2), x2) < FP64_MAP_TOL
+
+
+@pytest.fixture(scope="module")
+def config2():
+    from synth import make_config
+    p = make_config(2)
+    S = system_for(p)
+    return p, S
+
+
+def test_config2_operator_sampled_outputs(config2):
+    torch = _torch()
+    p, S = config2
+    plan = make_plan(p)
+    assert plan.n_obs == S.n_obs
+    o2g, _ = plan.observed()
+    assert np.array_equal(host(o2g).astype(np.int64), S.obs2glob)
+    x = np.random.default_rng(2).standard_normal((S.n_obs, 3))
+    pk = np.random.default_rng(3).choice(S.n_obs, 12, replace=False)
+    ref = S.H_sampled(x, pk)
+    for prec, tol in [("fp64", FP64_OP_TOL), ("fp32", FP32_OP_TOL)]:
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        y = host(plan.apply_ATNA(cuda(x, dt), precision=prec))[0]
+        assert rel_rms(y[pk], ref) < (tol if prec == "fp64" else 1e-4)
+
+
+def test_config2_mixed_solve_residual_by_oracle(config2):
+    p, S = config2
+    plan = make_plan(p)
+    m, info = plan.solve(cuda(p.d[0]), precision="mixed", rel_tol=1e-8, max_iter=400, max_outer=10)
+    b = S.rhs(p.d[0])
+    r = b - S.H(host(m))
+    res = float(np.sqrt(np.sum(r * r) / np.sum(b * b)))
+    assert res <= max(2.0 * info["best_rel_res"], 1e-8 * 1.5)
+
+
+# ------------------------------------------------------------------ edge cases and errors
+def test_empty_plan():
+    torch = _torch()
+    from paper_0906_1775_gb300 import Plan
+    plan = Plan(torch.empty(0, dtype=torch.int32, device="cuda"), None, 16, np.array([0]), np.zeros(0, np.int32),
+                np.array([[1.0, 0.1]]))
+    assert plan.n_obs == 0
+    m, info = plan.solve(torch.empty(0, dtype=torch.float32, device="cuda"))
+    assert m.shape == (0, 1) and info["iters"] == 0
+
+
+def test_invalid_pixel_is_rejected():
+    torch = _torch()
+    import paper_0906_1775_gb300 as mm
+    pix = torch.tensor([0, 1, 5, 2], dtype=torch.int32, device="cuda")
+    with pytest.raises(mm.MadmapError) as e:
+        mm.Plan(pix, None, 4, np.array([0, 4]), np.array([0], np.int32), np.array([[1.0]]))
+    assert e.value.status == mm._lib.MADMAP_ERR_INVALID_ARG
+
+
+def test_non_positive_definite_filter_is_rejected():
+    torch = _torch()
+    import paper_0906_1775_gb300 as mm
+    pix = torch.tensor([0, 1, 2, 3] * 10, dtype=torch.int32, device="cuda")
+    with pytest.raises(mm.MadmapError) as e:
+        mm.Plan(pix, None, 4, np.array([0, 40]), np.array([0], np.int32), np.array([[1.0, 0.9, 0.9]]))
+    assert e.value.status == mm._lib.MADMAP_ERR_NOT_PD
+
+
+def test_bad_offsets_are_rejected():
+    torch = _torch()
+    import paper_0906_1775_gb300 as mm
+    pix = torch.zeros(10, dtype=torch.int32, device="cuda")
+    for off in ([0, 5], [0, 6, 4, 10], [1, 10]):
+        with pytest.raises(mm.MadmapError):
+            mm.Plan(pix, None, 4, np.array(off), np.zeros(len(off) - 1, np.int32), np.array([[1.0]]))
+
+
+def test_injected_allocation_failure_reports_oom():
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch, paper_0906_1775_gb300 as mm\n"
+        "pix = torch.zeros(10, dtype=torch.int32, device='cuda')\n"
+        "try:\n"
+        "    mm.Plan(pix, None, 4, np.array([0, 10]), np.zeros(1, np.int32), np.array([[1.0]]))\n"
+        "    print('NOERR')\n"
+        "except mm.MadmapError as e:\n"
+        "    print('STATUS', e.status)\n")
+    import os
+    env = dict(os.environ, MADMAP_FAULT_ALLOC_FAIL_AT="3")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=root, timeout=300)
+    assert "STATUS -3" in out.stdout, out.stdout + out.stderr
+
+
+def test_single_sample_and_short_intervals():
+    p = _ragged(8, 1, lens=(1, 1, 2, 3, 5, 8, 13, 21), width=3, n_lags=6, flag_frac=0.0)
+    S = system_for(p)
+    plan = make_plan(p)
+    m, info = plan.solve(cuda(p.d[0]), rel_tol=1e-13, max_iter=200)
+    x, _ = S.solve(p.d[0], rel_tol=1e-13, max_iter=200)
+    assert rel_rms(host(m), x) < FP64_MAP_TOL
+
+
+def test_set_filters_matches_new_plan():
+    torch = _torch()
+    p = tiny_IQU(seed=13)
+    plan = make_plan(p)
+    new = lib_lags(p) * 0.5
+    new[:, 1:] *= 0.3
+    new[:, 0] = 1.0 + 2 * np.abs(new[:, 1:]).sum(axis=1)
+    plan.set_filters(new)
+    fresh = make_plan(p, lags=new)
+    x = np.random.default_rng(1).standard_normal((plan.n_obs, 3))
+    a = host(plan.apply_ATNA(cuda(x, torch.float64)))
+    b = host(fresh.apply_ATNA(cuda(x, torch.float64)))
+    assert np.allclose(a, b, rtol=0, atol=1e-13 * np.abs(b).max())
+    d = cuda(p.d[0])
+    m1, _ = plan.solve(d, rel_tol=1e-12, max_iter=300)
+    m2, _ = fresh.solve(d, rel_tol=1e-12, max_iter=300)
+    assert rel_rms(host(m1), host(m2)) < 1e-12
+
+
+def test_oracle_lags_agree_with_library_lags():
+    p = tiny_IQU()
+    assert np.allclose(lib_lags(p), lags_for(p), rtol=1e-12, atol=1e-15)

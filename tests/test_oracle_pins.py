@@ -367,3 +367,12 @@ def test_flagged_samples_are_zero_rows():
     xs = S.dense_solve(p.d[0])
     x, _ = S.solve(p.d[0], rel_tol=1e-13, max_iter=300)
     assert rel_rms(x, xs) < 1e-10
+
+
+def test_sampled_operator_matches_full_operator():
+    p = tiny_IQU(seed=21)
+    S = system_for(p)
+    x = np.random.default_rng(4).standard_normal((S.n_obs, 3))
+    full = S.H(x)
+    pk = [0, 5, S.n_obs // 2, S.n_obs - 1]
+    assert np.allclose(S.H_sampled(x, pk), full[pk], rtol=1e-12, atol=1e-12 * np.abs(full).max())
