@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark of the MADmap PCG map-making solve on GB300.
+
+Workload: the IQU mixed-precision problem (4 detectors x 2^22 samples at polariser
+angles 0/45/90/135 deg behind a half-wave plate stepping 22.5 deg per sweep,
+512 x 512 pixels = 786,432 unknowns, stationary intervals 2^16-2^20 samples,
+filters of 2^14 lags), seeded synthetic data.
+
+A step is one complete solve: right-hand side A^T N^-1 d (float64), float32
+PCG iterations inside float64 iterative refinement, and the float64 residuals,
+run to the smallest stopping tolerance whose map is within 1e-6 (relative RMS
+per Stokes map) of a reference map solved to 1e-11 in float64 on the same GPU.
+The metric is samples x PCG iterations per second over the timed steps; the
+same time-to-1e-6 is also measured for the plain float64 GPU solve.
+
+--impl reference times the FP64 CPU oracle on bounded samples of the same
+workload (one oracle PCG iteration per step).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = ("IQU mixed precision: 4 det x 2^22 samples, 512x512 grid (786,432 unknowns), HWP 22.5 deg/sweep, "
+            "intervals 2^16-2^20, n_c = 2^14 lags")
+METRIC = "samples x PCG iters/s (time to 1e-6 map error, mixed vs FP64 on the same GPU)"
+UNIT = "samples*iters/s"
+MAP_TARGET = 1e-6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=3, help="oracle PCG iterations in the CPU baseline sample")
+    ap.add_argument("--operator-only", type=int, default=0, metavar="R",
+                    help="only build the plan and time R float32 operator applications (profiling runs)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v, device):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, v, device):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def stokes_err(m, ref, keep):
+    import numpy as np
+    out = []
+    for s in range(ref.shape[1]):
+        a, b = m[keep, s], ref[keep, s]
+        out.append(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)))
+    return max(out), out
+
+
+def lib_lags(p):
+    import numpy as np
+    import paper_0906_1775_gb300 as mm
+    return np.stack([mm.noise_filter(p.n_lags, p.fs, *p.noise_params[k]) for k in range(p.n_filters)])
+
+
+def cpu_oracle_rate(p, iters):
+    """FP64 oracle on the host: samples x PCG iterations / s over `iters` iterations."""
+    import numpy as np
+    from oracle.noise import filter_lags
+    from oracle.solver import System
+    lags = np.stack([filter_lags(p.n_lags, p.fs, *p.noise_params[k]) for k in range(p.n_filters)])
+    S = System(p.pix, p.psi, p.n_pix, p.n_stokes, p.interval_offsets, p.interval_filter, lags)
+    b = S.rhs(p.d[0])
+    t0, c0 = time.perf_counter(), time.process_time()
+    _, info = S.pcg(b, rel_tol=0.0, max_iter=iters)
+    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
+    its = max(info["iters"], 1)
+    return p.n_samples * its / wall, wall, its, max(1, round(cpu / wall))
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from synth import make_config
+    p = make_config(2)
+    import numpy as np  # noqa: F401
+    from oracle.noise import filter_lags
+    from oracle.solver import System
+    lags = np.stack([filter_lags(p.n_lags, p.fs, *p.noise_params[k]) for k in range(p.n_filters)])
+    S = System(p.pix, p.psi, p.n_pix, p.n_stokes, p.interval_offsets, p.interval_filter, lags)
+    b = S.rhs(p.d[0])
+    for _ in range(args.warmup):
+        S.pcg(b, rel_tol=0.0, max_iter=1)
+    times, c0 = [], time.process_time()
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        S.pcg(b, rel_tol=0.0, max_iter=1)
+        times.append(time.perf_counter() - t0)
+    wall = time.perf_counter() - t_all
+    cores = max(1, round((time.process_time() - c0) / wall))
+    value = p.n_samples * args.steps / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_samples": p.n_samples, "unknowns": int(S.n_obs * 3),
+                       "l2_flush": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "one FP64 oracle PCG iteration (H application + CG update) per step on the "
+                                       "full-size workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import numpy as np
+    import torch
+
+    import paper_0906_1775_gb300 as mm
+    from synth import make_config
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mm.load()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    # one independent replica per rank (weak scaling, no data-path collective)
+    p = make_config(2, seed=2000 + rank)
+    pix = torch.from_numpy(p.pix).to(dev)
+    psi = torch.from_numpy(p.psi).to(dev)
+    plan = mm.Plan(pix, psi, p.n_pix, p.interval_offsets, p.interval_filter, lib_lags(p))
+    del pix, psi
+    if args.operator_only:
+        ms, n = plan.time_operator("fp32", reps=args.operator_only)
+        ms64, _ = plan.time_operator("fp64", reps=max(1, args.operator_only // 4))
+        print(json.dumps({"operator_fp32_ms_per_launch": list(ms), "launches": [int(x) for x in n],
+                          "operator_fp32_ms": float((ms * n).sum()), "operator_fp64_ms": float((ms64 * n).sum()),
+                          "stats": plan.stats}), flush=True)
+        plan.close()
+        return
+    d_host = torch.from_numpy(p.d[0]).pin_memory()
+    d = d_host.to(dev)
+    _, exc = plan.observed()
+    keep = ~exc.cpu().numpy().astype(bool)
+
+    # reference map (float64, tight) and the tolerances that reach the 1e-6 map error
+    ref, rinfo = plan.solve(d, precision="fp64", rel_tol=1e-11, max_iter=3000)
+    ref = ref.cpu().numpy()
+
+    def first_tol(precision, **kw):
+        last = None
+        for tol in [1e-6, 5e-7, 2e-7, 1e-7, 5e-8, 2e-8, 1e-8, 5e-9, 2e-9, 1e-9, 5e-10, 1e-10]:
+            m, info = plan.solve(d, precision=precision, rel_tol=tol, max_iter=3000, **kw)
+            err, per = stokes_err(m.cpu().numpy(), ref, keep)
+            last = (tol, info, err, per)
+            if err <= MAP_TARGET:
+                return last
+        return last
+
+    mixed_kw = dict(max_outer=20, inner_rel_tol=1e-4)
+    tol_mixed, info_mixed, err_mixed, per_mixed = first_tol("mixed", **mixed_kw)
+    tol_64, info_64, err_64, per_64 = first_tol("fp64")
+
+    def solve_step():
+        return plan.solve(d, precision="mixed", rel_tol=tol_mixed, max_iter=3000, **mixed_kw)
+
+    for _ in range(max(args.warmup, 0)):
+        solve_step()
+
+    # ---------------- timed region
+    gpu_index = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        gpu_index = vis.split(",")[local]
+    clocks = Clocks(gpu_index)
+    time.sleep(0.3)
+    launches0 = mm.madmap_kernel_launch_count()
+    iters = 0
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        _, info = solve_step()
+        iters += info["iters"]
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = mm.madmap_kernel_launch_count() - launches0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(world, ms, dev)
+    samples_iters = sum_over_ranks(world, float(p.n_samples) * iters, dev)
+    value = samples_iters / (ms_max / 1e3)
+
+    # ---------------- float64 time to the same map error
+    plan.solve(d, precision="fp64", rel_tol=tol_64, max_iter=3000)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    _, i64 = plan.solve(d, precision="fp64", rel_tol=tol_64, max_iter=3000)
+    f1.record()
+    torch.cuda.synchronize()
+    ms_fp64 = f0.elapsed_time(f1)
+
+    # ---------------- roofline of the float32 operator (events on the kernels' own stream)
+    op_ms, op_launch = plan.time_operator("fp32", reps=20)
+    op64_ms, _ = plan.time_operator("fp64", reps=5)
+    t_op = float(np.sum(op_ms * op_launch))
+    n_obs = plan.n_obs
+    b_alg = p.n_samples * 8 + 2 * n_obs * 4 * 3       # pointing read once + map read and written
+    achieved = b_alg / (t_op * 1e-3) / 1e9
+    k_dom = int(np.argmax(op_ms * op_launch))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "kernel": "operator A^T N^-1 A, float32 (k_f1 gather+column FFTs, k_f2 row FFTs x filter, "
+                          "k_f3 inverse column FFTs+scatter), one application",
+                "alg_bytes_per_launch": int(b_alg), "ms_per_launch": t_op,
+                "peak_source": f"{hbm_peak_src} hbm_gbs (MEASURED_PEAKS.json)" if hbm_peak_src == "measured"
+                else "fallback 6800 GB/s",
+                "per_kernel_ms": [float(x) for x in op_ms], "launches_per_application": [int(x) for x in op_launch],
+                "dominant_kernel": ["k_f1", "k_f2", "k_f3"][k_dom],
+                "fp64_operator_ms": float(np.sum(op64_ms * op_launch))}
+    traffic_file = os.path.join(ROOT, "profiles", "operator_traffic.json")
+    if os.path.exists(traffic_file):
+        try:
+            tr = json.load(open(traffic_file))
+            if tr.get("fft_len") == plan.stats["fft_len"] and tr.get("n_tiles") == plan.stats["n_tiles"]:
+                roofline["traffic"] = tr["dram_bytes_per_application"]
+        except Exception:
+            pass
+
+    # ---------------- end to end: host d in, host map out, through the public API
+    m_host = torch.empty((n_obs, 3), dtype=torch.float64).pin_memory()
+    barrier(world)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record()
+    e2e_iters = 0
+    for _ in range(args.steps):
+        d2 = d_host.to(dev, non_blocking=True)
+        m, info = plan.solve(d2, precision="mixed", rel_tol=tol_mixed, max_iter=3000, **mixed_kw)
+        m_host.copy_(m, non_blocking=True)
+        e2e_iters += info["iters"]
+    g1.record()
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(world, g0.elapsed_time(g1), dev)
+    e2e_value = sum_over_ranks(world, float(p.n_samples) * e2e_iters, dev) / (ms_e2e / 1e3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, wall, its, cores = cpu_oracle_rate(p, args.cpu_iters)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{its} FP64 oracle PCG iterations on the full-size workload ({wall:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_samples": p.n_samples, "unknowns": int(n_obs * 3),
+                           "fft_len": plan.stats["fft_len"], "n_tiles": plan.stats["n_tiles"],
+                           "l2_flush": "inputs larger than L2 (pix+psi+d = 201 MB > 129 MB L2)",
+                           "replicas": "one independent problem per rank"},
+                "time_to_1e-6_map_error": {
+                    "mixed_ms": ms_max / args.steps, "mixed_iters": iters // max(args.steps, 1),
+                    "mixed_rel_tol": tol_mixed, "mixed_map_err": err_mixed, "mixed_map_err_IQU": per_mixed,
+                    "mixed_outer": info_mixed["outer_iters"],
+                    "fp64_ms": ms_fp64, "fp64_iters": i64["iters"], "fp64_rel_tol": tol_64,
+                    "fp64_map_err": err_64, "speedup_mixed_vs_fp64": ms_fp64 / (ms_max / args.steps),
+                    "reference": f"FP64 GPU solve to rel. residual 1e-11 ({rinfo['iters']} iterations)"},
+                "roofline": roofline,
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(p.n_samples * 4),
+                        "d2h_bytes_per_step": int(n_obs * 3 * 8)},
+                "gpu_launches": int(launches),
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

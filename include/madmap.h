@@ -184,6 +184,23 @@ void madmap_solve_opts_default(madmap_solve_opts* opts);
 madmap_status madmap_solve(madmap_plan_t plan, const float* d, double* m, const madmap_solve_opts* opts,
                            madmap_solve_info* info, void* stream);
 
+/* ------------------------------------------------------------------ diagnostics */
+
+/* Number of kernels this library has launched in the process (each kernel
+ * node of a replayed CUDA graph counts once per replay; kernels that return
+ * at once because a solve already finished still count). */
+int64_t madmap_kernel_launch_count(void);
+
+/* Times the operator H = A^T N^-1 A in the plan's launch configuration:
+ * `reps` applications to the plan's current search-direction buffer, with
+ * CUDA events recorded on `stream` around every launch of each of the three
+ * operator kernels (gather + column FFTs; row FFTs x filter spectrum; inverse
+ * column FFTs + scatter).  ms_out (host [3]) receives the mean duration of one
+ * launch of each kernel; launches_out (host [3], may be NULL) the launches of
+ * each kernel per application.  Synchronises `stream`.  precision: FP64 or FP32. */
+madmap_status madmap_time_operator(madmap_plan_t plan, int32_t precision, int32_t reps, double* ms_out,
+                                   int32_t* launches_out, void* stream);
+
 /* ------------------------------------------------------------------ host helpers */
 
 /* Inverse-noise filter lags from the PSD p(f) = sigma^2 (1 + (fknee/f)^alpha)

@@ -21,7 +21,8 @@ from ._lib import (MADMAP_FP32, MADMAP_FP64, MADMAP_MIXED, MadmapError, check, l
 __all__ = ["Plan", "noise_filter", "paper_fft_length", "MadmapError", "load", "library_path",
            "madmap_plan_create", "madmap_plan_destroy", "madmap_plan_get_stats", "madmap_plan_observed",
            "madmap_plan_set_filters", "madmap_apply_ATNA", "madmap_rhs", "madmap_apply_ninv", "madmap_solve",
-           "madmap_noise_filter", "madmap_paper_fft_length", "madmap_last_error"]
+           "madmap_noise_filter", "madmap_paper_fft_length", "madmap_last_error", "madmap_kernel_launch_count",
+           "madmap_time_operator"]
 
 _PREC = {"fp64": MADMAP_FP64, "mixed": MADMAP_MIXED, "fp32": MADMAP_FP32,
          MADMAP_FP64: MADMAP_FP64, MADMAP_MIXED: MADMAP_MIXED, MADMAP_FP32: MADMAP_FP32}
@@ -118,6 +119,18 @@ def madmap_paper_fft_length(n_lags, longest) -> int:
     return int(load().madmap_paper_fft_length(int(n_lags), int(longest)))
 
 
+def madmap_kernel_launch_count() -> int:
+    return int(load().madmap_kernel_launch_count())
+
+
+def madmap_time_operator(h, precision, reps, stream=None):
+    ms = np.zeros(3)
+    n = np.zeros(3, dtype=np.int32)
+    check(load().madmap_time_operator(h, precision, int(reps), ms.ctypes.data, n.ctypes.data,
+                                      C.c_void_p(_stream_ptr(stream))), "madmap_time_operator")
+    return ms, n
+
+
 def madmap_last_error() -> str:
     return load().madmap_last_error().decode(errors="replace")
 
@@ -181,6 +194,11 @@ class Plan:
         e = torch.empty(max(self.n_obs, 1), dtype=torch.uint8, device="cuda")
         madmap_plan_observed(self._h, o.data_ptr(), e.data_ptr(), stream)
         return o[:self.n_obs], e[:self.n_obs]
+
+    def time_operator(self, precision="fp32", reps=10, stream=None):
+        """Mean duration (ms) of one launch of each of the three operator kernels, and
+        the launches of each per operator application."""
+        return madmap_time_operator(self._h, _PREC[precision], reps, stream)
 
     def set_filters(self, filter_lags, stream=None):
         madmap_plan_set_filters(self._h, np.atleast_2d(filter_lags), stream)

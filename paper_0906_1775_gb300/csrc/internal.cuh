@@ -113,6 +113,18 @@ madmap_status op_launch(Plan* p, bool fp64, int in_mode, int out_mode, const voi
 
 size_t f1_smem_bytes(const Plan* p, bool fp64);
 
+// Per-kernel event timing of the map-to-map operator (ms[3]: mean per launch).
+madmap_status op_time(Plan* p, bool fp64, const void* in, void* out, int reps, double ms[3], cudaStream_t s);
+
+// Resident CTAs per SM of the operator kernels and CTAs per tile.
+void op_occupancy(const Plan* p, bool fp64, int& ctas_per_sm, int& ctas_per_tile);
+
+// Number of operator launches per application and tiles per launch.
+void chunking(const Plan* p, int& n_chunks, int& per_chunk);
+
+// Kernel launch accounting (library-wide).
+void count_launches(long long n);
+
 // host FFT (radix 2, float64), used at plan time only
 void host_fft(std::vector<double>& re, std::vector<double>& im, bool inverse);
 
@@ -162,86 +174,200 @@ __device__ __forceinline__ C csub(C a, C b) {
 __device__ __forceinline__ int sidx(int i) { return i + (i >> 5); }
 __host__ __device__ inline int row_stride(int n) { return n + (n >> 5) + 1; }
 
-// One pass of in-place radix-2 decimation-in-frequency (forward) or
-// decimation-in-time (inverse, conjugate twiddles) stages, R = 1..3 stages fused
-// in registers.  `s` is the index of the first stage; stage s has span
-// N >> (s+1).  Each thread owns groups of 2^R elements spaced hR = N >> (s+R)
-// apart.  tw[k] = exp(-2 pi i k / N), k < N/2.  Forward passes run s = 0, 3,
-// 6, ...; the output is in bit-reversed order.  The inverse runs the same
-// passes in reverse order and returns N times the input.
+// Multiplication by the constant w8^k = exp(-2 pi i k / 8), k = 0..3, or its
+// conjugate, written out so no general complex product is spent on it.
+template <int K, bool CONJ, typename C>
+__device__ __forceinline__ C mul_w8(C v) {
+  typedef decltype(v.x) R;
+  const R h = (R)0.70710678118654752440;
+  C r;
+  if (K == 0) return v;
+  if (K == 2) {  // -i (conj: +i)
+    if (!CONJ) { r.x = v.y; r.y = -v.x; } else { r.x = -v.y; r.y = v.x; }
+    return r;
+  }
+  if (K == 1) {  // (1 - i)/sqrt2 (conj: (1 + i)/sqrt2)
+    if (!CONJ) { r.x = (v.x + v.y) * h; r.y = (v.y - v.x) * h; } else { r.x = (v.x - v.y) * h; r.y = (v.x + v.y) * h; }
+    return r;
+  }
+  // K == 3: (-1 - i)/sqrt2 (conj: (-1 + i)/sqrt2)
+  if (!CONJ) { r.x = (v.y - v.x) * h; r.y = -(v.x + v.y) * h; } else { r.x = -(v.x + v.y) * h; r.y = (v.x - v.y) * h; }
+  return r;
+}
+
+template <int R>
+__device__ __forceinline__ constexpr int brev_small(int m) {
+  return R == 1 ? m : (R == 2 ? (((m & 1) << 1) | (m >> 1)) : (((m & 1) << 2) | (m & 2) | (m >> 2)));
+}
+
+// 2^R-point DFT of v in registers with the output in bit-reversed order
+// (R radix-2 decimation-in-frequency stages with constant twiddles), or its
+// exact inverse (input in bit-reversed order, unnormalised).
 template <typename C, int R, bool INV>
-__device__ __forceinline__ void fft_pass(C* buf, int rows, int rs, int logN, int s, const C* tw) {
-  const int logh = logN - s - R;
-  const int hR = 1 << logh;
-  const int gpr_log = logN - R;  // groups per row = N >> R
-  const int total = rows << gpr_log;
-  for (int g = threadIdx.x; g < total; g += blockDim.x) {
-    const int row = g >> gpr_log;
-    const int gr = g & ((1 << gpr_log) - 1);
-    const int blk = gr >> logh;
-    const int j = gr & (hR - 1);
-    const int base = (blk << (logh + R)) + j;
-    C* rp = buf + row * rs;
-    C v[1 << R];
+__device__ __forceinline__ void small_dft(C (&v)[1 << R]) {
+  if (!INV) {
 #pragma unroll
-    for (int m = 0; m < (1 << R); ++m) v[m] = rp[sidx(base + m * hR)];
-    if (!INV) {
+    for (int st = 0; st < R; ++st) {
+      const int span = 1 << (R - 1 - st);
 #pragma unroll
-      for (int st = 0; st < R; ++st) {
-        const int span = 1 << (R - 1 - st);
-#pragma unroll
-        for (int m = 0; m < (1 << R); ++m) {
-          if ((m & span) == 0) {
-            const int pos = j + (m & (span - 1)) * hR;
-            const C w = tw[pos << (s + st)];
-            const C x = v[m], y = v[m + span];
-            v[m] = cadd(x, y);
-            v[m + span] = cmul(csub(x, y), w);
-          }
-        }
-      }
-    } else {
-#pragma unroll
-      for (int st = R - 1; st >= 0; --st) {
-        const int span = 1 << (R - 1 - st);
-#pragma unroll
-        for (int m = 0; m < (1 << R); ++m) {
-          if ((m & span) == 0) {
-            const int pos = j + (m & (span - 1)) * hR;
-            const C w = tw[pos << (s + st)];
-            const C x = v[m];
-            const C y = cmulc(v[m + span], w);
-            v[m] = cadd(x, y);
-            v[m + span] = csub(x, y);
-          }
+      for (int m = 0; m < (1 << R); ++m) {
+        if ((m & span) == 0) {
+          const C x = v[m], y = v[m + span];
+          const C d = csub(x, y);
+          v[m] = cadd(x, y);
+          const int k8 = ((m & (span - 1)) << st) << (3 - R);
+          v[m + span] = k8 == 0 ? d : (k8 == 1 ? mul_w8<1, false>(d) : (k8 == 2 ? mul_w8<2, false>(d) : mul_w8<3, false>(d)));
         }
       }
     }
+  } else {
 #pragma unroll
-    for (int m = 0; m < (1 << R); ++m) rp[sidx(base + m * hR)] = v[m];
+    for (int st = R - 1; st >= 0; --st) {
+      const int span = 1 << (R - 1 - st);
+#pragma unroll
+      for (int m = 0; m < (1 << R); ++m) {
+        if ((m & span) == 0) {
+          const int k8 = ((m & (span - 1)) << st) << (3 - R);
+          const C b = v[m + span];
+          const C y = k8 == 0 ? b : (k8 == 1 ? mul_w8<1, true>(b) : (k8 == 2 ? mul_w8<2, true>(b) : mul_w8<3, true>(b)));
+          const C x = v[m];
+          v[m] = cadd(x, y);
+          v[m + span] = csub(x, y);
+        }
+      }
+    }
   }
 }
 
-// Full FFT of `rows` rows of length N = 2^logN held in shared memory.
+// Group geometry of a pass: R radix-2 stages starting at stage s of an
+// N = 2^logN transform; group g of a row owns the 2^R elements
+// base + m * hR (m = 0 .. 2^R - 1) and its output twiddles are
+// tw[(j << s) * brev_R(m)], tw[k] = exp(-2 pi i k / N) for k < N.
+struct PassGeom {
+  int logh, hR, gpr_log;
+  __device__ __forceinline__ PassGeom(int logN, int s, int R) {
+    logh = logN - s - R;
+    hR = 1 << logh;
+    gpr_log = logN - R;
+  }
+  __device__ __forceinline__ void group(int g, int R, int& row, int& base, int& j) const {
+    row = g >> gpr_log;
+    const int gr = g & ((1 << gpr_log) - 1);
+    const int blk = gr >> logh;
+    j = gr & (hR - 1);
+    base = (blk << (logh + R)) + j;
+  }
+};
+
+// One radix-2^R pass (R = 1..3) over `rows` rows held in shared memory:
+// forward = small DFT then output twiddles (decimation in frequency, output
+// bit-reversed after all passes); inverse = conjugate twiddles then inverse
+// small DFT, passes in reverse order, returning N times the input.
+template <typename C, int R, bool INV>
+__device__ __forceinline__ void fft_pass(C* buf, int rows, int rs, int logN, int s, const C* tw) {
+  const PassGeom G(logN, s, R);
+  const int total = rows << G.gpr_log;
+  for (int g = threadIdx.x; g < total; g += blockDim.x) {
+    int row, base, j;
+    G.group(g, R, row, base, j);
+    C* rp = buf + row * rs;
+    C v[1 << R];
+#pragma unroll
+    for (int m = 0; m < (1 << R); ++m) v[m] = rp[sidx(base + m * G.hR)];
+    const int js = j << s;
+    if (!INV) {
+      small_dft<C, R, false>(v);
+#pragma unroll
+      for (int m = 1; m < (1 << R); ++m) v[m] = cmul(v[m], tw[js * brev_small<R>(m)]);
+    } else {
+#pragma unroll
+      for (int m = 1; m < (1 << R); ++m) v[m] = cmulc(v[m], tw[js * brev_small<R>(m)]);
+      small_dft<C, R, true>(v);
+    }
+#pragma unroll
+    for (int m = 0; m < (1 << R); ++m) rp[sidx(base + m * G.hR)] = v[m];
+  }
+}
+
+template <typename C, bool INV>
+__device__ __forceinline__ void fft_pass_any(C* buf, int rows, int rs, int logN, int s, const C* tw) {
+  const int R = (logN - s) >= 3 ? 3 : (logN - s);
+  if (R == 3) fft_pass<C, 3, INV>(buf, rows, rs, logN, s, tw);
+  else if (R == 2) fft_pass<C, 2, INV>(buf, rows, rs, logN, s, tw);
+  else fft_pass<C, 1, INV>(buf, rows, rs, logN, s, tw);
+}
+
+__host__ __device__ __forceinline__ int last_pass_start(int logN) { return ((logN - 1) / 3) * 3; }
+
+// Full FFT of `rows` rows of length N = 2^logN held in shared memory
+// (tw: N entries).
 template <typename C, bool INV>
 __device__ void fft_rows(C* buf, int rows, int rs, int logN, const C* tw) {
   if (!INV) {
     for (int s = 0; s < logN; s += 3) {
-      const int R = (logN - s) >= 3 ? 3 : (logN - s);
-      if (R == 3) fft_pass<C, 3, false>(buf, rows, rs, logN, s, tw);
-      else if (R == 2) fft_pass<C, 2, false>(buf, rows, rs, logN, s, tw);
-      else fft_pass<C, 1, false>(buf, rows, rs, logN, s, tw);
+      fft_pass_any<C, false>(buf, rows, rs, logN, s, tw);
       __syncthreads();
     }
   } else {
-    int last = ((logN - 1) / 3) * 3;
-    for (int s = last; s >= 0; s -= 3) {
-      const int R = (logN - s) >= 3 ? 3 : (logN - s);
-      if (R == 3) fft_pass<C, 3, true>(buf, rows, rs, logN, s, tw);
-      else if (R == 2) fft_pass<C, 2, true>(buf, rows, rs, logN, s, tw);
-      else fft_pass<C, 1, true>(buf, rows, rs, logN, s, tw);
+    for (int s = last_pass_start(logN); s >= 0; s -= 3) {
+      fft_pass_any<C, true>(buf, rows, rs, logN, s, tw);
       __syncthreads();
     }
+  }
+}
+
+// Forward FFT, pointwise product with a real spectrum and inverse FFT of
+// `rows` rows: the last forward pass, the product and the first inverse pass
+// act on the same element groups, so they run back to back in registers.
+// Hrow(row) points at the row's spectrum (bit-reversed order, as the forward
+// transform leaves it).
+template <typename C, int R, typename HF>
+__device__ __forceinline__ void fused_middle(C* buf, int rows, int rs, int logN, int s, HF Hrow) {
+  typedef decltype(C().x) Real;
+  const PassGeom G(logN, s, R);
+  const int total = rows << G.gpr_log;
+  for (int g = threadIdx.x; g < total; g += blockDim.x) {
+    int row, base, j;
+    G.group(g, R, row, base, j);
+    C* rp = buf + row * rs;
+    const Real* H = Hrow(row);
+    C v[1 << R];
+    Real hv[1 << R];
+#pragma unroll
+    for (int m = 0; m < (1 << R); ++m) {
+      v[m] = rp[sidx(base + m * G.hR)];
+      hv[m] = H[base + m * G.hR];
+    }
+    // The forward pass ends with output twiddles w and the inverse pass starts
+    // with their conjugates; |w| = 1, so between the two small DFTs only the
+    // filter product remains.
+    small_dft<C, R, false>(v);
+#pragma unroll
+    for (int m = 0; m < (1 << R); ++m) {
+      v[m].x *= hv[m];
+      v[m].y *= hv[m];
+    }
+    small_dft<C, R, true>(v);
+#pragma unroll
+    for (int m = 0; m < (1 << R); ++m) rp[sidx(base + m * G.hR)] = v[m];
+  }
+}
+
+template <typename C, typename HF>
+__device__ void fft_rows_filter(C* buf, int rows, int rs, int logN, const C* tw, HF Hrow) {
+  const int sl = last_pass_start(logN);
+  for (int s = 0; s < sl; s += 3) {
+    fft_pass_any<C, false>(buf, rows, rs, logN, s, tw);
+    __syncthreads();
+  }
+  const int R = logN - sl;
+  if (R == 3) fused_middle<C, 3>(buf, rows, rs, logN, sl, Hrow);
+  else if (R == 2) fused_middle<C, 2>(buf, rows, rs, logN, sl, Hrow);
+  else fused_middle<C, 1>(buf, rows, rs, logN, sl, Hrow);
+  __syncthreads();
+  for (int s = sl - 3; s >= 0; s -= 3) {
+    fft_pass_any<C, true>(buf, rows, rs, logN, s, tw);
+    __syncthreads();
   }
 }
 

@@ -20,6 +20,9 @@
 // The row/column FFTs run in shared memory as radix-2 stages fused three at a
 // time in registers; forward transforms leave bit-reversed order and the
 // inverses consume it, so no reordering pass exists anywhere.
+#include <algorithm>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace mm {
@@ -47,9 +50,21 @@ struct OpArgs {
 
 template <typename Real>
 __device__ __forceinline__ void weights(const OpArgs& a, long long t, Real& c, Real& s);
+// cos 2psi, sin 2psi for the float32 operator: 2 psi is reduced to [-pi, pi]
+// by subtracting the nearest multiple of 2 pi in two parts (2 pi rounded to
+// float, then the remainder of 2 pi), and the hardware approximations take
+// it from there (absolute error about 4e-7 on [-pi, pi], far inside the
+// float32 operator's own rounding; the float64 operator uses exact weights).
+__device__ __forceinline__ void sincos_2psi(float psi, float& s, float& c) {
+  const float x = 2.0f * psi;
+  const float k = rintf(x * 0.15915494309189535f);
+  float r = fmaf(-k, 6.2831854820251465f, x);
+  r = fmaf(-k, -1.7484556000744970e-07f, r);
+  __sincosf(r, &s, &c);
+}
 template <>
 __device__ __forceinline__ void weights<float>(const OpArgs& a, long long t, float& c, float& s) {
-  sincosf(2.0f * a.psi[t], &s, &c);
+  sincos_2psi(a.psi[t], s, c);
 }
 template <>
 __device__ __forceinline__ void weights<double>(const OpArgs& a, long long t, double& c, double& s) {
@@ -102,49 +117,77 @@ __device__ __forceinline__ void scatter<double, 3>(double* y, int p, double v, d
   atomicAdd(q + 2, v * s);
 }
 
-template <typename Real, int NS, int IN>
-__device__ __forceinline__ Real load_sample(const OpArgs& a, const Lane& L, int n) {
-  const long long t = L.ws + n;
-  if (t < L.lo || t >= L.hi) return Real(0);
-  if (IN == IN_TODF) return (Real)(static_cast<const float*>(a.in)[L.rhs * a.in_stride + t]);
-  if (IN == IN_TODR) return static_cast<const Real*>(a.in)[L.rhs * a.in_stride + t];
-  const int p = a.pix[t];
-  if (p < 0) return Real(0);
-  Real c = 0, s = 0;
-  if (NS == 3) weights<Real>(a, t, c, s);
-  return gather<Real, NS>(static_cast<const Real*>(a.in) + L.rhs * a.in_stride, p, c, s);
+// A lane seen from one CTA: valid input window positions [in_lo, in_hi),
+// kept outputs [out_lo, out_hi), and base pointers already offset by the
+// window start so every access is base[n] with a 32-bit window position n.
+template <typename Real>
+struct LaneView {
+  int in_lo, in_hi, out_lo, out_hi;
+  const int* pix;
+  const float* psi;
+  const double2* cs;
+  const void* in;
+  void* out;
+};
+
+template <typename Real, int IN, int OUT>
+__device__ __forceinline__ LaneView<Real> lane_view(const OpArgs& a, const Lane& g) {
+  LaneView<Real> v;
+  const long long ws = g.ws;
+  long long lo = g.lo - ws, hi = g.hi - ws;
+  lo = lo < 0 ? 0 : (lo > a.M ? a.M : lo);
+  hi = hi < lo ? lo : (hi > a.M ? a.M : hi);
+  v.in_lo = (int)lo;
+  v.in_hi = (int)hi;
+  v.out_lo = g.out_lo;
+  v.out_hi = g.out_hi;
+  v.pix = a.pix + ws;
+  v.psi = a.psi + ws;
+  v.cs = a.cs64 + ws;
+  if (IN == IN_TODF) v.in = static_cast<const float*>(a.in) + g.rhs * a.in_stride + ws;
+  else if (IN == IN_TODR) v.in = static_cast<const Real*>(a.in) + g.rhs * a.in_stride + ws;
+  else v.in = static_cast<const Real*>(a.in) + g.rhs * a.in_stride;
+  if (OUT == OUT_TOD) v.out = static_cast<Real*>(a.out) + g.rhs * a.out_stride + ws;
+  else v.out = static_cast<Real*>(a.out) + g.rhs * a.out_stride;
+  return v;
 }
 
-template <typename Real, int NS, int OUT>
-__device__ __forceinline__ void emit_sample(const OpArgs& a, const Lane& L, int n, Real v) {
-  if (n < L.out_lo || n >= L.out_hi) return;
-  const long long t = L.ws + n;
-  if (OUT == OUT_TOD) {
-    static_cast<Real*>(a.out)[L.rhs * a.out_stride + t] = v;
-    return;
+__device__ __forceinline__ bool in_range(int n, int lo, int hi) { return (unsigned)(n - lo) < (unsigned)(hi - lo); }
+
+// cos/sin weights of window position n of a lane (psi or cached float64 pair)
+template <typename Real>
+__device__ __forceinline__ void lane_angle(const LaneView<Real>& L, int n, bool ok, Real& c, Real& s);
+template <>
+__device__ __forceinline__ void lane_angle<float>(const LaneView<float>& L, int n, bool ok, float& c, float& s) {
+  c = ok ? __ldg(L.psi + n) : 0.f;  // the angle; turned into weights after the loads
+  s = 0.f;
+}
+template <>
+__device__ __forceinline__ void lane_angle<double>(const LaneView<double>& L, int n, bool ok, double& c, double& s) {
+  if (ok) {
+    const double2 cs = L.cs[n];
+    c = cs.x;
+    s = cs.y;
+  } else {
+    c = s = 0.0;
   }
-  const int p = a.pix[t];
-  if (p < 0) return;
-  Real c = 0, s = 0;
-  if (NS == 3) weights<Real>(a, t, c, s);
-  scatter<Real, NS>(static_cast<Real*>(a.out) + L.rhs * a.out_stride, p, v, c, s);
+}
+template <typename Real>
+__device__ __forceinline__ void finish_angle(Real& c, Real& s) {}
+template <>
+__device__ __forceinline__ void finish_angle<float>(float& c, float& s) {
+  const float psi = c;
+  sincos_2psi(psi, s, c);
 }
 
-__device__ __forceinline__ Lane load_lane(const Lane& g) {
-  Lane L;
-  L.ws = g.ws;
-  L.lo = g.lo;
-  L.hi = g.hi;
-  L.out_lo = g.out_lo;
-  L.out_hi = g.out_hi;
-  L.rhs = g.rhs;
-  L.pad = 0;
-  return L;
-}
+// The memory phases below work in batches: every thread first issues all the
+// independent loads of U elements (pointing, then map gathers; or scratch and
+// twiddles), and only then consumes them, so each thread keeps U loads in
+// flight instead of one.
 
 // ---------------------------------------------------------------- k_f1
 template <typename Real, int NS, int IN>
-__global__ void __launch_bounds__(256) k_f1(OpArgs a) {
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a) {
   typedef typename CxT<Real>::type C;
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -152,38 +195,95 @@ __global__ void __launch_bounds__(256) k_f1(OpArgs a) {
   const int rs = row_stride(a.N2);
   C* tw = buf + a.B1 * rs;
   const C* twM = static_cast<const C*>(a.tw);
-  for (int k = threadIdx.x; k < (a.N2 >> 1); k += blockDim.x) tw[k] = twM[(long long)k * a.N1];
+  for (int k = threadIdx.x; k < a.N2; k += blockDim.x) tw[k] = twM[(long long)k * a.N1];
   const int tl = blockIdx.y;
   const Tile* T = a.tiles + a.tile0 + tl;
-  const Lane L0 = load_lane(T->l[0]);
-  const Lane L1 = load_lane(T->l[1]);
+  LaneView<Real> L[2];
+  L[0] = lane_view<Real, IN, OUT_MAP>(a, T->l[0]);
+  L[1] = lane_view<Real, IN, OUT_MAP>(a, T->l[1]);
   const int n1_0 = blockIdx.x * a.B1;
   const int total = a.B1 << a.logN2;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int j = e & (a.B1 - 1);
-    const int n2 = e >> a.logB1;
-    const int n = n1_0 + j + (n2 << a.logN1);
-    C v;
-    v.x = load_sample<Real, NS, IN>(a, L0, n);
-    v.y = load_sample<Real, NS, IN>(a, L1, n);
-    buf[j * rs + sidx(n2)] = v;
+  const int bd = blockDim.x;
+  constexpr int U = (IN == IN_MAPX && NS == 3) ? 4 : 8;
+  for (int e0 = threadIdx.x; e0 < total; e0 += bd * U) {
+    int nn[U];
+    bool ok[2][U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * bd;
+      nn[u] = n1_0 + (e & (a.B1 - 1)) + ((e >> a.logB1) << a.logN1);
+#pragma unroll
+      for (int l = 0; l < 2; ++l) ok[l][u] = e < total && in_range(nn[u], L[l].in_lo, L[l].in_hi);
+    }
+    Real v[2][U];
+    if (IN != IN_MAPX) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+          if (IN == IN_TODF)
+            v[l][u] = ok[l][u] ? (Real)__ldg(static_cast<const float*>(L[l].in) + nn[u]) : Real(0);
+          else
+            v[l][u] = ok[l][u] ? static_cast<const Real*>(L[l].in)[nn[u]] : Real(0);
+        }
+    } else {
+      int pp[2][U];
+      Real cc[2][U], ss[2][U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+          pp[l][u] = ok[l][u] ? __ldg(L[l].pix + nn[u]) : -1;
+          cc[l][u] = ss[l][u] = 0;
+          if (NS == 3) lane_angle<Real>(L[l], nn[u], ok[l][u], cc[l][u], ss[l][u]);
+        }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+          Real c = cc[l][u], sn = ss[l][u];
+          if (NS == 3) finish_angle<Real>(c, sn);
+          v[l][u] = pp[l][u] >= 0 ? gather<Real, NS>(static_cast<const Real*>(L[l].in), pp[l][u], c, sn) : Real(0);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * bd;
+      if (e < total) {
+        C z;
+        z.x = v[0][u];
+        z.y = v[1][u];
+        buf[(e & (a.B1 - 1)) * rs + sidx(e >> a.logB1)] = z;
+      }
+    }
   }
   __syncthreads();
   fft_rows<C, false>(buf, a.B1, rs, a.logN2, tw);
   C* sc = static_cast<C*>(a.scratch) + (long long)tl * a.M;
   const int mask = a.M - 1;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int j = e & (a.B1 - 1);
-    const int pos = e >> a.logB1;
-    const int n1 = n1_0 + j;
-    const int k2 = brev_n(pos, a.logN2);
-    sc[(long long)pos * a.N1 + n1] = cmul(buf[j * rs + sidx(pos)], twM[(n1 * k2) & mask]);
+  for (int e0 = threadIdx.x; e0 < total; e0 += bd * 8) {
+    C w[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * bd;
+      const int n1 = n1_0 + (e & (a.B1 - 1));
+      const int k2 = brev_n(e >> a.logB1, a.logN2);
+      if (e < total) w[u] = twM[(n1 * k2) & mask];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * bd;
+      if (e < total) {
+        const int j = e & (a.B1 - 1), pos = e >> a.logB1;
+        sc[(long long)pos * a.N1 + n1_0 + j] = cmul(buf[j * rs + sidx(pos)], w[u]);
+      }
+    }
   }
 }
 
 // ---------------------------------------------------------------- k_f2
 template <typename Real>
-__global__ void __launch_bounds__(256) k_f2(OpArgs a) {
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f2(OpArgs a) {
   typedef typename CxT<Real>::type C;
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -191,41 +291,35 @@ __global__ void __launch_bounds__(256) k_f2(OpArgs a) {
   const int rs = row_stride(a.N1);
   C* tw = buf + a.B2 * rs;
   const C* twM = static_cast<const C*>(a.tw);
-  for (int k = threadIdx.x; k < (a.N1 >> 1); k += blockDim.x) tw[k] = twM[(long long)k * a.N2];
+  for (int k = threadIdx.x; k < a.N1; k += blockDim.x) tw[k] = twM[(long long)k * a.N2];
   const int tl = blockIdx.y;
   const Tile* T = a.tiles + a.tile0 + tl;
   const int filt = T->filter;
   const int pos0 = blockIdx.x * a.B2;
   C* sc = static_cast<C*>(a.scratch) + (long long)tl * a.M + (long long)pos0 * a.N1;
   const int total = a.B2 << a.logN1;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int i = e >> a.logN1;
-    const int n1 = e & (a.N1 - 1);
-    buf[i * rs + sidx(n1)] = sc[e];
+  const int bd = blockDim.x;
+  for (int e0 = threadIdx.x; e0 < total; e0 += bd * 8) {
+    C v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (e0 + u * bd < total) v[u] = sc[e0 + u * bd];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * bd;
+      if (e < total) buf[(e >> a.logN1) * rs + sidx(e & (a.N1 - 1))] = v[u];
+    }
   }
   __syncthreads();
-  fft_rows<C, false>(buf, a.B2, rs, a.logN1, tw);
   const Real* H = static_cast<const Real*>(a.H) + (long long)filt * a.M + (long long)pos0 * a.N1;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int i = e >> a.logN1;
-    const int p1 = e & (a.N1 - 1);
-    const Real h = H[e];
-    C& z = buf[i * rs + sidx(p1)];
-    z.x *= h;
-    z.y *= h;
-  }
-  __syncthreads();
-  fft_rows<C, true>(buf, a.B2, rs, a.logN1, tw);
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int i = e >> a.logN1;
-    const int n1 = e & (a.N1 - 1);
-    sc[e] = buf[i * rs + sidx(n1)];
-  }
+  const int N1 = a.N1;
+  fft_rows_filter<C>(buf, a.B2, rs, a.logN1, tw, [H, N1](int row) { return H + (long long)row * N1; });
+  for (int e = threadIdx.x; e < total; e += bd) sc[e] = buf[(e >> a.logN1) * rs + sidx(e & (a.N1 - 1))];
 }
 
 // ---------------------------------------------------------------- k_f3
 template <typename Real, int NS, int OUT>
-__global__ void __launch_bounds__(256) k_f3(OpArgs a) {
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a) {
   typedef typename CxT<Real>::type C;
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -233,37 +327,99 @@ __global__ void __launch_bounds__(256) k_f3(OpArgs a) {
   const int rs = row_stride(a.N2);
   C* tw = buf + a.B1 * rs;
   const C* twM = static_cast<const C*>(a.tw);
-  for (int k = threadIdx.x; k < (a.N2 >> 1); k += blockDim.x) tw[k] = twM[(long long)k * a.N1];
+  for (int k = threadIdx.x; k < a.N2; k += blockDim.x) tw[k] = twM[(long long)k * a.N1];
   const int tl = blockIdx.y;
   const Tile* T = a.tiles + a.tile0 + tl;
-  const Lane L0 = load_lane(T->l[0]);
-  const Lane L1 = load_lane(T->l[1]);
+  LaneView<Real> L[2];
+  L[0] = lane_view<Real, IN_MAPX, OUT>(a, T->l[0]);
+  L[1] = lane_view<Real, IN_MAPX, OUT>(a, T->l[1]);
   const int n1_0 = blockIdx.x * a.B1;
   const int total = a.B1 << a.logN2;
+  const int bd = blockDim.x;
   const C* sc = static_cast<const C*>(a.scratch) + (long long)tl * a.M;
   const int mask = a.M - 1;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int j = e & (a.B1 - 1);
-    const int pos = e >> a.logB1;
-    const int n1 = n1_0 + j;
-    const int k2 = brev_n(pos, a.logN2);
-    buf[j * rs + sidx(pos)] = cmulc(sc[(long long)pos * a.N1 + n1], twM[(n1 * k2) & mask]);
+  for (int e0 = threadIdx.x; e0 < total; e0 += bd * 8) {
+    C v[8], w[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * bd;
+      if (e < total) {
+        const int n1 = n1_0 + (e & (a.B1 - 1));
+        const int pos = e >> a.logB1;
+        v[u] = sc[(long long)pos * a.N1 + n1];
+        w[u] = twM[(n1 * brev_n(pos, a.logN2)) & mask];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * bd;
+      if (e < total) buf[(e & (a.B1 - 1)) * rs + sidx(e >> a.logB1)] = cmulc(v[u], w[u]);
+    }
   }
   __syncthreads();
   fft_rows<C, true>(buf, a.B1, rs, a.logN2, tw);
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int j = e & (a.B1 - 1);
-    const int n2 = e >> a.logB1;
-    const int n = n1_0 + j + (n2 << a.logN1);
-    const C v = buf[j * rs + sidx(n2)];
-    emit_sample<Real, NS, OUT>(a, L0, n, v.x);
-    emit_sample<Real, NS, OUT>(a, L1, n, v.y);
+  constexpr int U = 8;
+  for (int e0 = threadIdx.x; e0 < total; e0 += bd * U) {
+    int nn[U];
+    bool ok[2][U];
+    Real val[2][U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * bd;
+      const int j = e & (a.B1 - 1), n2 = e >> a.logB1;
+      nn[u] = n1_0 + j + (n2 << a.logN1);
+      C z;
+      z.x = z.y = 0;
+      if (e < total) z = buf[j * rs + sidx(n2)];
+      val[0][u] = z.x;
+      val[1][u] = z.y;
+#pragma unroll
+      for (int l = 0; l < 2; ++l) ok[l][u] = e < total && in_range(nn[u], L[l].out_lo, L[l].out_hi);
+    }
+    if (OUT == OUT_TOD) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int l = 0; l < 2; ++l)
+          if (ok[l][u]) static_cast<Real*>(L[l].out)[nn[u]] = val[l][u];
+    } else {
+      int pp[2][U];
+      Real cc[2][U], ss[2][U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+          pp[l][u] = ok[l][u] ? __ldg(L[l].pix + nn[u]) : -1;
+          cc[l][u] = ss[l][u] = 0;
+          if (NS == 3) lane_angle<Real>(L[l], nn[u], ok[l][u], cc[l][u], ss[l][u]);
+        }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+          if (pp[l][u] < 0) continue;
+          Real c = cc[l][u], sn = ss[l][u];
+          if (NS == 3) finish_angle<Real>(c, sn);
+          scatter<Real, NS>(static_cast<Real*>(L[l].out), pp[l][u], val[l][u], c, sn);
+        }
+    }
   }
 }
 
+}  // namespace
+
+// Tiles are processed in n_chunks launches of (nearly) equal size, at most
+// tiles_per_chunk each, so no launch is left with a small tail of work.
+void chunking(const Plan* p, int& n_chunks, int& per_chunk) {
+  n_chunks = p->n_tiles ? (p->n_tiles + p->tiles_per_chunk - 1) / p->tiles_per_chunk : 0;
+  per_chunk = n_chunks ? (p->n_tiles + n_chunks - 1) / n_chunks : 0;
+}
+
+namespace {
+
 template <typename Real>
 inline int elems_per_cta() {
-  return sizeof(Real) == 4 ? 8192 : 4096;
+  return sizeof(Real) == 4 ? 4096 : 2048;
 }
 
 template <typename Real>
@@ -281,13 +437,13 @@ template <typename Real>
 size_t smem_f13(const Plan* p) {
   int B1, B2;
   geometry<Real>(p, B1, B2);
-  return (size_t)(B1 * row_stride(p->N2) + (p->N2 >> 1)) * sizeof(typename CxT<Real>::type);
+  return (size_t)(B1 * row_stride(p->N2) + p->N2) * sizeof(typename CxT<Real>::type);
 }
 template <typename Real>
 size_t smem_f2(const Plan* p) {
   int B1, B2;
   geometry<Real>(p, B1, B2);
-  return (size_t)(B2 * row_stride(p->N1) + (p->N1 >> 1)) * sizeof(typename CxT<Real>::type);
+  return (size_t)(B2 * row_stride(p->N1) + p->N1) * sizeof(typename CxT<Real>::type);
 }
 
 template <typename K>
@@ -297,7 +453,7 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 
 template <typename Real, int NS, int IN, int OUT>
 madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride, long long out_stride,
-                         int n_rhs, const int* skip, cudaStream_t s) {
+                         int n_rhs, const int* skip, cudaStream_t s, cudaEvent_t* ev = nullptr, int reps = 1) {
   OpArgs a;
   a.M = p->M;
   a.N1 = p->N1;
@@ -327,21 +483,31 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
     MM_CUDA(set_smem(k_f2<Real>, sm2));
     set2 = sm2;
   }
-  for (int r = 0; r < n_rhs; ++r) {
-    a.in = static_cast<const char*>(in) + (size_t)r * in_stride *
-                                              (IN == IN_TODF ? sizeof(float) : sizeof(Real));
-    a.out = static_cast<char*>(out) + (size_t)r * out_stride * sizeof(Real);
-    a.in_stride = 0;
-    a.out_stride = 0;
-    for (int t0 = 0; t0 < p->n_tiles; t0 += p->tiles_per_chunk) {
-      const int nt = (p->n_tiles - t0) < p->tiles_per_chunk ? (p->n_tiles - t0) : p->tiles_per_chunk;
-      a.tile0 = t0;
-      dim3 g13(p->N1 / a.B1, nt), g2(p->N2 / a.B2, nt);
-      k_f1<Real, NS, IN><<<g13, 256, sm13, s>>>(a);
-      k_f2<Real><<<g2, 256, sm2, s>>>(a);
-      k_f3<Real, NS, OUT><<<g13, 256, sm13, s>>>(a);
+  int n_chunks, per_chunk;
+  chunking(p, n_chunks, per_chunk);
+  int ei = 0;
+  for (int rep = 0; rep < reps; ++rep) {
+    for (int r = 0; r < n_rhs; ++r) {
+      a.in = static_cast<const char*>(in) + (size_t)r * in_stride *
+                                                (IN == IN_TODF ? sizeof(float) : sizeof(Real));
+      a.out = static_cast<char*>(out) + (size_t)r * out_stride * sizeof(Real);
+      a.in_stride = 0;
+      a.out_stride = 0;
+      for (int t0 = 0; t0 < p->n_tiles; t0 += per_chunk) {
+        const int nt = (p->n_tiles - t0) < per_chunk ? (p->n_tiles - t0) : per_chunk;
+        a.tile0 = t0;
+        dim3 g13(p->N1 / a.B1, nt), g2(p->N2 / a.B2, nt);
+        if (ev) cudaEventRecord(ev[ei++], s);
+        k_f1<Real, NS, IN><<<g13, 256, sm13, s>>>(a);
+        if (ev) cudaEventRecord(ev[ei++], s);
+        k_f2<Real><<<g2, 256, sm2, s>>>(a);
+        if (ev) cudaEventRecord(ev[ei++], s);
+        k_f3<Real, NS, OUT><<<g13, 256, sm13, s>>>(a);
+        if (ev) cudaEventRecord(ev[ei++], s);
+      }
     }
   }
+  count_launches(3LL * n_chunks * n_rhs * reps);
   MM_CUDA(cudaGetLastError());
   return MADMAP_OK;
 }
@@ -361,7 +527,95 @@ madmap_status dispatch_io(Plan* p, int in_mode, int out_mode, const void* in, vo
   return MADMAP_ERR_INTERNAL;
 }
 
+template <typename Real, int NS>
+madmap_status time_impl(Plan* p, const void* in, void* out, int reps, double ms[3], cudaStream_t s) {
+  int n_chunks, per_chunk;
+  chunking(p, n_chunks, per_chunk);
+  const int n_ev = reps * n_chunks * 4;
+  std::vector<cudaEvent_t> ev(n_ev, nullptr);
+  madmap_status st = MADMAP_OK;
+  for (int i = 0; i < n_ev && st == MADMAP_OK; ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "cudaEventCreate");
+  if (st == MADMAP_OK) {
+    const long long nv = (long long)std::max(1, p->n_obs) * p->ns_pad;
+    for (int rep = 0; rep < reps && st == MADMAP_OK; ++rep) {
+      if (cudaMemsetAsync(out, 0, sizeof(Real) * nv, s) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "memset");
+      if (st == MADMAP_OK)
+        st = launch_all<Real, NS, IN_MAPX, OUT_MAP>(p, in, out, 0, 0, 1, nullptr, s, ev.data() + rep * n_chunks * 4, 1);
+    }
+  }
+  if (st == MADMAP_OK && cudaStreamSynchronize(s) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "sync");
+  if (st == MADMAP_OK) {
+    ms[0] = ms[1] = ms[2] = 0.0;
+    for (int c = 0; c < reps * n_chunks; ++c)
+      for (int k = 0; k < 3; ++k) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev[c * 4 + k], ev[c * 4 + k + 1]);
+        ms[k] += t;
+      }
+    for (int k = 0; k < 3; ++k) ms[k] /= (double)(reps * n_chunks);
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  return st;
+}
+
 }  // namespace
+
+static long long g_launches = 0;
+void count_launches(long long n) { g_launches += n; }
+
+madmap_status op_time(Plan* p, bool fp64, const void* in, void* out, int reps, double ms[3], cudaStream_t s) {
+  if (p->n_tiles == 0) {
+    ms[0] = ms[1] = ms[2] = 0.0;
+    return MADMAP_OK;
+  }
+  if (fp64)
+    return p->n_stokes == 1 ? time_impl<double, 1>(p, in, out, reps, ms, s) : time_impl<double, 3>(p, in, out, reps, ms, s);
+  return p->n_stokes == 1 ? time_impl<float, 1>(p, in, out, reps, ms, s) : time_impl<float, 3>(p, in, out, reps, ms, s);
+}
+
+// Resident CTAs per SM of the operator kernels (the least of the three) and
+// CTAs per tile of the column kernels, for wave-aligned chunk sizes.
+void op_occupancy(const Plan* p, bool fp64, int& ctas_per_sm, int& ctas_per_tile) {
+  int b1 = 0, b2 = 0, n1 = 0, n2 = 0, n3 = 0;
+  if (fp64) {
+    geometry<double>(p, b1, b2);
+    const size_t s13 = smem_f13<double>(p), s2 = smem_f2<double>(p);
+    if (p->n_stokes == 1) {
+      set_smem(k_f1<double, 1, IN_MAPX>, s13);
+      set_smem(k_f3<double, 1, OUT_MAP>, s13);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_f1<double, 1, IN_MAPX>, 256, s13);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n3, k_f3<double, 1, OUT_MAP>, 256, s13);
+    } else {
+      set_smem(k_f1<double, 3, IN_MAPX>, s13);
+      set_smem(k_f3<double, 3, OUT_MAP>, s13);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_f1<double, 3, IN_MAPX>, 256, s13);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n3, k_f3<double, 3, OUT_MAP>, 256, s13);
+    }
+    set_smem(k_f2<double>, s2);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_f2<double>, 256, s2);
+  } else {
+    geometry<float>(p, b1, b2);
+    const size_t s13 = smem_f13<float>(p), s2 = smem_f2<float>(p);
+    if (p->n_stokes == 1) {
+      set_smem(k_f1<float, 1, IN_MAPX>, s13);
+      set_smem(k_f3<float, 1, OUT_MAP>, s13);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_f1<float, 1, IN_MAPX>, 256, s13);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n3, k_f3<float, 1, OUT_MAP>, 256, s13);
+    } else {
+      set_smem(k_f1<float, 3, IN_MAPX>, s13);
+      set_smem(k_f3<float, 3, OUT_MAP>, s13);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_f1<float, 3, IN_MAPX>, 256, s13);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n3, k_f3<float, 3, OUT_MAP>, 256, s13);
+    }
+    set_smem(k_f2<float>, s2);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_f2<float>, 256, s2);
+  }
+  cudaGetLastError();
+  ctas_per_sm = std::max(1, std::min(n1, std::min(n2, n3)));
+  ctas_per_tile = std::max(1, p->N1 / std::max(1, b1));
+}
 
 size_t f1_smem_bytes(const Plan* p, bool fp64) {
   return fp64 ? smem_f13<double>(p) : smem_f13<float>(p);
@@ -385,3 +639,5 @@ madmap_status op_launch(Plan* p, bool fp64, int in_mode, int out_mode, const voi
 }
 
 }  // namespace mm
+
+extern "C" int64_t madmap_kernel_launch_count(void) { return (int64_t)mm::g_launches; }

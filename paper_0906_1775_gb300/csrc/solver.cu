@@ -52,6 +52,7 @@ struct SolveBuffers {
   double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *t64 = nullptr, *xbest64 = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_iters = 0;
+  long long graph_launches = 0;  // kernel nodes per replay
   std::vector<void*> allocs;
 };
 
@@ -429,6 +430,7 @@ static void enqueue_iteration(Plan* p, SolveBuffers* sb, cudaStream_t s, madmap_
   const int n = p->n_obs;
   const int g = grid_vec(n);
   *st = op_launch(p, sizeof(Real) == 8, IN_MAP, OUT_MAP, pp, q, 0, 0, 1, &sb->st->done, s);
+  count_launches(3);
   k_cg_alpha<Real, NS><<<g, NT, 0, s>>>(pp, q, n, sb->st, sb->partials);
   k_cg_update<Real, NS><<<g, NT, 0, s>>>(x, r, z, pp, q, n, p->P64, p->P32, p->fp64flag, sb->st, sb->partials);
   k_cg_direction<Real, NS><<<g, NT, 0, s>>>(x, z, pp, q, xb, n, sb->st);
@@ -450,9 +452,13 @@ static madmap_status enqueue_chunk(Plan* p, SolveBuffers* sb, int iters, bool us
       sb->exec = nullptr;
     }
     cudaGraph_t graph = nullptr;
+    const int64_t before = madmap_kernel_launch_count();
     MM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
     for (int i = 0; i < iters && st == MADMAP_OK; ++i) enqueue_iteration<Real, NS>(p, sb, s, &st);
     cudaError_t e = cudaStreamEndCapture(s, &graph);
+    // captured kernels did not run: count them once per replay instead
+    sb->graph_launches = madmap_kernel_launch_count() - before;
+    count_launches(-sb->graph_launches);
     if (st != MADMAP_OK) {
       if (graph) cudaGraphDestroy(graph);
       return st;
@@ -464,6 +470,7 @@ static madmap_status enqueue_chunk(Plan* p, SolveBuffers* sb, int iters, bool us
     sb->graph_iters = iters;
   }
   MM_CUDA(cudaGraphLaunch(sb->exec, s));
+  count_launches(sb->graph_launches);
   return MADMAP_OK;
 }
 
@@ -478,6 +485,7 @@ template <typename Real, int NS, typename Bt>
 static madmap_status run_pcg(Plan* p, SolveBuffers* sb, const Bt* b, double tol, int max_iter, int per_sync,
                              bool use_graph, cudaStream_t s, PcgResult* out) {
   const int n = p->n_obs;
+  count_launches(1);
   k_cg_init<Real, NS, Bt><<<grid_vec(n), NT, 0, s>>>((Real*)sb->x, (Real*)sb->r, (Real*)sb->z, (Real*)sb->p,
                                                      (Real*)sb->q, (Real*)sb->xb, b, n, p->P64, p->P32,
                                                      p->fp64flag, sb->st, sb->partials, tol, max_iter);
@@ -540,6 +548,7 @@ static madmap_status solve_impl(Plan* p, const float* d, double* m, const madmap
     PcgResult R;
     st = run_pcg<double, NS, double>(p, sb64, sb64->b64, o.rel_tol, o.max_iter, o.iters_per_sync, graph, s, &R);
     if (st != MADMAP_OK) return st;
+    count_launches(1);
     k_unpack<double, double><<<grid_vec((long long)n * p->n_stokes), NT, 0, s>>>((const double*)sb64->xb, m, n,
                                                                                 p->n_stokes, p->ns_pad);
     I.iters = R.iters;
@@ -555,6 +564,7 @@ static madmap_status solve_impl(Plan* p, const float* d, double* m, const madmap
     if (st != MADMAP_OK) return st;
     // r64 = b64 and ||b||
     MM_CUDA(cudaMemsetAsync(sb64->t64, 0, sizeof(double) * nv, s));
+    count_launches(1);
     k_residual<<<grid_vec(nv), NT, 0, s>>>(sb64->b64, sb64->t64, sb64->r64, nv, sb64->st, sb64->partials);
     CgState h;
     MM_CUDA(cudaMemcpyAsync(&h, sb64->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
@@ -573,6 +583,7 @@ static madmap_status solve_impl(Plan* p, const float* d, double* m, const madmap
       I.fp32_applies += R.iters;
       ++outer;
       if (R.status != 0) inner_status = R.status;
+      count_launches(2);
       k_refine_add<<<grid_vec(nv), NT, 0, s>>>(sb64->x64, (const float*)sb32->xb, sb64->t64, nv);
       st = op_launch(p, true, IN_MAP, OUT_MAP, sb64->x64, sb64->t64, 0, 0, 1, nullptr, s);
       if (st != MADMAP_OK) return st;
@@ -588,6 +599,7 @@ static madmap_status solve_impl(Plan* p, const float* d, double* m, const madmap
       }
       if (R.iters == 0) break;
     }
+    count_launches(1);
     k_unpack<double, double><<<grid_vec((long long)n * p->n_stokes), NT, 0, s>>>(sb64->xbest64, m, n, p->n_stokes,
                                                                                 p->ns_pad);
     I.iters = total;
@@ -615,6 +627,7 @@ static madmap_status apply_impl(Plan* p, bool fp64, int n_rhs, const void* x, vo
   for (int r = 0; r < n_rhs; ++r) {
     const Real* xr = static_cast<const Real*>(x) + r * user;
     Real* yr = static_cast<Real*>(y) + r * user;
+    count_launches(2);
     k_pack<Real, Real><<<grid_vec((long long)n * np), NT, 0, s>>>(xr, (Real*)sb->p, n, ns, np);
     MM_CUDA(cudaMemsetAsync(sb->q, 0, sizeof(Real) * sb->nvec, s));
     st = op_launch(p, fp64, IN_MAP, OUT_MAP, sb->p, sb->q, 0, 0, 1, nullptr, s);
@@ -636,6 +649,7 @@ static madmap_status rhs_impl(Plan* p, bool fp64, int n_rhs, const float* d, voi
     MM_CUDA(cudaMemsetAsync(sb->q, 0, sizeof(Real) * sb->nvec, s));
     st = op_launch(p, fp64, IN_TOD, OUT_MAP, d + (long long)r * p->n_t, sb->q, 0, 0, 1, nullptr, s);
     if (st != MADMAP_OK) return st;
+    count_launches(1);
     k_unpack<Real, Real><<<grid_vec(user), NT, 0, s>>>((const Real*)sb->q, static_cast<Real*>(b) + r * user, n, ns,
                                                        np);
   }
@@ -741,4 +755,22 @@ extern "C" madmap_status madmap_solve(madmap_plan_t plan, const float* d, double
   madmap_status st = p->n_stokes == 1 ? solve_impl<1>(p, d, m, o, info, s) : solve_impl<3>(p, d, m, o, info, s);
   cudaStreamSynchronize(s);
   return st;
+}
+
+extern "C" madmap_status madmap_time_operator(madmap_plan_t plan, int32_t precision, int32_t reps, double* ms_out,
+                                              int32_t* launches_out, void* stream) {
+  MM_CHECK(plan && ms_out && reps >= 1, MADMAP_ERR_INVALID_ARG, "time_operator: bad arguments");
+  MM_CHECK(precision == MADMAP_FP64 || precision == MADMAP_FP32, MADMAP_ERR_INVALID_ARG,
+           "time_operator: precision must be FP64 or FP32");
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  const bool fp64 = precision == MADMAP_FP64;
+  SolveBuffers* sb = nullptr;
+  madmap_status st = get_buffers(p, fp64, &sb);
+  if (st != MADMAP_OK) return st;
+  int n_chunks, per_chunk;
+  chunking(p, n_chunks, per_chunk);
+  if (launches_out)
+    for (int k = 0; k < 3; ++k) launches_out[k] = n_chunks;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return op_time(p, fp64, sb->p, sb->q, reps, ms_out, s);
 }
