@@ -184,6 +184,39 @@ void madmap_solve_opts_default(madmap_solve_opts* opts);
 madmap_status madmap_solve(madmap_plan_t plan, const float* d, double* m, const madmap_solve_opts* opts,
                            madmap_solve_info* info, void* stream);
 
+/* ------------------------------------------------------------------ allocation-free weighting */
+
+/* Size of the fixed device array used by madmap_apply_ninv_noalloc, and the
+ * largest n_lags it accepts. */
+#define MADMAP_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define MADMAP_NOALLOC_MAX_LAGS (1 << 15)
+
+/* w = N^-1 y on timestreams, like madmap_apply_ninv, for callers that cannot
+ * allocate device memory (an allocator that forbids new allocations after
+ * start-up, a real-time loop that must not stall in cudaMalloc, or host code
+ * without its own CUDA memory management).  There is no counterpart in the
+ * paper: it is an interface convenience, not part of the method.
+ *
+ * No plan is needed and nothing is allocated: the derived tables and the FFT
+ * intermediate live in a fixed device array of MADMAP_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading the library holds until the process exits.  The
+ * caller passes the inputs and outputs: precision FP64 (y, w double) or FP32
+ * (float); y, w: device [n_samples]; interval_offsets (host [n_intervals+1]),
+ * interval_filter (host [n_intervals]) and filter_lags (host
+ * [n_filters][n_lags]) as in madmap_plan_desc.  Sizes that do not fit the
+ * array (n_lags > MADMAP_NOALLOC_MAX_LAGS, or too many filters or windows)
+ * return MADMAP_ERR_INVALID_ARG with a message; a filter that is not positive
+ * definite returns MADMAP_ERR_NOT_PD.
+ *
+ * The array is shared by all calls and keeps the last call's contents; calls
+ * that overlap on the GPU race on it.  The first call on a device looks up the
+ * array's device address; make that call before any stream capture.  Ordered
+ * on `stream`; returns once the work is enqueued. */
+madmap_status madmap_apply_ninv_noalloc(int32_t precision, int64_t n_samples, int32_t n_intervals,
+                                        const int64_t* interval_offsets, const int32_t* interval_filter,
+                                        int32_t n_filters, int32_t n_lags, const double* filter_lags,
+                                        const void* y, void* w, void* stream);
+
 /* ------------------------------------------------------------------ diagnostics */
 
 /* Number of kernels this library has launched in the process (each kernel

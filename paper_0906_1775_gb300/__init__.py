@@ -22,7 +22,7 @@ __all__ = ["Plan", "noise_filter", "paper_fft_length", "MadmapError", "load", "l
            "madmap_plan_create", "madmap_plan_destroy", "madmap_plan_get_stats", "madmap_plan_observed",
            "madmap_plan_set_filters", "madmap_apply_ATNA", "madmap_rhs", "madmap_apply_ninv", "madmap_solve",
            "madmap_noise_filter", "madmap_paper_fft_length", "madmap_last_error", "madmap_kernel_launch_count",
-           "madmap_time_operator"]
+           "madmap_time_operator", "madmap_apply_ninv_noalloc"]
 
 _PREC = {"fp64": MADMAP_FP64, "mixed": MADMAP_MIXED, "fp32": MADMAP_FP32,
          MADMAP_FP64: MADMAP_FP64, MADMAP_MIXED: MADMAP_MIXED, MADMAP_FP32: MADMAP_FP32}
@@ -117,6 +117,18 @@ def madmap_noise_filter(n_lags, fs, sigma, fknee, alpha, with_grad=False):
 
 def madmap_paper_fft_length(n_lags, longest) -> int:
     return int(load().madmap_paper_fft_length(int(n_lags), int(longest)))
+
+
+def madmap_apply_ninv_noalloc(precision, n_samples, interval_offsets, interval_filter, filter_lags, y_ptr, w_ptr,
+                              stream=None):
+    """w = N^-1 y without a plan and without any device allocation (fixed scratch)."""
+    off = np.ascontiguousarray(interval_offsets, dtype=np.int64)
+    filt = np.ascontiguousarray(interval_filter, dtype=np.int32)
+    lags = np.ascontiguousarray(np.atleast_2d(filter_lags), dtype=np.float64)
+    check(load().madmap_apply_ninv_noalloc(_PREC[precision], int(n_samples), int(filt.shape[0]), off.ctypes.data,
+                                           filt.ctypes.data if filt.size else None, int(lags.shape[0]),
+                                           int(lags.shape[1]), lags.ctypes.data, y_ptr, w_ptr,
+                                           C.c_void_p(_stream_ptr(stream))), "madmap_apply_ninv_noalloc")
 
 
 def madmap_kernel_launch_count() -> int:

@@ -73,6 +73,8 @@ PROTOTYPES = [
     ("madmap_noise_filter", C.c_int, [C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p,
                                       C.c_void_p]),
     ("madmap_paper_fft_length", C.c_int64, [C.c_int64, C.c_int64]),
+    ("madmap_apply_ninv_noalloc", C.c_int, [C.c_int32, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                                            C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("madmap_kernel_launch_count", C.c_int64, []),
     ("madmap_time_operator", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("madmap_last_error", C.c_char_p, []),

@@ -125,6 +125,11 @@ void chunking(const Plan* p, int& n_chunks, int& per_chunk);
 // Kernel launch accounting (library-wide).
 void count_launches(long long n);
 
+// Overlap-save windows of the intervals [off[i], off[i+1]) for FFT length M,
+// paired two per complex FFT within each filter.
+void build_tiles(const std::vector<long long>& off, const std::vector<int>& filt, int n_filters, int n_lags, int M,
+                 std::vector<Tile>& tiles);
+
 // host FFT (radix 2, float64), used at plan time only
 void host_fft(std::vector<double>& re, std::vector<double>& im, bool inverse);
 

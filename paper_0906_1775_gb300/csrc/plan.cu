@@ -415,6 +415,15 @@ static void pair_tiles(const std::vector<Seg>& segs, int n_filters, std::vector<
   }
 }
 
+// Overlap-save windows of every interval, paired two per complex FFT
+// (used by the allocation-free weighting entry point).
+void build_tiles(const std::vector<long long>& off, const std::vector<int>& filt, int n_filters, int n_lags, int M,
+                 std::vector<Tile>& tiles) {
+  std::vector<Seg> segs;
+  make_segments(off, filt, n_lags, M, segs);
+  pair_tiles(segs, n_filters, tiles);
+}
+
 // Autotuning model for the FFT length: work ~ tiles * M * (log2 M + c), where
 // c stands for the gather/scatter and memory passes per complex element.
 static int choose_fft_len(const std::vector<long long>& off, const std::vector<int>& filt, int n_filters,
