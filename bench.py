@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=3, help="oracle PCG iterations in the CPU baseline sample")
+    ap.add_argument("--profile-step", type=float, default=0.0, metavar="TOL",
+                    help="profiling runs: skip the reference map and tolerance search and run exactly one "
+                         "mixed-precision solve at this stopping tolerance")
     ap.add_argument("--operator-only", type=int, default=0, metavar="R",
                     help="only build the plan and time R float32 operator applications (profiling runs)")
     return ap.parse_args()
@@ -150,6 +153,14 @@ def stokes_err(m, ref, keep):
     return max(out), out
 
 
+def operator_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("operator.cu", "internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_0906_1775_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def lib_lags(p):
     import numpy as np
     import paper_0906_1775_gb300 as mm
@@ -246,6 +257,13 @@ def main():
         return
     d_host = torch.from_numpy(p.d[0]).pin_memory()
     d = d_host.to(dev)
+    if args.profile_step > 0:
+        _, info = plan.solve(d, precision="mixed", rel_tol=args.profile_step, max_iter=3000, max_outer=20,
+                             inner_rel_tol=1e-4)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_step": info, "launches": mm.madmap_kernel_launch_count()}), flush=True)
+        plan.close()
+        return
     _, exc = plan.observed()
     keep = ~exc.cpu().numpy().astype(bool)
 
@@ -314,25 +332,41 @@ def main():
     op64_ms, _ = plan.time_operator("fp64", reps=5)
     t_op = float(np.sum(op_ms * op_launch))
     n_obs = plan.n_obs
-    b_alg = p.n_samples * 8 + 2 * n_obs * 4 * 3       # pointing read once + map read and written
-    achieved = b_alg / (t_op * 1e-3) / 1e9
+    # algorithmic bytes and flops of one application (pointing read once, map read
+    # and written; FFT flops at the paper's FFT length, Section 5.2 Eq. 22)
+    b_alg = p.n_samples * 8 + 2 * n_obs * 4 * 3
+    n_c = p.n_lags
+    n_f = mm.paper_fft_length(n_c, int(np.diff(p.interval_offsets).max()))
+    f_per_sample = (5.0 * n_f * np.log2(n_f) + n_f) / (n_f - 2 * n_c)
+    f_alg = p.n_samples * f_per_sample
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12     # FP32 FMA lanes x 2 x clock
+    achieved_tf = f_alg / (t_op * 1e-3) / 1e12
+    achieved_gbs = b_alg / (t_op * 1e-3) / 1e9
     k_dom = int(np.argmax(op_ms * op_launch))
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
-                "kernel": "operator A^T N^-1 A, float32 (k_f1 gather+column FFTs, k_f2 row FFTs x filter, "
-                          "k_f3 inverse column FFTs+scatter), one application",
-                "alg_bytes_per_launch": int(b_alg), "ms_per_launch": t_op,
-                "peak_source": f"{hbm_peak_src} hbm_gbs (MEASURED_PEAKS.json)" if hbm_peak_src == "measured"
-                else "fallback 6800 GB/s",
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved_tf / alu_peak, "traffic": None,
+                "kernel": "operator A^T N^-1 A, float32: one application = k_f1 (gather + column FFTs), "
+                          "k_f2 (row FFTs x filter), k_f3 (inverse column FFTs + scatter) over all tile chunks",
+                "alg_flops_per_launch": float(f_alg), "alg_bytes_per_launch": int(b_alg), "ms_per_launch": t_op,
+                "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz",
+                "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
+                        "peak_source": f"{hbm_peak_src} hbm_gbs (MEASURED_PEAKS.json)"},
+                "t_roof_us": {"bytes": b_alg / (hbm_peak * 1e9) * 1e6, "flops": f_alg / (alu_peak * 1e12) * 1e6},
                 "per_kernel_ms": [float(x) for x in op_ms], "launches_per_application": [int(x) for x in op_launch],
                 "dominant_kernel": ["k_f1", "k_f2", "k_f3"][k_dom],
                 "fp64_operator_ms": float(np.sum(op64_ms * op_launch))}
-    traffic_file = os.path.join(ROOT, "profiles", "operator_traffic.json")
+    # DRAM traffic per application from the committed ncu summary, used only while
+    # the operator source is the one the counters were taken with
+    traffic_file = os.path.join(ROOT, "profiles", "operator_traffic_config2.json")
     if os.path.exists(traffic_file):
         try:
             tr = json.load(open(traffic_file))
-            if tr.get("fft_len") == plan.stats["fft_len"] and tr.get("n_tiles") == plan.stats["n_tiles"]:
+            if (tr.get("source_sha256") == operator_source_hash() and tr.get("fft_len") == plan.stats["fft_len"]
+                    and tr.get("n_tiles") == plan.stats["n_tiles"]):
                 roofline["traffic"] = tr["dram_bytes_per_application"]
+                roofline["traffic_source"] = tr.get("how")
         except Exception:
             pass
 

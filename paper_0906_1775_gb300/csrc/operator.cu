@@ -51,8 +51,6 @@ struct OpArgs {
   const int* skip;
 };
 
-template <typename Real>
-__device__ __forceinline__ void weights(const OpArgs& a, long long t, Real& c, Real& s);
 // cos 2psi, sin 2psi for the float32 operator: 2 psi is reduced to [-pi, pi]
 // by subtracting the nearest multiple of 2 pi in two parts (2 pi rounded to
 // float, then the remainder of 2 pi), and the hardware approximations take
@@ -65,17 +63,6 @@ __device__ __forceinline__ void sincos_2psi(float psi, float& s, float& c) {
   r = fmaf(-k, -1.7484556000744970e-07f, r);
   __sincosf(r, &s, &c);
 }
-template <>
-__device__ __forceinline__ void weights<float>(const OpArgs& a, long long t, float& c, float& s) {
-  sincos_2psi(a.psi[t], s, c);
-}
-template <>
-__device__ __forceinline__ void weights<double>(const OpArgs& a, long long t, double& c, double& s) {
-  const double2 cs = a.cs64[t];
-  c = cs.x;
-  s = cs.y;
-}
-
 template <typename Real, int NS>
 __device__ __forceinline__ Real gather(const Real* x, int p, Real c, Real s);
 template <>
