@@ -234,6 +234,18 @@ int64_t madmap_kernel_launch_count(void);
 madmap_status madmap_time_operator(madmap_plan_t plan, int32_t precision, int32_t reps, double* ms_out,
                                    int32_t* launches_out, void* stream);
 
+/* Batched solve: n_rhs right-hand sides sharing the plan's pointing (e.g.
+ * noise Monte Carlo realisations), each solved as madmap_solve would, in one
+ * pass of work: every kernel launch covers all unfinished right-hand sides,
+ * the noise weighting pairs right-hand sides of the same window in one
+ * complex FFT (so the pointing is read once per pair), and each right-hand
+ * side stops on its own (MIXED: each keeps its own float64 refinement).
+ * d: device float [n_rhs][n_samples]; m: device double [n_rhs][n_obs][n_stokes];
+ * info: host [n_rhs] or NULL.  Returns the most severe per-rhs status.
+ * Synchronises `stream`. */
+madmap_status madmap_solve_batched(madmap_plan_t plan, int32_t n_rhs, const float* d, double* m,
+                                   const madmap_solve_opts* opts, madmap_solve_info* info, void* stream);
+
 /* ------------------------------------------------------------------ host helpers */
 
 /* Inverse-noise filter lags from the PSD p(f) = sigma^2 (1 + (fknee/f)^alpha)

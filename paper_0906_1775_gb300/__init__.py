@@ -21,6 +21,7 @@ from ._lib import (MADMAP_FP32, MADMAP_FP64, MADMAP_MIXED, MadmapError, check, l
 __all__ = ["Plan", "noise_filter", "paper_fft_length", "MadmapError", "load", "library_path",
            "madmap_plan_create", "madmap_plan_destroy", "madmap_plan_get_stats", "madmap_plan_observed",
            "madmap_plan_set_filters", "madmap_apply_ATNA", "madmap_rhs", "madmap_apply_ninv", "madmap_solve",
+           "madmap_solve_batched",
            "madmap_noise_filter", "madmap_paper_fft_length", "madmap_last_error", "madmap_kernel_launch_count",
            "madmap_time_operator", "madmap_apply_ninv_noalloc"]
 
@@ -105,6 +106,13 @@ def madmap_solve(h, d_ptr, m_ptr, opts, stream=None):
     st = load().madmap_solve(h, d_ptr, m_ptr, C.byref(opts), C.byref(info), C.c_void_p(_stream_ptr(stream)))
     check(st, "madmap_solve", allow_warn=True)
     return info
+
+
+def madmap_solve_batched(h, n_rhs, d_ptr, m_ptr, opts, stream=None):
+    infos = (_lib.madmap_solve_info * n_rhs)()
+    st = load().madmap_solve_batched(h, int(n_rhs), d_ptr, m_ptr, C.byref(opts), infos, C.c_void_p(_stream_ptr(stream)))
+    check(st, "madmap_solve_batched", allow_warn=True)
+    return infos
 
 
 def madmap_noise_filter(n_lags, fs, sigma, fknee, alpha, with_grad=False):
@@ -245,14 +253,32 @@ class Plan:
         madmap_apply_ninv(self._h, prec, y.shape[0], _dev_ptr(y, dt, "y"), w.data_ptr(), stream)
         return w
 
-    def solve(self, d, precision="fp64", max_iter=50, rel_tol=1e-6, max_outer=10, inner_rel_tol=1e-4,
-              use_graph=True, iters_per_sync=8, out=None, stream=None):
-        """Maximum-likelihood map [n_obs, n_stokes] (float64) and the solve info dict."""
-        torch = _torch()
+    @staticmethod
+    def _opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync):
         o = _lib.madmap_solve_opts()
         o.max_iter, o.rel_tol, o.precision = int(max_iter), float(rel_tol), _PREC[precision]
         o.max_outer, o.inner_rel_tol = int(max_outer), float(inner_rel_tol)
         o.use_graph, o.iters_per_sync = int(bool(use_graph)), int(iters_per_sync)
+        return o
+
+    def solve_batched(self, d, precision="fp64", max_iter=50, rel_tol=1e-6, max_outer=10, inner_rel_tol=1e-4,
+                      use_graph=True, iters_per_sync=8, out=None, stream=None):
+        """Maps [n_rhs, n_obs, n_stokes] (float64) for d [n_rhs, n_samples], and per-rhs info dicts."""
+        torch = _torch()
+        d = d.reshape(-1, self.n_samples)
+        n_rhs = d.shape[0]
+        o = self._opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync)
+        m = out if out is not None else torch.empty((n_rhs, self.n_obs, self.n_stokes), dtype=torch.float64,
+                                                    device="cuda")
+        infos = madmap_solve_batched(self._h, n_rhs, _dev_ptr(d, torch.float32, "d") if d.numel() else None,
+                                     _dev_ptr(m, torch.float64, "m") if m.numel() else None, o, stream)
+        return m, [{k: getattr(i, k) for k, _ in i._fields_} for i in infos]
+
+    def solve(self, d, precision="fp64", max_iter=50, rel_tol=1e-6, max_outer=10, inner_rel_tol=1e-4,
+              use_graph=True, iters_per_sync=8, out=None, stream=None):
+        """Maximum-likelihood map [n_obs, n_stokes] (float64) and the solve info dict."""
+        torch = _torch()
+        o = self._opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync)
         m = out if out is not None else torch.empty((self.n_obs, self.n_stokes), dtype=torch.float64,
                                                     device="cuda")
         info = madmap_solve(self._h, _dev_ptr(d.reshape(-1), torch.float32, "d"), _dev_ptr(m, torch.float64, "m"),

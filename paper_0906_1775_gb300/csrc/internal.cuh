@@ -47,6 +47,13 @@ struct Tile {
   int pad[3];
 };
 
+// A list of tiles whose lanes name their right-hand side (batched solves).
+struct TileSet {
+  Tile* tiles = nullptr;  // device
+  int n_tiles = 0;
+  int n_rhs = 0;
+};
+
 // ---------------------------------------------------------------- plan
 struct SolveBuffers;  // solver.cu
 
@@ -88,6 +95,7 @@ struct Plan {
   // allowed on the legacy default stream), ordered after the caller's stream
   cudaStream_t solve_stream = nullptr;
   cudaEvent_t solve_event = nullptr;
+  std::vector<TileSet*> tile_sets;  // batched tile lists by n_rhs (device memory in allocs)
   ~Plan();
 };
 
@@ -120,7 +128,14 @@ madmap_status op_time(Plan* p, bool fp64, const void* in, void* out, int reps, d
 void op_occupancy(const Plan* p, bool fp64, int& ctas_per_sm, int& ctas_per_tile);
 
 // Number of operator launches per application and tiles per launch.
-void chunking(const Plan* p, int& n_chunks, int& per_chunk);
+void chunking(const Plan* p, int& n_chunks, int& per_chunk, int n_tiles = -1);
+
+// The operator over a tile set (lanes carry their rhs; per-rhs strides in
+// elements; skip[rhs * skip_stride], if skip is not NULL, marks right-hand
+// sides whose tiles need no work).
+madmap_status op_launch_set(Plan* p, bool fp64, int in_mode, int out_mode, const void* in, void* out,
+                            long long in_stride, long long out_stride, const int* skip, int skip_stride,
+                            const TileSet* ts, cudaStream_t s);
 
 // Kernel launch accounting (library-wide).
 void count_launches(long long n);
@@ -129,6 +144,9 @@ void count_launches(long long n);
 // paired two per complex FFT within each filter.
 void build_tiles(const std::vector<long long>& off, const std::vector<int>& filt, int n_filters, int n_lags, int M,
                  std::vector<Tile>& tiles);
+
+// Tile set for n_rhs right-hand sides (cached in the plan).
+madmap_status get_tile_set(Plan* p, int n_rhs, TileSet** out);
 
 // host FFT (radix 2, float64), used at plan time only
 void host_fft(std::vector<double>& re, std::vector<double>& im, bool inverse);

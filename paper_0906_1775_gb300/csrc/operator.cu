@@ -48,8 +48,16 @@ struct OpArgs {
   void* scratch;
   const void* H;
   const void* tw;
-  const int* skip;
+  const int* skip;    // done flag(s): one shared flag, or one per right-hand side
+  int skip_stride;    // 0: *skip covers every tile; > 0: skip[rhs * skip_stride] per lane
 };
+
+// A tile is skipped when its solve (or both of its right-hand sides) is done.
+__device__ __forceinline__ bool skip_tile(const OpArgs& a, const Tile* T) {
+  if (!a.skip) return false;
+  if (a.skip_stride == 0) return *a.skip != 0;
+  return a.skip[T->l[0].rhs * a.skip_stride] != 0 && a.skip[T->l[1].rhs * a.skip_stride] != 0;
+}
 
 // cos 2psi, sin 2psi for the float32 operator: 2 psi is reduced to [-pi, pi]
 // by subtracting the nearest multiple of 2 pi in two parts (2 pi rounded to
@@ -179,15 +187,15 @@ __device__ __forceinline__ void finish_angle<float>(float& c, float& s) {
 template <typename Real, int NS, int IN>
 __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a) {
   typedef typename CxT<Real>::type C;
-  if (a.skip && *a.skip) return;
+  const int tl = blockIdx.y;
+  const Tile* T = a.tiles + a.tile0 + tl;
+  if (skip_tile(a, T)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int rs = row_stride(a.N2);
   C* tw = buf + a.B1 * rs;
   const C* twM = static_cast<const C*>(a.tw);
   for (int k = threadIdx.x; k < a.N2; k += blockDim.x) tw[k] = twM[(long long)k * a.N1];
-  const int tl = blockIdx.y;
-  const Tile* T = a.tiles + a.tile0 + tl;
   LaneView<Real> L[2];
   L[0] = lane_view<Real, IN, OUT_MAP>(a, T->l[0]);
   L[1] = lane_view<Real, IN, OUT_MAP>(a, T->l[1]);
@@ -275,15 +283,15 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
 template <typename Real>
 __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f2(OpArgs a) {
   typedef typename CxT<Real>::type C;
-  if (a.skip && *a.skip) return;
+  const int tl = blockIdx.y;
+  const Tile* T = a.tiles + a.tile0 + tl;
+  if (skip_tile(a, T)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int rs = row_stride(a.N1);
   C* tw = buf + a.B2 * rs;
   const C* twM = static_cast<const C*>(a.tw);
   for (int k = threadIdx.x; k < a.N1; k += blockDim.x) tw[k] = twM[(long long)k * a.N2];
-  const int tl = blockIdx.y;
-  const Tile* T = a.tiles + a.tile0 + tl;
   const int filt = T->filter;
   const int pos0 = blockIdx.x * a.B2;
   C* sc = static_cast<C*>(a.scratch) + (long long)tl * a.M + (long long)pos0 * a.N1;
@@ -311,15 +319,15 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f2(OpArgs a)
 template <typename Real, int NS, int OUT>
 __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a) {
   typedef typename CxT<Real>::type C;
-  if (a.skip && *a.skip) return;
+  const int tl = blockIdx.y;
+  const Tile* T = a.tiles + a.tile0 + tl;
+  if (skip_tile(a, T)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int rs = row_stride(a.N2);
   C* tw = buf + a.B1 * rs;
   const C* twM = static_cast<const C*>(a.tw);
   for (int k = threadIdx.x; k < a.N2; k += blockDim.x) tw[k] = twM[(long long)k * a.N1];
-  const int tl = blockIdx.y;
-  const Tile* T = a.tiles + a.tile0 + tl;
   LaneView<Real> L[2];
   L[0] = lane_view<Real, IN_MAPX, OUT>(a, T->l[0]);
   L[1] = lane_view<Real, IN_MAPX, OUT>(a, T->l[1]);
@@ -400,9 +408,10 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
 
 // Tiles are processed in n_chunks launches of (nearly) equal size, at most
 // tiles_per_chunk each, so no launch is left with a small tail of work.
-void chunking(const Plan* p, int& n_chunks, int& per_chunk) {
-  n_chunks = p->n_tiles ? (p->n_tiles + p->tiles_per_chunk - 1) / p->tiles_per_chunk : 0;
-  per_chunk = n_chunks ? (p->n_tiles + n_chunks - 1) / n_chunks : 0;
+void chunking(const Plan* p, int& n_chunks, int& per_chunk, int n_tiles) {
+  if (n_tiles < 0) n_tiles = p->n_tiles;
+  n_chunks = n_tiles ? (n_tiles + p->tiles_per_chunk - 1) / p->tiles_per_chunk : 0;
+  per_chunk = n_chunks ? (n_tiles + n_chunks - 1) / n_chunks : 0;
 }
 
 namespace {
@@ -443,7 +452,8 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 
 template <typename Real, int NS, int IN, int OUT>
 madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride, long long out_stride,
-                         int n_rhs, const int* skip, cudaStream_t s, cudaEvent_t* ev = nullptr, int reps = 1) {
+                         int n_rhs, const int* skip, cudaStream_t s, cudaEvent_t* ev = nullptr, int reps = 1,
+                         const TileSet* ts = nullptr, int skip_stride = 0) {
   OpArgs a;
   a.M = p->M;
   a.N1 = p->N1;
@@ -459,7 +469,9 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
   a.H = sizeof(Real) == 8 ? (const void*)p->H64 : (const void*)p->H32;
   a.tw = sizeof(Real) == 8 ? (const void*)p->tw64 : (const void*)p->tw32;
   a.skip = skip;
-  a.tiles = p->tiles;
+  a.skip_stride = ts ? skip_stride : 0;
+  a.tiles = ts ? ts->tiles : p->tiles;
+  const int n_tiles = ts ? ts->n_tiles : p->n_tiles;
   const size_t sm13 = smem_f13<Real>(p), sm2 = smem_f2<Real>(p);
   // opt-in to large dynamic shared memory once per kernel instance (raised when
   // a plan needs more); n_rhs == 0 only does this, so it can precede a capture
@@ -474,17 +486,19 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
     set2 = sm2;
   }
   int n_chunks, per_chunk;
-  chunking(p, n_chunks, per_chunk);
+  chunking(p, n_chunks, per_chunk, n_tiles);
   int ei = 0;
   for (int rep = 0; rep < reps; ++rep) {
     for (int r = 0; r < n_rhs; ++r) {
       a.in = static_cast<const char*>(in) + (size_t)r * in_stride *
                                                 (IN == IN_TODF ? sizeof(float) : sizeof(Real));
       a.out = static_cast<char*>(out) + (size_t)r * out_stride * sizeof(Real);
-      a.in_stride = 0;
-      a.out_stride = 0;
-      for (int t0 = 0; t0 < p->n_tiles; t0 += per_chunk) {
-        const int nt = (p->n_tiles - t0) < per_chunk ? (p->n_tiles - t0) : per_chunk;
+      // a tile set names each lane's right-hand side, with per-rhs strides;
+      // otherwise the plan's tiles are replayed once per right-hand side
+      a.in_stride = ts ? in_stride : 0;
+      a.out_stride = ts ? out_stride : 0;
+      for (int t0 = 0; t0 < n_tiles; t0 += per_chunk) {
+        const int nt = (n_tiles - t0) < per_chunk ? (n_tiles - t0) : per_chunk;
         a.tile0 = t0;
         dim3 g13(p->N1 / a.B1, nt), g2(p->N2 / a.B2, nt);
         if (ev) cudaEventRecord(ev[ei++], s);
@@ -550,7 +564,32 @@ madmap_status time_impl(Plan* p, const void* in, void* out, int reps, double ms[
   return st;
 }
 
+template <typename Real, int NS>
+madmap_status dispatch_set(Plan* p, int in_mode, int out_mode, const void* in, void* out, long long is,
+                           long long os, const int* skip, int ss, cudaStream_t s, const TileSet* ts) {
+  if (in_mode == IN_MAP && out_mode == OUT_MAP)
+    return launch_all<Real, NS, IN_MAPX, OUT_MAP>(p, in, out, is, os, 1, skip, s, nullptr, 1, ts, ss);
+  if (in_mode == IN_TOD && out_mode == OUT_MAP)
+    return launch_all<Real, NS, IN_TODF, OUT_MAP>(p, in, out, is, os, 1, skip, s, nullptr, 1, ts, ss);
+  set_error("unsupported batched operator mode");
+  return MADMAP_ERR_INTERNAL;
+}
+
 }  // namespace
+
+// Operator over a tile set whose lanes name their right-hand side (maps and
+// timestreams strided by in_stride / out_stride elements per rhs).
+madmap_status op_launch_set(Plan* p, bool fp64, int in_mode, int out_mode, const void* in, void* out,
+                            long long in_stride, long long out_stride, const int* skip, int skip_stride,
+                            const TileSet* ts, cudaStream_t s) {
+  if (ts->n_tiles == 0) return MADMAP_OK;
+  const int ss = skip_stride;
+  if (fp64)
+    return p->n_stokes == 1 ? dispatch_set<double, 1>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts)
+                            : dispatch_set<double, 3>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts);
+  return p->n_stokes == 1 ? dispatch_set<float, 1>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts)
+                          : dispatch_set<float, 3>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts);
+}
 
 static long long g_launches = 0;
 void count_launches(long long n) { g_launches += n; }

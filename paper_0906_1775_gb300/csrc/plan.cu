@@ -52,10 +52,12 @@ madmap_status dalloc(Plan* p, void** ptr, size_t bytes) {
   return MADMAP_OK;
 }
 
-void free_solve_buffers(Plan* p);  // solver.cu
+void free_solve_buffers(Plan* p);          // solver.cu
+size_t solve_buffer_bytes(const Plan* p);  // solver.cu
 
 Plan::~Plan() {
   free_solve_buffers(this);
+  for (TileSet* t : tile_sets) delete t;
   if (solve_event) cudaEventDestroy(solve_event);
   if (solve_stream) cudaStreamDestroy(solve_stream);
   for (void* a : allocs) cudaFree(a);
@@ -424,6 +426,65 @@ void build_tiles(const std::vector<long long>& off, const std::vector<int>& filt
   pair_tiles(segs, n_filters, tiles);
 }
 
+// Tile set for n_rhs right-hand sides sharing the pointing: lanes are
+// (window, rhs) ordered by filter, window, rhs and paired consecutively, so
+// right-hand sides 2j and 2j+1 of one window share a complex FFT and the
+// pointing loads of the gather and scatter.
+madmap_status get_tile_set(Plan* p, int n_rhs, TileSet** out) {
+  for (TileSet* t : p->tile_sets)
+    if (t->n_rhs == n_rhs) {
+      *out = t;
+      return MADMAP_OK;
+    }
+  std::vector<Seg> segs;
+  make_segments(p->offsets, p->ivl_filter, p->n_lags, p->M, segs);
+  std::vector<Tile> tiles;
+  for (int f = 0; f < p->n_filters; ++f) {
+    std::vector<std::pair<const Seg*, int>> lanes;
+    for (const Seg& sg : segs)
+      if (sg.filter == f)
+        for (int r = 0; r < n_rhs; ++r) lanes.push_back({&sg, r});
+    for (size_t k = 0; k < lanes.size(); k += 2) {
+      Tile T;
+      memset(&T, 0, sizeof(T));
+      T.filter = f;
+      for (int l = 0; l < 2; ++l) {
+        Lane& L = T.l[l];
+        if (k + l < lanes.size()) {
+          const Seg* sg = lanes[k + l].first;
+          L.ws = sg->ws;
+          L.lo = sg->lo;
+          L.hi = sg->hi;
+          L.out_lo = sg->out_lo;
+          L.out_hi = sg->out_hi;
+          L.rhs = lanes[k + l].second;
+        } else {
+          L.rhs = lanes[k].second;  // empty lane: no input, no output
+        }
+      }
+      tiles.push_back(T);
+    }
+  }
+  TileSet* t = new TileSet();
+  t->n_rhs = n_rhs;
+  t->n_tiles = (int)tiles.size();
+  madmap_status st = dalloc_t(p, &t->tiles, std::max<size_t>(1, tiles.size()));
+  if (st != MADMAP_OK) {
+    delete t;
+    return st;
+  }
+  if (!tiles.empty()) {
+    cudaError_t e = cudaMemcpy(t->tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      delete t;
+      return cuda_fail(e, "cudaMemcpy (tile set)");
+    }
+  }
+  p->tile_sets.push_back(t);
+  *out = t;
+  return MADMAP_OK;
+}
+
 // Autotuning model for the FFT length: work ~ tiles * M * (log2 M + c), where
 // c stands for the gather/scatter and memory passes per complex element.
 static int choose_fft_len(const std::vector<long long>& off, const std::vector<int>& filt, int n_filters,
@@ -748,7 +809,7 @@ extern "C" madmap_status madmap_plan_get_stats(madmap_plan_t plan, madmap_plan_s
   o->n_lags = p->n_lags;
   o->n_filters = p->n_filters;
   o->n_samples = p->n_t;
-  o->device_bytes = (int64_t)p->device_bytes;
+  o->device_bytes = (int64_t)(p->device_bytes + solve_buffer_bytes(p));
   return MADMAP_OK;
 }
 

@@ -21,6 +21,12 @@
 // refinement: b and the residual b - H x are float64 (float64 operator), the
 // correction solve H e = r runs in float32 with float64 dots and scalars, and
 // pixels flagged as poorly conditioned keep float64 preconditioner blocks.
+//
+// Batched solves (many right-hand sides over one pointing) run every kernel
+// with blockIdx.y = right-hand side: vectors, partials and scalars are per
+// right-hand side, each stops on its own, and the operator takes a tile set
+// whose lanes pair right-hand sides of one window (so they share one FFT and
+// one pass over the pointing) and skips tiles whose right-hand sides are done.
 #include <math.h>
 #include <stdlib.h>
 
@@ -39,36 +45,49 @@ struct CgState {
   unsigned counter;
   int pad;
 };
+static_assert(sizeof(CgState) % sizeof(int) == 0, "per-rhs done flags are strided in ints");
+static const int ST_STRIDE = (int)(sizeof(CgState) / sizeof(int));
 
 struct SolveBuffers {
   bool fp64 = false;
-  long long nvec = 0;  // n_obs * ns_pad
+  int cap_rhs = 0;
+  long long nvec = 0;  // n_obs * ns_pad per right-hand side
   void *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *xb = nullptr;
-  double* partials = nullptr;
-  CgState* st = nullptr;
-  CgState* host_st = nullptr;  // pinned, 2 slots
+  double* partials = nullptr;  // [cap_rhs][NB][4]
+  CgState* st = nullptr;       // [cap_rhs]
+  CgState* host_st = nullptr;  // pinned, 2 slots of cap_rhs
+  int* flags = nullptr;        // [cap_rhs] per-rhs skip / inactive flags
   cudaEvent_t ev[2] = {nullptr, nullptr};
   // float64 refinement vectors (allocated with the float64 buffers)
   double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *t64 = nullptr, *xbest64 = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int graph_iters = 0;
+  int graph_iters = 0, graph_rhs = 0;
+  const void* graph_ts = nullptr;
   long long graph_launches = 0;  // kernel nodes per replay
   std::vector<void*> allocs;
+  size_t bytes = 0;
 };
 
 static const int NB = 304;  // blocks of the vector kernels (2 per SM)
 static const int NT = 256;
 
+static void free_one(SolveBuffers* sb) {
+  if (!sb) return;
+  if (sb->exec) cudaGraphExecDestroy(sb->exec);
+  for (int i = 0; i < 2; ++i)
+    if (sb->ev[i]) cudaEventDestroy(sb->ev[i]);
+  if (sb->host_st) cudaFreeHost(sb->host_st);
+  for (void* a : sb->allocs) cudaFree(a);
+  delete sb;
+}
+
+size_t solve_buffer_bytes(const Plan* p) {
+  return (p->sb64 ? p->sb64->bytes : 0) + (p->sb32 ? p->sb32->bytes : 0);
+}
+
 void free_solve_buffers(Plan* p) {
-  for (SolveBuffers* sb : {p->sb64, p->sb32}) {
-    if (!sb) continue;
-    if (sb->exec) cudaGraphExecDestroy(sb->exec);
-    for (int i = 0; i < 2; ++i)
-      if (sb->ev[i]) cudaEventDestroy(sb->ev[i]);
-    if (sb->host_st) cudaFreeHost(sb->host_st);
-    for (void* a : sb->allocs) cudaFree(a);
-    delete sb;
-  }
+  free_one(p->sb64);
+  free_one(p->sb32);
   p->sb64 = p->sb32 = nullptr;
 }
 
@@ -77,36 +96,47 @@ static madmap_status sb_alloc(Plan* p, SolveBuffers* sb, void** ptr, size_t byte
   if (st != MADMAP_OK) return st;
   // ownership moves to the solve buffers
   p->allocs.pop_back();
+  p->device_bytes -= bytes;
   sb->allocs.push_back(*ptr);
+  sb->bytes += bytes;
   return MADMAP_OK;
 }
 
-static madmap_status get_buffers(Plan* p, bool fp64, SolveBuffers** out) {
+// Work buffers for `n_rhs` right-hand sides in one precision (kept with the
+// plan and grown when a larger batch arrives).
+static madmap_status get_buffers(Plan* p, bool fp64, int n_rhs, SolveBuffers** out) {
   SolveBuffers*& slot = fp64 ? p->sb64 : p->sb32;
-  if (slot) {
+  if (slot && slot->cap_rhs >= n_rhs) {
     *out = slot;
     return MADMAP_OK;
   }
+  if (slot) {
+    cudaDeviceSynchronize();
+    free_one(slot);
+    slot = nullptr;
+  }
   SolveBuffers* sb = new SolveBuffers();
   sb->fp64 = fp64;
+  sb->cap_rhs = n_rhs;
   sb->nvec = (long long)std::max(1, p->n_obs) * p->ns_pad;
-  const size_t vb = (size_t)sb->nvec * (fp64 ? sizeof(double) : sizeof(float));
+  const size_t vb = (size_t)sb->nvec * n_rhs * (fp64 ? sizeof(double) : sizeof(float));
   madmap_status st = MADMAP_OK;
   void** vecs[6] = {&sb->x, &sb->r, &sb->z, &sb->p, &sb->q, &sb->xb};
   for (void** v : vecs)
     if ((st = sb_alloc(p, sb, v, vb)) != MADMAP_OK) break;
-  if (st == MADMAP_OK) st = sb_alloc(p, sb, (void**)&sb->partials, sizeof(double) * NB * 4);
-  if (st == MADMAP_OK) st = sb_alloc(p, sb, (void**)&sb->st, sizeof(CgState));
+  if (st == MADMAP_OK) st = sb_alloc(p, sb, (void**)&sb->partials, sizeof(double) * NB * 4 * n_rhs);
+  if (st == MADMAP_OK) st = sb_alloc(p, sb, (void**)&sb->st, sizeof(CgState) * n_rhs);
+  if (st == MADMAP_OK) st = sb_alloc(p, sb, (void**)&sb->flags, sizeof(int) * n_rhs);
   if (st == MADMAP_OK && fp64) {
     double** v64[5] = {&sb->b64, &sb->x64, &sb->r64, &sb->t64, &sb->xbest64};
     for (double** v : v64)
-      if ((st = sb_alloc(p, sb, (void**)v, sizeof(double) * sb->nvec)) != MADMAP_OK) break;
+      if ((st = sb_alloc(p, sb, (void**)v, sizeof(double) * sb->nvec * n_rhs)) != MADMAP_OK) break;
   }
   if (st == MADMAP_OK) {
-    cudaError_t e = cudaMallocHost(&sb->host_st, 2 * sizeof(CgState));
+    cudaError_t e = cudaMallocHost(&sb->host_st, 2 * sizeof(CgState) * n_rhs);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sb->ev[0], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sb->ev[1], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMemset(sb->st, 0, sizeof(CgState));
+    if (e == cudaSuccess) e = cudaMemset(sb->st, 0, sizeof(CgState) * n_rhs);
     if (e != cudaSuccess) st = cuda_fail(e, "solve buffers");
   }
   slot = sb;  // freed with the plan, even when partially built
@@ -222,11 +252,17 @@ __device__ __forceinline__ void final_sums(const double* partials, double (&out)
 }
 
 // ---------------------------------------------------------------- CG kernels
+// All kernels take the right-hand side from blockIdx.y; `nvec` is the length
+// of one right-hand side's vectors.
 template <typename Real, int NS, typename Bt>
 __global__ void __launch_bounds__(NT) k_cg_init(Real* x, Real* r, Real* z, Real* p, Real* q, Real* xb, const Bt* b,
-                                                int n_obs, const double* P64, const float* P32,
+                                                long long nvec, int n_obs, const double* P64, const float* P32,
                                                 const unsigned char* f64, CgState* st, double* partials,
-                                                double tol, int max_iter) {
+                                                double tol, int max_iter, const int* inactive) {
+  const long long o = blockIdx.y * nvec;
+  x += o; r += o; z += o; p += o; q += o; xb += o; b += o;
+  st += blockIdx.y;
+  partials += (long long)blockIdx.y * NB * 4;
   double acc[2] = {0.0, 0.0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_obs; i += gridDim.x * blockDim.x) {
     V3<Real, NS> rv;
@@ -264,14 +300,19 @@ __global__ void __launch_bounds__(NT) k_cg_init(Real* x, Real* r, Real* z, Real*
     st->max_iter = max_iter;
     st->status = 0;
     st->alpha = st->beta = 0.0;
-    st->done = (st->bnorm == 0.0 || max_iter <= 0 || st->res <= tol) ? 1 : 0;
+    const bool off = inactive && inactive[blockIdx.y];
+    st->done = (off || st->bnorm == 0.0 || max_iter <= 0 || st->res <= tol) ? 1 : 0;
   }
 }
 
 template <typename Real, int NS>
-__global__ void __launch_bounds__(NT) k_cg_alpha(const Real* p, const Real* q, int n_obs, CgState* st,
-                                                 double* partials) {
+__global__ void __launch_bounds__(NT) k_cg_alpha(const Real* p, const Real* q, long long nvec, int n_obs,
+                                                 CgState* st, double* partials) {
+  st += blockIdx.y;
   if (st->done) return;
+  p += blockIdx.y * nvec;
+  q += blockIdx.y * nvec;
+  partials += (long long)blockIdx.y * NB * 4;
   double acc[1] = {0.0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_obs; i += gridDim.x * blockDim.x)
     acc[0] += dotv(ldv<Real, NS>(p, i), ldv<Real, NS>(q, i));
@@ -289,10 +330,14 @@ __global__ void __launch_bounds__(NT) k_cg_alpha(const Real* p, const Real* q, i
 }
 
 template <typename Real, int NS>
-__global__ void __launch_bounds__(NT) k_cg_update(Real* x, Real* r, Real* z, const Real* p, const Real* q, int n_obs,
-                                                  const double* P64, const float* P32, const unsigned char* f64,
-                                                  CgState* st, double* partials) {
+__global__ void __launch_bounds__(NT) k_cg_update(Real* x, Real* r, Real* z, const Real* p, const Real* q,
+                                                  long long nvec, int n_obs, const double* P64, const float* P32,
+                                                  const unsigned char* f64, CgState* st, double* partials) {
+  st += blockIdx.y;
   if (st->done) return;
+  const long long o = blockIdx.y * nvec;
+  x += o; r += o; z += o; p += o; q += o;
+  partials += (long long)blockIdx.y * NB * 4;
   const Real alpha = (Real)st->alpha;
   double acc[2] = {0.0, 0.0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_obs; i += gridDim.x * blockDim.x) {
@@ -333,9 +378,12 @@ __global__ void __launch_bounds__(NT) k_cg_update(Real* x, Real* r, Real* z, con
 
 template <typename Real, int NS>
 __global__ void __launch_bounds__(NT) k_cg_direction(const Real* x, const Real* z, Real* p, Real* q, Real* xb,
-                                                     int n_obs, CgState* st) {
+                                                     long long nvec, int n_obs, CgState* st) {
+  st += blockIdx.y;
   const int k = st->k;
   if (st->dir_k >= k) return;
+  const long long o = blockIdx.y * nvec;
+  x += o; z += o; p += o; q += o; xb += o;
   const bool copy = st->best_k == k;
   const bool more = !st->done;
   const Real beta = (Real)st->beta;
@@ -388,21 +436,27 @@ __global__ void k_unpack(const Real* in, U* out, int n_obs, int ns, int ns_pad) 
   }
 }
 
-// x64 += e (float32 correction), t64 = 0
-__global__ void k_refine_add(double* x64, const float* e, double* t64, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    x64[i] += (double)e[i];
-    t64[i] = 0.0;
+// x64 += e (float32 correction) for active right-hand sides, t64 = 0
+__global__ void k_refine_add(double* x64, const float* e, double* t64, long long nvec, const int* inactive) {
+  if (inactive && inactive[blockIdx.y]) return;
+  const long long o = blockIdx.y * nvec;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvec; i += (long long)gridDim.x * blockDim.x) {
+    x64[o + i] += (double)e[o + i];
+    t64[o + i] = 0.0;
   }
 }
 
-// r64 = b64 - t64, ||r64||^2 -> st->res (relative to st->bnorm) by the last block
-__global__ void __launch_bounds__(NT) k_residual(const double* b64, const double* t64, double* r64, long long n,
-                                                 CgState* st, double* partials) {
+// r64 = b64 - t64 and ||r64|| -> st[rhs].res (by the last block of the rhs)
+__global__ void __launch_bounds__(NT) k_residual(const double* b64, const double* t64, double* r64, long long nvec,
+                                                 CgState* st, double* partials, const int* inactive) {
+  if (inactive && inactive[blockIdx.y]) return;
+  const long long o = blockIdx.y * nvec;
+  st += blockIdx.y;
+  partials += (long long)blockIdx.y * NB * 4;
   double acc[1] = {0.0};
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double v = b64[i] - t64[i];
-    r64[i] = v;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvec; i += (long long)gridDim.x * blockDim.x) {
+    const double v = b64[o + i] - t64[o + i];
+    r64[o + i] = v;
     acc[0] += v * v;
   }
   if (block_reduce_publish<1>(acc, partials, &st->counter) && threadIdx.x == 0) {
@@ -413,14 +467,27 @@ __global__ void __launch_bounds__(NT) k_residual(const double* b64, const double
   }
 }
 
+// xbest64 = x64 for right-hand sides flagged in `take`
+__global__ void k_take_best(const double* x64, double* xbest64, long long nvec, const int* take) {
+  if (!take[blockIdx.y]) return;
+  const long long o = blockIdx.y * nvec;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvec; i += (long long)gridDim.x * blockDim.x)
+    xbest64[o + i] = x64[o + i];
+}
+
 static int grid_vec(long long n) {
   long long g = (n + NT - 1) / NT;
   return (int)std::max(1LL, std::min<long long>(g, NB));
 }
 
 // ---------------------------------------------------------------- PCG driver
+struct Batch {
+  int n_rhs = 1;
+  const TileSet* ts = nullptr;  // NULL: single right-hand side over the plan's own tiles
+};
+
 template <typename Real, int NS>
-static void enqueue_iteration(Plan* p, SolveBuffers* sb, cudaStream_t s, madmap_status* st) {
+static void enqueue_iteration(Plan* p, SolveBuffers* sb, const Batch& B, cudaStream_t s, madmap_status* st) {
   Real* x = (Real*)sb->x;
   Real* r = (Real*)sb->r;
   Real* z = (Real*)sb->z;
@@ -428,22 +495,27 @@ static void enqueue_iteration(Plan* p, SolveBuffers* sb, cudaStream_t s, madmap_
   Real* q = (Real*)sb->q;
   Real* xb = (Real*)sb->xb;
   const int n = p->n_obs;
-  const int g = grid_vec(n);
-  *st = op_launch(p, sizeof(Real) == 8, IN_MAP, OUT_MAP, pp, q, 0, 0, 1, &sb->st->done, s);
+  const long long nv = sb->nvec;
+  const dim3 g(grid_vec(n), B.n_rhs);
+  if (B.ts)
+    *st = op_launch_set(p, sizeof(Real) == 8, IN_MAP, OUT_MAP, pp, q, nv, nv, &sb->st->done, ST_STRIDE, B.ts, s);
+  else
+    *st = op_launch(p, sizeof(Real) == 8, IN_MAP, OUT_MAP, pp, q, 0, 0, 1, &sb->st->done, s);
   count_launches(3);
-  k_cg_alpha<Real, NS><<<g, NT, 0, s>>>(pp, q, n, sb->st, sb->partials);
-  k_cg_update<Real, NS><<<g, NT, 0, s>>>(x, r, z, pp, q, n, p->P64, p->P32, p->fp64flag, sb->st, sb->partials);
-  k_cg_direction<Real, NS><<<g, NT, 0, s>>>(x, z, pp, q, xb, n, sb->st);
+  k_cg_alpha<Real, NS><<<g, NT, 0, s>>>(pp, q, nv, n, sb->st, sb->partials);
+  k_cg_update<Real, NS><<<g, NT, 0, s>>>(x, r, z, pp, q, nv, n, p->P64, p->P32, p->fp64flag, sb->st, sb->partials);
+  k_cg_direction<Real, NS><<<g, NT, 0, s>>>(x, z, pp, q, xb, nv, n, sb->st);
 }
 
 template <typename Real, int NS>
-static madmap_status enqueue_chunk(Plan* p, SolveBuffers* sb, int iters, bool use_graph, cudaStream_t s) {
+static madmap_status enqueue_chunk(Plan* p, SolveBuffers* sb, const Batch& B, int iters, bool use_graph,
+                                   cudaStream_t s) {
   madmap_status st = MADMAP_OK;
   if (!use_graph) {
-    for (int i = 0; i < iters && st == MADMAP_OK; ++i) enqueue_iteration<Real, NS>(p, sb, s, &st);
+    for (int i = 0; i < iters && st == MADMAP_OK; ++i) enqueue_iteration<Real, NS>(p, sb, B, s, &st);
     return st;
   }
-  if (!sb->exec || sb->graph_iters != iters) {
+  if (!sb->exec || sb->graph_iters != iters || sb->graph_rhs != B.n_rhs || sb->graph_ts != (const void*)B.ts) {
     // kernel attributes are set before capture begins
     st = op_launch(p, sizeof(Real) == 8, IN_MAP, OUT_MAP, nullptr, nullptr, 0, 0, 0, nullptr, s);
     if (st != MADMAP_OK) return st;
@@ -454,7 +526,7 @@ static madmap_status enqueue_chunk(Plan* p, SolveBuffers* sb, int iters, bool us
     cudaGraph_t graph = nullptr;
     const int64_t before = madmap_kernel_launch_count();
     MM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-    for (int i = 0; i < iters && st == MADMAP_OK; ++i) enqueue_iteration<Real, NS>(p, sb, s, &st);
+    for (int i = 0; i < iters && st == MADMAP_OK; ++i) enqueue_iteration<Real, NS>(p, sb, B, s, &st);
     cudaError_t e = cudaStreamEndCapture(s, &graph);
     // captured kernels did not run: count them once per replay instead
     sb->graph_launches = madmap_kernel_launch_count() - before;
@@ -468,6 +540,8 @@ static madmap_status enqueue_chunk(Plan* p, SolveBuffers* sb, int iters, bool us
     cudaGraphDestroy(graph);
     MM_CUDA(e);
     sb->graph_iters = iters;
+    sb->graph_rhs = B.n_rhs;
+    sb->graph_ts = B.ts;
   }
   MM_CUDA(cudaGraphLaunch(sb->exec, s));
   count_launches(sb->graph_launches);
@@ -479,33 +553,40 @@ struct PcgResult {
   double best_res = 0.0, final_res = 0.0;
 };
 
-// Runs PCG on H e = b for the plan in the buffers' precision.  b: Bt vector in
-// the padded working layout.  Result: best iterate in sb->xb.
+// Runs PCG on H e = b for every right-hand side of the batch, in the buffers'
+// precision.  b: Bt vectors in the padded working layout, nvec apart.
+// inactive (device, may be NULL): right-hand sides to leave untouched.
+// Results: best iterates in sb->xb, summaries in out[rhs].
 template <typename Real, int NS, typename Bt>
-static madmap_status run_pcg(Plan* p, SolveBuffers* sb, const Bt* b, double tol, int max_iter, int per_sync,
-                             bool use_graph, cudaStream_t s, PcgResult* out) {
-  const int n = p->n_obs;
+static madmap_status run_pcg(Plan* p, SolveBuffers* sb, const Batch& B, const Bt* b, const int* inactive, double tol,
+                             int max_iter, int per_sync, bool use_graph, cudaStream_t s, std::vector<PcgResult>& out) {
+  const int n = p->n_obs, R = B.n_rhs;
   count_launches(1);
-  k_cg_init<Real, NS, Bt><<<grid_vec(n), NT, 0, s>>>((Real*)sb->x, (Real*)sb->r, (Real*)sb->z, (Real*)sb->p,
-                                                     (Real*)sb->q, (Real*)sb->xb, b, n, p->P64, p->P32,
-                                                     p->fp64flag, sb->st, sb->partials, tol, max_iter);
+  k_cg_init<Real, NS, Bt><<<dim3(grid_vec(n), R), NT, 0, s>>>(
+      (Real*)sb->x, (Real*)sb->r, (Real*)sb->z, (Real*)sb->p, (Real*)sb->q, (Real*)sb->xb, b, sb->nvec, n, p->P64,
+      p->P32, p->fp64flag, sb->st, sb->partials, tol, max_iter, inactive);
   MM_CUDA(cudaGetLastError());
   int launched = 0, slot = 0;
   bool pending = false;
   const int G = std::max(1, per_sync);
+  auto all_done = [&](int sl) {
+    for (int k = 0; k < R; ++k)
+      if (!sb->host_st[sl * sb->cap_rhs + k].done) return false;
+    return true;
+  };
   // one chunk in flight ahead of the host check
   while (true) {
     if (launched < max_iter) {
-      madmap_status st = enqueue_chunk<Real, NS>(p, sb, G, use_graph, s);
+      madmap_status st = enqueue_chunk<Real, NS>(p, sb, B, G, use_graph, s);
       if (st != MADMAP_OK) return st;
       launched += G;
     }
-    MM_CUDA(cudaMemcpyAsync(&sb->host_st[slot], sb->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    MM_CUDA(cudaMemcpyAsync(&sb->host_st[slot * sb->cap_rhs], sb->st, sizeof(CgState) * R, cudaMemcpyDeviceToHost, s));
     MM_CUDA(cudaEventRecord(sb->ev[slot], s));
     if (pending) {
       const int prev = slot ^ 1;
       MM_CUDA(cudaEventSynchronize(sb->ev[prev]));
-      if (sb->host_st[prev].done) break;
+      if (all_done(prev)) break;
     }
     if (launched >= max_iter && pending) {
       MM_CUDA(cudaEventSynchronize(sb->ev[slot]));
@@ -515,112 +596,171 @@ static madmap_status run_pcg(Plan* p, SolveBuffers* sb, const Bt* b, double tol,
     slot ^= 1;
   }
   MM_CUDA(cudaStreamSynchronize(s));
-  CgState h;
-  MM_CUDA(cudaMemcpy(&h, sb->st, sizeof(CgState), cudaMemcpyDeviceToHost));
-  out->iters = h.k;
-  out->best_iter = h.best_k;
-  out->best_res = h.best_res;
-  out->final_res = h.res;
-  out->status = h.status;
+  std::vector<CgState> h(R);
+  MM_CUDA(cudaMemcpy(h.data(), sb->st, sizeof(CgState) * R, cudaMemcpyDeviceToHost));
+  out.assign(R, PcgResult());
+  for (int k = 0; k < R; ++k) {
+    out[k].iters = h[k].k;
+    out[k].best_iter = h[k].best_k;
+    out[k].best_res = h[k].best_res;
+    out[k].final_res = h[k].res;
+    out[k].status = h[k].status;
+  }
   return MADMAP_OK;
 }
 
 template <int NS>
-static madmap_status solve_impl(Plan* p, const float* d, double* m, const madmap_solve_opts& o,
+static madmap_status solve_impl(Plan* p, int n_rhs, const float* d, double* m, const madmap_solve_opts& o,
                                 madmap_solve_info* info, cudaStream_t s) {
   auto t_start = std::chrono::steady_clock::now();
+  Batch B;
+  B.n_rhs = n_rhs;
+  if (n_rhs > 1) {
+    TileSet* ts = nullptr;
+    madmap_status st = get_tile_set(p, n_rhs, &ts);
+    if (st != MADMAP_OK) return st;
+    B.ts = ts;
+  }
   SolveBuffers* sb64 = nullptr;
-  madmap_status st = get_buffers(p, true, &sb64);
+  madmap_status st = get_buffers(p, true, n_rhs, &sb64);
   if (st != MADMAP_OK) return st;
   const long long nv = sb64->nvec;
   const int n = p->n_obs;
-  madmap_solve_info I;
-  memset(&I, 0, sizeof(I));
-  // right-hand side b = A^T N^-1 d in float64
-  MM_CUDA(cudaMemsetAsync(sb64->b64, 0, sizeof(double) * nv, s));
-  st = op_launch(p, true, IN_TOD, OUT_MAP, d, sb64->b64, 0, 0, 1, nullptr, s);
+  const dim3 gv(grid_vec(nv), n_rhs);
+  std::vector<madmap_solve_info> I(n_rhs);
+  for (auto& x : I) memset(&x, 0, sizeof(x));
+  // right-hand sides b = A^T N^-1 d in float64
+  MM_CUDA(cudaMemsetAsync(sb64->b64, 0, sizeof(double) * nv * n_rhs, s));
+  if (B.ts)
+    st = op_launch_set(p, true, IN_TOD, OUT_MAP, d, sb64->b64, p->n_t, nv, nullptr, 0, B.ts, s);
+  else
+    st = op_launch(p, true, IN_TOD, OUT_MAP, d, sb64->b64, 0, 0, 1, nullptr, s);
   if (st != MADMAP_OK) return st;
-  I.fp64_applies = 1;
   MM_CUDA(cudaStreamSynchronize(s));
-  I.t_rhs_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  const double t_rhs =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  for (auto& x : I) {
+    x.fp64_applies = 1;
+    x.t_rhs_ms = t_rhs;
+  }
   const bool graph = o.use_graph != 0;
+  std::vector<PcgResult> R;
   if (o.precision == MADMAP_FP64) {
-    PcgResult R;
-    st = run_pcg<double, NS, double>(p, sb64, sb64->b64, o.rel_tol, o.max_iter, o.iters_per_sync, graph, s, &R);
+    st = run_pcg<double, NS, double>(p, sb64, B, sb64->b64, nullptr, o.rel_tol, o.max_iter, o.iters_per_sync, graph, s,
+                                     R);
     if (st != MADMAP_OK) return st;
-    count_launches(1);
-    k_unpack<double, double><<<grid_vec((long long)n * p->n_stokes), NT, 0, s>>>((const double*)sb64->xb, m, n,
-                                                                                p->n_stokes, p->ns_pad);
-    I.iters = R.iters;
-    I.outer_iters = 1;
-    I.best_iter = R.best_iter;
-    I.fp64_applies += R.iters;
-    I.final_rel_res = R.final_res;
-    I.best_rel_res = R.best_res;
-    I.status = R.status != 0 ? R.status : (R.best_res <= o.rel_tol ? MADMAP_OK : MADMAP_WARN_MAXITER);
+    for (int k = 0; k < n_rhs; ++k) {
+      count_launches(1);
+      k_unpack<double, double><<<grid_vec((long long)n * p->n_stokes), NT, 0, s>>>(
+          (const double*)sb64->xb + k * nv, m + (long long)k * n * p->n_stokes, n, p->n_stokes, p->ns_pad);
+      I[k].iters = R[k].iters;
+      I[k].outer_iters = 1;
+      I[k].best_iter = R[k].best_iter;
+      I[k].fp64_applies += R[k].iters;
+      I[k].final_rel_res = R[k].final_res;
+      I[k].best_rel_res = R[k].best_res;
+      I[k].status = R[k].status != 0 ? R[k].status : (R[k].best_res <= o.rel_tol ? MADMAP_OK : MADMAP_WARN_MAXITER);
+    }
   } else {
     SolveBuffers* sb32 = nullptr;
-    st = get_buffers(p, false, &sb32);
+    st = get_buffers(p, false, n_rhs, &sb32);
     if (st != MADMAP_OK) return st;
-    // r64 = b64 and ||b||
-    MM_CUDA(cudaMemsetAsync(sb64->t64, 0, sizeof(double) * nv, s));
+    // r64 = b64 and ||b|| per right-hand side
+    MM_CUDA(cudaMemsetAsync(sb64->t64, 0, sizeof(double) * nv * n_rhs, s));
     count_launches(1);
-    k_residual<<<grid_vec(nv), NT, 0, s>>>(sb64->b64, sb64->t64, sb64->r64, nv, sb64->st, sb64->partials);
-    CgState h;
-    MM_CUDA(cudaMemcpyAsync(&h, sb64->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    k_residual<<<gv, NT, 0, s>>>(sb64->b64, sb64->t64, sb64->r64, nv, sb64->st, sb64->partials, nullptr);
+    std::vector<CgState> h(n_rhs);
+    MM_CUDA(cudaMemcpyAsync(h.data(), sb64->st, sizeof(CgState) * n_rhs, cudaMemcpyDeviceToHost, s));
     MM_CUDA(cudaStreamSynchronize(s));
-    const double bnorm = h.res;
-    MM_CUDA(cudaMemsetAsync(sb64->x64, 0, sizeof(double) * nv, s));
-    MM_CUDA(cudaMemsetAsync(sb64->xbest64, 0, sizeof(double) * nv, s));
-    double best = bnorm > 0 ? 1.0 : 0.0, res = best;
-    int best_iter = 0, total = 0, outer = 0, inner_status = 0;
-    while (bnorm > 0 && res > o.rel_tol && total < o.max_iter && outer < o.max_outer) {
-      PcgResult R;
-      const int budget = o.max_iter - total;
-      st = run_pcg<float, NS, double>(p, sb32, sb64->r64, o.inner_rel_tol, budget, o.iters_per_sync, graph, s, &R);
-      if (st != MADMAP_OK) return st;
-      total += R.iters;
-      I.fp32_applies += R.iters;
-      ++outer;
-      if (R.status != 0) inner_status = R.status;
-      count_launches(2);
-      k_refine_add<<<grid_vec(nv), NT, 0, s>>>(sb64->x64, (const float*)sb32->xb, sb64->t64, nv);
-      st = op_launch(p, true, IN_MAP, OUT_MAP, sb64->x64, sb64->t64, 0, 0, 1, nullptr, s);
-      if (st != MADMAP_OK) return st;
-      ++I.fp64_applies;
-      k_residual<<<grid_vec(nv), NT, 0, s>>>(sb64->b64, sb64->t64, sb64->r64, nv, sb64->st, sb64->partials);
-      MM_CUDA(cudaMemcpyAsync(&h, sb64->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
-      MM_CUDA(cudaStreamSynchronize(s));
-      res = h.res / bnorm;
-      if (res < best) {
-        best = res;
-        best_iter = total;
-        MM_CUDA(cudaMemcpyAsync(sb64->xbest64, sb64->x64, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
-      }
-      if (R.iters == 0) break;
+    std::vector<double> bnorm(n_rhs), best(n_rhs), res(n_rhs);
+    std::vector<int> total(n_rhs, 0), best_iter(n_rhs, 0), inner_status(n_rhs, 0), inactive(n_rhs), take(n_rhs);
+    int n_active = 0;
+    for (int k = 0; k < n_rhs; ++k) {
+      bnorm[k] = h[k].res;
+      best[k] = res[k] = bnorm[k] > 0 ? 1.0 : 0.0;
+      inactive[k] = !(bnorm[k] > 0 && res[k] > o.rel_tol && o.max_iter > 0);
+      n_active += !inactive[k];
     }
-    count_launches(1);
-    k_unpack<double, double><<<grid_vec((long long)n * p->n_stokes), NT, 0, s>>>(sb64->xbest64, m, n, p->n_stokes,
-                                                                                p->ns_pad);
-    I.iters = total;
-    I.outer_iters = outer;
-    I.best_iter = best_iter;
-    I.final_rel_res = res;
-    I.best_rel_res = best;
-    I.status = best <= o.rel_tol ? MADMAP_OK : (inner_status != 0 ? inner_status : MADMAP_WARN_MAXITER);
+    MM_CUDA(cudaMemsetAsync(sb64->x64, 0, sizeof(double) * nv * n_rhs, s));
+    MM_CUDA(cudaMemsetAsync(sb64->xbest64, 0, sizeof(double) * nv * n_rhs, s));
+    int outer = 0;
+    while (n_active > 0 && outer < o.max_outer) {
+      int budget = 0;
+      for (int k = 0; k < n_rhs; ++k)
+        if (!inactive[k]) budget = std::max(budget, o.max_iter - total[k]);
+      MM_CUDA(cudaMemcpyAsync(sb64->flags, inactive.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, s));
+      st = run_pcg<float, NS, double>(p, sb32, B, sb64->r64, sb64->flags, o.inner_rel_tol, budget, o.iters_per_sync,
+                                      graph, s, R);
+      if (st != MADMAP_OK) return st;
+      ++outer;
+      count_launches(2);
+      k_refine_add<<<gv, NT, 0, s>>>(sb64->x64, (const float*)sb32->xb, sb64->t64, nv, sb64->flags);
+      if (B.ts)
+        st = op_launch_set(p, true, IN_MAP, OUT_MAP, sb64->x64, sb64->t64, nv, nv, sb64->flags, 1, B.ts, s);
+      else
+        st = op_launch(p, true, IN_MAP, OUT_MAP, sb64->x64, sb64->t64, 0, 0, 1, nullptr, s);
+      if (st != MADMAP_OK) return st;
+      k_residual<<<gv, NT, 0, s>>>(sb64->b64, sb64->t64, sb64->r64, nv, sb64->st, sb64->partials, sb64->flags);
+      MM_CUDA(cudaMemcpyAsync(h.data(), sb64->st, sizeof(CgState) * n_rhs, cudaMemcpyDeviceToHost, s));
+      MM_CUDA(cudaStreamSynchronize(s));
+      bool any_take = false;
+      for (int k = 0; k < n_rhs; ++k) {
+        take[k] = 0;
+        if (inactive[k]) continue;
+        total[k] += R[k].iters;
+        I[k].fp32_applies += R[k].iters;
+        ++I[k].fp64_applies;
+        ++I[k].outer_iters;
+        if (R[k].status != 0) inner_status[k] = R[k].status;
+        res[k] = h[k].res / bnorm[k];
+        if (res[k] < best[k]) {
+          best[k] = res[k];
+          best_iter[k] = total[k];
+          take[k] = 1;
+          any_take = true;
+        }
+        if (res[k] <= o.rel_tol || total[k] >= o.max_iter || R[k].iters == 0) {
+          inactive[k] = 1;
+          --n_active;
+        }
+      }
+      if (any_take) {
+        // the flags buffer is reused for `take`; the next round rewrites it
+        MM_CUDA(cudaMemcpyAsync(sb64->flags, take.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, s));
+        count_launches(1);
+        k_take_best<<<gv, NT, 0, s>>>(sb64->x64, sb64->xbest64, nv, sb64->flags);
+        MM_CUDA(cudaStreamSynchronize(s));
+      }
+    }
+    for (int k = 0; k < n_rhs; ++k) {
+      count_launches(1);
+      k_unpack<double, double><<<grid_vec((long long)n * p->n_stokes), NT, 0, s>>>(
+          sb64->xbest64 + k * nv, m + (long long)k * n * p->n_stokes, n, p->n_stokes, p->ns_pad);
+      I[k].iters = total[k];
+      I[k].best_iter = best_iter[k];
+      I[k].final_rel_res = res[k];
+      I[k].best_rel_res = best[k];
+      I[k].status = best[k] <= o.rel_tol ? MADMAP_OK : (inner_status[k] != 0 ? inner_status[k] : MADMAP_WARN_MAXITER);
+    }
   }
   MM_CUDA(cudaStreamSynchronize(s));
   MM_CUDA(cudaGetLastError());
-  I.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-  if (info) *info = I;
-  return (madmap_status)I.status;
+  const double t_all = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  int worst = MADMAP_OK;
+  for (auto& x : I) {
+    x.t_solve_ms = t_all;
+    if (x.status < 0) worst = x.status;
+    else if (worst == MADMAP_OK && x.status != MADMAP_OK) worst = x.status;
+  }
+  if (info) memcpy(info, I.data(), sizeof(madmap_solve_info) * n_rhs);
+  return (madmap_status)worst;
 }
 
 // ---------------------------------------------------------------- operator entry points
 template <typename Real>
 static madmap_status apply_impl(Plan* p, bool fp64, int n_rhs, const void* x, void* y, cudaStream_t s) {
   SolveBuffers* sb = nullptr;
-  madmap_status st = get_buffers(p, fp64, &sb);
+  madmap_status st = get_buffers(p, fp64, 1, &sb);
   if (st != MADMAP_OK) return st;
   const int n = p->n_obs, ns = p->n_stokes, np = p->ns_pad;
   const long long user = (long long)n * ns;
@@ -641,7 +781,7 @@ static madmap_status apply_impl(Plan* p, bool fp64, int n_rhs, const void* x, vo
 template <typename Real>
 static madmap_status rhs_impl(Plan* p, bool fp64, int n_rhs, const float* d, void* b, cudaStream_t s) {
   SolveBuffers* sb = nullptr;
-  madmap_status st = get_buffers(p, fp64, &sb);
+  madmap_status st = get_buffers(p, fp64, 1, &sb);
   if (st != MADMAP_OK) return st;
   const int n = p->n_obs, ns = p->n_stokes, np = p->ns_pad;
   const long long user = (long long)n * ns;
@@ -752,7 +892,40 @@ extern "C" madmap_status madmap_solve(madmap_plan_t plan, const float* d, double
   cudaStream_t s = p->solve_stream;
   MM_CUDA(cudaEventRecord(p->solve_event, caller));
   MM_CUDA(cudaStreamWaitEvent(s, p->solve_event, 0));
-  madmap_status st = p->n_stokes == 1 ? solve_impl<1>(p, d, m, o, info, s) : solve_impl<3>(p, d, m, o, info, s);
+  madmap_status st = p->n_stokes == 1 ? solve_impl<1>(p, 1, d, m, o, info, s) : solve_impl<3>(p, 1, d, m, o, info, s);
+  cudaStreamSynchronize(s);
+  return st;
+}
+
+extern "C" madmap_status madmap_solve_batched(madmap_plan_t plan, int32_t n_rhs, const float* d, double* m,
+                                              const madmap_solve_opts* opts, madmap_solve_info* info, void* stream) {
+  MM_CHECK(plan && n_rhs >= 1, MADMAP_ERR_INVALID_ARG, "solve_batched: NULL plan or n_rhs < 1");
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  MM_CHECK(m || p->n_obs == 0, MADMAP_ERR_INVALID_ARG, "solve_batched: m is NULL");
+  MM_CHECK(d || p->n_t == 0, MADMAP_ERR_INVALID_ARG, "solve_batched: d is NULL");
+  MM_CHECK(n_rhs <= 65535, MADMAP_ERR_INVALID_ARG, "solve_batched: at most 65535 right-hand sides");
+  madmap_solve_opts o;
+  madmap_solve_opts_default(&o);
+  if (opts) o = *opts;
+  MM_CHECK(o.precision == MADMAP_FP64 || o.precision == MADMAP_MIXED, MADMAP_ERR_INVALID_ARG,
+           "solve_batched: precision must be FP64 or MIXED");
+  MM_CHECK(o.max_iter >= 0 && o.rel_tol >= 0 && o.iters_per_sync >= 1 && o.max_outer >= 1 &&
+               o.inner_rel_tol > 0 && o.inner_rel_tol < 1,
+           MADMAP_ERR_INVALID_ARG, "solve_batched: bad options");
+  cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  if (p->n_obs == 0) {
+    if (info) memset(info, 0, sizeof(*info) * n_rhs);
+    return MADMAP_OK;
+  }
+  if (!p->solve_stream) {
+    MM_CUDA(cudaStreamCreateWithFlags(&p->solve_stream, cudaStreamNonBlocking));
+    MM_CUDA(cudaEventCreateWithFlags(&p->solve_event, cudaEventDisableTiming));
+  }
+  cudaStream_t s = p->solve_stream;
+  MM_CUDA(cudaEventRecord(p->solve_event, caller));
+  MM_CUDA(cudaStreamWaitEvent(s, p->solve_event, 0));
+  madmap_status st = p->n_stokes == 1 ? solve_impl<1>(p, n_rhs, d, m, o, info, s)
+                                      : solve_impl<3>(p, n_rhs, d, m, o, info, s);
   cudaStreamSynchronize(s);
   return st;
 }
@@ -765,7 +938,7 @@ extern "C" madmap_status madmap_time_operator(madmap_plan_t plan, int32_t precis
   Plan* p = reinterpret_cast<Plan*>(plan);
   const bool fp64 = precision == MADMAP_FP64;
   SolveBuffers* sb = nullptr;
-  madmap_status st = get_buffers(p, fp64, &sb);
+  madmap_status st = get_buffers(p, fp64, 1, &sb);
   if (st != MADMAP_OK) return st;
   int n_chunks, per_chunk;
   chunking(p, n_chunks, per_chunk);

@@ -336,3 +336,62 @@ def test_set_filters_matches_new_plan():
 def test_oracle_lags_agree_with_library_lags():
     p = tiny_IQU()
     assert np.allclose(lib_lags(p), lags_for(p), rtol=1e-12, atol=1e-15)
+
+
+# ------------------------------------------------------------------ batched right-hand sides
+def _batched_problem(kind, n_rhs):
+    from synth import make_config, make_flat_problem
+    if kind == "T":
+        return make_flat_problem("bT", 51, 6, 1, 3000, 1, 24, interval_lengths=lambda r, n: [700, 1300, 1000],
+                                 noise=(1.0, 3.0, 1.7), n_rhs=n_rhs, flag_frac=0.02)
+    if kind == "IQU":
+        return make_flat_problem("bIQU", 52, 5, 4, 900, 3, 16, det_angles_deg=[0.0, 45.0, 90.0, 135.0],
+                                 hwp_step_deg=22.5, noise=(1.0, 4.0, 1.5), n_rhs=n_rhs, det_sweep_offset=True)
+    return make_config(4, scale=6, n_rhs=n_rhs)
+
+
+@pytest.mark.parametrize("kind,n_rhs", [("T", 5), ("IQU", 3), ("IQU", 2), ("cfg4", 7)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_batched_matches_single_solves_and_oracle(kind, n_rhs, prec):
+    p = _batched_problem(kind, n_rhs)
+    S = system_for(p)
+    plan = make_plan(p)
+    d = cuda(p.d)
+    tol = 1e-12 if prec == "fp64" else 1e-10
+    kw = dict(precision=prec, rel_tol=tol, max_iter=800, max_outer=20)
+    mb, infos = plan.solve_batched(d, **kw)
+    assert mb.shape == (n_rhs, plan.n_obs, p.n_stokes) and len(infos) == n_rhs
+    keep = ~S.excised
+    for r in range(n_rhs):
+        m1, i1 = plan.solve(d[r].contiguous(), **kw)
+        x, _ = S.solve(p.d[r], rel_tol=1e-13, max_iter=800)
+        if prec == "fp64":
+            assert infos[r]["iters"] == i1["iters"]
+            assert rel_rms(host(mb[r]), host(m1)) < 1e-11
+            assert rel_rms(host(mb[r]), x) < FP64_MAP_TOL
+        else:
+            for s in range(p.n_stokes):
+                assert rel_rms(host(mb[r])[keep, s], x[keep, s]) < MIXED_MAP_TOL
+        assert infos[r]["best_rel_res"] <= tol * 1.0001
+
+
+def test_solve_batched_of_one_equals_solve():
+    p = _batched_problem("IQU", 1)
+    plan = make_plan(p)
+    d = cuda(p.d)
+    mb, ib = plan.solve_batched(d, rel_tol=1e-11, max_iter=300)
+    m1, i1 = plan.solve(d[0].contiguous(), rel_tol=1e-11, max_iter=300)
+    assert ib[0]["iters"] == i1["iters"]
+    assert rel_rms(host(mb[0]), host(m1)) < 1e-12
+
+
+def test_solve_batched_reuses_and_grows_buffers():
+    p = _batched_problem("T", 6)
+    plan = make_plan(p)
+    d = cuda(p.d)
+    m3, _ = plan.solve_batched(d[:3].contiguous(), rel_tol=1e-12, max_iter=500)
+    m6, _ = plan.solve_batched(d, rel_tol=1e-12, max_iter=500)
+    m3b, _ = plan.solve_batched(d[:3].contiguous(), rel_tol=1e-12, max_iter=500)
+    for r in range(3):
+        assert rel_rms(host(m6[r]), host(m3[r])) < 1e-11
+        assert rel_rms(host(m3b[r]), host(m3[r])) < 1e-11
