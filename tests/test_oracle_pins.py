@@ -376,3 +376,78 @@ def test_sampled_operator_matches_full_operator():
     full = S.H(x)
     pk = [0, 5, S.n_obs // 2, S.n_obs - 1]
     assert np.allclose(S.H_sampled(x, pk), full[pk], rtol=1e-12, atol=1e-12 * np.abs(full).max())
+
+
+# ----------------------------------------------------------------------------- adjoint
+def _loss_setup(seed=61):
+    from oracle.adjoint import solve_backward  # noqa: F401
+    p = tiny_IQU(seed=seed, n_per_det=400, n_lags=12, n_ivl_lo=40, n_ivl_hi=250)
+    rng = np.random.default_rng(seed)
+    return p, rng
+
+
+def _loss(S, d, target):
+    m, _ = S.solve(d, rel_tol=1e-14, max_iter=3000)
+    keep = ~S.excised
+    return float(np.sum((m - target)[keep] ** 2)), m
+
+
+def test_adjoint_grad_d_matches_finite_difference():
+    from oracle.adjoint import solve_backward
+    p, rng = _loss_setup()
+    S = system_for(p)
+    d = p.d[0].astype(np.float64)
+    target = rng.standard_normal((S.n_obs, 3))
+    L0, m = _loss(S, d, target)
+    g = 2.0 * (m - target)
+    gd, _, _ = solve_backward(S, d, m, g)
+    for _ in range(3):
+        v = rng.standard_normal(d.shape)
+        eps = 1e-3
+        fd = (_loss(S, d + eps * v, target)[0] - _loss(S, d - eps * v, target)[0]) / (2 * eps)
+        assert float(gd @ v) == pytest.approx(fd, rel=1e-8)
+
+
+def test_adjoint_lag_gradient_matches_finite_difference():
+    from oracle.adjoint import solve_backward
+    p, rng = _loss_setup(62)
+    lags = lags_for(p)
+    S = system_for(p, lags=lags)
+    d = p.d[0].astype(np.float64)
+    target = rng.standard_normal((S.n_obs, 3))
+    _, m = _loss(S, d, target)
+    _, gf, _ = solve_backward(S, d, m, 2.0 * (m - target))
+    for _ in range(3):
+        delta = rng.standard_normal(lags.shape) * np.abs(lags).max() * 1e-2
+        eps = 1e-3
+        lp = system_for(p, lags=lags + eps * delta)
+        lm = system_for(p, lags=lags - eps * delta)
+        fd = (_loss(lp, d, target)[0] - _loss(lm, d, target)[0]) / (2 * eps)
+        assert float(np.sum(gf * delta)) == pytest.approx(fd, rel=1e-6)
+
+
+def test_adjoint_psd_parameter_gradient_and_sigma_invariance():
+    from oracle.adjoint import params_gradient, solve_backward
+    p, rng = _loss_setup(63)
+    S = system_for(p)
+    d = p.d[0].astype(np.float64)
+    target = rng.standard_normal((S.n_obs, 3))
+    _, m = _loss(S, d, target)
+    _, gf, _ = solve_backward(S, d, m, 2.0 * (m - target))
+    gp = params_gradient(gf, p.n_lags, p.fs, p.noise_params)
+    base = p.noise_params.copy()
+    for k in range(p.n_filters):
+        for j in range(3):
+            h = 1e-4 * base[k, j]
+            vals = []
+            for sgn in (1, -1):
+                prm = base.copy()
+                prm[k, j] += sgn * h
+                from oracle.noise import filter_lags
+                lg = np.stack([filter_lags(p.n_lags, p.fs, *prm[q]) for q in range(p.n_filters)])
+                vals.append(_loss(system_for(p, lags=lg), d, target)[0])
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert gp[k, j] == pytest.approx(fd, rel=2e-4, abs=1e-9 * np.abs(gp).max())
+    # scaling every sigma together scales N^-1 uniformly: the map does not move
+    s_dot = float(np.sum(base[:, 0] * gp[:, 0]))
+    assert abs(s_dot) <= 1e-8 * float(np.sum(np.abs(base[:, 0] * gp[:, 0])))
