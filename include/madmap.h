@@ -246,6 +246,24 @@ madmap_status madmap_time_operator(madmap_plan_t plan, int32_t precision, int32_
 madmap_status madmap_solve_batched(madmap_plan_t plan, int32_t n_rhs, const float* d, double* m,
                                    const madmap_solve_opts* opts, madmap_solve_info* info, void* stream);
 
+/* Gradients of a loss L(m) through the solve, by the implicit adjoint (the
+ * paper does not differentiate the solve; with lambda = H^-1 dL/dm, one more
+ * solve with the self-adjoint H, perturbing N^-1 and d in m = H^-1 A^T N^-1 d
+ * gives):
+ *   grad_d         = dL/dd = N^-1 A lambda                  (float32 operator)
+ *   grad_lags[k,t] = dL/df_k(t) = sum over intervals of filter k of
+ *                    sum_{|t1 - t2| = t} (A lambda)_t1 (d - A m)_t2
+ * (both orders of each pair for t > 0; direct sums, float32 products with
+ * float64 totals).  d: device float [n_samples]; m and grad_m: device double
+ * [n_obs][n_stokes] (m the solution for d; grad_m is ignored at excised
+ * pixels); grad_d: device float [n_samples] or NULL; grad_lags: device
+ * double [n_filters][n_lags] or NULL.  opts/info as in madmap_solve, for the
+ * adjoint solve.  Gradients with respect to PSD parameters follow by the
+ * chain rule through madmap_noise_filter's dlags_out.  Synchronises `stream`. */
+madmap_status madmap_solve_backward(madmap_plan_t plan, const float* d, const double* m, const double* grad_m,
+                                    float* grad_d, double* grad_lags, const madmap_solve_opts* opts,
+                                    madmap_solve_info* info, void* stream);
+
 /* ------------------------------------------------------------------ host helpers */
 
 /* Inverse-noise filter lags from the PSD p(f) = sigma^2 (1 + (fknee/f)^alpha)
@@ -257,6 +275,12 @@ madmap_status madmap_solve_batched(madmap_plan_t plan, int32_t n_rhs, const floa
  * (d/dsigma, d/dfknee, d/dalpha) or NULL.  Host only, synchronous. */
 madmap_status madmap_noise_filter(int32_t n_lags, double fs, double sigma, double fknee, double alpha,
                                   double* lags_out, double* dlags_out);
+
+/* Chain rule through madmap_noise_filter: given grad_lags = dL/df (host
+ * [n_lags]) for the filter built from (sigma, fknee, alpha), writes
+ * grad_params_out (host [3]) = dL/d(sigma, fknee, alpha).  Host only. */
+madmap_status madmap_noise_filter_vjp(int32_t n_lags, double fs, double sigma, double fknee, double alpha,
+                                      const double* grad_lags, double* grad_params_out);
 
 /* FFT length of Section 5.2: the smallest power of two above the longest
  * interval, halved while h'(n_f) (Eq. 24) stays positive and n_f/2 > 2 n_c. */

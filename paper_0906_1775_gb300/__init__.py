@@ -21,7 +21,7 @@ from ._lib import (MADMAP_FP32, MADMAP_FP64, MADMAP_MIXED, MadmapError, check, l
 __all__ = ["Plan", "noise_filter", "paper_fft_length", "MadmapError", "load", "library_path",
            "madmap_plan_create", "madmap_plan_destroy", "madmap_plan_get_stats", "madmap_plan_observed",
            "madmap_plan_set_filters", "madmap_apply_ATNA", "madmap_rhs", "madmap_apply_ninv", "madmap_solve",
-           "madmap_solve_batched",
+           "madmap_solve_batched", "madmap_solve_backward", "madmap_noise_filter_vjp", "MadmapSolve",
            "madmap_noise_filter", "madmap_paper_fft_length", "madmap_last_error", "madmap_kernel_launch_count",
            "madmap_time_operator", "madmap_apply_ninv_noalloc"]
 
@@ -113,6 +113,22 @@ def madmap_solve_batched(h, n_rhs, d_ptr, m_ptr, opts, stream=None):
     st = load().madmap_solve_batched(h, int(n_rhs), d_ptr, m_ptr, C.byref(opts), infos, C.c_void_p(_stream_ptr(stream)))
     check(st, "madmap_solve_batched", allow_warn=True)
     return infos
+
+
+def madmap_solve_backward(h, d_ptr, m_ptr, gm_ptr, gd_ptr, gl_ptr, opts, stream=None):
+    info = _lib.madmap_solve_info()
+    st = load().madmap_solve_backward(h, d_ptr, m_ptr, gm_ptr, gd_ptr, gl_ptr, C.byref(opts), C.byref(info),
+                                      C.c_void_p(_stream_ptr(stream)))
+    check(st, "madmap_solve_backward", allow_warn=True)
+    return info
+
+
+def madmap_noise_filter_vjp(n_lags, fs, sigma, fknee, alpha, grad_lags):
+    g = np.ascontiguousarray(grad_lags, dtype=np.float64)
+    out = np.zeros(3)
+    check(load().madmap_noise_filter_vjp(int(n_lags), fs, sigma, fknee, alpha, g.ctypes.data, out.ctypes.data),
+          "madmap_noise_filter_vjp")
+    return out
 
 
 def madmap_noise_filter(n_lags, fs, sigma, fknee, alpha, with_grad=False):
@@ -274,6 +290,22 @@ class Plan:
                                      _dev_ptr(m, torch.float64, "m") if m.numel() else None, o, stream)
         return m, [{k: getattr(i, k) for k, _ in i._fields_} for i in infos]
 
+    def solve_backward(self, d, m, grad_m, want_d=True, want_lags=True, precision="mixed", max_iter=500,
+                       rel_tol=1e-10, max_outer=20, inner_rel_tol=1e-4, use_graph=True, iters_per_sync=8,
+                       stream=None):
+        """(dL/dd float32 [n_samples] or None, dL/dlags float64 [n_filters, n_lags] or None, info) for the
+        map m of data d and grad_m = dL/dm, by one adjoint solve."""
+        torch = _torch()
+        o = self._opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync)
+        gd = torch.empty(self.n_samples, dtype=torch.float32, device="cuda") if want_d else None
+        gl = (torch.empty((self.stats["n_filters"], self.stats["n_lags"]), dtype=torch.float64, device="cuda")
+              if want_lags else None)
+        info = madmap_solve_backward(self._h, _dev_ptr(d.reshape(-1), torch.float32, "d"),
+                                     _dev_ptr(m, torch.float64, "m"), _dev_ptr(grad_m, torch.float64, "grad_m"),
+                                     gd.data_ptr() if gd is not None else None,
+                                     gl.data_ptr() if gl is not None else None, o, stream)
+        return gd, gl, {k: getattr(info, k) for k, _ in info._fields_}
+
     def solve(self, d, precision="fp64", max_iter=50, rel_tol=1e-6, max_outer=10, inner_rel_tol=1e-4,
               use_graph=True, iters_per_sync=8, out=None, stream=None):
         """Maximum-likelihood map [n_obs, n_stokes] (float64) and the solve info dict."""
@@ -284,3 +316,60 @@ class Plan:
         info = madmap_solve(self._h, _dev_ptr(d.reshape(-1), torch.float32, "d"), _dev_ptr(m, torch.float64, "m"),
                             o, stream)
         return m, {k: getattr(info, k) for k, _ in info._fields_}
+
+
+# ----------------------------------------------------------------- differentiable solve
+def _autograd_function():
+    torch = _torch()
+
+    class MadmapSolve(torch.autograd.Function):
+        """m = MadmapSolve.apply(d, params, plan, fs, solve_kwargs)
+
+        d: float32 CUDA tensor [n_samples]; params: float64 tensor [n_filters, 3]
+        of (sigma, f_knee, alpha) per filter; plan: a Plan whose filters are
+        rebuilt from params (madmap_noise_filter) before the solve.  The
+        backward pass runs madmap_solve_backward (one adjoint solve) and the
+        chain rule madmap_noise_filter_vjp; it returns gradients for d and params.
+        """
+
+        @staticmethod
+        def forward(ctx, d, params, plan, fs, solve_kwargs):
+            prm = params.detach().cpu().numpy().astype(np.float64)
+            n_lags = plan.stats["n_lags"]
+            lags = np.stack([madmap_noise_filter(n_lags, fs, *prm[k]) for k in range(prm.shape[0])])
+            plan.set_filters(lags)
+            kw = dict(solve_kwargs or {})
+            m, info = plan.solve(d.detach().contiguous(), **kw)
+            ctx.save_for_backward(d, m, params)
+            ctx.plan, ctx.fs, ctx.kw = plan, fs, kw
+            ctx.info = info
+            return m
+
+        @staticmethod
+        def backward(ctx, grad_m):
+            d, m, params = ctx.saved_tensors
+            plan = ctx.plan
+            bkw = {k: v for k, v in ctx.kw.items() if k in ("precision", "max_iter", "rel_tol", "max_outer",
+                                                            "inner_rel_tol", "use_graph", "iters_per_sync")}
+            gd, gl, _ = plan.solve_backward(d.detach().contiguous(), m.detach().contiguous(),
+                                            grad_m.detach().contiguous().to(torch.float64),
+                                            want_d=ctx.needs_input_grad[0], want_lags=ctx.needs_input_grad[1],
+                                            **bkw)
+            gp = None
+            if ctx.needs_input_grad[1]:
+                prm = params.detach().cpu().numpy().astype(np.float64)
+                glh = gl.cpu().numpy()
+                n_lags = plan.stats["n_lags"]
+                out = np.stack([madmap_noise_filter_vjp(n_lags, ctx.fs, *prm[k], glh[k]) for k in range(prm.shape[0])])
+                gp = torch.from_numpy(out).to(dtype=params.dtype, device=params.device)
+            return (gd.view_as(d) if gd is not None else None), gp, None, None, None
+
+    return MadmapSolve
+
+
+def __getattr__(name):
+    if name == "MadmapSolve":
+        fn = _autograd_function()
+        globals()["MadmapSolve"] = fn
+        return fn
+    raise AttributeError(name)

@@ -72,6 +72,10 @@ PROTOTYPES = [
                                C.POINTER(madmap_solve_info), C.c_void_p]),
     ("madmap_solve_batched", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(madmap_solve_opts),
                                        C.c_void_p, C.c_void_p]),
+    ("madmap_solve_backward", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.POINTER(madmap_solve_opts), C.POINTER(madmap_solve_info), C.c_void_p]),
+    ("madmap_noise_filter_vjp", C.c_int, [C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p,
+                                          C.c_void_p]),
     ("madmap_noise_filter", C.c_int, [C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p,
                                       C.c_void_p]),
     ("madmap_paper_fft_length", C.c_int64, [C.c_int64, C.c_int64]),

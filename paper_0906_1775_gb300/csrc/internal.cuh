@@ -96,6 +96,11 @@ struct Plan {
   cudaStream_t solve_stream = nullptr;
   cudaEvent_t solve_event = nullptr;
   std::vector<TileSet*> tile_sets;  // batched tile lists by n_rhs (device memory in allocs)
+  // backward pass: timestreams A lambda and d - A m, lag-correlation work items
+  float* bw_a = nullptr;
+  float* bw_r = nullptr;
+  void* corr_items = nullptr;
+  int n_corr_items = 0;
   ~Plan();
 };
 

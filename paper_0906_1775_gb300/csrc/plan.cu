@@ -151,6 +151,20 @@ extern "C" madmap_status madmap_noise_filter(int32_t n_lags, double fs, double s
   return MADMAP_OK;
 }
 
+extern "C" madmap_status madmap_noise_filter_vjp(int32_t n_lags, double fs, double sigma, double fknee, double alpha,
+                                                 const double* grad_lags, double* grad_params_out) {
+  MM_CHECK(n_lags >= 1 && grad_lags && grad_params_out, MADMAP_ERR_INVALID_ARG, "noise_filter_vjp: bad arguments");
+  std::vector<double> lags(n_lags), dl(3 * (size_t)n_lags);
+  madmap_status st = madmap_noise_filter(n_lags, fs, sigma, fknee, alpha, lags.data(), dl.data());
+  if (st != MADMAP_OK) return st;
+  for (int k = 0; k < 3; ++k) {
+    double acc = 0.0;
+    for (int t = 0; t < n_lags; ++t) acc += dl[(size_t)k * n_lags + t] * grad_lags[t];
+    grad_params_out[k] = acc;
+  }
+  return MADMAP_OK;
+}
+
 static double hprime(double nf, double nc) {
   return (1.0 + log(nf)) / (nf - 2 * nc) - nf * log(nf) / ((nf - 2 * nc) * (nf - 2 * nc));
 }

@@ -609,6 +609,126 @@ static madmap_status run_pcg(Plan* p, SolveBuffers* sb, const Batch& B, const Bt
   return MADMAP_OK;
 }
 
+// PCG (FP64) or refined mixed-precision PCG (MIXED) on H x = b for every
+// right-hand side of the batch, b already in sb64->b64.  On return *x_pad
+// points at the best iterates (padded layout, nvec apart) and I holds the
+// per-rhs summaries (fp64_applies counts the right-hand side's own as 1).
+template <int NS>
+static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, const madmap_solve_opts& o,
+                                std::vector<madmap_solve_info>& I, cudaStream_t s, const double** x_pad) {
+  const int n_rhs = B.n_rhs;
+  const long long nv = sb64->nvec;
+  const dim3 gv(grid_vec(nv), n_rhs);
+  const bool graph = o.use_graph != 0;
+  madmap_status st = MADMAP_OK;
+  std::vector<PcgResult> R;
+  if (o.precision == MADMAP_FP64) {
+    st = run_pcg<double, NS, double>(p, sb64, B, sb64->b64, nullptr, o.rel_tol, o.max_iter, o.iters_per_sync, graph, s,
+                                     R);
+    if (st != MADMAP_OK) return st;
+    for (int k = 0; k < n_rhs; ++k) {
+      I[k].iters = R[k].iters;
+      I[k].outer_iters = 1;
+      I[k].best_iter = R[k].best_iter;
+      I[k].fp64_applies += R[k].iters;
+      I[k].final_rel_res = R[k].final_res;
+      I[k].best_rel_res = R[k].best_res;
+      I[k].status = R[k].status != 0 ? R[k].status : (R[k].best_res <= o.rel_tol ? MADMAP_OK : MADMAP_WARN_MAXITER);
+    }
+    *x_pad = (const double*)sb64->xb;
+    return MADMAP_OK;
+  }
+  SolveBuffers* sb32 = nullptr;
+  st = get_buffers(p, false, n_rhs, &sb32);
+  if (st != MADMAP_OK) return st;
+  // r64 = b64 and ||b|| per right-hand side
+  MM_CUDA(cudaMemsetAsync(sb64->t64, 0, sizeof(double) * nv * n_rhs, s));
+  count_launches(1);
+  k_residual<<<gv, NT, 0, s>>>(sb64->b64, sb64->t64, sb64->r64, nv, sb64->st, sb64->partials, nullptr);
+  std::vector<CgState> h(n_rhs);
+  MM_CUDA(cudaMemcpyAsync(h.data(), sb64->st, sizeof(CgState) * n_rhs, cudaMemcpyDeviceToHost, s));
+  MM_CUDA(cudaStreamSynchronize(s));
+  std::vector<double> bnorm(n_rhs), best(n_rhs), res(n_rhs);
+  std::vector<int> total(n_rhs, 0), best_iter(n_rhs, 0), inner_status(n_rhs, 0), inactive(n_rhs), take(n_rhs);
+  int n_active = 0;
+  for (int k = 0; k < n_rhs; ++k) {
+    bnorm[k] = h[k].res;
+    best[k] = res[k] = bnorm[k] > 0 ? 1.0 : 0.0;
+    inactive[k] = !(bnorm[k] > 0 && res[k] > o.rel_tol && o.max_iter > 0);
+    n_active += !inactive[k];
+  }
+  MM_CUDA(cudaMemsetAsync(sb64->x64, 0, sizeof(double) * nv * n_rhs, s));
+  MM_CUDA(cudaMemsetAsync(sb64->xbest64, 0, sizeof(double) * nv * n_rhs, s));
+  int outer = 0;
+  while (n_active > 0 && outer < o.max_outer) {
+    int budget = 0;
+    for (int k = 0; k < n_rhs; ++k)
+      if (!inactive[k]) budget = std::max(budget, o.max_iter - total[k]);
+    MM_CUDA(cudaMemcpyAsync(sb64->flags, inactive.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, s));
+    st = run_pcg<float, NS, double>(p, sb32, B, sb64->r64, sb64->flags, o.inner_rel_tol, budget, o.iters_per_sync,
+                                    graph, s, R);
+    if (st != MADMAP_OK) return st;
+    ++outer;
+    count_launches(2);
+    k_refine_add<<<gv, NT, 0, s>>>(sb64->x64, (const float*)sb32->xb, sb64->t64, nv, sb64->flags);
+    if (B.ts)
+      st = op_launch_set(p, true, IN_MAP, OUT_MAP, sb64->x64, sb64->t64, nv, nv, sb64->flags, 1, B.ts, s);
+    else
+      st = op_launch(p, true, IN_MAP, OUT_MAP, sb64->x64, sb64->t64, 0, 0, 1, nullptr, s);
+    if (st != MADMAP_OK) return st;
+    k_residual<<<gv, NT, 0, s>>>(sb64->b64, sb64->t64, sb64->r64, nv, sb64->st, sb64->partials, sb64->flags);
+    MM_CUDA(cudaMemcpyAsync(h.data(), sb64->st, sizeof(CgState) * n_rhs, cudaMemcpyDeviceToHost, s));
+    MM_CUDA(cudaStreamSynchronize(s));
+    bool any_take = false;
+    for (int k = 0; k < n_rhs; ++k) {
+      take[k] = 0;
+      if (inactive[k]) continue;
+      total[k] += R[k].iters;
+      I[k].fp32_applies += R[k].iters;
+      ++I[k].fp64_applies;
+      ++I[k].outer_iters;
+      if (R[k].status != 0) inner_status[k] = R[k].status;
+      res[k] = h[k].res / bnorm[k];
+      if (res[k] < best[k]) {
+        best[k] = res[k];
+        best_iter[k] = total[k];
+        take[k] = 1;
+        any_take = true;
+      }
+      if (res[k] <= o.rel_tol || total[k] >= o.max_iter || R[k].iters == 0) {
+        inactive[k] = 1;
+        --n_active;
+      }
+    }
+    if (any_take) {
+      // the flags buffer is reused for `take`; the next round rewrites it
+      MM_CUDA(cudaMemcpyAsync(sb64->flags, take.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, s));
+      count_launches(1);
+      k_take_best<<<gv, NT, 0, s>>>(sb64->x64, sb64->xbest64, nv, sb64->flags);
+      MM_CUDA(cudaStreamSynchronize(s));
+    }
+  }
+  for (int k = 0; k < n_rhs; ++k) {
+    I[k].iters = total[k];
+    I[k].best_iter = best_iter[k];
+    I[k].final_rel_res = res[k];
+    I[k].best_rel_res = best[k];
+    I[k].status = best[k] <= o.rel_tol ? MADMAP_OK : (inner_status[k] != 0 ? inner_status[k] : MADMAP_WARN_MAXITER);
+  }
+  *x_pad = sb64->xbest64;
+  return MADMAP_OK;
+}
+
+static int worst_status(std::vector<madmap_solve_info>& I, double t_all) {
+  int worst = MADMAP_OK;
+  for (auto& x : I) {
+    x.t_solve_ms = t_all;
+    if (x.status < 0) worst = x.status;
+    else if (worst == MADMAP_OK && x.status != MADMAP_OK) worst = x.status;
+  }
+  return worst;
+}
+
 template <int NS>
 static madmap_status solve_impl(Plan* p, int n_rhs, const float* d, double* m, const madmap_solve_opts& o,
                                 madmap_solve_info* info, cudaStream_t s) {
@@ -626,7 +746,6 @@ static madmap_status solve_impl(Plan* p, int n_rhs, const float* d, double* m, c
   if (st != MADMAP_OK) return st;
   const long long nv = sb64->nvec;
   const int n = p->n_obs;
-  const dim3 gv(grid_vec(nv), n_rhs);
   std::vector<madmap_solve_info> I(n_rhs);
   for (auto& x : I) memset(&x, 0, sizeof(x));
   // right-hand sides b = A^T N^-1 d in float64
@@ -643,116 +762,169 @@ static madmap_status solve_impl(Plan* p, int n_rhs, const float* d, double* m, c
     x.fp64_applies = 1;
     x.t_rhs_ms = t_rhs;
   }
-  const bool graph = o.use_graph != 0;
-  std::vector<PcgResult> R;
-  if (o.precision == MADMAP_FP64) {
-    st = run_pcg<double, NS, double>(p, sb64, B, sb64->b64, nullptr, o.rel_tol, o.max_iter, o.iters_per_sync, graph, s,
-                                     R);
-    if (st != MADMAP_OK) return st;
-    for (int k = 0; k < n_rhs; ++k) {
-      count_launches(1);
-      k_unpack<double, double><<<grid_vec((long long)n * p->n_stokes), NT, 0, s>>>(
-          (const double*)sb64->xb + k * nv, m + (long long)k * n * p->n_stokes, n, p->n_stokes, p->ns_pad);
-      I[k].iters = R[k].iters;
-      I[k].outer_iters = 1;
-      I[k].best_iter = R[k].best_iter;
-      I[k].fp64_applies += R[k].iters;
-      I[k].final_rel_res = R[k].final_res;
-      I[k].best_rel_res = R[k].best_res;
-      I[k].status = R[k].status != 0 ? R[k].status : (R[k].best_res <= o.rel_tol ? MADMAP_OK : MADMAP_WARN_MAXITER);
-    }
-  } else {
-    SolveBuffers* sb32 = nullptr;
-    st = get_buffers(p, false, n_rhs, &sb32);
-    if (st != MADMAP_OK) return st;
-    // r64 = b64 and ||b|| per right-hand side
-    MM_CUDA(cudaMemsetAsync(sb64->t64, 0, sizeof(double) * nv * n_rhs, s));
+  const double* xr = nullptr;
+  st = solve_core<NS>(p, B, sb64, o, I, s, &xr);
+  if (st != MADMAP_OK) return st;
+  for (int k = 0; k < n_rhs; ++k) {
     count_launches(1);
-    k_residual<<<gv, NT, 0, s>>>(sb64->b64, sb64->t64, sb64->r64, nv, sb64->st, sb64->partials, nullptr);
-    std::vector<CgState> h(n_rhs);
-    MM_CUDA(cudaMemcpyAsync(h.data(), sb64->st, sizeof(CgState) * n_rhs, cudaMemcpyDeviceToHost, s));
-    MM_CUDA(cudaStreamSynchronize(s));
-    std::vector<double> bnorm(n_rhs), best(n_rhs), res(n_rhs);
-    std::vector<int> total(n_rhs, 0), best_iter(n_rhs, 0), inner_status(n_rhs, 0), inactive(n_rhs), take(n_rhs);
-    int n_active = 0;
-    for (int k = 0; k < n_rhs; ++k) {
-      bnorm[k] = h[k].res;
-      best[k] = res[k] = bnorm[k] > 0 ? 1.0 : 0.0;
-      inactive[k] = !(bnorm[k] > 0 && res[k] > o.rel_tol && o.max_iter > 0);
-      n_active += !inactive[k];
-    }
-    MM_CUDA(cudaMemsetAsync(sb64->x64, 0, sizeof(double) * nv * n_rhs, s));
-    MM_CUDA(cudaMemsetAsync(sb64->xbest64, 0, sizeof(double) * nv * n_rhs, s));
-    int outer = 0;
-    while (n_active > 0 && outer < o.max_outer) {
-      int budget = 0;
-      for (int k = 0; k < n_rhs; ++k)
-        if (!inactive[k]) budget = std::max(budget, o.max_iter - total[k]);
-      MM_CUDA(cudaMemcpyAsync(sb64->flags, inactive.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, s));
-      st = run_pcg<float, NS, double>(p, sb32, B, sb64->r64, sb64->flags, o.inner_rel_tol, budget, o.iters_per_sync,
-                                      graph, s, R);
-      if (st != MADMAP_OK) return st;
-      ++outer;
-      count_launches(2);
-      k_refine_add<<<gv, NT, 0, s>>>(sb64->x64, (const float*)sb32->xb, sb64->t64, nv, sb64->flags);
-      if (B.ts)
-        st = op_launch_set(p, true, IN_MAP, OUT_MAP, sb64->x64, sb64->t64, nv, nv, sb64->flags, 1, B.ts, s);
-      else
-        st = op_launch(p, true, IN_MAP, OUT_MAP, sb64->x64, sb64->t64, 0, 0, 1, nullptr, s);
-      if (st != MADMAP_OK) return st;
-      k_residual<<<gv, NT, 0, s>>>(sb64->b64, sb64->t64, sb64->r64, nv, sb64->st, sb64->partials, sb64->flags);
-      MM_CUDA(cudaMemcpyAsync(h.data(), sb64->st, sizeof(CgState) * n_rhs, cudaMemcpyDeviceToHost, s));
-      MM_CUDA(cudaStreamSynchronize(s));
-      bool any_take = false;
-      for (int k = 0; k < n_rhs; ++k) {
-        take[k] = 0;
-        if (inactive[k]) continue;
-        total[k] += R[k].iters;
-        I[k].fp32_applies += R[k].iters;
-        ++I[k].fp64_applies;
-        ++I[k].outer_iters;
-        if (R[k].status != 0) inner_status[k] = R[k].status;
-        res[k] = h[k].res / bnorm[k];
-        if (res[k] < best[k]) {
-          best[k] = res[k];
-          best_iter[k] = total[k];
-          take[k] = 1;
-          any_take = true;
-        }
-        if (res[k] <= o.rel_tol || total[k] >= o.max_iter || R[k].iters == 0) {
-          inactive[k] = 1;
-          --n_active;
-        }
-      }
-      if (any_take) {
-        // the flags buffer is reused for `take`; the next round rewrites it
-        MM_CUDA(cudaMemcpyAsync(sb64->flags, take.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, s));
-        count_launches(1);
-        k_take_best<<<gv, NT, 0, s>>>(sb64->x64, sb64->xbest64, nv, sb64->flags);
-        MM_CUDA(cudaStreamSynchronize(s));
+    k_unpack<double, double><<<grid_vec((long long)n * p->n_stokes), NT, 0, s>>>(
+        xr + k * nv, m + (long long)k * n * p->n_stokes, n, p->n_stokes, p->ns_pad);
+  }
+  MM_CUDA(cudaStreamSynchronize(s));
+  MM_CUDA(cudaGetLastError());
+  const double t_all = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  const int worst = worst_status(I, t_all);
+  if (info) memcpy(info, I.data(), sizeof(madmap_solve_info) * n_rhs);
+  return (madmap_status)worst;
+}
+
+// ---------------------------------------------------------------- backward
+// Gradients of a loss L(m) through the solve by the implicit adjoint: with
+// lambda = H^-1 dL/dm (one more solve with the self-adjoint H),
+//   dL/dd = N^-1 A lambda,
+//   dL/df_k(tau) = sum over intervals of filter k of sum_{|t-t'| = tau}
+//                  (A lambda)_t (d - A m)_t'   (both orders for tau > 0),
+// from perturbing N^-1 and d in m = H^-1 A^T N^-1 d.
+
+// out_t = alpha d_t + beta (A x)_t (float64 weights and map, float output)
+template <int NS>
+__global__ void k_unpoint(const double* x, const int* pix, const double2* cs, const float* d, double alpha,
+                          double beta, float* out, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int q = pix[t];
+    double ax = 0.0;
+    if (q >= 0) {
+      if (NS == 1) {
+        ax = x[q];
+      } else {
+        const double2 w = cs[t];
+        ax = x[4LL * q] + x[4LL * q + 1] * w.x + x[4LL * q + 2] * w.y;
       }
     }
-    for (int k = 0; k < n_rhs; ++k) {
+    out[t] = (float)((d ? alpha * (double)d[t] : 0.0) + beta * ax);
+  }
+}
+
+// zero the adjoint right-hand side at excised pixels (no row of H there)
+__global__ void k_mask_excised(double* b, long long nvec_pixels, int ns_pad, const unsigned char* excised) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvec_pixels * ns_pad;
+       i += (long long)gridDim.x * blockDim.x)
+    if (excised[i / ns_pad]) b[i] = 0.0;
+}
+
+// Lag correlation sum_{|t-t'|=tau} a_t r_t' by direct sums: CTA (tau chunk,
+// work item) covers lags [tau0, tau0 + LT) over the samples [t_lo, t_hi) of
+// one interval, in tiles of TT samples staged in shared memory; each thread
+// owns one lag, sums a tile in float32 and folds it into a float64 total,
+// then adds the total to grad[filter][tau] (float64 atomics, one per lag and
+// work item).
+struct CorrItem {
+  long long lo, hi;      // interval bounds
+  long long t_lo, t_hi;  // samples of this item
+  int filter, pad;
+};
+
+constexpr int CORR_LT = 256;
+constexpr int CORR_TT = 1024;
+
+__global__ void __launch_bounds__(CORR_LT) k_lag_corr(const float* a, const float* r, const CorrItem* items,
+                                                      int n_lags, double* grad) {
+  __shared__ float sa[CORR_TT];
+  __shared__ float sp[CORR_TT + CORR_LT];  // r[t + tau0 + j]
+  __shared__ float sm[CORR_TT + CORR_LT];  // r[t - tau0 - (LT - 1) + j]
+  const CorrItem it = items[blockIdx.y];
+  const int tau0 = blockIdx.x * CORR_LT;
+  const int j = threadIdx.x;
+  const int tau = tau0 + j;
+  double total = 0.0;
+  for (long long t0 = it.t_lo; t0 < it.t_hi; t0 += CORR_TT) {
+    const int nt = (int)min((long long)CORR_TT, it.t_hi - t0);
+    __syncthreads();
+    for (int k = j; k < CORR_TT; k += CORR_LT) sa[k] = k < nt ? a[t0 + k] : 0.f;
+    for (int k = j; k < CORR_TT + CORR_LT; k += CORR_LT) {
+      const long long tp = t0 + tau0 + k;
+      const long long tm = t0 - tau0 - (CORR_LT - 1) + k;
+      sp[k] = (tp >= it.lo && tp < it.hi) ? r[tp] : 0.f;
+      sm[k] = (tm >= it.lo && tm < it.hi) ? r[tm] : 0.f;
+    }
+    __syncthreads();
+    float acc = 0.f;
+    if (tau == 0) {
+      for (int k = 0; k < nt; ++k) acc = fmaf(sa[k], sp[k + j], acc);
+    } else {
+      for (int k = 0; k < nt; ++k) acc = fmaf(sa[k], sp[k + j] + sm[k + (CORR_LT - 1) - j], acc);
+    }
+    total += (double)acc;
+  }
+  if (tau < n_lags) atomicAdd(grad + (long long)it.filter * n_lags + tau, total);
+}
+
+template <int NS>
+static madmap_status backward_impl(Plan* p, const float* d, const double* m, const double* gm, float* grad_d,
+                                   double* grad_lags, const madmap_solve_opts& o, madmap_solve_info* info,
+                                   cudaStream_t s) {
+  auto t_start = std::chrono::steady_clock::now();
+  Batch B;
+  SolveBuffers* sb64 = nullptr;
+  madmap_status st = get_buffers(p, true, 1, &sb64);
+  if (st != MADMAP_OK) return st;
+  const long long nv = sb64->nvec;
+  const int n = p->n_obs, ns = p->n_stokes, np = p->ns_pad;
+  const long long nt = p->n_t;
+  if (!p->bw_a) {
+    st = dalloc_t(p, &p->bw_a, std::max(1LL, nt));
+    if (st == MADMAP_OK) st = dalloc_t(p, &p->bw_r, std::max(1LL, nt));
+    if (st != MADMAP_OK) return st;
+  }
+  // adjoint solve H lambda = dL/dm (zero at excised pixels)
+  count_launches(2);
+  k_pack<double, double><<<grid_vec(nv), NT, 0, s>>>(gm, sb64->b64, n, ns, np);
+  k_mask_excised<<<grid_vec(nv), NT, 0, s>>>(sb64->b64, n, np, p->excised);
+  std::vector<madmap_solve_info> I(1);
+  memset(&I[0], 0, sizeof(I[0]));
+  const double* lam = nullptr;
+  st = solve_core<NS>(p, B, sb64, o, I, s, &lam);
+  if (st != MADMAP_OK) return st;
+  // a = A lambda; r = d - A m  (m packed into the spare float64 vector t64)
+  const int gt = (int)std::min<long long>((nt + 255) / 256, 152LL * 32);
+  count_launches(3);
+  k_unpoint<NS><<<std::max(1, gt), 256, 0, s>>>(lam, p->pix_obs, p->cs64, nullptr, 0.0, 1.0, p->bw_a, nt);
+  k_pack<double, double><<<grid_vec(nv), NT, 0, s>>>(m, sb64->t64, n, ns, np);
+  k_unpoint<NS><<<std::max(1, gt), 256, 0, s>>>(sb64->t64, p->pix_obs, p->cs64, d, 1.0, -1.0, p->bw_r, nt);
+  if (grad_d) {
+    st = op_launch(p, false, IN_TOD_REAL, OUT_TOD, p->bw_a, grad_d, 0, 0, 1, nullptr, s);
+    if (st != MADMAP_OK) return st;
+  }
+  if (grad_lags) {
+    if (!p->corr_items) {
+      std::vector<CorrItem> items;
+      const long long chunk = 65536;
+      for (int i = 0; i < p->n_ivl; ++i)
+        for (long long t = p->offsets[i]; t < p->offsets[i + 1]; t += chunk)
+          items.push_back({p->offsets[i], p->offsets[i + 1], t, std::min(p->offsets[i + 1], t + chunk),
+                           p->ivl_filter[i], 0});
+      p->n_corr_items = (int)items.size();
+      CorrItem* dev = nullptr;
+      st = dalloc(p, (void**)&dev, sizeof(CorrItem) * std::max<size_t>(1, items.size()));
+      if (st != MADMAP_OK) return st;
+      if (!items.empty())
+        MM_CUDA(cudaMemcpy(dev, items.data(), sizeof(CorrItem) * items.size(), cudaMemcpyHostToDevice));
+      p->corr_items = dev;
+    }
+    MM_CUDA(cudaMemsetAsync(grad_lags, 0, sizeof(double) * p->n_filters * p->n_lags, s));
+    const CorrItem* items = static_cast<const CorrItem*>(p->corr_items);
+    for (int y0 = 0; y0 < p->n_corr_items; y0 += 65535) {
+      const int ny = std::min(65535, p->n_corr_items - y0);
       count_launches(1);
-      k_unpack<double, double><<<grid_vec((long long)n * p->n_stokes), NT, 0, s>>>(
-          sb64->xbest64 + k * nv, m + (long long)k * n * p->n_stokes, n, p->n_stokes, p->ns_pad);
-      I[k].iters = total[k];
-      I[k].best_iter = best_iter[k];
-      I[k].final_rel_res = res[k];
-      I[k].best_rel_res = best[k];
-      I[k].status = best[k] <= o.rel_tol ? MADMAP_OK : (inner_status[k] != 0 ? inner_status[k] : MADMAP_WARN_MAXITER);
+      k_lag_corr<<<dim3((p->n_lags + CORR_LT - 1) / CORR_LT, ny), CORR_LT, 0, s>>>(p->bw_a, p->bw_r, items + y0,
+                                                                                  p->n_lags, grad_lags);
     }
   }
   MM_CUDA(cudaStreamSynchronize(s));
   MM_CUDA(cudaGetLastError());
   const double t_all = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-  int worst = MADMAP_OK;
-  for (auto& x : I) {
-    x.t_solve_ms = t_all;
-    if (x.status < 0) worst = x.status;
-    else if (worst == MADMAP_OK && x.status != MADMAP_OK) worst = x.status;
-  }
-  if (info) memcpy(info, I.data(), sizeof(madmap_solve_info) * n_rhs);
+  const int worst = worst_status(I, t_all);
+  if (info) *info = I[0];
   return (madmap_status)worst;
 }
 
@@ -893,6 +1065,42 @@ extern "C" madmap_status madmap_solve(madmap_plan_t plan, const float* d, double
   MM_CUDA(cudaEventRecord(p->solve_event, caller));
   MM_CUDA(cudaStreamWaitEvent(s, p->solve_event, 0));
   madmap_status st = p->n_stokes == 1 ? solve_impl<1>(p, 1, d, m, o, info, s) : solve_impl<3>(p, 1, d, m, o, info, s);
+  cudaStreamSynchronize(s);
+  return st;
+}
+
+extern "C" madmap_status madmap_solve_backward(madmap_plan_t plan, const float* d, const double* m,
+                                               const double* grad_m, float* grad_d, double* grad_lags,
+                                               const madmap_solve_opts* opts, madmap_solve_info* info, void* stream) {
+  MM_CHECK(plan, MADMAP_ERR_INVALID_ARG, "solve_backward: NULL plan");
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  MM_CHECK((m && grad_m) || p->n_obs == 0, MADMAP_ERR_INVALID_ARG, "solve_backward: NULL map or map gradient");
+  MM_CHECK(d || p->n_t == 0, MADMAP_ERR_INVALID_ARG, "solve_backward: d is NULL");
+  madmap_solve_opts o;
+  madmap_solve_opts_default(&o);
+  if (opts) o = *opts;
+  MM_CHECK(o.precision == MADMAP_FP64 || o.precision == MADMAP_MIXED, MADMAP_ERR_INVALID_ARG,
+           "solve_backward: precision must be FP64 or MIXED");
+  MM_CHECK(o.max_iter >= 0 && o.rel_tol >= 0 && o.iters_per_sync >= 1 && o.max_outer >= 1 &&
+               o.inner_rel_tol > 0 && o.inner_rel_tol < 1,
+           MADMAP_ERR_INVALID_ARG, "solve_backward: bad options");
+  cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  if (p->n_obs == 0) {
+    if (info) memset(info, 0, sizeof(*info));
+    if (grad_lags) MM_CUDA(cudaMemsetAsync(grad_lags, 0, sizeof(double) * p->n_filters * p->n_lags, caller));
+    if (grad_d && p->n_t) MM_CUDA(cudaMemsetAsync(grad_d, 0, sizeof(float) * p->n_t, caller));
+    MM_CUDA(cudaStreamSynchronize(caller));
+    return MADMAP_OK;
+  }
+  if (!p->solve_stream) {
+    MM_CUDA(cudaStreamCreateWithFlags(&p->solve_stream, cudaStreamNonBlocking));
+    MM_CUDA(cudaEventCreateWithFlags(&p->solve_event, cudaEventDisableTiming));
+  }
+  cudaStream_t s = p->solve_stream;
+  MM_CUDA(cudaEventRecord(p->solve_event, caller));
+  MM_CUDA(cudaStreamWaitEvent(s, p->solve_event, 0));
+  madmap_status st = p->n_stokes == 1 ? backward_impl<1>(p, d, m, grad_m, grad_d, grad_lags, o, info, s)
+                                      : backward_impl<3>(p, d, m, grad_m, grad_d, grad_lags, o, info, s);
   cudaStreamSynchronize(s);
   return st;
 }

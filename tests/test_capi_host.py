@@ -69,3 +69,13 @@ def test_paper_fft_length_matches_oracle(n_c, longest):
     from oracle.noise import fft_length
     mm = _lib()
     assert mm.paper_fft_length(n_c, longest) == fft_length(n_c, longest)
+
+
+def test_noise_filter_vjp_matches_oracle_chain_rule():
+    from oracle.noise import filter_lags
+    mm = _lib()
+    rng = np.random.default_rng(3)
+    for params in [(1.0, 0.1, 2.0), (0.8, 0.05, 1.3)]:
+        g = rng.standard_normal(64)
+        _, dl = filter_lags(64, 100.0, *params, with_grad=True)
+        assert np.allclose(mm.madmap_noise_filter_vjp(64, 100.0, *params, g), dl @ g, rtol=1e-11, atol=1e-14)

@@ -395,3 +395,72 @@ def test_solve_batched_reuses_and_grows_buffers():
     for r in range(3):
         assert rel_rms(host(m6[r]), host(m3[r])) < 1e-11
         assert rel_rms(host(m3b[r]), host(m3[r])) < 1e-11
+
+
+# ------------------------------------------------------------------ backward
+def _bw_problem(kind):
+    from synth import make_config
+    if kind == "cfg5":
+        return make_config(5, scale=8)
+    return tiny_IQU(seed=71, n_per_det=500, n_lags=12, n_ivl_lo=40, n_ivl_hi=300)
+
+
+@pytest.mark.parametrize("kind", ["tiny", "cfg5"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_backward_matches_oracle_adjoint(kind, prec):
+    from oracle.adjoint import solve_backward
+    p = _bw_problem(kind)
+    S = system_for(p)
+    plan = make_plan(p)
+    d = cuda(p.d[0])
+    m, _ = plan.solve(d, precision="fp64", rel_tol=1e-13, max_iter=2000)
+    target = p.target[S.obs2glob] if p.target is not None else np.random.default_rng(1).standard_normal(m.shape)
+    g = 2.0 * (host(m) - target)
+    gd, gl, info = plan.solve_backward(d, m, cuda(g), precision=prec, rel_tol=1e-12, max_iter=2000)
+    ogd, ogl, _ = solve_backward(S, p.d[0].astype(np.float64), host(m), g)
+    assert rel_rms(host(gd), ogd) < 2e-5
+    assert rel_rms(host(gl), ogl) < 2e-5
+    assert info["best_rel_res"] <= 1e-12 * 1.0001
+
+
+def test_backward_params_match_finite_differences():
+    import torch
+    import paper_0906_1775_gb300 as mm
+    p = _bw_problem("cfg5")
+    plan = make_plan(p)
+    d = cuda(p.d[0])
+    o2g, exc = plan.observed()
+    keep = torch.from_numpy(~host(exc).astype(bool)).cuda()
+    target = cuda(p.target[host(o2g)])
+    kw = dict(precision="fp64", rel_tol=1e-13, max_iter=3000)
+
+    def loss(params, dd):
+        m = mm.MadmapSolve.apply(dd, params, plan, p.fs, kw)
+        return ((m - target) ** 2)[keep].sum()
+
+    params = torch.tensor(p.noise_params, dtype=torch.float64, requires_grad=True)
+    dd = d.clone().requires_grad_(True)
+    L = loss(params, dd)
+    L.backward()
+    gp = params.grad.numpy().copy()
+    base = p.noise_params.copy()
+    rng = np.random.default_rng(0)
+    for k in rng.choice(p.n_filters, 3, replace=False):
+        for j in range(3):
+            h = 1e-4 * base[k, j]
+            vals = []
+            for sgn in (1, -1):
+                prm = base.copy()
+                prm[k, j] += sgn * h
+                with torch.no_grad():
+                    vals.append(float(loss(torch.tensor(prm), d)))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert gp[k, j] == pytest.approx(fd, rel=2e-3, abs=2e-3 * np.abs(gp).max())
+    # d-gradient: exact directional derivative for a quadratic loss
+    v = torch.randn_like(d)
+    eps = 1e-2
+    with torch.no_grad():
+        fd = (float(loss(torch.tensor(base), d + eps * v)) - float(loss(torch.tensor(base), d - eps * v))) / (2 * eps)
+    assert float((dd.grad * v).sum()) == pytest.approx(fd, rel=1e-4)
+    # a common scale of every sigma leaves the map unchanged
+    assert abs(float(np.sum(base[:, 0] * gp[:, 0]))) <= 1e-4 * float(np.sum(np.abs(base[:, 0] * gp[:, 0])))
