@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=3, help="oracle PCG iterations in the CPU baseline sample")
+    ap.add_argument("--workload", default="config2", choices=["config2", "config1", "config4", "config5"],
+                    help="config2 (default) prints the headline line; the others print secondary measurements")
     ap.add_argument("--profile-step", type=float, default=0.0, metavar="TOL",
                     help="profiling runs: skip the reference map and tolerance search and run exactly one "
                          "mixed-precision solve at this stopping tolerance")
@@ -217,12 +219,112 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- secondary workloads
+def _timed(fn, reps):
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def run_secondary(args):
+    import numpy as np
+    import torch
+
+    import paper_0906_1775_gb300 as mm
+    from synth import make_config
+    from synth.flat import device_timestreams
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    mm.load()
+    steps, warm = max(1, args.steps), max(1, args.warmup)
+    line = {"workload": args.workload, "unit": UNIT}
+    if args.workload == "config1":
+        p = make_config(1)
+        plan = mm.Plan(torch.from_numpy(p.pix).to(dev), None, p.n_pix, p.interval_offsets, p.interval_filter,
+                       lib_lags(p))
+        d = torch.from_numpy(p.d[0]).to(dev)
+        for prec in ("fp64", "mixed"):
+            fn = lambda: plan.solve(d, precision=prec, rel_tol=1e-8, max_iter=500)  # noqa: E731
+            for _ in range(warm):
+                fn()
+            ms, (m, info) = _timed(fn, steps)
+            line[prec] = {"ms_per_solve": ms, "iters": info["iters"], "rel_res": info["best_rel_res"],
+                          "value": p.n_samples * info["iters"] / (ms / 1e3)}
+        v, wall, its, cores = cpu_oracle_rate(p, 13)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"full FP64 oracle solve to 1e-8 ({its} iterations, {wall:.2f} s)"}
+        line["workload_desc"] = "T-only FP64, 1 det, 2^18 samples, 64x64, n_c=2^12, rel. residual 1e-8"
+    elif args.workload == "config4":
+        n_rhs = 64
+        p = make_config(4, n_rhs=0)
+        d = device_timestreams(p, n_rhs, seed=4000, device=dev)
+        plan = mm.Plan(torch.from_numpy(p.pix).to(dev), None, p.n_pix, p.interval_offsets, p.interval_filter,
+                       lib_lags(p))
+        kw = dict(precision="mixed", rel_tol=1e-8, max_iter=500, max_outer=10)
+        plan.solve_batched(d[:2].contiguous(), **kw)
+        ms_b, (mb, infos) = _timed(lambda: plan.solve_batched(d, **kw), 1)
+        rows = [d[r].contiguous() for r in range(n_rhs)]
+        plan.solve(rows[0], **kw)
+        torch.cuda.synchronize()
+        ms_s, its_s = 0.0, 0
+        for r in range(n_rhs):
+            t, (_, info) = _timed(lambda: plan.solve(rows[r], **kw), 1)
+            ms_s += t
+            its_s += info["iters"]
+        its_b = sum(i["iters"] for i in infos)
+        line.update({"n_rhs": n_rhs, "n_samples": p.n_samples, "fft_len": plan.stats["fft_len"],
+                     "batched": {"ms": ms_b, "iters_total": its_b, "value": p.n_samples * its_b / (ms_b / 1e3)},
+                     "sequential": {"ms": ms_s, "iters_total": its_s, "value": p.n_samples * its_s / (ms_s / 1e3)},
+                     "speedup_batched_vs_sequential": ms_s / ms_b,
+                     "workload_desc": "T, 64 RHS over one pointing, 500 intervals 2^12-2^20, n_c=2^12, mixed to 1e-8"})
+    else:
+        p = make_config(5)
+        plan = mm.Plan(torch.from_numpy(p.pix).to(dev), torch.from_numpy(p.psi).to(dev), p.n_pix,
+                       p.interval_offsets, p.interval_filter, lib_lags(p))
+        d = torch.from_numpy(p.d[0]).to(dev)
+        o2g, exc = plan.observed()
+        keep = torch.from_numpy(~exc.cpu().numpy().astype(bool)).to(dev)
+        target = torch.from_numpy(p.target[o2g.cpu().numpy()]).to(dev)
+        kw = dict(precision="mixed", rel_tol=1e-8, max_iter=500, max_outer=10)
+
+        def step():
+            params = torch.tensor(p.noise_params, dtype=torch.float64, requires_grad=True)
+            dd = d.clone().requires_grad_(True)
+            m = mm.MadmapSolve.apply(dd, params, plan, p.fs, kw)
+            loss = ((m - target) ** 2)[keep].sum()
+            loss.backward()
+            return params.grad
+
+        for _ in range(warm):
+            step()
+        ms, _ = _timed(step, steps)
+        fwd_ms, (m, info) = _timed(lambda: plan.solve(d, **kw), steps)
+        g = 2.0 * (m - target) * keep[:, None]
+        bwd_ms, (_, _, binfo) = _timed(lambda: plan.solve_backward(d, m, g.contiguous(), rel_tol=1e-8), steps)
+        line.update({"n_samples": p.n_samples, "ms_forward_backward": ms, "ms_forward": fwd_ms, "ms_backward": bwd_ms,
+                     "forward_iters": info["iters"], "adjoint_iters": binfo["iters"],
+                     "workload_desc": "IQU, 16 det x 2^22, 256x256, n_c=2^12; loss |m - t|^2; grads wrt d and "
+                                      "(sigma, f_knee, alpha) per detector"})
+    print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- our arm
 def main():
     args = parse()
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload != "config2":
+        if rank == 0:
+            run_secondary(args)
         return
     import numpy as np
     import torch

@@ -292,3 +292,44 @@ def make_config(k: int, scale: int = 0, n_rhs: int | None = None, seed: int | No
                                  det_angles_deg=[11.25 * i for i in range(16)], noise=nz,
                                  make_target=True)
     raise ValueError(f"unknown workload {k}")
+
+
+def device_timestreams(problem: Problem, n_rhs: int, seed: int, device="cuda"):
+    """float32 [n_rhs, n_t] timestreams d_r = A z + n_r synthesised on a GPU.
+
+    For workloads whose many noise realisations are too large to draw on the
+    host (e.g. 64 right-hand sides of 10^8 samples).  Same recipe as the host
+    path (signal from the float32 angles, noise coloured to the PSD with the
+    zero-frequency bin set to the first non-zero one), drawn from torch's
+    seeded device generator instead of numpy's, so the values differ from the
+    host path while following the same distribution.
+    """
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    pix = torch.from_numpy(problem.pix.astype(np.int64)).to(device)
+    ok = pix >= 0
+    sky = torch.from_numpy(problem.sky).to(device)
+    sig = sky[pix.clamp(min=0), 0]
+    if problem.n_stokes == 3:
+        two = 2.0 * torch.from_numpy(problem.psi).to(device).to(torch.float64)
+        sig = sig + sky[pix.clamp(min=0), 1] * torch.cos(two) + sky[pix.clamp(min=0), 2] * torch.sin(two)
+    sig = torch.where(ok, sig, torch.zeros_like(sig))
+    out = torch.empty((n_rhs, problem.n_samples), dtype=torch.float32, device=device)
+    off = problem.interval_offsets
+    for i in range(problem.n_intervals):
+        a, b = int(off[i]), int(off[i + 1])
+        n = b - a
+        if n == 0:
+            continue
+        s, fk, al = problem.noise_params[problem.interval_filter[i]]
+        w = torch.randn((n_rhs, n), generator=g, device=device, dtype=torch.float64)
+        if n >= 2 and fk > 0:
+            nu = torch.fft.rfftfreq(n, d=1.0 / problem.fs, device=device, dtype=torch.float64)
+            nu[0] = nu[1]
+            amp = s * torch.sqrt(1.0 + (fk / nu) ** al)
+            w = torch.fft.irfft(torch.fft.rfft(w, dim=1) * amp, n=n, dim=1)
+        else:
+            w = s * w
+        out[:, a:b] = (sig[a:b].unsqueeze(0) + w).to(torch.float32)
+    return out
