@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--profile-step", type=float, default=0.0, metavar="TOL",
                     help="profiling runs: skip the reference map and tolerance search and run exactly one "
                          "mixed-precision solve at this stopping tolerance")
+    ap.add_argument("--tpc", type=int, default=0, help="override the plan's tiles per launch chunk (0 = plan's choice)")
     ap.add_argument("--operator-only", type=int, default=0, metavar="R",
                     help="only build the plan and time R float32 operator applications (profiling runs)")
     return ap.parse_args()
@@ -347,7 +348,7 @@ def main():
     p = make_config(2, seed=2000 + rank)
     pix = torch.from_numpy(p.pix).to(dev)
     psi = torch.from_numpy(p.psi).to(dev)
-    plan = mm.Plan(pix, psi, p.n_pix, p.interval_offsets, p.interval_filter, lib_lags(p))
+    plan = mm.Plan(pix, psi, p.n_pix, p.interval_offsets, p.interval_filter, lib_lags(p), tiles_per_chunk=args.tpc)
     del pix, psi
     if args.operator_only:
         ms, n = plan.time_operator("fp32", reps=args.operator_only)

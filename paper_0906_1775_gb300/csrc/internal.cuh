@@ -202,6 +202,9 @@ __device__ __forceinline__ C csub(C a, C b) {
 __device__ __forceinline__ int sidx(int i) { return i + (i >> 5); }
 __host__ __device__ inline int row_stride(int n) { return n + (n >> 5) + 1; }
 
+// Threads per CTA of the operator kernels (every launch uses this many).
+constexpr int OP_THREADS = 256;
+
 // Multiplication by the constant w8^k = exp(-2 pi i k / 8), k = 0..3, or its
 // conjugate, written out so no general complex product is spent on it.
 template <int K, bool CONJ, typename C>
@@ -295,7 +298,8 @@ template <typename C, int R, bool INV>
 __device__ __forceinline__ void fft_pass(C* buf, int rows, int rs, int logN, int s, const C* tw) {
   const PassGeom G(logN, s, R);
   const int total = rows << G.gpr_log;
-  for (int g = threadIdx.x; g < total; g += blockDim.x) {
+#pragma unroll 4
+  for (int g = threadIdx.x; g < total; g += OP_THREADS) {
     int row, base, j;
     G.group(g, R, row, base, j);
     C* rp = buf + row * rs;
@@ -330,13 +334,15 @@ __host__ __device__ __forceinline__ int last_pass_start(int logN) { return ((log
 // Full FFT of `rows` rows of length N = 2^logN held in shared memory
 // (tw: N entries).
 template <typename C, bool INV>
-__device__ void fft_rows(C* buf, int rows, int rs, int logN, const C* tw) {
+__device__ __forceinline__ void fft_rows(C* buf, int rows, int rs, int logN, const C* tw) {
   if (!INV) {
+#pragma unroll
     for (int s = 0; s < logN; s += 3) {
       fft_pass_any<C, false>(buf, rows, rs, logN, s, tw);
       __syncthreads();
     }
   } else {
+#pragma unroll
     for (int s = last_pass_start(logN); s >= 0; s -= 3) {
       fft_pass_any<C, true>(buf, rows, rs, logN, s, tw);
       __syncthreads();
@@ -354,7 +360,8 @@ __device__ __forceinline__ void fused_middle(C* buf, int rows, int rs, int logN,
   typedef decltype(C().x) Real;
   const PassGeom G(logN, s, R);
   const int total = rows << G.gpr_log;
-  for (int g = threadIdx.x; g < total; g += blockDim.x) {
+#pragma unroll 4
+  for (int g = threadIdx.x; g < total; g += OP_THREADS) {
     int row, base, j;
     G.group(g, R, row, base, j);
     C* rp = buf + row * rs;
@@ -382,8 +389,9 @@ __device__ __forceinline__ void fused_middle(C* buf, int rows, int rs, int logN,
 }
 
 template <typename C, typename HF>
-__device__ void fft_rows_filter(C* buf, int rows, int rs, int logN, const C* tw, HF Hrow) {
+__device__ __forceinline__ void fft_rows_filter(C* buf, int rows, int rs, int logN, const C* tw, HF Hrow) {
   const int sl = last_pass_start(logN);
+#pragma unroll
   for (int s = 0; s < sl; s += 3) {
     fft_pass_any<C, false>(buf, rows, rs, logN, s, tw);
     __syncthreads();
@@ -393,6 +401,7 @@ __device__ void fft_rows_filter(C* buf, int rows, int rs, int logN, const C* tw,
   else if (R == 2) fused_middle<C, 2>(buf, rows, rs, logN, sl, Hrow);
   else fused_middle<C, 1>(buf, rows, rs, logN, sl, Hrow);
   __syncthreads();
+#pragma unroll
   for (int s = sl - 3; s >= 0; s -= 3) {
     fft_pass_any<C, true>(buf, rows, rs, logN, s, tw);
     __syncthreads();

@@ -184,24 +184,30 @@ __device__ __forceinline__ void finish_angle<float>(float& c, float& s) {
 // flight instead of one.
 
 // ---------------------------------------------------------------- k_f1
-template <typename Real, int NS, int IN>
+// LG2 > 0 fixes the column length N2 = 2^LG2 at compile time (and with it the
+// CTA's column count); LG2 = 0 reads the geometry from the arguments.
+template <typename Real, int NS, int IN, int LG2>
 __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a) {
   typedef typename CxT<Real>::type C;
+  constexpr int ELOG = sizeof(Real) == 4 ? 12 : 11;
+  const int logN2 = LG2 ? LG2 : a.logN2;
+  const int logB1 = LG2 ? ELOG - LG2 : a.logB1;
+  const int N2 = 1 << logN2, B1 = 1 << logB1;
   const int tl = blockIdx.y;
   const Tile* T = a.tiles + a.tile0 + tl;
   if (skip_tile(a, T)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int rs = row_stride(a.N2);
-  C* tw = buf + a.B1 * rs;
+  const int rs = row_stride(N2);
+  C* tw = buf + B1 * rs;
   const C* twM = static_cast<const C*>(a.tw);
-  for (int k = threadIdx.x; k < a.N2; k += blockDim.x) tw[k] = twM[(long long)k * a.N1];
+  for (int k = threadIdx.x; k < N2; k += OP_THREADS) tw[k] = twM[(long long)k * a.N1];
   LaneView<Real> L[2];
   L[0] = lane_view<Real, IN, OUT_MAP>(a, T->l[0]);
   L[1] = lane_view<Real, IN, OUT_MAP>(a, T->l[1]);
-  const int n1_0 = blockIdx.x * a.B1;
-  const int total = a.B1 << a.logN2;
-  const int bd = blockDim.x;
+  const int n1_0 = blockIdx.x * B1;
+  const int total = B1 << logN2;
+  constexpr int bd = OP_THREADS;
   constexpr int U = (IN == IN_MAPX && NS == 3) ? 4 : 8;
   for (int e0 = threadIdx.x; e0 < total; e0 += bd * U) {
     int nn[U];
@@ -209,7 +215,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * bd;
-      nn[u] = n1_0 + (e & (a.B1 - 1)) + ((e >> a.logB1) << a.logN1);
+      nn[u] = n1_0 + (e & (B1 - 1)) + ((e >> logB1) << a.logN1);
 #pragma unroll
       for (int l = 0; l < 2; ++l) ok[l][u] = e < total && in_range(nn[u], L[l].in_lo, L[l].in_hi);
     }
@@ -251,12 +257,12 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
         C z;
         z.x = v[0][u];
         z.y = v[1][u];
-        buf[(e & (a.B1 - 1)) * rs + sidx(e >> a.logB1)] = z;
+        buf[(e & (B1 - 1)) * rs + sidx(e >> logB1)] = z;
       }
     }
   }
   __syncthreads();
-  fft_rows<C, false>(buf, a.B1, rs, a.logN2, tw);
+  fft_rows<C, false>(buf, B1, rs, logN2, tw);
   C* sc = static_cast<C*>(a.scratch) + (long long)tl * a.M;
   const int mask = a.M - 1;
   for (int e0 = threadIdx.x; e0 < total; e0 += bd * 8) {
@@ -264,15 +270,15 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int e = e0 + u * bd;
-      const int n1 = n1_0 + (e & (a.B1 - 1));
-      const int k2 = brev_n(e >> a.logB1, a.logN2);
+      const int n1 = n1_0 + (e & (B1 - 1));
+      const int k2 = brev_n(e >> logB1, logN2);
       if (e < total) w[u] = twM[(n1 * k2) & mask];
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int e = e0 + u * bd;
       if (e < total) {
-        const int j = e & (a.B1 - 1), pos = e >> a.logB1;
+        const int j = e & (B1 - 1), pos = e >> logB1;
         sc[(long long)pos * a.N1 + n1_0 + j] = cmul(buf[j * rs + sidx(pos)], w[u]);
       }
     }
@@ -280,23 +286,28 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
 }
 
 // ---------------------------------------------------------------- k_f2
-template <typename Real>
+// LG1 > 0 fixes the row length N1 = 2^LG1 at compile time.
+template <typename Real, int LG1>
 __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f2(OpArgs a) {
   typedef typename CxT<Real>::type C;
+  constexpr int ELOG = sizeof(Real) == 4 ? 12 : 11;
+  const int logN1 = LG1 ? LG1 : a.logN1;
+  const int N1 = 1 << logN1;
+  const int B2 = LG1 ? (1 << (ELOG - LG1)) : a.B2;
   const int tl = blockIdx.y;
   const Tile* T = a.tiles + a.tile0 + tl;
   if (skip_tile(a, T)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int rs = row_stride(a.N1);
-  C* tw = buf + a.B2 * rs;
+  const int rs = row_stride(N1);
+  C* tw = buf + B2 * rs;
   const C* twM = static_cast<const C*>(a.tw);
-  for (int k = threadIdx.x; k < a.N1; k += blockDim.x) tw[k] = twM[(long long)k * a.N2];
+  for (int k = threadIdx.x; k < N1; k += OP_THREADS) tw[k] = twM[(long long)k * a.N2];
   const int filt = T->filter;
-  const int pos0 = blockIdx.x * a.B2;
-  C* sc = static_cast<C*>(a.scratch) + (long long)tl * a.M + (long long)pos0 * a.N1;
-  const int total = a.B2 << a.logN1;
-  const int bd = blockDim.x;
+  const int pos0 = blockIdx.x * B2;
+  C* sc = static_cast<C*>(a.scratch) + (long long)tl * a.M + (long long)pos0 * N1;
+  const int total = B2 << logN1;
+  constexpr int bd = OP_THREADS;
   for (int e0 = threadIdx.x; e0 < total; e0 += bd * 8) {
     C v[8];
 #pragma unroll
@@ -305,35 +316,38 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f2(OpArgs a)
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int e = e0 + u * bd;
-      if (e < total) buf[(e >> a.logN1) * rs + sidx(e & (a.N1 - 1))] = v[u];
+      if (e < total) buf[(e >> logN1) * rs + sidx(e & (N1 - 1))] = v[u];
     }
   }
   __syncthreads();
-  const Real* H = static_cast<const Real*>(a.H) + (long long)filt * a.M + (long long)pos0 * a.N1;
-  const int N1 = a.N1;
-  fft_rows_filter<C>(buf, a.B2, rs, a.logN1, tw, [H, N1](int row) { return H + (long long)row * N1; });
-  for (int e = threadIdx.x; e < total; e += bd) sc[e] = buf[(e >> a.logN1) * rs + sidx(e & (a.N1 - 1))];
+  const Real* H = static_cast<const Real*>(a.H) + (long long)filt * a.M + (long long)pos0 * N1;
+  fft_rows_filter<C>(buf, B2, rs, logN1, tw, [H, N1](int row) { return H + (long long)row * N1; });
+  for (int e = threadIdx.x; e < total; e += bd) sc[e] = buf[(e >> logN1) * rs + sidx(e & (N1 - 1))];
 }
 
 // ---------------------------------------------------------------- k_f3
-template <typename Real, int NS, int OUT>
+template <typename Real, int NS, int OUT, int LG2>
 __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a) {
   typedef typename CxT<Real>::type C;
+  constexpr int ELOG = sizeof(Real) == 4 ? 12 : 11;
+  const int logN2 = LG2 ? LG2 : a.logN2;
+  const int logB1 = LG2 ? ELOG - LG2 : a.logB1;
+  const int N2 = 1 << logN2, B1 = 1 << logB1;
   const int tl = blockIdx.y;
   const Tile* T = a.tiles + a.tile0 + tl;
   if (skip_tile(a, T)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int rs = row_stride(a.N2);
-  C* tw = buf + a.B1 * rs;
+  const int rs = row_stride(N2);
+  C* tw = buf + B1 * rs;
   const C* twM = static_cast<const C*>(a.tw);
-  for (int k = threadIdx.x; k < a.N2; k += blockDim.x) tw[k] = twM[(long long)k * a.N1];
+  for (int k = threadIdx.x; k < N2; k += OP_THREADS) tw[k] = twM[(long long)k * a.N1];
   LaneView<Real> L[2];
   L[0] = lane_view<Real, IN_MAPX, OUT>(a, T->l[0]);
   L[1] = lane_view<Real, IN_MAPX, OUT>(a, T->l[1]);
-  const int n1_0 = blockIdx.x * a.B1;
-  const int total = a.B1 << a.logN2;
-  const int bd = blockDim.x;
+  const int n1_0 = blockIdx.x * B1;
+  const int total = B1 << logN2;
+  constexpr int bd = OP_THREADS;
   const C* sc = static_cast<const C*>(a.scratch) + (long long)tl * a.M;
   const int mask = a.M - 1;
   for (int e0 = threadIdx.x; e0 < total; e0 += bd * 8) {
@@ -342,20 +356,20 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
     for (int u = 0; u < 8; ++u) {
       const int e = e0 + u * bd;
       if (e < total) {
-        const int n1 = n1_0 + (e & (a.B1 - 1));
-        const int pos = e >> a.logB1;
+        const int n1 = n1_0 + (e & (B1 - 1));
+        const int pos = e >> logB1;
         v[u] = sc[(long long)pos * a.N1 + n1];
-        w[u] = twM[(n1 * brev_n(pos, a.logN2)) & mask];
+        w[u] = twM[(n1 * brev_n(pos, logN2)) & mask];
       }
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int e = e0 + u * bd;
-      if (e < total) buf[(e & (a.B1 - 1)) * rs + sidx(e >> a.logB1)] = cmulc(v[u], w[u]);
+      if (e < total) buf[(e & (B1 - 1)) * rs + sidx(e >> logB1)] = cmulc(v[u], w[u]);
     }
   }
   __syncthreads();
-  fft_rows<C, true>(buf, a.B1, rs, a.logN2, tw);
+  fft_rows<C, true>(buf, B1, rs, logN2, tw);
   constexpr int U = 8;
   for (int e0 = threadIdx.x; e0 < total; e0 += bd * U) {
     int nn[U];
@@ -364,7 +378,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * bd;
-      const int j = e & (a.B1 - 1), n2 = e >> a.logB1;
+      const int j = e & (B1 - 1), n2 = e >> logB1;
       nn[u] = n1_0 + j + (n2 << a.logN1);
       C z;
       z.x = z.y = 0;
@@ -445,9 +459,49 @@ size_t smem_f2(const Plan* p) {
   return (size_t)(B2 * row_stride(p->N1) + p->N1) * sizeof(typename CxT<Real>::type);
 }
 
-template <typename K>
-cudaError_t set_smem(K kernel, size_t bytes) {
+typedef void (*OpKernel)(OpArgs);
+
+// Raise a kernel's dynamic shared-memory limit when a plan needs more than it
+// was last given (once per kernel instance and size; host-side bookkeeping).
+cudaError_t set_smem(OpKernel kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, size_t>> done;
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& d : done)
+    if (d.first == (const void*)kernel) {
+      if (d.second >= bytes) return cudaSuccess;
+      d.second = bytes;
+      return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    }
+  done.push_back({(const void*)kernel, bytes});
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// The three operator kernels for a plan: instances with compile-time FFT
+// geometry for the common sizes, the generic instances otherwise.
+struct OpKernels {
+  OpKernel f1, f2, f3;
+};
+
+template <typename Real, int NS, int IN, int OUT>
+OpKernels pick_kernels(const Plan* p) {
+  OpKernels k;
+  switch (p->logN2) {
+    case 7: k.f1 = k_f1<Real, NS, IN, 7>; k.f3 = k_f3<Real, NS, OUT, 7>; break;
+    case 8: k.f1 = k_f1<Real, NS, IN, 8>; k.f3 = k_f3<Real, NS, OUT, 8>; break;
+    case 9: k.f1 = k_f1<Real, NS, IN, 9>; k.f3 = k_f3<Real, NS, OUT, 9>; break;
+    case 10: k.f1 = k_f1<Real, NS, IN, 10>; k.f3 = k_f3<Real, NS, OUT, 10>; break;
+    default: k.f1 = k_f1<Real, NS, IN, 0>; k.f3 = k_f3<Real, NS, OUT, 0>; break;
+  }
+  switch (p->logN1) {
+    case 6: k.f2 = k_f2<Real, 6>; break;
+    case 7: k.f2 = k_f2<Real, 7>; break;
+    case 8: k.f2 = k_f2<Real, 8>; break;
+    case 9: k.f2 = k_f2<Real, 9>; break;
+    case 10: k.f2 = k_f2<Real, 10>; break;
+    default: k.f2 = k_f2<Real, 0>; break;
+  }
+  return k;
 }
 
 template <typename Real, int NS, int IN, int OUT>
@@ -473,18 +527,11 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
   a.tiles = ts ? ts->tiles : p->tiles;
   const int n_tiles = ts ? ts->n_tiles : p->n_tiles;
   const size_t sm13 = smem_f13<Real>(p), sm2 = smem_f2<Real>(p);
-  // opt-in to large dynamic shared memory once per kernel instance (raised when
-  // a plan needs more); n_rhs == 0 only does this, so it can precede a capture
-  static size_t set13 = 0, set2 = 0;
-  if (sm13 > set13) {
-    MM_CUDA(set_smem(k_f1<Real, NS, IN>, sm13));
-    MM_CUDA(set_smem(k_f3<Real, NS, OUT>, sm13));
-    set13 = sm13;
-  }
-  if (sm2 > set2) {
-    MM_CUDA(set_smem(k_f2<Real>, sm2));
-    set2 = sm2;
-  }
+  const OpKernels K = pick_kernels<Real, NS, IN, OUT>(p);
+  // n_rhs == 0 only sets the kernels' attributes, so it can precede a capture
+  MM_CUDA(set_smem(K.f1, sm13));
+  MM_CUDA(set_smem(K.f3, sm13));
+  MM_CUDA(set_smem(K.f2, sm2));
   int n_chunks, per_chunk;
   chunking(p, n_chunks, per_chunk, n_tiles);
   int ei = 0;
@@ -502,11 +549,11 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
         a.tile0 = t0;
         dim3 g13(p->N1 / a.B1, nt), g2(p->N2 / a.B2, nt);
         if (ev) cudaEventRecord(ev[ei++], s);
-        k_f1<Real, NS, IN><<<g13, 256, sm13, s>>>(a);
+        K.f1<<<g13, OP_THREADS, sm13, s>>>(a);
         if (ev) cudaEventRecord(ev[ei++], s);
-        k_f2<Real><<<g2, 256, sm2, s>>>(a);
+        K.f2<<<g2, OP_THREADS, sm2, s>>>(a);
         if (ev) cudaEventRecord(ev[ei++], s);
-        k_f3<Real, NS, OUT><<<g13, 256, sm13, s>>>(a);
+        K.f3<<<g13, OP_THREADS, sm13, s>>>(a);
         if (ev) cudaEventRecord(ev[ei++], s);
       }
     }
@@ -608,39 +655,25 @@ madmap_status op_time(Plan* p, bool fp64, const void* in, void* out, int reps, d
 // CTAs per tile of the column kernels, for wave-aligned chunk sizes.
 void op_occupancy(const Plan* p, bool fp64, int& ctas_per_sm, int& ctas_per_tile) {
   int b1 = 0, b2 = 0, n1 = 0, n2 = 0, n3 = 0;
+  size_t s13 = 0, s2 = 0;
+  OpKernels K;
   if (fp64) {
     geometry<double>(p, b1, b2);
-    const size_t s13 = smem_f13<double>(p), s2 = smem_f2<double>(p);
-    if (p->n_stokes == 1) {
-      set_smem(k_f1<double, 1, IN_MAPX>, s13);
-      set_smem(k_f3<double, 1, OUT_MAP>, s13);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_f1<double, 1, IN_MAPX>, 256, s13);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n3, k_f3<double, 1, OUT_MAP>, 256, s13);
-    } else {
-      set_smem(k_f1<double, 3, IN_MAPX>, s13);
-      set_smem(k_f3<double, 3, OUT_MAP>, s13);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_f1<double, 3, IN_MAPX>, 256, s13);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n3, k_f3<double, 3, OUT_MAP>, 256, s13);
-    }
-    set_smem(k_f2<double>, s2);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_f2<double>, 256, s2);
+    s13 = smem_f13<double>(p);
+    s2 = smem_f2<double>(p);
+    K = p->n_stokes == 1 ? pick_kernels<double, 1, IN_MAPX, OUT_MAP>(p) : pick_kernels<double, 3, IN_MAPX, OUT_MAP>(p);
   } else {
     geometry<float>(p, b1, b2);
-    const size_t s13 = smem_f13<float>(p), s2 = smem_f2<float>(p);
-    if (p->n_stokes == 1) {
-      set_smem(k_f1<float, 1, IN_MAPX>, s13);
-      set_smem(k_f3<float, 1, OUT_MAP>, s13);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_f1<float, 1, IN_MAPX>, 256, s13);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n3, k_f3<float, 1, OUT_MAP>, 256, s13);
-    } else {
-      set_smem(k_f1<float, 3, IN_MAPX>, s13);
-      set_smem(k_f3<float, 3, OUT_MAP>, s13);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_f1<float, 3, IN_MAPX>, 256, s13);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n3, k_f3<float, 3, OUT_MAP>, 256, s13);
-    }
-    set_smem(k_f2<float>, s2);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_f2<float>, 256, s2);
+    s13 = smem_f13<float>(p);
+    s2 = smem_f2<float>(p);
+    K = p->n_stokes == 1 ? pick_kernels<float, 1, IN_MAPX, OUT_MAP>(p) : pick_kernels<float, 3, IN_MAPX, OUT_MAP>(p);
   }
+  set_smem(K.f1, s13);
+  set_smem(K.f2, s2);
+  set_smem(K.f3, s13);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, K.f1, OP_THREADS, s13);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, K.f2, OP_THREADS, s2);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n3, K.f3, OP_THREADS, s13);
   cudaGetLastError();
   ctas_per_sm = std::max(1, std::min(n1, std::min(n2, n3)));
   ctas_per_tile = std::max(1, p->N1 / std::max(1, b1));

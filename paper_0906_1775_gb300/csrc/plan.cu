@@ -743,30 +743,12 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
   p->n_segments = (int)segs.size();
   p->n_tiles = (int)p->host_tiles.size();
   {
-    // Chunk size: at most 32 MB of float32 scratch (so a chunk's intermediate
-    // stays in L2), chosen to minimise the number of CTA waves over all chunks
-    // (balanced chunks; a small cost per extra launch breaks ties).
+    // Chunk size: as many tiles per launch as fit a 1 GB scratch budget
+    // (float64 sizing).  Launches of many CTA waves let CTAs in different
+    // phases (gather, FFT passes, scatter) overlap on each SM, which was
+    // measured to beat wave-sized chunks whose scratch stays in L2.
     long long tpc = d->tiles_per_chunk;
-    if (tpc <= 0) {
-      const long long cap = std::max(1LL, std::min<long long>((32LL << 20) / (8LL * p->M), std::max(1, p->n_tiles)));
-      int dev = 0, n_sm = 1, per_sm = 1, per_tile = 1;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-      op_occupancy(p, false, per_sm, per_tile);
-      const double wave = (double)per_sm * n_sm;
-      double best = 1e300;
-      tpc = cap;
-      for (long long c = 1; c <= cap; ++c) {
-        const long long nch = (p->n_tiles + c - 1) / c;
-        const long long per = nch ? (p->n_tiles + nch - 1) / nch : 0;
-        const double waves = (double)nch * std::ceil((double)(per * per_tile) / wave);
-        const double cost = waves + 0.05 * nch;
-        if (cost < best - 1e-9) {
-          best = cost;
-          tpc = c;
-        }
-      }
-    }
+    if (tpc <= 0) tpc = std::max(1LL, (1LL << 30) / (16LL * p->M));
     tpc = std::max(1LL, std::min<long long>(tpc, std::max(1, p->n_tiles)));
     tpc = std::min<long long>(tpc, 65535);
     p->tiles_per_chunk = (int)tpc;
