@@ -374,9 +374,13 @@ def main():
     ref, rinfo = plan.solve(d, precision="fp64", rel_tol=1e-11, max_iter=3000)
     ref = ref.cpu().numpy()
 
+    TOLS = [1e-4, 5e-5, 2e-5, 1e-5, 5e-6, 2e-6, 1e-6, 5e-7, 2e-7, 1e-7, 5e-8, 2e-8, 1e-8, 5e-9, 2e-9, 1e-9,
+            5e-10, 1e-10]
+
     def first_tol(precision, **kw):
+        """Loosest stopping tolerance whose map is within MAP_TARGET of the reference."""
         last = None
-        for tol in [1e-6, 5e-7, 2e-7, 1e-7, 5e-8, 2e-8, 1e-8, 5e-9, 2e-9, 1e-9, 5e-10, 1e-10]:
+        for tol in TOLS:
             m, info = plan.solve(d, precision=precision, rel_tol=tol, max_iter=3000, **kw)
             err, per = stokes_err(m.cpu().numpy(), ref, keep)
             last = (tol, info, err, per)
@@ -384,10 +388,29 @@ def main():
                 return last
         return last
 
-    mixed_kw = dict(max_outer=20, inner_rel_tol=1e-4)
-    tol_mixed, info_mixed, err_mixed, per_mixed = first_tol("mixed", **mixed_kw)
-    tol_64, info_64, err_64, per_64 = first_tol("fp64")
+    def time_solve(precision, tol, **kw):
+        plan.solve(d, precision=precision, rel_tol=tol, max_iter=3000, **kw)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        plan.solve(d, precision=precision, rel_tol=tol, max_iter=3000, **kw)
+        t1.record()
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1)
 
+    # mixed precision: the inner float32 tolerance is a free parameter of the
+    # method; pick the fastest setting that reaches the map error
+    best_mixed = None
+    for inner in (1e-4, 1e-5, 1e-6):
+        kw_i = dict(max_outer=20, inner_rel_tol=inner)
+        cand = first_tol("mixed", **kw_i)
+        if cand[2] > MAP_TARGET:
+            continue
+        t = time_solve("mixed", cand[0], **kw_i)
+        if best_mixed is None or t < best_mixed[0]:
+            best_mixed = (t, kw_i, cand)
+    mixed_kw, (tol_mixed, info_mixed, err_mixed, per_mixed) = best_mixed[1], best_mixed[2]
+    tol_64, info_64, err_64, per_64 = first_tol("fp64")
     def solve_step():
         return plan.solve(d, precision="mixed", rel_tol=tol_mixed, max_iter=3000, **mixed_kw)
 
@@ -507,7 +530,7 @@ def main():
                 "time_to_1e-6_map_error": {
                     "mixed_ms": ms_max / args.steps, "mixed_iters": iters // max(args.steps, 1),
                     "mixed_rel_tol": tol_mixed, "mixed_map_err": err_mixed, "mixed_map_err_IQU": per_mixed,
-                    "mixed_outer": info_mixed["outer_iters"],
+                    "mixed_outer": info_mixed["outer_iters"], "mixed_inner_rel_tol": mixed_kw["inner_rel_tol"],
                     "fp64_ms": ms_fp64, "fp64_iters": i64["iters"], "fp64_rel_tol": tol_64,
                     "fp64_map_err": err_64, "speedup_mixed_vs_fp64": ms_fp64 / (ms_max / args.steps),
                     "reference": f"FP64 GPU solve to rel. residual 1e-11 ({rinfo['iters']} iterations)"},

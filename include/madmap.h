@@ -110,8 +110,11 @@ typedef struct {
   int32_t max_outer;       /* MIXED: refinement steps, default 10 */
   double inner_rel_tol;    /* MIXED: inner float32 PCG stops at this reduction of its residual,
                               default 1e-4 */
-  int32_t use_graph;       /* 1 (default): replay iterations as CUDA graphs */
-  int32_t iters_per_sync;  /* iterations enqueued between host checks, default 8 */
+  int32_t use_graph;       /* 2 (default): one CUDA graph runs all iterations on the device (a
+                              conditional WHILE node, capped at max_iter + 2 passes); 1: chunks of
+                              iters_per_sync iterations replayed as graphs with host checks
+                              between them; 0: direct launches with host checks */
+  int32_t iters_per_sync;  /* iterations enqueued between host checks (modes 0 and 1), default 8 */
 } madmap_solve_opts;
 
 typedef struct {

@@ -274,7 +274,7 @@ class Plan:
         o = _lib.madmap_solve_opts()
         o.max_iter, o.rel_tol, o.precision = int(max_iter), float(rel_tol), _PREC[precision]
         o.max_outer, o.inner_rel_tol = int(max_outer), float(inner_rel_tol)
-        o.use_graph, o.iters_per_sync = int(bool(use_graph)), int(iters_per_sync)
+        o.use_graph, o.iters_per_sync = (2 if use_graph is True else int(use_graph)), int(iters_per_sync)
         return o
 
     def solve_batched(self, d, precision="fp64", max_iter=50, rel_tol=1e-6, max_outer=10, inner_rel_tol=1e-4,

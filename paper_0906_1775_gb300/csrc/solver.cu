@@ -64,6 +64,15 @@ struct SolveBuffers {
   int graph_iters = 0, graph_rhs = 0;
   const void* graph_ts = nullptr;
   long long graph_launches = 0;  // kernel nodes per replay
+  // device-side loop: a graph whose conditional WHILE node repeats one
+  // iteration until every right-hand side is done (or a hard cap is hit)
+  cudaGraph_t wgraph = nullptr;
+  cudaGraphExec_t wexec = nullptr;
+  int w_rhs = 0;
+  const void* w_ts = nullptr;
+  long long w_body_launches = 0;
+  bool w_unsupported = false;
+  int* loop = nullptr;  // [0] body executions, [1] cap
   std::vector<void*> allocs;
   size_t bytes = 0;
 };
@@ -74,6 +83,8 @@ static const int NT = 256;
 static void free_one(SolveBuffers* sb) {
   if (!sb) return;
   if (sb->exec) cudaGraphExecDestroy(sb->exec);
+  if (sb->wexec) cudaGraphExecDestroy(sb->wexec);
+  if (sb->wgraph) cudaGraphDestroy(sb->wgraph);
   for (int i = 0; i < 2; ++i)
     if (sb->ev[i]) cudaEventDestroy(sb->ev[i]);
   if (sb->host_st) cudaFreeHost(sb->host_st);
@@ -127,6 +138,7 @@ static madmap_status get_buffers(Plan* p, bool fp64, int n_rhs, SolveBuffers** o
   if (st == MADMAP_OK) st = sb_alloc(p, sb, (void**)&sb->partials, sizeof(double) * NB * 4 * n_rhs);
   if (st == MADMAP_OK) st = sb_alloc(p, sb, (void**)&sb->st, sizeof(CgState) * n_rhs);
   if (st == MADMAP_OK) st = sb_alloc(p, sb, (void**)&sb->flags, sizeof(int) * n_rhs);
+  if (st == MADMAP_OK) st = sb_alloc(p, sb, (void**)&sb->loop, sizeof(int) * 2);
   if (st == MADMAP_OK && fp64) {
     double** v64[5] = {&sb->b64, &sb->x64, &sb->r64, &sb->t64, &sb->xbest64};
     for (double** v : v64)
@@ -548,6 +560,63 @@ static madmap_status enqueue_chunk(Plan* p, SolveBuffers* sb, const Batch& B, in
   return MADMAP_OK;
 }
 
+// Condition of the device-side loop: continue while some right-hand side is
+// not done, and never beyond the cap (loop[1]) iterations.
+__global__ void k_loop_cond(const CgState* st, int n_rhs, int* loop, cudaGraphConditionalHandle h) {
+  int live = 0;
+  for (int r = threadIdx.x; r < n_rhs; r += 32) live |= !st[r].done;
+  live = __any_sync(0xffffffffu, live);
+  if (threadIdx.x == 0) {
+    const int it = loop[0] + 1;
+    loop[0] = it;
+    cudaGraphSetConditional(h, (live && it < loop[1]) ? 1u : 0u);
+  }
+}
+
+template <typename Real, int NS>
+static madmap_status build_while_graph(Plan* p, SolveBuffers* sb, const Batch& B, cudaStream_t s) {
+  if (sb->wexec && sb->w_rhs == B.n_rhs && sb->w_ts == (const void*)B.ts) return MADMAP_OK;
+  if (sb->wexec) {
+    cudaGraphExecDestroy(sb->wexec);
+    sb->wexec = nullptr;
+  }
+  if (sb->wgraph) {
+    cudaGraphDestroy(sb->wgraph);
+    sb->wgraph = nullptr;
+  }
+  madmap_status st = op_launch(p, sizeof(Real) == 8, IN_MAP, OUT_MAP, nullptr, nullptr, 0, 0, 0, nullptr, s);
+  if (st != MADMAP_OK) return st;
+  cudaGraph_t g = nullptr;
+  MM_CUDA(cudaGraphCreate(&g, 0));
+  sb->wgraph = g;
+  cudaGraphConditionalHandle h;
+  MM_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault));
+  // zeroed storage: the parameter union has no default constructor
+  alignas(cudaGraphNodeParams) unsigned char np_raw[sizeof(cudaGraphNodeParams)] = {};
+  cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_raw);
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  MM_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  const int64_t before = madmap_kernel_launch_count();
+  MM_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  enqueue_iteration<Real, NS>(p, sb, B, s, &st);
+  k_loop_cond<<<1, 32, 0, s>>>(sb->st, B.n_rhs, sb->loop, h);
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &captured);
+  sb->w_body_launches = madmap_kernel_launch_count() - before + 1;
+  count_launches(-(sb->w_body_launches - 1));
+  if (st != MADMAP_OK) return st;
+  MM_CUDA(e);
+  MM_CUDA(cudaGraphInstantiate(&sb->wexec, g, 0));
+  sb->w_rhs = B.n_rhs;
+  sb->w_ts = B.ts;
+  return MADMAP_OK;
+}
+
 struct PcgResult {
   int iters = 0, best_iter = 0, status = 0;
   double best_res = 0.0, final_res = 0.0;
@@ -559,13 +628,47 @@ struct PcgResult {
 // Results: best iterates in sb->xb, summaries in out[rhs].
 template <typename Real, int NS, typename Bt>
 static madmap_status run_pcg(Plan* p, SolveBuffers* sb, const Batch& B, const Bt* b, const int* inactive, double tol,
-                             int max_iter, int per_sync, bool use_graph, cudaStream_t s, std::vector<PcgResult>& out) {
+                             int max_iter, int per_sync, int graph_mode, cudaStream_t s, std::vector<PcgResult>& out) {
   const int n = p->n_obs, R = B.n_rhs;
   count_launches(1);
   k_cg_init<Real, NS, Bt><<<dim3(grid_vec(n), R), NT, 0, s>>>(
       (Real*)sb->x, (Real*)sb->r, (Real*)sb->z, (Real*)sb->p, (Real*)sb->q, (Real*)sb->xb, b, sb->nvec, n, p->P64,
       p->P32, p->fp64flag, sb->st, sb->partials, tol, max_iter, inactive);
   MM_CUDA(cudaGetLastError());
+  if (graph_mode == 2 && !sb->w_unsupported) {
+    // one graph launch runs every iteration on the device
+    if (build_while_graph<Real, NS>(p, sb, B, s) != MADMAP_OK) {
+      // conditional graph nodes unavailable here: fall back to host-checked chunks
+      sb->w_unsupported = true;
+      cudaGetLastError();
+      cudaStreamCaptureStatus cs;
+      if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(s, &junk);
+        if (junk) cudaGraphDestroy(junk);
+      }
+    } else {
+      const int ctl[2] = {0, max_iter + 2};
+      MM_CUDA(cudaMemcpyAsync(sb->loop, ctl, sizeof(ctl), cudaMemcpyHostToDevice, s));
+      MM_CUDA(cudaGraphLaunch(sb->wexec, s));
+      int ran[2] = {0, 0};
+      MM_CUDA(cudaMemcpyAsync(ran, sb->loop, sizeof(ran), cudaMemcpyDeviceToHost, s));
+      std::vector<CgState> h(R);
+      MM_CUDA(cudaMemcpyAsync(h.data(), sb->st, sizeof(CgState) * R, cudaMemcpyDeviceToHost, s));
+      MM_CUDA(cudaStreamSynchronize(s));
+      count_launches((long long)ran[0] * sb->w_body_launches);
+      out.assign(R, PcgResult());
+      for (int k = 0; k < R; ++k) {
+        out[k].iters = h[k].k;
+        out[k].best_iter = h[k].best_k;
+        out[k].best_res = h[k].best_res;
+        out[k].final_res = h[k].res;
+        out[k].status = h[k].status;
+      }
+      return MADMAP_OK;
+    }
+  }
+  const bool use_graph = graph_mode != 0;
   int launched = 0, slot = 0;
   bool pending = false;
   const int G = std::max(1, per_sync);
@@ -619,7 +722,7 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
   const int n_rhs = B.n_rhs;
   const long long nv = sb64->nvec;
   const dim3 gv(grid_vec(nv), n_rhs);
-  const bool graph = o.use_graph != 0;
+  const int graph = o.use_graph;
   madmap_status st = MADMAP_OK;
   std::vector<PcgResult> R;
   if (o.precision == MADMAP_FP64) {
@@ -1032,7 +1135,7 @@ extern "C" void madmap_solve_opts_default(madmap_solve_opts* o) {
   o->precision = MADMAP_FP64;
   o->max_outer = 10;
   o->inner_rel_tol = 1e-4;
-  o->use_graph = 1;
+  o->use_graph = 2;
   o->iters_per_sync = 8;
 }
 

@@ -168,15 +168,36 @@ def test_solve_mixed_reaches_fp64_map(case):
     assert info["outer_iters"] >= 1 and info["fp64_applies"] == info["outer_iters"] + 1
 
 
-def test_solve_without_graphs_is_identical():
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_iteration_drivers_agree(prec):
+    """Device-side loop (2), host-checked graph chunks (1) and direct launches (0)."""
     p = tiny_IQU(seed=5)
     plan = make_plan(p)
     d = cuda(p.d[0])
-    m1, i1 = plan.solve(d, rel_tol=1e-10, max_iter=200, use_graph=True)
-    m2, i2 = plan.solve(d, rel_tol=1e-10, max_iter=200, use_graph=False, iters_per_sync=3)
-    assert i1["iters"] == i2["iters"]
-    # dot products reduce in a fixed order, but the scatter's float atomics do not
-    assert rel_rms(host(m1), host(m2)) < 1e-12
+    runs = [plan.solve(d, precision=prec, rel_tol=1e-10, max_iter=200, use_graph=g, iters_per_sync=k)
+            for g, k in ((2, 8), (1, 8), (0, 3))]
+    for m, info in runs[1:]:
+        assert info["iters"] == runs[0][1]["iters"]
+        # dot products reduce in a fixed order, but the scatter's float atomics do not
+        assert rel_rms(host(m), host(runs[0][0])) < 1e-12
+
+
+def test_iteration_drivers_agree_batched():
+    p = _batched_problem("T", 3)
+    plan = make_plan(p)
+    d = cuda(p.d)
+    m2, i2 = plan.solve_batched(d, rel_tol=1e-11, max_iter=400, use_graph=2)
+    m1, i1 = plan.solve_batched(d, rel_tol=1e-11, max_iter=400, use_graph=1, iters_per_sync=5)
+    for r in range(3):
+        assert i1[r]["iters"] == i2[r]["iters"]
+        assert rel_rms(host(m1[r]), host(m2[r])) < 1e-12
+
+
+def test_max_iter_cap_with_device_loop():
+    p = tiny_IQU(seed=15)
+    plan = make_plan(p)
+    m, info = plan.solve(cuda(p.d[0]), rel_tol=1e-30, max_iter=4, use_graph=2)
+    assert info["iters"] == 4 and info["status"] == 1
 
 
 def test_white_noise_solve_is_binned_average():
