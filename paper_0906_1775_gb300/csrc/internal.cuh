@@ -201,6 +201,9 @@ __device__ __forceinline__ C csub(C a, C b) {
 // apart so column-wise accesses spread over the banks.
 __device__ __forceinline__ int sidx(int i) { return i + (i >> 5); }
 __host__ __device__ inline int row_stride(int n) { return n + (n >> 5) + 1; }
+// Row stride for the column kernels, whose load and store phases walk down
+// `rows` rows at once: the pad spreads those accesses over the banks.
+__host__ __device__ inline int row_stride_cols(int n, int rows) { return n + (n >> 5) + (rows <= 4 ? 4 : 2); }
 
 // Threads per CTA of the operator kernels (every launch uses this many).
 constexpr int OP_THREADS = 256;
@@ -273,7 +276,9 @@ __device__ __forceinline__ void small_dft(C (&v)[1 << R]) {
 // Group geometry of a pass: R radix-2 stages starting at stage s of an
 // N = 2^logN transform; group g of a row owns the 2^R elements
 // base + m * hR (m = 0 .. 2^R - 1) and its output twiddles are
-// tw[(j << s) * brev_R(m)], tw[k] = exp(-2 pi i k / N) for k < N.
+// exp(-2 pi i (j << s) k / N) for k = brev_R(m).  They are read from the
+// pass's own table twp[(k - 1) * hR + j] (see build_pass_twiddles), so the
+// threads of a warp read consecutive entries.
 struct PassGeom {
   int logh, hR, gpr_log;
   __device__ __forceinline__ PassGeom(int logN, int s, int R) {
@@ -306,14 +311,13 @@ __device__ __forceinline__ void fft_pass(C* buf, int rows, int rs, int logN, int
     C v[1 << R];
 #pragma unroll
     for (int m = 0; m < (1 << R); ++m) v[m] = rp[sidx(base + m * G.hR)];
-    const int js = j << s;
     if (!INV) {
       small_dft<C, R, false>(v);
 #pragma unroll
-      for (int m = 1; m < (1 << R); ++m) v[m] = cmul(v[m], tw[js * brev_small<R>(m)]);
+      for (int m = 1; m < (1 << R); ++m) v[m] = cmul(v[m], tw[((brev_small<R>(m) - 1) << G.logh) + j]);
     } else {
 #pragma unroll
-      for (int m = 1; m < (1 << R); ++m) v[m] = cmulc(v[m], tw[js * brev_small<R>(m)]);
+      for (int m = 1; m < (1 << R); ++m) v[m] = cmulc(v[m], tw[((brev_small<R>(m) - 1) << G.logh) + j]);
       small_dft<C, R, true>(v);
     }
 #pragma unroll
@@ -321,15 +325,45 @@ __device__ __forceinline__ void fft_pass(C* buf, int rows, int rs, int logN, int
   }
 }
 
+__host__ __device__ __forceinline__ int last_pass_start(int logN) { return ((logN - 1) / 3) * 3; }
+
+// Offset of pass s's twiddle table: passes before it hold (2^R - 1) N/2^(s'+R)
+// entries each (N - 1 entries in all).
+__device__ __forceinline__ int pass_offset(int logN, int s) {
+  int off = 0;
+  for (int q = 0; q < s; q += 3) {
+    const int R = (logN - q) >= 3 ? 3 : (logN - q);
+    off += ((1 << R) - 1) << (logN - q - R);
+  }
+  return off;
+}
+
+// Per-pass output-twiddle tables of an N = 2^logN transform, from the plan's
+// table twM (exp(-2 pi i j / M), read with stride M/N): entry (k - 1) * hR + j
+// of pass s is exp(-2 pi i (j << s) k / N).
+template <typename C>
+__device__ __forceinline__ void build_pass_twiddles(C* twp, int logN, const C* twM, long long stride) {
+  int off = 0;
+  for (int s = 0; s < logN; s += 3) {
+    const int R = (logN - s) >= 3 ? 3 : (logN - s);
+    const int logh = logN - s - R;
+    const int cnt = ((1 << R) - 1) << logh;
+    for (int i = threadIdx.x; i < cnt; i += OP_THREADS) {
+      const int k = (i >> logh) + 1, j = i & ((1 << logh) - 1);
+      twp[off + i] = twM[(long long)((j << s) * k) * stride];
+    }
+    off += cnt;
+  }
+}
+
 template <typename C, bool INV>
 __device__ __forceinline__ void fft_pass_any(C* buf, int rows, int rs, int logN, int s, const C* tw) {
   const int R = (logN - s) >= 3 ? 3 : (logN - s);
-  if (R == 3) fft_pass<C, 3, INV>(buf, rows, rs, logN, s, tw);
-  else if (R == 2) fft_pass<C, 2, INV>(buf, rows, rs, logN, s, tw);
-  else fft_pass<C, 1, INV>(buf, rows, rs, logN, s, tw);
+  const C* twp = tw + pass_offset(logN, s);
+  if (R == 3) fft_pass<C, 3, INV>(buf, rows, rs, logN, s, twp);
+  else if (R == 2) fft_pass<C, 2, INV>(buf, rows, rs, logN, s, twp);
+  else fft_pass<C, 1, INV>(buf, rows, rs, logN, s, twp);
 }
-
-__host__ __device__ __forceinline__ int last_pass_start(int logN) { return ((logN - 1) / 3) * 3; }
 
 // Full FFT of `rows` rows of length N = 2^logN held in shared memory
 // (tw: N entries).

@@ -198,10 +198,10 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
   if (skip_tile(a, T)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int rs = row_stride(N2);
+  const int rs = row_stride_cols(N2, B1);
   C* tw = buf + B1 * rs;
   const C* twM = static_cast<const C*>(a.tw);
-  for (int k = threadIdx.x; k < N2; k += OP_THREADS) tw[k] = twM[(long long)k * a.N1];
+  build_pass_twiddles(tw, logN2, twM, a.N1);
   LaneView<Real> L[2];
   L[0] = lane_view<Real, IN, OUT_MAP>(a, T->l[0]);
   L[1] = lane_view<Real, IN, OUT_MAP>(a, T->l[1]);
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f2(OpArgs a)
   const int rs = row_stride(N1);
   C* tw = buf + B2 * rs;
   const C* twM = static_cast<const C*>(a.tw);
-  for (int k = threadIdx.x; k < N1; k += OP_THREADS) tw[k] = twM[(long long)k * a.N2];
+  build_pass_twiddles(tw, logN1, twM, a.N2);
   const int filt = T->filter;
   const int pos0 = blockIdx.x * B2;
   C* sc = static_cast<C*>(a.scratch) + (long long)tl * a.M + (long long)pos0 * N1;
@@ -338,10 +338,10 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
   if (skip_tile(a, T)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int rs = row_stride(N2);
+  const int rs = row_stride_cols(N2, B1);
   C* tw = buf + B1 * rs;
   const C* twM = static_cast<const C*>(a.tw);
-  for (int k = threadIdx.x; k < N2; k += OP_THREADS) tw[k] = twM[(long long)k * a.N1];
+  build_pass_twiddles(tw, logN2, twM, a.N1);
   LaneView<Real> L[2];
   L[0] = lane_view<Real, IN_MAPX, OUT>(a, T->l[0]);
   L[1] = lane_view<Real, IN_MAPX, OUT>(a, T->l[1]);
@@ -450,7 +450,7 @@ template <typename Real>
 size_t smem_f13(const Plan* p) {
   int B1, B2;
   geometry<Real>(p, B1, B2);
-  return (size_t)(B1 * row_stride(p->N2) + p->N2) * sizeof(typename CxT<Real>::type);
+  return (size_t)(B1 * row_stride_cols(p->N2, B1) + p->N2) * sizeof(typename CxT<Real>::type);
 }
 template <typename Real>
 size_t smem_f2(const Plan* p) {
