@@ -21,15 +21,20 @@ from __future__ import annotations
 import numpy as np
 
 
-def observed_pixels(pix: np.ndarray, n_pix: int):
+def observed_pixels(pix: np.ndarray, n_pix: int, chunk: int | None = None):
     """Global -> observed re-indexing through the n_z-bit array of Section 5.4.
 
     Returns (obs2glob int64 [n_obs] ascending, glob2obs int64 [n_pix] with -1
-    for unobserved pixels).  Parity pinned by test_observed_pixels_bruteforce.
+    for unobserved pixels).  ``chunk`` sets the bits from that many samples at
+    a time (for pointing too large to copy whole).  Parity pinned by
+    test_observed_pixels_bruteforce.
     """
     bits = np.zeros(n_pix, dtype=bool)          # the n_z-bit array
-    hit = pix[pix >= 0].astype(np.int64)
-    bits[hit] = True
+    n_t = int(pix.shape[0])
+    step = n_t if not chunk else int(chunk)
+    for lo in range(0, n_t, max(step, 1)):
+        c = np.asarray(pix[lo:lo + step])
+        bits[c[c >= 0].astype(np.int64)] = True
     obs2glob = np.flatnonzero(bits)             # set bits in ascending global order
     glob2obs = np.full(n_pix, -1, dtype=np.int64)
     glob2obs[obs2glob] = np.arange(obs2glob.size)

@@ -72,37 +72,10 @@ class System:
 
     # ---------------------------------------------------------------- set-up
     def _classify(self, pixl, f0, rcond_excise, rcond_fp64):
-        n_obs, n_s = self.n_obs, self.n_s
-        ok = pixl >= 0
-        p = pixl[ok]
-        self.hits = np.bincount(p, minlength=n_obs)
-        if n_s == 1:
-            wsum = np.bincount(p, weights=f0[ok], minlength=n_obs)
-            self.blocks = wsum.reshape(n_obs, 1, 1)
-            self.excised = self.hits == 0
-            self.fp64 = np.zeros(n_obs, dtype=bool)
-            self.rcond = np.ones(n_obs)
-            with np.errstate(divide="ignore"):
-                self.Pinv = np.where(self.excised, 0.0, 1.0 / wsum).reshape(n_obs, 1, 1)
-            return
-        w = self.w[ok]
-        AtA = np.zeros((n_obs, 3, 3))
-        AtWA = np.zeros((n_obs, 3, 3))
-        for a in range(3):
-            for b in range(3):
-                AtA[:, a, b] = np.bincount(p, weights=w[:, a] * w[:, b], minlength=n_obs)
-                AtWA[:, a, b] = np.bincount(p, weights=f0[ok] * w[:, a] * w[:, b], minlength=n_obs)
-        ev = np.linalg.eigvalsh(AtA)                    # ascending
-        with np.errstate(divide="ignore", invalid="ignore"):
-            rc = np.where(ev[:, 2] > 0, ev[:, 0] / ev[:, 2], 0.0)
-        self.rcond = rc
-        self.excised = (self.hits < 3) | (rc < rcond_excise)
-        self.fp64 = (~self.excised) & (rc < rcond_fp64)
-        self.blocks = AtWA
-        Pinv = np.zeros_like(AtWA)
-        good = ~self.excised
-        Pinv[good] = np.linalg.inv(AtWA[good])
-        self.Pinv = Pinv
+        hits, AtA, AtWA = pixel_blocks(pixl, self.w, f0, self.n_obs, self.n_s)
+        c = classify_blocks(hits, AtA, AtWA, rcond_excise, rcond_fp64)
+        self.hits, self.blocks, self.rcond = hits, AtWA, c["rcond"]
+        self.excised, self.fp64, self.Pinv = c["excised"], c["fp64"], c["Pinv"]
 
     # ---------------------------------------------------------------- operators
     def unpoint(self, x):
@@ -127,30 +100,16 @@ class System:
     def H_sampled(self, x, pixels):
         """(H x)_p for a few observed pixels p, each computed on its own from Eq. 15.
 
-        For every sample t of pixel p: (N^-1 A x)_t = sum over |tau| < n_c inside
-        t's interval of f(|tau|) (A x)_{t+tau}; then weight and sum into p.  Used
-        to check full-size operator outputs one by one.
+        Used to check full-size operator outputs one by one (see sampled_rows).
         """
         x = np.asarray(x, dtype=np.float64).reshape(self.n_obs, self.n_s)
-        out = np.zeros((len(pixels), self.n_s))
-        for k, p in enumerate(pixels):
-            ts = np.flatnonzero(self.pixl == p)
-            for t in ts:
-                i = int(np.searchsorted(self.offsets, t, side="right") - 1)
-                a, b = int(self.offsets[i]), int(self.offsets[i + 1])
-                lo, hi = max(a, t - self.n_c + 1), min(b, t + self.n_c)
-                sl = slice(lo, hi)
-                pl = self.pixl[sl]
-                ok = pl >= 0
-                w = None if self.w is None else self.w[sl]
-                ax = _pt.unpoint(x, pl, w)
-                f = self.lags[self.ivl_filter[i]][np.abs(np.arange(lo, hi) - t)]
-                v = float(np.sum(f[ok] * ax[ok]))
-                if self.w is None:
-                    out[k, 0] += v
-                else:
-                    out[k] += v * self.w[t]
-        return out
+
+        def ax(lo, hi):
+            return _pt.unpoint(x, self.pixl[lo:hi], None if self.w is None else self.w[lo:hi])
+
+        hits = [np.flatnonzero(self.pixl == p) for p in pixels]
+        return sampled_rows(hits, ax, lambda ts: None if self.w is None else self.w[ts],
+                            self.offsets, self.ivl_filter, self.lags, self.n_s)
 
     def precond(self, r):
         return np.einsum("pab,pb->pa", self.Pinv, r)
@@ -180,6 +139,174 @@ class System:
         L = np.linalg.cholesky(Hk)
         x[keep] = np.linalg.solve(L.T, np.linalg.solve(L, b[keep]))
         return x.reshape(self.n_obs, self.n_s)
+
+
+def pixel_blocks(pixl, w, f0, n_obs, n_s, out=None):
+    """Per pixel: hits, A^T A and A^T W^-1 A blocks [n_obs, n_s, n_s] (W^-1 = diag of N^-1).
+
+    pixl: pixel of each sample (-1 = no row); w: row weights or None (T);
+    f0: f(0) of each sample's filter.  With ``out`` = (hits, AtA, AtWA) the
+    sums are added to it (chunked accumulation).
+    """
+    if out is None:
+        out = (np.zeros(n_obs, dtype=np.int64), np.zeros((n_obs, n_s, n_s)), np.zeros((n_obs, n_s, n_s)))
+    hits, AtA, AtWA = out
+    ok = pixl >= 0
+    p = pixl[ok]
+    h = np.bincount(p, minlength=n_obs)
+    hits += h
+    f = f0[ok]
+    if w is None:
+        AtA[:, 0, 0] += h
+        AtWA[:, 0, 0] += np.bincount(p, weights=f, minlength=n_obs)
+        return out
+    wk = w[ok]
+    for a in range(n_s):
+        for b in range(a, n_s):
+            ww = wk[:, a] * wk[:, b]
+            v = np.bincount(p, weights=ww, minlength=n_obs)
+            vw = np.bincount(p, weights=f * ww, minlength=n_obs)
+            AtA[:, a, b] += v
+            AtWA[:, a, b] += vw
+            if b != a:
+                AtA[:, b, a] += v
+                AtWA[:, b, a] += vw
+    return out
+
+
+def classify_blocks(hits, AtA, AtWA, rcond_excise, rcond_fp64):
+    """Excision, float64 flags and block inverses of the preconditioner (Section 4, Section 5).
+
+    T: a pixel is excised when unobserved; its preconditioner is 1 / (A^T W^-1 A).
+    IQU: excised when hits < 3 or rcond(A^T A) = lambda_min / lambda_max < rcond_excise;
+    flagged float64 when kept with rcond < rcond_fp64; preconditioner (A^T W^-1 A)^-1.
+    """
+    n_obs, n_s = AtA.shape[0], AtA.shape[1]
+    if n_s == 1:
+        wsum = AtWA[:, 0, 0]
+        excised = hits == 0
+        with np.errstate(divide="ignore"):
+            Pinv = np.where(excised, 0.0, 1.0 / wsum).reshape(n_obs, 1, 1)
+        return dict(excised=excised, fp64=np.zeros(n_obs, dtype=bool), rcond=np.ones(n_obs), Pinv=Pinv)
+    ev = np.linalg.eigvalsh(AtA)                    # ascending
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rc = np.where(ev[:, 2] > 0, ev[:, 0] / ev[:, 2], 0.0)
+    excised = (hits < 3) | (rc < rcond_excise)
+    fp64 = (~excised) & (rc < rcond_fp64)
+    Pinv = np.zeros_like(AtWA)
+    good = ~excised
+    Pinv[good] = np.linalg.inv(AtWA[good])
+    return dict(excised=excised, fp64=fp64, rcond=rc, Pinv=Pinv)
+
+
+def sampled_rows(hits, values, w_at, offsets, ivl_filter, lags, n_s):
+    """(A^T N^-1 y)_p for a few pixels, each from Eq. 15 on its own.
+
+    hits[k]: the samples t of pixel k (rows of A that are not zero);
+    values(lo, hi): y on samples lo .. hi-1; w_at(ts): the row weights of
+    samples ts (None for T).  For every t: (N^-1 y)_t = sum over |tau| < n_c
+    inside t's interval of f(|tau|) y_{t+tau}; then weight and sum into p.
+    """
+    n_c = lags.shape[1]
+    out = np.zeros((len(hits), n_s))
+    for k, ts in enumerate(hits):
+        ts = np.asarray(ts, dtype=np.int64)
+        wt = w_at(ts)
+        for m, t in enumerate(ts):
+            i = int(np.searchsorted(offsets, t, side="right") - 1)
+            a, b = int(offsets[i]), int(offsets[i + 1])
+            lo, hi = max(a, t - n_c + 1), min(b, t + n_c)
+            f = lags[ivl_filter[i]][np.abs(np.arange(lo, hi) - t)]
+            v = float(f @ np.asarray(values(lo, hi), dtype=np.float64))
+            if wt is None:
+                out[k, 0] += v
+            else:
+                out[k] += v * wt[m]
+    return out
+
+
+class StreamedSystem:
+    """Sampled rows of H and b for pointing too large for System (same definitions).
+
+    Keeps the caller's int32 pixels and float32 angles by reference and walks
+    them in chunks: the observed-pixel bit array (Section 5.4), the per-pixel
+    blocks and their classification (Section 4) are accumulated chunk by chunk,
+    and rows of H x or b (Eq. 10) are evaluated one pixel at a time from Eq. 15.
+    Nothing of size n_t is held in float64.
+    """
+
+    def __init__(self, pix, psi, n_pix, n_stokes, offsets, ivl_filter, lags,
+                 rcond_excise=1e-6, rcond_fp64=1e-2, chunk=1 << 22):
+        self.pix, self.psi = pix, psi
+        self.n_s = int(n_stokes)
+        self.offsets = np.asarray(offsets, dtype=np.int64)
+        self.ivl_filter = np.asarray(ivl_filter, dtype=np.int64)
+        self.lags = np.atleast_2d(np.asarray(lags, dtype=np.float64))
+        self.n_c = self.lags.shape[1]
+        self.chunk = int(chunk)
+        n_t = int(pix.shape[0])
+        self.n_t = n_t
+        self.obs2glob, self.glob2obs = _pt.observed_pixels(pix, int(n_pix), chunk=self.chunk)
+        self.n_obs = int(self.obs2glob.size)
+        acc = None
+        for lo in range(0, n_t, self.chunk):
+            hi = min(n_t, lo + self.chunk)
+            pl, w, f0 = self._rows(lo, hi, excise=False)
+            acc = pixel_blocks(pl, w, f0, self.n_obs, self.n_s, out=acc)
+        if acc is None:
+            acc = pixel_blocks(np.zeros(0, np.int64), None if self.n_s == 1 else np.zeros((0, 3)),
+                               np.zeros(0), self.n_obs, self.n_s)
+        self.hits = acc[0]
+        c = classify_blocks(*acc, rcond_excise, rcond_fp64)
+        self.excised, self.fp64, self.rcond, self.Pinv = c["excised"], c["fp64"], c["rcond"], c["Pinv"]
+
+    def _rows(self, lo, hi, excise=True):
+        """Observed pixel (excised -> -1 when ``excise``), weights and f(0) of samples lo .. hi-1."""
+        pl = _pt.local_pixels(np.asarray(self.pix[lo:hi]), self.glob2obs)
+        if excise:
+            ok = pl >= 0
+            pl[ok & self.excised[np.where(ok, pl, 0)]] = -1
+        w = _pt.weights(None if self.psi is None else self.psi[lo:hi], self.n_s)
+        i0 = int(np.searchsorted(self.offsets, lo, side="right") - 1)
+        i1 = int(np.searchsorted(self.offsets, hi - 1, side="right") - 1)
+        f0 = np.empty(hi - lo)
+        for i in range(i0, i1 + 1):
+            a, b = max(lo, int(self.offsets[i])), min(hi, int(self.offsets[i + 1]))
+            f0[a - lo:b - lo] = self.lags[self.ivl_filter[i], 0]
+        return pl, w, f0
+
+    def hits_of(self, pixels):
+        """Samples of each observed pixel in ``pixels`` (empty for excised pixels)."""
+        sel = np.full(self.n_obs, -1, dtype=np.int64)
+        sel[np.asarray(pixels, dtype=np.int64)] = np.arange(len(pixels))
+        found = [[] for _ in pixels]
+        for lo in range(0, self.n_t, self.chunk):
+            hi = min(self.n_t, lo + self.chunk)
+            pl = _pt.local_pixels(np.asarray(self.pix[lo:hi]), self.glob2obs)
+            k = np.where(pl >= 0, sel[np.where(pl >= 0, pl, 0)], -1)
+            for t in np.flatnonzero(k >= 0):
+                found[k[t]].append(lo + t)
+        return [np.asarray(f if not self.excised[p] else [], dtype=np.int64) for f, p in zip(found, pixels)]
+
+    def _w_at(self, ts):
+        return None if self.n_s == 1 else _pt.weights(np.asarray(self.psi)[ts], self.n_s)
+
+    def H_sampled(self, x, pixels, hits=None):
+        """(H x)_p for observed pixels p (x over the observed pixels, [n_obs, n_s])."""
+        x = np.asarray(x, dtype=np.float64).reshape(self.n_obs, self.n_s)
+        hits = self.hits_of(pixels) if hits is None else hits
+
+        def ax(lo, hi):
+            pl, w, _ = self._rows(lo, hi)
+            return _pt.unpoint(x, pl, w)
+
+        return sampled_rows(hits, ax, self._w_at, self.offsets, self.ivl_filter, self.lags, self.n_s)
+
+    def rhs_sampled(self, d, pixels, hits=None):
+        """b_p = (A^T N^-1 d)_p for observed pixels p."""
+        hits = self.hits_of(pixels) if hits is None else hits
+        return sampled_rows(hits, lambda lo, hi: d[lo:hi], self._w_at, self.offsets, self.ivl_filter,
+                            self.lags, self.n_s)
 
 
 def pcg(apply_H, apply_P, b, rel_tol, max_iter, keep_history=False):

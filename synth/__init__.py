@@ -10,3 +10,4 @@ other.
 """
 
 from .flat import Problem, make_config, make_flat_problem, config_spec  # noqa: F401
+from .allsky import make_allsky_problem  # noqa: F401

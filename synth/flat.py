@@ -302,17 +302,21 @@ def device_timestreams(problem: Problem, n_rhs: int, seed: int, device="cuda"):
     path (signal from the float32 angles, noise coloured to the PSD with the
     zero-frequency bin set to the first non-zero one), drawn from torch's
     seeded device generator instead of numpy's, so the values differ from the
-    host path while following the same distribution.
+    host path while following the same distribution.  pix, psi and sky may be
+    numpy arrays or torch tensors.
     """
     import torch
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
-    pix = torch.from_numpy(problem.pix.astype(np.int64)).to(device)
+    def dev(a):
+        return a.to(device) if isinstance(a, torch.Tensor) else torch.from_numpy(np.asarray(a)).to(device)
+
+    pix = dev(problem.pix).to(torch.int64)
     ok = pix >= 0
-    sky = torch.from_numpy(problem.sky).to(device)
+    sky = dev(problem.sky).to(torch.float64)
     sig = sky[pix.clamp(min=0), 0]
     if problem.n_stokes == 3:
-        two = 2.0 * torch.from_numpy(problem.psi).to(device).to(torch.float64)
+        two = 2.0 * dev(problem.psi).to(torch.float64)
         sig = sig + sky[pix.clamp(min=0), 1] * torch.cos(two) + sky[pix.clamp(min=0), 2] * torch.sin(two)
     sig = torch.where(ok, sig, torch.zeros_like(sig))
     out = torch.empty((n_rhs, problem.n_samples), dtype=torch.float32, device=device)

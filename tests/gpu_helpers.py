@@ -20,8 +20,12 @@ def make_plan(problem, lags=None, **kw):
     import torch
     from paper_0906_1775_gb300 import Plan
     lags = lib_lags(problem) if lags is None else lags
-    pix = torch.from_numpy(problem.pix).cuda()
-    psi = torch.from_numpy(problem.psi).cuda() if problem.psi is not None else None
+
+    def dev(a):
+        return a.cuda() if isinstance(a, torch.Tensor) else torch.from_numpy(a).cuda()
+
+    pix = dev(problem.pix)
+    psi = dev(problem.psi) if problem.psi is not None else None
     return Plan(pix, psi, problem.n_pix, problem.interval_offsets, problem.interval_filter, lags, **kw)
 
 

@@ -1,0 +1,106 @@
+"""GPU parity on the all-sky ring-scan workload (HEALPix N_side = 512 RING at full size).
+
+Three sizes of the same recipe (synth.allsky): a small one compared with the
+in-memory FP64 oracle on every output (operator, right-hand side, FP64 and
+mixed solves); a medium one (8.4e6 samples, 512 lags, many FFT tiles per
+interval) compared on every operator output; and the full 5.4e8-sample
+workload in the launch configuration the benchmark times, compared on the
+observed-pixel indexing (bit for bit), the excision flags, and sampled rows of
+H x and b that the chunked oracle computes one pixel at a time (Eq. 15).
+Tolerances as in test_gpu_parity.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from tests.gpu_helpers import cuda, host, make_plan
+from tests.helpers import lags_for, rel_rms, system_for
+
+pytestmark = pytest.mark.gpu
+
+FP64_OP_TOL = 1e-11
+FP32_OP_TOL = 2e-5
+FP64_MAP_TOL = 1e-10
+MIXED_MAP_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def small():
+    from synth.allsky import make_allsky_problem
+    p = make_allsky_problem(scale=10, n_det=8, seed=3001)
+    return p, system_for(p)
+
+
+def test_allsky_small_indexing_and_operator(small):
+    import torch
+    p, S = small
+    plan = make_plan(p)
+    o2g, exc = plan.observed()
+    assert np.array_equal(host(o2g).astype(np.int64), S.obs2glob)
+    assert np.array_equal(host(exc).astype(bool), S.excised)
+    x = np.random.default_rng(0).standard_normal((S.n_obs, 3))
+    ref = S.H(x)
+    for prec, tol, dt in [("fp64", FP64_OP_TOL, torch.float64), ("fp32", FP32_OP_TOL, torch.float32)]:
+        y = host(plan.apply_ATNA(cuda(x, dt), precision=prec))[0]
+        assert rel_rms(y, ref) < tol, prec
+        b = host(plan.rhs(cuda(p.d), precision=prec))[0]
+        assert rel_rms(b, S.rhs(p.d[0])) < tol, prec
+
+
+def test_allsky_small_solves(small):
+    p, S = small
+    plan = make_plan(p)
+    x, oi = S.solve(p.d[0], rel_tol=1e-12, max_iter=500)
+    m64, i64 = plan.solve(cuda(p.d[0]), precision="fp64", rel_tol=1e-12, max_iter=500)
+    assert rel_rms(host(m64), x) < FP64_MAP_TOL
+    mm, im = plan.solve(cuda(p.d[0]), precision="mixed", rel_tol=1e-9, max_iter=500, max_outer=10)
+    assert rel_rms(host(mm), x) < MIXED_MAP_TOL
+
+
+def test_allsky_medium_operator():
+    import torch
+    from synth.allsky import make_allsky_problem
+    p = make_allsky_problem(scale=6, n_det=32, seed=3002)
+    S = system_for(p)
+    plan = make_plan(p)
+    st = plan.stats
+    assert st["n_obs"] == S.n_obs and st["n_excised"] == int(S.excised.sum())
+    x = np.random.default_rng(1).standard_normal((S.n_obs, 3))
+    ref = S.H(x)
+    y64 = host(plan.apply_ATNA(cuda(x, torch.float64), precision="fp64"))[0]
+    assert rel_rms(y64, ref) < FP64_OP_TOL
+    y32 = host(plan.apply_ATNA(cuda(x, torch.float32), precision="fp32"))[0]
+    assert rel_rms(y32, ref) < FP32_OP_TOL
+
+
+def test_allsky_full_size_sampled_rows():
+    """The full workload (32 detectors x 2^24 samples) generated on the GPU, planned
+    with the default FFT length and chunking, checked on sampled rows."""
+    import torch
+    from oracle.solver import StreamedSystem
+    from synth.allsky import make_allsky_problem
+    p = make_allsky_problem(scale=0, device="cuda", seed=3000)
+    plan = make_plan(p)
+    pix_h, psi_h = host(p.pix), host(p.psi)
+    T = StreamedSystem(pix_h, psi_h, p.n_pix, 3, p.interval_offsets, p.interval_filter,
+                       lags_for(p), chunk=1 << 23)
+    o2g, exc = plan.observed()
+    assert np.array_equal(host(o2g).astype(np.int64), T.obs2glob)
+    assert np.array_equal(host(exc).astype(bool), T.excised)
+    rng = np.random.default_rng(5)
+    keep = np.flatnonzero((~T.excised) & (T.hits <= 1500))
+    pk = rng.choice(keep, 8, replace=False)
+    hits = T.hits_of(pk)
+    x = rng.standard_normal((T.n_obs, 3))
+    x[T.excised] = 0.0
+    ref = T.H_sampled(x, pk, hits)
+    y64 = host(plan.apply_ATNA(cuda(x, torch.float64), precision="fp64"))[0]
+    assert rel_rms(y64[pk], ref) < FP64_OP_TOL
+    y32 = host(plan.apply_ATNA(cuda(x, torch.float32), precision="fp32"))[0]
+    assert rel_rms(y32[pk], ref) < 1e-4
+    d_h = host(p.d[0])
+    bref = T.rhs_sampled(d_h, pk, hits)
+    b64 = host(plan.rhs(p.d, precision="fp64"))[0]
+    assert rel_rms(b64[pk], bref) < FP64_OP_TOL
