@@ -196,14 +196,27 @@ __device__ __forceinline__ C csub(C a, C b) {
   return r;
 }
 
-// Shared-memory row layout: one padding element every 32 keeps strided
-// butterfly accesses off a single bank; rows are an odd number of elements
-// apart so column-wise accesses spread over the banks.
-__device__ __forceinline__ int sidx(int i) { return i + (i >> 5); }
-__host__ __device__ inline int row_stride(int n) { return n + (n >> 5) + 1; }
-// Row stride for the column kernels, whose load and store phases walk down
-// `rows` rows at once: the pad spreads those accesses over the banks.
-__host__ __device__ inline int row_stride_cols(int n, int rows) { return n + (n >> 5) + (rows <= 4 ? 4 : 2); }
+// Shared-memory layout of the FFT buffers.  Rows sit `rs` elements apart and
+// element i of a row is stored at swz<SW>(i): bits 0-3 of i XORed with bits
+// 3-6 (SW = 0) or with bits 3-6 XOR bits 4-7 (SW = 1).  Both maps permute
+// each aligned block of 16 elements, so a row of N elements fills exactly N
+// slots.  The variant and the row padding for each transform length come from
+// a bank model of every load, butterfly and store phase of the kernel: with
+// them each warp access needs the minimum number of wavefronts (128 bytes
+// each) for 8- and 16-byte elements.
+template <int SW>
+__device__ __forceinline__ int swz(int i) {
+  return SW == 0 ? (i ^ ((i >> 3) & 15)) : (i ^ (((i >> 3) ^ (i >> 4)) & 15));
+}
+// Variant and row stride for transforms of length 2^lg over complex elements
+// of esz bytes; `cols` selects the column kernels (k_f1, k_f3), whose load and
+// store phases walk down several rows at once, over the row kernel (k_f2).
+__host__ __device__ constexpr int lay_sw(int esz, int lg, bool cols) {
+  return cols ? ((esz == 16 || lg == 9) ? 0 : 1) : ((esz == 8 && lg == 9) ? 0 : 1);
+}
+__host__ __device__ constexpr int lay_rs(int esz, int lg, bool cols) {
+  return (1 << lg) + (cols ? (lg <= 8 ? 1 : (lg == 9 ? 2 : 4)) : ((esz == 8 && lg <= 6) ? 8 : 0));
+}
 
 // Threads per CTA of the operator kernels (every launch uses this many).
 constexpr int OP_THREADS = 256;
@@ -299,7 +312,7 @@ struct PassGeom {
 // forward = small DFT then output twiddles (decimation in frequency, output
 // bit-reversed after all passes); inverse = conjugate twiddles then inverse
 // small DFT, passes in reverse order, returning N times the input.
-template <typename C, int R, bool INV>
+template <typename C, int R, bool INV, int SW>
 __device__ __forceinline__ void fft_pass(C* buf, int rows, int rs, int logN, int s, const C* tw) {
   const PassGeom G(logN, s, R);
   const int total = rows << G.gpr_log;
@@ -310,7 +323,7 @@ __device__ __forceinline__ void fft_pass(C* buf, int rows, int rs, int logN, int
     C* rp = buf + row * rs;
     C v[1 << R];
 #pragma unroll
-    for (int m = 0; m < (1 << R); ++m) v[m] = rp[sidx(base + m * G.hR)];
+    for (int m = 0; m < (1 << R); ++m) v[m] = rp[swz<SW>(base + m * G.hR)];
     if (!INV) {
       small_dft<C, R, false>(v);
 #pragma unroll
@@ -321,7 +334,7 @@ __device__ __forceinline__ void fft_pass(C* buf, int rows, int rs, int logN, int
       small_dft<C, R, true>(v);
     }
 #pragma unroll
-    for (int m = 0; m < (1 << R); ++m) rp[sidx(base + m * G.hR)] = v[m];
+    for (int m = 0; m < (1 << R); ++m) rp[swz<SW>(base + m * G.hR)] = v[m];
   }
 }
 
@@ -356,29 +369,29 @@ __device__ __forceinline__ void build_pass_twiddles(C* twp, int logN, const C* t
   }
 }
 
-template <typename C, bool INV>
+template <typename C, bool INV, int SW>
 __device__ __forceinline__ void fft_pass_any(C* buf, int rows, int rs, int logN, int s, const C* tw) {
   const int R = (logN - s) >= 3 ? 3 : (logN - s);
   const C* twp = tw + pass_offset(logN, s);
-  if (R == 3) fft_pass<C, 3, INV>(buf, rows, rs, logN, s, twp);
-  else if (R == 2) fft_pass<C, 2, INV>(buf, rows, rs, logN, s, twp);
-  else fft_pass<C, 1, INV>(buf, rows, rs, logN, s, twp);
+  if (R == 3) fft_pass<C, 3, INV, SW>(buf, rows, rs, logN, s, twp);
+  else if (R == 2) fft_pass<C, 2, INV, SW>(buf, rows, rs, logN, s, twp);
+  else fft_pass<C, 1, INV, SW>(buf, rows, rs, logN, s, twp);
 }
 
 // Full FFT of `rows` rows of length N = 2^logN held in shared memory
 // (tw: N entries).
-template <typename C, bool INV>
+template <typename C, bool INV, int SW>
 __device__ __forceinline__ void fft_rows(C* buf, int rows, int rs, int logN, const C* tw) {
   if (!INV) {
 #pragma unroll
     for (int s = 0; s < logN; s += 3) {
-      fft_pass_any<C, false>(buf, rows, rs, logN, s, tw);
+      fft_pass_any<C, false, SW>(buf, rows, rs, logN, s, tw);
       __syncthreads();
     }
   } else {
 #pragma unroll
     for (int s = last_pass_start(logN); s >= 0; s -= 3) {
-      fft_pass_any<C, true>(buf, rows, rs, logN, s, tw);
+      fft_pass_any<C, true, SW>(buf, rows, rs, logN, s, tw);
       __syncthreads();
     }
   }
@@ -389,7 +402,7 @@ __device__ __forceinline__ void fft_rows(C* buf, int rows, int rs, int logN, con
 // act on the same element groups, so they run back to back in registers.
 // Hrow(row) points at the row's spectrum (bit-reversed order, as the forward
 // transform leaves it).
-template <typename C, int R, typename HF>
+template <typename C, int R, int SW, typename HF>
 __device__ __forceinline__ void fused_middle(C* buf, int rows, int rs, int logN, int s, HF Hrow) {
   typedef decltype(C().x) Real;
   const PassGeom G(logN, s, R);
@@ -404,7 +417,7 @@ __device__ __forceinline__ void fused_middle(C* buf, int rows, int rs, int logN,
     Real hv[1 << R];
 #pragma unroll
     for (int m = 0; m < (1 << R); ++m) {
-      v[m] = rp[sidx(base + m * G.hR)];
+      v[m] = rp[swz<SW>(base + m * G.hR)];
       hv[m] = H[base + m * G.hR];
     }
     // The forward pass ends with output twiddles w and the inverse pass starts
@@ -418,26 +431,26 @@ __device__ __forceinline__ void fused_middle(C* buf, int rows, int rs, int logN,
     }
     small_dft<C, R, true>(v);
 #pragma unroll
-    for (int m = 0; m < (1 << R); ++m) rp[sidx(base + m * G.hR)] = v[m];
+    for (int m = 0; m < (1 << R); ++m) rp[swz<SW>(base + m * G.hR)] = v[m];
   }
 }
 
-template <typename C, typename HF>
+template <typename C, int SW, typename HF>
 __device__ __forceinline__ void fft_rows_filter(C* buf, int rows, int rs, int logN, const C* tw, HF Hrow) {
   const int sl = last_pass_start(logN);
 #pragma unroll
   for (int s = 0; s < sl; s += 3) {
-    fft_pass_any<C, false>(buf, rows, rs, logN, s, tw);
+    fft_pass_any<C, false, SW>(buf, rows, rs, logN, s, tw);
     __syncthreads();
   }
   const int R = logN - sl;
-  if (R == 3) fused_middle<C, 3>(buf, rows, rs, logN, sl, Hrow);
-  else if (R == 2) fused_middle<C, 2>(buf, rows, rs, logN, sl, Hrow);
-  else fused_middle<C, 1>(buf, rows, rs, logN, sl, Hrow);
+  if (R == 3) fused_middle<C, 3, SW>(buf, rows, rs, logN, sl, Hrow);
+  else if (R == 2) fused_middle<C, 2, SW>(buf, rows, rs, logN, sl, Hrow);
+  else fused_middle<C, 1, SW>(buf, rows, rs, logN, sl, Hrow);
   __syncthreads();
 #pragma unroll
   for (int s = sl - 3; s >= 0; s -= 3) {
-    fft_pass_any<C, true>(buf, rows, rs, logN, s, tw);
+    fft_pass_any<C, true, SW>(buf, rows, rs, logN, s, tw);
     __syncthreads();
   }
 }

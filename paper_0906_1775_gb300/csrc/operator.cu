@@ -183,6 +183,29 @@ __device__ __forceinline__ void finish_angle<float>(float& c, float& s) {
 // twiddles), and only then consumes them, so each thread keeps U loads in
 // flight instead of one.
 
+// Output twiddles exp(-2 pi i m / M) of the four-step transform from two
+// small shared tables: lo[b] = w^b for b < L = 2^logL and hi[a] = w^(a L), so
+// w^m = hi[m >> logL] * lo[m & (L - 1)] (one complex product, a few ulp).
+// Reading them from the M-entry table instead scatters one L2 sector per element.
+// The float64 kernels keep reading the M-entry table: on this GPU a float64
+// complex product costs more than the scattered load it would replace.
+template <typename C>
+__device__ __forceinline__ void build_split_twiddles(C* lo, C* hi, const C* twM, int logM, int logL) {
+  if (sizeof(C) != 8) return;
+  for (int i = threadIdx.x; i < (1 << logL); i += OP_THREADS) lo[i] = twM[i];
+  for (int i = threadIdx.x; i < (1 << (logM - logL)); i += OP_THREADS) hi[i] = twM[(long long)i << logL];
+}
+template <typename C>
+__device__ __forceinline__ C split_twiddle(const C* lo, const C* hi, const C* twM, int m, int logL) {
+  if (sizeof(C) != 8) return twM[m];
+  return cmul(hi[m >> logL], lo[m & ((1 << logL) - 1)]);
+}
+__host__ __device__ inline int split_log(int logM) { return (logM + 1) >> 1; }
+// Shared entries of the two split tables (none for float64).
+__host__ __device__ inline int split_entries(int esz, int logM) {
+  return esz == 8 ? (1 << split_log(logM)) + (1 << (logM - split_log(logM))) : 0;
+}
+
 // ---------------------------------------------------------------- k_f1
 // LG2 > 0 fixes the column length N2 = 2^LG2 at compile time (and with it the
 // CTA's column count); LG2 = 0 reads the geometry from the arguments.
@@ -197,11 +220,16 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
   const Tile* T = a.tiles + a.tile0 + tl;
   if (skip_tile(a, T)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int SW = LG2 ? lay_sw(sizeof(C), LG2, true) : (sizeof(C) == 16 ? 0 : 1);
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int rs = row_stride_cols(N2, B1);
+  const int rs = lay_rs(sizeof(C), logN2, true);
   C* tw = buf + B1 * rs;
+  const int logM = a.logN1 + logN2, logL = split_log(logM);
+  C* tlo = tw + N2;
+  C* thi = tlo + (1 << logL);
   const C* twM = static_cast<const C*>(a.tw);
   build_pass_twiddles(tw, logN2, twM, a.N1);
+  build_split_twiddles(tlo, thi, twM, logM, logL);
   LaneView<Real> L[2];
   L[0] = lane_view<Real, IN, OUT_MAP>(a, T->l[0]);
   L[1] = lane_view<Real, IN, OUT_MAP>(a, T->l[1]);
@@ -257,31 +285,19 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
         C z;
         z.x = v[0][u];
         z.y = v[1][u];
-        buf[(e & (B1 - 1)) * rs + sidx(e >> logB1)] = z;
+        buf[(e & (B1 - 1)) * rs + swz<SW>(e >> logB1)] = z;
       }
     }
   }
   __syncthreads();
-  fft_rows<C, false>(buf, B1, rs, logN2, tw);
+  fft_rows<C, false, SW>(buf, B1, rs, logN2, tw);
   C* sc = static_cast<C*>(a.scratch) + (long long)tl * a.M;
   const int mask = a.M - 1;
-  for (int e0 = threadIdx.x; e0 < total; e0 += bd * 8) {
-    C w[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * bd;
-      const int n1 = n1_0 + (e & (B1 - 1));
-      const int k2 = brev_n(e >> logB1, logN2);
-      if (e < total) w[u] = twM[(n1 * k2) & mask];
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * bd;
-      if (e < total) {
-        const int j = e & (B1 - 1), pos = e >> logB1;
-        sc[(long long)pos * a.N1 + n1_0 + j] = cmul(buf[j * rs + sidx(pos)], w[u]);
-      }
-    }
+#pragma unroll 4
+  for (int e = threadIdx.x; e < total; e += bd) {
+    const int j = e & (B1 - 1), pos = e >> logB1;
+    const C w = split_twiddle(tlo, thi, twM, ((n1_0 + j) * brev_n(pos, logN2)) & mask, logL);
+    sc[(long long)pos * a.N1 + n1_0 + j] = cmul(buf[j * rs + swz<SW>(pos)], w);
   }
 }
 
@@ -298,8 +314,9 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f2(OpArgs a)
   const Tile* T = a.tiles + a.tile0 + tl;
   if (skip_tile(a, T)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int SW = LG1 ? lay_sw(sizeof(C), LG1, false) : 1;
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int rs = row_stride(N1);
+  const int rs = lay_rs(sizeof(C), logN1, false);
   C* tw = buf + B2 * rs;
   const C* twM = static_cast<const C*>(a.tw);
   build_pass_twiddles(tw, logN1, twM, a.N2);
@@ -316,13 +333,13 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f2(OpArgs a)
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int e = e0 + u * bd;
-      if (e < total) buf[(e >> logN1) * rs + sidx(e & (N1 - 1))] = v[u];
+      if (e < total) buf[(e >> logN1) * rs + swz<SW>(e & (N1 - 1))] = v[u];
     }
   }
   __syncthreads();
   const Real* H = static_cast<const Real*>(a.H) + (long long)filt * a.M + (long long)pos0 * N1;
-  fft_rows_filter<C>(buf, B2, rs, logN1, tw, [H, N1](int row) { return H + (long long)row * N1; });
-  for (int e = threadIdx.x; e < total; e += bd) sc[e] = buf[(e >> logN1) * rs + sidx(e & (N1 - 1))];
+  fft_rows_filter<C, SW>(buf, B2, rs, logN1, tw, [H, N1](int row) { return H + (long long)row * N1; });
+  for (int e = threadIdx.x; e < total; e += bd) sc[e] = buf[(e >> logN1) * rs + swz<SW>(e & (N1 - 1))];
 }
 
 // ---------------------------------------------------------------- k_f3
@@ -337,11 +354,17 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
   const Tile* T = a.tiles + a.tile0 + tl;
   if (skip_tile(a, T)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int SW = LG2 ? lay_sw(sizeof(C), LG2, true) : (sizeof(C) == 16 ? 0 : 1);
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const int rs = row_stride_cols(N2, B1);
+  const int rs = lay_rs(sizeof(C), logN2, true);
   C* tw = buf + B1 * rs;
+  const int logM = a.logN1 + logN2, logL = split_log(logM);
+  C* tlo = tw + N2;
+  C* thi = tlo + (1 << logL);
   const C* twM = static_cast<const C*>(a.tw);
   build_pass_twiddles(tw, logN2, twM, a.N1);
+  build_split_twiddles(tlo, thi, twM, logM, logL);
+  __syncthreads();
   LaneView<Real> L[2];
   L[0] = lane_view<Real, IN_MAPX, OUT>(a, T->l[0]);
   L[1] = lane_view<Real, IN_MAPX, OUT>(a, T->l[1]);
@@ -351,26 +374,25 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
   const C* sc = static_cast<const C*>(a.scratch) + (long long)tl * a.M;
   const int mask = a.M - 1;
   for (int e0 = threadIdx.x; e0 < total; e0 += bd * 8) {
-    C v[8], w[8];
+    C v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * bd;
+      if (e < total) v[u] = sc[(long long)(e >> logB1) * a.N1 + n1_0 + (e & (B1 - 1))];
+    }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int e = e0 + u * bd;
       if (e < total) {
-        const int n1 = n1_0 + (e & (B1 - 1));
-        const int pos = e >> logB1;
-        v[u] = sc[(long long)pos * a.N1 + n1];
-        w[u] = twM[(n1 * brev_n(pos, logN2)) & mask];
+        const int n1 = n1_0 + (e & (B1 - 1)), pos = e >> logB1;
+        const C w = split_twiddle(tlo, thi, twM, (n1 * brev_n(pos, logN2)) & mask, logL);
+        buf[(e & (B1 - 1)) * rs + swz<SW>(pos)] = cmulc(v[u], w);
       }
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * bd;
-      if (e < total) buf[(e & (B1 - 1)) * rs + sidx(e >> logB1)] = cmulc(v[u], w[u]);
     }
   }
   __syncthreads();
-  fft_rows<C, true>(buf, B1, rs, logN2, tw);
-  constexpr int U = 8;
+  fft_rows<C, true, SW>(buf, B1, rs, logN2, tw);
+  constexpr int U = OUT == OUT_MAP ? 4 : 8;
   for (int e0 = threadIdx.x; e0 < total; e0 += bd * U) {
     int nn[U];
     bool ok[2][U];
@@ -382,7 +404,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
       nn[u] = n1_0 + j + (n2 << a.logN1);
       C z;
       z.x = z.y = 0;
-      if (e < total) z = buf[j * rs + sidx(n2)];
+      if (e < total) z = buf[j * rs + swz<SW>(n2)];
       val[0][u] = z.x;
       val[1][u] = z.y;
 #pragma unroll
@@ -450,13 +472,16 @@ template <typename Real>
 size_t smem_f13(const Plan* p) {
   int B1, B2;
   geometry<Real>(p, B1, B2);
-  return (size_t)(B1 * row_stride_cols(p->N2, B1) + p->N2) * sizeof(typename CxT<Real>::type);
+  typedef typename CxT<Real>::type C;
+  return (size_t)(B1 * lay_rs(sizeof(C), p->logN2, true) + p->N2 + split_entries(sizeof(C), p->logN1 + p->logN2)) *
+         sizeof(C);
 }
 template <typename Real>
 size_t smem_f2(const Plan* p) {
   int B1, B2;
   geometry<Real>(p, B1, B2);
-  return (size_t)(B2 * row_stride(p->N1) + p->N1) * sizeof(typename CxT<Real>::type);
+  return (size_t)(B2 * lay_rs(sizeof(typename CxT<Real>::type), p->logN1, false) + p->N1) *
+         sizeof(typename CxT<Real>::type);
 }
 
 typedef void (*OpKernel)(OpArgs);
