@@ -56,7 +56,12 @@ typedef enum {
 typedef enum {
   MADMAP_FP64 = 0,   /* operator, vectors and scalars in float64 */
   MADMAP_MIXED = 1,  /* float32 operator and vectors inside float64 iterative refinement */
-  MADMAP_FP32 = 2    /* float32 operator (madmap_apply_ATNA / madmap_apply_ninv / madmap_rhs only) */
+  MADMAP_FP32 = 2,   /* float32 operator (madmap_apply_ATNA / madmap_apply_ninv / madmap_rhs only) */
+  MADMAP_DF64 = 3    /* double-float operator: every product and sum on pairs of float32 numbers
+                        (about 48 significant bits), float64 maps in and out.  Accepted by
+                        madmap_apply_ATNA, madmap_rhs and madmap_time_operator, and as
+                        madmap_solve_opts.refine_precision.  Not in the paper: GB300 runs float32
+                        arithmetic many times faster than float64. */
 } madmap_precision;
 
 /* Description of the data a plan is built over.  Section 3 (data model),
@@ -115,6 +120,9 @@ typedef struct {
                               iters_per_sync iterations replayed as graphs with host checks
                               between them; 0: direct launches with host checks */
   int32_t iters_per_sync;  /* iterations enqueued between host checks (modes 0 and 1), default 8 */
+  int32_t refine_precision; /* MIXED: arithmetic of the right-hand side b = A^T N^-1 d and of the
+                              refinement residuals b - H x: MADMAP_DF64 (default) or MADMAP_FP64.
+                              Vectors, dot products and the refinement update stay float64. */
 } madmap_solve_opts;
 
 typedef struct {
@@ -122,7 +130,8 @@ typedef struct {
   int32_t iters;           /* PCG iterations performed (sum of inner iterations for MIXED) */
   int32_t outer_iters;     /* MIXED refinement steps (FP64: 1) */
   int32_t best_iter;       /* iteration count at which the returned iterate was produced */
-  int32_t fp64_applies;    /* float64 operator applications, including the right-hand side */
+  int32_t fp64_applies;    /* full-precision operator applications (float64, or double-float per
+                              refine_precision), including the right-hand side */
   int32_t fp32_applies;    /* float32 operator applications */
   double final_rel_res;    /* last relative residual ||b - H x_k|| / ||b|| (recursive for FP64) */
   double best_rel_res;     /* relative residual of the returned map */

@@ -16,7 +16,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (MADMAP_FP32, MADMAP_FP64, MADMAP_MIXED, MadmapError, check, load)  # noqa: F401
+from ._lib import (MADMAP_DF64, MADMAP_FP32, MADMAP_FP64, MADMAP_MIXED, MadmapError, check, load)  # noqa: F401
 
 __all__ = ["Plan", "noise_filter", "paper_fft_length", "MadmapError", "load", "library_path",
            "madmap_plan_create", "madmap_plan_destroy", "madmap_plan_get_stats", "madmap_plan_observed",
@@ -25,8 +25,8 @@ __all__ = ["Plan", "noise_filter", "paper_fft_length", "MadmapError", "load", "l
            "madmap_noise_filter", "madmap_paper_fft_length", "madmap_last_error", "madmap_kernel_launch_count",
            "madmap_time_operator", "madmap_apply_ninv_noalloc"]
 
-_PREC = {"fp64": MADMAP_FP64, "mixed": MADMAP_MIXED, "fp32": MADMAP_FP32,
-         MADMAP_FP64: MADMAP_FP64, MADMAP_MIXED: MADMAP_MIXED, MADMAP_FP32: MADMAP_FP32}
+_PREC = {"fp64": MADMAP_FP64, "mixed": MADMAP_MIXED, "fp32": MADMAP_FP32, "df64": MADMAP_DF64,
+         MADMAP_FP64: MADMAP_FP64, MADMAP_MIXED: MADMAP_MIXED, MADMAP_FP32: MADMAP_FP32, MADMAP_DF64: MADMAP_DF64}
 
 
 def library_path() -> str:
@@ -245,7 +245,7 @@ class Plan:
     def apply_ATNA(self, x, precision="fp64", stream=None):
         torch = _torch()
         prec = _PREC[precision]
-        dt = torch.float64 if prec == MADMAP_FP64 else torch.float32
+        dt = torch.float32 if prec == MADMAP_FP32 else torch.float64
         x = x.reshape(-1, self.n_obs, self.n_stokes)
         y = torch.empty_like(x)
         madmap_apply_ATNA(self._h, prec, x.shape[0], _dev_ptr(x, dt, "x"), y.data_ptr(), stream)
@@ -255,7 +255,7 @@ class Plan:
         torch = _torch()
         prec = _PREC[precision]
         d = d.reshape(-1, self.n_samples)
-        b = torch.empty(self._map_shape(d.shape[0]), dtype=torch.float64 if prec == MADMAP_FP64 else torch.float32,
+        b = torch.empty(self._map_shape(d.shape[0]), dtype=torch.float32 if prec == MADMAP_FP32 else torch.float64,
                         device=d.device)
         madmap_rhs(self._h, prec, d.shape[0], _dev_ptr(d, torch.float32, "d"), b.data_ptr(), stream)
         return b
@@ -270,20 +270,22 @@ class Plan:
         return w
 
     @staticmethod
-    def _opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync):
+    def _opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync, refine="df64"):
         o = _lib.madmap_solve_opts()
         o.max_iter, o.rel_tol, o.precision = int(max_iter), float(rel_tol), _PREC[precision]
         o.max_outer, o.inner_rel_tol = int(max_outer), float(inner_rel_tol)
         o.use_graph, o.iters_per_sync = (2 if use_graph is True else int(use_graph)), int(iters_per_sync)
+        o.refine_precision = _PREC[refine]
         return o
 
     def solve_batched(self, d, precision="fp64", max_iter=50, rel_tol=1e-6, max_outer=10, inner_rel_tol=1e-4,
-                      use_graph=True, iters_per_sync=8, out=None, stream=None):
-        """Maps [n_rhs, n_obs, n_stokes] (float64) for d [n_rhs, n_samples], and per-rhs info dicts."""
+                      use_graph=True, iters_per_sync=8, out=None, stream=None, refine="df64"):
+        """Maps [n_rhs, n_obs, n_stokes] (float64) for d [n_rhs, n_samples], and per-rhs info dicts.
+        refine ("df64" or "fp64"): arithmetic of the mixed solve's right-hand side and residuals."""
         torch = _torch()
         d = d.reshape(-1, self.n_samples)
         n_rhs = d.shape[0]
-        o = self._opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync)
+        o = self._opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync, refine)
         m = out if out is not None else torch.empty((n_rhs, self.n_obs, self.n_stokes), dtype=torch.float64,
                                                     device="cuda")
         infos = madmap_solve_batched(self._h, n_rhs, _dev_ptr(d, torch.float32, "d") if d.numel() else None,
@@ -292,11 +294,11 @@ class Plan:
 
     def solve_backward(self, d, m, grad_m, want_d=True, want_lags=True, precision="mixed", max_iter=500,
                        rel_tol=1e-10, max_outer=20, inner_rel_tol=1e-4, use_graph=True, iters_per_sync=8,
-                       stream=None):
+                       stream=None, refine="df64"):
         """(dL/dd float32 [n_samples] or None, dL/dlags float64 [n_filters, n_lags] or None, info) for the
         map m of data d and grad_m = dL/dm, by one adjoint solve."""
         torch = _torch()
-        o = self._opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync)
+        o = self._opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync, refine)
         gd = torch.empty(self.n_samples, dtype=torch.float32, device="cuda") if want_d else None
         gl = (torch.empty((self.stats["n_filters"], self.stats["n_lags"]), dtype=torch.float64, device="cuda")
               if want_lags else None)
@@ -307,10 +309,11 @@ class Plan:
         return gd, gl, {k: getattr(info, k) for k, _ in info._fields_}
 
     def solve(self, d, precision="fp64", max_iter=50, rel_tol=1e-6, max_outer=10, inner_rel_tol=1e-4,
-              use_graph=True, iters_per_sync=8, out=None, stream=None):
-        """Maximum-likelihood map [n_obs, n_stokes] (float64) and the solve info dict."""
+              use_graph=True, iters_per_sync=8, out=None, stream=None, refine="df64"):
+        """Maximum-likelihood map [n_obs, n_stokes] (float64) and the solve info dict.
+        refine ("df64" or "fp64"): arithmetic of the mixed solve's right-hand side and residuals."""
         torch = _torch()
-        o = self._opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync)
+        o = self._opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync, refine)
         m = out if out is not None else torch.empty((self.n_obs, self.n_stokes), dtype=torch.float64,
                                                     device="cuda")
         info = madmap_solve(self._h, _dev_ptr(d.reshape(-1), torch.float32, "d"), _dev_ptr(m, torch.float64, "m"),

@@ -24,6 +24,7 @@ MADMAP_ERR_INTERNAL = -6
 MADMAP_FP64 = 0
 MADMAP_MIXED = 1
 MADMAP_FP32 = 2
+MADMAP_DF64 = 3
 
 STATUS_NAMES = {0: "OK", 1: "WARN_MAXITER", -1: "ERR_INVALID_ARG", -2: "ERR_CUDA", -3: "ERR_OOM",
                 -4: "ERR_NOT_PD", -5: "ERR_TIMEOUT", -6: "ERR_INTERNAL"}
@@ -47,7 +48,8 @@ class madmap_plan_stats(C.Structure):
 class madmap_solve_opts(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("rel_tol", C.c_double), ("precision", C.c_int32),
                 ("max_outer", C.c_int32), ("inner_rel_tol", C.c_double), ("use_graph", C.c_int32),
-                ("iters_per_sync", C.c_int32)]
+                ("iters_per_sync", C.c_int32),
+                ("refine_precision", C.c_int32)]
 
 
 class madmap_solve_info(C.Structure):

@@ -54,6 +54,51 @@ struct TileSet {
   int n_rhs = 0;
 };
 
+// ---------------------------------------------------------------- double-float
+// A double-float number is the unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi) / 2: about 48 significant bits from float32 arithmetic.
+// Sums use Knuth's two-sum for the high parts, products Dekker's exact
+// product through a fused multiply-add; the error terms are folded in once
+// and renormalised (the double-double scheme of Hida, Li and Bailey, 2001,
+// at float width).  The intrinsics keep the compiler from contracting the
+// error-free steps.  On GB300 these run at the float32 rate, far above the
+// float64 rate.
+struct __align__(8) df64 {
+  float hi, lo;
+  __host__ __device__ constexpr df64() : hi(0.f), lo(0.f) {}
+  __host__ __device__ constexpr df64(int v) : hi((float)v), lo(0.f) {}
+  __host__ __device__ constexpr df64(float v) : hi(v), lo(0.f) {}
+  __host__ __device__ constexpr df64(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+  __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+};
+struct __align__(16) cdf64 {
+  df64 x, y;
+};
+__host__ __device__ inline double to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ df64 df_renorm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return df64(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return df_renorm(s, e);
+}
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_renorm(p, e);
+}
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
+__device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b; }
+__device__ __forceinline__ df64& operator*=(df64& a, df64 b) { return a = a * b; }
+
 // ---------------------------------------------------------------- plan
 struct SolveBuffers;  // solver.cu
 
@@ -85,6 +130,9 @@ struct Plan {
   float* H32 = nullptr;
   double2* tw64 = nullptr;         // [M] exp(-2 pi i j / M)
   float2* tw32 = nullptr;
+  df64* Hdf = nullptr;             // [n_filters][M] H64 as double-float pairs
+  cdf64* twdf = nullptr;           // [M] tw64 as double-float pairs
+  float4* csdf = nullptr;          // [n_t] cs64 as double-float pairs (IQU)
   void* scratch = nullptr;         // tiles_per_chunk * M complex (float64 size)
   int* dev_flag = nullptr;         // small device flag words
   size_t device_bytes = 0;
@@ -111,26 +159,30 @@ inline madmap_status dalloc_t(Plan* p, T** ptr, size_t count) {
 }
 
 // ---------------------------------------------------------------- operator launch
+// Arithmetic of an operator application: float32, float64, or double-float
+// (float pairs; maps and outputs in float64, the input map pre-split into pairs).
+enum { OPP_F32 = 0, OPP_F64 = 1, OPP_DF64 = 2 };
 enum { IN_MAP = 0, IN_TOD = 1, IN_TOD_REAL = 2 };
 enum { OUT_MAP = 0, OUT_TOD = 1 };
 
 // Runs the three-kernel noise-weighting pipeline over the plan's tiles with
 // input taken from a map (gather, y = A x) or a timestream, and output
 // scattered into a map (A^T w, accumulated: caller zeroes it) or written to a
-// timestream.  in/out element types follow `fp64`.  `skip` (device int, may be
+// timestream.  in/out element types follow `prec` (OPP_DF64: input map of
+// df64 pairs or float timestream, output float64 map).  `skip` (device int, may be
 // NULL) makes every kernel return at once when non-zero.  n_rhs == 0 only sets
 // kernel attributes (call it before a stream capture).
-madmap_status op_launch(Plan* p, bool fp64, int in_mode, int out_mode, const void* in, void* out,
+madmap_status op_launch(Plan* p, int prec, int in_mode, int out_mode, const void* in, void* out,
                         long long in_stride, long long out_stride, int n_rhs, const int* skip,
                         cudaStream_t s);
 
-size_t f1_smem_bytes(const Plan* p, bool fp64);
+size_t f1_smem_bytes(const Plan* p, int prec);
 
 // Per-kernel event timing of the map-to-map operator (ms[3]: mean per launch).
-madmap_status op_time(Plan* p, bool fp64, const void* in, void* out, int reps, double ms[3], cudaStream_t s);
+madmap_status op_time(Plan* p, int prec, const void* in, void* out, int reps, double ms[3], cudaStream_t s);
 
 // Resident CTAs per SM of the operator kernels and CTAs per tile.
-void op_occupancy(const Plan* p, bool fp64, int& ctas_per_sm, int& ctas_per_tile);
+void op_occupancy(const Plan* p, int prec, int& ctas_per_sm, int& ctas_per_tile);
 
 // Number of operator launches per application and tiles per launch.
 void chunking(const Plan* p, int& n_chunks, int& per_chunk, int n_tiles = -1);
@@ -138,7 +190,7 @@ void chunking(const Plan* p, int& n_chunks, int& per_chunk, int n_tiles = -1);
 // The operator over a tile set (lanes carry their rhs; per-rhs strides in
 // elements; skip[rhs * skip_stride], if skip is not NULL, marks right-hand
 // sides whose tiles need no work).
-madmap_status op_launch_set(Plan* p, bool fp64, int in_mode, int out_mode, const void* in, void* out,
+madmap_status op_launch_set(Plan* p, int prec, int in_mode, int out_mode, const void* in, void* out,
                             long long in_stride, long long out_stride, const int* skip, int skip_stride,
                             const TileSet* ts, cudaStream_t s);
 
@@ -166,6 +218,10 @@ __host__ __device__ inline int ilog2(unsigned v) {
 template <typename R> struct CxT;
 template <> struct CxT<float> { typedef float2 type; };
 template <> struct CxT<double> { typedef double2 type; };
+template <> struct CxT<df64> { typedef cdf64 type; };
+// Element type of the maps and timestreams an operator instance writes.
+template <typename R> struct OutT { typedef R type; };
+template <> struct OutT<df64> { typedef double type; };
 
 template <typename C>
 __device__ __forceinline__ C cmul(C a, C b) {
@@ -226,7 +282,7 @@ constexpr int OP_THREADS = 256;
 template <int K, bool CONJ, typename C>
 __device__ __forceinline__ C mul_w8(C v) {
   typedef decltype(v.x) R;
-  const R h = (R)0.70710678118654752440;
+  constexpr R h = R(0.70710678118654752440);
   C r;
   if (K == 0) return v;
   if (K == 2) {  // -i (conj: +i)

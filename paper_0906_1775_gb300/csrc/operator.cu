@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -41,6 +42,7 @@ struct OpArgs {
   const int* pix;
   const float* psi;
   const double2* cs64;
+  const float4* csdf;
   const void* in;
   long long in_stride;
   void* out;
@@ -93,8 +95,20 @@ __device__ __forceinline__ double gather<double, 3>(const double* x, int p, doub
   return u.x + u.y * c + v.x * s;
 }
 
+// double-float: the map holds float pairs ([n_obs][4] pairs for IQU)
+template <>
+__device__ __forceinline__ df64 gather<df64, 1>(const df64* x, int p, df64, df64) {
+  return x[p];
+}
+template <>
+__device__ __forceinline__ df64 gather<df64, 3>(const df64* x, int p, df64 c, df64 s) {
+  const float4* xp = reinterpret_cast<const float4*>(x + 4LL * p);
+  const float4 u = xp[0], v = xp[1];
+  return df64(u.x, u.y) + df64(u.z, u.w) * c + df64(v.x, v.y) * s;
+}
+
 template <typename Real, int NS>
-__device__ __forceinline__ void scatter(Real* y, int p, Real v, Real c, Real s);
+__device__ __forceinline__ void scatter(typename OutT<Real>::type* y, int p, Real v, Real c, Real s);
 template <>
 __device__ __forceinline__ void scatter<float, 1>(float* y, int p, float v, float, float) {
   atomicAdd(y + p, v);
@@ -114,6 +128,19 @@ __device__ __forceinline__ void scatter<double, 3>(double* y, int p, double v, d
   atomicAdd(q + 1, v * c);
   atomicAdd(q + 2, v * s);
 }
+// double-float results are rounded to float64 once per sample and added with
+// float64 atomics
+template <>
+__device__ __forceinline__ void scatter<df64, 1>(double* y, int p, df64 v, df64, df64) {
+  atomicAdd(y + p, to_double(v));
+}
+template <>
+__device__ __forceinline__ void scatter<df64, 3>(double* y, int p, df64 v, df64 c, df64 s) {
+  double* q = y + 4LL * p;
+  atomicAdd(q, to_double(v));
+  atomicAdd(q + 1, to_double(v * c));
+  atomicAdd(q + 2, to_double(v * s));
+}
 
 // A lane seen from one CTA: valid input window positions [in_lo, in_hi),
 // kept outputs [out_lo, out_hi), and base pointers already offset by the
@@ -124,6 +151,7 @@ struct LaneView {
   const int* pix;
   const float* psi;
   const double2* cs;
+  const float4* csd;
   const void* in;
   void* out;
 };
@@ -142,11 +170,13 @@ __device__ __forceinline__ LaneView<Real> lane_view(const OpArgs& a, const Lane&
   v.pix = a.pix + ws;
   v.psi = a.psi + ws;
   v.cs = a.cs64 + ws;
+  v.csd = a.csdf + ws;
   if (IN == IN_TODF) v.in = static_cast<const float*>(a.in) + g.rhs * a.in_stride + ws;
   else if (IN == IN_TODR) v.in = static_cast<const Real*>(a.in) + g.rhs * a.in_stride + ws;
   else v.in = static_cast<const Real*>(a.in) + g.rhs * a.in_stride;
-  if (OUT == OUT_TOD) v.out = static_cast<Real*>(a.out) + g.rhs * a.out_stride + ws;
-  else v.out = static_cast<Real*>(a.out) + g.rhs * a.out_stride;
+  typedef typename OutT<Real>::type Out;
+  if (OUT == OUT_TOD) v.out = static_cast<Out*>(a.out) + g.rhs * a.out_stride + ws;
+  else v.out = static_cast<Out*>(a.out) + g.rhs * a.out_stride;
   return v;
 }
 
@@ -168,6 +198,16 @@ __device__ __forceinline__ void lane_angle<double>(const LaneView<double>& L, in
     s = cs.y;
   } else {
     c = s = 0.0;
+  }
+}
+template <>
+__device__ __forceinline__ void lane_angle<df64>(const LaneView<df64>& L, int n, bool ok, df64& c, df64& s) {
+  if (ok) {
+    const float4 cs = L.csd[n];
+    c = df64(cs.x, cs.y);
+    s = df64(cs.z, cs.w);
+  } else {
+    c = s = df64();
   }
 }
 template <typename Real>
@@ -415,7 +455,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int l = 0; l < 2; ++l)
-          if (ok[l][u]) static_cast<Real*>(L[l].out)[nn[u]] = val[l][u];
+          if (ok[l][u]) static_cast<Real*>(L[l].out)[nn[u]] = val[l][u];  // float and float64 only
     } else {
       int pp[2][U];
       Real cc[2][U], ss[2][U];
@@ -434,7 +474,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
           if (pp[l][u] < 0) continue;
           Real c = cc[l][u], sn = ss[l][u];
           if (NS == 3) finish_angle<Real>(c, sn);
-          scatter<Real, NS>(static_cast<Real*>(L[l].out), pp[l][u], val[l][u], c, sn);
+          scatter<Real, NS>(static_cast<typename OutT<Real>::type*>(L[l].out), pp[l][u], val[l][u], c, sn);
         }
     }
   }
@@ -544,9 +584,11 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
   a.pix = p->pix_obs;
   a.psi = p->psi;
   a.cs64 = p->cs64;
+  a.csdf = p->csdf;
   a.scratch = p->scratch;
-  a.H = sizeof(Real) == 8 ? (const void*)p->H64 : (const void*)p->H32;
-  a.tw = sizeof(Real) == 8 ? (const void*)p->tw64 : (const void*)p->tw32;
+  constexpr bool DF = std::is_same<Real, df64>::value;
+  a.H = DF ? (const void*)p->Hdf : sizeof(Real) == 8 ? (const void*)p->H64 : (const void*)p->H32;
+  a.tw = DF ? (const void*)p->twdf : sizeof(Real) == 8 ? (const void*)p->tw64 : (const void*)p->tw32;
   a.skip = skip;
   a.skip_stride = ts ? skip_stride : 0;
   a.tiles = ts ? ts->tiles : p->tiles;
@@ -564,7 +606,7 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
     for (int r = 0; r < n_rhs; ++r) {
       a.in = static_cast<const char*>(in) + (size_t)r * in_stride *
                                                 (IN == IN_TODF ? sizeof(float) : sizeof(Real));
-      a.out = static_cast<char*>(out) + (size_t)r * out_stride * sizeof(Real);
+      a.out = static_cast<char*>(out) + (size_t)r * out_stride * sizeof(typename OutT<Real>::type);
       // a tile set names each lane's right-hand side, with per-rhs strides;
       // otherwise the plan's tiles are replayed once per right-hand side
       a.in_stride = ts ? in_stride : 0;
@@ -603,6 +645,18 @@ madmap_status dispatch_io(Plan* p, int in_mode, int out_mode, const void* in, vo
   return MADMAP_ERR_INTERNAL;
 }
 
+// double-float: map or float timestream in, float64 map out
+template <int NS>
+madmap_status dispatch_df(Plan* p, int in_mode, int out_mode, const void* in, void* out, long long is, long long os,
+                          int n_rhs, const int* skip, cudaStream_t s) {
+  if (in_mode == IN_MAP && out_mode == OUT_MAP)
+    return launch_all<df64, NS, IN_MAPX, OUT_MAP>(p, in, out, is, os, n_rhs, skip, s);
+  if (in_mode == IN_TOD && out_mode == OUT_MAP)
+    return launch_all<df64, NS, IN_TODF, OUT_MAP>(p, in, out, is, os, n_rhs, skip, s);
+  set_error("unsupported double-float operator mode");
+  return MADMAP_ERR_INTERNAL;
+}
+
 template <typename Real, int NS>
 madmap_status time_impl(Plan* p, const void* in, void* out, int reps, double ms[3], cudaStream_t s) {
   int n_chunks, per_chunk;
@@ -615,7 +669,8 @@ madmap_status time_impl(Plan* p, const void* in, void* out, int reps, double ms[
   if (st == MADMAP_OK) {
     const long long nv = (long long)std::max(1, p->n_obs) * p->ns_pad;
     for (int rep = 0; rep < reps && st == MADMAP_OK; ++rep) {
-      if (cudaMemsetAsync(out, 0, sizeof(Real) * nv, s) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "memset");
+      if (cudaMemsetAsync(out, 0, sizeof(typename OutT<Real>::type) * nv, s) != cudaSuccess)
+        st = cuda_fail(cudaGetLastError(), "memset");
       if (st == MADMAP_OK)
         st = launch_all<Real, NS, IN_MAPX, OUT_MAP>(p, in, out, 0, 0, 1, nullptr, s, ev.data() + rep * n_chunks * 4, 1);
     }
@@ -651,12 +706,15 @@ madmap_status dispatch_set(Plan* p, int in_mode, int out_mode, const void* in, v
 
 // Operator over a tile set whose lanes name their right-hand side (maps and
 // timestreams strided by in_stride / out_stride elements per rhs).
-madmap_status op_launch_set(Plan* p, bool fp64, int in_mode, int out_mode, const void* in, void* out,
+madmap_status op_launch_set(Plan* p, int prec, int in_mode, int out_mode, const void* in, void* out,
                             long long in_stride, long long out_stride, const int* skip, int skip_stride,
                             const TileSet* ts, cudaStream_t s) {
   if (ts->n_tiles == 0) return MADMAP_OK;
   const int ss = skip_stride;
-  if (fp64)
+  if (prec == OPP_DF64)
+    return p->n_stokes == 1 ? dispatch_set<df64, 1>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts)
+                            : dispatch_set<df64, 3>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts);
+  if (prec == OPP_F64)
     return p->n_stokes == 1 ? dispatch_set<double, 1>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts)
                             : dispatch_set<double, 3>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts);
   return p->n_stokes == 1 ? dispatch_set<float, 1>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts)
@@ -666,19 +724,22 @@ madmap_status op_launch_set(Plan* p, bool fp64, int in_mode, int out_mode, const
 static long long g_launches = 0;
 void count_launches(long long n) { g_launches += n; }
 
-madmap_status op_time(Plan* p, bool fp64, const void* in, void* out, int reps, double ms[3], cudaStream_t s) {
+madmap_status op_time(Plan* p, int prec, const void* in, void* out, int reps, double ms[3], cudaStream_t s) {
   if (p->n_tiles == 0) {
     ms[0] = ms[1] = ms[2] = 0.0;
     return MADMAP_OK;
   }
-  if (fp64)
+  if (prec == OPP_DF64)
+    return p->n_stokes == 1 ? time_impl<df64, 1>(p, in, out, reps, ms, s) : time_impl<df64, 3>(p, in, out, reps, ms, s);
+  if (prec == OPP_F64)
     return p->n_stokes == 1 ? time_impl<double, 1>(p, in, out, reps, ms, s) : time_impl<double, 3>(p, in, out, reps, ms, s);
   return p->n_stokes == 1 ? time_impl<float, 1>(p, in, out, reps, ms, s) : time_impl<float, 3>(p, in, out, reps, ms, s);
 }
 
 // Resident CTAs per SM of the operator kernels (the least of the three) and
 // CTAs per tile of the column kernels, for wave-aligned chunk sizes.
-void op_occupancy(const Plan* p, bool fp64, int& ctas_per_sm, int& ctas_per_tile) {
+void op_occupancy(const Plan* p, int prec, int& ctas_per_sm, int& ctas_per_tile) {
+  const bool fp64 = prec != OPP_F32;
   int b1 = 0, b2 = 0, n1 = 0, n2 = 0, n3 = 0;
   size_t s13 = 0, s2 = 0;
   OpKernels K;
@@ -704,18 +765,21 @@ void op_occupancy(const Plan* p, bool fp64, int& ctas_per_sm, int& ctas_per_tile
   ctas_per_tile = std::max(1, p->N1 / std::max(1, b1));
 }
 
-size_t f1_smem_bytes(const Plan* p, bool fp64) {
-  return fp64 ? smem_f13<double>(p) : smem_f13<float>(p);
+size_t f1_smem_bytes(const Plan* p, int prec) {
+  return prec == OPP_DF64 ? smem_f13<df64>(p) : prec == OPP_F64 ? smem_f13<double>(p) : smem_f13<float>(p);
 }
 
 // in_mode: IN_MAP (gather from a map), IN_TOD (float timestream, e.g. the
 // data d) or IN_TOD_REAL (timestream of the working precision).  n_rhs == 0
 // only prepares the kernels (shared-memory opt-in) and launches nothing.
-madmap_status op_launch(Plan* p, bool fp64, int in_mode, int out_mode, const void* in, void* out,
+madmap_status op_launch(Plan* p, int prec, int in_mode, int out_mode, const void* in, void* out,
                         long long in_stride, long long out_stride, int n_rhs, const int* skip,
                         cudaStream_t s) {
   if (p->n_tiles == 0) return MADMAP_OK;
-  if (fp64) {
+  if (prec == OPP_DF64)
+    return p->n_stokes == 1 ? dispatch_df<1>(p, in_mode, out_mode, in, out, in_stride, out_stride, n_rhs, skip, s)
+                            : dispatch_df<3>(p, in_mode, out_mode, in, out, in_stride, out_stride, n_rhs, skip, s);
+  if (prec == OPP_F64) {
     if (p->n_stokes == 1)
       return dispatch_io<double, 1>(p, in_mode, out_mode, in, out, in_stride, out_stride, n_rhs, skip, s);
     return dispatch_io<double, 3>(p, in_mode, out_mode, in, out, in_stride, out_stride, n_rhs, skip, s);

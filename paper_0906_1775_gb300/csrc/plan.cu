@@ -265,12 +265,14 @@ __device__ __forceinline__ int interval_of(const long long* off, int n_ivl, long
 // operator.  acc layout per pixel: T: [wsum]; IQU: [6 AtA | 6 AtWA].
 __global__ void k_accumulate(const int* pix_obs, const float* psi, long long n, const long long* off, int n_ivl,
                              const int* ivl_filter, const double* f0, int ns, double* acc, int* hits,
-                             double2* cs64) {
+                             double2* cs64, float4* csdf) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     double c = 1.0, s = 0.0;
     if (ns == 3) {
       sincos(2.0 * (double)psi[t], &s, &c);
       cs64[t] = make_double2(c, s);
+      const df64 cd(c), sd(s);
+      csdf[t] = make_float4(cd.hi, cd.lo, sd.hi, sd.lo);
     }
     const int p = pix_obs[t];
     if (p < 0) continue;
@@ -525,6 +527,7 @@ static madmap_status build_spectra(Plan* p) {
   const int M = p->M;
   std::vector<double> h64((size_t)p->n_filters * M);
   std::vector<float> h32((size_t)p->n_filters * M);
+  std::vector<df64> hdf((size_t)p->n_filters * M);
   std::vector<double> re(M), im(M);
   for (int f = 0; f < p->n_filters; ++f) {
     std::fill(re.begin(), re.end(), 0.0);
@@ -552,11 +555,13 @@ static madmap_status build_spectra(Plan* p) {
         const double v = re[k2 + (size_t)p->N2 * k1] / (double)M;
         h64[(size_t)f * M + (size_t)pos2 * p->N1 + pos1] = v;
         h32[(size_t)f * M + (size_t)pos2 * p->N1 + pos1] = (float)v;
+        hdf[(size_t)f * M + (size_t)pos2 * p->N1 + pos1] = df64(v);
       }
     }
   }
   MM_CUDA(cudaMemcpy(p->H64, h64.data(), h64.size() * sizeof(double), cudaMemcpyHostToDevice));
   MM_CUDA(cudaMemcpy(p->H32, h32.data(), h32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  MM_CUDA(cudaMemcpy(p->Hdf, hdf.data(), hdf.size() * sizeof(df64), cudaMemcpyHostToDevice));
   return MADMAP_OK;
 }
 
@@ -600,7 +605,7 @@ static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
   cudaMemcpyAsync(df0, f0.data(), sizeof(double) * p->n_filters, cudaMemcpyHostToDevice, s);
   if (n > 0)
     k_accumulate<<<grid_for(n), 256, 0, s>>>(p->pix_obs, p->psi, n, doff, p->n_ivl, dfilt, df0, ns, acc, hits,
-                                              p->cs64);
+                                              p->cs64, p->csdf);
   if (n_obs > 0)
     k_classify<<<grid_for(n_obs), 256, 0, s>>>(acc, hits, n_obs, ns, p->rcond_excise, p->rcond_fp64, p->P64,
                                                 p->P32, p->excised, p->fp64flag, counts);
@@ -686,6 +691,7 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
   if (p->n_stokes == 3) {
     MM_TRY(dalloc_t(p, &p->psi, std::max(1LL, n)));
     MM_TRY(dalloc_t(p, &p->cs64, std::max(1LL, n)));
+    MM_TRY(dalloc_t(p, &p->csdf, std::max(1LL, n)));
   }
   MM_TRYC(cudaMemsetAsync(p->dev_flag, 0, 16 * sizeof(int), s));
   MM_TRYC(cudaMemsetAsync(bits, 0, sizeof(unsigned) * n_words, s));
@@ -758,19 +764,25 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
     MM_TRYC(cudaMemcpy(p->tiles, p->host_tiles.data(), sizeof(Tile) * p->n_tiles, cudaMemcpyHostToDevice));
   MM_TRY(dalloc_t(p, &p->H64, (size_t)p->n_filters * p->M));
   MM_TRY(dalloc_t(p, &p->H32, (size_t)p->n_filters * p->M));
+  MM_TRY(dalloc_t(p, &p->Hdf, (size_t)p->n_filters * p->M));
   MM_TRY(build_spectra(p));
   {
     std::vector<double2> t64(p->M);
     std::vector<float2> t32(p->M);
+    std::vector<cdf64> tdf(p->M);
     for (int j = 0; j < p->M; ++j) {
       const double ang = 2.0 * M_PI * (double)j / (double)p->M;
       t64[j] = make_double2(cos(ang), -sin(ang));
       t32[j] = make_float2((float)t64[j].x, (float)t64[j].y);
+      tdf[j].x = df64(t64[j].x);
+      tdf[j].y = df64(t64[j].y);
     }
     MM_TRY(dalloc_t(p, &p->tw64, p->M));
     MM_TRY(dalloc_t(p, &p->tw32, p->M));
+    MM_TRY(dalloc_t(p, &p->twdf, p->M));
     MM_TRYC(cudaMemcpy(p->tw64, t64.data(), sizeof(double2) * p->M, cudaMemcpyHostToDevice));
     MM_TRYC(cudaMemcpy(p->tw32, t32.data(), sizeof(float2) * p->M, cudaMemcpyHostToDevice));
+    MM_TRYC(cudaMemcpy(p->twdf, tdf.data(), sizeof(cdf64) * p->M, cudaMemcpyHostToDevice));
   }
   MM_TRY(dalloc(p, &p->scratch, (size_t)p->tiles_per_chunk * p->M * sizeof(double2)));
   MM_TRYC(cudaStreamSynchronize(s));

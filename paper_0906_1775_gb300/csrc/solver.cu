@@ -60,6 +60,7 @@ struct SolveBuffers {
   cudaEvent_t ev[2] = {nullptr, nullptr};
   // float64 refinement vectors (allocated with the float64 buffers)
   double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *t64 = nullptr, *xbest64 = nullptr;
+  df64* xdf = nullptr;  // x64 split into double-float pairs (input of the double-float operator)
   cudaGraphExec_t exec = nullptr;
   int graph_iters = 0, graph_rhs = 0;
   const void* graph_ts = nullptr;
@@ -143,6 +144,7 @@ static madmap_status get_buffers(Plan* p, bool fp64, int n_rhs, SolveBuffers** o
     double** v64[5] = {&sb->b64, &sb->x64, &sb->r64, &sb->t64, &sb->xbest64};
     for (double** v : v64)
       if ((st = sb_alloc(p, sb, (void**)v, sizeof(double) * sb->nvec * n_rhs)) != MADMAP_OK) break;
+    if (st == MADMAP_OK) st = sb_alloc(p, sb, (void**)&sb->xdf, sizeof(df64) * sb->nvec * n_rhs);
   }
   if (st == MADMAP_OK) {
     cudaError_t e = cudaMallocHost(&sb->host_st, 2 * sizeof(CgState) * n_rhs);
@@ -456,6 +458,17 @@ __global__ void k_refine_add(double* x64, const float* e, double* t64, long long
     x64[o + i] += (double)e[o + i];
     t64[o + i] = 0.0;
   }
+}
+
+// y = x as double-float pairs
+__global__ void k_split(const double* x, df64* y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = df64(x[i]);
+}
+
+// Arithmetic of the right-hand side and the refinement residuals.
+static int refine_prec(const madmap_solve_opts& o) {
+  return (o.precision == MADMAP_MIXED && o.refine_precision == MADMAP_DF64) ? OPP_DF64 : OPP_F64;
 }
 
 // r64 = b64 - t64 and ||r64|| -> st[rhs].res (by the last block of the rhs)
@@ -774,10 +787,17 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
     ++outer;
     count_launches(2);
     k_refine_add<<<gv, NT, 0, s>>>(sb64->x64, (const float*)sb32->xb, sb64->t64, nv, sb64->flags);
+    const int rp = refine_prec(o);
+    const void* xin = sb64->x64;
+    if (rp == OPP_DF64) {
+      count_launches(1);
+      k_split<<<grid_vec(nv * n_rhs), NT, 0, s>>>(sb64->x64, sb64->xdf, nv * n_rhs);
+      xin = sb64->xdf;
+    }
     if (B.ts)
-      st = op_launch_set(p, true, IN_MAP, OUT_MAP, sb64->x64, sb64->t64, nv, nv, sb64->flags, 1, B.ts, s);
+      st = op_launch_set(p, rp, IN_MAP, OUT_MAP, xin, sb64->t64, nv, nv, sb64->flags, 1, B.ts, s);
     else
-      st = op_launch(p, true, IN_MAP, OUT_MAP, sb64->x64, sb64->t64, 0, 0, 1, nullptr, s);
+      st = op_launch(p, rp, IN_MAP, OUT_MAP, xin, sb64->t64, 0, 0, 1, nullptr, s);
     if (st != MADMAP_OK) return st;
     k_residual<<<gv, NT, 0, s>>>(sb64->b64, sb64->t64, sb64->r64, nv, sb64->st, sb64->partials, sb64->flags);
     MM_CUDA(cudaMemcpyAsync(h.data(), sb64->st, sizeof(CgState) * n_rhs, cudaMemcpyDeviceToHost, s));
@@ -851,12 +871,12 @@ static madmap_status solve_impl(Plan* p, int n_rhs, const float* d, double* m, c
   const int n = p->n_obs;
   std::vector<madmap_solve_info> I(n_rhs);
   for (auto& x : I) memset(&x, 0, sizeof(x));
-  // right-hand sides b = A^T N^-1 d in float64
+  // right-hand sides b = A^T N^-1 d into float64 maps (float64 or double-float arithmetic)
   MM_CUDA(cudaMemsetAsync(sb64->b64, 0, sizeof(double) * nv * n_rhs, s));
   if (B.ts)
-    st = op_launch_set(p, true, IN_TOD, OUT_MAP, d, sb64->b64, p->n_t, nv, nullptr, 0, B.ts, s);
+    st = op_launch_set(p, refine_prec(o), IN_TOD, OUT_MAP, d, sb64->b64, p->n_t, nv, nullptr, 0, B.ts, s);
   else
-    st = op_launch(p, true, IN_TOD, OUT_MAP, d, sb64->b64, 0, 0, 1, nullptr, s);
+    st = op_launch(p, refine_prec(o), IN_TOD, OUT_MAP, d, sb64->b64, 0, 0, 1, nullptr, s);
   if (st != MADMAP_OK) return st;
   MM_CUDA(cudaStreamSynchronize(s));
   const double t_rhs =
@@ -1033,9 +1053,9 @@ static madmap_status backward_impl(Plan* p, const float* d, const double* m, con
 
 // ---------------------------------------------------------------- operator entry points
 template <typename Real>
-static madmap_status apply_impl(Plan* p, bool fp64, int n_rhs, const void* x, void* y, cudaStream_t s) {
+static madmap_status apply_impl(Plan* p, int prec, int n_rhs, const void* x, void* y, cudaStream_t s) {
   SolveBuffers* sb = nullptr;
-  madmap_status st = get_buffers(p, fp64, 1, &sb);
+  madmap_status st = get_buffers(p, prec != OPP_F32, 1, &sb);
   if (st != MADMAP_OK) return st;
   const int n = p->n_obs, ns = p->n_stokes, np = p->ns_pad;
   const long long user = (long long)n * ns;
@@ -1045,7 +1065,13 @@ static madmap_status apply_impl(Plan* p, bool fp64, int n_rhs, const void* x, vo
     count_launches(2);
     k_pack<Real, Real><<<grid_vec((long long)n * np), NT, 0, s>>>(xr, (Real*)sb->p, n, ns, np);
     MM_CUDA(cudaMemsetAsync(sb->q, 0, sizeof(Real) * sb->nvec, s));
-    st = op_launch(p, fp64, IN_MAP, OUT_MAP, sb->p, sb->q, 0, 0, 1, nullptr, s);
+    const void* xin = sb->p;
+    if (prec == OPP_DF64) {
+      count_launches(1);
+      k_split<<<grid_vec(sb->nvec), NT, 0, s>>>((const double*)sb->p, sb->xdf, sb->nvec);
+      xin = sb->xdf;
+    }
+    st = op_launch(p, prec, IN_MAP, OUT_MAP, xin, sb->q, 0, 0, 1, nullptr, s);
     if (st != MADMAP_OK) return st;
     k_unpack<Real, Real><<<grid_vec(user), NT, 0, s>>>((const Real*)sb->q, yr, n, ns, np);
   }
@@ -1054,15 +1080,15 @@ static madmap_status apply_impl(Plan* p, bool fp64, int n_rhs, const void* x, vo
 }
 
 template <typename Real>
-static madmap_status rhs_impl(Plan* p, bool fp64, int n_rhs, const float* d, void* b, cudaStream_t s) {
+static madmap_status rhs_impl(Plan* p, int prec, int n_rhs, const float* d, void* b, cudaStream_t s) {
   SolveBuffers* sb = nullptr;
-  madmap_status st = get_buffers(p, fp64, 1, &sb);
+  madmap_status st = get_buffers(p, prec != OPP_F32, 1, &sb);
   if (st != MADMAP_OK) return st;
   const int n = p->n_obs, ns = p->n_stokes, np = p->ns_pad;
   const long long user = (long long)n * ns;
   for (int r = 0; r < n_rhs; ++r) {
     MM_CUDA(cudaMemsetAsync(sb->q, 0, sizeof(Real) * sb->nvec, s));
-    st = op_launch(p, fp64, IN_TOD, OUT_MAP, d + (long long)r * p->n_t, sb->q, 0, 0, 1, nullptr, s);
+    st = op_launch(p, prec, IN_TOD, OUT_MAP, d + (long long)r * p->n_t, sb->q, 0, 0, 1, nullptr, s);
     if (st != MADMAP_OK) return st;
     count_launches(1);
     k_unpack<Real, Real><<<grid_vec(user), NT, 0, s>>>((const Real*)sb->q, static_cast<Real*>(b) + r * user, n, ns,
@@ -1076,24 +1102,28 @@ static madmap_status rhs_impl(Plan* p, bool fp64, int n_rhs, const float* d, voi
 
 using namespace mm;
 
-static madmap_status check_prec(int precision, bool allow_mixed) {
+static madmap_status check_prec(int precision, bool allow_mixed, bool allow_df = false) {
   if (precision == MADMAP_FP64 || precision == MADMAP_FP32) return MADMAP_OK;
   if (allow_mixed && precision == MADMAP_MIXED) return MADMAP_OK;
+  if (allow_df && precision == MADMAP_DF64) return MADMAP_OK;
   set_error("unsupported precision");
   return MADMAP_ERR_INVALID_ARG;
+}
+static int op_prec(int precision) {
+  return precision == MADMAP_DF64 ? OPP_DF64 : precision == MADMAP_FP64 ? OPP_F64 : OPP_F32;
 }
 
 extern "C" madmap_status madmap_apply_ATNA(madmap_plan_t plan, int32_t precision, int32_t n_rhs, const void* x,
                                            void* y, void* stream) {
   MM_CHECK(plan && n_rhs >= 1, MADMAP_ERR_INVALID_ARG, "apply_ATNA: bad arguments");
-  madmap_status st = check_prec(precision, false);
+  madmap_status st = check_prec(precision, false, true);
   if (st != MADMAP_OK) return st;
   Plan* p = reinterpret_cast<Plan*>(plan);
   MM_CHECK((x && y) || p->n_obs == 0, MADMAP_ERR_INVALID_ARG, "apply_ATNA: NULL map");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (p->n_obs == 0) return MADMAP_OK;
-  return precision == MADMAP_FP64 ? apply_impl<double>(p, true, n_rhs, x, y, s)
-                                  : apply_impl<float>(p, false, n_rhs, x, y, s);
+  return precision == MADMAP_FP32 ? apply_impl<float>(p, OPP_F32, n_rhs, x, y, s)
+                                  : apply_impl<double>(p, op_prec(precision), n_rhs, x, y, s);
 }
 
 extern "C" madmap_status madmap_rhs(madmap_plan_t plan, int32_t precision, int32_t n_rhs, const float* d, void* b,
@@ -1102,12 +1132,12 @@ extern "C" madmap_status madmap_rhs(madmap_plan_t plan, int32_t precision, int32
   Plan* p = reinterpret_cast<Plan*>(plan);
   MM_CHECK(b || p->n_obs == 0, MADMAP_ERR_INVALID_ARG, "rhs: b is NULL");
   MM_CHECK(d || p->n_t == 0, MADMAP_ERR_INVALID_ARG, "rhs: d is NULL");
-  madmap_status st = check_prec(precision, false);
+  madmap_status st = check_prec(precision, false, true);
   if (st != MADMAP_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (p->n_obs == 0) return MADMAP_OK;
-  return precision == MADMAP_FP64 ? rhs_impl<double>(p, true, n_rhs, d, b, s)
-                                  : rhs_impl<float>(p, false, n_rhs, d, b, s);
+  return precision == MADMAP_FP32 ? rhs_impl<float>(p, OPP_F32, n_rhs, d, b, s)
+                                  : rhs_impl<double>(p, op_prec(precision), n_rhs, d, b, s);
 }
 
 extern "C" madmap_status madmap_apply_ninv(madmap_plan_t plan, int32_t precision, int32_t n_rhs, const void* y,
@@ -1137,6 +1167,7 @@ extern "C" void madmap_solve_opts_default(madmap_solve_opts* o) {
   o->inner_rel_tol = 1e-4;
   o->use_graph = 2;
   o->iters_per_sync = 8;
+  o->refine_precision = MADMAP_DF64;
 }
 
 extern "C" madmap_status madmap_solve(madmap_plan_t plan, const float* d, double* m, const madmap_solve_opts* opts,
@@ -1151,7 +1182,8 @@ extern "C" madmap_status madmap_solve(madmap_plan_t plan, const float* d, double
   MM_CHECK(o.precision == MADMAP_FP64 || o.precision == MADMAP_MIXED, MADMAP_ERR_INVALID_ARG,
            "solve: precision must be FP64 or MIXED");
   MM_CHECK(o.max_iter >= 0 && o.rel_tol >= 0 && o.iters_per_sync >= 1 && o.max_outer >= 1 &&
-               o.inner_rel_tol > 0 && o.inner_rel_tol < 1,
+               o.inner_rel_tol > 0 && o.inner_rel_tol < 1 &&
+               (o.refine_precision == MADMAP_DF64 || o.refine_precision == MADMAP_FP64),
            MADMAP_ERR_INVALID_ARG, "solve: bad options");
   cudaStream_t caller = static_cast<cudaStream_t>(stream);
   if (p->n_obs == 0) {
@@ -1185,7 +1217,8 @@ extern "C" madmap_status madmap_solve_backward(madmap_plan_t plan, const float* 
   MM_CHECK(o.precision == MADMAP_FP64 || o.precision == MADMAP_MIXED, MADMAP_ERR_INVALID_ARG,
            "solve_backward: precision must be FP64 or MIXED");
   MM_CHECK(o.max_iter >= 0 && o.rel_tol >= 0 && o.iters_per_sync >= 1 && o.max_outer >= 1 &&
-               o.inner_rel_tol > 0 && o.inner_rel_tol < 1,
+               o.inner_rel_tol > 0 && o.inner_rel_tol < 1 &&
+               (o.refine_precision == MADMAP_DF64 || o.refine_precision == MADMAP_FP64),
            MADMAP_ERR_INVALID_ARG, "solve_backward: bad options");
   cudaStream_t caller = static_cast<cudaStream_t>(stream);
   if (p->n_obs == 0) {
@@ -1221,7 +1254,8 @@ extern "C" madmap_status madmap_solve_batched(madmap_plan_t plan, int32_t n_rhs,
   MM_CHECK(o.precision == MADMAP_FP64 || o.precision == MADMAP_MIXED, MADMAP_ERR_INVALID_ARG,
            "solve_batched: precision must be FP64 or MIXED");
   MM_CHECK(o.max_iter >= 0 && o.rel_tol >= 0 && o.iters_per_sync >= 1 && o.max_outer >= 1 &&
-               o.inner_rel_tol > 0 && o.inner_rel_tol < 1,
+               o.inner_rel_tol > 0 && o.inner_rel_tol < 1 &&
+               (o.refine_precision == MADMAP_DF64 || o.refine_precision == MADMAP_FP64),
            MADMAP_ERR_INVALID_ARG, "solve_batched: bad options");
   cudaStream_t caller = static_cast<cudaStream_t>(stream);
   if (p->n_obs == 0) {
@@ -1244,17 +1278,17 @@ extern "C" madmap_status madmap_solve_batched(madmap_plan_t plan, int32_t n_rhs,
 extern "C" madmap_status madmap_time_operator(madmap_plan_t plan, int32_t precision, int32_t reps, double* ms_out,
                                               int32_t* launches_out, void* stream) {
   MM_CHECK(plan && ms_out && reps >= 1, MADMAP_ERR_INVALID_ARG, "time_operator: bad arguments");
-  MM_CHECK(precision == MADMAP_FP64 || precision == MADMAP_FP32, MADMAP_ERR_INVALID_ARG,
-           "time_operator: precision must be FP64 or FP32");
+  MM_CHECK(precision == MADMAP_FP64 || precision == MADMAP_FP32 || precision == MADMAP_DF64, MADMAP_ERR_INVALID_ARG,
+           "time_operator: precision must be FP64, FP32 or DF64");
   Plan* p = reinterpret_cast<Plan*>(plan);
-  const bool fp64 = precision == MADMAP_FP64;
+  const int prec = op_prec(precision);
   SolveBuffers* sb = nullptr;
-  madmap_status st = get_buffers(p, fp64, 1, &sb);
+  madmap_status st = get_buffers(p, prec != OPP_F32, 1, &sb);
   if (st != MADMAP_OK) return st;
   int n_chunks, per_chunk;
   chunking(p, n_chunks, per_chunk);
   if (launches_out)
     for (int k = 0; k < 3; ++k) launches_out[k] = n_chunks;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return op_time(p, fp64, sb->p, sb->q, reps, ms_out, s);
+  return op_time(p, prec, prec == OPP_DF64 ? (const void*)sb->xdf : sb->p, sb->q, reps, ms_out, s);
 }

@@ -100,7 +100,11 @@ def test_allsky_full_size_sampled_rows():
     assert rel_rms(y64[pk], ref) < FP64_OP_TOL
     y32 = host(plan.apply_ATNA(cuda(x, torch.float32), precision="fp32"))[0]
     assert rel_rms(y32[pk], ref) < 1e-4
+    ydf = host(plan.apply_ATNA(cuda(x, torch.float64), precision="df64"))[0]
+    assert rel_rms(ydf[pk], ref) < FP64_OP_TOL
     d_h = host(p.d[0])
     bref = T.rhs_sampled(d_h, pk, hits)
     b64 = host(plan.rhs(p.d, precision="fp64"))[0]
     assert rel_rms(b64[pk], bref) < FP64_OP_TOL
+    bdf = host(plan.rhs(p.d, precision="df64"))[0]
+    assert rel_rms(bdf[pk], bref) < FP64_OP_TOL
