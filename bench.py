@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--profile-step", type=float, default=0.0, metavar="TOL",
                     help="profiling runs: skip the reference map and tolerance search and run exactly one "
                          "mixed-precision solve at this stopping tolerance")
+    ap.add_argument("--profile-graph", type=int, default=2, choices=[0, 1, 2],
+                    help="iteration driver of the --profile-step solve: 2 device-side graph loop (as timed), "
+                         "0 direct launches (every kernel visible to a profiler)")
     ap.add_argument("--tpc", type=int, default=0, help="override the plan's tiles per launch chunk (0 = plan's choice)")
     ap.add_argument("--operator-only", type=int, default=0, metavar="R",
                     help="only build the plan and time R float32 operator applications (profiling runs)")
@@ -420,6 +423,7 @@ def main():
     d = d_host.to(dev)
     if args.profile_step > 0:
         _, info = plan.solve(d, precision="mixed", rel_tol=args.profile_step, max_iter=3000, max_outer=20,
+                             use_graph=args.profile_graph,
                              inner_rel_tol=1e-4)
         torch.cuda.synchronize()
         print(json.dumps({"profile_step": info, "launches": mm.madmap_kernel_launch_count()}), flush=True)

@@ -170,10 +170,17 @@ __device__ __forceinline__ V3<Real, NS> ldv(const Real* v, int p) {
   if (NS == 1) {
     o.a = v[p];
     o.b = o.c = 0;
+  } else if (sizeof(Real) == 4) {  // one 16-byte load per pixel (the vectors are 16-byte aligned)
+    const float4 m = reinterpret_cast<const float4*>(v)[p];
+    o.a = (Real)m.x;
+    o.b = (Real)m.y;
+    o.c = (Real)m.z;
   } else {
-    o.a = v[4LL * p];
-    o.b = v[4LL * p + 1];
-    o.c = v[4LL * p + 2];
+    const double2 m0 = reinterpret_cast<const double2*>(v)[2LL * p];
+    const double2 m1 = reinterpret_cast<const double2*>(v)[2LL * p + 1];
+    o.a = (Real)m0.x;
+    o.b = (Real)m0.y;
+    o.c = (Real)m1.x;
   }
   return o;
 }
@@ -181,11 +188,11 @@ template <typename Real, int NS>
 __device__ __forceinline__ void stv(Real* v, int p, const V3<Real, NS>& o) {
   if (NS == 1) {
     v[p] = o.a;
+  } else if (sizeof(Real) == 4) {
+    reinterpret_cast<float4*>(v)[p] = make_float4((float)o.a, (float)o.b, (float)o.c, 0.f);
   } else {
-    v[4LL * p] = o.a;
-    v[4LL * p + 1] = o.b;
-    v[4LL * p + 2] = o.c;
-    v[4LL * p + 3] = 0;
+    reinterpret_cast<double2*>(v)[2LL * p] = make_double2((double)o.a, (double)o.b);
+    reinterpret_cast<double2*>(v)[2LL * p + 1] = make_double2((double)o.c, 0.0);
   }
 }
 template <typename Real, int NS>
@@ -254,15 +261,37 @@ __device__ __forceinline__ bool block_reduce_publish(double (&v)[K], double* par
   return last;
 }
 
+// Sum of all blocks' partials, computed by every thread of the block that
+// finished last (block_reduce_publish returned true in all of its threads):
+// thread i adds blocks i, i + blockDim.x, ..., then a fixed shuffle tree and
+// a fixed pass over the warps combine them, so the result does not depend on
+// the order in which blocks finished.  Valid in thread 0.
 template <int K>
 __device__ __forceinline__ void final_sums(const double* partials, double (&out)[K]) {
-  // executed by thread 0 of the last block: fixed order over blocks
+  __shared__ double shf[32][K];
   __threadfence();
+  double v[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) out[k] = 0.0;
-  for (unsigned b = 0; b < gridDim.x; ++b)
+  for (int k = 0; k < K; ++k) v[k] = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
 #pragma unroll
-    for (int k = 0; k < K; ++k) out[k] += ((volatile const double*)partials)[b * 4 + k];
+    for (int k = 0; k < K; ++k) v[k] += ((volatile const double*)partials)[b * 4 + k];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) shf[wid][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      out[k] = 0.0;
+      for (int w = 0; w < nw; ++w) out[k] += shf[w][k];
+    }
+  }
 }
 
 // ---------------------------------------------------------------- CG kernels
@@ -299,23 +328,25 @@ __global__ void __launch_bounds__(NT) k_cg_init(Real* x, Real* r, Real* z, Real*
     acc[0] += dotv(rv, zv);
     acc[1] += dotv(rv, rv);
   }
-  if (block_reduce_publish<2>(acc, partials, &st->counter) && threadIdx.x == 0) {
+  if (block_reduce_publish<2>(acc, partials, &st->counter)) {
     double s[2];
     final_sums<2>(partials, s);
-    st->counter = 0;
-    st->rz = s[0];
-    st->bnorm = sqrt(s[1]);
-    st->res = st->bnorm > 0.0 ? 1.0 : 0.0;
-    st->best_res = st->res;
-    st->tol = tol;
-    st->k = 0;
-    st->best_k = 0;
-    st->dir_k = 0;
-    st->max_iter = max_iter;
-    st->status = 0;
-    st->alpha = st->beta = 0.0;
-    const bool off = inactive && inactive[blockIdx.y];
-    st->done = (off || st->bnorm == 0.0 || max_iter <= 0 || st->res <= tol) ? 1 : 0;
+    if (threadIdx.x == 0) {
+      st->counter = 0;
+      st->rz = s[0];
+      st->bnorm = sqrt(s[1]);
+      st->res = st->bnorm > 0.0 ? 1.0 : 0.0;
+      st->best_res = st->res;
+      st->tol = tol;
+      st->k = 0;
+      st->best_k = 0;
+      st->dir_k = 0;
+      st->max_iter = max_iter;
+      st->status = 0;
+      st->alpha = st->beta = 0.0;
+      const bool off = inactive && inactive[blockIdx.y];
+      st->done = (off || st->bnorm == 0.0 || max_iter <= 0 || st->res <= tol) ? 1 : 0;
+    }
   }
 }
 
@@ -330,15 +361,17 @@ __global__ void __launch_bounds__(NT) k_cg_alpha(const Real* p, const Real* q, l
   double acc[1] = {0.0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_obs; i += gridDim.x * blockDim.x)
     acc[0] += dotv(ldv<Real, NS>(p, i), ldv<Real, NS>(q, i));
-  if (block_reduce_publish<1>(acc, partials, &st->counter) && threadIdx.x == 0) {
+  if (block_reduce_publish<1>(acc, partials, &st->counter)) {
     double s[1];
     final_sums<1>(partials, s);
-    st->counter = 0;
-    if (!(s[0] > 0.0) || !isfinite(s[0])) {
-      st->status = (int)MADMAP_ERR_NOT_PD;
-      st->done = 1;
-    } else {
-      st->alpha = st->rz / s[0];
+    if (threadIdx.x == 0) {
+      st->counter = 0;
+      if (!(s[0] > 0.0) || !isfinite(s[0])) {
+        st->status = (int)MADMAP_ERR_NOT_PD;
+        st->done = 1;
+      } else {
+        st->alpha = st->rz / s[0];
+      }
     }
   }
 }
@@ -372,21 +405,23 @@ __global__ void __launch_bounds__(NT) k_cg_update(Real* x, Real* r, Real* z, con
     acc[0] += dotv(rv, zv);
     acc[1] += dotv(rv, rv);
   }
-  if (block_reduce_publish<2>(acc, partials, &st->counter) && threadIdx.x == 0) {
+  if (block_reduce_publish<2>(acc, partials, &st->counter)) {
     double s[2];
     final_sums<2>(partials, s);
-    st->counter = 0;
-    const int k = st->k + 1;
-    st->k = k;
-    const double res = sqrt(s[1]) / st->bnorm;
-    st->res = res;
-    if (res < st->best_res) {
-      st->best_res = res;
-      st->best_k = k;
+    if (threadIdx.x == 0) {
+      st->counter = 0;
+      const int k = st->k + 1;
+      st->k = k;
+      const double res = sqrt(s[1]) / st->bnorm;
+      st->res = res;
+      if (res < st->best_res) {
+        st->best_res = res;
+        st->best_k = k;
+      }
+      if (res <= st->tol || k >= st->max_iter || !isfinite(res)) st->done = 1;
+      st->beta = s[0] / st->rz;
+      st->rz = s[0];
     }
-    if (res <= st->tol || k >= st->max_iter || !isfinite(res)) st->done = 1;
-    st->beta = s[0] / st->rz;
-    st->rz = s[0];
   }
 }
 
@@ -484,11 +519,13 @@ __global__ void __launch_bounds__(NT) k_residual(const double* b64, const double
     r64[o + i] = v;
     acc[0] += v * v;
   }
-  if (block_reduce_publish<1>(acc, partials, &st->counter) && threadIdx.x == 0) {
+  if (block_reduce_publish<1>(acc, partials, &st->counter)) {
     double s[1];
     final_sums<1>(partials, s);
-    st->counter = 0;
-    st->res = sqrt(s[0]);
+    if (threadIdx.x == 0) {
+      st->counter = 0;
+      st->res = sqrt(s[0]);
+    }
   }
 }
 
