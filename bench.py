@@ -463,7 +463,7 @@ def main():
     # mixed precision: the inner float32 tolerance is a free parameter of the
     # method; pick the fastest setting that reaches the map error
     best_mixed = None
-    for inner in (1e-4, 1e-5, 1e-6):
+    for inner in (1e-4, 5e-5, 3e-5, 2e-5, 1e-5, 1e-6):
         kw_i = dict(max_outer=20, inner_rel_tol=inner)
         cand = first_tol("mixed", **kw_i)
         if cand[2] > MAP_TARGET:
