@@ -237,12 +237,16 @@ madmap_status madmap_apply_ninv_noalloc(int32_t precision, int64_t n_samples, in
 int64_t madmap_kernel_launch_count(void);
 
 /* Times the operator H = A^T N^-1 A in the plan's launch configuration:
- * `reps` applications to the plan's current search-direction buffer, with
- * CUDA events recorded on `stream` around every launch of each of the three
- * operator kernels (gather + column FFTs; row FFTs x filter spectrum; inverse
- * column FFTs + scatter).  ms_out (host [3]) receives the mean duration of one
- * launch of each kernel; launches_out (host [3], may be NULL) the launches of
- * each kernel per application.  Synchronises `stream`.  precision: FP64 or FP32. */
+ * `reps` applications to the plan's current search-direction buffer.  First
+ * with CUDA events recorded on `stream` around every launch of each of the
+ * three operator kernels (gather + column FFTs; row FFTs x filter spectrum;
+ * inverse column FFTs + scatter), the chunks run one after another; then
+ * `reps` applications as the solver launches them (chunks of one application
+ * overlapped on two plan streams) between two events on `stream`.
+ * ms_out (host [4]): [0..2] mean duration of one launch of each kernel, [3]
+ * mean duration of one application.  launches_out (host [3], may be NULL):
+ * launches of each kernel per application.  Synchronises `stream`.
+ * precision: FP64, FP32 or DF64. */
 madmap_status madmap_time_operator(madmap_plan_t plan, int32_t precision, int32_t reps, double* ms_out,
                                    int32_t* launches_out, void* stream);
 

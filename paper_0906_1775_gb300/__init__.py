@@ -160,7 +160,9 @@ def madmap_kernel_launch_count() -> int:
 
 
 def madmap_time_operator(h, precision, reps, stream=None):
-    ms = np.zeros(3)
+    """(ms[4], launches[3]): mean ms per launch of k_f1, k_f2, k_f3 (chunks in sequence) and, in
+    ms[3], mean ms of one application as solves launch it (chunks overlapped)."""
+    ms = np.zeros(4)
     n = np.zeros(3, dtype=np.int32)
     check(load().madmap_time_operator(h, precision, int(reps), ms.ctypes.data, n.ctypes.data,
                                       C.c_void_p(_stream_ptr(stream))), "madmap_time_operator")

@@ -133,7 +133,14 @@ struct Plan {
   df64* Hdf = nullptr;             // [n_filters][M] H64 as double-float pairs
   cdf64* twdf = nullptr;           // [M] tw64 as double-float pairs
   float4* csdf = nullptr;          // [n_t] cs64 as double-float pairs (IQU)
-  void* scratch = nullptr;         // tiles_per_chunk * M complex (float64 size)
+  void* scratch = nullptr;         // scratch_slots * tiles_per_chunk * M complex (float64 size)
+  int scratch_slots = 1;           // 2 when an application has several chunks (see op_stream)
+  // An application of several chunks alternates them between two streams,
+  // each with its own scratch slot, so one chunk's kernels overlap the
+  // previous chunk's tail and its scratch and pointing stay in L2.
+  cudaStream_t op_stream[2] = {nullptr, nullptr};
+  cudaEvent_t op_fork = nullptr;
+  cudaEvent_t op_join[2] = {nullptr, nullptr};
   int* dev_flag = nullptr;         // small device flag words
   size_t device_bytes = 0;
   std::vector<void*> allocs;
@@ -178,8 +185,10 @@ madmap_status op_launch(Plan* p, int prec, int in_mode, int out_mode, const void
 
 size_t f1_smem_bytes(const Plan* p, int prec);
 
-// Per-kernel event timing of the map-to-map operator (ms[3]: mean per launch).
-madmap_status op_time(Plan* p, int prec, const void* in, void* out, int reps, double ms[3], cudaStream_t s);
+// Event timing of the map-to-map operator: ms[0..2] mean duration of one
+// launch of each kernel (chunks run one after another on `s`), ms[3] mean
+// duration of one application as the solver launches it.
+madmap_status op_time(Plan* p, int prec, const void* in, void* out, int reps, double ms[4], cudaStream_t s);
 
 // Resident CTAs per SM of the operator kernels and CTAs per tile.
 void op_occupancy(const Plan* p, int prec, int& ctas_per_sm, int& ctas_per_tile);

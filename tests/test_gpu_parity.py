@@ -185,6 +185,30 @@ def test_iteration_drivers_agree(prec):
         assert rel_rms(host(m), host(runs[0][0])) < 1e-12
 
 
+def test_chunks_on_two_streams_match_one_launch():
+    """Several chunks per application run on two plan streams (inside the solver's
+    graphs too); operator and solves agree with the one-launch plan and the oracle."""
+    torch = _torch()
+    p = tiny_IQU(seed=23, n_per_det=2000, n_ivl_lo=100, n_ivl_hi=900)
+    S = system_for(p)
+    one = make_plan(p, fft_len=256)
+    many = make_plan(p, fft_len=256, tiles_per_chunk=2)
+    assert many.stats["n_tiles"] >= 8 and many.stats["tiles_per_chunk"] == 2
+    x = np.random.default_rng(2).standard_normal((S.n_obs, 3))
+    ref = S.H(x)
+    for prec, tol in [("fp64", FP64_OP_TOL), ("df64", FP64_OP_TOL), ("fp32", FP32_OP_TOL)]:
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        xin = x.astype(np.float32).astype(np.float64) if prec == "fp32" else x
+        y = host(many.apply_ATNA(cuda(x, dt), precision=prec))[0]
+        assert rel_rms(y, S.H(xin)) < tol, prec
+    d = cuda(p.d[0])
+    m1, i1 = one.solve(d, precision="mixed", rel_tol=1e-10, max_iter=300, max_outer=10)
+    for g in (2, 1, 0):
+        m2, i2 = many.solve(d, precision="mixed", rel_tol=1e-10, max_iter=300, max_outer=10, use_graph=g)
+        assert i2["iters"] == i1["iters"] and rel_rms(host(m2), host(m1)) < 1e-9, g
+    assert rel_rms(host(many.apply_ATNA(cuda(x, torch.float64)))[0], ref) < FP64_OP_TOL
+
+
 def test_iteration_drivers_agree_batched():
     p = _batched_problem("T", 3)
     plan = make_plan(p)
@@ -480,11 +504,14 @@ def test_backward_params_match_finite_differences():
                     vals.append(float(loss(torch.tensor(prm), d)))
             fd = (vals[0] - vals[1]) / (2 * h)
             assert gp[k, j] == pytest.approx(fd, rel=2e-3, abs=2e-3 * np.abs(gp).max())
-    # d-gradient: exact directional derivative for a quadratic loss
-    v = torch.randn_like(d)
+    # d-gradient: exact directional derivative for a quadratic loss.  dL/dd comes from the
+    # float32 weighting N^-1 (A lambda), so its error is relative to sum |g_t v_t|, not to the
+    # (possibly cancelling) sum itself.
+    v = torch.randn(d.shape, generator=torch.Generator(device="cuda").manual_seed(0), device="cuda")
     eps = 1e-2
     with torch.no_grad():
         fd = (float(loss(torch.tensor(base), d + eps * v)) - float(loss(torch.tensor(base), d - eps * v))) / (2 * eps)
-    assert float((dd.grad * v).sum()) == pytest.approx(fd, rel=1e-4)
+    gv = dd.grad * v
+    assert float(gv.sum()) == pytest.approx(fd, rel=1e-4, abs=1e-5 * float(gv.abs().sum()))
     # a common scale of every sigma leaves the map unchanged
     assert abs(float(np.sum(base[:, 0] * gp[:, 0]))) <= 1e-4 * float(np.sum(np.abs(base[:, 0] * gp[:, 0])))
