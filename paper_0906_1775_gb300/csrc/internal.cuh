@@ -133,6 +133,7 @@ struct Plan {
   df64* Hdf = nullptr;             // [n_filters][M] H64 as double-float pairs
   cdf64* twdf = nullptr;           // [M] tw64 as double-float pairs
   float4* csdf = nullptr;          // [n_t] cs64 as double-float pairs (IQU)
+  int2* pw = nullptr;              // [n_t] (pix_obs, bits of psi) for the float32 operator (IQU)
   void* scratch = nullptr;         // scratch_slots * tiles_per_chunk * M complex (float64 size)
   int scratch_slots = 1;           // 2 when an application has several chunks (see op_stream)
   // An application of several chunks alternates them between two streams,

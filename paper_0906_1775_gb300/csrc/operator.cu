@@ -43,6 +43,7 @@ struct OpArgs {
   const float* psi;
   const double2* cs64;
   const float4* csdf;
+  const int2* pw;      // (pixel, angle bits) per sample, IQU
   const void* in;
   long long in_stride;
   void* out;
@@ -152,6 +153,7 @@ struct LaneView {
   const float* psi;
   const double2* cs;
   const float4* csd;
+  const int2* pw;
   const void* in;
   void* out;
 };
@@ -171,6 +173,7 @@ __device__ __forceinline__ LaneView<Real> lane_view(const OpArgs& a, const Lane&
   v.psi = a.psi + ws;
   v.cs = a.cs64 + ws;
   v.csd = a.csdf + ws;
+  v.pw = a.pw + ws;
   if (IN == IN_TODF) v.in = static_cast<const float*>(a.in) + g.rhs * a.in_stride + ws;
   else if (IN == IN_TODR) v.in = static_cast<const Real*>(a.in) + g.rhs * a.in_stride + ws;
   else v.in = static_cast<const Real*>(a.in) + g.rhs * a.in_stride;
@@ -212,6 +215,28 @@ __device__ __forceinline__ void lane_angle<df64>(const LaneView<df64>& L, int n,
 }
 template <typename Real>
 __device__ __forceinline__ void finish_angle(Real& c, Real& s) {}
+
+// Pixel and weights' source of window position n of a lane: the float32
+// operator reads pixel and angle as one 8-byte pair; the others the pixel and
+// their cached cos/sin pairs.
+template <typename Real, int NS>
+__device__ __forceinline__ void load_pointing(const LaneView<Real>& L, int n, bool ok, int& pp, Real& c, Real& s) {
+  if (NS == 3 && std::is_same<Real, float>::value) {
+    if (ok) {
+      const int2 w = __ldg(L.pw + n);
+      pp = w.x;
+      c = (Real)__int_as_float(w.y);
+    } else {
+      pp = -1;
+      c = Real(0);
+    }
+    s = Real(0);
+  } else {
+    pp = ok ? __ldg(L.pix + n) : -1;
+    c = s = Real(0);
+    if (NS == 3) lane_angle<Real>(L, n, ok, c, s);
+  }
+}
 template <>
 __device__ __forceinline__ void finish_angle<float>(float& c, float& s) {
   const float psi = c;
@@ -305,9 +330,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
-          pp[l][u] = ok[l][u] ? __ldg(L[l].pix + nn[u]) : -1;
-          cc[l][u] = ss[l][u] = 0;
-          if (NS == 3) lane_angle<Real>(L[l], nn[u], ok[l][u], cc[l][u], ss[l][u]);
+          load_pointing<Real, NS>(L[l], nn[u], ok[l][u], pp[l][u], cc[l][u], ss[l][u]);
         }
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -463,9 +486,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
-          pp[l][u] = ok[l][u] ? __ldg(L[l].pix + nn[u]) : -1;
-          cc[l][u] = ss[l][u] = 0;
-          if (NS == 3) lane_angle<Real>(L[l], nn[u], ok[l][u], cc[l][u], ss[l][u]);
+          load_pointing<Real, NS>(L[l], nn[u], ok[l][u], pp[l][u], cc[l][u], ss[l][u]);
         }
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -585,6 +606,7 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
   a.psi = p->psi;
   a.cs64 = p->cs64;
   a.csdf = p->csdf;
+  a.pw = p->pw;
   a.scratch = p->scratch;
   constexpr bool DF = std::is_same<Real, df64>::value;
   a.H = DF ? (const void*)p->Hdf : sizeof(Real) == 8 ? (const void*)p->H64 : (const void*)p->H32;

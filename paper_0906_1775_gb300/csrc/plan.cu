@@ -365,6 +365,12 @@ __global__ void k_classify(const double* acc, const int* hits, int n_obs, int ns
 }
 
 // Rows of A observing excised pixels become zero (Section 4, gap filling).
+// (pixel, angle) pairs read with one 8-byte load by the float32 operator
+__global__ void k_pack_pw(const int* pix_obs, const float* psi, long long n, int2* pw) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    pw[t] = make_int2(pix_obs[t], __float_as_int(psi[t]));
+}
+
 __global__ void k_zero_excised_rows(int* pix_obs, long long n, const unsigned char* excised) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int p = pix_obs[t];
@@ -615,6 +621,7 @@ static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
     k_classify<<<grid_for(n_obs), 256, 0, s>>>(acc, hits, n_obs, ns, p->rcond_excise, p->rcond_fp64, p->P64,
                                                 p->P32, p->excised, p->fp64flag, counts);
   if (n > 0) k_zero_excised_rows<<<grid_for(n), 256, 0, s>>>(p->pix_obs, n, p->excised);
+  if (n > 0 && ns == 3) k_pack_pw<<<grid_for(n), 256, 0, s>>>(p->pix_obs, p->psi, n, p->pw);
   int hc[2] = {0, 0};
   e = cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -697,6 +704,7 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
     MM_TRY(dalloc_t(p, &p->psi, std::max(1LL, n)));
     MM_TRY(dalloc_t(p, &p->cs64, std::max(1LL, n)));
     MM_TRY(dalloc_t(p, &p->csdf, std::max(1LL, n)));
+    MM_TRY(dalloc_t(p, &p->pw, std::max(1LL, n)));
   }
   MM_TRYC(cudaMemsetAsync(p->dev_flag, 0, 16 * sizeof(int), s));
   MM_TRYC(cudaMemsetAsync(bits, 0, sizeof(unsigned) * n_words, s));
