@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--profile-graph", type=int, default=2, choices=[0, 1, 2],
                     help="iteration driver of the --profile-step solve: 2 device-side graph loop (as timed), "
                          "0 direct launches (every kernel visible to a profiler)")
+    ap.add_argument("--fft-len", type=int, default=0, help="override the plan's FFT length (0 = plan's choice)")
     ap.add_argument("--tpc", type=int, default=0, help="override the plan's tiles per launch chunk (0 = plan's choice)")
     ap.add_argument("--operator-only", type=int, default=0, metavar="R",
                     help="only build the plan and time R float32 operator applications (profiling runs)")
@@ -407,7 +408,8 @@ def main():
     p = make_config(2, seed=2000 + rank)
     pix = torch.from_numpy(p.pix).to(dev)
     psi = torch.from_numpy(p.psi).to(dev)
-    plan = mm.Plan(pix, psi, p.n_pix, p.interval_offsets, p.interval_filter, lib_lags(p), tiles_per_chunk=args.tpc)
+    plan = mm.Plan(pix, psi, p.n_pix, p.interval_offsets, p.interval_filter, lib_lags(p), tiles_per_chunk=args.tpc,
+                   fft_len=args.fft_len)
     del pix, psi
     if args.operator_only:
         ms, n = plan.time_operator("fp32", reps=args.operator_only)
