@@ -45,6 +45,7 @@ typedef struct madmap_plan_s* madmap_plan_t;
 typedef enum {
   MADMAP_OK = 0,
   MADMAP_WARN_MAXITER = 1,      /* result valid: lowest-residual iterate returned */
+  MADMAP_STOPPED = 2,           /* result valid: a checkpoint callback stopped the solve */
   MADMAP_ERR_INVALID_ARG = -1,  /* bad sizes, pointers, indices, offsets or filters */
   MADMAP_ERR_CUDA = -2,         /* a CUDA runtime call failed */
   MADMAP_ERR_OOM = -3,          /* device allocation failed (or was injected to fail) */
@@ -123,7 +124,32 @@ typedef struct {
   int32_t refine_precision; /* MIXED: arithmetic of the right-hand side b = A^T N^-1 d and of the
                               refinement residuals b - H x: MADMAP_DF64 (default) or MADMAP_FP64.
                               Vectors, dot products and the refinement update stay float64. */
+  /* Checkpoints (Section 5: the solver state is saved every 20 PCG iterations by
+   * default, as five map vectors and six scalars, and a run can restart from any
+   * of them).  FP64 solves of one right-hand side only. */
+  int32_t checkpoint_every;              /* write the state every this many iterations; 0 (default): never */
+  struct madmap_checkpoint_s* checkpoint; /* host: where the state is written (caller-owned buffers) */
+  int32_t (*on_checkpoint)(const struct madmap_checkpoint_s* state, void* user);
+                                         /* called after each checkpoint, may be NULL; a nonzero return
+                                            stops the solve with MADMAP_STOPPED (m = best iterate so far) */
+  void* checkpoint_user;                 /* passed to on_checkpoint */
 } madmap_solve_opts;
+
+/* Solver state at a checkpoint, independent of the launch configuration (a
+ * different plan over the same pointing and filters can resume it).  The five
+ * maps are host [n_obs][n_stokes] float64 arrays owned by the caller: the
+ * iterate x, the residual r, the preconditioned residual z = P r, the next
+ * search direction p, and the iterate with the lowest residual so far. */
+typedef struct madmap_checkpoint_s {
+  int32_t n_obs, n_stokes;   /* layout of the maps (checked on resume) */
+  int32_t iters;             /* PCG iterations done */
+  int32_t best_iter;         /* iteration of x_best */
+  double rz;                 /* <r, z> */
+  double bnorm;              /* ||b|| */
+  double rel_res;            /* ||r|| / ||b|| */
+  double best_rel_res;       /* relative residual of x_best */
+  double *x, *r, *z, *p, *x_best;
+} madmap_checkpoint;
 
 typedef struct {
   int32_t status;          /* madmap_status of the solve */
@@ -195,6 +221,17 @@ void madmap_solve_opts_default(madmap_solve_opts* opts);
  * rel_tol was not reached (m is still the best iterate). */
 madmap_status madmap_solve(madmap_plan_t plan, const float* d, double* m, const madmap_solve_opts* opts,
                            madmap_solve_info* info, void* stream);
+
+/* Continue an FP64 PCG solve from a checkpoint written by madmap_solve (or a
+ * previous resume) with the same pointing and filters: the iteration counts,
+ * lowest-residual rule and stopping tests carry on from the saved state
+ * (opts->rel_tol and opts->max_iter apply to the total), and further
+ * checkpoints may be written.  The right-hand side is not needed.  m: device
+ * double [n_obs][n_stokes], the best iterate.  state: host, read during the
+ * call.  MADMAP_ERR_INVALID_ARG when the state's layout does not match the
+ * plan or opts->precision is not FP64. */
+madmap_status madmap_solve_resume(madmap_plan_t plan, const madmap_checkpoint* state, double* m,
+                                  const madmap_solve_opts* opts, madmap_solve_info* info, void* stream);
 
 /* ------------------------------------------------------------------ allocation-free weighting */
 

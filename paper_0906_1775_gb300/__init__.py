@@ -23,7 +23,8 @@ __all__ = ["Plan", "noise_filter", "paper_fft_length", "MadmapError", "load", "l
            "madmap_plan_set_filters", "madmap_apply_ATNA", "madmap_rhs", "madmap_apply_ninv", "madmap_solve",
            "madmap_solve_batched", "madmap_solve_backward", "madmap_noise_filter_vjp", "MadmapSolve",
            "madmap_noise_filter", "madmap_paper_fft_length", "madmap_last_error", "madmap_kernel_launch_count",
-           "madmap_time_operator", "madmap_apply_ninv_noalloc"]
+           "madmap_time_operator", "madmap_apply_ninv_noalloc", "madmap_solve_resume", "save_checkpoint",
+           "load_checkpoint"]
 
 _PREC = {"fp64": MADMAP_FP64, "mixed": MADMAP_MIXED, "fp32": MADMAP_FP32, "df64": MADMAP_DF64,
          MADMAP_FP64: MADMAP_FP64, MADMAP_MIXED: MADMAP_MIXED, MADMAP_FP32: MADMAP_FP32, MADMAP_DF64: MADMAP_DF64}
@@ -106,6 +107,68 @@ def madmap_solve(h, d_ptr, m_ptr, opts, stream=None):
     st = load().madmap_solve(h, d_ptr, m_ptr, C.byref(opts), C.byref(info), C.c_void_p(_stream_ptr(stream)))
     check(st, "madmap_solve", allow_warn=True)
     return info
+
+
+def madmap_solve_resume(h, state, m_ptr, opts, stream=None):
+    """state: a filled _lib.madmap_checkpoint (host maps)."""
+    info = _lib.madmap_solve_info()
+    st = load().madmap_solve_resume(h, C.byref(state), m_ptr, C.byref(opts), C.byref(info),
+                                    C.c_void_p(_stream_ptr(stream)))
+    check(st, "madmap_solve_resume", allow_warn=True)
+    return info
+
+
+# ----------------------------------------------------------------- checkpoints
+_CKPT_MAPS = ("x", "r", "z", "p", "x_best")
+_CKPT_SCALARS = ("n_obs", "n_stokes", "iters", "best_iter", "rz", "bnorm", "rel_res", "best_rel_res")
+
+
+class _CheckpointBuffers:
+    """Host buffers a solve writes its checkpoints into, and the C callback that hands
+    each one to a Python function as a dict of numpy copies."""
+
+    def __init__(self, n_obs, n_stokes, on_checkpoint):
+        self.maps = {k: np.zeros((max(n_obs, 1), n_stokes)) for k in _CKPT_MAPS}
+        self.c = _lib.madmap_checkpoint()
+        for k in _CKPT_MAPS:
+            setattr(self.c, k, self.maps[k].ctypes.data)
+        self.user = on_checkpoint
+        self.error = None
+
+        def fn(ptr, _user):
+            try:
+                state = checkpoint_state(ptr.contents, self.maps)
+                return 1 if (self.user is not None and self.user(state)) else 0
+            except BaseException as e:  # keep the exception for the caller; stop the solve
+                self.error = e
+                return 1
+        self.fn = _lib.CHECKPOINT_FN(fn)
+
+
+def checkpoint_state(c, maps=None):
+    """Dict of a madmap_checkpoint: its six scalars, the layout and copies of its five maps."""
+    out = {k: getattr(c, k) for k in _CKPT_SCALARS}
+    n, ns = int(c.n_obs), int(c.n_stokes)
+    for k in _CKPT_MAPS:
+        if maps is not None:
+            out[k] = maps[k][:n].copy()
+        else:
+            out[k] = np.ctypeslib.as_array(C.cast(getattr(c, k), C.POINTER(C.c_double)), shape=(n, ns)).copy()
+    return out
+
+
+def save_checkpoint(path, state):
+    """Write a checkpoint dict to an .npz file (the paper keeps its checkpoints on disk)."""
+    np.savez(path, **{k: np.asarray(v) for k, v in state.items()})
+
+
+def load_checkpoint(path):
+    z = np.load(path)
+    out = {k: z[k] for k in _CKPT_MAPS}
+    for k in _CKPT_SCALARS:
+        v = z[k]
+        out[k] = int(v) if k in ("n_obs", "n_stokes", "iters", "best_iter") else float(v)
+    return out
 
 
 def madmap_solve_batched(h, n_rhs, d_ptr, m_ptr, opts, stream=None):
@@ -310,16 +373,52 @@ class Plan:
                                      gl.data_ptr() if gl is not None else None, o, stream)
         return gd, gl, {k: getattr(info, k) for k, _ in info._fields_}
 
+    def _checkpoints(self, o, checkpoint_every, on_checkpoint):
+        if not checkpoint_every:
+            return None
+        cb = _CheckpointBuffers(self.n_obs, self.n_stokes, on_checkpoint)
+        o.checkpoint_every = int(checkpoint_every)
+        o.checkpoint = C.pointer(cb.c)
+        o.on_checkpoint = cb.fn
+        return cb
+
     def solve(self, d, precision="fp64", max_iter=50, rel_tol=1e-6, max_outer=10, inner_rel_tol=1e-4,
-              use_graph=True, iters_per_sync=8, out=None, stream=None, refine="df64"):
+              use_graph=True, iters_per_sync=8, out=None, stream=None, refine="df64", checkpoint_every=0,
+              on_checkpoint=None):
         """Maximum-likelihood map [n_obs, n_stokes] (float64) and the solve info dict.
-        refine ("df64" or "fp64"): arithmetic of the mixed solve's right-hand side and residuals."""
+        refine ("df64" or "fp64"): arithmetic of the mixed solve's right-hand side and residuals.
+        checkpoint_every > 0 (float64 solves): every that many iterations the solver state is
+        passed to on_checkpoint(state dict); a true return stops the solve (status STOPPED)."""
         torch = _torch()
         o = self._opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync, refine)
+        cb = self._checkpoints(o, checkpoint_every, on_checkpoint)
         m = out if out is not None else torch.empty((self.n_obs, self.n_stokes), dtype=torch.float64,
                                                     device="cuda")
         info = madmap_solve(self._h, _dev_ptr(d.reshape(-1), torch.float32, "d"), _dev_ptr(m, torch.float64, "m"),
                             o, stream)
+        if cb is not None and cb.error is not None:
+            raise cb.error
+        return m, {k: getattr(info, k) for k, _ in info._fields_}
+
+    def solve_resume(self, state, max_iter=50, rel_tol=1e-6, use_graph=True, iters_per_sync=8, out=None,
+                     stream=None, checkpoint_every=0, on_checkpoint=None):
+        """Continue a float64 solve from a checkpoint dict (as passed to on_checkpoint or read by
+        load_checkpoint); returns the best map and the info dict of the whole solve."""
+        torch = _torch()
+        o = self._opts("fp64", max_iter, rel_tol, 1, 1e-4, use_graph, iters_per_sync, "fp64")
+        cb = self._checkpoints(o, checkpoint_every, on_checkpoint)
+        c = _lib.madmap_checkpoint()
+        keep = {}
+        for k in _CKPT_MAPS:
+            keep[k] = np.ascontiguousarray(state[k], dtype=np.float64).reshape(-1, self.n_stokes)
+            setattr(c, k, keep[k].ctypes.data)
+        for k in _CKPT_SCALARS:
+            setattr(c, k, state[k])
+        m = out if out is not None else torch.empty((self.n_obs, self.n_stokes), dtype=torch.float64,
+                                                    device="cuda")
+        info = madmap_solve_resume(self._h, c, _dev_ptr(m, torch.float64, "m"), o, stream)
+        if cb is not None and cb.error is not None:
+            raise cb.error
         return m, {k: getattr(info, k) for k, _ in info._fields_}
 
 

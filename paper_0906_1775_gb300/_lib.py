@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmadmap.s
 
 MADMAP_OK = 0
 MADMAP_WARN_MAXITER = 1
+MADMAP_STOPPED = 2
 MADMAP_ERR_INVALID_ARG = -1
 MADMAP_ERR_CUDA = -2
 MADMAP_ERR_OOM = -3
@@ -26,7 +27,7 @@ MADMAP_MIXED = 1
 MADMAP_FP32 = 2
 MADMAP_DF64 = 3
 
-STATUS_NAMES = {0: "OK", 1: "WARN_MAXITER", -1: "ERR_INVALID_ARG", -2: "ERR_CUDA", -3: "ERR_OOM",
+STATUS_NAMES = {0: "OK", 1: "WARN_MAXITER", 2: "STOPPED", -1: "ERR_INVALID_ARG", -2: "ERR_CUDA", -3: "ERR_OOM",
                 -4: "ERR_NOT_PD", -5: "ERR_TIMEOUT", -6: "ERR_INTERNAL"}
 
 
@@ -45,11 +46,22 @@ class madmap_plan_stats(C.Structure):
                                          "n_filters")] + [("n_samples", C.c_int64), ("device_bytes", C.c_int64)]
 
 
+class madmap_checkpoint(C.Structure):
+    _fields_ = [("n_obs", C.c_int32), ("n_stokes", C.c_int32), ("iters", C.c_int32), ("best_iter", C.c_int32),
+                ("rz", C.c_double), ("bnorm", C.c_double), ("rel_res", C.c_double), ("best_rel_res", C.c_double),
+                ("x", C.c_void_p), ("r", C.c_void_p), ("z", C.c_void_p), ("p", C.c_void_p), ("x_best", C.c_void_p)]
+
+
+CHECKPOINT_FN = C.CFUNCTYPE(C.c_int32, C.POINTER(madmap_checkpoint), C.c_void_p)
+
+
 class madmap_solve_opts(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("rel_tol", C.c_double), ("precision", C.c_int32),
                 ("max_outer", C.c_int32), ("inner_rel_tol", C.c_double), ("use_graph", C.c_int32),
                 ("iters_per_sync", C.c_int32),
-                ("refine_precision", C.c_int32)]
+                ("refine_precision", C.c_int32),
+                ("checkpoint_every", C.c_int32), ("checkpoint", C.POINTER(madmap_checkpoint)),
+                ("on_checkpoint", CHECKPOINT_FN), ("checkpoint_user", C.c_void_p)]
 
 
 class madmap_solve_info(C.Structure):
@@ -72,6 +84,8 @@ PROTOTYPES = [
     ("madmap_solve_opts_default", None, [C.POINTER(madmap_solve_opts)]),
     ("madmap_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(madmap_solve_opts),
                                C.POINTER(madmap_solve_info), C.c_void_p]),
+    ("madmap_solve_resume", C.c_int, [C.c_void_p, C.POINTER(madmap_checkpoint), C.c_void_p,
+                                      C.POINTER(madmap_solve_opts), C.POINTER(madmap_solve_info), C.c_void_p]),
     ("madmap_solve_batched", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(madmap_solve_opts),
                                        C.c_void_p, C.c_void_p]),
     ("madmap_solve_backward", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -115,7 +129,7 @@ class MadmapError(RuntimeError):
 
 
 def check(status: int, where: str, allow_warn: bool = False) -> int:
-    if status == MADMAP_OK or (allow_warn and status == MADMAP_WARN_MAXITER):
+    if status == MADMAP_OK or (allow_warn and status in (MADMAP_WARN_MAXITER, MADMAP_STOPPED)):
         return status
     msg = load().madmap_last_error().decode(errors="replace")
     raise MadmapError(status, where, msg)

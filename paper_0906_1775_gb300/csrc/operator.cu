@@ -256,14 +256,15 @@ __device__ __forceinline__ void finish_angle<float>(float& c, float& s) {
 // complex product costs more than the scattered load it would replace.
 template <typename C>
 __device__ __forceinline__ void build_split_twiddles(C* lo, C* hi, const C* twM, int logM, int logL) {
-  if (sizeof(C) != 8) return;
-  for (int i = threadIdx.x; i < (1 << logL); i += OP_THREADS) lo[i] = twM[i];
-  for (int i = threadIdx.x; i < (1 << (logM - logL)); i += OP_THREADS) hi[i] = twM[(long long)i << logL];
+  if constexpr (sizeof(C) == 8) {
+    for (int i = threadIdx.x; i < (1 << logL); i += OP_THREADS) lo[i] = twM[i];
+    for (int i = threadIdx.x; i < (1 << (logM - logL)); i += OP_THREADS) hi[i] = twM[(long long)i << logL];
+  }
 }
 template <typename C>
 __device__ __forceinline__ C split_twiddle(const C* lo, const C* hi, const C* twM, int m, int logL) {
-  if (sizeof(C) != 8) return twM[m];
-  return cmul(hi[m >> logL], lo[m & ((1 << logL) - 1)]);
+  if constexpr (sizeof(C) != 8) return twM[m];
+  else return cmul(hi[m >> logL], lo[m & ((1 << logL) - 1)]);
 }
 __host__ __device__ inline int split_log(int logM) { return (logM + 1) >> 1; }
 // Shared entries of the two split tables (none for float64).

@@ -32,6 +32,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cstring>
 #include <vector>
 
@@ -39,9 +40,12 @@
 
 namespace mm {
 
+// done: converged, failed or at max_iter.  halt: done, or paused at a
+// checkpoint (k >= pause_k); the kernels skip work while halt is set, but the
+// search direction of the pausing iteration is still formed.
 struct CgState {
   double rz, alpha, beta, bnorm, res, best_res, tol;
-  int k, best_k, dir_k, max_iter, done, status;
+  int k, best_k, dir_k, max_iter, done, status, halt, pause_k;
   unsigned counter;
   int pad;
 };
@@ -301,7 +305,7 @@ template <typename Real, int NS, typename Bt>
 __global__ void __launch_bounds__(NT) k_cg_init(Real* x, Real* r, Real* z, Real* p, Real* q, Real* xb, const Bt* b,
                                                 long long nvec, int n_obs, const double* P64, const float* P32,
                                                 const unsigned char* f64, CgState* st, double* partials,
-                                                double tol, int max_iter, const int* inactive) {
+                                                double tol, int max_iter, const int* inactive, int pause_k) {
   const long long o = blockIdx.y * nvec;
   x += o; r += o; z += o; p += o; q += o; xb += o; b += o;
   st += blockIdx.y;
@@ -346,6 +350,8 @@ __global__ void __launch_bounds__(NT) k_cg_init(Real* x, Real* r, Real* z, Real*
       st->alpha = st->beta = 0.0;
       const bool off = inactive && inactive[blockIdx.y];
       st->done = (off || st->bnorm == 0.0 || max_iter <= 0 || st->res <= tol) ? 1 : 0;
+      st->pause_k = pause_k;
+      st->halt = st->done || pause_k <= 0;
     }
   }
 }
@@ -354,7 +360,7 @@ template <typename Real, int NS>
 __global__ void __launch_bounds__(NT) k_cg_alpha(const Real* p, const Real* q, long long nvec, int n_obs,
                                                  CgState* st, double* partials) {
   st += blockIdx.y;
-  if (st->done) return;
+  if (st->halt) return;
   p += blockIdx.y * nvec;
   q += blockIdx.y * nvec;
   partials += (long long)blockIdx.y * NB * 4;
@@ -369,6 +375,7 @@ __global__ void __launch_bounds__(NT) k_cg_alpha(const Real* p, const Real* q, l
       if (!(s[0] > 0.0) || !isfinite(s[0])) {
         st->status = (int)MADMAP_ERR_NOT_PD;
         st->done = 1;
+        st->halt = 1;
       } else {
         st->alpha = st->rz / s[0];
       }
@@ -381,7 +388,7 @@ __global__ void __launch_bounds__(NT) k_cg_update(Real* x, Real* r, Real* z, con
                                                   long long nvec, int n_obs, const double* P64, const float* P32,
                                                   const unsigned char* f64, CgState* st, double* partials) {
   st += blockIdx.y;
-  if (st->done) return;
+  if (st->halt) return;
   const long long o = blockIdx.y * nvec;
   x += o; r += o; z += o; p += o; q += o;
   partials += (long long)blockIdx.y * NB * 4;
@@ -419,6 +426,7 @@ __global__ void __launch_bounds__(NT) k_cg_update(Real* x, Real* r, Real* z, con
         st->best_k = k;
       }
       if (res <= st->tol || k >= st->max_iter || !isfinite(res)) st->done = 1;
+      st->halt = st->done || k >= st->pause_k;
       st->beta = s[0] / st->rz;
       st->rz = s[0];
     }
@@ -560,9 +568,9 @@ static void enqueue_iteration(Plan* p, SolveBuffers* sb, const Batch& B, cudaStr
   const long long nv = sb->nvec;
   const dim3 g(grid_vec(n), B.n_rhs);
   if (B.ts)
-    *st = op_launch_set(p, sizeof(Real) == 8, IN_MAP, OUT_MAP, pp, q, nv, nv, &sb->st->done, ST_STRIDE, B.ts, s);
+    *st = op_launch_set(p, sizeof(Real) == 8, IN_MAP, OUT_MAP, pp, q, nv, nv, &sb->st->halt, ST_STRIDE, B.ts, s);
   else
-    *st = op_launch(p, sizeof(Real) == 8, IN_MAP, OUT_MAP, pp, q, 0, 0, 1, &sb->st->done, s);
+    *st = op_launch(p, sizeof(Real) == 8, IN_MAP, OUT_MAP, pp, q, 0, 0, 1, &sb->st->halt, s);
   count_launches(3);
   k_cg_alpha<Real, NS><<<g, NT, 0, s>>>(pp, q, nv, n, sb->st, sb->partials);
   k_cg_update<Real, NS><<<g, NT, 0, s>>>(x, r, z, pp, q, nv, n, p->P64, p->P32, p->fp64flag, sb->st, sb->partials);
@@ -614,7 +622,7 @@ static madmap_status enqueue_chunk(Plan* p, SolveBuffers* sb, const Batch& B, in
 // not done, and never beyond the cap (loop[1]) iterations.
 __global__ void k_loop_cond(const CgState* st, int n_rhs, int* loop, cudaGraphConditionalHandle h) {
   int live = 0;
-  for (int r = threadIdx.x; r < n_rhs; r += 32) live |= !st[r].done;
+  for (int r = threadIdx.x; r < n_rhs; r += 32) live |= !st[r].halt;
   live = __any_sync(0xffffffffu, live);
   if (threadIdx.x == 0) {
     const int it = loop[0] + 1;
@@ -676,15 +684,21 @@ struct PcgResult {
 // precision.  b: Bt vectors in the padded working layout, nvec apart.
 // inactive (device, may be NULL): right-hand sides to leave untouched.
 // Results: best iterates in sb->xb, summaries in out[rhs].
+// pause_k: iteration at which to halt for a checkpoint (INT_MAX: never).
+// init = false continues from the state already in the buffers (a resumed or
+// paused solve) instead of starting from x = 0.
 template <typename Real, int NS, typename Bt>
 static madmap_status run_pcg(Plan* p, SolveBuffers* sb, const Batch& B, const Bt* b, const int* inactive, double tol,
-                             int max_iter, int per_sync, int graph_mode, cudaStream_t s, std::vector<PcgResult>& out) {
+                             int max_iter, int per_sync, int graph_mode, cudaStream_t s, std::vector<PcgResult>& out,
+                             int pause_k = INT_MAX, bool init = true) {
   const int n = p->n_obs, R = B.n_rhs;
-  count_launches(1);
-  k_cg_init<Real, NS, Bt><<<dim3(grid_vec(n), R), NT, 0, s>>>(
-      (Real*)sb->x, (Real*)sb->r, (Real*)sb->z, (Real*)sb->p, (Real*)sb->q, (Real*)sb->xb, b, sb->nvec, n, p->P64,
-      p->P32, p->fp64flag, sb->st, sb->partials, tol, max_iter, inactive);
-  MM_CUDA(cudaGetLastError());
+  if (init) {
+    count_launches(1);
+    k_cg_init<Real, NS, Bt><<<dim3(grid_vec(n), R), NT, 0, s>>>(
+        (Real*)sb->x, (Real*)sb->r, (Real*)sb->z, (Real*)sb->p, (Real*)sb->q, (Real*)sb->xb, b, sb->nvec, n, p->P64,
+        p->P32, p->fp64flag, sb->st, sb->partials, tol, max_iter, inactive, pause_k);
+    MM_CUDA(cudaGetLastError());
+  }
   if (graph_mode == 2 && !sb->w_unsupported) {
     // one graph launch runs every iteration on the device
     if (build_while_graph<Real, NS>(p, sb, B, s) != MADMAP_OK) {
@@ -724,7 +738,7 @@ static madmap_status run_pcg(Plan* p, SolveBuffers* sb, const Batch& B, const Bt
   const int G = std::max(1, per_sync);
   auto all_done = [&](int sl) {
     for (int k = 0; k < R; ++k)
-      if (!sb->host_st[sl * sb->cap_rhs + k].done) return false;
+      if (!sb->host_st[sl * sb->cap_rhs + k].halt) return false;
     return true;
   };
   // one chunk in flight ahead of the host check
@@ -766,6 +780,65 @@ static madmap_status run_pcg(Plan* p, SolveBuffers* sb, const Batch& B, const Bt
 // right-hand side of the batch, b already in sb64->b64.  On return *x_pad
 // points at the best iterates (padded layout, nvec apart) and I holds the
 // per-rhs summaries (fp64_applies counts the right-hand side's own as 1).
+// Copies the float64 solver state (single right-hand side) to a checkpoint:
+// the padded device vectors are unpacked through b64, which the float64 PCG
+// no longer needs once started.
+template <int NS>
+static madmap_status write_checkpoint(Plan* p, SolveBuffers* sb, const CgState& h, madmap_checkpoint* c,
+                                      cudaStream_t s) {
+  const int n = p->n_obs, ns = p->n_stokes, np = p->ns_pad;
+  const long long user = (long long)n * ns;
+  const double* src[5] = {(const double*)sb->x, (const double*)sb->r, (const double*)sb->z, (const double*)sb->p,
+                          (const double*)sb->xb};
+  double* dst[5] = {c->x, c->r, c->z, c->p, c->x_best};
+  for (int k = 0; k < 5; ++k) {
+    count_launches(1);
+    k_unpack<double, double><<<grid_vec(user), NT, 0, s>>>(src[k], sb->b64, n, ns, np);
+    MM_CUDA(cudaMemcpyAsync(dst[k], sb->b64, sizeof(double) * user, cudaMemcpyDeviceToHost, s));
+  }
+  MM_CUDA(cudaStreamSynchronize(s));
+  c->n_obs = n;
+  c->n_stokes = ns;
+  c->iters = h.k;
+  c->best_iter = h.best_k;
+  c->rz = h.rz;
+  c->bnorm = h.bnorm;
+  c->rel_res = h.res;
+  c->best_rel_res = h.best_res;
+  return MADMAP_OK;
+}
+
+// Float64 PCG, in segments of opts.checkpoint_every iterations when
+// checkpoints are requested: at each pause the state is written to
+// opts.checkpoint and opts.on_checkpoint may stop the solve (*stopped = 1).
+// init = false continues from the state in the buffers (a resume).
+template <int NS>
+static madmap_status pcg64(Plan* p, SolveBuffers* sb, const Batch& B, const madmap_solve_opts& o, cudaStream_t s,
+                           std::vector<PcgResult>& R, bool init, int first_pause, int* stopped) {
+  const int every = (o.checkpoint_every > 0 && B.n_rhs == 1) ? o.checkpoint_every : 0;
+  int pause = every ? first_pause : INT_MAX;
+  *stopped = 0;
+  while (true) {
+    madmap_status st = run_pcg<double, NS, double>(p, sb, B, sb->b64, nullptr, o.rel_tol, o.max_iter,
+                                                   o.iters_per_sync, o.use_graph, s, R, pause, init);
+    if (st != MADMAP_OK) return st;
+    init = false;
+    if (!every) return MADMAP_OK;
+    CgState h;
+    MM_CUDA(cudaMemcpy(&h, sb->st, sizeof(CgState), cudaMemcpyDeviceToHost));
+    if (h.done) return MADMAP_OK;
+    st = write_checkpoint<NS>(p, sb, h, o.checkpoint, s);
+    if (st != MADMAP_OK) return st;
+    if (o.on_checkpoint && o.on_checkpoint(o.checkpoint, o.checkpoint_user) != 0) {
+      *stopped = 1;
+      return MADMAP_OK;
+    }
+    pause = h.k + every;
+    const int ctl[2] = {0, pause};  // halt, pause_k
+    MM_CUDA(cudaMemcpyAsync(&sb->st->halt, ctl, sizeof(ctl), cudaMemcpyHostToDevice, s));
+  }
+}
+
 template <int NS>
 static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, const madmap_solve_opts& o,
                                 std::vector<madmap_solve_info>& I, cudaStream_t s, const double** x_pad) {
@@ -776,8 +849,8 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
   madmap_status st = MADMAP_OK;
   std::vector<PcgResult> R;
   if (o.precision == MADMAP_FP64) {
-    st = run_pcg<double, NS, double>(p, sb64, B, sb64->b64, nullptr, o.rel_tol, o.max_iter, o.iters_per_sync, graph, s,
-                                     R);
+    int stopped = 0;
+    st = pcg64<NS>(p, sb64, B, o, s, R, true, o.checkpoint_every, &stopped);
     if (st != MADMAP_OK) return st;
     for (int k = 0; k < n_rhs; ++k) {
       I[k].iters = R[k].iters;
@@ -787,6 +860,7 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
       I[k].final_rel_res = R[k].final_res;
       I[k].best_rel_res = R[k].best_res;
       I[k].status = R[k].status != 0 ? R[k].status : (R[k].best_res <= o.rel_tol ? MADMAP_OK : MADMAP_WARN_MAXITER);
+      if (stopped && I[k].status == MADMAP_WARN_MAXITER) I[k].status = MADMAP_STOPPED;
     }
     *x_pad = (const double*)sb64->xb;
     return MADMAP_OK;
@@ -936,6 +1010,64 @@ static madmap_status solve_impl(Plan* p, int n_rhs, const float* d, double* m, c
   const int worst = worst_status(I, t_all);
   if (info) memcpy(info, I.data(), sizeof(madmap_solve_info) * n_rhs);
   return (madmap_status)worst;
+}
+
+// Continue a float64 solve from a checkpoint (single right-hand side).
+template <int NS>
+static madmap_status resume_impl(Plan* p, const madmap_checkpoint* c, double* m, const madmap_solve_opts& o,
+                                 madmap_solve_info* info, cudaStream_t s) {
+  auto t_start = std::chrono::steady_clock::now();
+  Batch B;
+  SolveBuffers* sb = nullptr;
+  madmap_status st = get_buffers(p, true, 1, &sb);
+  if (st != MADMAP_OK) return st;
+  const int n = p->n_obs, ns = p->n_stokes, np = p->ns_pad;
+  const long long user = (long long)n * ns;
+  const double* src[5] = {c->x, c->r, c->z, c->p, c->x_best};
+  double* dst[5] = {(double*)sb->x, (double*)sb->r, (double*)sb->z, (double*)sb->p, (double*)sb->xb};
+  for (int k = 0; k < 5; ++k) {
+    MM_CUDA(cudaMemcpyAsync(sb->b64, src[k], sizeof(double) * user, cudaMemcpyHostToDevice, s));
+    count_launches(1);
+    k_pack<double, double><<<grid_vec((long long)n * np), NT, 0, s>>>(sb->b64, dst[k], n, ns, np);
+  }
+  MM_CUDA(cudaMemsetAsync(sb->q, 0, sizeof(double) * sb->nvec, s));
+  const int every = o.checkpoint_every > 0 ? o.checkpoint_every : 0;
+  CgState h;
+  memset(&h, 0, sizeof(h));
+  h.rz = c->rz;
+  h.bnorm = c->bnorm;
+  h.res = c->rel_res;
+  h.best_res = c->best_rel_res;
+  h.tol = o.rel_tol;
+  h.k = c->iters;
+  h.best_k = c->best_iter;
+  h.dir_k = c->iters;  // p already holds the next search direction
+  h.max_iter = o.max_iter;
+  h.done = (!(c->bnorm > 0.0) || c->rel_res <= o.rel_tol || c->iters >= o.max_iter) ? 1 : 0;
+  h.pause_k = every ? c->iters + every : INT_MAX;
+  h.halt = h.done;
+  MM_CUDA(cudaMemcpyAsync(sb->st, &h, sizeof(CgState), cudaMemcpyHostToDevice, s));
+  std::vector<PcgResult> R;
+  int stopped = 0;
+  st = pcg64<NS>(p, sb, B, o, s, R, false, h.pause_k, &stopped);
+  if (st != MADMAP_OK) return st;
+  count_launches(1);
+  k_unpack<double, double><<<grid_vec(user), NT, 0, s>>>((const double*)sb->xb, m, n, ns, np);
+  MM_CUDA(cudaStreamSynchronize(s));
+  MM_CUDA(cudaGetLastError());
+  madmap_solve_info I;
+  memset(&I, 0, sizeof(I));
+  I.iters = R[0].iters;
+  I.outer_iters = 1;
+  I.best_iter = R[0].best_iter;
+  I.fp64_applies = R[0].iters - c->iters;
+  I.final_rel_res = R[0].final_res;
+  I.best_rel_res = R[0].best_res;
+  I.status = R[0].status != 0 ? R[0].status : (R[0].best_res <= o.rel_tol ? MADMAP_OK : MADMAP_WARN_MAXITER);
+  if (stopped && I.status == MADMAP_WARN_MAXITER) I.status = MADMAP_STOPPED;
+  I.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  if (info) *info = I;
+  return (madmap_status)I.status;
 }
 
 // ---------------------------------------------------------------- backward
@@ -1205,6 +1337,10 @@ extern "C" void madmap_solve_opts_default(madmap_solve_opts* o) {
   o->use_graph = 2;
   o->iters_per_sync = 8;
   o->refine_precision = MADMAP_DF64;
+  o->checkpoint_every = 0;
+  o->checkpoint = nullptr;
+  o->on_checkpoint = nullptr;
+  o->checkpoint_user = nullptr;
 }
 
 extern "C" madmap_status madmap_solve(madmap_plan_t plan, const float* d, double* m, const madmap_solve_opts* opts,
@@ -1218,6 +1354,9 @@ extern "C" madmap_status madmap_solve(madmap_plan_t plan, const float* d, double
   if (opts) o = *opts;
   MM_CHECK(o.precision == MADMAP_FP64 || o.precision == MADMAP_MIXED, MADMAP_ERR_INVALID_ARG,
            "solve: precision must be FP64 or MIXED");
+  MM_CHECK(o.checkpoint_every <= 0 || (o.precision == MADMAP_FP64 && o.checkpoint && o.checkpoint->x &&
+                                       o.checkpoint->r && o.checkpoint->z && o.checkpoint->p && o.checkpoint->x_best),
+           MADMAP_ERR_INVALID_ARG, "solve: checkpoints need precision FP64 and a checkpoint with five host maps");
   MM_CHECK(o.max_iter >= 0 && o.rel_tol >= 0 && o.iters_per_sync >= 1 && o.max_outer >= 1 &&
                o.inner_rel_tol > 0 && o.inner_rel_tol < 1 &&
                (o.refine_precision == MADMAP_DF64 || o.refine_precision == MADMAP_FP64),
@@ -1241,6 +1380,42 @@ extern "C" madmap_status madmap_solve(madmap_plan_t plan, const float* d, double
   return st;
 }
 
+extern "C" madmap_status madmap_solve_resume(madmap_plan_t plan, const madmap_checkpoint* state, double* m,
+                                             const madmap_solve_opts* opts, madmap_solve_info* info, void* stream) {
+  MM_CHECK(plan && state, MADMAP_ERR_INVALID_ARG, "solve_resume: NULL plan or state");
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  MM_CHECK(state->n_obs == p->n_obs && state->n_stokes == p->n_stokes, MADMAP_ERR_INVALID_ARG,
+           "solve_resume: the state's map layout does not match the plan");
+  MM_CHECK(p->n_obs == 0 || (m && state->x && state->r && state->z && state->p && state->x_best),
+           MADMAP_ERR_INVALID_ARG, "solve_resume: NULL map");
+  MM_CHECK(state->iters >= 0 && state->best_iter >= 0 && state->best_iter <= state->iters, MADMAP_ERR_INVALID_ARG,
+           "solve_resume: bad iteration counts");
+  madmap_solve_opts o;
+  madmap_solve_opts_default(&o);
+  if (opts) o = *opts;
+  MM_CHECK(o.precision == MADMAP_FP64, MADMAP_ERR_INVALID_ARG, "solve_resume: precision must be FP64");
+  MM_CHECK(o.max_iter >= 0 && o.rel_tol >= 0 && o.iters_per_sync >= 1, MADMAP_ERR_INVALID_ARG,
+           "solve_resume: bad options");
+  MM_CHECK(o.checkpoint_every <= 0 || (o.checkpoint && o.checkpoint->x && o.checkpoint->r && o.checkpoint->z &&
+                                       o.checkpoint->p && o.checkpoint->x_best),
+           MADMAP_ERR_INVALID_ARG, "solve_resume: checkpoints need a checkpoint with five host maps");
+  cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  if (p->n_obs == 0) {
+    if (info) memset(info, 0, sizeof(*info));
+    return MADMAP_OK;
+  }
+  if (!p->solve_stream) {
+    MM_CUDA(cudaStreamCreateWithFlags(&p->solve_stream, cudaStreamNonBlocking));
+    MM_CUDA(cudaEventCreateWithFlags(&p->solve_event, cudaEventDisableTiming));
+  }
+  cudaStream_t s = p->solve_stream;
+  MM_CUDA(cudaEventRecord(p->solve_event, caller));
+  MM_CUDA(cudaStreamWaitEvent(s, p->solve_event, 0));
+  madmap_status st = p->n_stokes == 1 ? resume_impl<1>(p, state, m, o, info, s) : resume_impl<3>(p, state, m, o, info, s);
+  cudaStreamSynchronize(s);
+  return st;
+}
+
 extern "C" madmap_status madmap_solve_backward(madmap_plan_t plan, const float* d, const double* m,
                                                const double* grad_m, float* grad_d, double* grad_lags,
                                                const madmap_solve_opts* opts, madmap_solve_info* info, void* stream) {
@@ -1253,6 +1428,7 @@ extern "C" madmap_status madmap_solve_backward(madmap_plan_t plan, const float* 
   if (opts) o = *opts;
   MM_CHECK(o.precision == MADMAP_FP64 || o.precision == MADMAP_MIXED, MADMAP_ERR_INVALID_ARG,
            "solve_backward: precision must be FP64 or MIXED");
+  MM_CHECK(o.checkpoint_every <= 0, MADMAP_ERR_INVALID_ARG, "solve_backward: checkpoints are for forward solves");
   MM_CHECK(o.max_iter >= 0 && o.rel_tol >= 0 && o.iters_per_sync >= 1 && o.max_outer >= 1 &&
                o.inner_rel_tol > 0 && o.inner_rel_tol < 1 &&
                (o.refine_precision == MADMAP_DF64 || o.refine_precision == MADMAP_FP64),
@@ -1290,6 +1466,7 @@ extern "C" madmap_status madmap_solve_batched(madmap_plan_t plan, int32_t n_rhs,
   if (opts) o = *opts;
   MM_CHECK(o.precision == MADMAP_FP64 || o.precision == MADMAP_MIXED, MADMAP_ERR_INVALID_ARG,
            "solve_batched: precision must be FP64 or MIXED");
+  MM_CHECK(o.checkpoint_every <= 0, MADMAP_ERR_INVALID_ARG, "solve_batched: checkpoints are for single solves");
   MM_CHECK(o.max_iter >= 0 && o.rel_tol >= 0 && o.iters_per_sync >= 1 && o.max_outer >= 1 &&
                o.inner_rel_tol > 0 && o.inner_rel_tol < 1 &&
                (o.refine_precision == MADMAP_DF64 || o.refine_precision == MADMAP_FP64),
