@@ -1104,51 +1104,81 @@ __global__ void k_mask_excised(double* b, long long nvec_pixels, int ns_pad, con
     if (excised[i / ns_pad]) b[i] = 0.0;
 }
 
-// Lag correlation sum_{|t-t'|=tau} a_t r_t' by direct sums: CTA (tau chunk,
-// work item) covers lags [tau0, tau0 + LT) over the samples [t_lo, t_hi) of
-// one interval, in tiles of TT samples staged in shared memory; each thread
-// owns one lag, sums a tile in float32 and folds it into a float64 total,
-// then adds the total to grad[filter][tau] (float64 atomics, one per lag and
-// work item).
+// Lag correlation sum_{|t-t'|=tau} a_t r_t' by direct sums: CTA (lag block,
+// work item) covers CORR_LB lags over the samples [t_lo, t_hi) of one
+// interval, in tiles of CORR_TT samples staged in shared memory, and adds
+// its totals to grad[filter][tau] (float64 atomics, one per lag and item).
 struct CorrItem {
   long long lo, hi;      // interval bounds
   long long t_lo, t_hi;  // samples of this item
   int filter, pad;
 };
 
-constexpr int CORR_LT = 256;
-constexpr int CORR_TT = 1024;
+// Lag correlation sum_{t in item} a_t (r_{t+tau} + r_{t-tau}) (r outside the
+// interval is 0; tau = 0 counts once).  Each thread owns CORR_R consecutive
+// lags: per block of CORR_R samples it loads 2 CORR_R - 1 values of r per
+// direction into registers and does CORR_R^2 multiply-adds per direction from
+// them.  Shared r is padded one word per 8 so the threads' stride-8 reads hit
+// distinct banks.  float32 products summed over a tile of CORR_TT samples,
+// float64 across tiles and items.
+constexpr int CORR_R = 8;
+constexpr int CORR_T = 256;
+constexpr int CORR_LB = CORR_R * CORR_T;  // lags per block
+constexpr int CORR_TT = 1024;             // samples per tile
+constexpr int CORR_W = CORR_TT + CORR_LB;
+__device__ __forceinline__ int cpad(int i) { return i + (i >> 3); }
 
-__global__ void __launch_bounds__(CORR_LT) k_lag_corr(const float* a, const float* r, const CorrItem* items,
-                                                      int n_lags, double* grad) {
+__global__ void __launch_bounds__(CORR_T) k_lag_corr(const float* a, const float* r, const CorrItem* items,
+                                                    int n_lags, double* grad) {
   __shared__ float sa[CORR_TT];
-  __shared__ float sp[CORR_TT + CORR_LT];  // r[t + tau0 + j]
-  __shared__ float sm[CORR_TT + CORR_LT];  // r[t - tau0 - (LT - 1) + j]
+  __shared__ float sp[CORR_W + CORR_W / 8];  // r[t0 + tau0 + i]
+  __shared__ float sm[CORR_W + CORR_W / 8];  // r[t0 - tau0 - (CORR_LB - 1) + i]
   const CorrItem it = items[blockIdx.y];
-  const int tau0 = blockIdx.x * CORR_LT;
-  const int j = threadIdx.x;
-  const int tau = tau0 + j;
-  double total = 0.0;
+  const int tau0 = blockIdx.x * CORR_LB;
+  const int base = CORR_R * threadIdx.x;
+  double tot[CORR_R];
+#pragma unroll
+  for (int j = 0; j < CORR_R; ++j) tot[j] = 0.0;
   for (long long t0 = it.t_lo; t0 < it.t_hi; t0 += CORR_TT) {
     const int nt = (int)min((long long)CORR_TT, it.t_hi - t0);
     __syncthreads();
-    for (int k = j; k < CORR_TT; k += CORR_LT) sa[k] = k < nt ? a[t0 + k] : 0.f;
-    for (int k = j; k < CORR_TT + CORR_LT; k += CORR_LT) {
-      const long long tp = t0 + tau0 + k;
-      const long long tm = t0 - tau0 - (CORR_LT - 1) + k;
-      sp[k] = (tp >= it.lo && tp < it.hi) ? r[tp] : 0.f;
-      sm[k] = (tm >= it.lo && tm < it.hi) ? r[tm] : 0.f;
+    for (int k = threadIdx.x; k < CORR_TT; k += CORR_T) sa[k] = k < nt ? a[t0 + k] : 0.f;
+    for (int i = threadIdx.x; i < CORR_W; i += CORR_T) {
+      const long long tp = t0 + tau0 + i;
+      const long long tm = t0 - tau0 - (CORR_LB - 1) + i;
+      sp[cpad(i)] = (tp >= it.lo && tp < it.hi) ? r[tp] : 0.f;
+      sm[cpad(i)] = (tm >= it.lo && tm < it.hi) ? r[tm] : 0.f;
     }
     __syncthreads();
-    float acc = 0.f;
-    if (tau == 0) {
-      for (int k = 0; k < nt; ++k) acc = fmaf(sa[k], sp[k + j], acc);
-    } else {
-      for (int k = 0; k < nt; ++k) acc = fmaf(sa[k], sp[k + j] + sm[k + (CORR_LT - 1) - j], acc);
+    float acc1[CORR_R], acc2[CORR_R];
+#pragma unroll
+    for (int j = 0; j < CORR_R; ++j) acc1[j] = acc2[j] = 0.f;
+    // samples past nt are zero in sa, so whole blocks of CORR_R are safe
+    for (int k0 = 0; k0 < nt; k0 += CORR_R) {
+      float v1[2 * CORR_R - 1], v2[2 * CORR_R - 1];
+#pragma unroll
+      for (int q = 0; q < 2 * CORR_R - 1; ++q) {
+        v1[q] = sp[cpad(k0 + base + q)];
+        v2[q] = sm[cpad(k0 + CORR_LB - CORR_R - base + q)];
+      }
+#pragma unroll
+      for (int kk = 0; kk < CORR_R; ++kk) {
+        const float ak = sa[k0 + kk];
+#pragma unroll
+        for (int j = 0; j < CORR_R; ++j) {
+          acc1[j] = fmaf(ak, v1[kk + j], acc1[j]);
+          acc2[j] = fmaf(ak, v2[kk - j + CORR_R - 1], acc2[j]);
+        }
+      }
     }
-    total += (double)acc;
+#pragma unroll
+    for (int j = 0; j < CORR_R; ++j) tot[j] += (double)acc1[j] + (tau0 + base + j == 0 ? 0.0 : (double)acc2[j]);
   }
-  if (tau < n_lags) atomicAdd(grad + (long long)it.filter * n_lags + tau, total);
+#pragma unroll
+  for (int j = 0; j < CORR_R; ++j) {
+    const int tau = tau0 + base + j;
+    if (tau < n_lags) atomicAdd(grad + (long long)it.filter * n_lags + tau, tot[j]);
+  }
 }
 
 template <int NS>
@@ -1208,8 +1238,8 @@ static madmap_status backward_impl(Plan* p, const float* d, const double* m, con
     for (int y0 = 0; y0 < p->n_corr_items; y0 += 65535) {
       const int ny = std::min(65535, p->n_corr_items - y0);
       count_launches(1);
-      k_lag_corr<<<dim3((p->n_lags + CORR_LT - 1) / CORR_LT, ny), CORR_LT, 0, s>>>(p->bw_a, p->bw_r, items + y0,
-                                                                                  p->n_lags, grad_lags);
+      k_lag_corr<<<dim3((p->n_lags + CORR_LB - 1) / CORR_LB, ny), CORR_T, 0, s>>>(p->bw_a, p->bw_r, items + y0,
+                                                                                 p->n_lags, grad_lags);
     }
   }
   MM_CUDA(cudaStreamSynchronize(s));
