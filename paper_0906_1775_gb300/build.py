@@ -72,7 +72,7 @@ def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) 
     if jobs or force or not os.path.exists(LIB):
         libdir = _cuda_lib_dir(nvcc)
         cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs,
-               "-Xlinker", "-rpath," + libdir]
+               "-Xlinker", "-rpath," + libdir, "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)

@@ -134,6 +134,10 @@ struct Plan {
   cdf64* twdf = nullptr;           // [M] tw64 as double-float pairs
   float4* csdf = nullptr;          // [n_t] cs64 as double-float pairs (IQU)
   int2* pw = nullptr;              // [n_t] (pix_obs, bits of psi) for the float32 operator (IQU)
+  int* hits = nullptr;             // [n_obs] samples per pixel before excision
+  double* G = nullptr;             // [n_filters][n_obs][6] (IQU) or [n_filters][n_obs] (T): sums of w w^T
+                                   // per filter, kept when they fit 512 MB (fast filter changes)
+  bool pre_built = false;          // the preconditioner has been built once
   void* scratch = nullptr;         // scratch_slots * tiles_per_chunk * M complex (float64 size)
   int scratch_slots = 1;           // 2 when an application has several chunks (see op_stream)
   // An application of several chunks alternates them between two streams,

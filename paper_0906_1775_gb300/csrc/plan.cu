@@ -7,8 +7,10 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.cuh"
@@ -268,21 +270,43 @@ __device__ __forceinline__ int interval_of(const long long* off, int n_ivl, long
 // A^T W^-1 A with W^-1 = diag(N^-1), i.e. each sample weighted by f(0) of its
 // interval's filter.  Also stores (cos 2psi, sin 2psi) in float64 for the FP64
 // operator.  acc layout per pixel: T: [wsum]; IQU: [6 AtA | 6 AtWA].
+// One pass over the samples: hit counts, and either the per-filter sums of
+// w w^T of every pixel (G[filter][pixel][6], or [filter][pixel] for T) or
+// directly A^T A and A^T W^-1 A (acc).  The first pass also stores the
+// float64 and double-float weights; later passes read them back.
 __global__ void k_accumulate(const int* pix_obs, const float* psi, long long n, const long long* off, int n_ivl,
                              const int* ivl_filter, const double* f0, int ns, double* acc, int* hits,
-                             double2* cs64, float4* csdf) {
+                             double2* cs64, float4* csdf, double* G, int n_obs, int first) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     double c = 1.0, s = 0.0;
     if (ns == 3) {
-      sincos(2.0 * (double)psi[t], &s, &c);
-      cs64[t] = make_double2(c, s);
-      const df64 cd(c), sd(s);
-      csdf[t] = make_float4(cd.hi, cd.lo, sd.hi, sd.lo);
+      if (first) {
+        sincos(2.0 * (double)psi[t], &s, &c);
+        cs64[t] = make_double2(c, s);
+        const df64 cd(c), sd(s);
+        csdf[t] = make_float4(cd.hi, cd.lo, sd.hi, sd.lo);
+      } else {
+        const double2 cs = cs64[t];
+        c = cs.x;
+        s = cs.y;
+      }
     }
     const int p = pix_obs[t];
     if (p < 0) continue;
-    const double w0 = f0[ivl_filter[interval_of(off, n_ivl, t)]];
+    const int f = ivl_filter[interval_of(off, n_ivl, t)];
     atomicAdd(hits + p, 1);
+    if (G) {
+      if (ns == 1) {
+        atomicAdd(G + (long long)f * n_obs + p, 1.0);
+      } else {
+        double* g = G + ((long long)f * n_obs + p) * 6;
+        const double v[6] = {1.0, c, s, c * c, c * s, s * s};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) atomicAdd(g + k, v[k]);
+      }
+      continue;
+    }
+    const double w0 = f0[f];
     if (ns == 1) {
       atomicAdd(acc + p, w0);
     } else {
@@ -293,6 +317,29 @@ __global__ void k_accumulate(const int* pix_obs, const float* psi, long long n, 
         atomicAdd(a + k, v[k]);
         atomicAdd(a + 6 + k, w0 * v[k]);
       }
+    }
+  }
+}
+
+// A^T A = sum_k G_k and A^T W^-1 A = sum_k f_k(0) G_k per pixel (the layout
+// k_classify reads), in a fixed order over the filters.
+__global__ void k_combine(const double* G, int n_filters, int n_obs, int ns, const double* f0, double* acc) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_obs; p += gridDim.x * blockDim.x) {
+    if (ns == 1) {
+      double sw = 0.0;
+      for (int f = 0; f < n_filters; ++f) sw += f0[f] * G[(long long)f * n_obs + p];
+      acc[p] = sw;
+      continue;
+    }
+    for (int k = 0; k < 6; ++k) {
+      double a = 0.0, aw = 0.0;
+      for (int f = 0; f < n_filters; ++f) {
+        const double g = G[((long long)f * n_obs + p) * 6 + k];
+        a += g;
+        aw += f0[f] * g;
+      }
+      acc[12LL * p + k] = a;
+      acc[12LL * p + 6 + k] = aw;
     }
   }
 }
@@ -364,13 +411,13 @@ __global__ void k_classify(const double* acc, const int* hits, int n_obs, int ns
   }
 }
 
-// Rows of A observing excised pixels become zero (Section 4, gap filling).
 // (pixel, angle) pairs read with one 8-byte load by the float32 operator
 __global__ void k_pack_pw(const int* pix_obs, const float* psi, long long n, int2* pw) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
     pw[t] = make_int2(pix_obs[t], __float_as_int(psi[t]));
 }
 
+// Rows of A observing excised pixels become zero (Section 4, gap filling).
 __global__ void k_zero_excised_rows(int* pix_obs, long long n, const unsigned char* excised) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int p = pix_obs[t];
@@ -534,54 +581,89 @@ static int choose_fft_len(const std::vector<long long>& off, const std::vector<i
   return bestM;
 }
 
-static madmap_status build_spectra(Plan* p) {
+// Spectrum of one filter's circulant embedding into h64/h32/hdf (the layout
+// the row kernel reads); returns false when the symbol is not positive.
+static bool filter_spectrum(const Plan* p, int f, double* h64, float* h32, df64* hdf, double* min_out) {
   const int M = p->M;
-  std::vector<double> h64((size_t)p->n_filters * M);
-  std::vector<float> h32((size_t)p->n_filters * M);
-  std::vector<df64> hdf((size_t)p->n_filters * M);
-  std::vector<double> re(M), im(M);
-  for (int f = 0; f < p->n_filters; ++f) {
-    std::fill(re.begin(), re.end(), 0.0);
-    std::fill(im.begin(), im.end(), 0.0);
-    const double* lg = &p->lags[(size_t)f * p->n_lags];
-    re[0] = lg[0];
-    for (int t = 1; t < p->n_lags; ++t) {
-      re[t] += lg[t];
-      re[M - t] += lg[t];
-    }
-    host_fft(re, im, false);
-    double mn = 1e300;
-    for (int k = 0; k < M; ++k) mn = std::min(mn, re[k]);
-    if (!(mn > 0.0)) {
-      set_error("filter " + std::to_string(f) + " is not positive definite (circulant symbol minimum " +
-                std::to_string(mn) + ")");
-      return MADMAP_ERR_NOT_PD;
-    }
-    for (int pos2 = 0; pos2 < p->N2; ++pos2) {
-      int k2 = 0;
-      for (int b = 0; b < p->logN2; ++b) k2 |= ((pos2 >> b) & 1) << (p->logN2 - 1 - b);
-      for (int pos1 = 0; pos1 < p->N1; ++pos1) {
-        int k1 = 0;
-        for (int b = 0; b < p->logN1; ++b) k1 |= ((pos1 >> b) & 1) << (p->logN1 - 1 - b);
-        const double v = re[k2 + (size_t)p->N2 * k1] / (double)M;
-        h64[(size_t)f * M + (size_t)pos2 * p->N1 + pos1] = v;
-        h32[(size_t)f * M + (size_t)pos2 * p->N1 + pos1] = (float)v;
-        hdf[(size_t)f * M + (size_t)pos2 * p->N1 + pos1] = df64(v);
-      }
+  std::vector<double> re(M, 0.0), im(M, 0.0);
+  const double* lg = &p->lags[(size_t)f * p->n_lags];
+  re[0] = lg[0];
+  for (int t = 1; t < p->n_lags; ++t) {
+    re[t] += lg[t];
+    re[M - t] += lg[t];
+  }
+  host_fft(re, im, false);
+  double mn = 1e300;
+  for (int k = 0; k < M; ++k) mn = std::min(mn, re[k]);
+  *min_out = mn;
+  if (!(mn > 0.0)) return false;
+  for (int pos2 = 0; pos2 < p->N2; ++pos2) {
+    int k2 = 0;
+    for (int b = 0; b < p->logN2; ++b) k2 |= ((pos2 >> b) & 1) << (p->logN2 - 1 - b);
+    for (int pos1 = 0; pos1 < p->N1; ++pos1) {
+      int k1 = 0;
+      for (int b = 0; b < p->logN1; ++b) k1 |= ((pos1 >> b) & 1) << (p->logN1 - 1 - b);
+      const double v = re[k2 + (size_t)p->N2 * k1] / (double)M;
+      const size_t o = (size_t)pos2 * p->N1 + pos1;
+      h64[o] = v;
+      h32[o] = (float)v;
+      hdf[o] = df64(v);
     }
   }
+  return true;
+}
+
+// All filters' spectra, computed on host threads (one filter per task).
+static madmap_status build_spectra(Plan* p) {
+  const int M = p->M, F = p->n_filters;
+  std::vector<double> h64((size_t)F * M);
+  std::vector<float> h32((size_t)F * M);
+  std::vector<df64> hdf((size_t)F * M);
+  std::vector<double> mins(F, 0.0);
+  std::vector<char> ok(F, 0);
+  const int T = std::max(1, std::min<int>(F, (int)std::max(1u, std::thread::hardware_concurrency())));
+  std::atomic<int> next(0);
+  auto work = [&]() {
+    for (int f = next++; f < F; f = next++)
+      ok[f] = filter_spectrum(p, f, &h64[(size_t)f * M], &h32[(size_t)f * M], &hdf[(size_t)f * M], &mins[f]);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < T; ++t) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
+  for (int f = 0; f < F; ++f)
+    if (!ok[f]) {
+      set_error("filter " + std::to_string(f) + " is not positive definite (circulant symbol minimum " +
+                std::to_string(mins[f]) + ")");
+      return MADMAP_ERR_NOT_PD;
+    }
   MM_CUDA(cudaMemcpy(p->H64, h64.data(), h64.size() * sizeof(double), cudaMemcpyHostToDevice));
   MM_CUDA(cudaMemcpy(p->H32, h32.data(), h32.size() * sizeof(float), cudaMemcpyHostToDevice));
   MM_CUDA(cudaMemcpy(p->Hdf, hdf.data(), hdf.size() * sizeof(df64), cudaMemcpyHostToDevice));
   return MADMAP_OK;
 }
 
+// Block preconditioner (A^T W^-1 A)^-1 and the pixel classification.  The
+// first call passes over the samples; when the per-filter sums G fit in
+// 512 MB they are kept, so a change of filters (set_filters) only recombines
+// them per pixel with the new f(0) and reinverts the blocks.  The first
+// call's hit counts are kept too, so the classification cannot change.
 static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
   const long long n = p->n_t;
   const int n_obs = p->n_obs;
   const int ns = p->n_stokes;
+  const int nb = ns == 1 ? 1 : 6;
+  const bool first = !p->pre_built;
+  if (first) {
+    madmap_status a = dalloc_t(p, &p->hits, (size_t)std::max(1, n_obs));
+    if (a != MADMAP_OK) return a;
+    const size_t gbytes = sizeof(double) * (size_t)p->n_filters * n_obs * nb;
+    if (n_obs > 0 && gbytes <= ((size_t)512 << 20)) {
+      a = dalloc(p, (void**)&p->G, gbytes);
+      if (a != MADMAP_OK) return a;
+    }
+  }
   double* acc = nullptr;
-  int* hits = nullptr;
   long long* doff = nullptr;
   int* dfilt = nullptr;
   double* df0 = nullptr;
@@ -591,7 +673,6 @@ static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
   madmap_status st = MADMAP_OK;
   auto cleanup = [&]() {
     cudaFree(acc);
-    cudaFree(hits);
     cudaFree(doff);
     cudaFree(dfilt);
     cudaFree(df0);
@@ -600,8 +681,7 @@ static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   std::vector<double> f0(p->n_filters);
   for (int f = 0; f < p->n_filters; ++f) f0[f] = p->lags[(size_t)f * p->n_lags];
-  if ((e = cudaMalloc(&hits, sizeof(int) * (size_t)std::max(1, n_obs))) != cudaSuccess ||
-      (e = cudaMalloc(&doff, sizeof(long long) * (p->n_ivl + 1))) != cudaSuccess ||
+  if ((e = cudaMalloc(&doff, sizeof(long long) * (p->n_ivl + 1))) != cudaSuccess ||
       (e = cudaMalloc(&dfilt, sizeof(int) * std::max(1, p->n_ivl))) != cudaSuccess ||
       (e = cudaMalloc(&df0, sizeof(double) * p->n_filters)) != cudaSuccess ||
       (e = cudaMalloc(&counts, sizeof(int) * 2)) != cudaSuccess) {
@@ -609,19 +689,24 @@ static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
     return cuda_fail(e, "cudaMalloc (preconditioner temporaries)");
   }
   cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)std::max(1, n_obs) * (ns == 1 ? 1 : 12), s);
-  cudaMemsetAsync(hits, 0, sizeof(int) * (size_t)std::max(1, n_obs), s);
   cudaMemsetAsync(counts, 0, sizeof(int) * 2, s);
   cudaMemcpyAsync(doff, p->offsets.data(), sizeof(long long) * (p->n_ivl + 1), cudaMemcpyHostToDevice, s);
   if (p->n_ivl) cudaMemcpyAsync(dfilt, p->ivl_filter.data(), sizeof(int) * p->n_ivl, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(df0, f0.data(), sizeof(double) * p->n_filters, cudaMemcpyHostToDevice, s);
-  if (n > 0)
-    k_accumulate<<<grid_for(n), 256, 0, s>>>(p->pix_obs, p->psi, n, doff, p->n_ivl, dfilt, df0, ns, acc, hits,
-                                              p->cs64, p->csdf);
+  if (first || !p->G) {
+    cudaMemsetAsync(p->hits, 0, sizeof(int) * (size_t)std::max(1, n_obs), s);
+    if (p->G) cudaMemsetAsync(p->G, 0, sizeof(double) * (size_t)p->n_filters * n_obs * nb, s);
+    if (n > 0)
+      k_accumulate<<<grid_for(n), 256, 0, s>>>(p->pix_obs, p->psi, n, doff, p->n_ivl, dfilt, df0, ns, acc, p->hits,
+                                                p->cs64, p->csdf, p->G, n_obs, first ? 1 : 0);
+  }
+  if (p->G && n_obs > 0)
+    k_combine<<<grid_for(n_obs), 256, 0, s>>>(p->G, p->n_filters, n_obs, ns, df0, acc);
   if (n_obs > 0)
-    k_classify<<<grid_for(n_obs), 256, 0, s>>>(acc, hits, n_obs, ns, p->rcond_excise, p->rcond_fp64, p->P64,
+    k_classify<<<grid_for(n_obs), 256, 0, s>>>(acc, p->hits, n_obs, ns, p->rcond_excise, p->rcond_fp64, p->P64,
                                                 p->P32, p->excised, p->fp64flag, counts);
-  if (n > 0) k_zero_excised_rows<<<grid_for(n), 256, 0, s>>>(p->pix_obs, n, p->excised);
-  if (n > 0 && ns == 3) k_pack_pw<<<grid_for(n), 256, 0, s>>>(p->pix_obs, p->psi, n, p->pw);
+  if (first && n > 0) k_zero_excised_rows<<<grid_for(n), 256, 0, s>>>(p->pix_obs, n, p->excised);
+  if (first && n > 0 && ns == 3) k_pack_pw<<<grid_for(n), 256, 0, s>>>(p->pix_obs, p->psi, n, p->pw);
   int hc[2] = {0, 0};
   e = cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -630,6 +715,7 @@ static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
   if (e != cudaSuccess) return cuda_fail(e, "preconditioner build");
   p->n_excised = hc[0];
   p->n_fp64 = hc[1];
+  p->pre_built = true;
   return st;
 }
 
