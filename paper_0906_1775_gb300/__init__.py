@@ -12,6 +12,7 @@ device memory and streams.
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -423,6 +424,15 @@ class Plan:
 
 
 # ----------------------------------------------------------------- differentiable solve
+def _per_filter(fn, n):
+    """[fn(0), ..., fn(n-1)] on host threads (the library calls release the interpreter lock)."""
+    if n < 2:
+        return [fn(k) for k in range(n)]
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=min(n, os.cpu_count() or 1)) as ex:
+        return list(ex.map(fn, range(n)))
+
+
 def _autograd_function():
     torch = _torch()
 
@@ -440,7 +450,7 @@ def _autograd_function():
         def forward(ctx, d, params, plan, fs, solve_kwargs):
             prm = params.detach().cpu().numpy().astype(np.float64)
             n_lags = plan.stats["n_lags"]
-            lags = np.stack([madmap_noise_filter(n_lags, fs, *prm[k]) for k in range(prm.shape[0])])
+            lags = np.stack(_per_filter(lambda k: madmap_noise_filter(n_lags, fs, *prm[k]), prm.shape[0]))
             plan.set_filters(lags)
             kw = dict(solve_kwargs or {})
             m, info = plan.solve(d.detach().contiguous(), **kw)
@@ -464,7 +474,8 @@ def _autograd_function():
                 prm = params.detach().cpu().numpy().astype(np.float64)
                 glh = gl.cpu().numpy()
                 n_lags = plan.stats["n_lags"]
-                out = np.stack([madmap_noise_filter_vjp(n_lags, ctx.fs, *prm[k], glh[k]) for k in range(prm.shape[0])])
+                out = np.stack(_per_filter(lambda k: madmap_noise_filter_vjp(n_lags, ctx.fs, *prm[k], glh[k]),
+                                           prm.shape[0]))
                 gp = torch.from_numpy(out).to(dtype=params.dtype, device=params.device)
             return (gd.view_as(d) if gd is not None else None), gp, None, None, None
 

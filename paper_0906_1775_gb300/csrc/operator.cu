@@ -135,13 +135,7 @@ template <>
 __device__ __forceinline__ void scatter<df64, 1>(double* y, int p, df64 v, df64, df64) {
   atomicAdd(y + p, to_double(v));
 }
-template <>
-__device__ __forceinline__ void scatter<df64, 3>(double* y, int p, df64 v, df64 c, df64 s) {
-  double* q = y + 4LL * p;
-  atomicAdd(q, to_double(v));
-  atomicAdd(q + 1, to_double(v * c));
-  atomicAdd(q + 2, to_double(v * s));
-}
+// (IQU double-float outputs are weighted in float64 inside k_f3)
 
 // A lane seen from one CTA: valid input window positions [in_lo, in_hi),
 // kept outputs [out_lo, out_hi), and base pointers already offset by the
@@ -480,6 +474,29 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
 #pragma unroll
         for (int l = 0; l < 2; ++l)
           if (ok[l][u]) static_cast<Real*>(L[l].out)[nn[u]] = val[l][u];  // float and float64 only
+    } else if constexpr (std::is_same<Real, df64>::value && NS == 3) {
+      // double-float: round the value to float64 once and weight it with the
+      // float64 (cos, sin) pair (5 float64 operations per sample, not 9)
+      int pp[2][U];
+      double2 cs[2][U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+          pp[l][u] = ok[l][u] ? __ldg(L[l].pix + nn[u]) : -1;
+          cs[l][u] = ok[l][u] ? L[l].cs[nn[u]] : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+          if (pp[l][u] < 0) continue;
+          double* q = static_cast<double*>(L[l].out) + 4LL * pp[l][u];
+          const double v = to_double(val[l][u]);
+          atomicAdd(q, v);
+          atomicAdd(q + 1, v * cs[l][u].x);
+          atomicAdd(q + 2, v * cs[l][u].y);
+        }
     } else {
       int pp[2][U];
       Real cc[2][U], ss[2][U];
