@@ -54,6 +54,9 @@ class Problem:
     sky: np.ndarray               # float64 [n_pix, n_stokes] true sky z
     target: np.ndarray | None = None   # float64 [n_pix, n_stokes] (differentiable-solve loss)
     meta: dict = field(default_factory=dict)
+    pix_pol: np.ndarray | None = None  # int32 [n_t]: Q/U pixel per sample (multi-resolution maps), or None
+    n_pix_pol: int = 0                 # global Q/U pixel count
+    sky_pol: np.ndarray | None = None  # float64 [n_pix_pol, 2] true Q, U on the Q/U pixels
 
     @property
     def n_samples(self) -> int:
@@ -160,8 +163,14 @@ def make_flat_problem(
     jitter: float = 0.3,
     make_target: bool = False,
     det_sweep_offset: bool = False,
+    pol_factor: int = 0,
 ) -> Problem:
-    """Build one flat-sky problem.  See the module docstring for the recipe."""
+    """Build one flat-sky problem.  See the module docstring for the recipe.
+
+    pol_factor = k > 0 (IQU): Q and U live on a coarser (W/k) x (W/k) grid (the
+    multi-resolution maps of Section 6): each sample's Q/U pixel is the coarse
+    pixel containing its (jittered) fine pixel, and the true Q, U are constant
+    within coarse pixels (the coarse field at each fine pixel)."""
     rs = _streams(seed)
     n_pix = width * width
     # sky
@@ -206,6 +215,17 @@ def make_flat_problem(
         flagged = rs["flags"].random(n_t) < flag_frac
         pix = pix.copy()
         pix[flagged] = -1
+    pix_pol, sky_pol, n_pix_pol = None, None, 0
+    if pol_factor and n_stokes == 3:
+        wc = width // pol_factor
+        n_pix_pol = wc * wc
+        okp = pix >= 0
+        r_, c_ = np.where(okp, pix, 0) // width, np.where(okp, pix, 0) % width
+        pix_pol = np.where(okp, (r_ // pol_factor) * wc + c_ // pol_factor, -1).astype(np.int32)
+        sky_pol = np.stack([gaussian_field(wc, rs["extra"], 0.1), gaussian_field(wc, rs["extra"], 0.1)], 1)
+        fine = np.arange(n_pix)
+        coarse = (fine // width // pol_factor) * wc + (fine % width) // pol_factor
+        sky[:, 1:] = sky_pol[coarse]
     # signal A z in float64 from the float32 angle
     ok = pix >= 0
     sig = np.zeros(n_t)
@@ -230,7 +250,8 @@ def make_flat_problem(
     return Problem(name=name, n_stokes=n_stokes, n_pix=n_pix, width=width, pix=pix.astype(np.int32),
                    psi=psi, d=d, interval_offsets=offsets, interval_filter=interval_filter,
                    interval_det=interval_det, noise_params=params, fs=fs, n_lags=n_lags, sky=sky,
-                   target=target, meta={"seed": seed, "n_det": n_det})
+                   target=target, meta={"seed": seed, "n_det": n_det}, pix_pol=pix_pol,
+                   n_pix_pol=n_pix_pol, sky_pol=sky_pol)
 
 
 # --------------------------------------------------------------------------------------

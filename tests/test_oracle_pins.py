@@ -451,3 +451,85 @@ def test_adjoint_psd_parameter_gradient_and_sigma_invariance():
     # scaling every sigma together scales N^-1 uniformly: the map does not move
     s_dot = float(np.sum(base[:, 0] * gp[:, 0]))
     assert abs(s_dot) <= 1e-8 * float(np.sum(np.abs(base[:, 0] * gp[:, 0])))
+
+
+# ------------------------------------------------------------------ multi-resolution maps (Section 6)
+def _mr_problem(seed=5, noiseless=False, width=8, factor=2, n=600):
+    from synth import make_flat_problem
+    from synth.flat import log_uniform_intervals
+
+    def lens(rng, tot):
+        return log_uniform_intervals(tot, 80, 300, rng)
+    return make_flat_problem("mr", seed, width, 4, n, 3, 10, det_angles_deg=[0.0, 45.0, 90.0, 135.0],
+                             hwp_step_deg=22.5, interval_lengths=lens, noise=(1.0, 4.0, 1.5),
+                             noiseless=noiseless, det_sweep_offset=True, pol_factor=factor)
+
+
+def _mr_system(p, pix_pol=None, n_pix_pol=None, **kw):
+    from oracle.multires import MultiResSystem
+    from tests.helpers import lags_for
+    pp = p.pix_pol if pix_pol is None else pix_pol
+    npp = p.n_pix_pol if n_pix_pol is None else n_pix_pol
+    return MultiResSystem(p.pix, pp, p.psi, p.n_pix, npp, p.interval_offsets, p.interval_filter, lags_for(p), **kw)
+
+
+def test_multires_reduces_to_single_resolution():
+    """With the same pixel for I and Q/U the operator and the right-hand side are those of
+    the single-resolution system (Eq. 10), and so is the map."""
+    p = _mr_problem(seed=6)
+    M = _mr_system(p, pix_pol=p.pix, n_pix_pol=p.n_pix)
+    S = system_for(p)
+    assert M.n_obs == S.n_obs and not S.excised.any() and not M.excised.any() and not M.excised_pol.any()
+    x = np.random.default_rng(1).standard_normal((S.n_obs, 3))
+    assert np.allclose(M.H(x), S.H(x), rtol=1e-12, atol=1e-12 * np.abs(S.H(x)).max())
+    assert np.allclose(M.rhs(p.d[0]), S.rhs(p.d[0]), rtol=1e-12, atol=1e-12)
+    xm, _ = M.solve(p.d[0], rel_tol=1e-13, max_iter=500)
+    xs, _ = S.solve(p.d[0], rel_tol=1e-13, max_iter=500)
+    assert rel_rms(xm, xs) < 1e-10
+
+
+def test_multires_pcg_matches_dense_cholesky_and_is_symmetric():
+    p = _mr_problem(seed=7)
+    M = _mr_system(p)
+    assert M.n_obs_pol < M.n_obs_i
+    xd = M.dense_solve(p.d[0])
+    xp, info = M.solve(p.d[0], rel_tol=1e-13, max_iter=1000)
+    assert info["best_res"] < 1e-12
+    act = M.active()
+    assert rel_rms(xp[act], xd[act]) < 1e-10 and np.all(xp[~act] == 0)
+    rng = np.random.default_rng(2)
+    x, y = rng.standard_normal((2, M.n_obs, 3)) * act
+    a, b = float(np.sum(y * M.H(x))), float(np.sum(x * M.H(y)))
+    assert abs(a - b) <= 1e-12 * abs(a) and float(np.sum(x * M.H(x))) > 0
+
+
+def test_multires_noiseless_recovery():
+    """Noiseless data whose Q and U are constant within Q/U pixels: the map recovers I on the
+    fine pixels and Q, U on the coarse ones."""
+    p = _mr_problem(seed=8, noiseless=True, n=1200)
+    M = _mr_system(p)
+    x, _ = M.solve(p.d[0], rel_tol=1e-14, max_iter=2000)
+    act = M.active()
+    ki = act[:, 0]
+    kq = act[:, 1]
+    assert ki.sum() > 50 and kq.sum() > 10
+    assert rel_rms(x[ki, 0], p.sky[M.obs2glob[ki[:M.n_obs_i]], 0]) < 1e-6
+    assert rel_rms(x[kq, 1:], p.sky_pol[M.obs2glob_pol[kq[:M.n_obs_pol]]]) < 1e-6
+
+
+def test_multires_excision_drops_rows():
+    """A Q/U pixel seen at a single angle cannot separate Q from U: it is excised, its rows
+    are zero, and an I pixel seen only through those rows is excised too."""
+    p = _mr_problem(seed=9)
+    pix, pol, psi = p.pix.copy(), p.pix_pol.copy(), p.psi.copy()
+    n_pix_pol = p.n_pix_pol + 1
+    n_pix = p.n_pix + 1
+    pix[:5], pol[:5], psi[:5] = p.n_pix, p.n_pix_pol, 0.3     # new I and Q/U pixels, one angle
+    from oracle.multires import MultiResSystem
+    from tests.helpers import lags_for
+    M = MultiResSystem(pix, pol, psi, n_pix, n_pix_pol, p.interval_offsets, p.interval_filter, lags_for(p))
+    k_pol = int(np.searchsorted(M.obs2glob_pol, p.n_pix_pol))
+    k_i = int(np.searchsorted(M.obs2glob, p.n_pix))
+    assert M.excised_pol[k_pol] and M.excised[k_i]
+    assert np.all(M.pi[:5] == -1) and np.all(M.pq[:5] == -1)
+    assert not M.excised[:M.n_obs_i][np.arange(M.n_obs_i) != k_i].any()
