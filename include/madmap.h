@@ -91,6 +91,11 @@ typedef struct {
   int32_t fft_len;                  /* complex FFT length M per window (power of two in
                                        [256, 2^20], > 2 (n_lags-1)); 0 = chosen by the plan */
   int32_t tiles_per_chunk;          /* windows pairs per operator launch chunk; 0 = chosen */
+  /* Multi-resolution maps (Section 6): Q and U on their own pixelisation.
+   * IQU only; NULL (default) puts all three Stokes parameters on pix. */
+  const int32_t* pix_pol;           /* device [n_samples]: Q/U pixel of each sample in [0, n_pix_pol),
+                                       or -1 (flagged: the sample's row is zero) */
+  int32_t n_pix_pol;                /* global Q/U pixel count (> 0 when pix_pol is set) */
 } madmap_plan_desc;
 
 typedef struct {
@@ -107,6 +112,8 @@ typedef struct {
   int32_t n_filters;
   int64_t n_samples;
   int64_t device_bytes;    /* device memory owned by the plan */
+  int32_t n_obs_pol;       /* multi-resolution plans: observed Q/U pixels (else 0) */
+  int32_t n_excised_pol;   /* multi-resolution plans: excised Q/U pixels */
 } madmap_plan_stats;
 
 typedef struct {
@@ -186,6 +193,19 @@ madmap_status madmap_plan_get_stats(madmap_plan_t plan, madmap_plan_stats* out);
  * first to learn n_obs. */
 madmap_status madmap_plan_observed(madmap_plan_t plan, int32_t* n_obs, int32_t* obs2glob, uint8_t* excised,
                                    void* stream);
+
+/* Multi-resolution plans (pix_pol set): maps are [n_slots][3] with n_slots =
+ * madmap_plan_stats.n_obs = max(observed I pixels, observed Q/U pixels).
+ * Column 0 of row k is I of observed I pixel k (madmap_plan_observed lists the
+ * I pixels and their excision flags), columns 1-2 of row k are Q, U of
+ * observed Q/U pixel k (listed here).  Entries past either count are 0.  The
+ * preconditioner blocks are the 1 x 1 I blocks and 2 x 2 (Q, U) blocks of
+ * A^T W^-1 A; a Q/U pixel with fewer than 2 hits or rcond of its 2 x 2 A^T A
+ * block below rcond_excise is excised with the rows of its samples, and an I
+ * pixel left without rows is excised too.  Arguments as madmap_plan_observed;
+ * *n_obs_pol = 0 for single-resolution plans. */
+madmap_status madmap_plan_observed_pol(madmap_plan_t plan, int32_t* n_obs_pol, int32_t* obs2glob_pol,
+                                       uint8_t* excised_pol, void* stream);
 
 /* Replace the filter lags (host [n_filters][n_lags]) without re-planning:
  * recomputes spectra and preconditioner blocks.  Synchronises `stream`. */

@@ -53,10 +53,15 @@ def lag_correlation(a, r, offsets, ivl_filter, n_filters, n_lags):
 def solve_backward(S, d, m, g, rel_tol=1e-13, max_iter=2000):
     """(dL/dd, dL/df [n_filters, n_lags], info) for the map m of data d and g = dL/dm.
 
-    S is an oracle.solver.System; m and g are [n_obs, n_s] over its observed pixels.
+    S is an oracle.solver.System (or a multires.MultiResSystem); m and g are
+    [n_obs, n_s] over its observed pixels (slots).  g is zeroed at unknowns
+    that do not exist (excised pixels): H has no row there.
     """
     g = np.asarray(g, dtype=np.float64).reshape(S.n_obs, S.n_s).copy()
-    g[S.excised] = 0.0
+    if hasattr(S, "active"):
+        g[~S.active()] = 0.0
+    else:
+        g[S.excised] = 0.0
     lam, info = S.pcg(g, rel_tol=rel_tol, max_iter=max_iter)
     a = S.unpoint(lam)
     grad_d = S.ninv(a)

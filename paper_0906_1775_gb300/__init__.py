@@ -21,6 +21,7 @@ from ._lib import (MADMAP_DF64, MADMAP_FP32, MADMAP_FP64, MADMAP_MIXED, MadmapEr
 
 __all__ = ["Plan", "noise_filter", "paper_fft_length", "MadmapError", "load", "library_path",
            "madmap_plan_create", "madmap_plan_destroy", "madmap_plan_get_stats", "madmap_plan_observed",
+           "madmap_plan_observed_pol",
            "madmap_plan_set_filters", "madmap_apply_ATNA", "madmap_rhs", "madmap_apply_ninv", "madmap_solve",
            "madmap_solve_batched", "madmap_solve_backward", "madmap_noise_filter_vjp", "MadmapSolve",
            "madmap_noise_filter", "madmap_paper_fft_length", "madmap_last_error", "madmap_kernel_launch_count",
@@ -80,6 +81,15 @@ def madmap_plan_observed(h, obs2glob_ptr=None, excised_ptr=None, stream=None) ->
     check(load().madmap_plan_observed(h, C.byref(n), obs2glob_ptr, excised_ptr,
                                       C.c_void_p(_stream_ptr(stream) if (obs2glob_ptr or excised_ptr) else 0)),
           "madmap_plan_observed")
+    return n.value
+
+
+def madmap_plan_observed_pol(h, obs2glob_pol_ptr=None, excised_pol_ptr=None, stream=None) -> int:
+    n = C.c_int32()
+    check(load().madmap_plan_observed_pol(h, C.byref(n), obs2glob_pol_ptr, excised_pol_ptr,
+                                          C.c_void_p(_stream_ptr(stream) if (obs2glob_pol_ptr or excised_pol_ptr)
+                                                     else 0)),
+          "madmap_plan_observed_pol")
     return n.value
 
 
@@ -248,10 +258,13 @@ class Plan:
     pix: int32 CUDA tensor [n_t] (global pixel, -1 flagged); psi: float32 CUDA
     tensor [n_t] or None (temperature); interval_offsets [n_ivl+1],
     interval_filter [n_ivl] and filter_lags [n_filters, n_lags] are host arrays.
+    pix_pol (int32 CUDA tensor [n_t], with n_pix_pol) puts Q and U on a second
+    pixelisation (multi-resolution maps, IQU only): maps are then [n_obs, 3]
+    slots, I of observed I pixel k and Q, U of observed Q/U pixel k in row k.
     """
 
     def __init__(self, pix, psi, n_pix, interval_offsets, interval_filter, filter_lags, rcond_excise=0.0,
-                 rcond_fp64=0.0, fft_len=0, tiles_per_chunk=0, stream=None):
+                 rcond_fp64=0.0, fft_len=0, tiles_per_chunk=0, stream=None, pix_pol=None, n_pix_pol=0):
         torch = _torch()
         self._h = None
         off = np.ascontiguousarray(interval_offsets, dtype=np.int64)
@@ -271,7 +284,16 @@ class Plan:
         d.filter_lags = lags.ctypes.data
         d.rcond_excise, d.rcond_fp64 = float(rcond_excise), float(rcond_fp64)
         d.fft_len, d.tiles_per_chunk = int(fft_len), int(tiles_per_chunk)
+        if pix_pol is not None:
+            if int(pix_pol.numel()) != n_t:
+                raise ValueError("pix_pol must have one entry per sample")
+            d.pix_pol = _dev_ptr(pix_pol, torch.int32, "pix_pol") if n_t else None
+            d.n_pix_pol = int(n_pix_pol)
+            if not n_t:  # the library reads no sample, but needs a non-NULL pointer to know the layout
+                pix_pol = torch.zeros(1, dtype=torch.int32, device="cuda")
+                d.pix_pol = _dev_ptr(pix_pol, torch.int32, "pix_pol")
         self._keep = (off, filt, lags)
+        self.multires = pix_pol is not None
         self._h = madmap_plan_create(d, stream)
         self.n_stokes = d.n_stokes
         self.n_samples = n_t
@@ -290,12 +312,23 @@ class Plan:
             pass
 
     def observed(self, stream=None):
-        """(obs2glob int32, excised uint8) CUDA tensors over the observed pixels."""
+        """(obs2glob int32, excised uint8) CUDA tensors over the observed (I) pixels."""
         torch = _torch()
-        o = torch.empty(max(self.n_obs, 1), dtype=torch.int32, device="cuda")
-        e = torch.empty(max(self.n_obs, 1), dtype=torch.uint8, device="cuda")
+        n = madmap_plan_observed(self._h)
+        o = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        e = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
         madmap_plan_observed(self._h, o.data_ptr(), e.data_ptr(), stream)
-        return o[:self.n_obs], e[:self.n_obs]
+        return o[:n], e[:n]
+
+    def observed_pol(self, stream=None):
+        """(obs2glob_pol int32, excised_pol uint8) CUDA tensors over the observed Q/U
+        pixels of a multi-resolution plan (empty otherwise)."""
+        torch = _torch()
+        n = madmap_plan_observed_pol(self._h)
+        o = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        e = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
+        madmap_plan_observed_pol(self._h, o.data_ptr(), e.data_ptr(), stream)
+        return o[:n], e[:n]
 
     def time_operator(self, precision="fp32", reps=10, stream=None):
         """Mean duration (ms) of one launch of each of the three operator kernels, and

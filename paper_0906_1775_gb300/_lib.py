@@ -37,13 +37,14 @@ class madmap_plan_desc(C.Structure):
                 ("interval_offsets", C.c_void_p), ("interval_filter", C.c_void_p),
                 ("n_filters", C.c_int32), ("n_lags", C.c_int32), ("filter_lags", C.c_void_p),
                 ("rcond_excise", C.c_double), ("rcond_fp64", C.c_double), ("fft_len", C.c_int32),
-                ("tiles_per_chunk", C.c_int32)]
+                ("tiles_per_chunk", C.c_int32), ("pix_pol", C.c_void_p), ("n_pix_pol", C.c_int32)]
 
 
 class madmap_plan_stats(C.Structure):
     _fields_ = [(n, C.c_int32) for n in ("n_obs", "n_excised", "n_fp64_pixels", "n_stokes", "fft_len", "n1",
                                          "n2", "n_segments", "n_tiles", "tiles_per_chunk", "n_lags",
-                                         "n_filters")] + [("n_samples", C.c_int64), ("device_bytes", C.c_int64)]
+                                         "n_filters")] + [("n_samples", C.c_int64), ("device_bytes", C.c_int64),
+                                                          ("n_obs_pol", C.c_int32), ("n_excised_pol", C.c_int32)]
 
 
 class madmap_checkpoint(C.Structure):
@@ -77,6 +78,7 @@ PROTOTYPES = [
     ("madmap_plan_destroy", C.c_int, [C.c_void_p]),
     ("madmap_plan_get_stats", C.c_int, [C.c_void_p, C.POINTER(madmap_plan_stats)]),
     ("madmap_plan_observed", C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("madmap_plan_observed_pol", C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_void_p, C.c_void_p, C.c_void_p]),
     ("madmap_plan_set_filters", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("madmap_apply_ATNA", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("madmap_rhs", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),

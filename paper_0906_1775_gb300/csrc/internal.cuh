@@ -138,6 +138,13 @@ struct Plan {
   double* G = nullptr;             // [n_filters][n_obs][6] (IQU) or [n_filters][n_obs] (T): sums of w w^T
                                    // per filter, kept when they fit 512 MB (fast filter changes)
   bool pre_built = false;          // the preconditioner has been built once
+  // multi-resolution maps: Q/U on a second pixelisation; vectors are slots
+  // holding I of I pixel k and Q, U of Q/U pixel k (n_obs = max of the counts)
+  bool multires = false;
+  int n_pix_pol = 0, n_obs_i = 0, n_obs_pol = 0, n_excised_pol = 0;
+  int* pix_obs_pol = nullptr;      // [n_t] observed Q/U pixel or -1
+  int* obs2glob_pol = nullptr;     // [n_obs_pol]
+  unsigned char* excised_pol = nullptr;  // [n_obs] (slots)
   void* scratch = nullptr;         // scratch_slots * tiles_per_chunk * M complex (float64 size)
   int scratch_slots = 1;           // 2 when an application has several chunks (see op_stream)
   // An application of several chunks alternates them between two streams,

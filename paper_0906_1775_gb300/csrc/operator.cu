@@ -35,6 +35,13 @@ namespace {
 
 enum { IN_MAPX = 0, IN_TODF = 1, IN_TODR = 2 };
 
+// Stokes layouts of the kernels' NS parameter: 1 = T, 3 = IQU on one
+// pixelisation, NS_MR = IQU with Q and U on a second pixelisation (Section 6;
+// each sample then carries an I pixel and a Q/U pixel of the slot layout).
+constexpr int NS_MR = 4;
+__host__ __device__ constexpr bool polarised(int ns) { return ns >= 3; }
+inline int layout(const Plan* p) { return p->multires ? NS_MR : p->n_stokes; }
+
 struct OpArgs {
   const Tile* tiles;
   int tile0;
@@ -44,6 +51,7 @@ struct OpArgs {
   const double2* cs64;
   const float4* csdf;
   const int2* pw;      // (pixel, angle bits) per sample, IQU
+  const int* pixq;     // Q/U pixel per sample (multi-resolution plans)
   const void* in;
   long long in_stride;
   void* out;
@@ -108,6 +116,17 @@ __device__ __forceinline__ df64 gather<df64, 3>(const df64* x, int p, df64 c, df
   return df64(u.x, u.y) + df64(u.z, u.w) * c + df64(v.x, v.y) * s;
 }
 
+// multi-resolution maps: I from slot p, Q and U from slot q
+template <typename Real>
+__device__ __forceinline__ Real gather_mr(const Real* x, int p, int q, Real c, Real s) {
+  if constexpr (std::is_same<Real, float>::value) {
+    const float4 m = reinterpret_cast<const float4*>(x)[q];
+    return x[4LL * p] + m.y * c + m.z * s;
+  } else {
+    return x[4LL * p] + x[4LL * q + 1] * c + x[4LL * q + 2] * s;
+  }
+}
+
 template <typename Real, int NS>
 __device__ __forceinline__ void scatter(typename OutT<Real>::type* y, int p, Real v, Real c, Real s);
 template <>
@@ -137,6 +156,18 @@ __device__ __forceinline__ void scatter<df64, 1>(double* y, int p, df64 v, df64,
 }
 // (IQU double-float outputs are weighted in float64 inside k_f3)
 
+template <typename Real>
+__device__ __forceinline__ void scatter_mr(typename OutT<Real>::type* y, int p, int q, Real v, Real c, Real s) {
+  if constexpr (std::is_same<Real, float>::value) {
+    atomicAdd(y + 4LL * p, v);
+    atomicAdd(reinterpret_cast<float4*>(y) + q, make_float4(0.0f, v * c, v * s, 0.0f));
+  } else {
+    atomicAdd(y + 4LL * p, v);
+    atomicAdd(y + 4LL * q + 1, v * c);
+    atomicAdd(y + 4LL * q + 2, v * s);
+  }
+}
+
 // A lane seen from one CTA: valid input window positions [in_lo, in_hi),
 // kept outputs [out_lo, out_hi), and base pointers already offset by the
 // window start so every access is base[n] with a 32-bit window position n.
@@ -148,6 +179,7 @@ struct LaneView {
   const double2* cs;
   const float4* csd;
   const int2* pw;
+  const int* pq;
   const void* in;
   void* out;
 };
@@ -168,6 +200,7 @@ __device__ __forceinline__ LaneView<Real> lane_view(const OpArgs& a, const Lane&
   v.cs = a.cs64 + ws;
   v.csd = a.csdf + ws;
   v.pw = a.pw + ws;
+  v.pq = a.pixq ? a.pixq + ws : nullptr;
   if (IN == IN_TODF) v.in = static_cast<const float*>(a.in) + g.rhs * a.in_stride + ws;
   else if (IN == IN_TODR) v.in = static_cast<const Real*>(a.in) + g.rhs * a.in_stride + ws;
   else v.in = static_cast<const Real*>(a.in) + g.rhs * a.in_stride;
@@ -215,7 +248,7 @@ __device__ __forceinline__ void finish_angle(Real& c, Real& s) {}
 // their cached cos/sin pairs.
 template <typename Real, int NS>
 __device__ __forceinline__ void load_pointing(const LaneView<Real>& L, int n, bool ok, int& pp, Real& c, Real& s) {
-  if (NS == 3 && std::is_same<Real, float>::value) {
+  if (polarised(NS) && std::is_same<Real, float>::value) {
     if (ok) {
       const int2 w = __ldg(L.pw + n);
       pp = w.x;
@@ -228,7 +261,7 @@ __device__ __forceinline__ void load_pointing(const LaneView<Real>& L, int n, bo
   } else {
     pp = ok ? __ldg(L.pix + n) : -1;
     c = s = Real(0);
-    if (NS == 3) lane_angle<Real>(L, n, ok, c, s);
+    if (polarised(NS)) lane_angle<Real>(L, n, ok, c, s);
   }
 }
 template <>
@@ -296,7 +329,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
   const int n1_0 = blockIdx.x * B1;
   const int total = B1 << logN2;
   constexpr int bd = OP_THREADS;
-  constexpr int U = (IN == IN_MAPX && NS == 3) ? 4 : 8;
+  constexpr int U = (IN == IN_MAPX && polarised(NS)) ? 4 : 8;
   for (int e0 = threadIdx.x; e0 < total; e0 += bd * U) {
     int nn[U];
     bool ok[2][U];
@@ -319,21 +352,26 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
             v[l][u] = ok[l][u] ? static_cast<const Real*>(L[l].in)[nn[u]] : Real(0);
         }
     } else {
-      int pp[2][U];
+      int pp[2][U], qq[2][U];
       Real cc[2][U], ss[2][U];
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
           load_pointing<Real, NS>(L[l], nn[u], ok[l][u], pp[l][u], cc[l][u], ss[l][u]);
+          if constexpr (NS == NS_MR) qq[l][u] = ok[l][u] ? __ldg(L[l].pq + nn[u]) : -1;
         }
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
           Real c = cc[l][u], sn = ss[l][u];
-          if (NS == 3) finish_angle<Real>(c, sn);
-          v[l][u] = pp[l][u] >= 0 ? gather<Real, NS>(static_cast<const Real*>(L[l].in), pp[l][u], c, sn) : Real(0);
+          if (polarised(NS)) finish_angle<Real>(c, sn);
+          if constexpr (NS == NS_MR)
+            v[l][u] = pp[l][u] >= 0 ? gather_mr<Real>(static_cast<const Real*>(L[l].in), pp[l][u], qq[l][u], c, sn)
+                                    : Real(0);
+          else
+            v[l][u] = pp[l][u] >= 0 ? gather<Real, NS>(static_cast<const Real*>(L[l].in), pp[l][u], c, sn) : Real(0);
         }
     }
 #pragma unroll
@@ -474,16 +512,18 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
 #pragma unroll
         for (int l = 0; l < 2; ++l)
           if (ok[l][u]) static_cast<Real*>(L[l].out)[nn[u]] = val[l][u];  // float and float64 only
-    } else if constexpr (std::is_same<Real, df64>::value && NS == 3) {
+    } else if constexpr (std::is_same<Real, df64>::value && polarised(NS)) {
       // double-float: round the value to float64 once and weight it with the
       // float64 (cos, sin) pair (5 float64 operations per sample, not 9)
-      int pp[2][U];
+      int pp[2][U], qq[2][U];
       double2 cs[2][U];
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
           pp[l][u] = ok[l][u] ? __ldg(L[l].pix + nn[u]) : -1;
+          if constexpr (NS == NS_MR) qq[l][u] = ok[l][u] ? __ldg(L[l].pq + nn[u]) : -1;
+          else qq[l][u] = pp[l][u];
           cs[l][u] = ok[l][u] ? L[l].cs[nn[u]] : make_double2(0.0, 0.0);
         }
 #pragma unroll
@@ -491,20 +531,21 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
           if (pp[l][u] < 0) continue;
-          double* q = static_cast<double*>(L[l].out) + 4LL * pp[l][u];
+          double* y = static_cast<double*>(L[l].out);
           const double v = to_double(val[l][u]);
-          atomicAdd(q, v);
-          atomicAdd(q + 1, v * cs[l][u].x);
-          atomicAdd(q + 2, v * cs[l][u].y);
+          atomicAdd(y + 4LL * pp[l][u], v);
+          atomicAdd(y + 4LL * qq[l][u] + 1, v * cs[l][u].x);
+          atomicAdd(y + 4LL * qq[l][u] + 2, v * cs[l][u].y);
         }
     } else {
-      int pp[2][U];
+      int pp[2][U], qq[2][U];
       Real cc[2][U], ss[2][U];
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
           load_pointing<Real, NS>(L[l], nn[u], ok[l][u], pp[l][u], cc[l][u], ss[l][u]);
+          if constexpr (NS == NS_MR) qq[l][u] = ok[l][u] ? __ldg(L[l].pq + nn[u]) : -1;
         }
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -512,8 +553,11 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
         for (int l = 0; l < 2; ++l) {
           if (pp[l][u] < 0) continue;
           Real c = cc[l][u], sn = ss[l][u];
-          if (NS == 3) finish_angle<Real>(c, sn);
-          scatter<Real, NS>(static_cast<typename OutT<Real>::type*>(L[l].out), pp[l][u], val[l][u], c, sn);
+          if (polarised(NS)) finish_angle<Real>(c, sn);
+          if constexpr (NS == NS_MR)
+            scatter_mr<Real>(static_cast<typename OutT<Real>::type*>(L[l].out), pp[l][u], qq[l][u], val[l][u], c, sn);
+          else
+            scatter<Real, NS>(static_cast<typename OutT<Real>::type*>(L[l].out), pp[l][u], val[l][u], c, sn);
         }
     }
   }
@@ -625,6 +669,7 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
   a.cs64 = p->cs64;
   a.csdf = p->csdf;
   a.pw = p->pw;
+  a.pixq = p->pix_obs_pol;
   a.scratch = p->scratch;
   constexpr bool DF = std::is_same<Real, df64>::value;
   a.H = DF ? (const void*)p->Hdf : sizeof(Real) == 8 ? (const void*)p->H64 : (const void*)p->H32;
@@ -693,8 +738,8 @@ madmap_status dispatch_io(Plan* p, int in_mode, int out_mode, const void* in, vo
     return launch_all<Real, NS, IN_MAPX, OUT_MAP>(p, in, out, is, os, n_rhs, skip, s);
   if (in_mode == IN_TOD && out_mode == OUT_MAP)
     return launch_all<Real, NS, IN_TODF, OUT_MAP>(p, in, out, is, os, n_rhs, skip, s);
-  if (in_mode == IN_TOD_REAL && out_mode == OUT_TOD)
-    return launch_all<Real, NS, IN_TODR, OUT_TOD>(p, in, out, is, os, n_rhs, skip, s);
+  if (in_mode == IN_TOD_REAL && out_mode == OUT_TOD)  // no pointing: the T instance serves every layout
+    return launch_all<Real, 1, IN_TODR, OUT_TOD>(p, in, out, is, os, n_rhs, skip, s);
   if (in_mode == IN_MAP && out_mode == OUT_TOD)
     return launch_all<Real, NS, IN_MAPX, OUT_TOD>(p, in, out, is, os, n_rhs, skip, s);
   set_error("unsupported operator mode");
@@ -787,14 +832,12 @@ madmap_status op_launch_set(Plan* p, int prec, int in_mode, int out_mode, const 
                             const TileSet* ts, cudaStream_t s) {
   if (ts->n_tiles == 0) return MADMAP_OK;
   const int ss = skip_stride;
-  if (prec == OPP_DF64)
-    return p->n_stokes == 1 ? dispatch_set<df64, 1>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts)
-                            : dispatch_set<df64, 3>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts);
-  if (prec == OPP_F64)
-    return p->n_stokes == 1 ? dispatch_set<double, 1>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts)
-                            : dispatch_set<double, 3>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts);
-  return p->n_stokes == 1 ? dispatch_set<float, 1>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts)
-                          : dispatch_set<float, 3>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts);
+  const int k = layout(p);
+#define MM_SET(R, NSV) dispatch_set<R, NSV>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts)
+  if (prec == OPP_DF64) return k == 1 ? MM_SET(df64, 1) : k == 3 ? MM_SET(df64, 3) : MM_SET(df64, NS_MR);
+  if (prec == OPP_F64) return k == 1 ? MM_SET(double, 1) : k == 3 ? MM_SET(double, 3) : MM_SET(double, NS_MR);
+  return k == 1 ? MM_SET(float, 1) : k == 3 ? MM_SET(float, 3) : MM_SET(float, NS_MR);
+#undef MM_SET
 }
 
 static long long g_launches = 0;
@@ -805,11 +848,12 @@ madmap_status op_time(Plan* p, int prec, const void* in, void* out, int reps, do
     ms[0] = ms[1] = ms[2] = ms[3] = 0.0;
     return MADMAP_OK;
   }
-  if (prec == OPP_DF64)
-    return p->n_stokes == 1 ? time_impl<df64, 1>(p, in, out, reps, ms, s) : time_impl<df64, 3>(p, in, out, reps, ms, s);
-  if (prec == OPP_F64)
-    return p->n_stokes == 1 ? time_impl<double, 1>(p, in, out, reps, ms, s) : time_impl<double, 3>(p, in, out, reps, ms, s);
-  return p->n_stokes == 1 ? time_impl<float, 1>(p, in, out, reps, ms, s) : time_impl<float, 3>(p, in, out, reps, ms, s);
+  const int k = layout(p);
+#define MM_TIME(R, NSV) time_impl<R, NSV>(p, in, out, reps, ms, s)
+  if (prec == OPP_DF64) return k == 1 ? MM_TIME(df64, 1) : k == 3 ? MM_TIME(df64, 3) : MM_TIME(df64, NS_MR);
+  if (prec == OPP_F64) return k == 1 ? MM_TIME(double, 1) : k == 3 ? MM_TIME(double, 3) : MM_TIME(double, NS_MR);
+  return k == 1 ? MM_TIME(float, 1) : k == 3 ? MM_TIME(float, 3) : MM_TIME(float, NS_MR);
+#undef MM_TIME
 }
 
 // Resident CTAs per SM of the operator kernels (the least of the three) and
@@ -823,12 +867,16 @@ void op_occupancy(const Plan* p, int prec, int& ctas_per_sm, int& ctas_per_tile)
     geometry<double>(p, b1, b2);
     s13 = smem_f13<double>(p);
     s2 = smem_f2<double>(p);
-    K = p->n_stokes == 1 ? pick_kernels<double, 1, IN_MAPX, OUT_MAP>(p) : pick_kernels<double, 3, IN_MAPX, OUT_MAP>(p);
+    K = layout(p) == 1   ? pick_kernels<double, 1, IN_MAPX, OUT_MAP>(p)
+        : layout(p) == 3 ? pick_kernels<double, 3, IN_MAPX, OUT_MAP>(p)
+                         : pick_kernels<double, NS_MR, IN_MAPX, OUT_MAP>(p);
   } else {
     geometry<float>(p, b1, b2);
     s13 = smem_f13<float>(p);
     s2 = smem_f2<float>(p);
-    K = p->n_stokes == 1 ? pick_kernels<float, 1, IN_MAPX, OUT_MAP>(p) : pick_kernels<float, 3, IN_MAPX, OUT_MAP>(p);
+    K = layout(p) == 1   ? pick_kernels<float, 1, IN_MAPX, OUT_MAP>(p)
+        : layout(p) == 3 ? pick_kernels<float, 3, IN_MAPX, OUT_MAP>(p)
+                         : pick_kernels<float, NS_MR, IN_MAPX, OUT_MAP>(p);
   }
   set_smem(K.f1, s13);
   set_smem(K.f2, s2);
@@ -852,17 +900,14 @@ madmap_status op_launch(Plan* p, int prec, int in_mode, int out_mode, const void
                         long long in_stride, long long out_stride, int n_rhs, const int* skip,
                         cudaStream_t s) {
   if (p->n_tiles == 0) return MADMAP_OK;
-  if (prec == OPP_DF64)
-    return p->n_stokes == 1 ? dispatch_df<1>(p, in_mode, out_mode, in, out, in_stride, out_stride, n_rhs, skip, s)
-                            : dispatch_df<3>(p, in_mode, out_mode, in, out, in_stride, out_stride, n_rhs, skip, s);
-  if (prec == OPP_F64) {
-    if (p->n_stokes == 1)
-      return dispatch_io<double, 1>(p, in_mode, out_mode, in, out, in_stride, out_stride, n_rhs, skip, s);
-    return dispatch_io<double, 3>(p, in_mode, out_mode, in, out, in_stride, out_stride, n_rhs, skip, s);
-  }
-  if (p->n_stokes == 1)
-    return dispatch_io<float, 1>(p, in_mode, out_mode, in, out, in_stride, out_stride, n_rhs, skip, s);
-  return dispatch_io<float, 3>(p, in_mode, out_mode, in, out, in_stride, out_stride, n_rhs, skip, s);
+  const int k = layout(p);
+#define MM_DF(NSV) dispatch_df<NSV>(p, in_mode, out_mode, in, out, in_stride, out_stride, n_rhs, skip, s)
+#define MM_IO(R, NSV) dispatch_io<R, NSV>(p, in_mode, out_mode, in, out, in_stride, out_stride, n_rhs, skip, s)
+  if (prec == OPP_DF64) return k == 1 ? MM_DF(1) : k == 3 ? MM_DF(3) : MM_DF(NS_MR);
+  if (prec == OPP_F64) return k == 1 ? MM_IO(double, 1) : k == 3 ? MM_IO(double, 3) : MM_IO(double, NS_MR);
+  return k == 1 ? MM_IO(float, 1) : k == 3 ? MM_IO(float, 3) : MM_IO(float, NS_MR);
+#undef MM_DF
+#undef MM_IO
 }
 
 }  // namespace mm

@@ -192,10 +192,10 @@ extern "C" const char* madmap_version(void) { return "madmap-gb300 0.1"; }
 namespace mm {
 
 // ---------------------------------------------------------------- plan kernels
-__global__ void k_validate_pix(const int* pix, long long n, int n_pix, int* bad) {
+__global__ void k_validate_pix(const int* pix, long long n, int n_pix, int* bad, int bit) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int g = pix[t];
-    if (g < -1 || g >= n_pix) atomicOr(bad, 1);
+    if (g < -1 || g >= n_pix) atomicOr(bad, bit);
   }
 }
 
@@ -206,10 +206,11 @@ __global__ void k_validate_psi(const float* psi, long long n, int* bad) {
 }
 
 // Section 5.4: one bit per global pixel, set when a sample observes it.
-__global__ void k_mark_bits(const int* pix, long long n, int n_pix, unsigned* bits) {
+// other (may be NULL): a second pixel per sample; -1 there flags the sample.
+__global__ void k_mark_bits(const int* pix, long long n, int n_pix, unsigned* bits, const int* other) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int g = pix[t];
-    if (g >= 0 && g < n_pix) atomicOr(bits + (g >> 5), 1u << (g & 31));
+    if (g >= 0 && g < n_pix && (!other || other[t] >= 0)) atomicOr(bits + (g >> 5), 1u << (g & 31));
   }
 }
 
@@ -249,10 +250,10 @@ __global__ void k_obs2glob(const unsigned* bits, const int* prefix, int n_pix, i
 }
 
 __global__ void k_pix_obs(const int* pix, long long n, int n_pix, const unsigned* bits, const int* prefix,
-                          int* pix_obs) {
+                          int* pix_obs, const int* other) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int g = pix[t];
-    pix_obs[t] = (g < 0 || g >= n_pix) ? -1 : rank_of(bits, prefix, g);
+    pix_obs[t] = (g < 0 || g >= n_pix || (other && other[t] < 0)) ? -1 : rank_of(bits, prefix, g);
   }
 }
 
@@ -422,6 +423,117 @@ __global__ void k_zero_excised_rows(int* pix_obs, long long n, const unsigned ch
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int p = pix_obs[t];
     if (p >= 0 && excised[p]) pix_obs[t] = -1;
+  }
+}
+
+// ---------------------------------------------------------------- multi-resolution preconditioner
+// Section 6 with the block diagonal of Section 5 on each pixelisation: a 2 x 2
+// (Q, U) block per polarisation pixel and a 1 x 1 block per intensity pixel;
+// the I-QU couplings join different pixels and are left out.
+// Polarisation sums per slot: hits, [cc cs ss] of A^T A and of A^T W^-1 A.
+__global__ void k_accumulate_pol(const int* pix_pol, const float* psi, long long n, const long long* off, int n_ivl,
+                                 const int* ivl_filter, const double* f0, double* acc, int* hits, double2* cs64,
+                                 float4* csdf, int first) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double c, s;
+    if (first) {
+      sincos(2.0 * (double)psi[t], &s, &c);
+      cs64[t] = make_double2(c, s);
+      const df64 cd(c), sd(s);
+      csdf[t] = make_float4(cd.hi, cd.lo, sd.hi, sd.lo);
+    } else {
+      const double2 cs = cs64[t];
+      c = cs.x;
+      s = cs.y;
+    }
+    const int q = pix_pol[t];
+    if (q < 0) continue;
+    const double w0 = f0[ivl_filter[interval_of(off, n_ivl, t)]];
+    atomicAdd(hits + q, 1);
+    double* a = acc + 6LL * q;
+    const double v[3] = {c * c, c * s, s * s};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      atomicAdd(a + k, v[k]);
+      atomicAdd(a + 3 + k, w0 * v[k]);
+    }
+  }
+}
+
+// Q/U blocks: excise below 2 hits or rcond(A^T A) < rc_ex (and slots past the
+// observed count), flag float64 blocks below rc_64, invert the weighted 2 x 2
+// block into entries (1,1), (1,2), (2,2) of the slot's 3 x 3 block.
+__global__ void k_classify_pol(const double* acc, const int* hits, int n_slots, int n_obs_pol, double rc_ex,
+                               double rc_64, double* P64, float* P32, unsigned char* excised_pol,
+                               unsigned char* fp64flag, int* counts) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_slots; k += gridDim.x * blockDim.x) {
+    bool ex = k >= n_obs_pol || hits[k] < 2;
+    double rc = 0.0, i11 = 0.0, i12 = 0.0, i22 = 0.0;
+    if (!ex) {
+      const double* a = acc + 6LL * k;
+      const double h = 0.5 * (a[0] + a[2]), d = 0.5 * (a[0] - a[2]);
+      const double r = sqrt(d * d + a[1] * a[1]);
+      const double lmax = h + r;
+      // smaller eigenvalue as det / lmax (no cancellation when the block is near-singular)
+      const double lmin = lmax > 0.0 ? (a[0] * a[2] - a[1] * a[1]) / lmax : 0.0;
+      rc = lmax > 0.0 ? lmin / lmax : 0.0;
+      ex = !(rc >= rc_ex);
+      const double det = a[3] * a[5] - a[4] * a[4];
+      if (!(det > 0.0)) ex = true;
+      if (!ex) {
+        const double id = 1.0 / det;
+        i11 = a[5] * id;
+        i12 = -a[4] * id;
+        i22 = a[3] * id;
+      }
+    }
+    const double v[6] = {0.0, 0.0, 0.0, i11, i12, i22};
+    for (int j = 1; j < 6; ++j) {
+      P64[6LL * k + j] = v[j];
+      P32[8LL * k + j] = (float)v[j];
+    }
+    P32[8LL * k + 6] = 0.f;
+    P32[8LL * k + 7] = 0.f;
+    excised_pol[k] = ex;
+    const bool f64 = !ex && rc < rc_64;
+    fp64flag[k] = f64;
+    if (ex && k < n_obs_pol) atomicAdd(counts + 1, 1);
+    if (f64) atomicAdd(counts + 2, 1);
+  }
+}
+
+// Rows whose polarisation pixel is excised become zero in both pixelisations.
+__global__ void k_drop_rows_pol(int* pix, int* pix_pol, long long n, const unsigned char* excised_pol) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int q = pix_pol[t];
+    if (q >= 0 && excised_pol[q]) {
+      pix[t] = -1;
+      pix_pol[t] = -1;
+    }
+  }
+}
+
+// Intensity sums from the remaining rows: hits and A^T W^-1 A (= sum of f(0)).
+__global__ void k_accumulate_int(const int* pix, long long n, const long long* off, int n_ivl, const int* ivl_filter,
+                                 const double* f0, double* acc, int* hits) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int p = pix[t];
+    if (p < 0) continue;
+    atomicAdd(hits + p, 1);
+    atomicAdd(acc + p, f0[ivl_filter[interval_of(off, n_ivl, t)]]);
+  }
+}
+
+// Intensity blocks: an I pixel without rows (or a slot past the count) is excised.
+__global__ void k_classify_int(const double* acc, const int* hits, int n_slots, int n_obs_i, double* P64, float* P32,
+                               unsigned char* excised, int* counts) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_slots; k += gridDim.x * blockDim.x) {
+    const bool ex = k >= n_obs_i || hits[k] == 0 || !(acc[k] > 0.0);
+    const double inv = ex ? 0.0 : 1.0 / acc[k];
+    P64[6LL * k] = inv;
+    P32[8LL * k] = (float)inv;
+    excised[k] = ex;
+    if (ex && k < n_obs_i) atomicAdd(counts, 1);
   }
 }
 
@@ -643,12 +755,87 @@ static madmap_status build_spectra(Plan* p) {
   return MADMAP_OK;
 }
 
+// Multi-resolution preconditioner and classification.  Every call passes over
+// the samples (no per-filter sums are kept); the first also stores the
+// float64 weights, zeroes the rows of excised Q/U pixels and packs the
+// float32 pointing.  Later calls see the same rows, so the classification
+// cannot change.
+static madmap_status build_preconditioner_mr(Plan* p, cudaStream_t s) {
+  const long long n = p->n_t;
+  const int n_obs = p->n_obs;
+  const bool first = !p->pre_built;
+  if (first) {
+    madmap_status a = dalloc_t(p, &p->hits, (size_t)std::max(1, n_obs));
+    if (a != MADMAP_OK) return a;
+  }
+  const size_t ns1 = (size_t)std::max(1, n_obs);
+  double *acc_pol = nullptr, *acc_i = nullptr, *df0 = nullptr;
+  int *hits_pol = nullptr, *dfilt = nullptr, *counts = nullptr;
+  long long* doff = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(acc_pol);
+    cudaFree(acc_i);
+    cudaFree(df0);
+    cudaFree(hits_pol);
+    cudaFree(dfilt);
+    cudaFree(counts);
+    cudaFree(doff);
+  };
+  cudaError_t e = cudaSuccess;
+  if ((e = cudaMalloc(&acc_pol, sizeof(double) * ns1 * 6)) != cudaSuccess ||
+      (e = cudaMalloc(&acc_i, sizeof(double) * ns1)) != cudaSuccess ||
+      (e = cudaMalloc(&hits_pol, sizeof(int) * ns1)) != cudaSuccess ||
+      (e = cudaMalloc(&doff, sizeof(long long) * (p->n_ivl + 1))) != cudaSuccess ||
+      (e = cudaMalloc(&dfilt, sizeof(int) * std::max(1, p->n_ivl))) != cudaSuccess ||
+      (e = cudaMalloc(&df0, sizeof(double) * p->n_filters)) != cudaSuccess ||
+      (e = cudaMalloc(&counts, sizeof(int) * 3)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "cudaMalloc (preconditioner temporaries)");
+  }
+  std::vector<double> f0(p->n_filters);
+  for (int f = 0; f < p->n_filters; ++f) f0[f] = p->lags[(size_t)f * p->n_lags];
+  cudaMemsetAsync(acc_pol, 0, sizeof(double) * ns1 * 6, s);
+  cudaMemsetAsync(acc_i, 0, sizeof(double) * ns1, s);
+  cudaMemsetAsync(hits_pol, 0, sizeof(int) * ns1, s);
+  cudaMemsetAsync(p->hits, 0, sizeof(int) * ns1, s);
+  cudaMemsetAsync(counts, 0, sizeof(int) * 3, s);
+  cudaMemcpyAsync(doff, p->offsets.data(), sizeof(long long) * (p->n_ivl + 1), cudaMemcpyHostToDevice, s);
+  if (p->n_ivl) cudaMemcpyAsync(dfilt, p->ivl_filter.data(), sizeof(int) * p->n_ivl, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(df0, f0.data(), sizeof(double) * p->n_filters, cudaMemcpyHostToDevice, s);
+  if (n > 0)
+    k_accumulate_pol<<<grid_for(n), 256, 0, s>>>(p->pix_obs_pol, p->psi, n, doff, p->n_ivl, dfilt, df0, acc_pol,
+                                                  hits_pol, p->cs64, p->csdf, first ? 1 : 0);
+  if (n_obs > 0)
+    k_classify_pol<<<grid_for(n_obs), 256, 0, s>>>(acc_pol, hits_pol, n_obs, p->n_obs_pol, p->rcond_excise,
+                                                    p->rcond_fp64, p->P64, p->P32, p->excised_pol, p->fp64flag,
+                                                    counts);
+  if (first && n > 0) k_drop_rows_pol<<<grid_for(n), 256, 0, s>>>(p->pix_obs, p->pix_obs_pol, n, p->excised_pol);
+  if (n > 0)
+    k_accumulate_int<<<grid_for(n), 256, 0, s>>>(p->pix_obs, n, doff, p->n_ivl, dfilt, df0, acc_i, p->hits);
+  if (n_obs > 0)
+    k_classify_int<<<grid_for(n_obs), 256, 0, s>>>(acc_i, p->hits, n_obs, p->n_obs_i, p->P64, p->P32, p->excised,
+                                                    counts);
+  if (first && n > 0) k_pack_pw<<<grid_for(n), 256, 0, s>>>(p->pix_obs, p->psi, n, p->pw);
+  int hc[3] = {0, 0, 0};
+  e = cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "preconditioner build");
+  p->n_excised = hc[0];
+  p->n_excised_pol = hc[1];
+  p->n_fp64 = hc[2];
+  p->pre_built = true;
+  return MADMAP_OK;
+}
+
 // Block preconditioner (A^T W^-1 A)^-1 and the pixel classification.  The
 // first call passes over the samples; when the per-filter sums G fit in
 // 512 MB they are kept, so a change of filters (set_filters) only recombines
 // them per pixel with the new f(0) and reinverts the blocks.  The first
 // call's hit counts are kept too, so the classification cannot change.
 static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
+  if (p->multires) return build_preconditioner_mr(p, s);
   const long long n = p->n_t;
   const int n_obs = p->n_obs;
   const int ns = p->n_stokes;
@@ -732,6 +919,8 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
   MM_CHECK(d->n_samples == 0 || d->pix != nullptr, MADMAP_ERR_INVALID_ARG, "pix is NULL");
   MM_CHECK((d->n_stokes == 1) == (d->psi == nullptr) || d->n_samples == 0, MADMAP_ERR_INVALID_ARG,
            "psi must be NULL for T and non-NULL for IQU");
+  MM_CHECK(!d->pix_pol || (d->n_stokes == 3 && d->n_pix_pol > 0), MADMAP_ERR_INVALID_ARG,
+           "pix_pol needs n_stokes = 3 and n_pix_pol > 0");
   MM_CHECK(d->n_intervals >= 0 && d->interval_offsets != nullptr, MADMAP_ERR_INVALID_ARG, "bad intervals");
   MM_CHECK(d->n_intervals == 0 || d->interval_filter != nullptr, MADMAP_ERR_INVALID_ARG, "interval_filter NULL");
   MM_CHECK(d->n_filters >= 1 && d->n_lags >= 1 && d->filter_lags != nullptr, MADMAP_ERR_INVALID_ARG,
@@ -784,8 +973,20 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
   MM_TRY(dalloc_t(p, &p->dev_flag, 16));
   MM_TRY(dalloc_t(p, &bits, n_words));
   MM_TRY(dalloc_t(p, &prefix, n_words));
-  MM_TRY(dalloc_t(p, &total, 1));
+  MM_TRY(dalloc_t(p, &total, 2));
   MM_TRY(dalloc_t(p, &p->pix_obs, std::max(1LL, n)));
+  // the second pixelisation of multi-resolution plans
+  p->multires = d->pix_pol != nullptr;
+  p->n_pix_pol = p->multires ? d->n_pix_pol : 0;
+  const int n_words_pol = (p->n_pix_pol + 31) / 32;
+  unsigned* bits_pol = nullptr;
+  int* prefix_pol = nullptr;
+  if (p->multires) {
+    MM_TRY(dalloc_t(p, &bits_pol, std::max(1, n_words_pol)));
+    MM_TRY(dalloc_t(p, &prefix_pol, std::max(1, n_words_pol)));
+    MM_TRY(dalloc_t(p, &p->pix_obs_pol, std::max(1LL, n)));
+    MM_TRYC(cudaMemsetAsync(bits_pol, 0, sizeof(unsigned) * std::max(1, n_words_pol), s));
+  }
   if (p->n_stokes == 3) {
     MM_TRY(dalloc_t(p, &p->psi, std::max(1LL, n)));
     MM_TRY(dalloc_t(p, &p->cs64, std::max(1LL, n)));
@@ -795,17 +996,20 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
   MM_TRYC(cudaMemsetAsync(p->dev_flag, 0, 16 * sizeof(int), s));
   MM_TRYC(cudaMemsetAsync(bits, 0, sizeof(unsigned) * n_words, s));
   if (n > 0) {
-    k_validate_pix<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, p->dev_flag);
+    k_validate_pix<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, p->dev_flag, 1);
+    if (p->multires) k_validate_pix<<<grid_for(n), 256, 0, s>>>(d->pix_pol, n, p->n_pix_pol, p->dev_flag, 4);
     if (p->n_stokes == 3) {
       MM_TRYC(cudaMemcpyAsync(p->psi, d->psi, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
       k_validate_psi<<<grid_for(n), 256, 0, s>>>(p->psi, n, p->dev_flag);
     }
-    k_mark_bits<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, bits);
+    k_mark_bits<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, bits, d->pix_pol);
+    if (p->multires) k_mark_bits<<<grid_for(n), 256, 0, s>>>(d->pix_pol, n, p->n_pix_pol, bits_pol, d->pix);
   }
   k_scan_words<<<1, 1024, 0, s>>>(bits, n_words, prefix, total);
-  int hv[2] = {0, 0};
+  if (p->multires) k_scan_words<<<1, 1024, 0, s>>>(bits_pol, n_words_pol, prefix_pol, total + 1);
+  int hv[3] = {0, 0, 0};
   MM_TRYC(cudaMemcpyAsync(&hv[0], p->dev_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-  MM_TRYC(cudaMemcpyAsync(&hv[1], total, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MM_TRYC(cudaMemcpyAsync(&hv[1], total, sizeof(int) * (p->multires ? 2 : 1), cudaMemcpyDeviceToHost, s));
   MM_TRYC(cudaStreamSynchronize(s));
   MM_TRYC(cudaGetLastError());
   if (hv[0] & 1) {
@@ -818,15 +1022,29 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
     set_error("psi holds non-finite values");
     return MADMAP_ERR_INVALID_ARG;
   }
-  p->n_obs = hv[1];
+  if (hv[0] & 4) {
+    delete p;
+    set_error("pix_pol holds values outside [-1, n_pix_pol)");
+    return MADMAP_ERR_INVALID_ARG;
+  }
+  p->n_obs_i = hv[1];
+  p->n_obs_pol = p->multires ? hv[2] : 0;
+  p->n_obs = std::max(p->n_obs_i, p->n_obs_pol);  // map rows (slots for multi-resolution plans)
   const int n_obs = p->n_obs;
-  MM_TRY(dalloc_t(p, &p->obs2glob, std::max(1, n_obs)));
+  MM_TRY(dalloc_t(p, &p->obs2glob, std::max(1, p->n_obs_i)));
   MM_TRY(dalloc_t(p, &p->excised, std::max(1, n_obs)));
   MM_TRY(dalloc_t(p, &p->fp64flag, std::max(1, n_obs)));
   MM_TRY(dalloc_t(p, &p->P64, (size_t)std::max(1, n_obs) * (p->n_stokes == 1 ? 1 : 6)));
   MM_TRY(dalloc_t(p, &p->P32, (size_t)std::max(1, n_obs) * (p->n_stokes == 1 ? 1 : 8)));
   k_obs2glob<<<grid_for(p->n_pix), 256, 0, s>>>(bits, prefix, p->n_pix, p->obs2glob);
-  if (n > 0) k_pix_obs<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, bits, prefix, p->pix_obs);
+  if (n > 0) k_pix_obs<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, bits, prefix, p->pix_obs, d->pix_pol);
+  if (p->multires) {
+    MM_TRY(dalloc_t(p, &p->obs2glob_pol, std::max(1, p->n_obs_pol)));
+    MM_TRY(dalloc_t(p, &p->excised_pol, std::max(1, n_obs)));
+    k_obs2glob<<<grid_for(p->n_pix_pol), 256, 0, s>>>(bits_pol, prefix_pol, p->n_pix_pol, p->obs2glob_pol);
+    if (n > 0)
+      k_pix_obs<<<grid_for(n), 256, 0, s>>>(d->pix_pol, n, p->n_pix_pol, bits_pol, prefix_pol, p->pix_obs_pol, d->pix);
+  }
   MM_TRY(build_preconditioner(p, s));
   // FFT geometry and windows
   p->M = d->fft_len ? d->fft_len : choose_fft_len(p->offsets, p->ivl_filter, p->n_filters, p->n_lags);
@@ -933,6 +1151,8 @@ extern "C" madmap_status madmap_plan_get_stats(madmap_plan_t plan, madmap_plan_s
   o->n_filters = p->n_filters;
   o->n_samples = p->n_t;
   o->device_bytes = (int64_t)(p->device_bytes + solve_buffer_bytes(p));
+  o->n_obs_pol = p->n_obs_pol;
+  o->n_excised_pol = p->n_excised_pol;
   return MADMAP_OK;
 }
 
@@ -941,11 +1161,24 @@ extern "C" madmap_status madmap_plan_observed(madmap_plan_t plan, int32_t* n_obs
   MM_CHECK(plan, MADMAP_ERR_INVALID_ARG, "plan_observed: NULL plan");
   const Plan* p = reinterpret_cast<const Plan*>(plan);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (n_obs) *n_obs = p->n_obs;
-  if (obs2glob && p->n_obs)
-    MM_CUDA(cudaMemcpyAsync(obs2glob, p->obs2glob, sizeof(int) * p->n_obs, cudaMemcpyDeviceToDevice, s));
-  if (excised && p->n_obs)
-    MM_CUDA(cudaMemcpyAsync(excised, p->excised, p->n_obs, cudaMemcpyDeviceToDevice, s));
+  if (n_obs) *n_obs = p->n_obs_i;
+  if (obs2glob && p->n_obs_i)
+    MM_CUDA(cudaMemcpyAsync(obs2glob, p->obs2glob, sizeof(int) * p->n_obs_i, cudaMemcpyDeviceToDevice, s));
+  if (excised && p->n_obs_i)
+    MM_CUDA(cudaMemcpyAsync(excised, p->excised, p->n_obs_i, cudaMemcpyDeviceToDevice, s));
+  return MADMAP_OK;
+}
+
+extern "C" madmap_status madmap_plan_observed_pol(madmap_plan_t plan, int32_t* n_obs_pol, int32_t* obs2glob_pol,
+                                                  uint8_t* excised_pol, void* stream) {
+  MM_CHECK(plan, MADMAP_ERR_INVALID_ARG, "plan_observed_pol: NULL plan");
+  const Plan* p = reinterpret_cast<const Plan*>(plan);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n_obs_pol) *n_obs_pol = p->n_obs_pol;
+  if (obs2glob_pol && p->n_obs_pol)
+    MM_CUDA(cudaMemcpyAsync(obs2glob_pol, p->obs2glob_pol, sizeof(int) * p->n_obs_pol, cudaMemcpyDeviceToDevice, s));
+  if (excised_pol && p->n_obs_pol)
+    MM_CUDA(cudaMemcpyAsync(excised_pol, p->excised_pol, p->n_obs_pol, cudaMemcpyDeviceToDevice, s));
   return MADMAP_OK;
 }
 

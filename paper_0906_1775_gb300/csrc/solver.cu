@@ -1078,10 +1078,11 @@ static madmap_status resume_impl(Plan* p, const madmap_checkpoint* c, double* m,
 //                  (A lambda)_t (d - A m)_t'   (both orders for tau > 0),
 // from perturbing N^-1 and d in m = H^-1 A^T N^-1 d.
 
-// out_t = alpha d_t + beta (A x)_t (float64 weights and map, float output)
+// out_t = alpha d_t + beta (A x)_t (float64 weights and map, float output);
+// pix_pol (multi-resolution plans, else NULL) gives the Q/U slot of each sample
 template <int NS>
-__global__ void k_unpoint(const double* x, const int* pix, const double2* cs, const float* d, double alpha,
-                          double beta, float* out, long long n) {
+__global__ void k_unpoint(const double* x, const int* pix, const int* pix_pol, const double2* cs, const float* d,
+                          double alpha, double beta, float* out, long long n) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int q = pix[t];
     double ax = 0.0;
@@ -1090,18 +1091,24 @@ __global__ void k_unpoint(const double* x, const int* pix, const double2* cs, co
         ax = x[q];
       } else {
         const double2 w = cs[t];
-        ax = x[4LL * q] + x[4LL * q + 1] * w.x + x[4LL * q + 2] * w.y;
+        const int qp = pix_pol ? pix_pol[t] : q;
+        ax = x[4LL * q] + x[4LL * qp + 1] * w.x + x[4LL * qp + 2] * w.y;
       }
     }
     out[t] = (float)((d ? alpha * (double)d[t] : 0.0) + beta * ax);
   }
 }
 
-// zero the adjoint right-hand side at excised pixels (no row of H there)
-__global__ void k_mask_excised(double* b, long long nvec_pixels, int ns_pad, const unsigned char* excised) {
+// zero the adjoint right-hand side at excised pixels (no row of H there);
+// excised_pol (multi-resolution plans, else NULL) covers the Q/U columns
+__global__ void k_mask_excised(double* b, long long nvec_pixels, int ns_pad, const unsigned char* excised,
+                               const unsigned char* excised_pol) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvec_pixels * ns_pad;
-       i += (long long)gridDim.x * blockDim.x)
-    if (excised[i / ns_pad]) b[i] = 0.0;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long k = i / ns_pad;
+    const bool ex = (excised_pol && i % ns_pad != 0) ? excised_pol[k] : excised[k];
+    if (ex) b[i] = 0.0;
+  }
 }
 
 // Lag correlation sum_{|t-t'|=tau} a_t r_t' by direct sums: CTA (lag block,
@@ -1201,7 +1208,7 @@ static madmap_status backward_impl(Plan* p, const float* d, const double* m, con
   // adjoint solve H lambda = dL/dm (zero at excised pixels)
   count_launches(2);
   k_pack<double, double><<<grid_vec(nv), NT, 0, s>>>(gm, sb64->b64, n, ns, np);
-  k_mask_excised<<<grid_vec(nv), NT, 0, s>>>(sb64->b64, n, np, p->excised);
+  k_mask_excised<<<grid_vec(nv), NT, 0, s>>>(sb64->b64, n, np, p->excised, p->multires ? p->excised_pol : nullptr);
   std::vector<madmap_solve_info> I(1);
   memset(&I[0], 0, sizeof(I[0]));
   const double* lam = nullptr;
@@ -1210,9 +1217,10 @@ static madmap_status backward_impl(Plan* p, const float* d, const double* m, con
   // a = A lambda; r = d - A m  (m packed into the spare float64 vector t64)
   const int gt = (int)std::min<long long>((nt + 255) / 256, 152LL * 32);
   count_launches(3);
-  k_unpoint<NS><<<std::max(1, gt), 256, 0, s>>>(lam, p->pix_obs, p->cs64, nullptr, 0.0, 1.0, p->bw_a, nt);
+  const int* pix_pol = p->multires ? p->pix_obs_pol : nullptr;
+  k_unpoint<NS><<<std::max(1, gt), 256, 0, s>>>(lam, p->pix_obs, pix_pol, p->cs64, nullptr, 0.0, 1.0, p->bw_a, nt);
   k_pack<double, double><<<grid_vec(nv), NT, 0, s>>>(m, sb64->t64, n, ns, np);
-  k_unpoint<NS><<<std::max(1, gt), 256, 0, s>>>(sb64->t64, p->pix_obs, p->cs64, d, 1.0, -1.0, p->bw_r, nt);
+  k_unpoint<NS><<<std::max(1, gt), 256, 0, s>>>(sb64->t64, p->pix_obs, pix_pol, p->cs64, d, 1.0, -1.0, p->bw_r, nt);
   if (grad_d) {
     st = op_launch(p, false, IN_TOD_REAL, OUT_TOD, p->bw_a, grad_d, 0, 0, 1, nullptr, s);
     if (st != MADMAP_OK) return st;

@@ -79,3 +79,38 @@ def test_noise_filter_vjp_matches_oracle_chain_rule():
         g = rng.standard_normal(64)
         _, dl = filter_lags(64, 100.0, *params, with_grad=True)
         assert np.allclose(mm.madmap_noise_filter_vjp(64, 100.0, *params, g), dl @ g, rtol=1e-11, atol=1e-14)
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding marshals has the header's size and field offsets
+    (compiled from include/madmap.h by the host C compiler)."""
+    import shutil
+    import subprocess
+    mm = _lib()
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    L = mm._lib
+    structs = {"madmap_plan_desc": L.madmap_plan_desc, "madmap_plan_stats": L.madmap_plan_stats,
+               "madmap_checkpoint": L.madmap_checkpoint, "madmap_solve_opts": L.madmap_solve_opts,
+               "madmap_solve_info": L.madmap_solve_info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "madmap.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    import ctypes
+    seen = 0
+    for line in filter(None, out):
+        name, field, value = line.split()
+        cls = structs[name]
+        got = ctypes.sizeof(cls) if field == "sizeof" else getattr(cls, field).offset
+        assert got == int(value), (name, field, got, value)
+        seen += 1
+    assert seen == sum(len(c._fields_) + 1 for c in structs.values())
