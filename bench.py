@@ -163,7 +163,7 @@ def stokes_err(m, ref, keep):
 def operator_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("operator.cu", "internal.cuh"):
+    for f in ("operator_kernels.cuh", "internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_0906_1775_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 

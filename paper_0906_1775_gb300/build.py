@@ -20,7 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmadmap.so")
-SOURCES = ["plan.cu", "operator.cu", "solver.cu"]
+SOURCES = ["plan.cu", "operator.cu", "operator_f32.cu", "operator_f64.cu", "operator_df64.cu", "solver.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -43,7 +43,8 @@ def flags(extra=()):
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "internal.cuh"), os.path.join(INCLUDE, "madmap.h")]
+    deps = [src, os.path.join(CSRC, "internal.cuh"), os.path.join(CSRC, "operator_kernels.cuh"),
+            os.path.join(INCLUDE, "madmap.h")]
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 

@@ -218,6 +218,22 @@ madmap_status op_launch_set(Plan* p, int prec, int in_mode, int out_mode, const 
 // Kernel launch accounting (library-wide).
 void count_launches(long long n);
 
+// The operator of one precision (float32, float64 or double-float), each
+// compiled in its own translation unit; operator.cu picks the table by `prec`.
+struct OpImpl {
+  madmap_status (*launch)(Plan* p, int in_mode, int out_mode, const void* in, void* out, long long in_stride,
+                          long long out_stride, int n_rhs, const int* skip, cudaStream_t s);
+  madmap_status (*launch_set)(Plan* p, int in_mode, int out_mode, const void* in, void* out, long long in_stride,
+                              long long out_stride, const int* skip, int skip_stride, const TileSet* ts,
+                              cudaStream_t s);
+  madmap_status (*time)(Plan* p, const void* in, void* out, int reps, double ms[4], cudaStream_t s);
+  void (*occupancy)(const Plan* p, int& ctas_per_sm, int& ctas_per_tile);  // NULL for double-float
+  size_t (*f13_smem)(const Plan* p);
+};
+const OpImpl& op_impl_f32();
+const OpImpl& op_impl_f64();
+const OpImpl& op_impl_df64();
+
 // Overlap-save windows of the intervals [off[i], off[i+1]) for FFT length M,
 // paired two per complex FFT within each filter.
 void build_tiles(const std::vector<long long>& off, const std::vector<int>& filt, int n_filters, int n_lags, int M,

@@ -20,550 +20,18 @@
 // The row/column FFTs run in shared memory as radix-2 stages fused three at a
 // time in registers; forward transforms leave bit-reversed order and the
 // inverses consume it, so no reordering pass exists anywhere.
+//
+// This file holds the precision-independent entry points and the
+// allocation-free weighting; the kernels are in operator_kernels.cuh.
 #include <math.h>
 
 #include <algorithm>
 #include <mutex>
-#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
 
 namespace mm {
-
-namespace {
-
-enum { IN_MAPX = 0, IN_TODF = 1, IN_TODR = 2 };
-
-// Stokes layouts of the kernels' NS parameter: 1 = T, 3 = IQU on one
-// pixelisation, NS_MR = IQU with Q and U on a second pixelisation (Section 6;
-// each sample then carries an I pixel and a Q/U pixel of the slot layout).
-constexpr int NS_MR = 4;
-__host__ __device__ constexpr bool polarised(int ns) { return ns >= 3; }
-inline int layout(const Plan* p) { return p->multires ? NS_MR : p->n_stokes; }
-
-struct OpArgs {
-  const Tile* tiles;
-  int tile0;
-  int M, N1, N2, logN1, logN2, B1, logB1, B2;
-  const int* pix;
-  const float* psi;
-  const double2* cs64;
-  const float4* csdf;
-  const int2* pw;      // (pixel, angle bits) per sample, IQU
-  const int* pixq;     // Q/U pixel per sample (multi-resolution plans)
-  const void* in;
-  long long in_stride;
-  void* out;
-  long long out_stride;
-  void* scratch;
-  const void* H;
-  const void* tw;
-  const int* skip;    // done flag(s): one shared flag, or one per right-hand side
-  int skip_stride;    // 0: *skip covers every tile; > 0: skip[rhs * skip_stride] per lane
-};
-
-// A tile is skipped when its solve (or both of its right-hand sides) is done.
-__device__ __forceinline__ bool skip_tile(const OpArgs& a, const Tile* T) {
-  if (!a.skip) return false;
-  if (a.skip_stride == 0) return *a.skip != 0;
-  return a.skip[T->l[0].rhs * a.skip_stride] != 0 && a.skip[T->l[1].rhs * a.skip_stride] != 0;
-}
-
-// cos 2psi, sin 2psi for the float32 operator: 2 psi is reduced to [-pi, pi]
-// by subtracting the nearest multiple of 2 pi in two parts (2 pi rounded to
-// float, then the remainder of 2 pi), and the hardware approximations take
-// it from there (absolute error about 4e-7 on [-pi, pi], far inside the
-// float32 operator's own rounding; the float64 operator uses exact weights).
-__device__ __forceinline__ void sincos_2psi(float psi, float& s, float& c) {
-  const float x = 2.0f * psi;
-  const float k = rintf(x * 0.15915494309189535f);
-  float r = fmaf(-k, 6.2831854820251465f, x);
-  r = fmaf(-k, -1.7484556000744970e-07f, r);
-  __sincosf(r, &s, &c);
-}
-template <typename Real, int NS>
-__device__ __forceinline__ Real gather(const Real* x, int p, Real c, Real s);
-template <>
-__device__ __forceinline__ float gather<float, 1>(const float* x, int p, float, float) {
-  return x[p];
-}
-template <>
-__device__ __forceinline__ double gather<double, 1>(const double* x, int p, double, double) {
-  return x[p];
-}
-template <>
-__device__ __forceinline__ float gather<float, 3>(const float* x, int p, float c, float s) {
-  const float4 m = reinterpret_cast<const float4*>(x)[p];
-  return m.x + m.y * c + m.z * s;
-}
-template <>
-__device__ __forceinline__ double gather<double, 3>(const double* x, int p, double c, double s) {
-  const double2* xp = reinterpret_cast<const double2*>(x + 4LL * p);
-  const double2 u = xp[0], v = xp[1];
-  return u.x + u.y * c + v.x * s;
-}
-
-// double-float: the map holds float pairs ([n_obs][4] pairs for IQU)
-template <>
-__device__ __forceinline__ df64 gather<df64, 1>(const df64* x, int p, df64, df64) {
-  return x[p];
-}
-template <>
-__device__ __forceinline__ df64 gather<df64, 3>(const df64* x, int p, df64 c, df64 s) {
-  const float4* xp = reinterpret_cast<const float4*>(x + 4LL * p);
-  const float4 u = xp[0], v = xp[1];
-  return df64(u.x, u.y) + df64(u.z, u.w) * c + df64(v.x, v.y) * s;
-}
-
-// multi-resolution maps: I from slot p, Q and U from slot q
-template <typename Real>
-__device__ __forceinline__ Real gather_mr(const Real* x, int p, int q, Real c, Real s) {
-  if constexpr (std::is_same<Real, float>::value) {
-    const float4 m = reinterpret_cast<const float4*>(x)[q];
-    return x[4LL * p] + m.y * c + m.z * s;
-  } else {
-    return x[4LL * p] + x[4LL * q + 1] * c + x[4LL * q + 2] * s;
-  }
-}
-
-template <typename Real, int NS>
-__device__ __forceinline__ void scatter(typename OutT<Real>::type* y, int p, Real v, Real c, Real s);
-template <>
-__device__ __forceinline__ void scatter<float, 1>(float* y, int p, float v, float, float) {
-  atomicAdd(y + p, v);
-}
-template <>
-__device__ __forceinline__ void scatter<double, 1>(double* y, int p, double v, double, double) {
-  atomicAdd(y + p, v);
-}
-template <>
-__device__ __forceinline__ void scatter<float, 3>(float* y, int p, float v, float c, float s) {
-  atomicAdd(reinterpret_cast<float4*>(y) + p, make_float4(v, v * c, v * s, 0.0f));
-}
-template <>
-__device__ __forceinline__ void scatter<double, 3>(double* y, int p, double v, double c, double s) {
-  double* q = y + 4LL * p;
-  atomicAdd(q, v);
-  atomicAdd(q + 1, v * c);
-  atomicAdd(q + 2, v * s);
-}
-// double-float results are rounded to float64 once per sample and added with
-// float64 atomics
-template <>
-__device__ __forceinline__ void scatter<df64, 1>(double* y, int p, df64 v, df64, df64) {
-  atomicAdd(y + p, to_double(v));
-}
-// (IQU double-float outputs are weighted in float64 inside k_f3)
-
-template <typename Real>
-__device__ __forceinline__ void scatter_mr(typename OutT<Real>::type* y, int p, int q, Real v, Real c, Real s) {
-  if constexpr (std::is_same<Real, float>::value) {
-    atomicAdd(y + 4LL * p, v);
-    atomicAdd(reinterpret_cast<float4*>(y) + q, make_float4(0.0f, v * c, v * s, 0.0f));
-  } else {
-    atomicAdd(y + 4LL * p, v);
-    atomicAdd(y + 4LL * q + 1, v * c);
-    atomicAdd(y + 4LL * q + 2, v * s);
-  }
-}
-
-// A lane seen from one CTA: valid input window positions [in_lo, in_hi),
-// kept outputs [out_lo, out_hi), and base pointers already offset by the
-// window start so every access is base[n] with a 32-bit window position n.
-template <typename Real>
-struct LaneView {
-  int in_lo, in_hi, out_lo, out_hi;
-  const int* pix;
-  const float* psi;
-  const double2* cs;
-  const float4* csd;
-  const int2* pw;
-  const int* pq;
-  const void* in;
-  void* out;
-};
-
-template <typename Real, int IN, int OUT>
-__device__ __forceinline__ LaneView<Real> lane_view(const OpArgs& a, const Lane& g) {
-  LaneView<Real> v;
-  const long long ws = g.ws;
-  long long lo = g.lo - ws, hi = g.hi - ws;
-  lo = lo < 0 ? 0 : (lo > a.M ? a.M : lo);
-  hi = hi < lo ? lo : (hi > a.M ? a.M : hi);
-  v.in_lo = (int)lo;
-  v.in_hi = (int)hi;
-  v.out_lo = g.out_lo;
-  v.out_hi = g.out_hi;
-  v.pix = a.pix + ws;
-  v.psi = a.psi + ws;
-  v.cs = a.cs64 + ws;
-  v.csd = a.csdf + ws;
-  v.pw = a.pw + ws;
-  v.pq = a.pixq ? a.pixq + ws : nullptr;
-  if (IN == IN_TODF) v.in = static_cast<const float*>(a.in) + g.rhs * a.in_stride + ws;
-  else if (IN == IN_TODR) v.in = static_cast<const Real*>(a.in) + g.rhs * a.in_stride + ws;
-  else v.in = static_cast<const Real*>(a.in) + g.rhs * a.in_stride;
-  typedef typename OutT<Real>::type Out;
-  if (OUT == OUT_TOD) v.out = static_cast<Out*>(a.out) + g.rhs * a.out_stride + ws;
-  else v.out = static_cast<Out*>(a.out) + g.rhs * a.out_stride;
-  return v;
-}
-
-__device__ __forceinline__ bool in_range(int n, int lo, int hi) { return (unsigned)(n - lo) < (unsigned)(hi - lo); }
-
-// cos/sin weights of window position n of a lane (psi or cached float64 pair)
-template <typename Real>
-__device__ __forceinline__ void lane_angle(const LaneView<Real>& L, int n, bool ok, Real& c, Real& s);
-template <>
-__device__ __forceinline__ void lane_angle<float>(const LaneView<float>& L, int n, bool ok, float& c, float& s) {
-  c = ok ? __ldg(L.psi + n) : 0.f;  // the angle; turned into weights after the loads
-  s = 0.f;
-}
-template <>
-__device__ __forceinline__ void lane_angle<double>(const LaneView<double>& L, int n, bool ok, double& c, double& s) {
-  if (ok) {
-    const double2 cs = L.cs[n];
-    c = cs.x;
-    s = cs.y;
-  } else {
-    c = s = 0.0;
-  }
-}
-template <>
-__device__ __forceinline__ void lane_angle<df64>(const LaneView<df64>& L, int n, bool ok, df64& c, df64& s) {
-  if (ok) {
-    const float4 cs = L.csd[n];
-    c = df64(cs.x, cs.y);
-    s = df64(cs.z, cs.w);
-  } else {
-    c = s = df64();
-  }
-}
-template <typename Real>
-__device__ __forceinline__ void finish_angle(Real& c, Real& s) {}
-
-// Pixel and weights' source of window position n of a lane: the float32
-// operator reads pixel and angle as one 8-byte pair; the others the pixel and
-// their cached cos/sin pairs.
-template <typename Real, int NS>
-__device__ __forceinline__ void load_pointing(const LaneView<Real>& L, int n, bool ok, int& pp, Real& c, Real& s) {
-  if (polarised(NS) && std::is_same<Real, float>::value) {
-    if (ok) {
-      const int2 w = __ldg(L.pw + n);
-      pp = w.x;
-      c = (Real)__int_as_float(w.y);
-    } else {
-      pp = -1;
-      c = Real(0);
-    }
-    s = Real(0);
-  } else {
-    pp = ok ? __ldg(L.pix + n) : -1;
-    c = s = Real(0);
-    if (polarised(NS)) lane_angle<Real>(L, n, ok, c, s);
-  }
-}
-template <>
-__device__ __forceinline__ void finish_angle<float>(float& c, float& s) {
-  const float psi = c;
-  sincos_2psi(psi, s, c);
-}
-
-// The memory phases below work in batches: every thread first issues all the
-// independent loads of U elements (pointing, then map gathers; or scratch and
-// twiddles), and only then consumes them, so each thread keeps U loads in
-// flight instead of one.
-
-// Output twiddles exp(-2 pi i m / M) of the four-step transform from two
-// small shared tables: lo[b] = w^b for b < L = 2^logL and hi[a] = w^(a L), so
-// w^m = hi[m >> logL] * lo[m & (L - 1)] (one complex product, a few ulp).
-// Reading them from the M-entry table instead scatters one L2 sector per element.
-// The float64 kernels keep reading the M-entry table: on this GPU a float64
-// complex product costs more than the scattered load it would replace.
-template <typename C>
-__device__ __forceinline__ void build_split_twiddles(C* lo, C* hi, const C* twM, int logM, int logL) {
-  if constexpr (sizeof(C) == 8) {
-    for (int i = threadIdx.x; i < (1 << logL); i += OP_THREADS) lo[i] = twM[i];
-    for (int i = threadIdx.x; i < (1 << (logM - logL)); i += OP_THREADS) hi[i] = twM[(long long)i << logL];
-  }
-}
-template <typename C>
-__device__ __forceinline__ C split_twiddle(const C* lo, const C* hi, const C* twM, int m, int logL) {
-  if constexpr (sizeof(C) != 8) return twM[m];
-  else return cmul(hi[m >> logL], lo[m & ((1 << logL) - 1)]);
-}
-__host__ __device__ inline int split_log(int logM) { return (logM + 1) >> 1; }
-// Shared entries of the two split tables (none for float64).
-__host__ __device__ inline int split_entries(int esz, int logM) {
-  return esz == 8 ? (1 << split_log(logM)) + (1 << (logM - split_log(logM))) : 0;
-}
-
-// ---------------------------------------------------------------- k_f1
-// LG2 > 0 fixes the column length N2 = 2^LG2 at compile time (and with it the
-// CTA's column count); LG2 = 0 reads the geometry from the arguments.
-template <typename Real, int NS, int IN, int LG2>
-__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a) {
-  typedef typename CxT<Real>::type C;
-  constexpr int ELOG = sizeof(Real) == 4 ? 12 : 11;
-  const int logN2 = LG2 ? LG2 : a.logN2;
-  const int logB1 = LG2 ? ELOG - LG2 : a.logB1;
-  const int N2 = 1 << logN2, B1 = 1 << logB1;
-  const int tl = blockIdx.y;
-  const Tile* T = a.tiles + a.tile0 + tl;
-  if (skip_tile(a, T)) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int SW = LG2 ? lay_sw(sizeof(C), LG2, true) : (sizeof(C) == 16 ? 0 : 1);
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  const int rs = lay_rs(sizeof(C), logN2, true);
-  C* tw = buf + B1 * rs;
-  const int logM = a.logN1 + logN2, logL = split_log(logM);
-  C* tlo = tw + N2;
-  C* thi = tlo + (1 << logL);
-  const C* twM = static_cast<const C*>(a.tw);
-  build_pass_twiddles(tw, logN2, twM, a.N1);
-  build_split_twiddles(tlo, thi, twM, logM, logL);
-  LaneView<Real> L[2];
-  L[0] = lane_view<Real, IN, OUT_MAP>(a, T->l[0]);
-  L[1] = lane_view<Real, IN, OUT_MAP>(a, T->l[1]);
-  const int n1_0 = blockIdx.x * B1;
-  const int total = B1 << logN2;
-  constexpr int bd = OP_THREADS;
-  constexpr int U = (IN == IN_MAPX && polarised(NS)) ? 4 : 8;
-  for (int e0 = threadIdx.x; e0 < total; e0 += bd * U) {
-    int nn[U];
-    bool ok[2][U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * bd;
-      nn[u] = n1_0 + (e & (B1 - 1)) + ((e >> logB1) << a.logN1);
-#pragma unroll
-      for (int l = 0; l < 2; ++l) ok[l][u] = e < total && in_range(nn[u], L[l].in_lo, L[l].in_hi);
-    }
-    Real v[2][U];
-    if (IN != IN_MAPX) {
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int l = 0; l < 2; ++l) {
-          if (IN == IN_TODF)
-            v[l][u] = ok[l][u] ? (Real)__ldg(static_cast<const float*>(L[l].in) + nn[u]) : Real(0);
-          else
-            v[l][u] = ok[l][u] ? static_cast<const Real*>(L[l].in)[nn[u]] : Real(0);
-        }
-    } else {
-      int pp[2][U], qq[2][U];
-      Real cc[2][U], ss[2][U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int l = 0; l < 2; ++l) {
-          load_pointing<Real, NS>(L[l], nn[u], ok[l][u], pp[l][u], cc[l][u], ss[l][u]);
-          if constexpr (NS == NS_MR) qq[l][u] = ok[l][u] ? __ldg(L[l].pq + nn[u]) : -1;
-        }
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int l = 0; l < 2; ++l) {
-          Real c = cc[l][u], sn = ss[l][u];
-          if (polarised(NS)) finish_angle<Real>(c, sn);
-          if constexpr (NS == NS_MR)
-            v[l][u] = pp[l][u] >= 0 ? gather_mr<Real>(static_cast<const Real*>(L[l].in), pp[l][u], qq[l][u], c, sn)
-                                    : Real(0);
-          else
-            v[l][u] = pp[l][u] >= 0 ? gather<Real, NS>(static_cast<const Real*>(L[l].in), pp[l][u], c, sn) : Real(0);
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * bd;
-      if (e < total) {
-        C z;
-        z.x = v[0][u];
-        z.y = v[1][u];
-        buf[(e & (B1 - 1)) * rs + swz<SW>(e >> logB1)] = z;
-      }
-    }
-  }
-  __syncthreads();
-  fft_rows<C, false, SW>(buf, B1, rs, logN2, tw);
-  C* sc = static_cast<C*>(a.scratch) + (long long)tl * a.M;
-  const int mask = a.M - 1;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < total; e += bd) {
-    const int j = e & (B1 - 1), pos = e >> logB1;
-    const C w = split_twiddle(tlo, thi, twM, ((n1_0 + j) * brev_n(pos, logN2)) & mask, logL);
-    sc[(long long)pos * a.N1 + n1_0 + j] = cmul(buf[j * rs + swz<SW>(pos)], w);
-  }
-}
-
-// ---------------------------------------------------------------- k_f2
-// LG1 > 0 fixes the row length N1 = 2^LG1 at compile time.
-template <typename Real, int LG1>
-__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f2(OpArgs a) {
-  typedef typename CxT<Real>::type C;
-  constexpr int ELOG = sizeof(Real) == 4 ? 12 : 11;
-  const int logN1 = LG1 ? LG1 : a.logN1;
-  const int N1 = 1 << logN1;
-  const int B2 = LG1 ? (1 << (ELOG - LG1)) : a.B2;
-  const int tl = blockIdx.y;
-  const Tile* T = a.tiles + a.tile0 + tl;
-  if (skip_tile(a, T)) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int SW = LG1 ? lay_sw(sizeof(C), LG1, false) : 1;
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  const int rs = lay_rs(sizeof(C), logN1, false);
-  C* tw = buf + B2 * rs;
-  const C* twM = static_cast<const C*>(a.tw);
-  build_pass_twiddles(tw, logN1, twM, a.N2);
-  const int filt = T->filter;
-  const int pos0 = blockIdx.x * B2;
-  C* sc = static_cast<C*>(a.scratch) + (long long)tl * a.M + (long long)pos0 * N1;
-  const int total = B2 << logN1;
-  constexpr int bd = OP_THREADS;
-  for (int e0 = threadIdx.x; e0 < total; e0 += bd * 8) {
-    C v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (e0 + u * bd < total) v[u] = sc[e0 + u * bd];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * bd;
-      if (e < total) buf[(e >> logN1) * rs + swz<SW>(e & (N1 - 1))] = v[u];
-    }
-  }
-  __syncthreads();
-  const Real* H = static_cast<const Real*>(a.H) + (long long)filt * a.M + (long long)pos0 * N1;
-  fft_rows_filter<C, SW>(buf, B2, rs, logN1, tw, [H, N1](int row) { return H + (long long)row * N1; });
-  for (int e = threadIdx.x; e < total; e += bd) sc[e] = buf[(e >> logN1) * rs + swz<SW>(e & (N1 - 1))];
-}
-
-// ---------------------------------------------------------------- k_f3
-template <typename Real, int NS, int OUT, int LG2>
-__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a) {
-  typedef typename CxT<Real>::type C;
-  constexpr int ELOG = sizeof(Real) == 4 ? 12 : 11;
-  const int logN2 = LG2 ? LG2 : a.logN2;
-  const int logB1 = LG2 ? ELOG - LG2 : a.logB1;
-  const int N2 = 1 << logN2, B1 = 1 << logB1;
-  const int tl = blockIdx.y;
-  const Tile* T = a.tiles + a.tile0 + tl;
-  if (skip_tile(a, T)) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int SW = LG2 ? lay_sw(sizeof(C), LG2, true) : (sizeof(C) == 16 ? 0 : 1);
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  const int rs = lay_rs(sizeof(C), logN2, true);
-  C* tw = buf + B1 * rs;
-  const int logM = a.logN1 + logN2, logL = split_log(logM);
-  C* tlo = tw + N2;
-  C* thi = tlo + (1 << logL);
-  const C* twM = static_cast<const C*>(a.tw);
-  build_pass_twiddles(tw, logN2, twM, a.N1);
-  build_split_twiddles(tlo, thi, twM, logM, logL);
-  __syncthreads();
-  LaneView<Real> L[2];
-  L[0] = lane_view<Real, IN_MAPX, OUT>(a, T->l[0]);
-  L[1] = lane_view<Real, IN_MAPX, OUT>(a, T->l[1]);
-  const int n1_0 = blockIdx.x * B1;
-  const int total = B1 << logN2;
-  constexpr int bd = OP_THREADS;
-  const C* sc = static_cast<const C*>(a.scratch) + (long long)tl * a.M;
-  const int mask = a.M - 1;
-  for (int e0 = threadIdx.x; e0 < total; e0 += bd * 8) {
-    C v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * bd;
-      if (e < total) v[u] = sc[(long long)(e >> logB1) * a.N1 + n1_0 + (e & (B1 - 1))];
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * bd;
-      if (e < total) {
-        const int n1 = n1_0 + (e & (B1 - 1)), pos = e >> logB1;
-        const C w = split_twiddle(tlo, thi, twM, (n1 * brev_n(pos, logN2)) & mask, logL);
-        buf[(e & (B1 - 1)) * rs + swz<SW>(pos)] = cmulc(v[u], w);
-      }
-    }
-  }
-  __syncthreads();
-  fft_rows<C, true, SW>(buf, B1, rs, logN2, tw);
-  constexpr int U = OUT == OUT_MAP ? 4 : 8;
-  for (int e0 = threadIdx.x; e0 < total; e0 += bd * U) {
-    int nn[U];
-    bool ok[2][U];
-    Real val[2][U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * bd;
-      const int j = e & (B1 - 1), n2 = e >> logB1;
-      nn[u] = n1_0 + j + (n2 << a.logN1);
-      C z;
-      z.x = z.y = 0;
-      if (e < total) z = buf[j * rs + swz<SW>(n2)];
-      val[0][u] = z.x;
-      val[1][u] = z.y;
-#pragma unroll
-      for (int l = 0; l < 2; ++l) ok[l][u] = e < total && in_range(nn[u], L[l].out_lo, L[l].out_hi);
-    }
-    if (OUT == OUT_TOD) {
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int l = 0; l < 2; ++l)
-          if (ok[l][u]) static_cast<Real*>(L[l].out)[nn[u]] = val[l][u];  // float and float64 only
-    } else if constexpr (std::is_same<Real, df64>::value && polarised(NS)) {
-      // double-float: round the value to float64 once and weight it with the
-      // float64 (cos, sin) pair (5 float64 operations per sample, not 9)
-      int pp[2][U], qq[2][U];
-      double2 cs[2][U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int l = 0; l < 2; ++l) {
-          pp[l][u] = ok[l][u] ? __ldg(L[l].pix + nn[u]) : -1;
-          if constexpr (NS == NS_MR) qq[l][u] = ok[l][u] ? __ldg(L[l].pq + nn[u]) : -1;
-          else qq[l][u] = pp[l][u];
-          cs[l][u] = ok[l][u] ? L[l].cs[nn[u]] : make_double2(0.0, 0.0);
-        }
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int l = 0; l < 2; ++l) {
-          if (pp[l][u] < 0) continue;
-          double* y = static_cast<double*>(L[l].out);
-          const double v = to_double(val[l][u]);
-          atomicAdd(y + 4LL * pp[l][u], v);
-          atomicAdd(y + 4LL * qq[l][u] + 1, v * cs[l][u].x);
-          atomicAdd(y + 4LL * qq[l][u] + 2, v * cs[l][u].y);
-        }
-    } else {
-      int pp[2][U], qq[2][U];
-      Real cc[2][U], ss[2][U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int l = 0; l < 2; ++l) {
-          load_pointing<Real, NS>(L[l], nn[u], ok[l][u], pp[l][u], cc[l][u], ss[l][u]);
-          if constexpr (NS == NS_MR) qq[l][u] = ok[l][u] ? __ldg(L[l].pq + nn[u]) : -1;
-        }
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int l = 0; l < 2; ++l) {
-          if (pp[l][u] < 0) continue;
-          Real c = cc[l][u], sn = ss[l][u];
-          if (polarised(NS)) finish_angle<Real>(c, sn);
-          if constexpr (NS == NS_MR)
-            scatter_mr<Real>(static_cast<typename OutT<Real>::type*>(L[l].out), pp[l][u], qq[l][u], val[l][u], c, sn);
-          else
-            scatter<Real, NS>(static_cast<typename OutT<Real>::type*>(L[l].out), pp[l][u], val[l][u], c, sn);
-        }
-    }
-  }
-}
-
-}  // namespace
 
 // Tiles are processed in n_chunks launches of (nearly) equal size, at most
 // tiles_per_chunk each, so no launch is left with a small tail of work.
@@ -573,257 +41,10 @@ void chunking(const Plan* p, int& n_chunks, int& per_chunk, int n_tiles) {
   per_chunk = n_chunks ? (n_tiles + n_chunks - 1) / n_chunks : 0;
 }
 
-namespace {
 
-template <typename Real>
-inline int elems_per_cta() {
-  return sizeof(Real) == 4 ? 4096 : 2048;
+static const OpImpl& impl_for(int prec) {
+  return prec == OPP_DF64 ? op_impl_df64() : prec == OPP_F64 ? op_impl_f64() : op_impl_f32();
 }
-
-template <typename Real>
-void geometry(const Plan* p, int& B1, int& B2) {
-  const int E = elems_per_cta<Real>();
-  B1 = E / p->N2;
-  if (B1 < 1) B1 = 1;
-  if (B1 > p->N1) B1 = p->N1;
-  B2 = E / p->N1;
-  if (B2 < 1) B2 = 1;
-  if (B2 > p->N2) B2 = p->N2;
-}
-
-template <typename Real>
-size_t smem_f13(const Plan* p) {
-  int B1, B2;
-  geometry<Real>(p, B1, B2);
-  typedef typename CxT<Real>::type C;
-  return (size_t)(B1 * lay_rs(sizeof(C), p->logN2, true) + p->N2 + split_entries(sizeof(C), p->logN1 + p->logN2)) *
-         sizeof(C);
-}
-template <typename Real>
-size_t smem_f2(const Plan* p) {
-  int B1, B2;
-  geometry<Real>(p, B1, B2);
-  return (size_t)(B2 * lay_rs(sizeof(typename CxT<Real>::type), p->logN1, false) + p->N1) *
-         sizeof(typename CxT<Real>::type);
-}
-
-typedef void (*OpKernel)(OpArgs);
-
-// Raise a kernel's dynamic shared-memory limit when a plan needs more than it
-// was last given (once per kernel instance and size; host-side bookkeeping).
-cudaError_t set_smem(OpKernel kernel, size_t bytes) {
-  static std::mutex mu;
-  static std::vector<std::pair<const void*, size_t>> done;
-  std::lock_guard<std::mutex> lk(mu);
-  for (auto& d : done)
-    if (d.first == (const void*)kernel) {
-      if (d.second >= bytes) return cudaSuccess;
-      d.second = bytes;
-      return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    }
-  done.push_back({(const void*)kernel, bytes});
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-// The three operator kernels for a plan: instances with compile-time FFT
-// geometry for the common sizes, the generic instances otherwise.
-struct OpKernels {
-  OpKernel f1, f2, f3;
-};
-
-template <typename Real, int NS, int IN, int OUT>
-OpKernels pick_kernels(const Plan* p) {
-  OpKernels k;
-  switch (p->logN2) {
-    case 7: k.f1 = k_f1<Real, NS, IN, 7>; k.f3 = k_f3<Real, NS, OUT, 7>; break;
-    case 8: k.f1 = k_f1<Real, NS, IN, 8>; k.f3 = k_f3<Real, NS, OUT, 8>; break;
-    case 9: k.f1 = k_f1<Real, NS, IN, 9>; k.f3 = k_f3<Real, NS, OUT, 9>; break;
-    case 10: k.f1 = k_f1<Real, NS, IN, 10>; k.f3 = k_f3<Real, NS, OUT, 10>; break;
-    default: k.f1 = k_f1<Real, NS, IN, 0>; k.f3 = k_f3<Real, NS, OUT, 0>; break;
-  }
-  switch (p->logN1) {
-    case 6: k.f2 = k_f2<Real, 6>; break;
-    case 7: k.f2 = k_f2<Real, 7>; break;
-    case 8: k.f2 = k_f2<Real, 8>; break;
-    case 9: k.f2 = k_f2<Real, 9>; break;
-    case 10: k.f2 = k_f2<Real, 10>; break;
-    default: k.f2 = k_f2<Real, 0>; break;
-  }
-  return k;
-}
-
-template <typename Real, int NS, int IN, int OUT>
-madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride, long long out_stride,
-                         int n_rhs, const int* skip, cudaStream_t s, cudaEvent_t* ev = nullptr, int reps = 1,
-                         const TileSet* ts = nullptr, int skip_stride = 0) {
-  OpArgs a;
-  a.M = p->M;
-  a.N1 = p->N1;
-  a.N2 = p->N2;
-  a.logN1 = p->logN1;
-  a.logN2 = p->logN2;
-  geometry<Real>(p, a.B1, a.B2);
-  a.logB1 = ilog2((unsigned)a.B1);
-  a.pix = p->pix_obs;
-  a.psi = p->psi;
-  a.cs64 = p->cs64;
-  a.csdf = p->csdf;
-  a.pw = p->pw;
-  a.pixq = p->pix_obs_pol;
-  a.scratch = p->scratch;
-  constexpr bool DF = std::is_same<Real, df64>::value;
-  a.H = DF ? (const void*)p->Hdf : sizeof(Real) == 8 ? (const void*)p->H64 : (const void*)p->H32;
-  a.tw = DF ? (const void*)p->twdf : sizeof(Real) == 8 ? (const void*)p->tw64 : (const void*)p->tw32;
-  a.skip = skip;
-  a.skip_stride = ts ? skip_stride : 0;
-  a.tiles = ts ? ts->tiles : p->tiles;
-  const int n_tiles = ts ? ts->n_tiles : p->n_tiles;
-  const size_t sm13 = smem_f13<Real>(p), sm2 = smem_f2<Real>(p);
-  const OpKernels K = pick_kernels<Real, NS, IN, OUT>(p);
-  // n_rhs == 0 only sets the kernels' attributes, so it can precede a capture
-  MM_CUDA(set_smem(K.f1, sm13));
-  MM_CUDA(set_smem(K.f3, sm13));
-  MM_CUDA(set_smem(K.f2, sm2));
-  int n_chunks, per_chunk;
-  chunking(p, n_chunks, per_chunk, n_tiles);
-  // several chunks: alternate two streams (own scratch slot each) so chunks overlap
-  const bool pipe = !ev && n_rhs > 0 && n_chunks > 1 && p->op_stream[0] && p->scratch_slots > 1;
-  const size_t slot_bytes = (size_t)p->tiles_per_chunk * p->M * sizeof(double2);
-  if (pipe) {
-    MM_CUDA(cudaEventRecord(p->op_fork, s));
-    for (int i = 0; i < 2; ++i) MM_CUDA(cudaStreamWaitEvent(p->op_stream[i], p->op_fork, 0));
-  }
-  int ei = 0, chunk = 0;
-  for (int rep = 0; rep < reps; ++rep) {
-    for (int r = 0; r < n_rhs; ++r) {
-      a.in = static_cast<const char*>(in) + (size_t)r * in_stride *
-                                                (IN == IN_TODF ? sizeof(float) : sizeof(Real));
-      a.out = static_cast<char*>(out) + (size_t)r * out_stride * sizeof(typename OutT<Real>::type);
-      // a tile set names each lane's right-hand side, with per-rhs strides;
-      // otherwise the plan's tiles are replayed once per right-hand side
-      a.in_stride = ts ? in_stride : 0;
-      a.out_stride = ts ? out_stride : 0;
-      for (int t0 = 0; t0 < n_tiles; t0 += per_chunk) {
-        const int nt = (n_tiles - t0) < per_chunk ? (n_tiles - t0) : per_chunk;
-        a.tile0 = t0;
-        const cudaStream_t cs = pipe ? p->op_stream[chunk & 1] : s;
-        a.scratch = static_cast<char*>(p->scratch) + (pipe ? (size_t)(chunk & 1) * slot_bytes : 0);
-        ++chunk;
-        dim3 g13(p->N1 / a.B1, nt), g2(p->N2 / a.B2, nt);
-        if (ev) cudaEventRecord(ev[ei++], s);
-        K.f1<<<g13, OP_THREADS, sm13, cs>>>(a);
-        if (ev) cudaEventRecord(ev[ei++], s);
-        K.f2<<<g2, OP_THREADS, sm2, cs>>>(a);
-        if (ev) cudaEventRecord(ev[ei++], s);
-        K.f3<<<g13, OP_THREADS, sm13, cs>>>(a);
-        if (ev) cudaEventRecord(ev[ei++], s);
-      }
-    }
-  }
-  if (pipe) {
-    for (int i = 0; i < 2; ++i) {
-      MM_CUDA(cudaEventRecord(p->op_join[i], p->op_stream[i]));
-      MM_CUDA(cudaStreamWaitEvent(s, p->op_join[i], 0));
-    }
-  }
-  count_launches(3LL * n_chunks * n_rhs * reps);
-  MM_CUDA(cudaGetLastError());
-  return MADMAP_OK;
-}
-
-template <typename Real, int NS>
-madmap_status dispatch_io(Plan* p, int in_mode, int out_mode, const void* in, void* out, long long is,
-                          long long os, int n_rhs, const int* skip, cudaStream_t s) {
-  if (in_mode == IN_MAP && out_mode == OUT_MAP)
-    return launch_all<Real, NS, IN_MAPX, OUT_MAP>(p, in, out, is, os, n_rhs, skip, s);
-  if (in_mode == IN_TOD && out_mode == OUT_MAP)
-    return launch_all<Real, NS, IN_TODF, OUT_MAP>(p, in, out, is, os, n_rhs, skip, s);
-  if (in_mode == IN_TOD_REAL && out_mode == OUT_TOD)  // no pointing: the T instance serves every layout
-    return launch_all<Real, 1, IN_TODR, OUT_TOD>(p, in, out, is, os, n_rhs, skip, s);
-  if (in_mode == IN_MAP && out_mode == OUT_TOD)
-    return launch_all<Real, NS, IN_MAPX, OUT_TOD>(p, in, out, is, os, n_rhs, skip, s);
-  set_error("unsupported operator mode");
-  return MADMAP_ERR_INTERNAL;
-}
-
-// double-float: map or float timestream in, float64 map out
-template <int NS>
-madmap_status dispatch_df(Plan* p, int in_mode, int out_mode, const void* in, void* out, long long is, long long os,
-                          int n_rhs, const int* skip, cudaStream_t s) {
-  if (in_mode == IN_MAP && out_mode == OUT_MAP)
-    return launch_all<df64, NS, IN_MAPX, OUT_MAP>(p, in, out, is, os, n_rhs, skip, s);
-  if (in_mode == IN_TOD && out_mode == OUT_MAP)
-    return launch_all<df64, NS, IN_TODF, OUT_MAP>(p, in, out, is, os, n_rhs, skip, s);
-  set_error("unsupported double-float operator mode");
-  return MADMAP_ERR_INTERNAL;
-}
-
-template <typename Real, int NS>
-madmap_status time_impl(Plan* p, const void* in, void* out, int reps, double ms[4], cudaStream_t s) {
-  int n_chunks, per_chunk;
-  chunking(p, n_chunks, per_chunk);
-  const int n_ev = reps * n_chunks * 4;
-  std::vector<cudaEvent_t> ev(n_ev, nullptr);
-  madmap_status st = MADMAP_OK;
-  for (int i = 0; i < n_ev && st == MADMAP_OK; ++i)
-    if (cudaEventCreate(&ev[i]) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "cudaEventCreate");
-  if (st == MADMAP_OK) {
-    const long long nv = (long long)std::max(1, p->n_obs) * p->ns_pad;
-    for (int rep = 0; rep < reps && st == MADMAP_OK; ++rep) {
-      if (cudaMemsetAsync(out, 0, sizeof(typename OutT<Real>::type) * nv, s) != cudaSuccess)
-        st = cuda_fail(cudaGetLastError(), "memset");
-      if (st == MADMAP_OK)
-        st = launch_all<Real, NS, IN_MAPX, OUT_MAP>(p, in, out, 0, 0, 1, nullptr, s, ev.data() + rep * n_chunks * 4, 1);
-    }
-  }
-  if (st == MADMAP_OK && cudaStreamSynchronize(s) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "sync");
-  // whole applications as the solver launches them (chunks overlapped)
-  cudaEvent_t a0 = nullptr, a1 = nullptr;
-  if (st == MADMAP_OK && (cudaEventCreate(&a0) != cudaSuccess || cudaEventCreate(&a1) != cudaSuccess))
-    st = cuda_fail(cudaGetLastError(), "cudaEventCreate");
-  if (st == MADMAP_OK) {
-    const long long nv = (long long)std::max(1, p->n_obs) * p->ns_pad;
-    cudaEventRecord(a0, s);
-    for (int rep = 0; rep < reps && st == MADMAP_OK; ++rep) {
-      if (cudaMemsetAsync(out, 0, sizeof(typename OutT<Real>::type) * nv, s) != cudaSuccess)
-        st = cuda_fail(cudaGetLastError(), "memset");
-      if (st == MADMAP_OK) st = launch_all<Real, NS, IN_MAPX, OUT_MAP>(p, in, out, 0, 0, 1, nullptr, s);
-    }
-    cudaEventRecord(a1, s);
-    if (st == MADMAP_OK && cudaStreamSynchronize(s) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "sync");
-    float t = 0.f;
-    if (st == MADMAP_OK) cudaEventElapsedTime(&t, a0, a1);
-    ms[3] = t / reps;
-  }
-  if (a0) cudaEventDestroy(a0);
-  if (a1) cudaEventDestroy(a1);
-  if (st == MADMAP_OK) {
-    ms[0] = ms[1] = ms[2] = 0.0;
-    for (int c = 0; c < reps * n_chunks; ++c)
-      for (int k = 0; k < 3; ++k) {
-        float t = 0.f;
-        cudaEventElapsedTime(&t, ev[c * 4 + k], ev[c * 4 + k + 1]);
-        ms[k] += t;
-      }
-    for (int k = 0; k < 3; ++k) ms[k] /= (double)(reps * n_chunks);
-  }
-  for (cudaEvent_t e : ev)
-    if (e) cudaEventDestroy(e);
-  return st;
-}
-
-template <typename Real, int NS>
-madmap_status dispatch_set(Plan* p, int in_mode, int out_mode, const void* in, void* out, long long is,
-                           long long os, const int* skip, int ss, cudaStream_t s, const TileSet* ts) {
-  if (in_mode == IN_MAP && out_mode == OUT_MAP)
-    return launch_all<Real, NS, IN_MAPX, OUT_MAP>(p, in, out, is, os, 1, skip, s, nullptr, 1, ts, ss);
-  if (in_mode == IN_TOD && out_mode == OUT_MAP)
-    return launch_all<Real, NS, IN_TODF, OUT_MAP>(p, in, out, is, os, 1, skip, s, nullptr, 1, ts, ss);
-  set_error("unsupported batched operator mode");
-  return MADMAP_ERR_INTERNAL;
-}
-
-}  // namespace
 
 // Operator over a tile set whose lanes name their right-hand side (maps and
 // timestreams strided by in_stride / out_stride elements per rhs).
@@ -831,13 +52,7 @@ madmap_status op_launch_set(Plan* p, int prec, int in_mode, int out_mode, const 
                             long long in_stride, long long out_stride, const int* skip, int skip_stride,
                             const TileSet* ts, cudaStream_t s) {
   if (ts->n_tiles == 0) return MADMAP_OK;
-  const int ss = skip_stride;
-  const int k = layout(p);
-#define MM_SET(R, NSV) dispatch_set<R, NSV>(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, ss, s, ts)
-  if (prec == OPP_DF64) return k == 1 ? MM_SET(df64, 1) : k == 3 ? MM_SET(df64, 3) : MM_SET(df64, NS_MR);
-  if (prec == OPP_F64) return k == 1 ? MM_SET(double, 1) : k == 3 ? MM_SET(double, 3) : MM_SET(double, NS_MR);
-  return k == 1 ? MM_SET(float, 1) : k == 3 ? MM_SET(float, 3) : MM_SET(float, NS_MR);
-#undef MM_SET
+  return impl_for(prec).launch_set(p, in_mode, out_mode, in, out, in_stride, out_stride, skip, skip_stride, ts, s);
 }
 
 static long long g_launches = 0;
@@ -848,50 +63,15 @@ madmap_status op_time(Plan* p, int prec, const void* in, void* out, int reps, do
     ms[0] = ms[1] = ms[2] = ms[3] = 0.0;
     return MADMAP_OK;
   }
-  const int k = layout(p);
-#define MM_TIME(R, NSV) time_impl<R, NSV>(p, in, out, reps, ms, s)
-  if (prec == OPP_DF64) return k == 1 ? MM_TIME(df64, 1) : k == 3 ? MM_TIME(df64, 3) : MM_TIME(df64, NS_MR);
-  if (prec == OPP_F64) return k == 1 ? MM_TIME(double, 1) : k == 3 ? MM_TIME(double, 3) : MM_TIME(double, NS_MR);
-  return k == 1 ? MM_TIME(float, 1) : k == 3 ? MM_TIME(float, 3) : MM_TIME(float, NS_MR);
-#undef MM_TIME
+  return impl_for(prec).time(p, in, out, reps, ms, s);
 }
 
-// Resident CTAs per SM of the operator kernels (the least of the three) and
-// CTAs per tile of the column kernels, for wave-aligned chunk sizes.
+// The float64 kernels' occupancy stands for the double-float ones too.
 void op_occupancy(const Plan* p, int prec, int& ctas_per_sm, int& ctas_per_tile) {
-  const bool fp64 = prec != OPP_F32;
-  int b1 = 0, b2 = 0, n1 = 0, n2 = 0, n3 = 0;
-  size_t s13 = 0, s2 = 0;
-  OpKernels K;
-  if (fp64) {
-    geometry<double>(p, b1, b2);
-    s13 = smem_f13<double>(p);
-    s2 = smem_f2<double>(p);
-    K = layout(p) == 1   ? pick_kernels<double, 1, IN_MAPX, OUT_MAP>(p)
-        : layout(p) == 3 ? pick_kernels<double, 3, IN_MAPX, OUT_MAP>(p)
-                         : pick_kernels<double, NS_MR, IN_MAPX, OUT_MAP>(p);
-  } else {
-    geometry<float>(p, b1, b2);
-    s13 = smem_f13<float>(p);
-    s2 = smem_f2<float>(p);
-    K = layout(p) == 1   ? pick_kernels<float, 1, IN_MAPX, OUT_MAP>(p)
-        : layout(p) == 3 ? pick_kernels<float, 3, IN_MAPX, OUT_MAP>(p)
-                         : pick_kernels<float, NS_MR, IN_MAPX, OUT_MAP>(p);
-  }
-  set_smem(K.f1, s13);
-  set_smem(K.f2, s2);
-  set_smem(K.f3, s13);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, K.f1, OP_THREADS, s13);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, K.f2, OP_THREADS, s2);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n3, K.f3, OP_THREADS, s13);
-  cudaGetLastError();
-  ctas_per_sm = std::max(1, std::min(n1, std::min(n2, n3)));
-  ctas_per_tile = std::max(1, p->N1 / std::max(1, b1));
+  (prec == OPP_F32 ? op_impl_f32() : op_impl_f64()).occupancy(p, ctas_per_sm, ctas_per_tile);
 }
 
-size_t f1_smem_bytes(const Plan* p, int prec) {
-  return prec == OPP_DF64 ? smem_f13<df64>(p) : prec == OPP_F64 ? smem_f13<double>(p) : smem_f13<float>(p);
-}
+size_t f1_smem_bytes(const Plan* p, int prec) { return impl_for(prec).f13_smem(p); }
 
 // in_mode: IN_MAP (gather from a map), IN_TOD (float timestream, e.g. the
 // data d) or IN_TOD_REAL (timestream of the working precision).  n_rhs == 0
@@ -900,14 +80,7 @@ madmap_status op_launch(Plan* p, int prec, int in_mode, int out_mode, const void
                         long long in_stride, long long out_stride, int n_rhs, const int* skip,
                         cudaStream_t s) {
   if (p->n_tiles == 0) return MADMAP_OK;
-  const int k = layout(p);
-#define MM_DF(NSV) dispatch_df<NSV>(p, in_mode, out_mode, in, out, in_stride, out_stride, n_rhs, skip, s)
-#define MM_IO(R, NSV) dispatch_io<R, NSV>(p, in_mode, out_mode, in, out, in_stride, out_stride, n_rhs, skip, s)
-  if (prec == OPP_DF64) return k == 1 ? MM_DF(1) : k == 3 ? MM_DF(3) : MM_DF(NS_MR);
-  if (prec == OPP_F64) return k == 1 ? MM_IO(double, 1) : k == 3 ? MM_IO(double, 3) : MM_IO(double, NS_MR);
-  return k == 1 ? MM_IO(float, 1) : k == 3 ? MM_IO(float, 3) : MM_IO(float, NS_MR);
-#undef MM_DF
-#undef MM_IO
+  return impl_for(prec).launch(p, in_mode, out_mode, in, out, in_stride, out_stride, n_rhs, skip, s);
 }
 
 }  // namespace mm
@@ -1077,8 +250,7 @@ extern "C" madmap_status madmap_apply_ninv_noalloc(int32_t precision, int64_t n_
   q.tiles = reinterpret_cast<Tile*>(b + off_T);
   q.scratch = b + off_S;
   if (q.n_tiles == 0) return MADMAP_OK;
-  st = fp64 ? launch_all<double, 1, IN_TODR, OUT_TOD>(&q, y, w, 0, 0, 1, nullptr, s)
-            : launch_all<float, 1, IN_TODR, OUT_TOD>(&q, y, w, 0, 0, 1, nullptr, s);
+  st = op_launch(&q, fp64 ? OPP_F64 : OPP_F32, IN_TOD_REAL, OUT_TOD, y, w, 0, 0, 1, nullptr, s);
   // the host tables above were copied from pageable memory, which completes
   // before cudaMemcpyAsync returns, so they may go out of scope here
   return st;
