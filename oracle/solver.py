@@ -46,7 +46,9 @@ class System:
     """
 
     def __init__(self, pix, psi, n_pix, n_stokes, offsets, ivl_filter, lags,
-                 rcond_excise=1e-6, rcond_fp64=1e-2, ninv="fft", n_f=None):
+                 rcond_excise=1e-6, rcond_fp64=1e-2, ninv="fft", n_f=None, weights=None):
+        """weights (IQU, optional): (cos 2psi, sin 2psi) per sample given directly, e.g. by
+        the expansion of compressed pointing (oracle.gcp); psi is then unused."""
         self.n_s = int(n_stokes)
         self.offsets = np.asarray(offsets, dtype=np.int64)
         self.ivl_filter = np.asarray(ivl_filter, dtype=np.int64)
@@ -55,7 +57,11 @@ class System:
         self.obs2glob, self.glob2obs = _pt.observed_pixels(np.asarray(pix), int(n_pix))
         self.n_obs = int(self.obs2glob.size)
         pixl = _pt.local_pixels(np.asarray(pix), self.glob2obs)
-        self.w = _pt.weights(psi, self.n_s)
+        if weights is not None and self.n_s == 3:
+            c2, s2 = (np.asarray(v, dtype=np.float64) for v in weights)
+            self.w = np.stack([np.ones_like(c2), c2, s2], axis=1)
+        else:
+            self.w = _pt.weights(psi, self.n_s)
         lengths = np.diff(self.offsets)
         f0 = np.repeat(self.lags[self.ivl_filter, 0], lengths)     # diag of N^-1 per sample
         self._classify(pixl, f0, rcond_excise, rcond_fp64)

@@ -533,3 +533,120 @@ def test_multires_excision_drops_rows():
     assert M.excised_pol[k_pol] and M.excised[k_i]
     assert np.all(M.pi[:5] == -1) and np.all(M.pq[:5] == -1)
     assert not M.excised[:M.n_obs_i][np.arange(M.n_obs_i) != k_i].any()
+
+
+# ------------------------------------------------------------------ compressed pointing (Section 5.3)
+def _exact_expand(bore, step, det, n_per_det, width, height):
+    """The expansion in exact rational arithmetic (one sample at a time)."""
+    from fractions import Fraction as Fr
+    out = []
+    for d in range(len(det)):
+        dx, dy, cd, sd = (Fr(float(v)) for v in det[d])
+        for j in range(n_per_det):
+            u, r = divmod(j, step)
+            f = Fr(r, step)
+            q = [Fr(float(bore[u][k])) + f * (Fr(float(bore[u + 1][k])) - Fr(float(bore[u][k]))) for k in range(4)]
+            x, y, c, s = q
+            X, Y = x + c * dx - s * dy, y + s * dx + c * dy
+            ix, iy = X.numerator // X.denominator, Y.numerator // Y.denominator
+            C, S = c * cd - s * sd, s * cd + c * sd
+            n = C * C + S * S
+            ok = 0 <= ix < width and 0 <= iy < height and n > 0
+            out.append((iy * width + ix if ok else -1, (C * C - S * S) / n if n else None,
+                        2 * C * S / n if n else None))
+    return out
+
+
+def test_gcp_dyadic_cases_equal_rational_arithmetic():
+    """Nodes, offsets and orientations chosen so every float32 step is exact: the pixels
+    and weights equal those of exact rational arithmetic (interpolation from node u to
+    u + 1, the rotation's signs, the pixel's row-major order, the double angle)."""
+    from oracle.gcp import expand
+    rng = np.random.default_rng(3)
+    width, height, step, n_per = 7, 5, 4, 37
+    n_bore = (n_per - 1) // step + 2
+    bore = np.zeros((n_bore, 4), dtype=np.float32)
+    bore[:, 0] = rng.integers(-4, 64, n_bore) / 8.0
+    bore[:, 1] = rng.integers(-4, 44, n_bore) / 8.0
+    rots = np.array([(1, 0), (0, 1), (-1, 0), (0, -1), (0.5, 0.5), (0.75, -0.25)], dtype=np.float32)
+    bore[:, 2:] = rots[rng.integers(0, len(rots), n_bore)]
+    det = np.array([[0.0, 0.0, 1.0, 0.0], [0.25, -0.5, 0.0, 1.0], [-0.375, 0.125, 0.5, -0.5]], dtype=np.float32)
+    pix, c2, s2 = expand(bore, step, det, n_per, width, height)
+    exact = _exact_expand(bore, step, det, n_per, width, height)
+    assert np.array_equal(pix, np.array([e[0] for e in exact]))
+    assert (pix >= 0).sum() > 60 and (pix < 0).sum() > 0
+    for t, (p, ce, se) in enumerate(exact):
+        if ce is not None:
+            assert abs(float(c2[t]) - float(ce)) <= 2e-7 and abs(float(s2[t]) - float(se)) <= 2e-7
+
+
+def test_gcp_weights_are_the_double_angle_of_the_summed_orientation():
+    from oracle.gcp import expand
+    rng = np.random.default_rng(4)
+    a = rng.uniform(-np.pi, np.pi, 50)
+    b = rng.uniform(-np.pi, np.pi, 3)
+    bore = np.stack([np.full(50, 3.3), np.full(50, 2.2), np.cos(a), np.sin(a)], 1).astype(np.float32)
+    det = np.stack([np.zeros(3), np.zeros(3), np.cos(b), np.sin(b)], 1).astype(np.float32)
+    pix, c2, s2 = expand(bore, 1, det, 49, 8, 8)        # step 1: every sample sits on a node
+    ang = (a[None, :49] + b[:, None]).reshape(-1)
+    assert np.all(pix == 2 * 8 + 3)
+    assert np.max(np.abs(c2 - np.cos(2 * ang))) < 1e-6 and np.max(np.abs(s2 - np.sin(2 * ang))) < 1e-6
+
+
+def test_gcp_pixels_follow_the_float64_position_away_from_edges():
+    """On a random smooth path the float32 expansion and the same geometry in float64
+    agree on the pixel wherever the float64 position is 1e-3 pixel or more from an edge."""
+    from oracle.gcp import expand
+    rng = np.random.default_rng(5)
+    width, step, n_per = 32, 8, 3000
+    n_bore = (n_per - 1) // step + 2
+    t = np.arange(n_bore)
+    ang = 0.01 * t + 0.3
+    bore = np.stack([16 + 12 * np.sin(0.013 * t), 16 + 12 * np.cos(0.017 * t), np.cos(ang), np.sin(ang)], 1)
+    bore = bore.astype(np.float32)
+    det = np.array([[0.4, -0.3, 1.0, 0.0], [-0.45, 0.2, 0.0, 1.0]], dtype=np.float32)
+    pix, _, _ = expand(bore, step, det, n_per, width, width)
+    b64 = bore.astype(np.float64)
+    for d in range(2):
+        j = np.arange(n_per)
+        u, f = j // step, (j % step) / step
+        q = b64[u] + f[:, None] * (b64[u + 1] - b64[u])
+        X = q[:, 0] + q[:, 2] * det[d, 0] - q[:, 3] * det[d, 1]
+        Y = q[:, 1] + q[:, 3] * det[d, 0] + q[:, 2] * det[d, 1]
+        far = (np.abs(X - np.round(X)) > 1e-3) & (np.abs(Y - np.round(Y)) > 1e-3)
+        ref = np.floor(Y).astype(np.int64) * width + np.floor(X).astype(np.int64)
+        got = pix[d * n_per:(d + 1) * n_per]
+        assert far.sum() > 0.9 * n_per
+        assert np.array_equal(got[far], ref[far])
+
+
+def test_gcp_flags_outside_and_degenerate_orientation():
+    from oracle.gcp import expand
+    bore = np.array([[-0.5, 1.5, 1, 0], [0.5, 1.5, 1, 0], [3.5, 1.5, 0, 0], [3.5, 3.5, 0, 0]], dtype=np.float32)
+    det = np.array([[0, 0, 1, 0]], dtype=np.float32)
+    pix, c2, s2 = expand(bore, 1, det, 3, 4, 3)
+    # sample 0: x = -0.5 (outside); 1: inside, pixel (1, 0); 2: orientation (0, 0) -> flagged
+    assert list(pix) == [-1, 1 * 4 + 0, -1]
+    assert c2[1] == 1.0 and s2[1] == 0.0
+    pix_t, c_t, _ = expand(bore, 1, det, 3, 4, 3, polarised=False)
+    assert c_t is None and list(pix_t) == [-1, 4, 1 * 4 + 3]
+
+
+def test_gcp_system_matches_angle_system():
+    """The oracle System fed the expansion's weights equals the System fed the angles they
+    come from (the weights argument is the same A), up to the float32 weights' length
+    (c^2 + s^2 = 1 within a few 1e-7)."""
+    from oracle.gcp import expand
+    from synth.boresight import make_boresight_problem
+    from tests.helpers import lags_for
+    from oracle.solver import System
+    p = make_boresight_problem("gcp", 21, 8, 2, 700, 8, 3, 10, noise=(1.0, 3.0, 1.5),
+                               interval_lengths=lambda rng, n: [300, 400])
+    pix, c2, s2 = expand(p.boresight, p.bore_step, p.det, p.samples_per_det, p.width, p.height)
+    lags = lags_for(p)
+    S1 = System(pix, None, p.n_pix, 3, p.interval_offsets, p.interval_filter, lags, weights=(c2, s2))
+    psi = 0.5 * np.arctan2(s2.astype(np.float64), c2.astype(np.float64))
+    S2 = System(pix, psi, p.n_pix, 3, p.interval_offsets, p.interval_filter, lags)
+    x = np.random.default_rng(0).standard_normal((S1.n_obs, 3))
+    assert rel_rms(S1.H(x), S2.H(x)) < 1e-6
+    assert S1.n_obs > 40 and not S1.excised.all()
