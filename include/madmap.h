@@ -96,6 +96,30 @@ typedef struct {
   const int32_t* pix_pol;           /* device [n_samples]: Q/U pixel of each sample in [0, n_pix_pol),
                                        or -1 (flagged: the sample's row is zero) */
   int32_t n_pix_pol;                /* global Q/U pixel count (> 0 when pix_pol is set) */
+  /* Pointing expanded on the fly from compressed boresight pointing
+   * (Section 5.3).  When boresight is set, pix, psi and pix_pol must be NULL,
+   * and the plan stores no per-sample pointing: every pass over the samples
+   * (the operator's gather and scatter, the preconditioner, the backward pass)
+   * recomputes each sample's pixel and weights.  Sample t = d * n_per_det + j
+   * of detector d (n_per_det = n_samples / n_det): with u = j / bore_step and
+   * f = (j mod bore_step) / bore_step, each node quantity q is interpolated as
+   * q_u + f (q_{u+1} - q_u); the detector sits at X = x + (c dx - s dy),
+   * Y = y + (s dx + c dy) and observes pixel floor(Y) * grid_width + floor(X)
+   * when 0 <= X < grid_width and 0 <= Y < grid_height (else the sample is
+   * flagged).  IQU weights: (C, S) = (c cd - s sd, s cd + c sd), n = C^2 + S^2,
+   * cos 2psi = (C^2 - S^2) / n, sin 2psi = 2 C S / n; n = 0 flags the sample.
+   * Every step is one float32 operation rounded to nearest, in this order
+   * (no contraction), so pixel decisions are reproducible bit for bit. */
+  const float* boresight;           /* device [n_bore][4]: node u = detector sample u * bore_step:
+                                       x, y (pixel units of the grid), cos and sin of the
+                                       boresight orientation; finite */
+  int32_t n_bore;                   /* >= (n_per_det - 1) / bore_step + 2 */
+  int32_t bore_step;                /* detector samples per node interval, >= 1 */
+  const float* det_pointing;        /* host [n_det][4]: dx, dy (focal-plane offset, pixel units),
+                                       cos and sin of the polariser orientation; finite */
+  int32_t n_det;                    /* detectors (>= 1; must divide n_samples); no interval
+                                       may span two detectors */
+  int32_t grid_width, grid_height;  /* flat pixel grid; n_pix must equal their product */
 } madmap_plan_desc;
 
 typedef struct {

@@ -294,11 +294,55 @@ class Plan:
                 d.pix_pol = _dev_ptr(pix_pol, torch.int32, "pix_pol")
         self._keep = (off, filt, lags)
         self.multires = pix_pol is not None
+        self._create(d, n_t, stream)
+
+    def _create(self, d, n_t, stream):
         self._h = madmap_plan_create(d, stream)
         self.n_stokes = d.n_stokes
         self.n_samples = n_t
         self.stats = madmap_plan_get_stats(self._h)
         self.n_obs = self.stats["n_obs"]
+
+    @classmethod
+    def from_boresight(cls, boresight, bore_step, det_pointing, samples_per_det, width, height, polarised,
+                       interval_offsets, interval_filter, filter_lags, rcond_excise=0.0, rcond_fp64=0.0, fft_len=0,
+                       tiles_per_chunk=0, stream=None):
+        """A plan whose pointing is expanded on the fly from compressed boresight pointing
+        (no per-sample pointing is stored).  boresight: float32 CUDA tensor [n_bore, 4]
+        (x, y, cos, sin per node, one node every bore_step detector samples);
+        det_pointing: host [n_det, 4] (dx, dy, cos, sin); the grid is width x height pixels."""
+        torch = _torch()
+        self = cls.__new__(cls)
+        self._h = None
+        off = np.ascontiguousarray(interval_offsets, dtype=np.int64)
+        filt = np.ascontiguousarray(interval_filter, dtype=np.int32)
+        lags = np.ascontiguousarray(np.atleast_2d(filter_lags), dtype=np.float64)
+        det = np.ascontiguousarray(det_pointing, dtype=np.float32).reshape(-1, 4)
+        if boresight.dim() != 2 or boresight.shape[1] != 4:
+            raise ValueError("boresight must be [n_bore, 4]")
+        n_t = int(det.shape[0]) * int(samples_per_det)
+        d = _lib.madmap_plan_desc()
+        d.n_stokes = 3 if polarised else 1
+        d.n_samples = n_t
+        d.n_pix = int(width) * int(height)
+        d.n_intervals = int(filt.shape[0])
+        d.interval_offsets = off.ctypes.data
+        d.interval_filter = filt.ctypes.data if filt.size else None
+        d.n_filters, d.n_lags = int(lags.shape[0]), int(lags.shape[1])
+        d.filter_lags = lags.ctypes.data
+        d.rcond_excise, d.rcond_fp64 = float(rcond_excise), float(rcond_fp64)
+        d.fft_len, d.tiles_per_chunk = int(fft_len), int(tiles_per_chunk)
+        bore = boresight if boresight.numel() else torch.zeros((1, 4), dtype=torch.float32, device="cuda")
+        d.boresight = _dev_ptr(bore, torch.float32, "boresight")
+        d.n_bore = int(boresight.shape[0])
+        d.bore_step = int(bore_step)
+        d.det_pointing = det.ctypes.data
+        d.n_det = int(det.shape[0])
+        d.grid_width, d.grid_height = int(width), int(height)
+        self._keep = (off, filt, lags, det)
+        self.multires = False
+        self._create(d, n_t, stream)
+        return self
 
     def close(self):
         if self._h is not None:

@@ -37,7 +37,10 @@ class madmap_plan_desc(C.Structure):
                 ("interval_offsets", C.c_void_p), ("interval_filter", C.c_void_p),
                 ("n_filters", C.c_int32), ("n_lags", C.c_int32), ("filter_lags", C.c_void_p),
                 ("rcond_excise", C.c_double), ("rcond_fp64", C.c_double), ("fft_len", C.c_int32),
-                ("tiles_per_chunk", C.c_int32), ("pix_pol", C.c_void_p), ("n_pix_pol", C.c_int32)]
+                ("tiles_per_chunk", C.c_int32), ("pix_pol", C.c_void_p), ("n_pix_pol", C.c_int32),
+                ("boresight", C.c_void_p), ("n_bore", C.c_int32), ("bore_step", C.c_int32),
+                ("det_pointing", C.c_void_p), ("n_det", C.c_int32), ("grid_width", C.c_int32),
+                ("grid_height", C.c_int32)]
 
 
 class madmap_plan_stats(C.Structure):

@@ -99,6 +99,58 @@ __device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b;
 __device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b; }
 __device__ __forceinline__ df64& operator*=(df64& a, df64 b) { return a = a * b; }
 
+// ---------------------------------------------------------------- compressed pointing
+// Section 5.3: the pointing of detector sample j (detector pointing dp =
+// (dx, dy, cd, sd)) expanded from the boresight nodes, in the float32
+// operation order stated with madmap_plan_desc (no contraction, so the pixel
+// decisions are reproducible).  Returns the global pixel or -1; c2, s2 get
+// cos 2psi and sin 2psi when `pol`.
+__device__ __forceinline__ int expand_pointing(const float4* __restrict__ bore, int step, int j, float4 dp, int W,
+                                               int H, bool pol, float& c2, float& s2) {
+  const int u = j / step;
+  const float f = __fdiv_rn((float)(j - u * step), (float)step);
+  const float4 a = __ldg(bore + u), b = __ldg(bore + u + 1);
+  const float x = __fadd_rn(a.x, __fmul_rn(f, __fsub_rn(b.x, a.x)));
+  const float y = __fadd_rn(a.y, __fmul_rn(f, __fsub_rn(b.y, a.y)));
+  const float c = __fadd_rn(a.z, __fmul_rn(f, __fsub_rn(b.z, a.z)));
+  const float s = __fadd_rn(a.w, __fmul_rn(f, __fsub_rn(b.w, a.w)));
+  const float X = __fadd_rn(x, __fsub_rn(__fmul_rn(c, dp.x), __fmul_rn(s, dp.y)));
+  const float Y = __fadd_rn(y, __fadd_rn(__fmul_rn(s, dp.x), __fmul_rn(c, dp.y)));
+  const float fx = floorf(X), fy = floorf(Y);
+  bool ok = fx >= 0.f && fx < (float)W && fy >= 0.f && fy < (float)H;
+  c2 = s2 = 0.f;
+  if (pol) {
+    const float C = __fsub_rn(__fmul_rn(c, dp.z), __fmul_rn(s, dp.w));
+    const float S = __fadd_rn(__fmul_rn(s, dp.z), __fmul_rn(c, dp.w));
+    const float cc = __fmul_rn(C, C), ss = __fmul_rn(S, S);
+    const float n = __fadd_rn(cc, ss);
+    const float cs = __fmul_rn(C, S);
+    ok = ok && n > 0.f;
+    if (ok) {
+      c2 = __fdiv_rn(__fsub_rn(cc, ss), n);
+      s2 = __fdiv_rn(__fadd_rn(cs, cs), n);
+    }
+  }
+  return ok ? (int)fy * W + (int)fx : -1;
+}
+
+// The compressed pointing of a plan as kernel arguments (bore == NULL: the
+// plan stores per-sample pointing instead).
+struct OtfPointing {
+  const float4* bore;
+  const float4* det;
+  const int* g2o;
+  int step, n_per_det, W, H;
+};
+
+// Observed row of sample t (or -1) and its weights, from compressed pointing.
+__device__ __forceinline__ int otf_row(const OtfPointing& o, long long t, bool pol, float& c2, float& s2) {
+  const int dd = (int)(t / o.n_per_det);
+  const int g = expand_pointing(o.bore, o.step, (int)(t - (long long)dd * o.n_per_det), o.det[dd], o.W, o.H, pol, c2,
+                                s2);
+  return g >= 0 ? o.g2o[g] : -1;
+}
+
 // ---------------------------------------------------------------- plan
 struct SolveBuffers;  // solver.cu
 
@@ -145,6 +197,13 @@ struct Plan {
   int* pix_obs_pol = nullptr;      // [n_t] observed Q/U pixel or -1
   int* obs2glob_pol = nullptr;     // [n_obs_pol]
   unsigned char* excised_pol = nullptr;  // [n_obs] (slots)
+  // pointing expanded on the fly from compressed boresight pointing (no
+  // per-sample arrays: pix_obs, psi, cs64, csdf, pw stay NULL)
+  bool otf = false;
+  const float4* bore = nullptr;    // [n_bore] device copy of the nodes
+  float4* det_pt = nullptr;        // [n_det] detector offsets and orientations
+  int n_bore = 0, bore_step = 1, n_det = 0, n_per_det = 0, grid_w = 0, grid_h = 0;
+  int* g2o = nullptr;              // [n_pix] observed row of each global pixel, -1 if unobserved or excised
   void* scratch = nullptr;         // scratch_slots * tiles_per_chunk * M complex (float64 size)
   int scratch_slots = 1;           // 2 when an application has several chunks (see op_stream)
   // An application of several chunks alternates them between two streams,
@@ -170,6 +229,18 @@ struct Plan {
   int n_corr_items = 0;
   ~Plan();
 };
+
+inline OtfPointing otf_pointing(const Plan* p) {
+  OtfPointing a;
+  a.bore = p->otf ? p->bore : nullptr;
+  a.det = p->det_pt;
+  a.g2o = p->g2o;
+  a.step = p->bore_step;
+  a.n_per_det = p->n_per_det > 0 ? p->n_per_det : 1;
+  a.W = p->grid_w;
+  a.H = p->grid_h;
+  return a;
+}
 
 madmap_status dalloc(Plan* p, void** ptr, size_t bytes);
 template <typename T>

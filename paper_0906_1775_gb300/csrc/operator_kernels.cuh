@@ -42,9 +42,22 @@ enum { IN_MAPX = 0, IN_TODF = 1, IN_TODR = 2 };
 // Stokes layouts of the kernels' NS parameter: 1 = T, 3 = IQU on one
 // pixelisation, NS_MR = IQU with Q and U on a second pixelisation (Section 6;
 // each sample then carries an I pixel and a Q/U pixel of the slot layout).
+// NS_OTF_T / NS_OTF_IQU: T / IQU with the pointing expanded on the fly from
+// compressed boresight pointing (Section 5.3) instead of read per sample.
 constexpr int NS_MR = 4;
-__host__ __device__ constexpr bool polarised(int ns) { return ns >= 3; }
-inline int layout(const Plan* p) { return p->multires ? NS_MR : p->n_stokes; }
+constexpr int NS_OTF_T = 5;
+constexpr int NS_OTF_IQU = 6;
+__host__ __device__ constexpr bool polarised(int ns) { return ns == 3 || ns == NS_MR || ns == NS_OTF_IQU; }
+__host__ __device__ constexpr bool on_the_fly(int ns) { return ns == NS_OTF_T || ns == NS_OTF_IQU; }
+// the map layout's gather/scatter of a pointing mode
+__host__ __device__ constexpr int map_ns(int ns) { return ns == NS_OTF_T ? 1 : ns == NS_OTF_IQU ? 3 : ns; }
+inline int layout(const Plan* p) {
+  if (p->otf) return p->n_stokes == 1 ? NS_OTF_T : NS_OTF_IQU;
+  return p->multires ? NS_MR : p->n_stokes;
+}
+// Calls X(ns) with the compile-time pointing mode ns of `k`.
+#define MM_FOR_LAYOUT(k, X)                          \
+  ((k) == 1 ? X(1) : (k) == 3 ? X(3) : (k) == NS_MR ? X(NS_MR) : (k) == NS_OTF_T ? X(NS_OTF_T) : X(NS_OTF_IQU))
 
 struct OpArgs {
   const Tile* tiles;
@@ -56,6 +69,11 @@ struct OpArgs {
   const float4* csdf;
   const int2* pw;      // (pixel, angle bits) per sample, IQU
   const int* pixq;     // Q/U pixel per sample (multi-resolution plans)
+  // compressed pointing (on-the-fly modes)
+  const float4* bore;
+  const float4* det;
+  const int* g2o;
+  int bore_step, n_per_det, n_det, grid_w, grid_h;
   const void* in;
   long long in_stride;
   void* out;
@@ -186,6 +204,8 @@ struct LaneView {
   const int* pq;
   const void* in;
   void* out;
+  int j0;        // on-the-fly pointing: detector sample of window position 0
+  float4 dp;     // and the lane's detector offset and orientation
 };
 
 template <typename Real, int IN, int OUT>
@@ -205,6 +225,16 @@ __device__ __forceinline__ LaneView<Real> lane_view(const OpArgs& a, const Lane&
   v.csd = a.csdf + ws;
   v.pw = a.pw + ws;
   v.pq = a.pixq ? a.pixq + ws : nullptr;
+  if (a.bore) {
+    // windows never leave their interval's detector
+    long long dd = a.n_per_det > 0 ? g.lo / a.n_per_det : 0;
+    dd = dd < 0 ? 0 : (dd >= a.n_det ? a.n_det - 1 : dd);
+    v.j0 = (int)(ws - dd * a.n_per_det);
+    v.dp = __ldg(a.det + dd);
+  } else {
+    v.j0 = 0;
+    v.dp = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   if (IN == IN_TODF) v.in = static_cast<const float*>(a.in) + g.rhs * a.in_stride + ws;
   else if (IN == IN_TODR) v.in = static_cast<const Real*>(a.in) + g.rhs * a.in_stride + ws;
   else v.in = static_cast<const Real*>(a.in) + g.rhs * a.in_stride;
@@ -251,8 +281,16 @@ __device__ __forceinline__ void finish_angle(Real& c, Real& s) {}
 // operator reads pixel and angle as one 8-byte pair; the others the pixel and
 // their cached cos/sin pairs.
 template <typename Real, int NS>
-__device__ __forceinline__ void load_pointing(const LaneView<Real>& L, int n, bool ok, int& pp, Real& c, Real& s) {
-  if (polarised(NS) && std::is_same<Real, float>::value) {
+__device__ __forceinline__ void load_pointing(const OpArgs& a, const LaneView<Real>& L, int n, bool ok, int& pp,
+                                              Real& c, Real& s) {
+  if constexpr (on_the_fly(NS)) {
+    float c2 = 0.f, s2 = 0.f;
+    int g = -1;
+    if (ok) g = expand_pointing(a.bore, a.bore_step, L.j0 + n, L.dp, a.grid_w, a.grid_h, polarised(NS), c2, s2);
+    pp = g >= 0 ? __ldg(a.g2o + g) : -1;
+    c = Real(c2);
+    s = Real(s2);
+  } else if (polarised(NS) && std::is_same<Real, float>::value) {
     if (ok) {
       const int2 w = __ldg(L.pw + n);
       pp = w.x;
@@ -362,7 +400,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
-          load_pointing<Real, NS>(L[l], nn[u], ok[l][u], pp[l][u], cc[l][u], ss[l][u]);
+          load_pointing<Real, NS>(a, L[l], nn[u], ok[l][u], pp[l][u], cc[l][u], ss[l][u]);
           if constexpr (NS == NS_MR) qq[l][u] = ok[l][u] ? __ldg(L[l].pq + nn[u]) : -1;
         }
 #pragma unroll
@@ -370,12 +408,13 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
           Real c = cc[l][u], sn = ss[l][u];
-          if (polarised(NS)) finish_angle<Real>(c, sn);
+          if (polarised(NS) && !on_the_fly(NS)) finish_angle<Real>(c, sn);
           if constexpr (NS == NS_MR)
             v[l][u] = pp[l][u] >= 0 ? gather_mr<Real>(static_cast<const Real*>(L[l].in), pp[l][u], qq[l][u], c, sn)
                                     : Real(0);
           else
-            v[l][u] = pp[l][u] >= 0 ? gather<Real, NS>(static_cast<const Real*>(L[l].in), pp[l][u], c, sn) : Real(0);
+            v[l][u] = pp[l][u] >= 0 ? gather<Real, map_ns(NS)>(static_cast<const Real*>(L[l].in), pp[l][u], c, sn)
+                                    : Real(0);
         }
     }
 #pragma unroll
@@ -525,10 +564,16 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
-          pp[l][u] = ok[l][u] ? __ldg(L[l].pix + nn[u]) : -1;
+          if constexpr (on_the_fly(NS)) {
+            df64 c, sn;
+            load_pointing<Real, NS>(a, L[l], nn[u], ok[l][u], pp[l][u], c, sn);
+            cs[l][u] = make_double2(to_double(c), to_double(sn));
+          } else {
+            pp[l][u] = ok[l][u] ? __ldg(L[l].pix + nn[u]) : -1;
+            cs[l][u] = ok[l][u] ? L[l].cs[nn[u]] : make_double2(0.0, 0.0);
+          }
           if constexpr (NS == NS_MR) qq[l][u] = ok[l][u] ? __ldg(L[l].pq + nn[u]) : -1;
           else qq[l][u] = pp[l][u];
-          cs[l][u] = ok[l][u] ? L[l].cs[nn[u]] : make_double2(0.0, 0.0);
         }
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -548,7 +593,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
-          load_pointing<Real, NS>(L[l], nn[u], ok[l][u], pp[l][u], cc[l][u], ss[l][u]);
+          load_pointing<Real, NS>(a, L[l], nn[u], ok[l][u], pp[l][u], cc[l][u], ss[l][u]);
           if constexpr (NS == NS_MR) qq[l][u] = ok[l][u] ? __ldg(L[l].pq + nn[u]) : -1;
         }
 #pragma unroll
@@ -557,11 +602,11 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
         for (int l = 0; l < 2; ++l) {
           if (pp[l][u] < 0) continue;
           Real c = cc[l][u], sn = ss[l][u];
-          if (polarised(NS)) finish_angle<Real>(c, sn);
+          if (polarised(NS) && !on_the_fly(NS)) finish_angle<Real>(c, sn);
           if constexpr (NS == NS_MR)
             scatter_mr<Real>(static_cast<typename OutT<Real>::type*>(L[l].out), pp[l][u], qq[l][u], val[l][u], c, sn);
           else
-            scatter<Real, NS>(static_cast<typename OutT<Real>::type*>(L[l].out), pp[l][u], val[l][u], c, sn);
+            scatter<Real, map_ns(NS)>(static_cast<typename OutT<Real>::type*>(L[l].out), pp[l][u], val[l][u], c, sn);
         }
     }
   }
@@ -627,12 +672,20 @@ struct OpKernels {
 template <typename Real, int NS, int IN, int OUT>
 OpKernels pick_kernels(const Plan* p) {
   OpKernels k;
-  switch (p->logN2) {
-    case 7: k.f1 = k_f1<Real, NS, IN, 7>; k.f3 = k_f3<Real, NS, OUT, 7>; break;
-    case 8: k.f1 = k_f1<Real, NS, IN, 8>; k.f3 = k_f3<Real, NS, OUT, 8>; break;
-    case 9: k.f1 = k_f1<Real, NS, IN, 9>; k.f3 = k_f3<Real, NS, OUT, 9>; break;
-    case 10: k.f1 = k_f1<Real, NS, IN, 10>; k.f3 = k_f3<Real, NS, OUT, 10>; break;
-    default: k.f1 = k_f1<Real, NS, IN, 0>; k.f3 = k_f3<Real, NS, OUT, 0>; break;
+  // the multi-resolution and T on-the-fly modes keep only the generic column
+  // kernels (fewer instances to compile)
+  constexpr bool generic_only = NS == NS_MR || NS == NS_OTF_T;
+  if constexpr (generic_only) {
+    k.f1 = k_f1<Real, NS, IN, 0>;
+    k.f3 = k_f3<Real, NS, OUT, 0>;
+  } else {
+    switch (p->logN2) {
+      case 7: k.f1 = k_f1<Real, NS, IN, 7>; k.f3 = k_f3<Real, NS, OUT, 7>; break;
+      case 8: k.f1 = k_f1<Real, NS, IN, 8>; k.f3 = k_f3<Real, NS, OUT, 8>; break;
+      case 9: k.f1 = k_f1<Real, NS, IN, 9>; k.f3 = k_f3<Real, NS, OUT, 9>; break;
+      case 10: k.f1 = k_f1<Real, NS, IN, 10>; k.f3 = k_f3<Real, NS, OUT, 10>; break;
+      default: k.f1 = k_f1<Real, NS, IN, 0>; k.f3 = k_f3<Real, NS, OUT, 0>; break;
+    }
   }
   switch (p->logN1) {
     case 6: k.f2 = k_f2<Real, 6>; break;
@@ -663,6 +716,14 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
   a.csdf = p->csdf;
   a.pw = p->pw;
   a.pixq = p->pix_obs_pol;
+  a.bore = p->otf ? p->bore : nullptr;
+  a.det = p->det_pt;
+  a.g2o = p->g2o;
+  a.bore_step = p->bore_step;
+  a.n_per_det = p->n_per_det;
+  a.n_det = p->n_det;
+  a.grid_w = p->grid_w;
+  a.grid_h = p->grid_h;
   a.scratch = p->scratch;
   constexpr bool DF = std::is_same<Real, df64>::value;
   a.H = DF ? (const void*)p->Hdf : sizeof(Real) == 8 ? (const void*)p->H64 : (const void*)p->H32;
@@ -826,11 +887,11 @@ madmap_status impl_launch(Plan* p, int in_mode, int out_mode, const void* in, vo
   const int k = layout(p);
   if constexpr (std::is_same<Real, df64>::value) {
 #define MM_DF(NSV) dispatch_df<NSV>(p, in_mode, out_mode, in, out, is, os, n_rhs, skip, s)
-    return k == 1 ? MM_DF(1) : k == 3 ? MM_DF(3) : MM_DF(NS_MR);
+    return MM_FOR_LAYOUT(k, MM_DF);
 #undef MM_DF
   } else {
 #define MM_IO(NSV) dispatch_io<Real, NSV>(p, in_mode, out_mode, in, out, is, os, n_rhs, skip, s)
-    return k == 1 ? MM_IO(1) : k == 3 ? MM_IO(3) : MM_IO(NS_MR);
+    return MM_FOR_LAYOUT(k, MM_IO);
 #undef MM_IO
   }
 }
@@ -840,16 +901,16 @@ madmap_status impl_launch_set(Plan* p, int in_mode, int out_mode, const void* in
                               long long os, const int* skip, int ss, const TileSet* ts, cudaStream_t s) {
   const int k = layout(p);
 #define MM_SET(NSV) dispatch_set<Real, NSV>(p, in_mode, out_mode, in, out, is, os, skip, ss, s, ts)
-  return k == 1 ? MM_SET(1) : k == 3 ? MM_SET(3) : MM_SET(NS_MR);
+  return MM_FOR_LAYOUT(k, MM_SET);
 #undef MM_SET
 }
 
 template <typename Real>
 madmap_status impl_time(Plan* p, const void* in, void* out, int reps, double ms[4], cudaStream_t s) {
   const int k = layout(p);
-  return k == 1 ? time_impl<Real, 1>(p, in, out, reps, ms, s)
-       : k == 3 ? time_impl<Real, 3>(p, in, out, reps, ms, s)
-                : time_impl<Real, NS_MR>(p, in, out, reps, ms, s);
+#define MM_TIME(NSV) time_impl<Real, NSV>(p, in, out, reps, ms, s)
+  return MM_FOR_LAYOUT(k, MM_TIME);
+#undef MM_TIME
 }
 
 // Resident CTAs per SM of the map-to-map kernels (the least of the three) and
@@ -860,9 +921,9 @@ void impl_occupancy(const Plan* p, int& ctas_per_sm, int& ctas_per_tile) {
   geometry<Real>(p, b1, b2);
   const size_t s13 = smem_f13<Real>(p), s2 = smem_f2<Real>(p);
   const int k = layout(p);
-  const OpKernels K = k == 1   ? pick_kernels<Real, 1, IN_MAPX, OUT_MAP>(p)
-                      : k == 3 ? pick_kernels<Real, 3, IN_MAPX, OUT_MAP>(p)
-                               : pick_kernels<Real, NS_MR, IN_MAPX, OUT_MAP>(p);
+#define MM_PICK(NSV) pick_kernels<Real, NSV, IN_MAPX, OUT_MAP>(p)
+  const OpKernels K = MM_FOR_LAYOUT(k, MM_PICK);
+#undef MM_PICK
   set_smem(K.f1, s13);
   set_smem(K.f2, s2);
   set_smem(K.f3, s13);

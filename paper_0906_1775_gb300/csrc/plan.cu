@@ -257,6 +257,37 @@ __global__ void k_pix_obs(const int* pix, long long n, int n_pix, const unsigned
   }
 }
 
+// ---------------------------------------------------------------- compressed pointing
+__global__ void k_validate_bore(const float4* bore, int n_bore, int* bad) {
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_bore; u += gridDim.x * blockDim.x) {
+    const float4 b = bore[u];
+    if (!isfinite(b.x) || !isfinite(b.y) || !isfinite(b.z) || !isfinite(b.w)) atomicOr(bad, 8);
+  }
+}
+
+// Section 5.4 bits for pointing expanded on the fly (Section 5.3).
+__global__ void k_mark_bits_otf(const float4* bore, int step, const float4* det, int n_per_det, long long n, int W,
+                                int H, bool pol, unsigned* bits) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int dd = (int)(t / n_per_det);
+    float c2, s2;
+    const int g = expand_pointing(bore, step, (int)(t - (long long)dd * n_per_det), det[dd], W, H, pol, c2, s2);
+    if (g >= 0) atomicOr(bits + (g >> 5), 1u << (g & 31));
+  }
+}
+
+// observed row of every global pixel (-1: not observed)
+__global__ void k_g2o(const unsigned* bits, const int* prefix, int n_pix, int* g2o) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_pix; g += gridDim.x * blockDim.x)
+    g2o[g] = (bits[g >> 5] & (1u << (g & 31))) ? rank_of(bits, prefix, g) : -1;
+}
+
+// rows of excised pixels become zero (Section 4, gap filling)
+__global__ void k_excise_g2o(const int* obs2glob, const unsigned char* excised, int n_obs, int* g2o) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_obs; k += gridDim.x * blockDim.x)
+    if (excised[k]) g2o[obs2glob[k]] = -1;
+}
+
 __device__ __forceinline__ int interval_of(const long long* off, int n_ivl, long long t) {
   int lo = 0, hi = n_ivl;  // find i with off[i] <= t < off[i+1]
   while (hi - lo > 1) {
@@ -275,12 +306,21 @@ __device__ __forceinline__ int interval_of(const long long* off, int n_ivl, long
 // w w^T of every pixel (G[filter][pixel][6], or [filter][pixel] for T) or
 // directly A^T A and A^T W^-1 A (acc).  The first pass also stores the
 // float64 and double-float weights; later passes read them back.
+// Compressed pointing (ob.bore != NULL): pixel and weights expanded from the
+// boresight nodes, the observed row looked up in g2o.
+
 __global__ void k_accumulate(const int* pix_obs, const float* psi, long long n, const long long* off, int n_ivl,
                              const int* ivl_filter, const double* f0, int ns, double* acc, int* hits,
-                             double2* cs64, float4* csdf, double* G, int n_obs, int first) {
+                             double2* cs64, float4* csdf, double* G, int n_obs, int first, const OtfPointing ob) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     double c = 1.0, s = 0.0;
-    if (ns == 3) {
+    int p;
+    if (ob.bore) {
+      float c2, s2;
+      p = otf_row(ob, t, ns == 3, c2, s2);
+      c = c2;
+      s = s2;
+    } else if (ns == 3) {
       if (first) {
         sincos(2.0 * (double)psi[t], &s, &c);
         cs64[t] = make_double2(c, s);
@@ -292,7 +332,7 @@ __global__ void k_accumulate(const int* pix_obs, const float* psi, long long n, 
         s = cs.y;
       }
     }
-    const int p = pix_obs[t];
+    if (!ob.bore) p = pix_obs[t];
     if (p < 0) continue;
     const int f = ivl_filter[interval_of(off, n_ivl, t)];
     atomicAdd(hits + p, 1);
@@ -885,15 +925,19 @@ static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
     if (p->G) cudaMemsetAsync(p->G, 0, sizeof(double) * (size_t)p->n_filters * n_obs * nb, s);
     if (n > 0)
       k_accumulate<<<grid_for(n), 256, 0, s>>>(p->pix_obs, p->psi, n, doff, p->n_ivl, dfilt, df0, ns, acc, p->hits,
-                                                p->cs64, p->csdf, p->G, n_obs, first ? 1 : 0);
+                                                p->cs64, p->csdf, p->G, n_obs, first ? 1 : 0, otf_pointing(p));
   }
   if (p->G && n_obs > 0)
     k_combine<<<grid_for(n_obs), 256, 0, s>>>(p->G, p->n_filters, n_obs, ns, df0, acc);
   if (n_obs > 0)
     k_classify<<<grid_for(n_obs), 256, 0, s>>>(acc, p->hits, n_obs, ns, p->rcond_excise, p->rcond_fp64, p->P64,
                                                 p->P32, p->excised, p->fp64flag, counts);
-  if (first && n > 0) k_zero_excised_rows<<<grid_for(n), 256, 0, s>>>(p->pix_obs, n, p->excised);
-  if (first && n > 0 && ns == 3) k_pack_pw<<<grid_for(n), 256, 0, s>>>(p->pix_obs, p->psi, n, p->pw);
+  if (p->otf) {
+    if (first && n_obs > 0) k_excise_g2o<<<grid_for(n_obs), 256, 0, s>>>(p->obs2glob, p->excised, n_obs, p->g2o);
+  } else {
+    if (first && n > 0) k_zero_excised_rows<<<grid_for(n), 256, 0, s>>>(p->pix_obs, n, p->excised);
+    if (first && n > 0 && ns == 3) k_pack_pw<<<grid_for(n), 256, 0, s>>>(p->pix_obs, p->psi, n, p->pw);
+  }
   int hc[2] = {0, 0};
   e = cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -916,9 +960,32 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
   MM_CHECK(d->n_stokes == 1 || d->n_stokes == 3, MADMAP_ERR_INVALID_ARG, "n_stokes must be 1 or 3");
   MM_CHECK(d->n_samples >= 0 && d->n_samples < (1LL << 40), MADMAP_ERR_INVALID_ARG, "bad n_samples");
   MM_CHECK(d->n_pix > 0, MADMAP_ERR_INVALID_ARG, "n_pix must be > 0");
-  MM_CHECK(d->n_samples == 0 || d->pix != nullptr, MADMAP_ERR_INVALID_ARG, "pix is NULL");
-  MM_CHECK((d->n_stokes == 1) == (d->psi == nullptr) || d->n_samples == 0, MADMAP_ERR_INVALID_ARG,
-           "psi must be NULL for T and non-NULL for IQU");
+  const bool otf = d->boresight != nullptr;
+  if (otf) {
+    MM_CHECK(!d->pix && !d->psi && !d->pix_pol, MADMAP_ERR_INVALID_ARG,
+             "compressed pointing: pix, psi and pix_pol must be NULL");
+    MM_CHECK(d->n_det >= 1 && d->det_pointing && d->n_samples % d->n_det == 0, MADMAP_ERR_INVALID_ARG,
+             "compressed pointing: need n_det >= 1 dividing n_samples and det_pointing");
+    MM_CHECK(d->n_samples / d->n_det < (1LL << 31) - 1, MADMAP_ERR_INVALID_ARG,
+             "compressed pointing: too many samples per detector");
+    MM_CHECK(d->bore_step >= 1, MADMAP_ERR_INVALID_ARG, "compressed pointing: bore_step must be >= 1");
+    const long long npd = d->n_samples / d->n_det;
+    MM_CHECK(npd == 0 || (long long)d->n_bore >= (npd - 1) / d->bore_step + 2, MADMAP_ERR_INVALID_ARG,
+             "compressed pointing: n_bore must be >= (n_per_det - 1) / bore_step + 2");
+    MM_CHECK(d->grid_width >= 1 && d->grid_height >= 1 && d->grid_width <= (1 << 24) &&
+                 d->grid_height <= (1 << 24) && (long long)d->grid_width * d->grid_height == d->n_pix,
+             MADMAP_ERR_INVALID_ARG, "compressed pointing: n_pix must equal grid_width * grid_height");
+    for (int k = 0; k < 4 * d->n_det; ++k)
+      MM_CHECK(isfinite(d->det_pointing[k]), MADMAP_ERR_INVALID_ARG, "compressed pointing: det_pointing not finite");
+    for (int i = 0; i < d->n_intervals && npd > 0 && d->interval_offsets; ++i)
+      MM_CHECK(d->interval_offsets[i + 1] <= d->interval_offsets[i] ||
+                   d->interval_offsets[i] / npd == (d->interval_offsets[i + 1] - 1) / npd,
+               MADMAP_ERR_INVALID_ARG, "compressed pointing: an interval spans two detectors");
+  } else {
+    MM_CHECK(d->n_samples == 0 || d->pix != nullptr, MADMAP_ERR_INVALID_ARG, "pix is NULL");
+    MM_CHECK((d->n_stokes == 1) == (d->psi == nullptr) || d->n_samples == 0, MADMAP_ERR_INVALID_ARG,
+             "psi must be NULL for T and non-NULL for IQU");
+  }
   MM_CHECK(!d->pix_pol || (d->n_stokes == 3 && d->n_pix_pol > 0), MADMAP_ERR_INVALID_ARG,
            "pix_pol needs n_stokes = 3 and n_pix_pol > 0");
   MM_CHECK(d->n_intervals >= 0 && d->interval_offsets != nullptr, MADMAP_ERR_INVALID_ARG, "bad intervals");
@@ -974,7 +1041,8 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
   MM_TRY(dalloc_t(p, &bits, n_words));
   MM_TRY(dalloc_t(p, &prefix, n_words));
   MM_TRY(dalloc_t(p, &total, 2));
-  MM_TRY(dalloc_t(p, &p->pix_obs, std::max(1LL, n)));
+  p->otf = otf;
+  if (!otf) MM_TRY(dalloc_t(p, &p->pix_obs, std::max(1LL, n)));
   // the second pixelisation of multi-resolution plans
   p->multires = d->pix_pol != nullptr;
   p->n_pix_pol = p->multires ? d->n_pix_pol : 0;
@@ -987,7 +1055,22 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
     MM_TRY(dalloc_t(p, &p->pix_obs_pol, std::max(1LL, n)));
     MM_TRYC(cudaMemsetAsync(bits_pol, 0, sizeof(unsigned) * std::max(1, n_words_pol), s));
   }
-  if (p->n_stokes == 3) {
+  if (otf) {
+    p->n_det = d->n_det;
+    p->n_per_det = (int)(n / d->n_det);
+    p->bore_step = d->bore_step;
+    p->n_bore = d->n_bore;
+    p->grid_w = d->grid_width;
+    p->grid_h = d->grid_height;
+    float4* bore = nullptr;
+    MM_TRY(dalloc_t(p, &bore, std::max(1, p->n_bore)));
+    if (p->n_bore > 0)
+      MM_TRYC(cudaMemcpyAsync(bore, d->boresight, sizeof(float4) * p->n_bore, cudaMemcpyDeviceToDevice, s));
+    p->bore = bore;
+    MM_TRY(dalloc_t(p, &p->det_pt, p->n_det));
+    MM_TRYC(cudaMemcpyAsync(p->det_pt, d->det_pointing, sizeof(float4) * p->n_det, cudaMemcpyHostToDevice, s));
+    MM_TRY(dalloc_t(p, &p->g2o, p->n_pix));
+  } else if (p->n_stokes == 3) {
     MM_TRY(dalloc_t(p, &p->psi, std::max(1LL, n)));
     MM_TRY(dalloc_t(p, &p->cs64, std::max(1LL, n)));
     MM_TRY(dalloc_t(p, &p->csdf, std::max(1LL, n)));
@@ -995,7 +1078,12 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
   }
   MM_TRYC(cudaMemsetAsync(p->dev_flag, 0, 16 * sizeof(int), s));
   MM_TRYC(cudaMemsetAsync(bits, 0, sizeof(unsigned) * n_words, s));
-  if (n > 0) {
+  if (otf) {
+    if (p->n_bore > 0) k_validate_bore<<<grid_for(p->n_bore), 256, 0, s>>>(p->bore, p->n_bore, p->dev_flag);
+    if (n > 0)
+      k_mark_bits_otf<<<grid_for(n), 256, 0, s>>>(p->bore, p->bore_step, p->det_pt, p->n_per_det, n, p->grid_w,
+                                                   p->grid_h, p->n_stokes == 3, bits);
+  } else if (n > 0) {
     k_validate_pix<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, p->dev_flag, 1);
     if (p->multires) k_validate_pix<<<grid_for(n), 256, 0, s>>>(d->pix_pol, n, p->n_pix_pol, p->dev_flag, 4);
     if (p->n_stokes == 3) {
@@ -1027,6 +1115,11 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
     set_error("pix_pol holds values outside [-1, n_pix_pol)");
     return MADMAP_ERR_INVALID_ARG;
   }
+  if (hv[0] & 8) {
+    delete p;
+    set_error("boresight holds non-finite values");
+    return MADMAP_ERR_INVALID_ARG;
+  }
   p->n_obs_i = hv[1];
   p->n_obs_pol = p->multires ? hv[2] : 0;
   p->n_obs = std::max(p->n_obs_i, p->n_obs_pol);  // map rows (slots for multi-resolution plans)
@@ -1037,7 +1130,10 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
   MM_TRY(dalloc_t(p, &p->P64, (size_t)std::max(1, n_obs) * (p->n_stokes == 1 ? 1 : 6)));
   MM_TRY(dalloc_t(p, &p->P32, (size_t)std::max(1, n_obs) * (p->n_stokes == 1 ? 1 : 8)));
   k_obs2glob<<<grid_for(p->n_pix), 256, 0, s>>>(bits, prefix, p->n_pix, p->obs2glob);
-  if (n > 0) k_pix_obs<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, bits, prefix, p->pix_obs, d->pix_pol);
+  if (otf)
+    k_g2o<<<grid_for(p->n_pix), 256, 0, s>>>(bits, prefix, p->n_pix, p->g2o);
+  else if (n > 0)
+    k_pix_obs<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, bits, prefix, p->pix_obs, d->pix_pol);
   if (p->multires) {
     MM_TRY(dalloc_t(p, &p->obs2glob_pol, std::max(1, p->n_obs_pol)));
     MM_TRY(dalloc_t(p, &p->excised_pol, std::max(1, n_obs)));
