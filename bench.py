@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=3, help="oracle PCG iterations in the CPU baseline sample")
-    ap.add_argument("--workload", default="config2", choices=["config2", "config1", "config3", "config4", "config5"],
+    ap.add_argument("--workload", default="config2", choices=["config2", "config1", "config3", "config4", "config5",
+                                                               "config2-boresight"],
                     help="config2 (default) prints the headline line; the others print secondary measurements")
     ap.add_argument("--profile-step", type=float, default=0.0, metavar="TOL",
                     help="profiling runs: skip the reference map and tolerance search and run exactly one "
@@ -345,6 +346,48 @@ def run_secondary(args):
                      "workload_desc": "IQU all-sky ring scan, 32 det x 2^24 samples at 180 Hz, HEALPix Nside=512 "
                                       "RING, pointing periods 40-60 min, f_knee=0.03 Hz, alpha=1.7, n_c=2^15"})
         plan.close()
+    elif args.workload == "config2-boresight":
+        # the same scan planned twice: pointing expanded on the fly from the
+        # boresight nodes, and the expansion stored per sample
+        from synth.boresight import make_boresight_config2
+        p = make_boresight_config2()
+        otf = mm.Plan.from_boresight(torch.from_numpy(p.boresight).to(dev), p.bore_step, p.det, p.samples_per_det,
+                                     p.width, p.height, True, p.interval_offsets, p.interval_filter, lib_lags(p))
+        if args.operator_only:      # a short run of the on-the-fly float32 operator alone (for ncu)
+            ms, n = otf.time_operator("fp32", reps=args.operator_only)
+            print(json.dumps({"operator_only": "config2-boresight on the fly", "fp32_ms": [float(x) for x in ms],
+                              "launches": [int(x) for x in n]}), flush=True)
+            otf.close()
+            return
+        pix, c2, s2 = otf.expand_pointing()
+        psi = (0.5 * torch.atan2(s2.double(), c2.double())).float()
+        stored = mm.Plan(pix, psi, p.n_pix, p.interval_offsets, p.interval_filter, lib_lags(p))
+        del pix, c2, s2, psi
+        d = torch.from_numpy(p.d[0]).to(dev)
+        res = {}
+        for name, plan in (("stored", stored), ("on_the_fly", otf)):
+            ops = {}
+            for prec in ("fp32", "df64", "fp64"):
+                ms, _ = plan.time_operator(prec, reps=20 if prec == "fp32" else 5)
+                ops[prec + "_ms"] = float(ms[3])
+                if prec == "fp32":
+                    ops["fp32_per_kernel_ms"] = [float(x) for x in ms[:3]]
+            kw = dict(precision="mixed", rel_tol=1e-6, max_iter=500, max_outer=10)
+            plan.solve(d, **kw)
+            ms_s, (m, info) = _timed(lambda: plan.solve(d, **kw), steps)
+            res[name] = {"operator": ops, "device_bytes": plan.stats["device_bytes"],
+                         "mixed_solve_to_1e-6": {"ms": ms_s, "iters": info["iters"],
+                                                 "value": p.n_samples * info["iters"] / (ms_s / 1e3)},
+                         "n_obs": plan.n_obs}
+        line.update({"n_samples": p.n_samples, "bore_step": p.bore_step, "n_bore": int(p.boresight.shape[0]),
+                     "fft_len": otf.stats["fft_len"], **res,
+                     "operator_fp32_speedup_on_the_fly": res["stored"]["operator"]["fp32_ms"]
+                     / res["on_the_fly"]["operator"]["fp32_ms"],
+                     "workload_desc": "IQU, 4 det x 2^22 samples, 512x512 grid, overshooting raster with off-grid "
+                                      "turnarounds, boresight nodes every 16 samples, focal plane turning once per "
+                                      "4 sweeps, intervals 2^16-2^20, n_c=2^14"})
+        stored.close()
+        otf.close()
     else:
         p = make_config(5)
         plan = mm.Plan(torch.from_numpy(p.pix).to(dev), torch.from_numpy(p.psi).to(dev), p.n_pix,

@@ -231,6 +231,15 @@ madmap_status madmap_plan_observed(madmap_plan_t plan, int32_t* n_obs, int32_t* 
 madmap_status madmap_plan_observed_pol(madmap_plan_t plan, int32_t* n_obs_pol, int32_t* obs2glob_pol,
                                        uint8_t* excised_pol, void* stream);
 
+/* Plans over compressed pointing (madmap_plan_desc.boresight): the expanded
+ * pointing of every sample, as the operator computes it (Section 5.3).
+ * pix: device int32 [n_samples], the global pixel or -1 (flagged); cos2psi,
+ * sin2psi: device float [n_samples] (IQU; may be NULL; 0 at flagged samples).
+ * Any output may be NULL.  INVALID_ARG for plans over stored pointing.
+ * Asynchronous on `stream`. */
+madmap_status madmap_plan_expand_pointing(madmap_plan_t plan, int32_t* pix, float* cos2psi, float* sin2psi,
+                                          void* stream);
+
 /* Replace the filter lags (host [n_filters][n_lags]) without re-planning:
  * recomputes spectra and preconditioner blocks.  Synchronises `stream`. */
 madmap_status madmap_plan_set_filters(madmap_plan_t plan, const double* filter_lags, void* stream);

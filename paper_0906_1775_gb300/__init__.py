@@ -21,7 +21,7 @@ from ._lib import (MADMAP_DF64, MADMAP_FP32, MADMAP_FP64, MADMAP_MIXED, MadmapEr
 
 __all__ = ["Plan", "noise_filter", "paper_fft_length", "MadmapError", "load", "library_path",
            "madmap_plan_create", "madmap_plan_destroy", "madmap_plan_get_stats", "madmap_plan_observed",
-           "madmap_plan_observed_pol",
+           "madmap_plan_observed_pol", "madmap_plan_expand_pointing",
            "madmap_plan_set_filters", "madmap_apply_ATNA", "madmap_rhs", "madmap_apply_ninv", "madmap_solve",
            "madmap_solve_batched", "madmap_solve_backward", "madmap_noise_filter_vjp", "MadmapSolve",
            "madmap_noise_filter", "madmap_paper_fft_length", "madmap_last_error", "madmap_kernel_launch_count",
@@ -91,6 +91,11 @@ def madmap_plan_observed_pol(h, obs2glob_pol_ptr=None, excised_pol_ptr=None, str
                                                      else 0)),
           "madmap_plan_observed_pol")
     return n.value
+
+
+def madmap_plan_expand_pointing(h, pix_ptr=None, cos2psi_ptr=None, sin2psi_ptr=None, stream=None):
+    check(load().madmap_plan_expand_pointing(h, pix_ptr, cos2psi_ptr, sin2psi_ptr, C.c_void_p(_stream_ptr(stream))),
+          "madmap_plan_expand_pointing")
 
 
 def madmap_plan_set_filters(h, lags: np.ndarray, stream=None):
@@ -363,6 +368,19 @@ class Plan:
         e = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
         madmap_plan_observed(self._h, o.data_ptr(), e.data_ptr(), stream)
         return o[:n], e[:n]
+
+    def expand_pointing(self, stream=None):
+        """(pix int32, cos2psi float32 or None, sin2psi float32 or None) CUDA tensors [n_samples]: the
+        pointing a plan over compressed pointing computes for every sample."""
+        torch = _torch()
+        n = max(self.n_samples, 1)
+        pix = torch.empty(n, dtype=torch.int32, device="cuda")
+        c2 = torch.empty(n, dtype=torch.float32, device="cuda") if self.n_stokes == 3 else None
+        s2 = torch.empty(n, dtype=torch.float32, device="cuda") if self.n_stokes == 3 else None
+        madmap_plan_expand_pointing(self._h, pix.data_ptr(), c2.data_ptr() if c2 is not None else None,
+                                    s2.data_ptr() if s2 is not None else None, stream)
+        k = self.n_samples
+        return pix[:k], (c2[:k] if c2 is not None else None), (s2[:k] if s2 is not None else None)
 
     def observed_pol(self, stream=None):
         """(obs2glob_pol int32, excised_pol uint8) CUDA tensors over the observed Q/U

@@ -83,6 +83,7 @@ PROTOTYPES = [
     ("madmap_plan_observed", C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_void_p, C.c_void_p, C.c_void_p]),
     ("madmap_plan_observed_pol", C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_void_p, C.c_void_p, C.c_void_p]),
     ("madmap_plan_set_filters", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("madmap_plan_expand_pointing", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("madmap_apply_ATNA", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("madmap_rhs", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("madmap_apply_ninv", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -282,6 +282,19 @@ __global__ void k_g2o(const unsigned* bits, const int* prefix, int n_pix, int* g
     g2o[g] = (bits[g >> 5] & (1u << (g & 31))) ? rank_of(bits, prefix, g) : -1;
 }
 
+// the expanded pointing of every sample (global pixel and weights)
+__global__ void k_expand_all(const float4* bore, int step, const float4* det, int n_per_det, long long n, int W,
+                             int H, bool pol, int* pix, float* c2o, float* s2o) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int dd = (int)(t / n_per_det);
+    float c2, s2;
+    const int g = expand_pointing(bore, step, (int)(t - (long long)dd * n_per_det), det[dd], W, H, pol, c2, s2);
+    if (pix) pix[t] = g;
+    if (c2o) c2o[t] = c2;
+    if (s2o) s2o[t] = s2;
+  }
+}
+
 // rows of excised pixels become zero (Section 4, gap filling)
 __global__ void k_excise_g2o(const int* obs2glob, const unsigned char* excised, int n_obs, int* g2o) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_obs; k += gridDim.x * blockDim.x)
@@ -1275,6 +1288,20 @@ extern "C" madmap_status madmap_plan_observed_pol(madmap_plan_t plan, int32_t* n
     MM_CUDA(cudaMemcpyAsync(obs2glob_pol, p->obs2glob_pol, sizeof(int) * p->n_obs_pol, cudaMemcpyDeviceToDevice, s));
   if (excised_pol && p->n_obs_pol)
     MM_CUDA(cudaMemcpyAsync(excised_pol, p->excised_pol, p->n_obs_pol, cudaMemcpyDeviceToDevice, s));
+  return MADMAP_OK;
+}
+
+extern "C" madmap_status madmap_plan_expand_pointing(madmap_plan_t plan, int32_t* pix, float* cos2psi,
+                                                     float* sin2psi, void* stream) {
+  MM_CHECK(plan, MADMAP_ERR_INVALID_ARG, "plan_expand_pointing: NULL plan");
+  const Plan* p = reinterpret_cast<const Plan*>(plan);
+  MM_CHECK(p->otf, MADMAP_ERR_INVALID_ARG, "plan_expand_pointing: the plan stores its pointing");
+  if (p->n_t == 0) return MADMAP_OK;
+  const bool pol = p->n_stokes == 3;
+  mm::k_expand_all<<<mm::grid_for(p->n_t), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      p->bore, p->bore_step, p->det_pt, p->n_per_det, p->n_t, p->grid_w, p->grid_h, pol, pix,
+      pol ? cos2psi : nullptr, pol ? sin2psi : nullptr);
+  MM_CUDA(cudaGetLastError());
   return MADMAP_OK;
 }
 

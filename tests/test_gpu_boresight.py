@@ -294,6 +294,8 @@ def test_config2_boresight_observed_and_sampled_outputs(config2_boresight):
     import torch
     p, S = config2_boresight
     plan = _plan(p)
+    gp, _, _ = plan.expand_pointing()
+    assert np.array_equal(host(gp).astype(np.int64), _expand(p)[0])
     assert plan.n_obs == S.n_obs
     o2g, exc = plan.observed()
     assert np.array_equal(host(o2g).astype(np.int64), S.obs2glob)
@@ -305,3 +307,29 @@ def test_config2_boresight_observed_and_sampled_outputs(config2_boresight):
         dt = torch.float32 if prec == "fp32" else torch.float64
         y = host(plan.apply_ATNA(cuda(x, dt), precision=prec))[0]
         assert rel_rms(y[pk], ref) < tol, prec
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_expanded_pointing_equals_oracle_bit_for_bit(problems, case):
+    """Pixels and float32 weights of every sample, as the kernels compute them, equal the
+    oracle's expansion exactly (the same float32 operations in the same order)."""
+    p = problems[case]
+    pix, c2, s2 = _expand(p)
+    plan = _plan(p)
+    gp, gc, gs = plan.expand_pointing()
+    assert np.array_equal(host(gp).astype(np.int64), pix)
+    if p.n_stokes == 3:
+        ok = pix >= 0
+        assert np.array_equal(host(gc)[ok], c2[ok]) and np.array_equal(host(gs)[ok], s2[ok])
+    else:
+        assert gc is None and gs is None
+
+
+def test_expand_pointing_rejects_stored_pointing_plans():
+    import paper_0906_1775_gb300 as mm
+    from tests.gpu_helpers import make_plan
+    from tests.helpers import tiny_IQU
+    plan = make_plan(tiny_IQU(seed=3))
+    with pytest.raises(mm.MadmapError) as e:
+        plan.expand_pointing()
+    assert e.value.status == mm._lib.MADMAP_ERR_INVALID_ARG
