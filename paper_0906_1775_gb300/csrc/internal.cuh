@@ -100,15 +100,60 @@ __device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b;
 __device__ __forceinline__ df64& operator*=(df64& a, df64 b) { return a = a * b; }
 
 // ---------------------------------------------------------------- compressed pointing
+// Division of a detector sample index j >= 0 by the node step: a shift for a
+// power of two, else a multiply-high by a precomputed reciprocal (division by
+// invariant integers, Granlund and Montgomery, PLDI 1994) followed by one
+// correction step, so the quotient is exact for every j < 2^31.
+struct StepDiv {
+  int step = 1, shift = 0;   // shift: log2(step) (power of two) or ceil(log2(step)) - 1
+  unsigned magic = 0;        // 0 for a power of two
+  float inv = 1.f;           // 1 / step (exact for a power of two)
+};
+inline StepDiv make_step_div(int step) {
+  StepDiv d;
+  d.step = step;
+  int l = 0;
+  while ((1LL << l) < step) ++l;
+  if ((1LL << l) == step) {
+    d.shift = l;
+    d.magic = 0;
+    d.inv = 1.0f / (float)step;
+  } else {
+    // m = ceil(2^(31 + l) / step) < 2^32
+    const unsigned long long num = 1ULL << (31 + l);
+    d.magic = (unsigned)((num + (unsigned long long)step - 1) / (unsigned long long)step);
+    d.shift = l - 1;
+    d.inv = 0.f;
+  }
+  return d;
+}
+__device__ __forceinline__ int step_quot(const StepDiv& d, int j, int& r) {
+  int q;
+  if (d.magic == 0) {
+    q = j >> d.shift;
+  } else {
+    q = (int)(__umulhi((unsigned)j, d.magic) >> d.shift);
+    const int rr = j - q * d.step;
+    if (rr < 0) --q;
+    else if (rr >= d.step) ++q;
+  }
+  r = j - q * d.step;
+  return q;
+}
+
 // Section 5.3: the pointing of detector sample j (detector pointing dp =
 // (dx, dy, cd, sd)) expanded from the boresight nodes, in the float32
 // operation order stated with madmap_plan_desc (no contraction, so the pixel
 // decisions are reproducible).  Returns the global pixel or -1; c2, s2 get
-// cos 2psi and sin 2psi when `pol`.
-__device__ __forceinline__ int expand_pointing(const float4* __restrict__ bore, int step, int j, float4 dp, int W,
-                                               int H, bool pol, float& c2, float& s2) {
-  const int u = j / step;
-  const float f = __fdiv_rn((float)(j - u * step), (float)step);
+// cos 2psi and sin 2psi when `pol`.  FAST_W: the weights' two divisions by n
+// become one approximate reciprocal (relative error ~1e-7, for the float32
+// operator); the pixel decision is the same either way.
+template <bool FAST_W = false>
+__device__ __forceinline__ int expand_pointing(const float4* __restrict__ bore, const StepDiv& sd, int j, float4 dp,
+                                               int W, int H, bool pol, float& c2, float& s2) {
+  int r;
+  const int u = step_quot(sd, j, r);
+  const float f = sd.magic == 0 ? __fmul_rn((float)r, sd.inv) : __fdiv_rn((float)r, (float)sd.step);
   const float4 a = __ldg(bore + u), b = __ldg(bore + u + 1);
   const float x = __fadd_rn(a.x, __fmul_rn(f, __fsub_rn(b.x, a.x)));
   const float y = __fadd_rn(a.y, __fmul_rn(f, __fsub_rn(b.y, a.y)));
@@ -127,8 +172,14 @@ __device__ __forceinline__ int expand_pointing(const float4* __restrict__ bore, 
     const float cs = __fmul_rn(C, S);
     ok = ok && n > 0.f;
     if (ok) {
-      c2 = __fdiv_rn(__fsub_rn(cc, ss), n);
-      s2 = __fdiv_rn(__fadd_rn(cs, cs), n);
+      if (FAST_W) {
+        const float in = __fdividef(1.0f, n);
+        c2 = (cc - ss) * in;
+        s2 = (cs + cs) * in;
+      } else {
+        c2 = __fdiv_rn(__fsub_rn(cc, ss), n);
+        s2 = __fdiv_rn(__fadd_rn(cs, cs), n);
+      }
     }
   }
   return ok ? (int)fy * W + (int)fx : -1;
@@ -140,13 +191,14 @@ struct OtfPointing {
   const float4* bore;
   const float4* det;
   const int* g2o;
-  int step, n_per_det, W, H;
+  StepDiv sd;
+  int n_per_det, W, H;
 };
 
 // Observed row of sample t (or -1) and its weights, from compressed pointing.
 __device__ __forceinline__ int otf_row(const OtfPointing& o, long long t, bool pol, float& c2, float& s2) {
   const int dd = (int)(t / o.n_per_det);
-  const int g = expand_pointing(o.bore, o.step, (int)(t - (long long)dd * o.n_per_det), o.det[dd], o.W, o.H, pol, c2,
+  const int g = expand_pointing(o.bore, o.sd, (int)(t - (long long)dd * o.n_per_det), o.det[dd], o.W, o.H, pol, c2,
                                 s2);
   return g >= 0 ? o.g2o[g] : -1;
 }
@@ -235,7 +287,7 @@ inline OtfPointing otf_pointing(const Plan* p) {
   a.bore = p->otf ? p->bore : nullptr;
   a.det = p->det_pt;
   a.g2o = p->g2o;
-  a.step = p->bore_step;
+  a.sd = make_step_div(p->bore_step > 0 ? p->bore_step : 1);
   a.n_per_det = p->n_per_det > 0 ? p->n_per_det : 1;
   a.W = p->grid_w;
   a.H = p->grid_h;

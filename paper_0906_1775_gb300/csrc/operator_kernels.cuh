@@ -73,7 +73,8 @@ struct OpArgs {
   const float4* bore;
   const float4* det;
   const int* g2o;
-  int bore_step, n_per_det, n_det, grid_w, grid_h;
+  StepDiv sd;
+  int n_per_det, n_det, grid_w, grid_h;
   const void* in;
   long long in_stride;
   void* out;
@@ -286,7 +287,9 @@ __device__ __forceinline__ void load_pointing(const OpArgs& a, const LaneView<Re
   if constexpr (on_the_fly(NS)) {
     float c2 = 0.f, s2 = 0.f;
     int g = -1;
-    if (ok) g = expand_pointing(a.bore, a.bore_step, L.j0 + n, L.dp, a.grid_w, a.grid_h, polarised(NS), c2, s2);
+    if (ok)
+      g = expand_pointing<std::is_same<Real, float>::value>(a.bore, a.sd, L.j0 + n, L.dp, a.grid_w, a.grid_h,
+                                                            polarised(NS), c2, s2);
     pp = g >= 0 ? __ldg(a.g2o + g) : -1;
     c = Real(c2);
     s = Real(s2);
@@ -719,7 +722,7 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
   a.bore = p->otf ? p->bore : nullptr;
   a.det = p->det_pt;
   a.g2o = p->g2o;
-  a.bore_step = p->bore_step;
+  a.sd = make_step_div(p->bore_step > 0 ? p->bore_step : 1);
   a.n_per_det = p->n_per_det;
   a.n_det = p->n_det;
   a.grid_w = p->grid_w;

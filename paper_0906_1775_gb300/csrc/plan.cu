@@ -266,8 +266,8 @@ __global__ void k_validate_bore(const float4* bore, int n_bore, int* bad) {
 }
 
 // Section 5.4 bits for pointing expanded on the fly (Section 5.3).
-__global__ void k_mark_bits_otf(const float4* bore, int step, const float4* det, int n_per_det, long long n, int W,
-                                int H, bool pol, unsigned* bits) {
+__global__ void k_mark_bits_otf(const float4* bore, const StepDiv step, const float4* det, int n_per_det, long long n,
+                                int W, int H, bool pol, unsigned* bits) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int dd = (int)(t / n_per_det);
     float c2, s2;
@@ -283,8 +283,8 @@ __global__ void k_g2o(const unsigned* bits, const int* prefix, int n_pix, int* g
 }
 
 // the expanded pointing of every sample (global pixel and weights)
-__global__ void k_expand_all(const float4* bore, int step, const float4* det, int n_per_det, long long n, int W,
-                             int H, bool pol, int* pix, float* c2o, float* s2o) {
+__global__ void k_expand_all(const float4* bore, const StepDiv step, const float4* det, int n_per_det, long long n,
+                             int W, int H, bool pol, int* pix, float* c2o, float* s2o) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int dd = (int)(t / n_per_det);
     float c2, s2;
@@ -1094,8 +1094,8 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
   if (otf) {
     if (p->n_bore > 0) k_validate_bore<<<grid_for(p->n_bore), 256, 0, s>>>(p->bore, p->n_bore, p->dev_flag);
     if (n > 0)
-      k_mark_bits_otf<<<grid_for(n), 256, 0, s>>>(p->bore, p->bore_step, p->det_pt, p->n_per_det, n, p->grid_w,
-                                                   p->grid_h, p->n_stokes == 3, bits);
+      k_mark_bits_otf<<<grid_for(n), 256, 0, s>>>(p->bore, make_step_div(p->bore_step), p->det_pt, p->n_per_det, n,
+                                                   p->grid_w, p->grid_h, p->n_stokes == 3, bits);
   } else if (n > 0) {
     k_validate_pix<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, p->dev_flag, 1);
     if (p->multires) k_validate_pix<<<grid_for(n), 256, 0, s>>>(d->pix_pol, n, p->n_pix_pol, p->dev_flag, 4);
@@ -1299,7 +1299,7 @@ extern "C" madmap_status madmap_plan_expand_pointing(madmap_plan_t plan, int32_t
   if (p->n_t == 0) return MADMAP_OK;
   const bool pol = p->n_stokes == 3;
   mm::k_expand_all<<<mm::grid_for(p->n_t), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      p->bore, p->bore_step, p->det_pt, p->n_per_det, p->n_t, p->grid_w, p->grid_h, pol, pix,
+      p->bore, mm::make_step_div(p->bore_step), p->det_pt, p->n_per_det, p->n_t, p->grid_w, p->grid_h, pol, pix,
       pol ? cos2psi : nullptr, pol ? sin2psi : nullptr);
   MM_CUDA(cudaGetLastError());
   return MADMAP_OK;

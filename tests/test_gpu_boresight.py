@@ -333,3 +333,37 @@ def test_expand_pointing_rejects_stored_pointing_plans():
     with pytest.raises(mm.MadmapError) as e:
         plan.expand_pointing()
     assert e.value.status == mm._lib.MADMAP_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("step,width,n_per", [(3, 24, 5000), (7, 21, 4000), (12, 24, 6000), (1, 8, 700)])
+def test_expansion_with_other_node_steps(step, width, n_per):
+    """Node steps that are not powers of two take the multiply-high division and the IEEE
+    division of the interpolation fraction: pixels and weights still equal the oracle's."""
+    from synth.boresight import make_boresight_problem
+    p = make_boresight_problem("bstep", 40 + step, width, 3, n_per, step, 3, 8, noise=(1.0, 3.0, 1.5),
+                               rot_period=5000)
+    pix, c2, s2 = _expand(p)
+    gp, gc, gs = _plan(p).expand_pointing()
+    assert np.array_equal(host(gp).astype(np.int64), pix)
+    ok = pix >= 0
+    assert ok.sum() > 0.3 * pix.size
+    assert np.array_equal(host(gc)[ok], c2[ok]) and np.array_equal(host(gs)[ok], s2[ok])
+
+
+def test_expansion_of_a_long_detector_stream():
+    """2^24 samples of one detector with a node every 7 samples (indices up to 2^24 through
+    the step division), temperature only: every pixel equals the oracle's."""
+    import torch
+    from oracle.gcp import expand
+    from paper_0906_1775_gb300 import Plan
+    n_per, step, width = 1 << 24, 7, 448
+    n_bore = (n_per - 1) // step + 2
+    u = np.arange(n_bore, dtype=np.float64)
+    bore = np.stack([width / 2 + 200 * np.sin(u * 1.1e-4), width / 2 + 200 * np.cos(u * 1.3e-4),
+                     np.cos(u * 1e-5), np.sin(u * 1e-5)], 1).astype(np.float32)
+    det = np.array([[0.3, -0.2, 1.0, 0.0]], dtype=np.float32)
+    pix, _, _ = expand(bore, step, det, n_per, width, width, polarised=False)
+    plan = Plan.from_boresight(torch.from_numpy(bore).cuda(), step, det, n_per, width, width, False,
+                               np.array([0, n_per]), np.zeros(1, np.int32), np.array([[1.0, 0.1]]))
+    gp, _, _ = plan.expand_pointing()
+    assert np.array_equal(host(gp).astype(np.int64), pix)
