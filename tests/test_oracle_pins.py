@@ -650,3 +650,73 @@ def test_gcp_system_matches_angle_system():
     x = np.random.default_rng(0).standard_normal((S1.n_obs, 3))
     assert rel_rms(S1.H(x), S2.H(x)) < 1e-6
     assert S1.n_obs > 40 and not S1.excised.all()
+
+
+# ------------------------------------------------------------------ extended pointing (Section 6)
+def _ext_system(p, idx, n_extra, lags=None, **kw):
+    from oracle.extended import ExtendedSystem
+    return ExtendedSystem(p.pix, p.psi, p.n_pix, p.n_stokes, p.interval_offsets, p.interval_filter,
+                          lags_for(p) if lags is None else lags, idx, n_extra, **kw)
+
+
+def test_extended_without_extra_columns_is_the_plain_system():
+    p = tiny_IQU(seed=51, n_per_det=400)
+    S = system_for(p)
+    E = _ext_system(p, np.full(p.n_samples, -1, np.int32), 3)
+    x = np.random.default_rng(0).standard_normal((E.n_obs, 3))
+    x[E.n_sky:] = 0.0
+    assert np.allclose(E.H(x)[:E.n_sky], S.H(x[:E.n_sky]), rtol=1e-12, atol=1e-12)
+    assert np.all(E.H(x)[E.n_sky:] == 0.0) and E.excised_extra.all()
+    xe, _ = E.solve(p.d[0], rel_tol=1e-13, max_iter=400)
+    xs, _ = S.solve(p.d[0], rel_tol=1e-13, max_iter=400)
+    assert rel_rms(xe[:E.n_sky], xs) < 1e-10 and np.all(xe[E.n_sky:] == 0.0)
+
+
+def test_extended_pcg_matches_dense_cholesky_and_is_symmetric():
+    from synth.extended import baseline_index
+    p = tiny_IQU(seed=52, n_per_det=300, n_lags=6)
+    idx, n_extra = baseline_index(300, 4, 64)
+    E = _ext_system(p, idx, n_extra)
+    xd = E.dense_solve(p.d[0])
+    xp, info = E.solve(p.d[0], rel_tol=1e-13, max_iter=2000)
+    act = E.active()
+    assert info["best_res"] < 1e-12
+    assert rel_rms(xp[act], xd[act]) < 1e-9 and np.all(xp[~act] == 0.0)
+    rng = np.random.default_rng(1)
+    x, y = rng.standard_normal((2, E.n_obs, 3)) * act
+    a, b = float(np.sum(y * E.H(x))), float(np.sum(x * E.H(y)))
+    assert abs(a - b) <= 1e-12 * abs(a) and float(np.sum(x * E.H(x))) > 0
+
+
+def test_extended_destriping_recovers_sky_and_offsets():
+    """White noise (one lag, no FFT involved) and noiseless data d = A z + B o: the
+    solution is the sky and the offsets (the reference baseline fixes the level)."""
+    from synth.extended import add_extra_signal, baseline_index
+    p = tiny_T(seed=53, n=1200, width=6, ivls=(500, 700), noiseless=True)
+    idx, n_extra = baseline_index(1200, 1, 50)
+    o = np.random.default_rng(2).normal(0.0, 3.0, n_extra)
+    d = add_extra_signal(p.d[0], idx, o)
+    white = np.array([[1.0]])
+    E = _ext_system(p, idx, n_extra, lags=white, ninv="direct")
+    x, info = E.solve(d, rel_tol=1e-14, max_iter=3000)
+    z, oo = E.split(x)
+    keep = ~E.excised_sky
+    assert rel_rms(z[keep, 0], p.sky[E.obs2glob[keep], 0]) < 1e-6       # d is float32
+    assert rel_rms(oo, o) < 1e-6
+
+
+def test_extended_binned_template_recovery():
+    """A chopper-synchronous signal binned in angle (item 1 of Section 6) on top of an IQU
+    sky, noiseless: both are recovered."""
+    from synth.extended import add_extra_signal, chop_bins
+    p = tiny_IQU(seed=54, n_per_det=1500, width=5, noiseless=True)
+    idx, n_extra = chop_bins(p.n_samples, 9, 37.0, np.random.default_rng(3))
+    amp = np.random.default_rng(4).normal(0.0, 2.0, n_extra)
+    d = add_extra_signal(p.d[0], idx, amp)
+    E = _ext_system(p, idx, n_extra)
+    x, _ = E.solve(d, rel_tol=1e-14, max_iter=3000)
+    z, oo = E.split(x)
+    keep = ~E.excised_sky
+    for s in range(3):
+        assert rel_rms(z[keep, s], p.sky[E.obs2glob[keep], s]) < 1e-5
+    assert rel_rms(oo, amp) < 1e-5
