@@ -120,6 +120,20 @@ typedef struct {
   int32_t n_det;                    /* detectors (>= 1; must divide n_samples); no interval
                                        may span two detectors */
   int32_t grid_width, grid_height;  /* flat pixel grid; n_pix must equal their product */
+  /* Extended pointing (Section 6, Eq. 26): extra unknowns o with A -> [A B],
+   * B one unit entry per sample, for destriping offsets (with a white-noise
+   * filter of one lag) or binned synchronous templates.  Stored pointing
+   * only (pix_pol and boresight NULL).  Maps then have n_obs + n_extra rows:
+   * the observed sky pixels, then one row per extra column with its
+   * amplitude in column 0 (other columns 0).  A sample that is flagged or
+   * whose sky pixel is excised has a zero row in both blocks; an extra
+   * column without samples is excised; its preconditioner block is
+   * 1 / (B^T W^-1 B).  The caller keeps the system non-singular (offsets on
+   * every sample are degenerate with a constant I map: leave one baseline
+   * without a column). */
+  const int32_t* extra_index;       /* device [n_samples]: extra column of each sample in
+                                       [0, n_extra), or -1 (none); NULL: no extra columns */
+  int32_t n_extra;                  /* extra columns (>= 1 when extra_index is set) */
 } madmap_plan_desc;
 
 typedef struct {
@@ -138,6 +152,9 @@ typedef struct {
   int64_t device_bytes;    /* device memory owned by the plan */
   int32_t n_obs_pol;       /* multi-resolution plans: observed Q/U pixels (else 0) */
   int32_t n_excised_pol;   /* multi-resolution plans: excised Q/U pixels */
+  int32_t n_extra;         /* extended pointing: extra columns (rows n_obs - n_extra .. n_obs - 1 of
+                              the map), else 0 */
+  int32_t n_excised_extra; /* extended pointing: extra columns without samples */
 } madmap_plan_stats;
 
 typedef struct {

@@ -61,6 +61,12 @@ class ExtendedSystem:
         with np.errstate(divide="ignore"):
             self.p_extra = np.where(self.excised_extra, 0.0, 1.0 / np.where(self.excised_extra, 1.0, wsum))
 
+    # the noise description (as the plain system's)
+    offsets = property(lambda self: self.sky.offsets)
+    ivl_filter = property(lambda self: self.sky.ivl_filter)
+    lags = property(lambda self: self.sky.lags)
+    n_c = property(lambda self: self.sky.n_c)
+
     # ---------------------------------------------------------------- layout
     def active(self):
         """[n_obs + n_extra, n_s] mask of the unknowns that exist."""

@@ -266,10 +266,15 @@ class Plan:
     pix_pol (int32 CUDA tensor [n_t], with n_pix_pol) puts Q and U on a second
     pixelisation (multi-resolution maps, IQU only): maps are then [n_obs, 3]
     slots, I of observed I pixel k and Q, U of observed Q/U pixel k in row k.
+    extra_index (int32 CUDA tensor [n_t], -1 = none, with n_extra) adds one
+    unit-weight extra column per sample (destriping offsets, binned templates):
+    maps then have n_obs = sky rows + n_extra rows, the extra amplitudes in
+    column 0 of the last n_extra rows.
     """
 
     def __init__(self, pix, psi, n_pix, interval_offsets, interval_filter, filter_lags, rcond_excise=0.0,
-                 rcond_fp64=0.0, fft_len=0, tiles_per_chunk=0, stream=None, pix_pol=None, n_pix_pol=0):
+                 rcond_fp64=0.0, fft_len=0, tiles_per_chunk=0, stream=None, pix_pol=None, n_pix_pol=0,
+                 extra_index=None, n_extra=0):
         torch = _torch()
         self._h = None
         off = np.ascontiguousarray(interval_offsets, dtype=np.int64)
@@ -297,6 +302,12 @@ class Plan:
             if not n_t:  # the library reads no sample, but needs a non-NULL pointer to know the layout
                 pix_pol = torch.zeros(1, dtype=torch.int32, device="cuda")
                 d.pix_pol = _dev_ptr(pix_pol, torch.int32, "pix_pol")
+        if extra_index is not None:
+            if int(extra_index.numel()) != n_t:
+                raise ValueError("extra_index must have one entry per sample")
+            keep_extra = extra_index if n_t else torch.full((1,), -1, dtype=torch.int32, device="cuda")
+            d.extra_index = _dev_ptr(keep_extra, torch.int32, "extra_index")
+            d.n_extra = int(n_extra)
         self._keep = (off, filt, lags)
         self.multires = pix_pol is not None
         self._create(d, n_t, stream)
@@ -307,6 +318,7 @@ class Plan:
         self.n_samples = n_t
         self.stats = madmap_plan_get_stats(self._h)
         self.n_obs = self.stats["n_obs"]
+        self.n_extra = self.stats["n_extra"]
 
     @classmethod
     def from_boresight(cls, boresight, bore_step, det_pointing, samples_per_det, width, height, polarised,

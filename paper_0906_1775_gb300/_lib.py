@@ -40,14 +40,15 @@ class madmap_plan_desc(C.Structure):
                 ("tiles_per_chunk", C.c_int32), ("pix_pol", C.c_void_p), ("n_pix_pol", C.c_int32),
                 ("boresight", C.c_void_p), ("n_bore", C.c_int32), ("bore_step", C.c_int32),
                 ("det_pointing", C.c_void_p), ("n_det", C.c_int32), ("grid_width", C.c_int32),
-                ("grid_height", C.c_int32)]
+                ("grid_height", C.c_int32), ("extra_index", C.c_void_p), ("n_extra", C.c_int32)]
 
 
 class madmap_plan_stats(C.Structure):
     _fields_ = [(n, C.c_int32) for n in ("n_obs", "n_excised", "n_fp64_pixels", "n_stokes", "fft_len", "n1",
                                          "n2", "n_segments", "n_tiles", "tiles_per_chunk", "n_lags",
                                          "n_filters")] + [("n_samples", C.c_int64), ("device_bytes", C.c_int64),
-                                                          ("n_obs_pol", C.c_int32), ("n_excised_pol", C.c_int32)]
+                                                          ("n_obs_pol", C.c_int32), ("n_excised_pol", C.c_int32),
+                                                          ("n_extra", C.c_int32), ("n_excised_extra", C.c_int32)]
 
 
 class madmap_checkpoint(C.Structure):

@@ -256,6 +256,10 @@ struct Plan {
   float4* det_pt = nullptr;        // [n_det] detector offsets and orientations
   int n_bore = 0, bore_step = 1, n_det = 0, n_per_det = 0, grid_w = 0, grid_h = 0;
   int* g2o = nullptr;              // [n_pix] observed row of each global pixel, -1 if unobserved or excised
+  // extended pointing: extra unit-weight columns after the sky rows
+  bool ext = false;
+  int n_extra = 0, n_obs_sky = 0, n_excised_extra = 0;
+  int* ext_row = nullptr;          // [n_t] map row of the sample's extra column (n_obs_sky + e) or -1
   void* scratch = nullptr;         // scratch_slots * tiles_per_chunk * M complex (float64 size)
   int scratch_slots = 1;           // 2 when an application has several chunks (see op_stream)
   // An application of several chunks alternates them between two streams,

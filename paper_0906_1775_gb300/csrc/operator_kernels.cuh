@@ -44,20 +44,31 @@ enum { IN_MAPX = 0, IN_TODF = 1, IN_TODR = 2 };
 // each sample then carries an I pixel and a Q/U pixel of the slot layout).
 // NS_OTF_T / NS_OTF_IQU: T / IQU with the pointing expanded on the fly from
 // compressed boresight pointing (Section 5.3) instead of read per sample.
+// NS_EXT_T / NS_EXT_IQU: T / IQU with extended pointing (Section 6, Eq. 26):
+// each sample may add one unit-weight extra column (a row after the sky rows).
 constexpr int NS_MR = 4;
 constexpr int NS_OTF_T = 5;
 constexpr int NS_OTF_IQU = 6;
-__host__ __device__ constexpr bool polarised(int ns) { return ns == 3 || ns == NS_MR || ns == NS_OTF_IQU; }
+constexpr int NS_EXT_T = 7;
+constexpr int NS_EXT_IQU = 8;
+__host__ __device__ constexpr bool polarised(int ns) {
+  return ns == 3 || ns == NS_MR || ns == NS_OTF_IQU || ns == NS_EXT_IQU;
+}
 __host__ __device__ constexpr bool on_the_fly(int ns) { return ns == NS_OTF_T || ns == NS_OTF_IQU; }
+__host__ __device__ constexpr bool extended(int ns) { return ns == NS_EXT_T || ns == NS_EXT_IQU; }
 // the map layout's gather/scatter of a pointing mode
-__host__ __device__ constexpr int map_ns(int ns) { return ns == NS_OTF_T ? 1 : ns == NS_OTF_IQU ? 3 : ns; }
+__host__ __device__ constexpr int map_ns(int ns) {
+  return (ns == NS_OTF_T || ns == NS_EXT_T) ? 1 : (ns == NS_OTF_IQU || ns == NS_EXT_IQU) ? 3 : ns;
+}
 inline int layout(const Plan* p) {
   if (p->otf) return p->n_stokes == 1 ? NS_OTF_T : NS_OTF_IQU;
+  if (p->ext) return p->n_stokes == 1 ? NS_EXT_T : NS_EXT_IQU;
   return p->multires ? NS_MR : p->n_stokes;
 }
 // Calls X(ns) with the compile-time pointing mode ns of `k`.
-#define MM_FOR_LAYOUT(k, X)                          \
-  ((k) == 1 ? X(1) : (k) == 3 ? X(3) : (k) == NS_MR ? X(NS_MR) : (k) == NS_OTF_T ? X(NS_OTF_T) : X(NS_OTF_IQU))
+#define MM_FOR_LAYOUT(k, X)                                                                                  \
+  ((k) == 1 ? X(1) : (k) == 3 ? X(3) : (k) == NS_MR ? X(NS_MR) : (k) == NS_OTF_T ? X(NS_OTF_T)             \
+   : (k) == NS_OTF_IQU ? X(NS_OTF_IQU) : (k) == NS_EXT_T ? X(NS_EXT_T) : X(NS_EXT_IQU))
 
 struct OpArgs {
   const Tile* tiles;
@@ -69,6 +80,7 @@ struct OpArgs {
   const float4* csdf;
   const int2* pw;      // (pixel, angle bits) per sample, IQU
   const int* pixq;     // Q/U pixel per sample (multi-resolution plans)
+  const int* ext;      // extra column's map row per sample (extended pointing)
   // compressed pointing (on-the-fly modes)
   const float4* bore;
   const float4* det;
@@ -139,6 +151,11 @@ __device__ __forceinline__ df64 gather<df64, 3>(const df64* x, int p, df64 c, df
   return df64(u.x, u.y) + df64(u.z, u.w) * c + df64(v.x, v.y) * s;
 }
 
+// a kernel's value in its output map's type (double-float results go out as float64)
+__device__ __forceinline__ float to_out(float v) { return v; }
+__device__ __forceinline__ double to_out(double v) { return v; }
+__device__ __forceinline__ double to_out(df64 v) { return to_double(v); }
+
 // multi-resolution maps: I from slot p, Q and U from slot q
 template <typename Real>
 __device__ __forceinline__ Real gather_mr(const Real* x, int p, int q, Real c, Real s) {
@@ -203,6 +220,7 @@ struct LaneView {
   const float4* csd;
   const int2* pw;
   const int* pq;
+  const int* pe;
   const void* in;
   void* out;
   int j0;        // on-the-fly pointing: detector sample of window position 0
@@ -226,6 +244,7 @@ __device__ __forceinline__ LaneView<Real> lane_view(const OpArgs& a, const Lane&
   v.csd = a.csdf + ws;
   v.pw = a.pw + ws;
   v.pq = a.pixq ? a.pixq + ws : nullptr;
+  v.pe = a.ext ? a.ext + ws : nullptr;
   if (a.bore) {
     // windows never leave their interval's detector
     long long dd = a.n_per_det > 0 ? g.lo / a.n_per_det : 0;
@@ -404,7 +423,8 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
           load_pointing<Real, NS>(a, L[l], nn[u], ok[l][u], pp[l][u], cc[l][u], ss[l][u]);
-          if constexpr (NS == NS_MR) qq[l][u] = ok[l][u] ? __ldg(L[l].pq + nn[u]) : -1;
+          if constexpr (NS == NS_MR || extended(NS))
+            qq[l][u] = ok[l][u] ? __ldg((NS == NS_MR ? L[l].pq : L[l].pe) + nn[u]) : -1;
         }
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -412,12 +432,15 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
         for (int l = 0; l < 2; ++l) {
           Real c = cc[l][u], sn = ss[l][u];
           if (polarised(NS) && !on_the_fly(NS)) finish_angle<Real>(c, sn);
-          if constexpr (NS == NS_MR)
-            v[l][u] = pp[l][u] >= 0 ? gather_mr<Real>(static_cast<const Real*>(L[l].in), pp[l][u], qq[l][u], c, sn)
-                                    : Real(0);
-          else
-            v[l][u] = pp[l][u] >= 0 ? gather<Real, map_ns(NS)>(static_cast<const Real*>(L[l].in), pp[l][u], c, sn)
-                                    : Real(0);
+          const Real* x = static_cast<const Real*>(L[l].in);
+          if constexpr (NS == NS_MR) {
+            v[l][u] = pp[l][u] >= 0 ? gather_mr<Real>(x, pp[l][u], qq[l][u], c, sn) : Real(0);
+          } else {
+            v[l][u] = pp[l][u] >= 0 ? gather<Real, map_ns(NS)>(x, pp[l][u], c, sn) : Real(0);
+            if constexpr (extended(NS)) {   // + the extra column's amplitude (slot 0 of its row)
+              if (pp[l][u] >= 0 && qq[l][u] >= 0) v[l][u] += x[(long long)qq[l][u] * (map_ns(NS) == 3 ? 4 : 1)];
+            }
+          }
         }
     }
 #pragma unroll
@@ -561,7 +584,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
     } else if constexpr (std::is_same<Real, df64>::value && polarised(NS)) {
       // double-float: round the value to float64 once and weight it with the
       // float64 (cos, sin) pair (5 float64 operations per sample, not 9)
-      int pp[2][U], qq[2][U];
+      int pp[2][U], qq[2][U], ee[2][U];
       double2 cs[2][U];
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -577,6 +600,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
           }
           if constexpr (NS == NS_MR) qq[l][u] = ok[l][u] ? __ldg(L[l].pq + nn[u]) : -1;
           else qq[l][u] = pp[l][u];
+          if constexpr (extended(NS)) ee[l][u] = ok[l][u] ? __ldg(L[l].pe + nn[u]) : -1;
         }
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -588,6 +612,9 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
           atomicAdd(y + 4LL * pp[l][u], v);
           atomicAdd(y + 4LL * qq[l][u] + 1, v * cs[l][u].x);
           atomicAdd(y + 4LL * qq[l][u] + 2, v * cs[l][u].y);
+          if constexpr (extended(NS)) {
+            if (ee[l][u] >= 0) atomicAdd(y + 4LL * ee[l][u], v);
+          }
         }
     } else {
       int pp[2][U], qq[2][U];
@@ -597,13 +624,20 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
           load_pointing<Real, NS>(a, L[l], nn[u], ok[l][u], pp[l][u], cc[l][u], ss[l][u]);
-          if constexpr (NS == NS_MR) qq[l][u] = ok[l][u] ? __ldg(L[l].pq + nn[u]) : -1;
+          if constexpr (NS == NS_MR || extended(NS))
+            qq[l][u] = ok[l][u] ? __ldg((NS == NS_MR ? L[l].pq : L[l].pe) + nn[u]) : -1;
         }
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
           if (pp[l][u] < 0) continue;
+          if constexpr (extended(NS)) {   // the extra column's share (slot 0 of its row)
+            typedef typename OutT<Real>::type Out;
+            if (qq[l][u] >= 0)
+              atomicAdd(static_cast<Out*>(L[l].out) + (long long)qq[l][u] * (map_ns(NS) == 3 ? 4 : 1),
+                        (Out)to_out(val[l][u]));
+          }
           Real c = cc[l][u], sn = ss[l][u];
           if (polarised(NS) && !on_the_fly(NS)) finish_angle<Real>(c, sn);
           if constexpr (NS == NS_MR)
@@ -677,7 +711,7 @@ OpKernels pick_kernels(const Plan* p) {
   OpKernels k;
   // the multi-resolution and T on-the-fly modes keep only the generic column
   // kernels (fewer instances to compile)
-  constexpr bool generic_only = NS == NS_MR || NS == NS_OTF_T;
+  constexpr bool generic_only = NS == NS_MR || NS == NS_OTF_T || extended(NS);
   if constexpr (generic_only) {
     k.f1 = k_f1<Real, NS, IN, 0>;
     k.f3 = k_f3<Real, NS, OUT, 0>;
@@ -719,6 +753,7 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
   a.csdf = p->csdf;
   a.pw = p->pw;
   a.pixq = p->pix_obs_pol;
+  a.ext = p->ext_row;
   a.bore = p->otf ? p->bore : nullptr;
   a.det = p->det_pt;
   a.g2o = p->g2o;

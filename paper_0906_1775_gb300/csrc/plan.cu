@@ -479,6 +479,46 @@ __global__ void k_zero_excised_rows(int* pix_obs, long long n, const unsigned ch
   }
 }
 
+// ---------------------------------------------------------------- extended pointing
+__global__ void k_ext_rows(const int* extra_index, long long n, int n_sky, int* ext_row) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int e = extra_index[t];
+    ext_row[t] = e >= 0 ? n_sky + e : -1;
+  }
+}
+
+// Extra columns' sums over the samples whose row survives (sky pixel observed
+// and not excised): hits and B^T W^-1 B (= sum of f(0)).
+__global__ void k_accumulate_ext(const int* pix_obs, const int* ext_row, long long n, const long long* off, int n_ivl,
+                                 const int* ivl_filter, const double* f0, int n_sky, int* hits, double* acc) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int r = ext_row[t];
+    if (r < 0 || pix_obs[t] < 0) continue;
+    atomicAdd(hits + (r - n_sky), 1);
+    atomicAdd(acc + (r - n_sky), f0[ivl_filter[interval_of(off, n_ivl, t)]]);
+  }
+}
+
+// Scalar blocks of the extra rows (slot 0; the rest of the row's block is 0).
+__global__ void k_classify_ext(const double* acc, const int* hits, int n_extra, int n_sky, int ns, double* P64,
+                               float* P32, unsigned char* excised, unsigned char* fp64flag, int* counts) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_extra; e += gridDim.x * blockDim.x) {
+    const long long r = n_sky + e;
+    const bool ex = hits[e] == 0 || !(acc[e] > 0.0);
+    const double inv = ex ? 0.0 : 1.0 / acc[e];
+    if (ns == 1) {
+      P64[r] = inv;
+      P32[r] = (float)inv;
+    } else {
+      for (int k = 0; k < 6; ++k) P64[6 * r + k] = k == 0 ? inv : 0.0;
+      for (int k = 0; k < 8; ++k) P32[8 * r + k] = k == 0 ? (float)inv : 0.f;
+    }
+    excised[r] = ex;
+    fp64flag[r] = 0;
+    if (ex) atomicAdd(counts, 1);
+  }
+}
+
 // ---------------------------------------------------------------- multi-resolution preconditioner
 // Section 6 with the block diagonal of Section 5 on each pixelisation: a 2 x 2
 // (Q, U) block per polarisation pixel and a 1 x 1 block per intensity pixel;
@@ -890,7 +930,7 @@ static madmap_status build_preconditioner_mr(Plan* p, cudaStream_t s) {
 static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
   if (p->multires) return build_preconditioner_mr(p, s);
   const long long n = p->n_t;
-  const int n_obs = p->n_obs;
+  const int n_obs = p->ext ? p->n_obs_sky : p->n_obs;  // sky rows (extra rows follow)
   const int ns = p->n_stokes;
   const int nb = ns == 1 ? 1 : 6;
   const bool first = !p->pre_built;
@@ -924,12 +964,12 @@ static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
   if ((e = cudaMalloc(&doff, sizeof(long long) * (p->n_ivl + 1))) != cudaSuccess ||
       (e = cudaMalloc(&dfilt, sizeof(int) * std::max(1, p->n_ivl))) != cudaSuccess ||
       (e = cudaMalloc(&df0, sizeof(double) * p->n_filters)) != cudaSuccess ||
-      (e = cudaMalloc(&counts, sizeof(int) * 2)) != cudaSuccess) {
+      (e = cudaMalloc(&counts, sizeof(int) * 3)) != cudaSuccess) {
     cleanup();
     return cuda_fail(e, "cudaMalloc (preconditioner temporaries)");
   }
   cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)std::max(1, n_obs) * (ns == 1 ? 1 : 12), s);
-  cudaMemsetAsync(counts, 0, sizeof(int) * 2, s);
+  cudaMemsetAsync(counts, 0, sizeof(int) * 3, s);
   cudaMemcpyAsync(doff, p->offsets.data(), sizeof(long long) * (p->n_ivl + 1), cudaMemcpyHostToDevice, s);
   if (p->n_ivl) cudaMemcpyAsync(dfilt, p->ivl_filter.data(), sizeof(int) * p->n_ivl, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(df0, f0.data(), sizeof(double) * p->n_filters, cudaMemcpyHostToDevice, s);
@@ -951,14 +991,35 @@ static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
     if (first && n > 0) k_zero_excised_rows<<<grid_for(n), 256, 0, s>>>(p->pix_obs, n, p->excised);
     if (first && n > 0 && ns == 3) k_pack_pw<<<grid_for(n), 256, 0, s>>>(p->pix_obs, p->psi, n, p->pw);
   }
-  int hc[2] = {0, 0};
+  int* hits_e = nullptr;
+  double* acc_e = nullptr;
+  if (p->ext) {  // the extra columns, from the rows that survive the sky's excision
+    if ((e = cudaMalloc(&hits_e, sizeof(int) * p->n_extra)) != cudaSuccess ||
+        (e = cudaMalloc(&acc_e, sizeof(double) * p->n_extra)) != cudaSuccess) {
+      cudaFree(hits_e);
+      cudaFree(acc_e);
+      cleanup();
+      return cuda_fail(e, "cudaMalloc (preconditioner temporaries)");
+    }
+    cudaMemsetAsync(hits_e, 0, sizeof(int) * p->n_extra, s);
+    cudaMemsetAsync(acc_e, 0, sizeof(double) * p->n_extra, s);
+    if (n > 0)
+      k_accumulate_ext<<<grid_for(n), 256, 0, s>>>(p->pix_obs, p->ext_row, n, doff, p->n_ivl, dfilt, df0, n_obs,
+                                                    hits_e, acc_e);
+    k_classify_ext<<<grid_for(p->n_extra), 256, 0, s>>>(acc_e, hits_e, p->n_extra, n_obs, ns, p->P64, p->P32,
+                                                         p->excised, p->fp64flag, counts + 2);
+  }
+  int hc[3] = {0, 0, 0};
   e = cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaGetLastError();
+  cudaFree(hits_e);
+  cudaFree(acc_e);
   cleanup();
   if (e != cudaSuccess) return cuda_fail(e, "preconditioner build");
   p->n_excised = hc[0];
   p->n_fp64 = hc[1];
+  p->n_excised_extra = hc[2];
   p->pre_built = true;
   return st;
 }
@@ -1001,6 +1062,9 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
   }
   MM_CHECK(!d->pix_pol || (d->n_stokes == 3 && d->n_pix_pol > 0), MADMAP_ERR_INVALID_ARG,
            "pix_pol needs n_stokes = 3 and n_pix_pol > 0");
+  MM_CHECK(!d->extra_index || (d->n_extra >= 1 && !d->pix_pol && !d->boresight), MADMAP_ERR_INVALID_ARG,
+           "extra_index needs n_extra >= 1 and stored single-resolution pointing");
+  MM_CHECK(d->n_extra < (1 << 30), MADMAP_ERR_INVALID_ARG, "n_extra too large");
   MM_CHECK(d->n_intervals >= 0 && d->interval_offsets != nullptr, MADMAP_ERR_INVALID_ARG, "bad intervals");
   MM_CHECK(d->n_intervals == 0 || d->interval_filter != nullptr, MADMAP_ERR_INVALID_ARG, "interval_filter NULL");
   MM_CHECK(d->n_filters >= 1 && d->n_lags >= 1 && d->filter_lags != nullptr, MADMAP_ERR_INVALID_ARG,
@@ -1105,6 +1169,7 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
     }
     k_mark_bits<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, bits, d->pix_pol);
     if (p->multires) k_mark_bits<<<grid_for(n), 256, 0, s>>>(d->pix_pol, n, p->n_pix_pol, bits_pol, d->pix);
+    if (d->extra_index) k_validate_pix<<<grid_for(n), 256, 0, s>>>(d->extra_index, n, d->n_extra, p->dev_flag, 16);
   }
   k_scan_words<<<1, 1024, 0, s>>>(bits, n_words, prefix, total);
   if (p->multires) k_scan_words<<<1, 1024, 0, s>>>(bits_pol, n_words_pol, prefix_pol, total + 1);
@@ -1133,9 +1198,22 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
     set_error("boresight holds non-finite values");
     return MADMAP_ERR_INVALID_ARG;
   }
+  if (hv[0] & 16) {
+    delete p;
+    set_error("extra_index holds values outside [-1, n_extra)");
+    return MADMAP_ERR_INVALID_ARG;
+  }
   p->n_obs_i = hv[1];
   p->n_obs_pol = p->multires ? hv[2] : 0;
   p->n_obs = std::max(p->n_obs_i, p->n_obs_pol);  // map rows (slots for multi-resolution plans)
+  if (d->extra_index) {  // extended pointing: the extra columns' rows follow the sky rows
+    p->ext = true;
+    p->n_extra = d->n_extra;
+    p->n_obs_sky = p->n_obs_i;
+    p->n_obs = p->n_obs_i + p->n_extra;
+    MM_TRY(dalloc_t(p, &p->ext_row, std::max(1LL, n)));
+    if (n > 0) k_ext_rows<<<grid_for(n), 256, 0, s>>>(d->extra_index, n, p->n_obs_sky, p->ext_row);
+  }
   const int n_obs = p->n_obs;
   MM_TRY(dalloc_t(p, &p->obs2glob, std::max(1, p->n_obs_i)));
   MM_TRY(dalloc_t(p, &p->excised, std::max(1, n_obs)));
@@ -1262,6 +1340,8 @@ extern "C" madmap_status madmap_plan_get_stats(madmap_plan_t plan, madmap_plan_s
   o->device_bytes = (int64_t)(p->device_bytes + solve_buffer_bytes(p));
   o->n_obs_pol = p->n_obs_pol;
   o->n_excised_pol = p->n_excised_pol;
+  o->n_extra = p->n_extra;
+  o->n_excised_extra = p->n_excised_extra;
   return MADMAP_OK;
 }
 

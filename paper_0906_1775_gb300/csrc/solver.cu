@@ -1081,9 +1081,11 @@ static madmap_status resume_impl(Plan* p, const madmap_checkpoint* c, double* m,
 // out_t = alpha d_t + beta (A x)_t (float64 weights and map, float output);
 // pix_pol (multi-resolution plans, else NULL) gives the Q/U slot of each sample
 // (compressed pointing: ob.bore set, pix and cs unused)
+// (extended pointing: ext gives the map row of each sample's extra column, or -1)
 template <int NS>
 __global__ void k_unpoint(const double* x, const int* pix, const int* pix_pol, const double2* cs, const float* d,
-                          double alpha, double beta, float* out, long long n, const OtfPointing ob) {
+                          double alpha, double beta, float* out, long long n, const OtfPointing ob,
+                          const int* ext) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     float c2 = 0.f, s2 = 0.f;
     const int q = ob.bore ? otf_row(ob, t, NS == 3, c2, s2) : pix[t];
@@ -1096,6 +1098,7 @@ __global__ void k_unpoint(const double* x, const int* pix, const int* pix_pol, c
         const int qp = pix_pol ? pix_pol[t] : q;
         ax = x[4LL * q] + x[4LL * qp + 1] * w.x + x[4LL * qp + 2] * w.y;
       }
+      if (ext && ext[t] >= 0) ax += x[(long long)ext[t] * (NS == 1 ? 1 : 4)];
     }
     out[t] = (float)((d ? alpha * (double)d[t] : 0.0) + beta * ax);
   }
@@ -1221,10 +1224,10 @@ static madmap_status backward_impl(Plan* p, const float* d, const double* m, con
   count_launches(3);
   const int* pix_pol = p->multires ? p->pix_obs_pol : nullptr;
   k_unpoint<NS><<<std::max(1, gt), 256, 0, s>>>(lam, p->pix_obs, pix_pol, p->cs64, nullptr, 0.0, 1.0, p->bw_a, nt,
-                                                otf_pointing(p));
+                                                otf_pointing(p), p->ext_row);
   k_pack<double, double><<<grid_vec(nv), NT, 0, s>>>(m, sb64->t64, n, ns, np);
   k_unpoint<NS><<<std::max(1, gt), 256, 0, s>>>(sb64->t64, p->pix_obs, pix_pol, p->cs64, d, 1.0, -1.0, p->bw_r, nt,
-                                                otf_pointing(p));
+                                                otf_pointing(p), p->ext_row);
   if (grad_d) {
     st = op_launch(p, false, IN_TOD_REAL, OUT_TOD, p->bw_a, grad_d, 0, 0, 1, nullptr, s);
     if (st != MADMAP_OK) return st;
