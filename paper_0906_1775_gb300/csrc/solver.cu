@@ -1104,14 +1104,16 @@ __global__ void k_unpoint(const double* x, const int* pix, const int* pix_pol, c
   }
 }
 
-// zero the adjoint right-hand side at excised pixels (no row of H there);
-// excised_pol (multi-resolution plans, else NULL) covers the Q/U columns
+// zero the adjoint right-hand side at unknowns without a row of H: excised
+// pixels; excised_pol (multi-resolution plans, else NULL) covers the Q/U
+// columns; rows from first_extra on (extended pointing) keep column 0 only
 __global__ void k_mask_excised(double* b, long long nvec_pixels, int ns_pad, const unsigned char* excised,
-                               const unsigned char* excised_pol) {
+                               const unsigned char* excised_pol, long long first_extra) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvec_pixels * ns_pad;
        i += (long long)gridDim.x * blockDim.x) {
     const long long k = i / ns_pad;
-    const bool ex = (excised_pol && i % ns_pad != 0) ? excised_pol[k] : excised[k];
+    bool ex = (excised_pol && i % ns_pad != 0) ? excised_pol[k] : excised[k];
+    if (k >= first_extra && i % ns_pad != 0) ex = true;
     if (ex) b[i] = 0.0;
   }
 }
@@ -1213,7 +1215,8 @@ static madmap_status backward_impl(Plan* p, const float* d, const double* m, con
   // adjoint solve H lambda = dL/dm (zero at excised pixels)
   count_launches(2);
   k_pack<double, double><<<grid_vec(nv), NT, 0, s>>>(gm, sb64->b64, n, ns, np);
-  k_mask_excised<<<grid_vec(nv), NT, 0, s>>>(sb64->b64, n, np, p->excised, p->multires ? p->excised_pol : nullptr);
+  k_mask_excised<<<grid_vec(nv), NT, 0, s>>>(sb64->b64, n, np, p->excised, p->multires ? p->excised_pol : nullptr,
+                                             p->ext ? (long long)p->n_obs_sky : (long long)n);
   std::vector<madmap_solve_info> I(1);
   memset(&I[0], 0, sizeof(I[0]));
   const double* lam = nullptr;

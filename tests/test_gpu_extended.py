@@ -185,7 +185,17 @@ def test_backward_matches_oracle_adjoint(cases, case):
     gd, gl, _ = plan.solve_backward(cuda(d), m, cuda(g), precision="fp64", rel_tol=1e-12, max_iter=3000)
     ogd, ogl, _ = solve_backward(E, d.astype(np.float64), host(m), g)
     assert rel_rms(host(gd), ogd) < 2e-5
-    assert rel_rms(host(gl), ogl) < 2e-5
+    # The lag gradient sums products a_t r_t' (a = A lambda, r = d - A m) in float32:
+    # its error is a few 1e-7 of ||a|| ||r||.  With a white-noise filter the lag-0
+    # gradient vanishes at the ML map (A^T r = 0), so the bound is taken against
+    # ||a|| ||r|| rather than the gradient itself.
+    lam, _ = E.pcg(g * E.active(), rel_tol=1e-13, max_iter=3000)
+    a = E.unpoint(lam)
+    r = d.astype(np.float64) - E.unpoint(host(m))
+    err = float(np.linalg.norm(host(gl) - ogl))
+    assert err <= 2e-5 * max(float(np.linalg.norm(ogl)), float(np.linalg.norm(a) * np.linalg.norm(r)))
+    if case != "destripe_T":
+        assert rel_rms(host(gl), ogl) < 2e-5
 
 
 def test_set_filters_matches_new_plan(cases):
