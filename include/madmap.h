@@ -379,8 +379,9 @@ madmap_status madmap_solve_batched(madmap_plan_t plan, int32_t n_rhs, const floa
  * (both orders of each pair for t > 0; direct sums, float32 products with
  * float64 totals).  d: device float [n_samples]; m and grad_m: device double
  * [n_obs][n_stokes] (m the solution for d; grad_m is ignored at excised
- * pixels and at the unused columns of extended pointing's extra rows); grad_d: device float [n_samples] or NULL; grad_lags: device
- * double [n_filters][n_lags] or NULL.  opts/info as in madmap_solve, for the
+ * pixels and at the unused columns of extended pointing's extra rows);
+ * grad_d: device float [n_samples] or NULL; grad_lags: device double
+ * [n_filters][n_lags] or NULL.  opts/info as in madmap_solve, for the
  * adjoint solve.  Gradients with respect to PSD parameters follow by the
  * chain rule through madmap_noise_filter's dlags_out.  Synchronises `stream`. */
 madmap_status madmap_solve_backward(madmap_plan_t plan, const float* d, const double* m, const double* grad_m,
