@@ -47,6 +47,13 @@ struct Tile {
   int pad[3];
 };
 
+// White noise (one filter lag): a run of samples of one interval, weighted by
+// its filter's f(0) in a single pass (no windows, no FFT).
+struct DiagItem {
+  long long lo, hi;
+  int filter, pad;
+};
+
 // A list of tiles whose lanes name their right-hand side (batched solves).
 struct TileSet {
   Tile* tiles = nullptr;  // device
@@ -260,6 +267,11 @@ struct Plan {
   bool ext = false;
   int n_extra = 0, n_obs_sky = 0, n_excised_extra = 0;
   int* ext_row = nullptr;          // [n_t] map row of the sample's extra column (n_obs_sky + e) or -1
+  // white noise (n_lags == 1): the operator is one diagonal pass over sample runs
+  bool diag = false;
+  DiagItem* diag_items = nullptr;  // [n_diag_items]
+  int n_diag_items = 0;
+  double* f0_64 = nullptr;         // [n_filters] f(0) of each filter
   void* scratch = nullptr;         // scratch_slots * tiles_per_chunk * M complex (float64 size)
   int scratch_slots = 1;           // 2 when an application has several chunks (see op_stream)
   // An application of several chunks alternates them between two streams,

@@ -36,6 +36,11 @@ namespace mm {
 // Tiles are processed in n_chunks launches of (nearly) equal size, at most
 // tiles_per_chunk each, so no launch is left with a small tail of work.
 void chunking(const Plan* p, int& n_chunks, int& per_chunk, int n_tiles) {
+  if (n_tiles < 0 && p->diag) {  // one diagonal pass per application
+    n_chunks = p->n_tiles ? 1 : 0;
+    per_chunk = p->n_tiles;
+    return;
+  }
   if (n_tiles < 0) n_tiles = p->n_tiles;
   n_chunks = n_tiles ? (n_tiles + p->tiles_per_chunk - 1) / p->tiles_per_chunk : 0;
   per_chunk = n_chunks ? (n_tiles + n_chunks - 1) / n_chunks : 0;

@@ -650,6 +650,85 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
 }
 
 
+// ---------------------------------------------------------------- k_diag
+// White noise (one filter lag, e.g. destriping runs, Section 6 item 3): N^-1
+// is f(0) of the interval's filter times the identity, so the operator is a
+// single pass, gather -> weight -> scatter, with no windows and no FFT.  One
+// CTA per run of samples of one interval.
+template <typename Real, int NS>
+__device__ __forceinline__ Real sample_gather(const OpArgs& a, const LaneView<Real>& L, int n) {
+  int pp;
+  Real c, sn;
+  load_pointing<Real, NS>(a, L, n, true, pp, c, sn);
+  if (pp < 0) return Real(0);
+  if (polarised(NS) && !on_the_fly(NS)) finish_angle<Real>(c, sn);
+  const Real* x = static_cast<const Real*>(L.in);
+  if constexpr (NS == NS_MR) {
+    return gather_mr<Real>(x, pp, __ldg(L.pq + n), c, sn);
+  } else {
+    Real v = gather<Real, map_ns(NS)>(x, pp, c, sn);
+    if constexpr (extended(NS)) {
+      const int e = __ldg(L.pe + n);
+      if (e >= 0) v += x[(long long)e * (map_ns(NS) == 3 ? 4 : 1)];
+    }
+    return v;
+  }
+}
+
+template <typename Real, int NS>
+__device__ __forceinline__ void sample_scatter(const OpArgs& a, const LaneView<Real>& L, int n, Real val) {
+  typedef typename OutT<Real>::type Out;
+  int pp;
+  Real c, sn;
+  load_pointing<Real, NS>(a, L, n, true, pp, c, sn);
+  if (pp < 0) return;
+  Out* y = static_cast<Out*>(L.out);
+  if constexpr (extended(NS)) {
+    const int e = __ldg(L.pe + n);
+    if (e >= 0) atomicAdd(y + (long long)e * (map_ns(NS) == 3 ? 4 : 1), (Out)to_out(val));
+  }
+  if constexpr (std::is_same<Real, df64>::value && polarised(NS)) {
+    // as k_f3: the value rounded to float64 once, weighted by the float64 pair
+    double2 cs;
+    if constexpr (on_the_fly(NS)) cs = make_double2(to_double(c), to_double(sn));
+    else cs = L.cs[n];
+    const int q = NS == NS_MR ? __ldg(L.pq + n) : pp;
+    const double v = to_double(val);
+    atomicAdd(y + 4LL * pp, v);
+    atomicAdd(y + 4LL * q + 1, v * cs.x);
+    atomicAdd(y + 4LL * q + 2, v * cs.y);
+  } else {
+    if (polarised(NS) && !on_the_fly(NS)) finish_angle<Real>(c, sn);
+    if constexpr (NS == NS_MR) scatter_mr<Real>(y, pp, __ldg(L.pq + n), val, c, sn);
+    else scatter<Real, map_ns(NS)>(y, pp, val, c, sn);
+  }
+}
+
+template <typename Real, int NS, int IN, int OUT>
+__global__ void __launch_bounds__(256) k_diag(OpArgs a, const DiagItem* __restrict__ items, const double* f0) {
+  if (a.skip && *a.skip) return;
+  const DiagItem it = items[blockIdx.x];
+  Lane g;
+  g.ws = it.lo;
+  g.lo = it.lo;
+  g.hi = it.hi;
+  g.out_lo = 0;
+  g.out_hi = (int)(it.hi - it.lo);
+  g.rhs = 0;
+  const LaneView<Real> L = lane_view<Real, IN, OUT>(a, g);
+  const Real w0 = Real(f0[it.filter]);
+  const int len = (int)(it.hi - it.lo);
+  for (int n = threadIdx.x; n < len; n += blockDim.x) {
+    Real v;
+    if (IN == IN_MAPX) v = sample_gather<Real, NS>(a, L, n);
+    else if (IN == IN_TODF) v = (Real)__ldg(static_cast<const float*>(L.in) + n);
+    else v = static_cast<const Real*>(L.in)[n];
+    v = v * w0;
+    if (OUT == OUT_TOD) static_cast<Real*>(L.out)[n] = v;   // float and float64 only
+    else sample_scatter<Real, NS>(a, L, n, v);
+  }
+}
+
 template <typename Real>
 inline int elems_per_cta() {
   return sizeof(Real) == 4 ? 4096 : 2048;
@@ -776,6 +855,23 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
   MM_CUDA(set_smem(K.f1, sm13));
   MM_CUDA(set_smem(K.f3, sm13));
   MM_CUDA(set_smem(K.f2, sm2));
+  if (p->diag && !ts) {
+    // white noise: one diagonal pass per right-hand side (launch events as
+    // four per application so per-kernel timing keeps its layout)
+    for (int rep = 0; rep < reps; ++rep)
+      for (int r = 0; r < n_rhs; ++r) {
+        a.in = static_cast<const char*>(in) + (size_t)r * in_stride * (IN == IN_TODF ? sizeof(float) : sizeof(Real));
+        a.out = static_cast<char*>(out) + (size_t)r * out_stride * sizeof(typename OutT<Real>::type);
+        a.in_stride = a.out_stride = 0;
+        if (ev) cudaEventRecord(ev[4 * (rep * n_rhs + r)], s);
+        k_diag<Real, NS, IN, OUT><<<p->n_diag_items, 256, 0, s>>>(a, p->diag_items, p->f0_64);
+        if (ev)
+          for (int k = 1; k < 4; ++k) cudaEventRecord(ev[4 * (rep * n_rhs + r) + k], s);
+      }
+    count_launches((long long)n_rhs * reps);
+    MM_CUDA(cudaGetLastError());
+    return MADMAP_OK;
+  }
   int n_chunks, per_chunk;
   chunking(p, n_chunks, per_chunk, n_tiles);
   // several chunks: alternate two streams (own scratch slot each) so chunks overlap

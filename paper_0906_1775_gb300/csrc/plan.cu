@@ -1268,6 +1268,23 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
     tpc = std::min<long long>(tpc, 65535);
     p->tiles_per_chunk = (int)tpc;
   }
+  if (p->n_lags == 1) {
+    // white noise: runs of at most 2048 samples within each interval
+    std::vector<DiagItem> items;
+    for (int i = 0; i < p->n_ivl; ++i)
+      for (long long t = p->offsets[i]; t < p->offsets[i + 1]; t += 2048)
+        items.push_back({t, std::min(p->offsets[i + 1], t + 2048), p->ivl_filter[i], 0});
+    p->n_diag_items = (int)items.size();
+    MM_CHECK(items.size() < (1ULL << 31), MADMAP_ERR_INVALID_ARG, "too many samples for the white-noise pass");
+    MM_TRY(dalloc_t(p, &p->diag_items, std::max<size_t>(1, items.size())));
+    if (!items.empty())
+      MM_TRYC(cudaMemcpy(p->diag_items, items.data(), sizeof(DiagItem) * items.size(), cudaMemcpyHostToDevice));
+    std::vector<double> f0(p->n_filters);
+    for (int f = 0; f < p->n_filters; ++f) f0[f] = p->lags[f];
+    MM_TRY(dalloc_t(p, &p->f0_64, p->n_filters));
+    MM_TRYC(cudaMemcpy(p->f0_64, f0.data(), sizeof(double) * p->n_filters, cudaMemcpyHostToDevice));
+    p->diag = true;
+  }
   MM_TRY(dalloc_t(p, &p->tiles, std::max(1, p->n_tiles)));
   if (p->n_tiles)
     MM_TRYC(cudaMemcpy(p->tiles, p->host_tiles.data(), sizeof(Tile) * p->n_tiles, cudaMemcpyHostToDevice));
@@ -1397,6 +1414,9 @@ extern "C" madmap_status madmap_plan_set_filters(madmap_plan_t plan, const doubl
     p->lags = old;
     build_spectra(p);
     return st;
+  }
+  if (p->diag) {  // the white-noise pass reads f(0) directly
+    MM_CUDA(cudaMemcpy(p->f0_64, p->lags.data(), sizeof(double) * p->n_filters, cudaMemcpyHostToDevice));
   }
   // The block preconditioner weighs samples by f(0) of their filter: rebuild it.
   // Rows of excised pixels are already zero, so those pixels have no hits and

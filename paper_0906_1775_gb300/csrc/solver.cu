@@ -1550,7 +1550,7 @@ extern "C" madmap_status madmap_time_operator(madmap_plan_t plan, int32_t precis
   int n_chunks, per_chunk;
   chunking(p, n_chunks, per_chunk);
   if (launches_out)
-    for (int k = 0; k < 3; ++k) launches_out[k] = n_chunks;
+    for (int k = 0; k < 3; ++k) launches_out[k] = (p->diag && k > 0) ? 0 : n_chunks;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return op_time(p, prec, prec == OPP_DF64 ? (const void*)sb->xdf : sb->p, sb->q, reps, ms_out, s);
 }
