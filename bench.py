@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=3, help="oracle PCG iterations in the CPU baseline sample")
     ap.add_argument("--workload", default="config2", choices=["config2", "config1", "config3", "config4", "config5",
-                                                               "config2-boresight"],
+                                                               "config2-boresight", "config2-destripe"],
                     help="config2 (default) prints the headline line; the others print secondary measurements")
     ap.add_argument("--profile-step", type=float, default=0.0, metavar="TOL",
                     help="profiling runs: skip the reference map and tolerance search and run exactly one "
@@ -345,6 +345,60 @@ def run_secondary(args):
                      "reference": f"FP64 GPU solve to rel. residual 1e-10 ({rinfo['iters']} iterations)",
                      "workload_desc": "IQU all-sky ring scan, 32 det x 2^24 samples at 180 Hz, HEALPix Nside=512 "
                                       "RING, pointing periods 40-60 min, f_knee=0.03 Hz, alpha=1.7, n_c=2^15"})
+        plan.close()
+    elif args.workload == "config2-destripe":
+        # destriping run (white noise, one offset per 6000-sample baseline) over the
+        # IQU workload's pointing, next to the full noise model's operator
+        from synth.extended import add_extra_signal, baseline_index
+        p = make_config(2)
+        idx, n_extra = baseline_index(p.n_samples // 4, 4, 6000)
+        d_host = add_extra_signal(p.d[0], idx, np.random.default_rng(7).normal(0.0, 1.0, n_extra))
+        pix, psi = torch.from_numpy(p.pix).to(dev), torch.from_numpy(p.psi).to(dev)
+        eidx = torch.from_numpy(idx).to(dev)
+        white = np.ones((p.n_filters, 1))
+        plan = mm.Plan(pix, psi, p.n_pix, p.interval_offsets, p.interval_filter, white, extra_index=eidx,
+                       n_extra=n_extra)
+        if args.operator_only:      # a short run of the diagonal pass alone (for ncu)
+            ms, n = plan.time_operator("fp32", reps=args.operator_only)
+            print(json.dumps({"operator_only": "config2-destripe", "fp32_ms": [float(x) for x in ms],
+                              "launches": [int(x) for x in n]}), flush=True)
+            plan.close()
+            return
+        d = torch.from_numpy(d_host).to(dev)
+        ops = {}
+        for prec in ("fp32", "df64", "fp64"):
+            ms, n = plan.time_operator(prec, reps=20 if prec == "fp32" else 5)
+            ops[prec + "_ms"] = float(ms[3])
+        n_rows = plan.n_obs
+        b_alg = p.n_samples * (8 + 4) + 2 * n_rows * 4 * 4      # (pixel, angle) + extra index; map read + written
+        hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+        ref, rinfo = plan.solve(d, precision="fp64", rel_tol=1e-11, max_iter=5000)
+        ref_h = ref.cpu().numpy()
+        keep = np.ones(n_rows, dtype=bool)
+        keep[:n_rows - n_extra] = ~plan.observed()[1].cpu().numpy().astype(bool)
+        solves = {}
+        for prec, kw in (("mixed", dict(max_outer=30)), ("fp64", {})):
+            fn = lambda: plan.solve(d, precision=prec, rel_tol=1e-7, max_iter=5000, **kw)  # noqa: E731
+            fn()
+            ms_t, (m, info) = _timed(fn, steps)
+            err, per = stokes_err(m.cpu().numpy(), ref_h, keep)
+            solves[prec] = {"ms": ms_t, "iters": info["iters"], "map_err": err,
+                            "value": p.n_samples * info["iters"] / (ms_t / 1e3)}
+        full = mm.Plan(pix, psi, p.n_pix, p.interval_offsets, p.interval_filter, lib_lags(p), extra_index=eidx,
+                       n_extra=n_extra)
+        full_ms, _ = full.time_operator("fp32", reps=10)
+        full.close()
+        line.update({"n_samples": p.n_samples, "n_extra": n_extra, "rows": n_rows,
+                     "operator_diag": ops, "alg_bytes": int(b_alg),
+                     "hbm": {"achieved_gbs": b_alg / (ops["fp32_ms"] * 1e-3) / 1e9, "peak_gbs": hbm,
+                             "frac": b_alg / (ops["fp32_ms"] * 1e-3) / 1e9 / hbm},
+                     "operator_full_noise_fp32_ms": float(full_ms[3]),
+                     "speedup_destripe_vs_full_noise_operator": float(full_ms[3]) / ops["fp32_ms"],
+                     "solve_to_rel_res_1e-7": solves,
+                     "reference": f"FP64 GPU solve to rel. residual 1e-11 ({rinfo['iters']} iterations)",
+                     "workload_desc": "IQU destriping: the IQU workload's pointing (4 det x 2^22, 512x512), white "
+                                      "noise, offsets on 6000-sample baselines (one reference baseline)"})
         plan.close()
     elif args.workload == "config2-boresight":
         # the same scan planned twice: pointing expanded on the fly from the
