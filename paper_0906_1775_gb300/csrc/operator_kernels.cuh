@@ -156,6 +156,25 @@ __device__ __forceinline__ float to_out(float v) { return v; }
 __device__ __forceinline__ double to_out(double v) { return v; }
 __device__ __forceinline__ double to_out(df64 v) { return to_double(v); }
 
+// base[idx] += v for the calling lanes with one atomic per distinct idx in the
+// warp: lanes that share an address (an extra column of extended pointing is
+// shared by a whole baseline of consecutive samples) add up their values by
+// shuffles first, so no address takes a stream of atomics from one warp.
+template <typename Out>
+__device__ __forceinline__ void atomic_add_warp(Out* base, long long idx, Out v) {
+  const unsigned active = __activemask();
+  const unsigned peers = __match_any_sync(active, (unsigned long long)idx);
+  Out acc = Out(0);
+  if (peers == 0xffffffffu) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(peers, v, o);
+    acc = v;
+  } else {
+    for (unsigned m = peers; m; m &= m - 1) acc += __shfl_sync(peers, v, __ffs(m) - 1);
+  }
+  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(base + idx, acc);
+}
+
 // multi-resolution maps: I from slot p, Q and U from slot q
 template <typename Real>
 __device__ __forceinline__ Real gather_mr(const Real* x, int p, int q, Real c, Real s) {
@@ -613,7 +632,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
           atomicAdd(y + 4LL * qq[l][u] + 1, v * cs[l][u].x);
           atomicAdd(y + 4LL * qq[l][u] + 2, v * cs[l][u].y);
           if constexpr (extended(NS)) {
-            if (ee[l][u] >= 0) atomicAdd(y + 4LL * ee[l][u], v);
+            if (ee[l][u] >= 0) atomic_add_warp(y, 4LL * ee[l][u], v);
           }
         }
     } else {
@@ -635,8 +654,8 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
           if constexpr (extended(NS)) {   // the extra column's share (slot 0 of its row)
             typedef typename OutT<Real>::type Out;
             if (qq[l][u] >= 0)
-              atomicAdd(static_cast<Out*>(L[l].out) + (long long)qq[l][u] * (map_ns(NS) == 3 ? 4 : 1),
-                        (Out)to_out(val[l][u]));
+              atomic_add_warp(static_cast<Out*>(L[l].out), (long long)qq[l][u] * (map_ns(NS) == 3 ? 4 : 1),
+                              (Out)to_out(val[l][u]));
           }
           Real c = cc[l][u], sn = ss[l][u];
           if (polarised(NS) && !on_the_fly(NS)) finish_angle<Real>(c, sn);
@@ -685,7 +704,7 @@ __device__ __forceinline__ void sample_scatter(const OpArgs& a, const LaneView<R
   Out* y = static_cast<Out*>(L.out);
   if constexpr (extended(NS)) {
     const int e = __ldg(L.pe + n);
-    if (e >= 0) atomicAdd(y + (long long)e * (map_ns(NS) == 3 ? 4 : 1), (Out)to_out(val));
+    if (e >= 0) atomic_add_warp(y, (long long)e * (map_ns(NS) == 3 ? 4 : 1), (Out)to_out(val));
   }
   if constexpr (std::is_same<Real, df64>::value && polarised(NS)) {
     // as k_f3: the value rounded to float64 once, weighted by the float64 pair
