@@ -9,7 +9,13 @@ sample: column e_t = ``extra_index[t]`` (-1: none).  That covers
 * destriping offsets (item 3): e_t = the baseline interval of sample t, with
   N white (one filter lag, so no FFT is involved);
 * non-parametric synchronous signals (item 1): e_t = the bin of the sample's
-  synchronous parameter (e.g. a chopper angle).
+  synchronous parameter (e.g. a chopper angle);
+
+and, for the parametric half-wave-plate signal of item 2 (Eqs. 27-28), a
+dense block C of 32 columns per group of intervals: with the polariser angle
+w_t and the time variable tau_t of sample t, C_{t,k} = cos k w_t,
+C_{t,8+k} = tau_t cos k w_t, C_{t,16+k} = sin k w_t, C_{t,24+k} = tau_t sin k w_t
+for k = 1..8 (the paper's column order).
 
 Readings where the paper is silent:
 * A sample that is flagged (pixel -1) or whose sky pixel is excised has a zero
@@ -24,6 +30,12 @@ Readings where the paper is silent:
 * The system must be non-singular: offsets that cover every sample are
   degenerate with a constant I map, so the caller gives one baseline no
   offset (extra index -1), as destripers fix one offset.
+* Half-wave-plate parameters: each interval belongs to a group (-1: none)
+  with its own 32 parameters; tau_t is supplied by the caller (its origin and
+  unit are the caller's choice); the preconditioner of each parameter is the
+  scalar 1 / sum_t f(0) C_{t,i}^2 (the paper gives none for templates; the
+  32 x 32 block is not formed); a parameter with a zero sum is excised.
+  Their rows follow the extra columns' rows, one row per parameter (slot 0).
 
 Pinned by tests/test_oracle_pins.py::test_extended_* (reduction to the plain
 system without extra columns, dense Cholesky and symmetry, noiseless recovery
@@ -40,14 +52,18 @@ from .solver import System, pcg as _pcg
 
 class ExtendedSystem:
     def __init__(self, pix, psi, n_pix, n_stokes, offsets, ivl_filter, lags, extra_index, n_extra,
-                 rcond_excise=1e-6, rcond_fp64=1e-2, ninv="fft", n_f=None, weights=None):
+                 rcond_excise=1e-6, rcond_fp64=1e-2, ninv="fft", n_f=None, weights=None, hwp=None):
+        """hwp (optional): (angle float32 [n_t], tau float32 [n_t], group of each interval [n_ivl],
+        n_groups) for the 32-parameter half-wave-plate model."""
         self.sky = System(pix, psi, n_pix, n_stokes, offsets, ivl_filter, lags, rcond_excise=rcond_excise,
                           rcond_fp64=rcond_fp64, ninv=ninv, n_f=n_f, weights=weights)
         S = self.sky
         self.n_s = S.n_s
         self.n_sky = S.n_obs
         self.n_extra = int(n_extra)
-        self.n_obs = self.n_sky + self.n_extra
+        self.n_groups = int(hwp[3]) if hwp is not None else 0
+        self.n_hwp = 32 * self.n_groups
+        self.n_obs = self.n_sky + self.n_extra + self.n_hwp
         self.obs2glob, self.excised_sky = S.obs2glob, S.excised
         e = np.asarray(extra_index, dtype=np.int64)
         # rows that are zero in A (flagged or excised sky pixel) are zero in B too
@@ -60,6 +76,26 @@ class ExtendedSystem:
         self.excised_extra = self.hits_extra == 0
         with np.errstate(divide="ignore"):
             self.p_extra = np.where(self.excised_extra, 0.0, 1.0 / np.where(self.excised_extra, 1.0, wsum))
+        # half-wave-plate block: group of every sample (-1 where its row is zero) and C
+        if self.n_groups:
+            ang, tau, grp, _ = hwp
+            g = np.repeat(np.asarray(grp, dtype=np.int64), lengths)
+            self.hg = np.where(S.pixl >= 0, g, -1)
+            self.C = hwp_columns(ang, tau)                       # [n_t, 32] float64
+            okh = self.hg >= 0
+            csum = np.zeros((self.n_groups, 32))
+            for i in range(32):
+                csum[:, i] = np.bincount(self.hg[okh], weights=f0[okh] * self.C[okh, i] ** 2,
+                                         minlength=self.n_groups)
+            csum = csum.reshape(-1)
+            self.excised_hwp = ~(csum > 0)
+            with np.errstate(divide="ignore"):
+                self.p_hwp = np.where(self.excised_hwp, 0.0, 1.0 / np.where(self.excised_hwp, 1.0, csum))
+        else:
+            self.hg = np.full(e.shape[0], -1, dtype=np.int64)
+            self.C = None
+            self.excised_hwp = np.zeros(0, dtype=bool)
+            self.p_hwp = np.zeros(0)
 
     # the noise description (as the plain system's)
     offsets = property(lambda self: self.sky.offsets)
@@ -72,26 +108,40 @@ class ExtendedSystem:
         """[n_obs + n_extra, n_s] mask of the unknowns that exist."""
         m = np.zeros((self.n_obs, self.n_s), dtype=bool)
         m[:self.n_sky] = ~self.excised_sky[:, None]
-        m[self.n_sky:, 0] = ~self.excised_extra
+        m[self.n_sky:self.n_sky + self.n_extra, 0] = ~self.excised_extra
+        m[self.n_sky + self.n_extra:, 0] = ~self.excised_hwp
         return m
 
     def split(self, x):
+        """(sky [n_sky, n_s], extra amplitudes [n_extra], half-wave-plate parameters [n_groups, 32])."""
         x = np.asarray(x, dtype=np.float64).reshape(self.n_obs, self.n_s)
-        return x[:self.n_sky], x[self.n_sky:, 0]
+        e0 = self.n_sky + self.n_extra
+        return x[:self.n_sky], x[self.n_sky:e0, 0], x[e0:, 0].reshape(self.n_groups, 32)
 
     # ---------------------------------------------------------------- operators
     def unpoint(self, x):
-        z, o = self.split(x)
+        z, o, b = self.split(x)
         y = self.sky.unpoint(z)
         ok = self.ex >= 0
         y[ok] += o[self.ex[ok]]
+        if self.n_groups:
+            okh = self.hg >= 0
+            y[okh] += np.einsum("ti,ti->t", self.C[okh], b[self.hg[okh]])
         return y
 
     def point(self, y):
+        y = np.asarray(y, dtype=np.float64)
         out = np.zeros((self.n_obs, self.n_s))
         out[:self.n_sky] = self.sky.point(y)
         ok = self.ex >= 0
-        out[self.n_sky:, 0] = np.bincount(self.ex[ok], weights=np.asarray(y)[ok], minlength=self.n_extra)
+        e0 = self.n_sky + self.n_extra
+        out[self.n_sky:e0, 0] = np.bincount(self.ex[ok], weights=y[ok], minlength=self.n_extra)
+        if self.n_groups:
+            okh = self.hg >= 0
+            hb = np.zeros((self.n_groups, 32))
+            for i in range(32):
+                hb[:, i] = np.bincount(self.hg[okh], weights=y[okh] * self.C[okh, i], minlength=self.n_groups)
+            out[e0:, 0] = hb.reshape(-1)
         return out
 
     def ninv(self, y):
@@ -107,8 +157,10 @@ class ExtendedSystem:
     def precond(self, r):
         r = np.asarray(r, dtype=np.float64).reshape(self.n_obs, self.n_s)
         out = np.zeros_like(r)
+        e0 = self.n_sky + self.n_extra
         out[:self.n_sky] = self.sky.precond(r[:self.n_sky])
-        out[self.n_sky:, 0] = self.p_extra * r[self.n_sky:, 0]
+        out[self.n_sky:e0, 0] = self.p_extra * r[self.n_sky:e0, 0]
+        out[e0:, 0] = self.p_hwp * r[e0:, 0]
         return out
 
     def pcg(self, b, rel_tol=1e-6, max_iter=50, keep_history=False):
@@ -133,6 +185,9 @@ class ExtendedSystem:
                 A[t, p * self.n_s:(p + 1) * self.n_s] = S.w[t]
             if self.ex[t] >= 0:
                 A[t, (self.n_sky + self.ex[t]) * self.n_s] = 1.0
+            if self.hg[t] >= 0:
+                base = self.n_sky + self.n_extra + 32 * self.hg[t]
+                A[t, (base + np.arange(32)) * self.n_s] = self.C[t]
         N = _noise.dense_ninv(S.offsets, S.ivl_filter, S.lags)
         return A, N, A.T @ N @ A
 
@@ -145,3 +200,12 @@ class ExtendedSystem:
         L = np.linalg.cholesky(H[np.ix_(keep, keep)])
         x[keep] = np.linalg.solve(L.T, np.linalg.solve(L, b[keep]))
         return x.reshape(self.n_obs, self.n_s)
+
+
+def hwp_columns(angle, tau):
+    """The 32 columns of Eq. 28 for every sample, float64 from the float32 inputs."""
+    w = np.asarray(angle, dtype=np.float32).astype(np.float64)
+    t = np.asarray(tau, dtype=np.float32).astype(np.float64)
+    k = np.arange(1, 9)
+    c, s = np.cos(np.outer(w, k)), np.sin(np.outer(w, k))
+    return np.concatenate([c, t[:, None] * c, s, t[:, None] * s], axis=1)

@@ -699,7 +699,7 @@ def test_extended_destriping_recovers_sky_and_offsets():
     white = np.array([[1.0]])
     E = _ext_system(p, idx, n_extra, lags=white, ninv="direct")
     x, info = E.solve(d, rel_tol=1e-14, max_iter=3000)
-    z, oo = E.split(x)
+    z, oo, _ = E.split(x)
     keep = ~E.excised_sky
     assert rel_rms(z[keep, 0], p.sky[E.obs2glob[keep], 0]) < 1e-6       # d is float32
     assert rel_rms(oo, o) < 1e-6
@@ -715,8 +715,53 @@ def test_extended_binned_template_recovery():
     d = add_extra_signal(p.d[0], idx, amp)
     E = _ext_system(p, idx, n_extra)
     x, _ = E.solve(d, rel_tol=1e-14, max_iter=3000)
-    z, oo = E.split(x)
+    z, oo, _ = E.split(x)
     keep = ~E.excised_sky
     for s in range(3):
         assert rel_rms(z[keep, s], p.sky[E.obs2glob[keep], s]) < 1e-5
     assert rel_rms(oo, amp) < 1e-5
+
+
+def _hwp_case(seed, noiseless=True, n_per=1500):
+    from synth.extended import add_hwp_signal, hwp_inputs
+    p = tiny_IQU(seed=seed, n_per_det=n_per, width=5, noiseless=noiseless, n_ivl_lo=500, n_ivl_hi=1500)
+    ang, tau, grp, n_groups = hwp_inputs(p.interval_offsets, p.fs, 1.3, np.random.default_rng(seed))
+    b = np.random.default_rng(seed + 1).normal(0.0, 0.3, (n_groups, 32))
+    d = add_hwp_signal(p.d[0], p.interval_offsets, ang, tau, grp, b)
+    return p, (ang, tau, grp, n_groups), b, d
+
+
+def test_extended_hwp_noiseless_recovery():
+    """An injected half-wave-plate signal (Eqs. 27-28, synthesised as the real part of a
+    complex-exponential sum) and an IQU sky, noiseless: both are recovered."""
+    p, hwp, b, d = _hwp_case(61)
+    E = _ext_system(p, np.full(p.n_samples, -1, np.int32), 1, hwp=hwp)
+    x, info = E.solve(d, rel_tol=1e-14, max_iter=5000)
+    z, _, bb = E.split(x)
+    keep = ~E.excised_sky
+    for s in range(3):
+        assert rel_rms(z[keep, s], p.sky[E.obs2glob[keep], s]) < 1e-5
+    assert rel_rms(bb, b) < 1e-5
+
+
+def test_extended_hwp_dense_cholesky_symmetry_and_reduction():
+    from synth.extended import baseline_index
+    p, hwp, b, d = _hwp_case(62, noiseless=False, n_per=400)
+    idx, n_extra = baseline_index(400, 4, 100)
+    E = _ext_system(p, idx, n_extra, hwp=hwp)
+    xd = E.dense_solve(d)
+    xp, info = E.solve(d, rel_tol=1e-13, max_iter=5000)
+    act = E.active()
+    assert info["best_res"] < 1e-12 and rel_rms(xp[act], xd[act]) < 1e-8
+    rng = np.random.default_rng(3)
+    x, y = rng.standard_normal((2, E.n_obs, 3)) * act
+    a, c = float(np.sum(y * E.H(x))), float(np.sum(x * E.H(y)))
+    assert abs(a - c) <= 1e-12 * abs(a)
+    # every group switched off: the system without the half-wave-plate block
+    ang, tau, grp, ng = hwp
+    E0 = _ext_system(p, idx, n_extra, hwp=(ang, tau, np.full_like(grp, -1), ng))
+    E1 = _ext_system(p, idx, n_extra)
+    x1 = rng.standard_normal((E1.n_obs, 3)) * E1.active()
+    x0 = np.zeros((E0.n_obs, 3))
+    x0[:E1.n_obs] = x1
+    assert np.allclose(E0.H(x0)[:E1.n_obs], E1.H(x1), rtol=1e-12, atol=1e-12) and E0.excised_hwp.all()
