@@ -134,6 +134,18 @@ typedef struct {
   const int32_t* extra_index;       /* device [n_samples]: extra column of each sample in
                                        [0, n_extra), or -1 (none); NULL: no extra columns */
   int32_t n_extra;                  /* extra columns (>= 1 when extra_index is set) */
+  /* Parametric half-wave-plate signal (Section 6, Eqs. 27-28), with or without
+   * extra_index, stored single-resolution pointing only: 32 unknowns per group
+   * of intervals, b_1..b_32 with the sample's columns cos k w, tau cos k w,
+   * sin k w, tau sin k w (k = 1..8, in that order), w = hwp_angle, tau =
+   * hwp_tau.  Their rows follow the extra columns' rows (32 per group, the
+   * parameter in column 0).  Each parameter's preconditioner block is
+   * 1 / sum_t f(0) C_{t,i}^2; a parameter with a zero sum is excised. */
+  const float* hwp_angle;           /* device [n_samples]: polariser angle w (radians); NULL: none */
+  const float* hwp_tau;             /* device [n_samples]: the model's time variable (caller's units) */
+  const int32_t* interval_hwp_group;/* host [n_intervals]: group of each interval in [0, n_hwp_groups)
+                                       or -1 (no half-wave-plate term) */
+  int32_t n_hwp_groups;             /* >= 1 when hwp_angle is set */
 } madmap_plan_desc;
 
 typedef struct {
@@ -155,6 +167,8 @@ typedef struct {
   int32_t n_extra;         /* extended pointing: extra columns (rows n_obs - n_extra .. n_obs - 1 of
                               the map), else 0 */
   int32_t n_excised_extra; /* extended pointing: extra columns without samples */
+  int32_t n_hwp_params;    /* half-wave-plate parameters (32 per group; the last rows of the map) */
+  int32_t n_excised_hwp;   /* half-wave-plate parameters without weight */
 } madmap_plan_stats;
 
 typedef struct {

@@ -270,11 +270,14 @@ class Plan:
     unit-weight extra column per sample (destriping offsets, binned templates):
     maps then have n_obs = sky rows + n_extra rows, the extra amplitudes in
     column 0 of the last n_extra rows.
+    hwp = (angle, tau, interval_group, n_groups) adds the 32-parameter half-wave-plate
+    model per group of intervals (angle, tau: float32 CUDA tensors [n_t]; interval_group:
+    host int32 [n_ivl], -1 = none): 32 * n_groups more rows after the extra rows.
     """
 
     def __init__(self, pix, psi, n_pix, interval_offsets, interval_filter, filter_lags, rcond_excise=0.0,
                  rcond_fp64=0.0, fft_len=0, tiles_per_chunk=0, stream=None, pix_pol=None, n_pix_pol=0,
-                 extra_index=None, n_extra=0):
+                 extra_index=None, n_extra=0, hwp=None):
         torch = _torch()
         self._h = None
         off = np.ascontiguousarray(interval_offsets, dtype=np.int64)
@@ -308,7 +311,22 @@ class Plan:
             keep_extra = extra_index if n_t else torch.full((1,), -1, dtype=torch.int32, device="cuda")
             d.extra_index = _dev_ptr(keep_extra, torch.int32, "extra_index")
             d.n_extra = int(n_extra)
-        self._keep = (off, filt, lags)
+        keep_hwp = None
+        if hwp is not None:
+            ang, tau, grp, n_groups = hwp
+            grp = np.ascontiguousarray(grp, dtype=np.int32)
+            if int(ang.numel()) != n_t or int(tau.numel()) != n_t or grp.shape[0] != filt.shape[0]:
+                raise ValueError("hwp angle and tau need one entry per sample, interval_group one per interval")
+            if n_t:
+                d.hwp_angle = _dev_ptr(ang, torch.float32, "hwp angle")
+                d.hwp_tau = _dev_ptr(tau, torch.float32, "hwp tau")
+            else:
+                keep_hwp = torch.zeros(1, dtype=torch.float32, device="cuda")
+                d.hwp_angle = d.hwp_tau = _dev_ptr(keep_hwp, torch.float32, "hwp")
+            d.interval_hwp_group = grp.ctypes.data if grp.size else np.zeros(1, np.int32).ctypes.data
+            d.n_hwp_groups = int(n_groups)
+            keep_hwp = (keep_hwp, grp)
+        self._keep = (off, filt, lags, keep_hwp)
         self.multires = pix_pol is not None
         self._create(d, n_t, stream)
 

@@ -40,7 +40,9 @@ class madmap_plan_desc(C.Structure):
                 ("tiles_per_chunk", C.c_int32), ("pix_pol", C.c_void_p), ("n_pix_pol", C.c_int32),
                 ("boresight", C.c_void_p), ("n_bore", C.c_int32), ("bore_step", C.c_int32),
                 ("det_pointing", C.c_void_p), ("n_det", C.c_int32), ("grid_width", C.c_int32),
-                ("grid_height", C.c_int32), ("extra_index", C.c_void_p), ("n_extra", C.c_int32)]
+                ("grid_height", C.c_int32), ("extra_index", C.c_void_p), ("n_extra", C.c_int32),
+                ("hwp_angle", C.c_void_p), ("hwp_tau", C.c_void_p), ("interval_hwp_group", C.c_void_p),
+                ("n_hwp_groups", C.c_int32)]
 
 
 class madmap_plan_stats(C.Structure):
@@ -48,7 +50,8 @@ class madmap_plan_stats(C.Structure):
                                          "n2", "n_segments", "n_tiles", "tiles_per_chunk", "n_lags",
                                          "n_filters")] + [("n_samples", C.c_int64), ("device_bytes", C.c_int64),
                                                           ("n_obs_pol", C.c_int32), ("n_excised_pol", C.c_int32),
-                                                          ("n_extra", C.c_int32), ("n_excised_extra", C.c_int32)]
+                                                          ("n_extra", C.c_int32), ("n_excised_extra", C.c_int32),
+                                                          ("n_hwp_params", C.c_int32), ("n_excised_hwp", C.c_int32)]
 
 
 class madmap_checkpoint(C.Structure):

@@ -192,6 +192,48 @@ __device__ __forceinline__ int expand_pointing(const float4* __restrict__ bore, 
   return ok ? (int)fy * W + (int)fx : -1;
 }
 
+// base[idx] += v for the calling lanes with one atomic per distinct idx in the
+// warp: lanes that share an address (an extra column of extended pointing is
+// shared by a whole baseline of consecutive samples, a half-wave-plate
+// parameter by a whole interval) add up their values by shuffles first, so no
+// address takes a stream of atomics from one warp.
+template <typename Out>
+__device__ __forceinline__ void atomic_add_warp(Out* base, long long idx, Out v) {
+  const unsigned active = __activemask();
+  const unsigned peers = __match_any_sync(active, (unsigned long long)idx);
+  Out acc = Out(0);
+  if (peers == 0xffffffffu) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(peers, v, o);
+    acc = v;
+  } else {
+    for (unsigned m = peers; m; m &= m - 1) acc += __shfl_sync(peers, v, __ffs(m) - 1);
+  }
+  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(base + idx, acc);
+}
+
+// Half-wave-plate columns of one sample (Section 6, Eq. 28), in the column
+// order b_1..b_32: cos k w, tau cos k w, sin k w, tau sin k w for k = 1..8.
+// The harmonics come from one sincos by the angle-addition recurrence.
+template <typename W>
+__device__ __forceinline__ void hwp_columns(float w, float tau, W* C) {
+  W c1, s1;
+  if constexpr (sizeof(W) == 4) sincosf(w, &s1, &c1);
+  else sincos((double)w, &s1, &c1);
+  W c = c1, s = s1;
+  const W t = (W)tau;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    C[k] = c;
+    C[8 + k] = t * c;
+    C[16 + k] = s;
+    C[24 + k] = t * s;
+    const W cn = c * c1 - s * s1;
+    s = s * c1 + c * s1;
+    c = cn;
+  }
+}
+
 // The compressed pointing of a plan as kernel arguments (bore == NULL: the
 // plan stores per-sample pointing instead).
 struct OtfPointing {
@@ -267,6 +309,11 @@ struct Plan {
   bool ext = false;
   int n_extra = 0, n_obs_sky = 0, n_excised_extra = 0;
   int* ext_row = nullptr;          // [n_t] map row of the sample's extra column (n_obs_sky + e) or -1
+  // half-wave-plate parameters (32 rows per group after the extra rows)
+  int n_hwp_groups = 0, hwp_row0 = 0, n_excised_hwp = 0;
+  float* hwp_ang = nullptr;        // [n_t] polariser angle
+  float* hwp_tau = nullptr;        // [n_t] the model's time variable
+  int* hwp_base = nullptr;         // [n_t] first row of the sample's group, or -1
   // white noise (n_lags == 1): the operator is one diagonal pass over sample runs
   bool diag = false;
   DiagItem* diag_items = nullptr;  // [n_diag_items]

@@ -80,7 +80,10 @@ struct OpArgs {
   const float4* csdf;
   const int2* pw;      // (pixel, angle bits) per sample, IQU
   const int* pixq;     // Q/U pixel per sample (multi-resolution plans)
-  const int* ext;      // extra column's map row per sample (extended pointing)
+  const int* ext;      // extra column's map row per sample (extended pointing), or NULL
+  const int* hwp_base; // first half-wave-plate row of the sample's group (or -1), or NULL
+  const float* hwp_ang;
+  const float* hwp_tau;
   // compressed pointing (on-the-fly modes)
   const float4* bore;
   const float4* det;
@@ -156,23 +159,29 @@ __device__ __forceinline__ float to_out(float v) { return v; }
 __device__ __forceinline__ double to_out(double v) { return v; }
 __device__ __forceinline__ double to_out(df64 v) { return to_double(v); }
 
-// base[idx] += v for the calling lanes with one atomic per distinct idx in the
-// warp: lanes that share an address (an extra column of extended pointing is
-// shared by a whole baseline of consecutive samples) add up their values by
-// shuffles first, so no address takes a stream of atomics from one warp.
-template <typename Out>
-__device__ __forceinline__ void atomic_add_warp(Out* base, long long idx, Out v) {
-  const unsigned active = __activemask();
-  const unsigned peers = __match_any_sync(active, (unsigned long long)idx);
-  Out acc = Out(0);
-  if (peers == 0xffffffffu) {
+// Half-wave-plate term of sample n of a lane (rows hb.. hb+31, column 0):
+// gather sum_i C_i x_i, or scatter v C_i into each parameter.  Float32
+// kernels take the columns in float32, the others in float64.
+template <typename Real>
+__device__ __forceinline__ Real hwp_gather(const Real* x, int hb, int stride, float w, float tau) {
+  typedef typename std::conditional<std::is_same<Real, float>::value, float, double>::type W;
+  W C[32];
+  hwp_columns<W>(w, tau, C);
+  W acc = W(0);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(peers, v, o);
-    acc = v;
-  } else {
-    for (unsigned m = peers; m; m &= m - 1) acc += __shfl_sync(peers, v, __ffs(m) - 1);
+  for (int i = 0; i < 32; ++i) {
+    const Real xi = x[(long long)(hb + i) * stride];
+    if constexpr (std::is_same<Real, df64>::value) acc += C[i] * to_double(xi);
+    else acc += C[i] * (W)xi;
   }
-  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(base + idx, acc);
+  return Real(acc);
+}
+template <typename Out>
+__device__ __forceinline__ void hwp_scatter(Out* y, int hb, int stride, float w, float tau, Out v) {
+  Out C[32];
+  hwp_columns<Out>(w, tau, C);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) atomic_add_warp(y, (long long)(hb + i) * stride, v * C[i]);
 }
 
 // multi-resolution maps: I from slot p, Q and U from slot q
@@ -240,6 +249,9 @@ struct LaneView {
   const int2* pw;
   const int* pq;
   const int* pe;
+  const int* hb;
+  const float* hang;
+  const float* htau;
   const void* in;
   void* out;
   int j0;        // on-the-fly pointing: detector sample of window position 0
@@ -264,6 +276,9 @@ __device__ __forceinline__ LaneView<Real> lane_view(const OpArgs& a, const Lane&
   v.pw = a.pw + ws;
   v.pq = a.pixq ? a.pixq + ws : nullptr;
   v.pe = a.ext ? a.ext + ws : nullptr;
+  v.hb = a.hwp_base ? a.hwp_base + ws : nullptr;
+  v.hang = a.hwp_ang ? a.hwp_ang + ws : nullptr;
+  v.htau = a.hwp_tau ? a.hwp_tau + ws : nullptr;
   if (a.bore) {
     // windows never leave their interval's detector
     long long dd = a.n_per_det > 0 ? g.lo / a.n_per_det : 0;
@@ -442,8 +457,10 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
           load_pointing<Real, NS>(a, L[l], nn[u], ok[l][u], pp[l][u], cc[l][u], ss[l][u]);
-          if constexpr (NS == NS_MR || extended(NS))
-            qq[l][u] = ok[l][u] ? __ldg((NS == NS_MR ? L[l].pq : L[l].pe) + nn[u]) : -1;
+          if constexpr (NS == NS_MR || extended(NS)) {
+            const int* qp = NS == NS_MR ? L[l].pq : L[l].pe;
+            qq[l][u] = (ok[l][u] && qp) ? __ldg(qp + nn[u]) : -1;
+          }
         }
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -458,6 +475,12 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
             v[l][u] = pp[l][u] >= 0 ? gather<Real, map_ns(NS)>(x, pp[l][u], c, sn) : Real(0);
             if constexpr (extended(NS)) {   // + the extra column's amplitude (slot 0 of its row)
               if (pp[l][u] >= 0 && qq[l][u] >= 0) v[l][u] += x[(long long)qq[l][u] * (map_ns(NS) == 3 ? 4 : 1)];
+              if (pp[l][u] >= 0 && L[l].hb) {   // + the half-wave-plate term
+                const int hb = __ldg(L[l].hb + nn[u]);
+                if (hb >= 0)
+                  v[l][u] += hwp_gather<Real>(x, hb, map_ns(NS) == 3 ? 4 : 1, __ldg(L[l].hang + nn[u]),
+                                              __ldg(L[l].htau + nn[u]));
+              }
             }
           }
         }
@@ -619,7 +642,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
           }
           if constexpr (NS == NS_MR) qq[l][u] = ok[l][u] ? __ldg(L[l].pq + nn[u]) : -1;
           else qq[l][u] = pp[l][u];
-          if constexpr (extended(NS)) ee[l][u] = ok[l][u] ? __ldg(L[l].pe + nn[u]) : -1;
+          if constexpr (extended(NS)) ee[l][u] = (ok[l][u] && L[l].pe) ? __ldg(L[l].pe + nn[u]) : -1;
         }
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -633,6 +656,10 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
           atomicAdd(y + 4LL * qq[l][u] + 2, v * cs[l][u].y);
           if constexpr (extended(NS)) {
             if (ee[l][u] >= 0) atomic_add_warp(y, 4LL * ee[l][u], v);
+            if (L[l].hb) {
+              const int hb = __ldg(L[l].hb + nn[u]);
+              if (hb >= 0) hwp_scatter<double>(y, hb, 4, __ldg(L[l].hang + nn[u]), __ldg(L[l].htau + nn[u]), v);
+            }
           }
         }
     } else {
@@ -643,8 +670,10 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
           load_pointing<Real, NS>(a, L[l], nn[u], ok[l][u], pp[l][u], cc[l][u], ss[l][u]);
-          if constexpr (NS == NS_MR || extended(NS))
-            qq[l][u] = ok[l][u] ? __ldg((NS == NS_MR ? L[l].pq : L[l].pe) + nn[u]) : -1;
+          if constexpr (NS == NS_MR || extended(NS)) {
+            const int* qp = NS == NS_MR ? L[l].pq : L[l].pe;
+            qq[l][u] = (ok[l][u] && qp) ? __ldg(qp + nn[u]) : -1;
+          }
         }
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -656,6 +685,12 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
             if (qq[l][u] >= 0)
               atomic_add_warp(static_cast<Out*>(L[l].out), (long long)qq[l][u] * (map_ns(NS) == 3 ? 4 : 1),
                               (Out)to_out(val[l][u]));
+            if (L[l].hb) {
+              const int hb = __ldg(L[l].hb + nn[u]);
+              if (hb >= 0)
+                hwp_scatter<Out>(static_cast<Out*>(L[l].out), hb, map_ns(NS) == 3 ? 4 : 1, __ldg(L[l].hang + nn[u]),
+                                 __ldg(L[l].htau + nn[u]), (Out)to_out(val[l][u]));
+            }
           }
           Real c = cc[l][u], sn = ss[l][u];
           if (polarised(NS) && !on_the_fly(NS)) finish_angle<Real>(c, sn);
@@ -687,8 +722,10 @@ __device__ __forceinline__ Real sample_gather(const OpArgs& a, const LaneView<Re
   } else {
     Real v = gather<Real, map_ns(NS)>(x, pp, c, sn);
     if constexpr (extended(NS)) {
-      const int e = __ldg(L.pe + n);
+      const int e = L.pe ? __ldg(L.pe + n) : -1;
       if (e >= 0) v += x[(long long)e * (map_ns(NS) == 3 ? 4 : 1)];
+      const int hb = L.hb ? __ldg(L.hb + n) : -1;
+      if (hb >= 0) v += hwp_gather<Real>(x, hb, map_ns(NS) == 3 ? 4 : 1, __ldg(L.hang + n), __ldg(L.htau + n));
     }
     return v;
   }
@@ -703,8 +740,11 @@ __device__ __forceinline__ void sample_scatter(const OpArgs& a, const LaneView<R
   if (pp < 0) return;
   Out* y = static_cast<Out*>(L.out);
   if constexpr (extended(NS)) {
-    const int e = __ldg(L.pe + n);
+    const int e = L.pe ? __ldg(L.pe + n) : -1;
     if (e >= 0) atomic_add_warp(y, (long long)e * (map_ns(NS) == 3 ? 4 : 1), (Out)to_out(val));
+    const int hb = L.hb ? __ldg(L.hb + n) : -1;
+    if (hb >= 0)
+      hwp_scatter<Out>(y, hb, map_ns(NS) == 3 ? 4 : 1, __ldg(L.hang + n), __ldg(L.htau + n), (Out)to_out(val));
   }
   if constexpr (std::is_same<Real, df64>::value && polarised(NS)) {
     // as k_f3: the value rounded to float64 once, weighted by the float64 pair
@@ -852,6 +892,9 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
   a.pw = p->pw;
   a.pixq = p->pix_obs_pol;
   a.ext = p->ext_row;
+  a.hwp_base = p->hwp_base;
+  a.hwp_ang = p->hwp_ang;
+  a.hwp_tau = p->hwp_tau;
   a.bore = p->otf ? p->bore : nullptr;
   a.det = p->det_pt;
   a.g2o = p->g2o;

@@ -487,6 +487,33 @@ __global__ void k_ext_rows(const int* extra_index, long long n, int n_sky, int* 
   }
 }
 
+// first half-wave-plate row of each sample's group (-1: none)
+__global__ void k_hwp_base(const long long* off, int n_ivl, const int* ivl_base, long long n, int* base) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    base[t] = ivl_base[interval_of(off, n_ivl, t)];
+}
+
+__global__ void k_validate_hwp(const float* ang, const float* tau, long long n, int* bad) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(ang[t]) || !isfinite(tau[t])) atomicOr(bad, 32);
+}
+
+// Half-wave-plate parameters: sum over the surviving samples of f(0) C_{t,i}^2
+// (the scalar preconditioner of each parameter).
+__global__ void k_accumulate_hwp(const int* pix_obs, const int* hwp_base, const float* ang, const float* tau,
+                                 long long n, const long long* off, int n_ivl, const int* ivl_filter, const double* f0,
+                                 int row0, double* acc) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int b = hwp_base[t];
+    if (b < 0 || pix_obs[t] < 0) continue;
+    const double w0 = f0[ivl_filter[interval_of(off, n_ivl, t)]];
+    double C[32];
+    hwp_columns<double>(ang[t], tau[t], C);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) atomic_add_warp(acc, (long long)(b - row0 + i), w0 * C[i] * C[i]);
+  }
+}
+
 // Extra columns' sums over the samples whose row survives (sky pixel observed
 // and not excised): hits and B^T W^-1 B (= sum of f(0)).
 __global__ void k_accumulate_ext(const int* pix_obs, const int* ext_row, long long n, const long long* off, int n_ivl,
@@ -500,11 +527,12 @@ __global__ void k_accumulate_ext(const int* pix_obs, const int* ext_row, long lo
 }
 
 // Scalar blocks of the extra rows (slot 0; the rest of the row's block is 0).
+// hits == NULL: half-wave-plate rows (excised when the weight sum is 0).
 __global__ void k_classify_ext(const double* acc, const int* hits, int n_extra, int n_sky, int ns, double* P64,
                                float* P32, unsigned char* excised, unsigned char* fp64flag, int* counts) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_extra; e += gridDim.x * blockDim.x) {
     const long long r = n_sky + e;
-    const bool ex = hits[e] == 0 || !(acc[e] > 0.0);
+    const bool ex = (hits && hits[e] == 0) || !(acc[e] > 0.0);
     const double inv = ex ? 0.0 : 1.0 / acc[e];
     if (ns == 1) {
       P64[r] = inv;
@@ -964,12 +992,12 @@ static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
   if ((e = cudaMalloc(&doff, sizeof(long long) * (p->n_ivl + 1))) != cudaSuccess ||
       (e = cudaMalloc(&dfilt, sizeof(int) * std::max(1, p->n_ivl))) != cudaSuccess ||
       (e = cudaMalloc(&df0, sizeof(double) * p->n_filters)) != cudaSuccess ||
-      (e = cudaMalloc(&counts, sizeof(int) * 3)) != cudaSuccess) {
+      (e = cudaMalloc(&counts, sizeof(int) * 4)) != cudaSuccess) {
     cleanup();
     return cuda_fail(e, "cudaMalloc (preconditioner temporaries)");
   }
   cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)std::max(1, n_obs) * (ns == 1 ? 1 : 12), s);
-  cudaMemsetAsync(counts, 0, sizeof(int) * 3, s);
+  cudaMemsetAsync(counts, 0, sizeof(int) * 4, s);
   cudaMemcpyAsync(doff, p->offsets.data(), sizeof(long long) * (p->n_ivl + 1), cudaMemcpyHostToDevice, s);
   if (p->n_ivl) cudaMemcpyAsync(dfilt, p->ivl_filter.data(), sizeof(int) * p->n_ivl, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(df0, f0.data(), sizeof(double) * p->n_filters, cudaMemcpyHostToDevice, s);
@@ -993,7 +1021,7 @@ static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
   }
   int* hits_e = nullptr;
   double* acc_e = nullptr;
-  if (p->ext) {  // the extra columns, from the rows that survive the sky's excision
+  if (p->n_extra > 0) {  // the extra columns, from the rows that survive the sky's excision
     if ((e = cudaMalloc(&hits_e, sizeof(int) * p->n_extra)) != cudaSuccess ||
         (e = cudaMalloc(&acc_e, sizeof(double) * p->n_extra)) != cudaSuccess) {
       cudaFree(hits_e);
@@ -1006,20 +1034,39 @@ static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
     if (n > 0)
       k_accumulate_ext<<<grid_for(n), 256, 0, s>>>(p->pix_obs, p->ext_row, n, doff, p->n_ivl, dfilt, df0, n_obs,
                                                     hits_e, acc_e);
-    k_classify_ext<<<grid_for(p->n_extra), 256, 0, s>>>(acc_e, hits_e, p->n_extra, n_obs, ns, p->P64, p->P32,
-                                                         p->excised, p->fp64flag, counts + 2);
+    if (p->n_extra > 0)
+      k_classify_ext<<<grid_for(p->n_extra), 256, 0, s>>>(acc_e, hits_e, p->n_extra, n_obs, ns, p->P64, p->P32,
+                                                           p->excised, p->fp64flag, counts + 2);
   }
-  int hc[3] = {0, 0, 0};
+  double* acc_h = nullptr;
+  const int n_hwp = 32 * p->n_hwp_groups;
+  if (n_hwp > 0) {
+    if ((e = cudaMalloc(&acc_h, sizeof(double) * n_hwp)) != cudaSuccess) {
+      cudaFree(hits_e);
+      cudaFree(acc_e);
+      cleanup();
+      return cuda_fail(e, "cudaMalloc (preconditioner temporaries)");
+    }
+    cudaMemsetAsync(acc_h, 0, sizeof(double) * n_hwp, s);
+    if (n > 0)
+      k_accumulate_hwp<<<grid_for(n), 256, 0, s>>>(p->pix_obs, p->hwp_base, p->hwp_ang, p->hwp_tau, n, doff, p->n_ivl,
+                                                    dfilt, df0, p->hwp_row0, acc_h);
+    k_classify_ext<<<grid_for(n_hwp), 256, 0, s>>>(acc_h, nullptr, n_hwp, p->hwp_row0, ns, p->P64, p->P32,
+                                                    p->excised, p->fp64flag, counts + 3);
+  }
+  int hc[4] = {0, 0, 0, 0};
   e = cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaGetLastError();
   cudaFree(hits_e);
   cudaFree(acc_e);
+  cudaFree(acc_h);
   cleanup();
   if (e != cudaSuccess) return cuda_fail(e, "preconditioner build");
   p->n_excised = hc[0];
   p->n_fp64 = hc[1];
   p->n_excised_extra = hc[2];
+  p->n_excised_hwp = hc[3];
   p->pre_built = true;
   return st;
 }
@@ -1065,6 +1112,14 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
   MM_CHECK(!d->extra_index || (d->n_extra >= 1 && !d->pix_pol && !d->boresight), MADMAP_ERR_INVALID_ARG,
            "extra_index needs n_extra >= 1 and stored single-resolution pointing");
   MM_CHECK(d->n_extra < (1 << 30), MADMAP_ERR_INVALID_ARG, "n_extra too large");
+  MM_CHECK(!d->hwp_angle || (d->hwp_tau && d->interval_hwp_group && d->n_hwp_groups >= 1 &&
+                             d->n_hwp_groups < (1 << 24) && !d->pix_pol && !d->boresight),
+           MADMAP_ERR_INVALID_ARG,
+           "hwp_angle needs hwp_tau, interval_hwp_group, n_hwp_groups >= 1 and stored single-resolution pointing");
+  if (d->hwp_angle)
+    for (int i = 0; i < d->n_intervals; ++i)
+      MM_CHECK(d->interval_hwp_group[i] >= -1 && d->interval_hwp_group[i] < d->n_hwp_groups, MADMAP_ERR_INVALID_ARG,
+               "interval_hwp_group out of range");
   MM_CHECK(d->n_intervals >= 0 && d->interval_offsets != nullptr, MADMAP_ERR_INVALID_ARG, "bad intervals");
   MM_CHECK(d->n_intervals == 0 || d->interval_filter != nullptr, MADMAP_ERR_INVALID_ARG, "interval_filter NULL");
   MM_CHECK(d->n_filters >= 1 && d->n_lags >= 1 && d->filter_lags != nullptr, MADMAP_ERR_INVALID_ARG,
@@ -1206,13 +1261,46 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
   p->n_obs_i = hv[1];
   p->n_obs_pol = p->multires ? hv[2] : 0;
   p->n_obs = std::max(p->n_obs_i, p->n_obs_pol);  // map rows (slots for multi-resolution plans)
-  if (d->extra_index) {  // extended pointing: the extra columns' rows follow the sky rows
+  if (d->extra_index || d->hwp_angle) {  // extended pointing: extra rows follow the sky rows
     p->ext = true;
-    p->n_extra = d->n_extra;
+    p->n_extra = d->extra_index ? d->n_extra : 0;
     p->n_obs_sky = p->n_obs_i;
-    p->n_obs = p->n_obs_i + p->n_extra;
-    MM_TRY(dalloc_t(p, &p->ext_row, std::max(1LL, n)));
-    if (n > 0) k_ext_rows<<<grid_for(n), 256, 0, s>>>(d->extra_index, n, p->n_obs_sky, p->ext_row);
+    p->n_hwp_groups = d->hwp_angle ? d->n_hwp_groups : 0;
+    p->hwp_row0 = p->n_obs_sky + p->n_extra;
+    p->n_obs = p->hwp_row0 + 32 * p->n_hwp_groups;
+    if (d->extra_index) {
+      MM_TRY(dalloc_t(p, &p->ext_row, std::max(1LL, n)));
+      if (n > 0) k_ext_rows<<<grid_for(n), 256, 0, s>>>(d->extra_index, n, p->n_obs_sky, p->ext_row);
+    }
+    if (d->hwp_angle) {
+      MM_TRY(dalloc_t(p, &p->hwp_ang, std::max(1LL, n)));
+      MM_TRY(dalloc_t(p, &p->hwp_tau, std::max(1LL, n)));
+      MM_TRY(dalloc_t(p, &p->hwp_base, std::max(1LL, n)));
+      std::vector<int> base(std::max(1, d->n_intervals));
+      for (int i = 0; i < d->n_intervals; ++i)
+        base[i] = d->interval_hwp_group[i] >= 0 ? p->hwp_row0 + 32 * d->interval_hwp_group[i] : -1;
+      int* dbase = nullptr;
+      long long* doff = nullptr;
+      MM_TRY(dalloc_t(p, &dbase, std::max(1, d->n_intervals)));
+      MM_TRY(dalloc_t(p, &doff, d->n_intervals + 1));
+      MM_TRYC(cudaMemcpyAsync(dbase, base.data(), sizeof(int) * std::max(1, d->n_intervals), cudaMemcpyHostToDevice, s));
+      MM_TRYC(cudaMemcpyAsync(doff, d->interval_offsets, sizeof(long long) * (d->n_intervals + 1),
+                              cudaMemcpyHostToDevice, s));
+      if (n > 0) {
+        MM_TRYC(cudaMemcpyAsync(p->hwp_ang, d->hwp_angle, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+        MM_TRYC(cudaMemcpyAsync(p->hwp_tau, d->hwp_tau, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+        k_hwp_base<<<grid_for(n), 256, 0, s>>>(doff, d->n_intervals, dbase, n, p->hwp_base);
+        k_validate_hwp<<<grid_for(n), 256, 0, s>>>(p->hwp_ang, p->hwp_tau, n, p->dev_flag);
+      }
+      MM_TRYC(cudaStreamSynchronize(s));
+      int bad = 0;
+      MM_TRYC(cudaMemcpy(&bad, p->dev_flag, sizeof(int), cudaMemcpyDeviceToHost));
+      if (bad & 32) {
+        delete p;
+        set_error("hwp_angle or hwp_tau holds non-finite values");
+        return MADMAP_ERR_INVALID_ARG;
+      }
+    }
   }
   const int n_obs = p->n_obs;
   MM_TRY(dalloc_t(p, &p->obs2glob, std::max(1, p->n_obs_i)));
@@ -1359,6 +1447,8 @@ extern "C" madmap_status madmap_plan_get_stats(madmap_plan_t plan, madmap_plan_s
   o->n_excised_pol = p->n_excised_pol;
   o->n_extra = p->n_extra;
   o->n_excised_extra = p->n_excised_extra;
+  o->n_hwp_params = 32 * p->n_hwp_groups;
+  o->n_excised_hwp = p->n_excised_hwp;
   return MADMAP_OK;
 }
 

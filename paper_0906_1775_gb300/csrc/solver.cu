@@ -1085,7 +1085,7 @@ static madmap_status resume_impl(Plan* p, const madmap_checkpoint* c, double* m,
 template <int NS>
 __global__ void k_unpoint(const double* x, const int* pix, const int* pix_pol, const double2* cs, const float* d,
                           double alpha, double beta, float* out, long long n, const OtfPointing ob,
-                          const int* ext) {
+                          const int* ext, const int* hwp_base, const float* hwp_ang, const float* hwp_tau) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     float c2 = 0.f, s2 = 0.f;
     const int q = ob.bore ? otf_row(ob, t, NS == 3, c2, s2) : pix[t];
@@ -1099,6 +1099,11 @@ __global__ void k_unpoint(const double* x, const int* pix, const int* pix_pol, c
         ax = x[4LL * q] + x[4LL * qp + 1] * w.x + x[4LL * qp + 2] * w.y;
       }
       if (ext && ext[t] >= 0) ax += x[(long long)ext[t] * (NS == 1 ? 1 : 4)];
+      if (hwp_base && hwp_base[t] >= 0) {
+        double C[32];
+        hwp_columns<double>(hwp_ang[t], hwp_tau[t], C);
+        for (int i = 0; i < 32; ++i) ax += C[i] * x[(long long)(hwp_base[t] + i) * (NS == 1 ? 1 : 4)];
+      }
     }
     out[t] = (float)((d ? alpha * (double)d[t] : 0.0) + beta * ax);
   }
@@ -1227,10 +1232,12 @@ static madmap_status backward_impl(Plan* p, const float* d, const double* m, con
   count_launches(3);
   const int* pix_pol = p->multires ? p->pix_obs_pol : nullptr;
   k_unpoint<NS><<<std::max(1, gt), 256, 0, s>>>(lam, p->pix_obs, pix_pol, p->cs64, nullptr, 0.0, 1.0, p->bw_a, nt,
-                                                otf_pointing(p), p->ext_row);
+                                                otf_pointing(p), p->ext_row, p->hwp_base, p->hwp_ang,
+                                                p->hwp_tau);
   k_pack<double, double><<<grid_vec(nv), NT, 0, s>>>(m, sb64->t64, n, ns, np);
   k_unpoint<NS><<<std::max(1, gt), 256, 0, s>>>(sb64->t64, p->pix_obs, pix_pol, p->cs64, d, 1.0, -1.0, p->bw_r, nt,
-                                                otf_pointing(p), p->ext_row);
+                                                otf_pointing(p), p->ext_row, p->hwp_base, p->hwp_ang,
+                                                p->hwp_tau);
   if (grad_d) {
     st = op_launch(p, false, IN_TOD_REAL, OUT_TOD, p->bw_a, grad_d, 0, 0, 1, nullptr, s);
     if (st != MADMAP_OK) return st;

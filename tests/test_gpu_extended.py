@@ -42,26 +42,45 @@ def _case(kind):
         idx, n_extra = chop_bins(p.n_samples, 12, 41.0, np.random.default_rng(3))
         amp = np.random.default_rng(4).normal(0.0, 1.0, n_extra)
         return p, idx, n_extra + 2, lags_for(p), lib_lags(p), add_extra_signal(p.d[0], idx, amp)
+    if kind in ("hwp_IQU", "hwp_destripe"):   # the 32-parameter half-wave-plate model (+ offsets)
+        from synth.extended import add_hwp_signal, hwp_inputs
+        p = tiny_IQU(seed=85, n_per_det=2400, width=8, n_lags=12, n_ivl_lo=400, n_ivl_hi=1500)
+        ang, tau, grp, n_groups = hwp_inputs(p.interval_offsets, p.fs, 1.7, np.random.default_rng(9))
+        grp = grp.copy()
+        grp[::3] = -1                          # some intervals without the term
+        grp = np.where(grp >= 0, grp % 3, -1)  # three groups shared by several intervals
+        b = np.random.default_rng(10).normal(0.0, 0.3, (3, 32))
+        d = add_hwp_signal(p.d[0], p.interval_offsets, ang, tau, grp, b)
+        if kind == "hwp_IQU":
+            idx, n_extra = np.full(p.n_samples, -1, np.int32), 0
+        else:
+            idx, n_extra = baseline_index(2400, 4, 200)
+            d = add_extra_signal(d, idx, np.random.default_rng(11).normal(0.0, 1.0, n_extra))
+        return p, idx, n_extra, lags_for(p), lib_lags(p), d, (ang, tau, grp, 3)
     raise ValueError(kind)
 
 
-CASES = ["destripe_T", "destripe_IQU", "template_IQU"]
+CASES = ["destripe_T", "destripe_IQU", "template_IQU", "hwp_IQU", "hwp_destripe"]
 
 
 def _system(c):
     from oracle.extended import ExtendedSystem
-    p, idx, n_extra, olags, _, _ = c
+    p, idx, n_extra, olags = c[:4]
     return ExtendedSystem(p.pix, p.psi, p.n_pix, p.n_stokes, p.interval_offsets, p.interval_filter, olags, idx,
-                          n_extra)
+                          n_extra, hwp=c[6] if len(c) > 6 else None)
 
 
 def _plan(c, **kw):
     import torch
     from paper_0906_1775_gb300 import Plan
-    p, idx, n_extra, _, llags, _ = c
+    p, idx, n_extra, _, llags = c[:5]
     psi = torch.from_numpy(p.psi).cuda() if p.psi is not None else None
+    ext = dict(extra_index=torch.from_numpy(idx).cuda(), n_extra=n_extra) if n_extra else {}
+    if len(c) > 6:
+        ang, tau, grp, ng = c[6]
+        ext["hwp"] = (torch.from_numpy(ang).cuda(), torch.from_numpy(tau).cuda(), grp, ng)
     return Plan(torch.from_numpy(p.pix).cuda(), psi, p.n_pix, p.interval_offsets, p.interval_filter, llags,
-                extra_index=torch.from_numpy(idx).cuda(), n_extra=n_extra, **kw)
+                **ext, **kw)
 
 
 @pytest.fixture(scope="module")
@@ -81,6 +100,7 @@ def test_layout_and_excision(cases, case):
     assert np.array_equal(host(exc).astype(bool), E.excised_sky)
     assert st["n_excised"] == int(E.excised_sky.sum())
     assert st["n_excised_extra"] == int(E.excised_extra.sum())
+    assert st["n_hwp_params"] == E.n_hwp and st["n_excised_hwp"] == int(E.excised_hwp.sum())
     if case == "template_IQU":
         assert st["n_excised_extra"] == 2
 
@@ -127,7 +147,7 @@ def test_solve_fp64_matches_oracle(cases, case):
         assert np.all(host(m)[~E.active()] == 0.0)
 
 
-@pytest.mark.parametrize("case", ["destripe_T", "template_IQU"])
+@pytest.mark.parametrize("case", ["destripe_T", "template_IQU", "hwp_destripe"])
 def test_solve_mixed_reaches_fp64_map(cases, case):
     c = cases[case]
     E = _system(c)
@@ -173,7 +193,7 @@ def test_solve_batched_matches_oracle(cases, prec):
         assert rel_rms(host(ms[k]), x) < (FP64_MAP_TOL if prec == "fp64" else MIXED_MAP_TOL)
 
 
-@pytest.mark.parametrize("case", ["destripe_T", "template_IQU"])
+@pytest.mark.parametrize("case", ["destripe_T", "template_IQU", "hwp_destripe"])
 def test_backward_matches_oracle_adjoint(cases, case):
     from oracle.adjoint import solve_backward
     c = cases[case]
@@ -205,7 +225,7 @@ def test_set_filters_matches_new_plan(cases):
     lags2 = c[4] * 1.3
     lags2[:, 1:] *= 0.5
     plan.set_filters(lags2)
-    fresh = _plan((c[0], c[1], c[2], c[3], lags2, c[5]))
+    fresh = _plan((c[0], c[1], c[2], c[3], lags2) + tuple(c[5:]))
     d = cuda(c[5])
     m1, i1 = plan.solve(d, precision="fp64", rel_tol=1e-13, max_iter=3000)
     m2, i2 = fresh.solve(d, precision="fp64", rel_tol=1e-13, max_iter=3000)
@@ -217,7 +237,7 @@ def test_bad_extra_columns_are_rejected(cases):
     import torch
     import paper_0906_1775_gb300 as mm
     from paper_0906_1775_gb300 import Plan
-    p, idx, n_extra, _, llags, _ = cases["destripe_IQU"]
+    p, idx, n_extra, _, llags = cases["destripe_IQU"][:5]
     pix, psi = torch.from_numpy(p.pix).cuda(), torch.from_numpy(p.psi).cuda()
     bad = idx.copy()
     bad[11] = n_extra
@@ -231,3 +251,24 @@ def test_bad_extra_columns_are_rejected(cases):
     with pytest.raises(mm.MadmapError):
         Plan(pix, psi, p.n_pix, p.interval_offsets, p.interval_filter, llags, extra_index=torch.from_numpy(idx).cuda(),
              n_extra=0)
+
+
+def test_hwp_noiseless_recovery_on_gpu():
+    """An injected half-wave-plate signal on an IQU sky, noiseless: the GPU solution holds the
+    sky and the 32 parameters of each group."""
+    import torch
+    from synth.extended import add_hwp_signal, hwp_inputs
+    from paper_0906_1775_gb300 import Plan
+    p = tiny_IQU(seed=86, n_per_det=1500, width=5, noiseless=True, n_ivl_lo=500, n_ivl_hi=1500)
+    ang, tau, grp, ng = hwp_inputs(p.interval_offsets, p.fs, 1.3, np.random.default_rng(12))
+    b = np.random.default_rng(13).normal(0.0, 0.3, (ng, 32))
+    d = add_hwp_signal(p.d[0], p.interval_offsets, ang, tau, grp, b)
+    plan = Plan(torch.from_numpy(p.pix).cuda(), torch.from_numpy(p.psi).cuda(), p.n_pix, p.interval_offsets,
+                p.interval_filter, lib_lags(p), hwp=(torch.from_numpy(ang).cuda(), torch.from_numpy(tau).cuda(), grp, ng))
+    m, _ = plan.solve(cuda(d), precision="fp64", rel_tol=1e-14, max_iter=5000)
+    m = host(m)
+    n_sky = plan.n_obs - 32 * ng
+    o2g, _ = plan.observed()
+    for s in range(3):
+        assert rel_rms(m[:n_sky, s], p.sky[host(o2g).astype(np.int64), s]) < 1e-5
+    assert rel_rms(m[n_sky:, 0].reshape(ng, 32), b) < 1e-5
