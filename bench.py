@@ -389,11 +389,20 @@ def run_secondary(args):
                        n_extra=n_extra)
         full_ms, _ = full.time_operator("fp32", reps=10)
         full.close()
+        # the same destriping pass with the 32-parameter half-wave-plate model, one group per detector
+        from synth.extended import hwp_inputs
+        ang, tau, _, _ = hwp_inputs(p.interval_offsets, p.fs, 2.0, np.random.default_rng(8))
+        hplan = mm.Plan(pix, psi, p.n_pix, p.interval_offsets, p.interval_filter, white, extra_index=eidx,
+                        n_extra=n_extra, hwp=(torch.from_numpy(ang).to(dev), torch.from_numpy(tau).to(dev),
+                                              p.interval_det, 4))
+        hwp_ms, _ = hplan.time_operator("fp32", reps=10)
+        hplan.close()
         line.update({"n_samples": p.n_samples, "n_extra": n_extra, "rows": n_rows,
                      "operator_diag": ops, "alg_bytes": int(b_alg),
                      "hbm": {"achieved_gbs": b_alg / (ops["fp32_ms"] * 1e-3) / 1e9, "peak_gbs": hbm,
                              "frac": b_alg / (ops["fp32_ms"] * 1e-3) / 1e9 / hbm},
                      "operator_full_noise_fp32_ms": float(full_ms[3]),
+                     "operator_diag_with_hwp_fp32_ms": float(hwp_ms[3]),
                      "speedup_destripe_vs_full_noise_operator": float(full_ms[3]) / ops["fp32_ms"],
                      "solve_to_rel_res_1e-7": solves,
                      "reference": f"FP64 GPU solve to rel. residual 1e-11 ({rinfo['iters']} iterations)",
