@@ -163,7 +163,7 @@ __device__ __forceinline__ double to_out(df64 v) { return to_double(v); }
 // gather sum_i C_i x_i, or scatter v C_i into each parameter.  Float32
 // kernels take the columns in float32, the others in float64.
 template <typename Real>
-__device__ __forceinline__ Real hwp_gather(const Real* x, int hb, int stride, float w, float tau) {
+__device__ __noinline__ Real hwp_gather(const Real* x, int hb, int stride, float w, float tau) {
   typedef typename std::conditional<std::is_same<Real, float>::value, float, double>::type W;
   W C[32];
   hwp_columns<W>(w, tau, C);
@@ -176,12 +176,43 @@ __device__ __forceinline__ Real hwp_gather(const Real* x, int hb, int stride, fl
   }
   return Real(acc);
 }
-template <typename Out>
-__device__ __forceinline__ void hwp_scatter(Out* y, int hb, int stride, float w, float tau, Out v) {
+// Scatter of one position of a tile lane by a whole (converged) warp: every
+// sample of a lane belongs to one interval, so the warp's samples share one
+// group; each lane forms its 32 products v C_i, a transposing butterfly of
+// 31 shuffles leaves lane i with the warp's sum for parameter i, and each
+// lane adds it with one atomic.  Lanes without a valid sample add zeros.
+template <typename Real>
+__device__ __noinline__ void hwp_scatter_warp(typename OutT<Real>::type* y, int stride, const int* pix, const int* hbp,
+                                              const float* ang, const float* tau, int n, bool ok, Real val) {
+  typedef typename OutT<Real>::type Out;
+  int hb = -1;
+  float w = 0.f, t = 0.f;
+  if (ok && __ldg(pix + n) >= 0) {
+    hb = __ldg(hbp + n);
+    if (hb >= 0) {
+      w = __ldg(ang + n);
+      t = __ldg(tau + n);
+    }
+  }
+  const int g = __reduce_max_sync(0xffffffffu, hb);
+  if (g < 0) return;
+  const Out v = hb >= 0 ? (Out)to_out(val) : Out(0);
   Out C[32];
-  hwp_columns<Out>(w, tau, C);
+  hwp_columns<Out>(w, t, C);
 #pragma unroll
-  for (int i = 0; i < 32; ++i) atomic_add_warp(y, (long long)(hb + i) * stride, v * C[i]);
+  for (int i = 0; i < 32; ++i) C[i] *= v;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 16; k >= 1; k >>= 1) {
+    const bool upper = (lane & k) != 0;
+#pragma unroll
+    for (int i = 0; i < k; ++i) {
+      const Out send = upper ? C[i] : C[i + k];
+      const Out keep = upper ? C[i + k] : C[i];
+      C[i] = keep + __shfl_xor_sync(0xffffffffu, send, k);
+    }
+  }
+  atomicAdd(y + (long long)(g + lane) * stride, C[0]);
 }
 
 // multi-resolution maps: I from slot p, Q and U from slot q
@@ -656,10 +687,6 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
           atomicAdd(y + 4LL * qq[l][u] + 2, v * cs[l][u].y);
           if constexpr (extended(NS)) {
             if (ee[l][u] >= 0) atomic_add_warp(y, 4LL * ee[l][u], v);
-            if (L[l].hb) {
-              const int hb = __ldg(L[l].hb + nn[u]);
-              if (hb >= 0) hwp_scatter<double>(y, hb, 4, __ldg(L[l].hang + nn[u]), __ldg(L[l].htau + nn[u]), v);
-            }
           }
         }
     } else {
@@ -685,12 +712,6 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
             if (qq[l][u] >= 0)
               atomic_add_warp(static_cast<Out*>(L[l].out), (long long)qq[l][u] * (map_ns(NS) == 3 ? 4 : 1),
                               (Out)to_out(val[l][u]));
-            if (L[l].hb) {
-              const int hb = __ldg(L[l].hb + nn[u]);
-              if (hb >= 0)
-                hwp_scatter<Out>(static_cast<Out*>(L[l].out), hb, map_ns(NS) == 3 ? 4 : 1, __ldg(L[l].hang + nn[u]),
-                                 __ldg(L[l].htau + nn[u]), (Out)to_out(val[l][u]));
-            }
           }
           Real c = cc[l][u], sn = ss[l][u];
           if (polarised(NS) && !on_the_fly(NS)) finish_angle<Real>(c, sn);
@@ -699,6 +720,16 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
           else
             scatter<Real, map_ns(NS)>(static_cast<typename OutT<Real>::type*>(L[l].out), pp[l][u], val[l][u], c, sn);
         }
+    }
+    if constexpr (extended(NS) && OUT == OUT_MAP) {
+      if (a.hwp_base) {   // half-wave-plate parameters, one converged warp at a time
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int l = 0; l < 2; ++l)
+            hwp_scatter_warp<Real>(static_cast<typename OutT<Real>::type*>(L[l].out), map_ns(NS) == 3 ? 4 : 1,
+                                   L[l].pix, L[l].hb, L[l].hang, L[l].htau, nn[u], ok[l][u], val[l][u]);
+      }
     }
   }
 }
@@ -742,9 +773,6 @@ __device__ __forceinline__ void sample_scatter(const OpArgs& a, const LaneView<R
   if constexpr (extended(NS)) {
     const int e = L.pe ? __ldg(L.pe + n) : -1;
     if (e >= 0) atomic_add_warp(y, (long long)e * (map_ns(NS) == 3 ? 4 : 1), (Out)to_out(val));
-    const int hb = L.hb ? __ldg(L.hb + n) : -1;
-    if (hb >= 0)
-      hwp_scatter<Out>(y, hb, map_ns(NS) == 3 ? 4 : 1, __ldg(L.hang + n), __ldg(L.htau + n), (Out)to_out(val));
   }
   if constexpr (std::is_same<Real, df64>::value && polarised(NS)) {
     // as k_f3: the value rounded to float64 once, weighted by the float64 pair
@@ -777,14 +805,24 @@ __global__ void __launch_bounds__(256) k_diag(OpArgs a, const DiagItem* __restri
   const LaneView<Real> L = lane_view<Real, IN, OUT>(a, g);
   const Real w0 = Real(f0[it.filter]);
   const int len = (int)(it.hi - it.lo);
-  for (int n = threadIdx.x; n < len; n += blockDim.x) {
-    Real v;
-    if (IN == IN_MAPX) v = sample_gather<Real, NS>(a, L, n);
-    else if (IN == IN_TODF) v = (Real)__ldg(static_cast<const float*>(L.in) + n);
-    else v = static_cast<const Real*>(L.in)[n];
-    v = v * w0;
-    if (OUT == OUT_TOD) static_cast<Real*>(L.out)[n] = v;   // float and float64 only
-    else sample_scatter<Real, NS>(a, L, n, v);
+  // whole-block rounds, so every warp stays converged for the half-wave-plate scatter
+  for (int n0 = 0; n0 < len; n0 += blockDim.x) {
+    const int n = n0 + threadIdx.x;
+    const bool in = n < len;
+    Real v = Real(0);
+    if (in) {
+      if (IN == IN_MAPX) v = sample_gather<Real, NS>(a, L, n);
+      else if (IN == IN_TODF) v = (Real)__ldg(static_cast<const float*>(L.in) + n);
+      else v = static_cast<const Real*>(L.in)[n];
+      v = v * w0;
+      if (OUT == OUT_TOD) static_cast<Real*>(L.out)[n] = v;   // float and float64 only
+      else sample_scatter<Real, NS>(a, L, n, v);
+    }
+    if constexpr (extended(NS) && OUT == OUT_MAP) {
+      if (a.hwp_base)
+        hwp_scatter_warp<Real>(static_cast<typename OutT<Real>::type*>(L.out), map_ns(NS) == 3 ? 4 : 1, L.pix, L.hb,
+                               L.hang, L.htau, n, in, v);
+    }
   }
 }
 
