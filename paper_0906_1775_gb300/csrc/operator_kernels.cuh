@@ -180,9 +180,11 @@ __device__ __noinline__ Real hwp_gather(const Real* x, int hb, int stride, float
 // sample of a lane belongs to one interval, so the warp's samples share one
 // group; each lane forms its 32 products v C_i, a transposing butterfly of
 // 31 shuffles leaves lane i with the warp's sum for parameter i, and each
-// lane adds it with one atomic.  Lanes without a valid sample add zeros.
+// lane adds it into the CTA's shared sums `acc` (the group's first row goes
+// to *grp); hwp_flush adds those to the map once per CTA.  Lanes without a
+// valid sample add zeros.
 template <typename Real>
-__device__ __noinline__ void hwp_scatter_warp(typename OutT<Real>::type* y, int stride, const int* pix, const int* hbp,
+__device__ __noinline__ void hwp_scatter_warp(typename OutT<Real>::type* acc, int* grp, const int* pix, const int* hbp,
                                               const float* ang, const float* tau, int n, bool ok, Real val) {
   typedef typename OutT<Real>::type Out;
   int hb = -1;
@@ -212,7 +214,17 @@ __device__ __noinline__ void hwp_scatter_warp(typename OutT<Real>::type* y, int 
       C[i] = keep + __shfl_xor_sync(0xffffffffu, send, k);
     }
   }
-  atomicAdd(y + (long long)(g + lane) * stride, C[0]);
+  atomicAdd(acc + lane, C[0]);
+  if (lane == 0) *grp = g;
+}
+
+// The CTA's shared half-wave-plate sums into the map (after a barrier).
+template <typename Out>
+__device__ __forceinline__ void hwp_flush(Out* y, int stride, const Out* acc, const int* grp, int n_groups) {
+  for (int i = threadIdx.x; i < 32 * n_groups; i += blockDim.x) {
+    const int g = grp[i / 32];
+    if (g >= 0 && acc[i] != Out(0)) atomicAdd(y + (long long)(g + (i & 31)) * stride, acc[i]);
+  }
 }
 
 // multi-resolution maps: I from slot p, Q and U from slot q
@@ -602,6 +614,14 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
   const C* twM = static_cast<const C*>(a.tw);
   build_pass_twiddles(tw, logN2, twM, a.N1);
   build_split_twiddles(tlo, thi, twM, logM, logL);
+  // half-wave-plate sums of the CTA, per tile lane (extended pointing only)
+  constexpr bool HWP = extended(NS) && OUT == OUT_MAP;
+  __shared__ typename OutT<Real>::type hacc[HWP ? 64 : 1];
+  __shared__ int hgrp[2];
+  if (HWP) {
+    for (int i = threadIdx.x; i < 64; i += OP_THREADS) hacc[i] = 0;
+    if (threadIdx.x < 2) hgrp[threadIdx.x] = -1;
+  }
   __syncthreads();
   LaneView<Real> L[2];
   L[0] = lane_view<Real, IN_MAPX, OUT>(a, T->l[0]);
@@ -727,9 +747,17 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
         for (int u = 0; u < U; ++u)
 #pragma unroll
           for (int l = 0; l < 2; ++l)
-            hwp_scatter_warp<Real>(static_cast<typename OutT<Real>::type*>(L[l].out), map_ns(NS) == 3 ? 4 : 1,
-                                   L[l].pix, L[l].hb, L[l].hang, L[l].htau, nn[u], ok[l][u], val[l][u]);
+            hwp_scatter_warp<Real>(hacc + 32 * l, hgrp + l, L[l].pix, L[l].hb, L[l].hang, L[l].htau, nn[u],
+                                   ok[l][u], val[l][u]);
       }
+    }
+  }
+  if constexpr (HWP) {
+    if (a.hwp_base) {
+      __syncthreads();
+      for (int l = 0; l < 2; ++l)
+        hwp_flush(static_cast<typename OutT<Real>::type*>(L[l].out), map_ns(NS) == 3 ? 4 : 1, hacc + 32 * l,
+                  hgrp + l, 1);
     }
   }
 }
@@ -805,6 +833,14 @@ __global__ void __launch_bounds__(256) k_diag(OpArgs a, const DiagItem* __restri
   const LaneView<Real> L = lane_view<Real, IN, OUT>(a, g);
   const Real w0 = Real(f0[it.filter]);
   const int len = (int)(it.hi - it.lo);
+  constexpr bool HWP = extended(NS) && OUT == OUT_MAP;
+  __shared__ typename OutT<Real>::type hacc[HWP ? 32 : 1];
+  __shared__ int hgrp[1];
+  if (HWP) {
+    if (threadIdx.x < 32) hacc[threadIdx.x] = 0;
+    if (threadIdx.x == 0) hgrp[0] = -1;
+    __syncthreads();
+  }
   // whole-block rounds, so every warp stays converged for the half-wave-plate scatter
   for (int n0 = 0; n0 < len; n0 += blockDim.x) {
     const int n = n0 + threadIdx.x;
@@ -819,9 +855,13 @@ __global__ void __launch_bounds__(256) k_diag(OpArgs a, const DiagItem* __restri
       else sample_scatter<Real, NS>(a, L, n, v);
     }
     if constexpr (extended(NS) && OUT == OUT_MAP) {
-      if (a.hwp_base)
-        hwp_scatter_warp<Real>(static_cast<typename OutT<Real>::type*>(L.out), map_ns(NS) == 3 ? 4 : 1, L.pix, L.hb,
-                               L.hang, L.htau, n, in, v);
+      if (a.hwp_base) hwp_scatter_warp<Real>(hacc, hgrp, L.pix, L.hb, L.hang, L.htau, n, in, v);
+    }
+  }
+  if constexpr (HWP) {
+    if (a.hwp_base) {
+      __syncthreads();
+      hwp_flush(static_cast<typename OutT<Real>::type*>(L.out), map_ns(NS) == 3 ? 4 : 1, hacc, hgrp, 1);
     }
   }
 }
