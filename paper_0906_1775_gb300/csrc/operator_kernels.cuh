@@ -819,7 +819,9 @@ __device__ __forceinline__ void sample_scatter(const OpArgs& a, const LaneView<R
   }
 }
 
-template <typename Real, int NS, int IN, int OUT>
+// HWP: the instance for plans with half-wave-plate parameters (extended
+// pointing); the others keep the plain loop.
+template <typename Real, int NS, int IN, int OUT, bool HWP>
 __global__ void __launch_bounds__(256) k_diag(OpArgs a, const DiagItem* __restrict__ items, const double* f0) {
   if (a.skip && *a.skip) return;
   const DiagItem it = items[blockIdx.x];
@@ -833,20 +835,9 @@ __global__ void __launch_bounds__(256) k_diag(OpArgs a, const DiagItem* __restri
   const LaneView<Real> L = lane_view<Real, IN, OUT>(a, g);
   const Real w0 = Real(f0[it.filter]);
   const int len = (int)(it.hi - it.lo);
-  constexpr bool HWP = extended(NS) && OUT == OUT_MAP;
-  __shared__ typename OutT<Real>::type hacc[HWP ? 32 : 1];
-  __shared__ int hgrp[1];
-  if (HWP) {
-    if (threadIdx.x < 32) hacc[threadIdx.x] = 0;
-    if (threadIdx.x == 0) hgrp[0] = -1;
-    __syncthreads();
-  }
-  // whole-block rounds, so every warp stays converged for the half-wave-plate scatter
-  for (int n0 = 0; n0 < len; n0 += blockDim.x) {
-    const int n = n0 + threadIdx.x;
-    const bool in = n < len;
-    Real v = Real(0);
-    if (in) {
+  if constexpr (!HWP) {
+    for (int n = threadIdx.x; n < len; n += blockDim.x) {
+      Real v;
       if (IN == IN_MAPX) v = sample_gather<Real, NS>(a, L, n);
       else if (IN == IN_TODF) v = (Real)__ldg(static_cast<const float*>(L.in) + n);
       else v = static_cast<const Real*>(L.in)[n];
@@ -854,15 +845,28 @@ __global__ void __launch_bounds__(256) k_diag(OpArgs a, const DiagItem* __restri
       if (OUT == OUT_TOD) static_cast<Real*>(L.out)[n] = v;   // float and float64 only
       else sample_scatter<Real, NS>(a, L, n, v);
     }
-    if constexpr (extended(NS) && OUT == OUT_MAP) {
-      if (a.hwp_base) hwp_scatter_warp<Real>(hacc, hgrp, L.pix, L.hb, L.hang, L.htau, n, in, v);
+  } else {
+    __shared__ typename OutT<Real>::type hacc[32];
+    __shared__ int hgrp[1];
+    if (threadIdx.x < 32) hacc[threadIdx.x] = 0;
+    if (threadIdx.x == 0) hgrp[0] = -1;
+    __syncthreads();
+    // whole-block rounds, so every warp stays converged for the half-wave-plate scatter
+    for (int n0 = 0; n0 < len; n0 += blockDim.x) {
+      const int n = n0 + threadIdx.x;
+      const bool in = n < len;
+      Real v = Real(0);
+      if (in) {
+        if (IN == IN_MAPX) v = sample_gather<Real, NS>(a, L, n);
+        else if (IN == IN_TODF) v = (Real)__ldg(static_cast<const float*>(L.in) + n);
+        else v = static_cast<const Real*>(L.in)[n];
+        v = v * w0;
+        sample_scatter<Real, NS>(a, L, n, v);
+      }
+      hwp_scatter_warp<Real>(hacc, hgrp, L.pix, L.hb, L.hang, L.htau, n, in, v);
     }
-  }
-  if constexpr (HWP) {
-    if (a.hwp_base) {
-      __syncthreads();
-      hwp_flush(static_cast<typename OutT<Real>::type*>(L.out), map_ns(NS) == 3 ? 4 : 1, hacc, hgrp, 1);
-    }
+    __syncthreads();
+    hwp_flush(static_cast<typename OutT<Real>::type*>(L.out), map_ns(NS) == 3 ? 4 : 1, hacc, hgrp, 1);
   }
 }
 
@@ -1004,7 +1008,14 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
         a.out = static_cast<char*>(out) + (size_t)r * out_stride * sizeof(typename OutT<Real>::type);
         a.in_stride = a.out_stride = 0;
         if (ev) cudaEventRecord(ev[4 * (rep * n_rhs + r)], s);
-        k_diag<Real, NS, IN, OUT><<<p->n_diag_items, 256, 0, s>>>(a, p->diag_items, p->f0_64);
+        if constexpr (extended(NS) && OUT == OUT_MAP) {
+          if (p->hwp_base)
+            k_diag<Real, NS, IN, OUT, true><<<p->n_diag_items, 256, 0, s>>>(a, p->diag_items, p->f0_64);
+          else
+            k_diag<Real, NS, IN, OUT, false><<<p->n_diag_items, 256, 0, s>>>(a, p->diag_items, p->f0_64);
+        } else {
+          k_diag<Real, NS, IN, OUT, false><<<p->n_diag_items, 256, 0, s>>>(a, p->diag_items, p->f0_64);
+        }
         if (ev)
           for (int k = 1; k < 4; ++k) cudaEventRecord(ev[4 * (rep * n_rhs + r) + k], s);
       }
