@@ -836,29 +836,14 @@ __global__ void __launch_bounds__(256) k_diag(OpArgs a, const DiagItem* __restri
   const Real w0 = Real(f0[it.filter]);
   const int len = (int)(it.hi - it.lo);
   if constexpr (!HWP) {
-    // four samples per thread and round: their pointing loads and map gathers
-    // are independent, so each thread keeps four load chains in flight
-    constexpr int UD = 4;
-    for (int n0 = threadIdx.x; n0 < len; n0 += blockDim.x * UD) {
-      Real v[UD];
-#pragma unroll
-      for (int u = 0; u < UD; ++u) {
-        const int n = n0 + u * blockDim.x;
-        v[u] = Real(0);
-        if (n < len) {
-          if (IN == IN_MAPX) v[u] = sample_gather<Real, NS>(a, L, n);
-          else if (IN == IN_TODF) v[u] = (Real)__ldg(static_cast<const float*>(L.in) + n);
-          else v[u] = static_cast<const Real*>(L.in)[n];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < UD; ++u) {
-        const int n = n0 + u * blockDim.x;
-        if (n >= len) continue;
-        const Real w = v[u] * w0;
-        if (OUT == OUT_TOD) static_cast<Real*>(L.out)[n] = w;   // float and float64 only
-        else sample_scatter<Real, NS>(a, L, n, w);
-      }
+    for (int n = threadIdx.x; n < len; n += blockDim.x) {
+      Real v;
+      if (IN == IN_MAPX) v = sample_gather<Real, NS>(a, L, n);
+      else if (IN == IN_TODF) v = (Real)__ldg(static_cast<const float*>(L.in) + n);
+      else v = static_cast<const Real*>(L.in)[n];
+      v = v * w0;
+      if (OUT == OUT_TOD) static_cast<Real*>(L.out)[n] = v;   // float and float64 only
+      else sample_scatter<Real, NS>(a, L, n, v);
     }
   } else {
     __shared__ typename OutT<Real>::type hacc[32];
