@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=3, help="oracle PCG iterations in the CPU baseline sample")
     ap.add_argument("--workload", default="config2", choices=["config2", "config1", "config3", "config4", "config5",
-                                                               "config2-boresight", "config2-destripe"],
+                                                               "config2-boresight", "config2-destripe",
+                                                               "config2-multires", "config2-checkpoint"],
                     help="config2 (default) prints the headline line; the others print secondary measurements")
     ap.add_argument("--profile-step", type=float, default=0.0, metavar="TOL",
                     help="profiling runs: skip the reference map and tolerance search and run exactly one "
@@ -408,6 +409,69 @@ def run_secondary(args):
                      "reference": f"FP64 GPU solve to rel. residual 1e-11 ({rinfo['iters']} iterations)",
                      "workload_desc": "IQU destriping: the IQU workload's pointing (4 det x 2^22, 512x512), white "
                                       "noise, offsets on 6000-sample baselines (one reference baseline)"})
+        plan.close()
+    elif args.workload == "config2-multires":
+        # the IQU workload with Q and U on a 256 x 256 grid (2 x 2 intensity pixels each)
+        from synth.flat import log_uniform_intervals
+        from synth import make_flat_problem
+
+        def ivls(rng, n):
+            return log_uniform_intervals(n, 1 << 16, 1 << 20, rng)
+
+        def nz(rng, nd):
+            return np.stack([np.ones(nd), rng.uniform(0.05, 0.2, nd), rng.uniform(1.0, 2.0, nd)], 1)
+
+        p = make_flat_problem("config2-multires", 2000, 512, 4, 1 << 22, 3, 1 << 14,
+                              det_angles_deg=[0.0, 45.0, 90.0, 135.0], hwp_step_deg=22.5, interval_lengths=ivls,
+                              noise=nz, pol_factor=2)
+        pix, psi = torch.from_numpy(p.pix).to(dev), torch.from_numpy(p.psi).to(dev)
+        d = torch.from_numpy(p.d[0]).to(dev)
+        res = {}
+        for name, kw in (("single_resolution", {}),
+                         ("multi_resolution", dict(pix_pol=torch.from_numpy(p.pix_pol).to(dev),
+                                                   n_pix_pol=p.n_pix_pol))):
+            plan = mm.Plan(pix, psi, p.n_pix, p.interval_offsets, p.interval_filter, lib_lags(p), **kw)
+            ops = {}
+            for prec in ("fp32", "df64", "fp64"):
+                ms, _ = plan.time_operator(prec, reps=20 if prec == "fp32" else 5)
+                ops[prec + "_ms"] = float(ms[3])
+            skw = dict(precision="mixed", rel_tol=1e-6, max_iter=500, max_outer=10)
+            plan.solve(d, **skw)
+            ms_s, (m, info) = _timed(lambda: plan.solve(d, **skw), steps)
+            res[name] = {"operator": ops, "rows": plan.n_obs, "n_obs_pol": plan.stats["n_obs_pol"],
+                         "mixed_solve_to_1e-6": {"ms": ms_s, "iters": info["iters"],
+                                                 "value": p.n_samples * info["iters"] / (ms_s / 1e3)}}
+            plan.close()
+        line.update({"n_samples": p.n_samples, **res,
+                     "workload_desc": "IQU, 4 det x 2^22 samples, I on 512x512, Q/U on 256x256 (multi-resolution) "
+                                      "against all three on 512x512, intervals 2^16-2^20, n_c=2^14"})
+    elif args.workload == "config2-checkpoint":
+        # float64 solves of the IQU workload with and without checkpoints every 20 iterations
+        # (the paper's default), the state written to host memory by the callback
+        p = make_config(2)
+        plan = mm.Plan(torch.from_numpy(p.pix).to(dev), torch.from_numpy(p.psi).to(dev), p.n_pix,
+                       p.interval_offsets, p.interval_filter, lib_lags(p))
+        d = torch.from_numpy(p.d[0]).to(dev)
+        kw = dict(precision="fp64", rel_tol=1e-10, max_iter=200)
+        plan.solve(d, **kw)
+        ms0, (m0, i0) = _timed(lambda: plan.solve(d, **kw), steps)
+        saved = []
+
+        def keep(state):
+            saved.append(state["iters"])
+            return False
+
+        plan.solve(d, checkpoint_every=20, on_checkpoint=keep, **kw)
+        saved.clear()
+        ms1, (m1, i1) = _timed(lambda: plan.solve(d, checkpoint_every=20, on_checkpoint=keep, **kw), steps)
+        n_ck = len(saved) // max(steps, 1)
+        diff = float((m1 - m0).norm() / m0.norm())
+        line.update({"n_samples": p.n_samples, "iters": i0["iters"], "ms_without": ms0, "ms_with": ms1,
+                     "checkpoints_per_solve": n_ck,
+                     "ms_per_checkpoint": (ms1 - ms0) / max(n_ck, 1), "map_rel_diff": diff,
+                     "checkpoint_bytes": 5 * plan.n_obs * 3 * 8,
+                     "workload_desc": "IQU workload, float64 solve to rel. residual 1e-10, checkpoints every 20 "
+                                      "iterations (five maps and six scalars to host memory)"})
         plan.close()
     elif args.workload == "config2-boresight":
         # the same scan planned twice: pointing expanded on the fly from the
