@@ -169,6 +169,8 @@ typedef struct {
   int32_t n_excised_extra; /* extended pointing: extra columns without samples */
   int32_t n_hwp_params;    /* half-wave-plate parameters (32 per group; the last rows of the map) */
   int32_t n_excised_hwp;   /* half-wave-plate parameters without weight */
+  int32_t n_map_replicas;  /* copies of the map the operator scatters into (8 for small maps under
+                              more than 1024 samples per row, else 1) */
 } madmap_plan_stats;
 
 typedef struct {

@@ -51,7 +51,8 @@ class madmap_plan_stats(C.Structure):
                                          "n_filters")] + [("n_samples", C.c_int64), ("device_bytes", C.c_int64),
                                                           ("n_obs_pol", C.c_int32), ("n_excised_pol", C.c_int32),
                                                           ("n_extra", C.c_int32), ("n_excised_extra", C.c_int32),
-                                                          ("n_hwp_params", C.c_int32), ("n_excised_hwp", C.c_int32)]
+                                                          ("n_hwp_params", C.c_int32), ("n_excised_hwp", C.c_int32),
+                                                          ("n_map_replicas", C.c_int32)]
 
 
 class madmap_checkpoint(C.Structure):

@@ -314,6 +314,11 @@ struct Plan {
   float* hwp_ang = nullptr;        // [n_t] polariser angle
   float* hwp_tau = nullptr;        // [n_t] the model's time variable
   int* hwp_base = nullptr;         // [n_t] first row of the sample's group, or -1
+  // small maps hit by many samples: the operator's scatter spreads over n_rep
+  // replicas of the map (picked per CTA) that one kernel then adds up, so no
+  // address takes every sample's atomic
+  int n_rep = 1;
+  void* rep = nullptr;             // n_rep x n_obs x ns_pad (float64 size), zero between applications
   // white noise (n_lags == 1): the operator is one diagonal pass over sample runs
   bool diag = false;
   DiagItem* diag_items = nullptr;  // [n_diag_items]

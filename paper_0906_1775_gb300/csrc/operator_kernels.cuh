@@ -97,6 +97,8 @@ struct OpArgs {
   void* scratch;
   const void* H;
   const void* tw;
+  int n_rep;          // > 1: map outputs go to replica (blockIdx.x + blockIdx.y) % n_rep, rep_stride apart
+  long long rep_stride;
   const int* skip;    // done flag(s): one shared flag, or one per right-hand side
   int skip_stride;    // 0: *skip covers every tile; > 0: skip[rhs * skip_stride] per lane
 };
@@ -337,7 +339,9 @@ __device__ __forceinline__ LaneView<Real> lane_view(const OpArgs& a, const Lane&
   else v.in = static_cast<const Real*>(a.in) + g.rhs * a.in_stride;
   typedef typename OutT<Real>::type Out;
   if (OUT == OUT_TOD) v.out = static_cast<Out*>(a.out) + g.rhs * a.out_stride + ws;
-  else v.out = static_cast<Out*>(a.out) + g.rhs * a.out_stride;
+  else
+    v.out = static_cast<Out*>(a.out) + g.rhs * a.out_stride +
+            (a.n_rep > 1 ? (long long)((blockIdx.x + blockIdx.y) % a.n_rep) * a.rep_stride : 0LL);
   return v;
 }
 
@@ -870,6 +874,19 @@ __global__ void __launch_bounds__(256) k_diag(OpArgs a, const DiagItem* __restri
   }
 }
 
+// out += the sum of the map replicas, which are left zero for the next application
+template <typename Out>
+__global__ void k_rep_reduce(Out* rep, int n_rep, long long stride, Out* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    Out acc = Out(0);
+    for (int k = 0; k < n_rep; ++k) {
+      acc += rep[k * stride + i];
+      rep[k * stride + i] = Out(0);
+    }
+    out[i] += acc;
+  }
+}
+
 template <typename Real>
 inline int elems_per_cta() {
   return sizeof(Real) == 4 ? 4096 : 2048;
@@ -991,6 +1008,8 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
   a.tw = DF ? (const void*)p->twdf : sizeof(Real) == 8 ? (const void*)p->tw64 : (const void*)p->tw32;
   a.skip = skip;
   a.skip_stride = ts ? skip_stride : 0;
+  a.n_rep = 1;
+  a.rep_stride = 0;
   a.tiles = ts ? ts->tiles : p->tiles;
   const int n_tiles = ts ? ts->n_tiles : p->n_tiles;
   const size_t sm13 = smem_f13<Real>(p), sm2 = smem_f2<Real>(p);
@@ -1025,8 +1044,15 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
   }
   int n_chunks, per_chunk;
   chunking(p, n_chunks, per_chunk, n_tiles);
+  // map replicas for small, heavily hit maps (single right-hand side per launch)
+  typedef typename OutT<Real>::type Out;
+  const bool use_rep = !ts && OUT == OUT_MAP && p->n_rep > 1 && p->rep;
+  const long long n_map = (long long)std::max(1, p->n_obs) * p->ns_pad;
   // several chunks: alternate two streams (own scratch slot each) so chunks overlap
-  const bool pipe = !ev && n_rhs > 0 && n_chunks > 1 && p->op_stream[0] && p->scratch_slots > 1;
+  // (with replicas only when one application is enqueued: the replicas are reused)
+  const bool pipe = !ev && n_rhs > 0 && n_chunks > 1 && p->op_stream[0] && p->scratch_slots > 1 &&
+                    (!use_rep || n_rhs * reps == 1);
+  const int rgrid = (int)std::min<long long>((n_map + 255) / 256, 152LL * 8);
   const size_t slot_bytes = (size_t)p->tiles_per_chunk * p->M * sizeof(double2);
   if (pipe) {
     MM_CUDA(cudaEventRecord(p->op_fork, s));
@@ -1038,6 +1064,12 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
       a.in = static_cast<const char*>(in) + (size_t)r * in_stride *
                                                 (IN == IN_TODF ? sizeof(float) : sizeof(Real));
       a.out = static_cast<char*>(out) + (size_t)r * out_stride * sizeof(typename OutT<Real>::type);
+      Out* const map_out = static_cast<Out*>(a.out);
+      if (use_rep) {
+        a.out = p->rep;
+        a.n_rep = p->n_rep;
+        a.rep_stride = n_map;
+      }
       // a tile set names each lane's right-hand side, with per-rhs strides;
       // otherwise the plan's tiles are replayed once per right-hand side
       a.in_stride = ts ? in_stride : 0;
@@ -1057,9 +1089,19 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
         K.f3<<<g13, OP_THREADS, sm13, cs>>>(a);
         if (ev) cudaEventRecord(ev[ei++], s);
       }
+      if (use_rep) {
+        if (pipe) {
+          for (int i = 0; i < 2; ++i) {
+            MM_CUDA(cudaEventRecord(p->op_join[i], p->op_stream[i]));
+            MM_CUDA(cudaStreamWaitEvent(s, p->op_join[i], 0));
+          }
+        }
+        k_rep_reduce<Out><<<rgrid, 256, 0, s>>>(static_cast<Out*>(p->rep), p->n_rep, n_map, map_out, n_map);
+        count_launches(1);
+      }
     }
   }
-  if (pipe) {
+  if (pipe && !use_rep) {
     for (int i = 0; i < 2; ++i) {
       MM_CUDA(cudaEventRecord(p->op_join[i], p->op_stream[i]));
       MM_CUDA(cudaStreamWaitEvent(s, p->op_join[i], 0));

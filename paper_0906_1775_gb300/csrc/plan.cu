@@ -1410,6 +1410,13 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
     }
   }
   MM_TRY(dalloc(p, &p->scratch, (size_t)p->scratch_slots * p->tiles_per_chunk * p->M * sizeof(double2)));
+  if (p->n_obs > 0 && p->n_t >= 1024LL * p->n_obs && (long long)p->n_obs * p->ns_pad <= (1LL << 17)) {
+    // a small map under more than 1024 samples per row: eight scatter replicas
+    p->n_rep = 8;
+    const size_t rb = sizeof(double) * (size_t)p->n_rep * p->n_obs * p->ns_pad;
+    MM_TRY(dalloc(p, &p->rep, rb));
+    MM_TRYC(cudaMemsetAsync(p->rep, 0, rb, s));
+  }
   MM_TRYC(cudaStreamSynchronize(s));
   MM_TRYC(cudaGetLastError());
 #undef MM_TRY
@@ -1449,6 +1456,7 @@ extern "C" madmap_status madmap_plan_get_stats(madmap_plan_t plan, madmap_plan_s
   o->n_excised_extra = p->n_excised_extra;
   o->n_hwp_params = 32 * p->n_hwp_groups;
   o->n_excised_hwp = p->n_excised_hwp;
+  o->n_map_replicas = p->n_rep;
   return MADMAP_OK;
 }
 

@@ -515,3 +515,34 @@ def test_backward_params_match_finite_differences():
     assert float(gv.sum()) == pytest.approx(fd, rel=1e-4, abs=1e-5 * float(gv.abs().sum()))
     # a common scale of every sigma leaves the map unchanged
     assert abs(float(np.sum(base[:, 0] * gp[:, 0]))) <= 1e-4 * float(np.sum(np.abs(base[:, 0] * gp[:, 0])))
+
+
+# ------------------------------------------------------------------ small maps under many samples
+@pytest.mark.parametrize("kind", ["T", "IQU"])
+def test_replicated_scatter_of_small_heavily_hit_maps(kind):
+    """A map of at most a few dozen rows under more than 1024 samples per row: the
+    operator scatters into eight replicas and adds them up; every product still
+    matches the oracle, including several right-hand sides in one call."""
+    torch = _torch()
+    if kind == "T":
+        p = tiny_T(seed=101, n=40000, width=4, ivls=(15000, 15000, 10000), n_lags=16)
+    else:
+        p = tiny_IQU(seed=102, n_per_det=10000, width=3, n_lags=12, n_ivl_lo=2000, n_ivl_hi=6000)
+    S = system_for(p)
+    plan = make_plan(p)
+    assert plan.stats["n_map_replicas"] == 8
+    x = np.random.default_rng(12).standard_normal((3, S.n_obs, p.n_stokes))
+    for prec in ("fp64", "df64", "fp32"):
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        y = host(plan.apply_ATNA(cuda(x, dt), precision=prec))
+        for k in range(3):
+            xin = x[k].astype(np.float32).astype(np.float64) if prec == "fp32" else x[k]
+            assert rel_rms(y[k], S.H(xin)) < (FP32_OP_TOL if prec == "fp32" else FP64_OP_TOL), prec
+    b = host(plan.rhs(cuda(p.d), precision="fp64"))[0]
+    assert rel_rms(b, S.rhs(p.d[0])) < FP64_OP_TOL
+    m, info = plan.solve(cuda(p.d[0]), precision="fp64", rel_tol=1e-13, max_iter=400)
+    xo, _ = S.solve(p.d[0], rel_tol=1e-13, max_iter=400)
+    assert rel_rms(host(m), xo) < FP64_MAP_TOL
+    mm_, _ = plan.solve(cuda(p.d[0]), precision="mixed", rel_tol=1e-12, max_iter=400, max_outer=20)
+    keep = ~S.excised
+    assert rel_rms(host(mm_)[keep], xo[keep]) < MIXED_MAP_TOL
