@@ -59,7 +59,6 @@ struct TileSet {
   Tile* tiles = nullptr;  // device
   int n_tiles = 0;
   int n_rhs = 0;
-  void* rep = nullptr;    // map replicas of every right-hand side (plans with n_rep > 1), zero between uses
 };
 
 // ---------------------------------------------------------------- double-float

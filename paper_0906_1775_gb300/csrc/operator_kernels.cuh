@@ -1046,7 +1046,7 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
   chunking(p, n_chunks, per_chunk, n_tiles);
   // map replicas for small, heavily hit maps (single right-hand side per launch)
   typedef typename OutT<Real>::type Out;
-  const bool use_rep = OUT == OUT_MAP && p->n_rep > 1 && (ts ? ts->rep != nullptr : p->rep != nullptr);
+  const bool use_rep = !ts && OUT == OUT_MAP && p->n_rep > 1 && p->rep;
   const long long n_map = (long long)std::max(1, p->n_obs) * p->ns_pad;
   // several chunks: alternate two streams (own scratch slot each) so chunks overlap
   // (with replicas only when one application is enqueued: the replicas are reused)
@@ -1065,10 +1065,10 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
                                                 (IN == IN_TODF ? sizeof(float) : sizeof(Real));
       a.out = static_cast<char*>(out) + (size_t)r * out_stride * sizeof(typename OutT<Real>::type);
       Out* const map_out = static_cast<Out*>(a.out);
-      if (use_rep) {  // tile sets: replica k holds every rhs's map, out_stride apart
-        a.out = ts ? ts->rep : p->rep;
+      if (use_rep) {
+        a.out = p->rep;
         a.n_rep = p->n_rep;
-        a.rep_stride = ts ? (long long)ts->n_rhs * out_stride : n_map;
+        a.rep_stride = n_map;
       }
       // a tile set names each lane's right-hand side, with per-rhs strides;
       // otherwise the plan's tiles are replayed once per right-hand side
@@ -1096,10 +1096,7 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
             MM_CUDA(cudaStreamWaitEvent(s, p->op_join[i], 0));
           }
         }
-        const long long n_red = ts ? (long long)ts->n_rhs * out_stride : n_map;
-        const int grid_red = (int)std::min<long long>((n_red + 255) / 256, 152LL * 8);
-        k_rep_reduce<Out><<<ts ? grid_red : rgrid, 256, 0, s>>>(static_cast<Out*>(a.out), p->n_rep, a.rep_stride,
-                                                               map_out, n_red);
+        k_rep_reduce<Out><<<rgrid, 256, 0, s>>>(static_cast<Out*>(p->rep), p->n_rep, n_map, map_out, n_map);
         count_launches(1);
       }
     }

@@ -787,15 +787,6 @@ madmap_status get_tile_set(Plan* p, int n_rhs, TileSet** out) {
       return cuda_fail(e, "cudaMemcpy (tile set)");
     }
   }
-  if (p->n_rep > 1) {  // replicas of the n_rhs maps for the scatter (see Plan::n_rep)
-    const size_t rb = sizeof(double) * (size_t)p->n_rep * n_rhs * std::max(1, p->n_obs) * p->ns_pad;
-    st = dalloc(p, &t->rep, rb);
-    cudaError_t e = st == MADMAP_OK ? cudaMemset(t->rep, 0, rb) : cudaSuccess;
-    if (st != MADMAP_OK || e != cudaSuccess) {
-      delete t;
-      return st != MADMAP_OK ? st : cuda_fail(e, "cudaMemset (tile set replicas)");
-    }
-  }
   p->tile_sets.push_back(t);
   *out = t;
   return MADMAP_OK;

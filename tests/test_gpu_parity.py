@@ -546,13 +546,3 @@ def test_replicated_scatter_of_small_heavily_hit_maps(kind):
     mm_, _ = plan.solve(cuda(p.d[0]), precision="mixed", rel_tol=1e-12, max_iter=400, max_outer=20)
     keep = ~S.excised
     assert rel_rms(host(mm_)[keep], xo[keep]) < MIXED_MAP_TOL
-    # batched solves scatter into replicas of every right-hand side's map
-    rng = np.random.default_rng(13)
-    D = np.stack([p.d[0], rng.standard_normal(p.d[0].shape).astype(np.float32),
-                  (p.d[0] * 0.3).astype(np.float32)])
-    for prec, tol in (("fp64", FP64_MAP_TOL), ("mixed", MIXED_MAP_TOL)):
-        mb, _ = plan.solve_batched(cuda(D), precision=prec, rel_tol=1e-13 if prec == "fp64" else 1e-12,
-                                   max_iter=400, max_outer=20)
-        for k in range(3):
-            xk, _ = S.solve(D[k], rel_tol=1e-13, max_iter=400)
-            assert rel_rms(host(mb[k])[keep], xk[keep]) < tol, (prec, k)
