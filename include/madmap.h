@@ -123,8 +123,8 @@ typedef struct {
   /* Extended pointing (Section 6, Eq. 26): extra unknowns o with A -> [A B],
    * B one unit entry per sample, for destriping offsets (with a white-noise
    * filter of one lag) or binned synchronous templates.  Stored pointing
-   * only (pix_pol and boresight NULL).  Maps then have n_obs + n_extra rows:
-   * the observed sky pixels, then one row per extra column with its
+   * only (pix_pol and boresight NULL).  Maps then have the observed sky
+   * pixels' rows followed by one row per extra column with its
    * amplitude in column 0 (other columns 0).  A sample that is flagged or
    * whose sky pixel is excised has a zero row in both blocks; an extra
    * column without samples is excised; its preconditioner block is
@@ -149,7 +149,8 @@ typedef struct {
 } madmap_plan_desc;
 
 typedef struct {
-  int32_t n_obs;           /* observed pixels */
+  int32_t n_obs;           /* map rows: observed pixels (slots for multi-resolution plans; plus the
+                              extra and half-wave-plate rows of extended pointing) */
   int32_t n_excised;       /* observed pixels excised (IQU, Section 4) */
   int32_t n_fp64_pixels;   /* pixels keeping float64 preconditioner blocks */
   int32_t n_stokes;
