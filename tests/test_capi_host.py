@@ -114,3 +114,48 @@ def test_ctypes_structs_match_the_header_layout(tmp_path):
         assert got == int(value), (name, field, got, value)
         seen += 1
     assert seen == sum(len(c._fields_) + 1 for c in structs.values())
+
+
+def test_plain_c_program_links_and_calls_the_library(tmp_path):
+    """The C ABI from plain C (no Python, no torch): a program compiled against
+    include/madmap.h and linked to libmadmap.so calls the host-side entry points and
+    gets argument errors as status codes with a message."""
+    import shutil
+    import subprocess
+    mm = _lib()
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    src = tmp_path / "use.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "madmap.h"
+int main(void) {
+  double lags[16], dl[48];
+  printf("version %s\n", madmap_version());
+  printf("filter %d", (int)madmap_noise_filter(16, 100.0, 1.0, 0.1, 2.0, lags, dl));
+  for (int i = 0; i < 16; ++i) printf(" %.17g", lags[i]);
+  printf("\n");
+  printf("fftlen %lld\n", (long long)madmap_paper_fft_length(1024, 100000));
+  madmap_plan_t plan = 0;
+  madmap_status st = madmap_plan_create(0, 0, &plan);
+  printf("create %d %s\n", (int)st, madmap_last_error());
+  st = madmap_noise_filter(0, 100.0, 1.0, 0.1, 2.0, lags, 0);
+  printf("badfilter %d\n", (int)st);
+  return 0;
+}
+''')
+    lib_dir = os.path.dirname(mm.library_path())
+    exe = tmp_path / "use"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe), "-L", lib_dir,
+                    "-lmadmap", "-Wl,-rpath," + lib_dir], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines()
+    assert out[0].startswith("version madmap")
+    f = out[1].split()
+    assert f[1] == "0"
+    vals = np.array([float(v) for v in f[2:]])
+    ref, _ = mm.noise_filter(16, 100.0, 1.0, 0.1, 2.0, with_grad=True)
+    assert np.array_equal(vals, ref)
+    assert int(out[2].split()[1]) == mm.paper_fft_length(1024, 100000)
+    assert out[3].startswith("create -1 ") and len(out[3]) > len("create -1 ")
+    assert out[4] == "badfilter -1"
