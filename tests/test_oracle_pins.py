@@ -765,3 +765,15 @@ def test_extended_hwp_dense_cholesky_symmetry_and_reduction():
     x0 = np.zeros((E0.n_obs, 3))
     x0[:E1.n_obs] = x1
     assert np.allclose(E0.H(x0)[:E1.n_obs], E1.H(x1), rtol=1e-12, atol=1e-12) and E0.excised_hwp.all()
+
+
+def test_gcp_expansion_does_not_depend_on_the_chunking():
+    """The expansion walks the samples in chunks; any chunk size gives the same pointing."""
+    from oracle.gcp import expand, nodes_needed
+    from synth.boresight import make_boresight_problem
+    p = make_boresight_problem("ch", 22, 16, 3, 2000, 8, 3, 6, noise=(1.0, 2.0, 1.5), rot_period=1500)
+    assert p.boresight.shape[0] == nodes_needed(p.samples_per_det, p.bore_step)
+    a = expand(p.boresight, p.bore_step, p.det, p.samples_per_det, p.width, p.height)
+    b = expand(p.boresight, p.bore_step, p.det, p.samples_per_det, p.width, p.height, chunk=37)
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
