@@ -17,6 +17,10 @@ solver     H = A^T N^-1 A, b = A^T N^-1 d, the block preconditioner, PCG with
            the lowest-residual output rule, and the dense Cholesky solve
            (Sections 3-5, Eqs. 8 and 10)
 adjoint    gradient of a map loss through the solve by the implicit adjoint
+multires   Q/U on a second pixelisation (Section 6, item 4)
+gcp        pointing expanded from compressed boresight pointing (Section 5.3)
+extended   extra columns [A B]: destriping offsets, binned templates and the
+           half-wave-plate block (Section 6, items 1-3, Eqs. 26-28)
 
 Every function carries "parity pinned by" notes naming the tests that tie it
 to something other than itself.
