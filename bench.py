@@ -163,10 +163,17 @@ def stokes_err(m, ref, keep):
 
 
 def operator_source_hash():
+    """SHA-256 of the operator's code (comments and blank lines removed, so a comment
+    edit does not orphan the committed traffic counters)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("operator_kernels.cuh", "internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_0906_1775_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_0906_1775_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        code = "\n".join(ln.rstrip() for ln in src.splitlines() if ln.strip())
+        h.update(code.encode())
     return h.hexdigest()
 
 

@@ -120,7 +120,7 @@ typedef struct {
   int32_t n_det;                    /* detectors (>= 1; must divide n_samples); no interval
                                        may span two detectors */
   int32_t grid_width, grid_height;  /* flat pixel grid; n_pix must equal their product */
-  /* Extended pointing (Section 6, Eq. 26): extra unknowns o with A -> [A B],
+  /* Extended pointing (Section 6, Eqs. 39-40): extra unknowns o with A -> [A B],
    * B one unit entry per sample, for destriping offsets (with a white-noise
    * filter of one lag) or binned synchronous templates.  Stored pointing
    * only (pix_pol and boresight NULL).  Maps then have the observed sky
@@ -134,7 +134,7 @@ typedef struct {
   const int32_t* extra_index;       /* device [n_samples]: extra column of each sample in
                                        [0, n_extra), or -1 (none); NULL: no extra columns */
   int32_t n_extra;                  /* extra columns (>= 1 when extra_index is set) */
-  /* Parametric half-wave-plate signal (Section 6, Eqs. 27-28), with or without
+  /* Parametric half-wave-plate signal (Section 6, Eqs. 41-42), with or without
    * extra_index, stored single-resolution pointing only: 32 unknowns per group
    * of intervals, b_1..b_32 with the sample's columns cos k w, tau cos k w,
    * sin k w, tau sin k w (k = 1..8, in that order), w = hwp_angle, tau =

@@ -20,7 +20,7 @@ adjoint    gradient of a map loss through the solve by the implicit adjoint
 multires   Q/U on a second pixelisation (Section 6, item 4)
 gcp        pointing expanded from compressed boresight pointing (Section 5.3)
 extended   extra columns [A B]: destriping offsets, binned templates and the
-           half-wave-plate block (Section 6, items 1-3, Eqs. 26-28)
+           half-wave-plate block (Section 6, items 1-3, Eqs. 39-43)
 
 Every function carries "parity pinned by" notes naming the tests that tie it
 to something other than itself.

@@ -3,7 +3,7 @@
 
 Section 6 (items 1 and 3): the data model gains a term B o, d = A z + B o + n,
 and the map vector and pointing matrix are extended to [z; o] and [A B]
-(Eq. 26), so the same PCG solves for both.  Here B has one unit entry per
+(Eqs. 39-40), so the same PCG solves for both.  Here B has one unit entry per
 sample: column e_t = ``extra_index[t]`` (-1: none).  That covers
 
 * destriping offsets (item 3): e_t = the baseline interval of sample t, with
@@ -11,7 +11,7 @@ sample: column e_t = ``extra_index[t]`` (-1: none).  That covers
 * non-parametric synchronous signals (item 1): e_t = the bin of the sample's
   synchronous parameter (e.g. a chopper angle);
 
-and, for the parametric half-wave-plate signal of item 2 (Eqs. 27-28), a
+and, for the parametric half-wave-plate signal of item 2 (Eqs. 41-42), a
 dense block C of 32 columns per group of intervals: with the polariser angle
 w_t and the time variable tau_t of sample t, C_{t,k} = cos k w_t,
 C_{t,8+k} = tau_t cos k w_t, C_{t,16+k} = sin k w_t, C_{t,24+k} = tau_t sin k w_t
@@ -148,7 +148,7 @@ class ExtendedSystem:
         return self.sky.ninv(y)
 
     def H(self, x):
-        """[A B]^T N^-1 [A B] x (Eq. 10 with the extended pointing of Eq. 26)."""
+        """[A B]^T N^-1 [A B] x (Eq. 10 with the extended pointing of Eq. 40)."""
         return self.point(self.ninv(self.unpoint(x)))
 
     def rhs(self, d):
@@ -203,7 +203,7 @@ class ExtendedSystem:
 
 
 def hwp_columns(angle, tau):
-    """The 32 columns of Eq. 28 for every sample, float64 from the float32 inputs."""
+    """The 32 columns of Eq. 42 for every sample, float64 from the float32 inputs."""
     w = np.asarray(angle, dtype=np.float32).astype(np.float64)
     t = np.asarray(tau, dtype=np.float32).astype(np.float64)
     k = np.arange(1, 9)

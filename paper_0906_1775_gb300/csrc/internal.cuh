@@ -212,7 +212,7 @@ __device__ __forceinline__ void atomic_add_warp(Out* base, long long idx, Out v)
   if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(base + idx, acc);
 }
 
-// Half-wave-plate columns of one sample (Section 6, Eq. 28), in the column
+// Half-wave-plate columns of one sample (Section 6, Eq. 42), in the column
 // order b_1..b_32: cos k w, tau cos k w, sin k w, tau sin k w for k = 1..8.
 // The harmonics come from one sincos by the angle-addition recurrence.
 template <typename W>

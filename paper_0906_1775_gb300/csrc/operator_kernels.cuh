@@ -44,7 +44,7 @@ enum { IN_MAPX = 0, IN_TODF = 1, IN_TODR = 2 };
 // each sample then carries an I pixel and a Q/U pixel of the slot layout).
 // NS_OTF_T / NS_OTF_IQU: T / IQU with the pointing expanded on the fly from
 // compressed boresight pointing (Section 5.3) instead of read per sample.
-// NS_EXT_T / NS_EXT_IQU: T / IQU with extended pointing (Section 6, Eq. 26):
+// NS_EXT_T / NS_EXT_IQU: T / IQU with extended pointing (Section 6, Eq. 40):
 // each sample may add one unit-weight extra column (a row after the sky rows).
 constexpr int NS_MR = 4;
 constexpr int NS_OTF_T = 5;

@@ -1,4 +1,4 @@
-"""Extended pointing on the GPU (Section 6, Eq. 26: destriping offsets and
+"""Extended pointing on the GPU (Section 6, Eq. 40: destriping offsets and
 binned synchronous templates as extra unit-weight columns) against the FP64
 oracle ``oracle.extended``.
 

@@ -732,7 +732,7 @@ def _hwp_case(seed, noiseless=True, n_per=1500):
 
 
 def test_extended_hwp_noiseless_recovery():
-    """An injected half-wave-plate signal (Eqs. 27-28, synthesised as the real part of a
+    """An injected half-wave-plate signal (Eqs. 41-42, synthesised as the real part of a
     complex-exponential sum) and an IQU sky, noiseless: both are recovered."""
     p, hwp, b, d = _hwp_case(61)
     E = _ext_system(p, np.full(p.n_samples, -1, np.int32), 1, hwp=hwp)
