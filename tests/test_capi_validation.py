@@ -95,3 +95,28 @@ KEYWORD = {
     "boresight_nodes": "n_bore", "boresight_grid": "grid_width", "boresight_det_finite": "det_pointing",
     "boresight_interval_spans_detectors": "spans two detectors",
 }
+
+
+@pytest.mark.parametrize("case", ["precision", "offsets", "filter", "lags", "too_many_lags"])
+def test_noalloc_weighting_checks_its_arguments_on_the_host(case):
+    mm = _lib()
+    L = mm.load()
+    off = np.array([0, 500, 1000], dtype=np.int64)
+    filt = np.array([0, 0], dtype=np.int32)
+    lags = np.array([[1.0, 0.1]])
+    prec, n_lags = mm._lib.MADMAP_FP64, 2
+    if case == "precision":
+        prec = mm._lib.MADMAP_MIXED
+    elif case == "offsets":
+        off = np.array([0, 500, 999], dtype=np.int64)
+    elif case == "filter":
+        filt = np.array([0, 3], dtype=np.int32)
+    elif case == "lags":
+        lags = np.array([[1.0, np.inf]])
+    else:
+        n_lags = (1 << 15) + 1
+        lags = np.ones((1, n_lags))
+    st = L.madmap_apply_ninv_noalloc(prec, 1000, 2, off.ctypes.data, filt.ctypes.data, 1, n_lags, lags.ctypes.data,
+                                     FAKE_DEV, FAKE_DEV, None)
+    assert st == mm._lib.MADMAP_ERR_INVALID_ARG, (case, st, mm.madmap_last_error())
+    assert "apply_ninv_noalloc" in mm.madmap_last_error()
