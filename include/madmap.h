@@ -54,6 +54,17 @@ typedef enum {
   MADMAP_ERR_INTERNAL = -6
 } madmap_status;
 
+/* Sums `count` elements of a device buffer, in place, over all ranks of a
+ * sharded solve (see madmap_plan_desc.allreduce).  dtype: MADMAP_REDUCE_F64
+ * (double), MADMAP_REDUCE_F32 (float) or MADMAP_REDUCE_I32 (int32).  The
+ * library calls it on the host, from the thread that made the library call,
+ * with work on `stream` (a cudaStream_t) producing the buffer; the sum must be
+ * complete, or ordered on `stream`, before the callback returns.  Every rank
+ * makes the same calls in the same order.  Returns 0 on success; any other
+ * value makes the library call fail with MADMAP_ERR_INTERNAL. */
+typedef int32_t (*madmap_reduce_fn)(void* buf, int64_t count, int32_t dtype, void* stream, void* user);
+enum { MADMAP_REDUCE_F64 = 0, MADMAP_REDUCE_F32 = 1, MADMAP_REDUCE_I32 = 2 };
+
 typedef enum {
   MADMAP_FP64 = 0,   /* operator, vectors and scalars in float64 */
   MADMAP_MIXED = 1,  /* float32 operator and vectors inside float64 iterative refinement */
@@ -146,6 +157,24 @@ typedef struct {
   const int32_t* interval_hwp_group;/* host [n_intervals]: group of each interval in [0, n_hwp_groups)
                                        or -1 (no half-wave-plate term) */
   int32_t n_hwp_groups;             /* >= 1 when hwp_angle is set */
+  /* Sharded solves over several processes, one GPU each (Section 5.1: each
+   * process holds a share of the time-ordered data made of whole stationary
+   * intervals, balanced by sample count, see madmap_partition_intervals;
+   * Section 5.5: the map-domain sum across processes once per operator
+   * application, the role of MM_SomeReduce).  With allreduce set, this plan
+   * holds one rank's samples and intervals; the observed-pixel set, the hit
+   * counts and the preconditioner blocks are summed across ranks at
+   * plan_create (so every rank has the same map rows and excisions), and every
+   * map that madmap_apply_ATNA, madmap_rhs, the solves and the backward pass
+   * produce (H x, b, the refinement residuals, grad_lags) is summed across ranks
+   * before it is used.  The PCG vector work and dot products then run
+   * redundantly on the identical maps of every rank, so the ranks take the
+   * same decisions with no further exchange.  Every rank must make the same
+   * calls on its plan in the same order.  Stored single-resolution pointing
+   * only; solves run with direct launches (use_graph is treated as 0).
+   * NULL: an ordinary single-process plan. */
+  madmap_reduce_fn allreduce;
+  void* allreduce_user;             /* passed to allreduce */
 } madmap_plan_desc;
 
 typedef struct {
@@ -198,6 +227,18 @@ typedef struct {
                                          /* called after each checkpoint, may be NULL; a nonzero return
                                             stops the solve with MADMAP_STOPPED (m = best iterate so far) */
   void* checkpoint_user;                 /* passed to on_checkpoint */
+  /* Residual history (Section 5 monitors the relative residual of every
+   * iteration; the paper keeps no record of it).  Host [n_rhs][history_capacity]
+   * or NULL.  Entry k is the relative residual ||r_k|| / ||b|| after PCG
+   * iteration k (entry 0 = 1): FP64 the recursively updated residual; MIXED
+   * the inner float32 residual scaled by the relative residual of the float64
+   * iterate its refinement step started from (an estimate of ||b - H x|| / ||b||),
+   * inner iterations of all refinement steps in order.  The solve records at
+   * most 4096 iterations; madmap_solve_info.history_len tells how many entries
+   * were written.  A resumed solve writes NaN for the iterations done before
+   * the checkpoint. */
+  double* residual_history;
+  int32_t history_capacity;
 } madmap_solve_opts;
 
 /* Solver state at a checkpoint, independent of the launch configuration (a
@@ -228,6 +269,10 @@ typedef struct {
   double best_rel_res;     /* relative residual of the returned map */
   double t_rhs_ms;         /* right-hand side time */
   double t_solve_ms;       /* total call time (right-hand side included) */
+  int32_t history_len;     /* entries written to madmap_solve_opts.residual_history */
+  int32_t pad_;
+  double t_pcg_ms;         /* host time spent in PCG iterations (MIXED: the inner float32 solves) */
+  double t_refine_ms;      /* MIXED: host time of the refinement steps (x += e, b - H x, best iterate) */
 } madmap_solve_info;
 
 /* ------------------------------------------------------------------ plans */
@@ -237,6 +282,17 @@ typedef struct {
  * spectra and work buffers.  Synchronises `stream` before returning.
  * out: receives the plan (NULL on error). */
 madmap_status madmap_plan_create(const madmap_plan_desc* desc, void* stream, madmap_plan_t* out);
+
+/* The concatenated data distribution of Section 5.1: the intervals, in
+ * order, are cut into n_ranks contiguous runs of whole intervals whose sample
+ * counts are as equal as the interval boundaries allow: rank r's run ends at
+ * the boundary (an index j into interval_offsets) nearest to
+ * (r + 1) n_samples / n_ranks, the lowest such j on ties, and never before the
+ * previous rank's end.  interval_offsets: host
+ * [n_intervals + 1] as in madmap_plan_desc; first_interval_out: host
+ * [n_ranks + 1], rank r gets intervals [first[r], first[r + 1]).  Host only. */
+madmap_status madmap_partition_intervals(int32_t n_intervals, const int64_t* interval_offsets, int32_t n_ranks,
+                                         int32_t* first_interval_out);
 
 /* Free all device memory of a plan.  NULL is accepted. */
 madmap_status madmap_plan_destroy(madmap_plan_t plan);
@@ -345,9 +401,13 @@ madmap_status madmap_solve_resume(madmap_plan_t plan, const madmap_checkpoint* s
  * definite returns MADMAP_ERR_NOT_PD.
  *
  * The array is shared by all calls and keeps the last call's contents; calls
- * that overlap on the GPU race on it.  The first call on a device looks up the
- * array's device address; make that call before any stream capture.  Ordered
- * on `stream`; returns once the work is enqueued. */
+ * that overlap on the GPU race on it.  Every call looks up the array's device
+ * address for the device that is current.  Ordered on `stream`.  The derived
+ * tables are uploaded from host memory that lives only during the call: the
+ * upload may hold the host until `stream` reaches it, and a call made while
+ * `stream` is being captured into a CUDA graph returns MADMAP_ERR_INVALID_ARG
+ * (a replay would read freed host memory).  Returns once the work is
+ * enqueued. */
 madmap_status madmap_apply_ninv_noalloc(int32_t precision, int64_t n_samples, int32_t n_intervals,
                                         const int64_t* interval_offsets, const int32_t* interval_filter,
                                         int32_t n_filters, int32_t n_lags, const double* filter_lags,
@@ -359,6 +419,17 @@ madmap_status madmap_apply_ninv_noalloc(int32_t precision, int64_t n_samples, in
  * node of a replayed CUDA graph counts once per replay; kernels that return
  * at once because a solve already finished still count). */
 int64_t madmap_kernel_launch_count(void);
+
+/* The polarisation weights (cos 2psi, sin 2psi) of Section 3, Eq. 4 (as
+ * relabelled above) for n angles, formed exactly as the operator kernels of
+ * `precision` form them: FP32 reduces 2 psi to [-pi, pi] (Cody-Waite, two
+ * parts of 2 pi) and uses the hardware sine and cosine approximations (absolute
+ * error below 1e-6 against the exact weights of the float32 angle); FP64
+ * uses correctly rounded float64 sincos of 2 (double) psi.  psi: device float
+ * [n] radians; cos2psi, sin2psi: device [n], float for FP32, double for FP64.
+ * A diagnostic of the weights alone.  Asynchronous on `stream`. */
+madmap_status madmap_polarisation_weights(int32_t precision, int64_t n, const float* psi, void* cos2psi,
+                                          void* sin2psi, void* stream);
 
 /* Times the operator H = A^T N^-1 A in the plan's launch configuration:
  * `reps` applications to the plan's current search-direction buffer.  First

@@ -20,13 +20,14 @@ from . import _lib
 from ._lib import (MADMAP_DF64, MADMAP_FP32, MADMAP_FP64, MADMAP_MIXED, MadmapError, check, load)  # noqa: F401
 
 __all__ = ["Plan", "noise_filter", "paper_fft_length", "MadmapError", "load", "library_path",
+           "madmap_partition_intervals", "partition_intervals", "shard_range", "torch_allreduce",
            "madmap_plan_create", "madmap_plan_destroy", "madmap_plan_get_stats", "madmap_plan_observed",
            "madmap_plan_observed_pol", "madmap_plan_expand_pointing",
            "madmap_plan_set_filters", "madmap_apply_ATNA", "madmap_rhs", "madmap_apply_ninv", "madmap_solve",
            "madmap_solve_batched", "madmap_solve_backward", "madmap_noise_filter_vjp", "MadmapSolve",
            "madmap_noise_filter", "madmap_paper_fft_length", "madmap_last_error", "madmap_kernel_launch_count",
-           "madmap_time_operator", "madmap_apply_ninv_noalloc", "madmap_solve_resume", "save_checkpoint",
-           "load_checkpoint"]
+           "madmap_time_operator", "madmap_polarisation_weights", "madmap_apply_ninv_noalloc",
+           "madmap_solve_resume", "save_checkpoint", "load_checkpoint"]
 
 _PREC = {"fp64": MADMAP_FP64, "mixed": MADMAP_MIXED, "fp32": MADMAP_FP32, "df64": MADMAP_DF64,
          MADMAP_FP64: MADMAP_FP64, MADMAP_MIXED: MADMAP_MIXED, MADMAP_FP32: MADMAP_FP32, MADMAP_DF64: MADMAP_DF64}
@@ -68,6 +69,76 @@ def madmap_plan_create(desc, stream=None):
 
 def madmap_plan_destroy(h):
     check(load().madmap_plan_destroy(h), "madmap_plan_destroy")
+
+
+def madmap_partition_intervals(interval_offsets, n_ranks) -> np.ndarray:
+    """First interval of each rank (int32 [n_ranks + 1]) under the concatenated
+    distribution of Section 5.1 (whole intervals, balanced by sample count)."""
+    off = np.ascontiguousarray(interval_offsets, dtype=np.int64)
+    first = np.zeros(int(n_ranks) + 1, dtype=np.int32)
+    check(load().madmap_partition_intervals(int(off.shape[0]) - 1, off.ctypes.data, int(n_ranks),
+                                            first.ctypes.data), "madmap_partition_intervals")
+    return first
+
+
+partition_intervals = madmap_partition_intervals
+
+
+def shard_range(interval_offsets, n_ranks, rank):
+    """(first interval, end interval, first sample, end sample) of one rank's share."""
+    first = madmap_partition_intervals(interval_offsets, n_ranks)
+    off = np.asarray(interval_offsets, dtype=np.int64)
+    i0, i1 = int(first[rank]), int(first[rank + 1])
+    return i0, i1, int(off[i0]), int(off[i1])
+
+
+class _DeviceArray:
+    """A raw device buffer seen through __cuda_array_interface__ (no copy)."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+_REDUCE_TYPES = {_lib.MADMAP_REDUCE_F64: "<f8", _lib.MADMAP_REDUCE_F32: "<f4", _lib.MADMAP_REDUCE_I32: "<i4"}
+
+
+def torch_allreduce(group=None):
+    """A madmap_reduce_fn over torch.distributed (sum over the ranks of `group`).
+
+    NCCL process groups sum the device buffer in place, ordered on the library's
+    stream; other backends (gloo) copy it to host memory, sum there and copy it
+    back before returning.  Pass the result as Plan(..., allreduce=...)."""
+    import torch.distributed as dist
+    torch = _torch()
+    nccl = dist.get_backend(group) == "nccl"
+
+    def reduce(ptr, count, dtype, stream):
+        t = torch.as_tensor(_DeviceArray(ptr, count, _REDUCE_TYPES[dtype]), device="cuda")
+        es = torch.cuda.ExternalStream(int(stream)) if stream else torch.cuda.default_stream()
+        with torch.cuda.stream(es):
+            if nccl:
+                dist.all_reduce(t, group=group)
+            else:
+                es.synchronize()
+                h = t.cpu()
+                dist.all_reduce(h, group=group)
+                t.copy_(h)
+    return reduce
+
+
+def _reduce_callback(fn):
+    """ctypes wrapper of a Python reducer fn(ptr, count, dtype, stream_ptr); exceptions
+    become a non-zero status (the library call then fails with ERR_INTERNAL)."""
+    def cb(buf, count, dtype, stream, _user):
+        try:
+            fn(buf or 0, count, dtype, stream or 0)
+            return 0
+        except Exception as e:  # pragma: no cover - reported through the status
+            cb.error = e
+            return 1
+    cb.error = None
+    return _lib.REDUCE_FN(cb), cb
 
 
 def madmap_plan_get_stats(h) -> dict:
@@ -238,6 +309,19 @@ def madmap_kernel_launch_count() -> int:
     return int(load().madmap_kernel_launch_count())
 
 
+def madmap_polarisation_weights(psi, precision="fp32", stream=None):
+    """(cos 2psi, sin 2psi) of a float32 CUDA tensor of angles, formed as the
+    operator kernels of `precision` ("fp32" or "fp64") form them."""
+    torch = _torch()
+    ptr = _dev_ptr(psi, torch.float32, "psi")
+    dt = torch.float32 if _PREC[precision] == MADMAP_FP32 else torch.float64
+    c = torch.empty(psi.shape, dtype=dt, device=psi.device)
+    s = torch.empty_like(c)
+    check(load().madmap_polarisation_weights(_PREC[precision], int(psi.numel()), ptr, c.data_ptr(), s.data_ptr(),
+                                             C.c_void_p(_stream_ptr(stream))), "madmap_polarisation_weights")
+    return c, s
+
+
 def madmap_time_operator(h, precision, reps, stream=None):
     """(ms[4], launches[3]): mean ms per launch of k_f1, k_f2, k_f3 (chunks in sequence) and, in
     ms[3], mean ms of one application as solves launch it (chunks overlapped)."""
@@ -273,13 +357,17 @@ class Plan:
     hwp = (angle, tau, interval_group, n_groups) adds the 32-parameter half-wave-plate
     model per group of intervals (angle, tau: float32 CUDA tensors [n_t]; interval_group:
     host int32 [n_ivl], -1 = none): 32 * n_groups more rows after the extra rows.
+    allreduce = fn(ptr, count, dtype, stream_ptr) makes a sharded plan over this
+    rank's share of the intervals (shard_range); fn sums a device buffer across
+    the ranks, e.g. torch_allreduce().  Every rank must make the same calls.
     """
 
     def __init__(self, pix, psi, n_pix, interval_offsets, interval_filter, filter_lags, rcond_excise=0.0,
                  rcond_fp64=0.0, fft_len=0, tiles_per_chunk=0, stream=None, pix_pol=None, n_pix_pol=0,
-                 extra_index=None, n_extra=0, hwp=None):
+                 extra_index=None, n_extra=0, hwp=None, allreduce=None):
         torch = _torch()
         self._h = None
+        self._reduce = None
         off = np.ascontiguousarray(interval_offsets, dtype=np.int64)
         filt = np.ascontiguousarray(interval_filter, dtype=np.int32)
         lags = np.ascontiguousarray(np.atleast_2d(filter_lags), dtype=np.float64)
@@ -326,6 +414,9 @@ class Plan:
             d.interval_hwp_group = grp.ctypes.data if grp.size else np.zeros(1, np.int32).ctypes.data
             d.n_hwp_groups = int(n_groups)
             keep_hwp = (keep_hwp, grp)
+        if allreduce is not None:
+            self._reduce = _reduce_callback(allreduce)
+            d.allreduce = self._reduce[0]
         self._keep = (off, filt, lags, keep_hwp)
         self.multires = pix_pol is not None
         self._create(d, n_t, stream)
@@ -469,19 +560,39 @@ class Plan:
         o.refine_precision = _PREC[refine]
         return o
 
+    @staticmethod
+    def _history(o, n_rhs, max_iter, want):
+        """Host buffer for the residual history (max_iter + 1 entries per right-hand side)."""
+        if not want:
+            return None
+        cap = min(int(max_iter), 4095) + 1
+        h = np.zeros((n_rhs, cap))
+        o.residual_history = h.ctypes.data
+        o.history_capacity = cap
+        return h
+
+    @staticmethod
+    def _info(i, hist=None, k=0):
+        out = {f: getattr(i, f) for f, _ in i._fields_ if f != "pad_"}
+        if hist is not None:
+            out["history"] = hist[k, :i.history_len].copy()
+        return out
+
     def solve_batched(self, d, precision="fp64", max_iter=50, rel_tol=1e-6, max_outer=10, inner_rel_tol=1e-4,
-                      use_graph=True, iters_per_sync=8, out=None, stream=None, refine="df64"):
+                      use_graph=True, iters_per_sync=8, out=None, stream=None, refine="df64", history=False):
         """Maps [n_rhs, n_obs, n_stokes] (float64) for d [n_rhs, n_samples], and per-rhs info dicts.
-        refine ("df64" or "fp64"): arithmetic of the mixed solve's right-hand side and residuals."""
+        refine ("df64" or "fp64"): arithmetic of the mixed solve's right-hand side and residuals.
+        history: add each right-hand side's residual history (numpy) as info["history"]."""
         torch = _torch()
         d = d.reshape(-1, self.n_samples)
         n_rhs = d.shape[0]
         o = self._opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync, refine)
+        hist = self._history(o, n_rhs, max_iter, history)
         m = out if out is not None else torch.empty((n_rhs, self.n_obs, self.n_stokes), dtype=torch.float64,
                                                     device="cuda")
         infos = madmap_solve_batched(self._h, n_rhs, _dev_ptr(d, torch.float32, "d") if d.numel() else None,
                                      _dev_ptr(m, torch.float64, "m") if m.numel() else None, o, stream)
-        return m, [{k: getattr(i, k) for k, _ in i._fields_} for i in infos]
+        return m, [self._info(i, hist, k) for k, i in enumerate(infos)]
 
     def solve_backward(self, d, m, grad_m, want_d=True, want_lags=True, precision="mixed", max_iter=500,
                        rel_tol=1e-10, max_outer=20, inner_rel_tol=1e-4, use_graph=True, iters_per_sync=8,
@@ -510,13 +621,15 @@ class Plan:
 
     def solve(self, d, precision="fp64", max_iter=50, rel_tol=1e-6, max_outer=10, inner_rel_tol=1e-4,
               use_graph=True, iters_per_sync=8, out=None, stream=None, refine="df64", checkpoint_every=0,
-              on_checkpoint=None):
+              on_checkpoint=None, history=False):
         """Maximum-likelihood map [n_obs, n_stokes] (float64) and the solve info dict.
         refine ("df64" or "fp64"): arithmetic of the mixed solve's right-hand side and residuals.
         checkpoint_every > 0 (float64 solves): every that many iterations the solver state is
-        passed to on_checkpoint(state dict); a true return stops the solve (status STOPPED)."""
+        passed to on_checkpoint(state dict); a true return stops the solve (status STOPPED).
+        history: add the residual history after every iteration (numpy) as info["history"]."""
         torch = _torch()
         o = self._opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync, refine)
+        hist = self._history(o, 1, max_iter, history)
         cb = self._checkpoints(o, checkpoint_every, on_checkpoint)
         m = out if out is not None else torch.empty((self.n_obs, self.n_stokes), dtype=torch.float64,
                                                     device="cuda")
@@ -524,14 +637,15 @@ class Plan:
                             o, stream)
         if cb is not None and cb.error is not None:
             raise cb.error
-        return m, {k: getattr(info, k) for k, _ in info._fields_}
+        return m, self._info(info, hist)
 
     def solve_resume(self, state, max_iter=50, rel_tol=1e-6, use_graph=True, iters_per_sync=8, out=None,
-                     stream=None, checkpoint_every=0, on_checkpoint=None):
+                     stream=None, checkpoint_every=0, on_checkpoint=None, history=False):
         """Continue a float64 solve from a checkpoint dict (as passed to on_checkpoint or read by
         load_checkpoint); returns the best map and the info dict of the whole solve."""
         torch = _torch()
         o = self._opts("fp64", max_iter, rel_tol, 1, 1e-4, use_graph, iters_per_sync, "fp64")
+        hist = self._history(o, 1, max_iter, history)
         cb = self._checkpoints(o, checkpoint_every, on_checkpoint)
         c = _lib.madmap_checkpoint()
         keep = {}
@@ -545,7 +659,7 @@ class Plan:
         info = madmap_solve_resume(self._h, c, _dev_ptr(m, torch.float64, "m"), o, stream)
         if cb is not None and cb.error is not None:
             raise cb.error
-        return m, {k: getattr(info, k) for k, _ in info._fields_}
+        return m, self._info(info, hist)
 
 
 # ----------------------------------------------------------------- differentiable solve

@@ -31,6 +31,11 @@ STATUS_NAMES = {0: "OK", 1: "WARN_MAXITER", 2: "STOPPED", -1: "ERR_INVALID_ARG",
                 -4: "ERR_NOT_PD", -5: "ERR_TIMEOUT", -6: "ERR_INTERNAL"}
 
 
+# madmap_reduce_fn: (buf, count, dtype, stream, user) -> 0 on success
+REDUCE_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p)
+MADMAP_REDUCE_F64, MADMAP_REDUCE_F32, MADMAP_REDUCE_I32 = 0, 1, 2
+
+
 class madmap_plan_desc(C.Structure):
     _fields_ = [("n_stokes", C.c_int32), ("n_samples", C.c_int64), ("n_pix", C.c_int32),
                 ("pix", C.c_void_p), ("psi", C.c_void_p), ("n_intervals", C.c_int32),
@@ -42,7 +47,7 @@ class madmap_plan_desc(C.Structure):
                 ("det_pointing", C.c_void_p), ("n_det", C.c_int32), ("grid_width", C.c_int32),
                 ("grid_height", C.c_int32), ("extra_index", C.c_void_p), ("n_extra", C.c_int32),
                 ("hwp_angle", C.c_void_p), ("hwp_tau", C.c_void_p), ("interval_hwp_group", C.c_void_p),
-                ("n_hwp_groups", C.c_int32)]
+                ("n_hwp_groups", C.c_int32), ("allreduce", REDUCE_FN), ("allreduce_user", C.c_void_p)]
 
 
 class madmap_plan_stats(C.Structure):
@@ -70,20 +75,23 @@ class madmap_solve_opts(C.Structure):
                 ("iters_per_sync", C.c_int32),
                 ("refine_precision", C.c_int32),
                 ("checkpoint_every", C.c_int32), ("checkpoint", C.POINTER(madmap_checkpoint)),
-                ("on_checkpoint", CHECKPOINT_FN), ("checkpoint_user", C.c_void_p)]
+                ("on_checkpoint", CHECKPOINT_FN), ("checkpoint_user", C.c_void_p),
+                ("residual_history", C.c_void_p), ("history_capacity", C.c_int32)]
 
 
 class madmap_solve_info(C.Structure):
     _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("outer_iters", C.c_int32),
                 ("best_iter", C.c_int32), ("fp64_applies", C.c_int32), ("fp32_applies", C.c_int32),
                 ("final_rel_res", C.c_double), ("best_rel_res", C.c_double), ("t_rhs_ms", C.c_double),
-                ("t_solve_ms", C.c_double)]
+                ("t_solve_ms", C.c_double), ("history_len", C.c_int32), ("pad_", C.c_int32),
+                ("t_pcg_ms", C.c_double), ("t_refine_ms", C.c_double)]
 
 
 # (name, restype, argtypes) of every entry point declared in include/madmap.h
 PROTOTYPES = [
     ("madmap_plan_create", C.c_int, [C.POINTER(madmap_plan_desc), C.c_void_p, C.POINTER(C.c_void_p)]),
     ("madmap_plan_destroy", C.c_int, [C.c_void_p]),
+    ("madmap_partition_intervals", C.c_int, [C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
     ("madmap_plan_get_stats", C.c_int, [C.c_void_p, C.POINTER(madmap_plan_stats)]),
     ("madmap_plan_observed", C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_void_p, C.c_void_p, C.c_void_p]),
     ("madmap_plan_observed_pol", C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -109,6 +117,8 @@ PROTOTYPES = [
     ("madmap_apply_ninv_noalloc", C.c_int, [C.c_int32, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
                                             C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("madmap_kernel_launch_count", C.c_int64, []),
+    ("madmap_polarisation_weights", C.c_int, [C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_void_p]),
     ("madmap_time_operator", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("madmap_last_error", C.c_char_p, []),
     ("madmap_version", C.c_char_p, []),

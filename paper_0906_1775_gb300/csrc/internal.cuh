@@ -347,8 +347,15 @@ struct Plan {
   float* bw_r = nullptr;
   void* corr_items = nullptr;
   int n_corr_items = 0;
+  // sharded solves: sums map-domain buffers across the ranks (NULL: one process)
+  madmap_reduce_fn allreduce = nullptr;
+  void* allreduce_user = nullptr;
   ~Plan();
 };
+
+// Sums a device buffer across the ranks of a sharded plan (nothing to do for
+// a single-process plan).  dtype: MADMAP_REDUCE_F64 / F32 / I32.
+madmap_status reduce_across(Plan* p, void* buf, long long count, int dtype, cudaStream_t s);
 
 inline OtfPointing otf_pointing(const Plan* p) {
   OtfPointing a;
@@ -420,6 +427,8 @@ struct OpImpl {
   madmap_status (*time)(Plan* p, const void* in, void* out, int reps, double ms[4], cudaStream_t s);
   void (*occupancy)(const Plan* p, int& ctas_per_sm, int& ctas_per_tile);  // NULL for double-float
   size_t (*f13_smem)(const Plan* p);
+  // the (cos 2psi, sin 2psi) weights of n angles as this precision's kernels form them
+  madmap_status (*weights)(long long n, const float* psi, void* c, void* s, cudaStream_t st);
 };
 const OpImpl& op_impl_f32();
 const OpImpl& op_impl_f64();

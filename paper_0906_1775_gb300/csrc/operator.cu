@@ -26,7 +26,6 @@
 #include <math.h>
 
 #include <algorithm>
-#include <mutex>
 #include <vector>
 
 #include "internal.cuh"
@@ -92,6 +91,18 @@ madmap_status op_launch(Plan* p, int prec, int in_mode, int out_mode, const void
 
 extern "C" int64_t madmap_kernel_launch_count(void) { return (int64_t)mm::g_launches; }
 
+extern "C" madmap_status madmap_polarisation_weights(int32_t precision, int64_t n, const float* psi, void* cos2psi,
+                                                     void* sin2psi, void* stream) {
+  using namespace mm;
+  MM_CHECK(precision == MADMAP_FP32 || precision == MADMAP_FP64, MADMAP_ERR_INVALID_ARG,
+           "polarisation_weights: precision must be FP32 or FP64");
+  MM_CHECK(n >= 0, MADMAP_ERR_INVALID_ARG, "polarisation_weights: n < 0");
+  if (n == 0) return MADMAP_OK;
+  MM_CHECK(psi && cos2psi && sin2psi, MADMAP_ERR_INVALID_ARG, "polarisation_weights: NULL pointer");
+  const OpImpl& impl = precision == MADMAP_FP32 ? op_impl_f32() : op_impl_f64();
+  return impl.weights(n, psi, cos2psi, sin2psi, static_cast<cudaStream_t>(stream));
+}
+
 // ---------------------------------------------------------------- allocation-free noise weighting
 // Some callers cannot allocate device memory at the point where they need the
 // noise weighting: code running under an allocator that forbids new device
@@ -105,29 +116,26 @@ extern "C" int64_t madmap_kernel_launch_count(void) { return (int64_t)mm::g_laun
 //
 // The array is shared by all calls: each call rewrites the parts it reads
 // (nothing needs to start at zero), and calls that overlap on the GPU (on
-// different streams, or from different host threads) race on it.  Its device
-// address is looked up once per device, by the first call made with that
-// device current; make that first call before any stream capture.
+// different streams, or from different host threads) race on it.  Each call
+// looks up the array's device address for the device that is current, so
+// the address stays right after a device reset.  The derived tables are
+// uploaded from host memory that lives only for the duration of the call, so
+// the call refuses to be recorded into a CUDA graph (a replay would read
+// freed host memory), and the upload may hold the host until the stream has
+// reached it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MADMAP_NOALLOC_SCRATCH_BYTES];
 
 namespace mm {
 namespace {
 
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[256] = {nullptr};
-
+// The array's device address on the current device (a host-side lookup; the
+// name g_noalloc_scratch is only a host stand-in and must not be handed to a
+// kernel).
 madmap_status noalloc_scratch(void** out) {
-  int dev = 0;
-  MM_CUDA(cudaGetDevice(&dev));
-  MM_CHECK(dev >= 0 && dev < 256, MADMAP_ERR_INTERNAL, "device ordinal out of range");
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-    g_noalloc_ptr[dev] = ptr;
-  }
-  *out = g_noalloc_ptr[dev];
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+  *out = ptr;
   return MADMAP_OK;
 }
 
@@ -162,6 +170,14 @@ extern "C" madmap_status madmap_apply_ninv_noalloc(int32_t precision, int64_t n_
            "apply_ninv_noalloc: n_lags above the limit of the fixed scratch (MADMAP_NOALLOC_MAX_LAGS)");
   if (n_samples == 0) return MADMAP_OK;
   MM_CHECK(y && w, MADMAP_ERR_INVALID_ARG, "apply_ninv_noalloc: NULL timestream");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    MM_CUDA(cudaStreamIsCapturing(s, &cs));
+    MM_CHECK(cs == cudaStreamCaptureStatusNone, MADMAP_ERR_INVALID_ARG,
+             "apply_ninv_noalloc: cannot be recorded by a stream capture (its tables are uploaded from host "
+             "memory that does not outlive the call)");
+  }
   const bool fp64 = precision == MADMAP_FP64;
   // FFT length: four bandwidths per window, so at least half of every window
   // is exact output
@@ -226,7 +242,6 @@ extern "C" madmap_status madmap_apply_ninv_noalloc(int32_t precision, int64_t n_
   madmap_status st = noalloc_scratch(&base);
   if (st != MADMAP_OK) return st;
   unsigned char* b = static_cast<unsigned char*>(base);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (fp64) {
     std::vector<double2> t64(M);
     for (int j = 0; j < M; ++j) {
@@ -256,7 +271,8 @@ extern "C" madmap_status madmap_apply_ninv_noalloc(int32_t precision, int64_t n_
   q.scratch = b + off_S;
   if (q.n_tiles == 0) return MADMAP_OK;
   st = op_launch(&q, fp64 ? OPP_F64 : OPP_F32, IN_TOD_REAL, OUT_TOD, y, w, 0, 0, 1, nullptr, s);
-  // the host tables above were copied from pageable memory, which completes
-  // before cudaMemcpyAsync returns, so they may go out of scope here
+  // the host tables above were copied from pageable memory: such a copy has
+  // read its source before cudaMemcpyAsync returns, so they may go out of
+  // scope here
   return st;
 }

@@ -110,11 +110,16 @@ __device__ __forceinline__ bool skip_tile(const OpArgs& a, const Tile* T) {
   return a.skip[T->l[0].rhs * a.skip_stride] != 0 && a.skip[T->l[1].rhs * a.skip_stride] != 0;
 }
 
-// cos 2psi, sin 2psi for the float32 operator: 2 psi is reduced to [-pi, pi]
-// by subtracting the nearest multiple of 2 pi in two parts (2 pi rounded to
-// float, then the remainder of 2 pi), and the hardware approximations take
-// it from there (absolute error about 4e-7 on [-pi, pi], far inside the
-// float32 operator's own rounding; the float64 operator uses exact weights).
+// cos 2psi, sin 2psi for the float32 operator.  x = 2 psi (exact) is reduced
+// to r = x - 2 pi k, k = rint(x / 2 pi), by Cody and Waite's method (Cody and
+// Waite, "Software Manual for the Elementary Functions", 1980): 2 pi is split
+// into C1 = 2 pi rounded to float and C2 = 2 pi - C1, and k C1 then k C2 are
+// subtracted, each with one fused multiply-add, so the product k C1 is exact
+// and r carries at most two roundings (about 2.4e-7 absolute on [-pi, pi]).
+// The hardware approximations (absolute error below 4e-7 on [-pi, pi]) take
+// it from there: |error| < 1e-6 against the exact weights of the float32
+// angle, far inside the float32 operator's own rounding.  The float64
+// operator uses correctly rounded float64 weights.
 __device__ __forceinline__ void sincos_2psi(float psi, float& s, float& c) {
   const float x = 2.0f * psi;
   const float k = rintf(x * 0.15915494309189535f);
@@ -442,6 +447,22 @@ __host__ __device__ inline int split_log(int logM) { return (logM + 1) >> 1; }
 // Shared entries of the two split tables (none for float64).
 __host__ __device__ inline int split_entries(int esz, int logM) {
   return esz == 8 ? (1 << split_log(logM)) + (1 << (logM - split_log(logM))) : 0;
+}
+
+// The polarisation weights (cos 2psi, sin 2psi) of each angle exactly as this
+// precision's operator kernels form them (a diagnostic of the weights alone).
+template <typename Real>
+__global__ void k_weights(long long n, const float* __restrict__ psi, Real* c, Real* s) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    Real cc, ss;
+    if constexpr (std::is_same<Real, float>::value) {
+      sincos_2psi(psi[t], ss, cc);
+    } else {
+      sincos(2.0 * (double)psi[t], &ss, &cc);
+    }
+    c[t] = cc;
+    s[t] = ss;
+  }
 }
 
 // ---------------------------------------------------------------- k_f1
@@ -1268,8 +1289,24 @@ size_t impl_f13_smem(const Plan* p) {
 }
 
 template <typename Real>
+madmap_status impl_weights(long long n, const float* psi, void* c, void* s, cudaStream_t st) {
+  if constexpr (std::is_same<Real, df64>::value) {
+    set_error("weights: no double-float instance");
+    return MADMAP_ERR_INTERNAL;
+  } else {
+    if (n <= 0) return MADMAP_OK;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    k_weights<Real><<<grid, 256, 0, st>>>(n, psi, static_cast<Real*>(c), static_cast<Real*>(s));
+    count_launches(1);
+    MM_CUDA(cudaGetLastError());
+    return MADMAP_OK;
+  }
+}
+
+template <typename Real>
 OpImpl make_impl() {
   OpImpl t;
+  t.weights = impl_weights<Real>;
   t.launch = impl_launch<Real>;
   t.launch_set = impl_launch_set<Real>;
   t.time = impl_time<Real>;

@@ -238,6 +238,26 @@ __global__ void __launch_bounds__(1024) k_scan_words(const unsigned* bits, int n
   if (tid == 1023) *total = part[1023];
 }
 
+// Sharded plans: samples per global pixel on this rank (summed across ranks
+// before the observed set is formed).
+__global__ void k_count_pix(const int* pix, long long n, int n_pix, int* counts) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int g = pix[t];
+    if (g >= 0 && g < n_pix) atomicAdd(counts + g, 1);
+  }
+}
+
+// One bit per global pixel observed by some rank (one thread per 32-pixel word).
+__global__ void k_bits_from_counts(const int* counts, int n_pix, unsigned* bits) {
+  const int n_words = (n_pix + 31) / 32;
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < n_words; w += gridDim.x * blockDim.x) {
+    unsigned b = 0;
+    for (int k = 0; k < 32 && 32 * w + k < n_pix; ++k)
+      if (counts[32 * w + k] > 0) b |= 1u << k;
+    bits[w] = b;
+  }
+}
+
 __device__ __forceinline__ int rank_of(const unsigned* bits, const int* prefix, int g) {
   const unsigned w = bits[g >> 5];
   return prefix[g >> 5] + __popc(w & ((1u << (g & 31)) - 1u));
@@ -1010,6 +1030,16 @@ static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
   }
   if (p->G && n_obs > 0)
     k_combine<<<grid_for(n_obs), 256, 0, s>>>(p->G, p->n_filters, n_obs, ns, df0, acc);
+  if (p->allreduce && n_obs > 0) {
+    // sharded plans: the blocks and hit counts of all ranks (hits only when
+    // they were accumulated anew: a kept per-filter sum reuses the global ones)
+    st = reduce_across(p, acc, (long long)n_obs * (ns == 1 ? 1 : 12), MADMAP_REDUCE_F64, s);
+    if (st == MADMAP_OK && (first || !p->G)) st = reduce_across(p, p->hits, n_obs, MADMAP_REDUCE_I32, s);
+    if (st != MADMAP_OK) {
+      cleanup();
+      return st;
+    }
+  }
   if (n_obs > 0)
     k_classify<<<grid_for(n_obs), 256, 0, s>>>(acc, p->hits, n_obs, ns, p->rcond_excise, p->rcond_fp64, p->P64,
                                                 p->P32, p->excised, p->fp64flag, counts);
@@ -1071,9 +1101,41 @@ static madmap_status build_preconditioner(Plan* p, cudaStream_t s) {
   return st;
 }
 
+madmap_status reduce_across(Plan* p, void* buf, long long count, int dtype, cudaStream_t s) {
+  if (!p->allreduce || count <= 0) return MADMAP_OK;
+  MM_CUDA(cudaGetLastError());
+  const int32_t rc = p->allreduce(buf, (int64_t)count, dtype, static_cast<void*>(s), p->allreduce_user);
+  MM_CHECK(rc == 0, MADMAP_ERR_INTERNAL, "the allreduce callback of a sharded plan failed");
+  return MADMAP_OK;
+}
+
 }  // namespace mm
 
 // ---------------------------------------------------------------- C ABI
+extern "C" madmap_status madmap_partition_intervals(int32_t n_intervals, const int64_t* off, int32_t n_ranks,
+                                                    int32_t* first) {
+  using namespace mm;
+  MM_CHECK(n_intervals >= 0 && n_ranks >= 1 && off && first, MADMAP_ERR_INVALID_ARG,
+           "partition_intervals: bad arguments");
+  MM_CHECK(off[0] == 0, MADMAP_ERR_INVALID_ARG, "partition_intervals: interval_offsets must start at 0");
+  for (int i = 0; i < n_intervals; ++i)
+    MM_CHECK(off[i + 1] >= off[i], MADMAP_ERR_INVALID_ARG, "partition_intervals: offsets must be non-decreasing");
+  const long long total = off[n_intervals];
+  first[0] = 0;
+  int j = 0;
+  for (int r = 0; r + 1 < n_ranks; ++r) {
+    // the boundary nearest to the rank's share of the samples (ties: the earlier one)
+    const long double target = (long double)total * (r + 1) / n_ranks;
+    const int prev = j;
+    while (j < n_intervals && (long double)off[j + 1] <= target) ++j;
+    if (j < n_intervals && (long double)off[j + 1] - target < target - (long double)off[j]) ++j;
+    while (j > prev && off[j - 1] == off[j]) --j;  // of equal boundaries (empty intervals), the earliest
+    first[r + 1] = j;
+  }
+  first[n_ranks] = n_intervals;
+  return MADMAP_OK;
+}
+
 extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* stream, madmap_plan_t* out) {
   MM_CHECK(out != nullptr, MADMAP_ERR_INVALID_ARG, "plan_create: out is NULL");
   *out = nullptr;
@@ -1120,6 +1182,8 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
     for (int i = 0; i < d->n_intervals; ++i)
       MM_CHECK(d->interval_hwp_group[i] >= -1 && d->interval_hwp_group[i] < d->n_hwp_groups, MADMAP_ERR_INVALID_ARG,
                "interval_hwp_group out of range");
+  MM_CHECK(!d->allreduce || (!d->boresight && !d->pix_pol && !d->extra_index && !d->hwp_angle),
+           MADMAP_ERR_INVALID_ARG, "sharded plans (allreduce set) need stored single-resolution pointing");
   MM_CHECK(d->n_intervals >= 0 && d->interval_offsets != nullptr, MADMAP_ERR_INVALID_ARG, "bad intervals");
   MM_CHECK(d->n_intervals == 0 || d->interval_filter != nullptr, MADMAP_ERR_INVALID_ARG, "interval_filter NULL");
   MM_CHECK(d->n_filters >= 1 && d->n_lags >= 1 && d->filter_lags != nullptr, MADMAP_ERR_INVALID_ARG,
@@ -1154,6 +1218,8 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
   p->offsets.assign(off, off + d->n_intervals + 1);
   p->ivl_filter.assign(d->interval_filter, d->interval_filter + d->n_intervals);
   p->lags.assign(d->filter_lags, d->filter_lags + (size_t)d->n_filters * d->n_lags);
+  p->allreduce = d->allreduce;
+  p->allreduce_user = d->allreduce_user;
   madmap_status st = MADMAP_OK;
 #define MM_TRY(x)                 \
   do {                            \
@@ -1222,9 +1288,18 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
       MM_TRYC(cudaMemcpyAsync(p->psi, d->psi, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
       k_validate_psi<<<grid_for(n), 256, 0, s>>>(p->psi, n, p->dev_flag);
     }
-    k_mark_bits<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, bits, d->pix_pol);
+    if (!p->allreduce) k_mark_bits<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, bits, d->pix_pol);
     if (p->multires) k_mark_bits<<<grid_for(n), 256, 0, s>>>(d->pix_pol, n, p->n_pix_pol, bits_pol, d->pix);
     if (d->extra_index) k_validate_pix<<<grid_for(n), 256, 0, s>>>(d->extra_index, n, d->n_extra, p->dev_flag, 16);
+  }
+  if (p->allreduce) {
+    // sharded plans: a pixel is observed when a sample of any rank hits it
+    int* counts = nullptr;
+    MM_TRY(dalloc_t(p, &counts, p->n_pix));
+    MM_TRYC(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)p->n_pix, s));
+    if (n > 0) k_count_pix<<<grid_for(n), 256, 0, s>>>(d->pix, n, p->n_pix, counts);
+    MM_TRY(reduce_across(p, counts, p->n_pix, MADMAP_REDUCE_I32, s));
+    k_bits_from_counts<<<grid_for((p->n_pix + 31) / 32), 256, 0, s>>>(counts, p->n_pix, bits);
   }
   k_scan_words<<<1, 1024, 0, s>>>(bits, n_words, prefix, total);
   if (p->multires) k_scan_words<<<1, 1024, 0, s>>>(bits_pol, n_words_pol, prefix_pol, total + 1);

@@ -78,11 +78,13 @@ struct SolveBuffers {
   long long w_body_launches = 0;
   bool w_unsupported = false;
   int* loop = nullptr;  // [0] body executions, [1] cap
+  double* hist = nullptr;  // [cap_rhs][HIST_CAP] relative residual after each iteration
   std::vector<void*> allocs;
   size_t bytes = 0;
 };
 
 static const int NB = 304;  // blocks of the vector kernels (2 per SM)
+static const int HIST_CAP = 4096;  // iterations whose residual is recorded per right-hand side
 static const int NT = 256;
 
 static void free_one(SolveBuffers* sb) {
@@ -144,6 +146,7 @@ static madmap_status get_buffers(Plan* p, bool fp64, int n_rhs, SolveBuffers** o
   if (st == MADMAP_OK) st = sb_alloc(p, sb, (void**)&sb->st, sizeof(CgState) * n_rhs);
   if (st == MADMAP_OK) st = sb_alloc(p, sb, (void**)&sb->flags, sizeof(int) * n_rhs);
   if (st == MADMAP_OK) st = sb_alloc(p, sb, (void**)&sb->loop, sizeof(int) * 2);
+  if (st == MADMAP_OK) st = sb_alloc(p, sb, (void**)&sb->hist, sizeof(double) * HIST_CAP * n_rhs);
   if (st == MADMAP_OK && fp64) {
     double** v64[5] = {&sb->b64, &sb->x64, &sb->r64, &sb->t64, &sb->xbest64};
     for (double** v : v64)
@@ -305,7 +308,8 @@ template <typename Real, int NS, typename Bt>
 __global__ void __launch_bounds__(NT) k_cg_init(Real* x, Real* r, Real* z, Real* p, Real* q, Real* xb, const Bt* b,
                                                 long long nvec, int n_obs, const double* P64, const float* P32,
                                                 const unsigned char* f64, CgState* st, double* partials,
-                                                double tol, int max_iter, const int* inactive, int pause_k) {
+                                                double tol, int max_iter, const int* inactive, int pause_k,
+                                                double* hist) {
   const long long o = blockIdx.y * nvec;
   x += o; r += o; z += o; p += o; q += o; xb += o; b += o;
   st += blockIdx.y;
@@ -352,6 +356,7 @@ __global__ void __launch_bounds__(NT) k_cg_init(Real* x, Real* r, Real* z, Real*
       st->done = (off || st->bnorm == 0.0 || max_iter <= 0 || st->res <= tol) ? 1 : 0;
       st->pause_k = pause_k;
       st->halt = st->done || pause_k <= 0;
+      if (hist) hist[(long long)blockIdx.y * HIST_CAP] = st->res;
     }
   }
 }
@@ -386,7 +391,8 @@ __global__ void __launch_bounds__(NT) k_cg_alpha(const Real* p, const Real* q, l
 template <typename Real, int NS>
 __global__ void __launch_bounds__(NT) k_cg_update(Real* x, Real* r, Real* z, const Real* p, const Real* q,
                                                   long long nvec, int n_obs, const double* P64, const float* P32,
-                                                  const unsigned char* f64, CgState* st, double* partials) {
+                                                  const unsigned char* f64, CgState* st, double* partials,
+                                                  double* hist) {
   st += blockIdx.y;
   if (st->halt) return;
   const long long o = blockIdx.y * nvec;
@@ -421,6 +427,7 @@ __global__ void __launch_bounds__(NT) k_cg_update(Real* x, Real* r, Real* z, con
       st->k = k;
       const double res = sqrt(s[1]) / st->bnorm;
       st->res = res;
+      if (hist && k < HIST_CAP) hist[(long long)blockIdx.y * HIST_CAP + k] = res;
       if (res < st->best_res) {
         st->best_res = res;
         st->best_k = k;
@@ -571,9 +578,13 @@ static void enqueue_iteration(Plan* p, SolveBuffers* sb, const Batch& B, cudaStr
     *st = op_launch_set(p, sizeof(Real) == 8, IN_MAP, OUT_MAP, pp, q, nv, nv, &sb->st->halt, ST_STRIDE, B.ts, s);
   else
     *st = op_launch(p, sizeof(Real) == 8, IN_MAP, OUT_MAP, pp, q, 0, 0, 1, &sb->st->halt, s);
+  // sharded plans: q = sum over the ranks of their shares of H p
+  if (*st == MADMAP_OK)
+    *st = reduce_across(p, q, nv * B.n_rhs, sizeof(Real) == 8 ? MADMAP_REDUCE_F64 : MADMAP_REDUCE_F32, s);
   count_launches(3);
   k_cg_alpha<Real, NS><<<g, NT, 0, s>>>(pp, q, nv, n, sb->st, sb->partials);
-  k_cg_update<Real, NS><<<g, NT, 0, s>>>(x, r, z, pp, q, nv, n, p->P64, p->P32, p->fp64flag, sb->st, sb->partials);
+  k_cg_update<Real, NS><<<g, NT, 0, s>>>(x, r, z, pp, q, nv, n, p->P64, p->P32, p->fp64flag, sb->st, sb->partials,
+                                         sb->hist);
   k_cg_direction<Real, NS><<<g, NT, 0, s>>>(x, z, pp, q, xb, nv, n, sb->st);
 }
 
@@ -692,11 +703,12 @@ static madmap_status run_pcg(Plan* p, SolveBuffers* sb, const Batch& B, const Bt
                              int max_iter, int per_sync, int graph_mode, cudaStream_t s, std::vector<PcgResult>& out,
                              int pause_k = INT_MAX, bool init = true) {
   const int n = p->n_obs, R = B.n_rhs;
+  if (p->allreduce) graph_mode = 0;  // the cross-rank sums run on the host between launches
   if (init) {
     count_launches(1);
     k_cg_init<Real, NS, Bt><<<dim3(grid_vec(n), R), NT, 0, s>>>(
         (Real*)sb->x, (Real*)sb->r, (Real*)sb->z, (Real*)sb->p, (Real*)sb->q, (Real*)sb->xb, b, sb->nvec, n, p->P64,
-        p->P32, p->fp64flag, sb->st, sb->partials, tol, max_iter, inactive, pause_k);
+        p->P32, p->fp64flag, sb->st, sb->partials, tol, max_iter, inactive, pause_k, sb->hist);
     MM_CUDA(cudaGetLastError());
   }
   if (graph_mode == 2 && !sb->w_unsupported) {
@@ -839,6 +851,37 @@ static madmap_status pcg64(Plan* p, SolveBuffers* sb, const Batch& B, const madm
   }
 }
 
+// Entries [from, to] of right-hand side k's device residual history, appended
+// to `out` multiplied by `scale` (entries past the recorded capacity are not kept).
+static madmap_status append_hist(SolveBuffers* sb, int k, int from, int to, double scale, std::vector<double>& out,
+                                 cudaStream_t s) {
+  to = std::min(to, HIST_CAP - 1);
+  if (to < from) return MADMAP_OK;
+  std::vector<double> h((size_t)(to - from + 1));
+  MM_CUDA(cudaMemcpyAsync(h.data(), sb->hist + (long long)k * HIST_CAP + from, sizeof(double) * h.size(),
+                          cudaMemcpyDeviceToHost, s));
+  MM_CUDA(cudaStreamSynchronize(s));
+  for (double v : h) out.push_back(v * scale);
+  return MADMAP_OK;
+}
+
+// The residual histories into the caller's buffer (opts.residual_history).
+static void write_hist(const madmap_solve_opts& o, const std::vector<std::vector<double>>& H,
+                       std::vector<madmap_solve_info>& I) {
+  for (size_t k = 0; k < H.size(); ++k) {
+    int len = 0;
+    if (o.residual_history && o.history_capacity > 0) {
+      len = (int)std::min<size_t>(H[k].size(), (size_t)o.history_capacity);
+      if (len > 0) memcpy(o.residual_history + (long long)k * o.history_capacity, H[k].data(), sizeof(double) * len);
+    }
+    I[k].history_len = len;
+  }
+}
+
+static double ms_since(std::chrono::steady_clock::time_point t) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+}
+
 template <int NS>
 static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, const madmap_solve_opts& o,
                                 std::vector<madmap_solve_info>& I, cudaStream_t s, const double** x_pad) {
@@ -848,11 +891,19 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
   const int graph = o.use_graph;
   madmap_status st = MADMAP_OK;
   std::vector<PcgResult> R;
+  const bool want_hist = o.residual_history && o.history_capacity > 0;
+  std::vector<std::vector<double>> Hh(n_rhs);
   if (o.precision == MADMAP_FP64) {
     int stopped = 0;
+    const auto t_pcg = std::chrono::steady_clock::now();
     st = pcg64<NS>(p, sb64, B, o, s, R, true, o.checkpoint_every, &stopped);
     if (st != MADMAP_OK) return st;
+    const double pcg_ms = ms_since(t_pcg);
+    for (int k = 0; k < n_rhs && want_hist; ++k)
+      if ((st = append_hist(sb64, k, 0, R[k].iters, 1.0, Hh[k], s)) != MADMAP_OK) return st;
+    write_hist(o, Hh, I);
     for (int k = 0; k < n_rhs; ++k) {
+      I[k].t_pcg_ms = pcg_ms;
       I[k].iters = R[k].iters;
       I[k].outer_iters = 1;
       I[k].best_iter = R[k].best_iter;
@@ -883,7 +934,9 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
     best[k] = res[k] = bnorm[k] > 0 ? 1.0 : 0.0;
     inactive[k] = !(bnorm[k] > 0 && res[k] > o.rel_tol && o.max_iter > 0);
     n_active += !inactive[k];
+    if (want_hist) Hh[k].push_back(res[k]);
   }
+  double pcg_ms = 0.0, refine_ms = 0.0;
   MM_CUDA(cudaMemsetAsync(sb64->x64, 0, sizeof(double) * nv * n_rhs, s));
   MM_CUDA(cudaMemsetAsync(sb64->xbest64, 0, sizeof(double) * nv * n_rhs, s));
   int outer = 0;
@@ -892,9 +945,14 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
     for (int k = 0; k < n_rhs; ++k)
       if (!inactive[k]) budget = std::max(budget, o.max_iter - total[k]);
     MM_CUDA(cudaMemcpyAsync(sb64->flags, inactive.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, s));
+    const auto t_pcg = std::chrono::steady_clock::now();
     st = run_pcg<float, NS, double>(p, sb32, B, sb64->r64, sb64->flags, o.inner_rel_tol, budget, o.iters_per_sync,
                                     graph, s, R);
     if (st != MADMAP_OK) return st;
+    pcg_ms += ms_since(t_pcg);
+    const auto t_ref = std::chrono::steady_clock::now();
+    for (int k = 0; k < n_rhs && want_hist; ++k)
+      if (!inactive[k] && (st = append_hist(sb32, k, 1, R[k].iters, res[k], Hh[k], s)) != MADMAP_OK) return st;
     ++outer;
     count_launches(2);
     k_refine_add<<<gv, NT, 0, s>>>(sb64->x64, (const float*)sb32->xb, sb64->t64, nv, sb64->flags);
@@ -909,6 +967,7 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
       st = op_launch_set(p, rp, IN_MAP, OUT_MAP, xin, sb64->t64, nv, nv, sb64->flags, 1, B.ts, s);
     else
       st = op_launch(p, rp, IN_MAP, OUT_MAP, xin, sb64->t64, 0, 0, 1, nullptr, s);
+    if (st == MADMAP_OK) st = reduce_across(p, sb64->t64, nv * n_rhs, MADMAP_REDUCE_F64, s);
     if (st != MADMAP_OK) return st;
     k_residual<<<gv, NT, 0, s>>>(sb64->b64, sb64->t64, sb64->r64, nv, sb64->st, sb64->partials, sb64->flags);
     MM_CUDA(cudaMemcpyAsync(h.data(), sb64->st, sizeof(CgState) * n_rhs, cudaMemcpyDeviceToHost, s));
@@ -941,8 +1000,12 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
       k_take_best<<<gv, NT, 0, s>>>(sb64->x64, sb64->xbest64, nv, sb64->flags);
       MM_CUDA(cudaStreamSynchronize(s));
     }
+    refine_ms += ms_since(t_ref);
   }
+  write_hist(o, Hh, I);
   for (int k = 0; k < n_rhs; ++k) {
+    I[k].t_pcg_ms = pcg_ms;
+    I[k].t_refine_ms = refine_ms;
     I[k].iters = total[k];
     I[k].best_iter = best_iter[k];
     I[k].final_rel_res = res[k];
@@ -988,6 +1051,7 @@ static madmap_status solve_impl(Plan* p, int n_rhs, const float* d, double* m, c
     st = op_launch_set(p, refine_prec(o), IN_TOD, OUT_MAP, d, sb64->b64, p->n_t, nv, nullptr, 0, B.ts, s);
   else
     st = op_launch(p, refine_prec(o), IN_TOD, OUT_MAP, d, sb64->b64, 0, 0, 1, nullptr, s);
+  if (st == MADMAP_OK) st = reduce_across(p, sb64->b64, nv * n_rhs, MADMAP_REDUCE_F64, s);
   if (st != MADMAP_OK) return st;
   MM_CUDA(cudaStreamSynchronize(s));
   const double t_rhs =
@@ -1049,14 +1113,26 @@ static madmap_status resume_impl(Plan* p, const madmap_checkpoint* c, double* m,
   MM_CUDA(cudaMemcpyAsync(sb->st, &h, sizeof(CgState), cudaMemcpyHostToDevice, s));
   std::vector<PcgResult> R;
   int stopped = 0;
+  const auto t_pcg = std::chrono::steady_clock::now();
   st = pcg64<NS>(p, sb, B, o, s, R, false, h.pause_k, &stopped);
   if (st != MADMAP_OK) return st;
+  const double pcg_ms = ms_since(t_pcg);
+  std::vector<std::vector<double>> Hh(1);
+  if (o.residual_history && o.history_capacity > 0) {
+    // iterations before the checkpoint were not seen by this call
+    Hh[0].assign((size_t)std::min(c->iters, HIST_CAP), NAN);
+    if (c->iters < HIST_CAP) Hh[0].push_back(c->rel_res);
+    if ((st = append_hist(sb, 0, c->iters + 1, R[0].iters, 1.0, Hh[0], s)) != MADMAP_OK) return st;
+  }
   count_launches(1);
   k_unpack<double, double><<<grid_vec(user), NT, 0, s>>>((const double*)sb->xb, m, n, ns, np);
   MM_CUDA(cudaStreamSynchronize(s));
   MM_CUDA(cudaGetLastError());
-  madmap_solve_info I;
-  memset(&I, 0, sizeof(I));
+  std::vector<madmap_solve_info> Iv(1);
+  memset(&Iv[0], 0, sizeof(Iv[0]));
+  write_hist(o, Hh, Iv);
+  madmap_solve_info& I = Iv[0];
+  I.t_pcg_ms = pcg_ms;
   I.iters = R[0].iters;
   I.outer_iters = 1;
   I.best_iter = R[0].best_iter;
@@ -1266,6 +1342,8 @@ static madmap_status backward_impl(Plan* p, const float* d, const double* m, con
       k_lag_corr<<<dim3((p->n_lags + CORR_LB - 1) / CORR_LB, ny), CORR_T, 0, s>>>(p->bw_a, p->bw_r, items + y0,
                                                                                  p->n_lags, grad_lags);
     }
+    st = reduce_across(p, grad_lags, (long long)p->n_filters * p->n_lags, MADMAP_REDUCE_F64, s);
+    if (st != MADMAP_OK) return st;
   }
   MM_CUDA(cudaStreamSynchronize(s));
   MM_CUDA(cudaGetLastError());
@@ -1296,6 +1374,8 @@ static madmap_status apply_impl(Plan* p, int prec, int n_rhs, const void* x, voi
       xin = sb->xdf;
     }
     st = op_launch(p, prec, IN_MAP, OUT_MAP, xin, sb->q, 0, 0, 1, nullptr, s);
+    if (st == MADMAP_OK)
+      st = reduce_across(p, sb->q, sb->nvec, prec == OPP_F32 ? MADMAP_REDUCE_F32 : MADMAP_REDUCE_F64, s);
     if (st != MADMAP_OK) return st;
     k_unpack<Real, Real><<<grid_vec(user), NT, 0, s>>>((const Real*)sb->q, yr, n, ns, np);
   }
@@ -1313,6 +1393,8 @@ static madmap_status rhs_impl(Plan* p, int prec, int n_rhs, const float* d, void
   for (int r = 0; r < n_rhs; ++r) {
     MM_CUDA(cudaMemsetAsync(sb->q, 0, sizeof(Real) * sb->nvec, s));
     st = op_launch(p, prec, IN_TOD, OUT_MAP, d + (long long)r * p->n_t, sb->q, 0, 0, 1, nullptr, s);
+    if (st == MADMAP_OK)
+      st = reduce_across(p, sb->q, sb->nvec, prec == OPP_F32 ? MADMAP_REDUCE_F32 : MADMAP_REDUCE_F64, s);
     if (st != MADMAP_OK) return st;
     count_launches(1);
     k_unpack<Real, Real><<<grid_vec(user), NT, 0, s>>>((const Real*)sb->q, static_cast<Real*>(b) + r * user, n, ns,
@@ -1396,6 +1478,8 @@ extern "C" void madmap_solve_opts_default(madmap_solve_opts* o) {
   o->checkpoint = nullptr;
   o->on_checkpoint = nullptr;
   o->checkpoint_user = nullptr;
+  o->residual_history = nullptr;
+  o->history_capacity = 0;
 }
 
 extern "C" madmap_status madmap_solve(madmap_plan_t plan, const float* d, double* m, const madmap_solve_opts* opts,
