@@ -175,6 +175,17 @@ typedef struct {
    * NULL: an ordinary single-process plan. */
   madmap_reduce_fn allreduce;
   void* allreduce_user;             /* passed to allreduce */
+  /* Bit-reproducible maps (the paper fixes no summation order): nonzero makes
+   * every map-domain sum of the operator (A^T w in madmap_apply_ATNA,
+   * madmap_rhs and every solve) a sum over each observed pixel's samples in
+   * ascending sample order, instead of floating-point atomics whose order
+   * varies run to run, so repeated calls on this plan give identical bits.
+   * The operator writes its weighted timestream (n_samples values per
+   * right-hand side, kept by the plan) and a second pass sums each pixel's
+   * samples.  Stored single-resolution pointing without extended pointing;
+   * n_samples < 2^31.  The preconditioner blocks are still summed with atomics
+   * at plan creation (plans built twice may differ in their last bits). */
+  int32_t deterministic;
 } madmap_plan_desc;
 
 typedef struct {
@@ -201,6 +212,8 @@ typedef struct {
   int32_t n_excised_hwp;   /* half-wave-plate parameters without weight */
   int32_t n_map_replicas;  /* copies of the map the operator scatters into (8 for small maps under
                               more than 1024 samples per row, else 1) */
+  int32_t deterministic;   /* 1 when map sums run in a fixed order (madmap_plan_desc.deterministic) */
+  int32_t sharded;         /* 1 for a sharded plan (madmap_plan_desc.allreduce set) */
 } madmap_plan_stats;
 
 typedef struct {

@@ -360,11 +360,12 @@ class Plan:
     allreduce = fn(ptr, count, dtype, stream_ptr) makes a sharded plan over this
     rank's share of the intervals (shard_range); fn sums a device buffer across
     the ranks, e.g. torch_allreduce().  Every rank must make the same calls.
+    deterministic = True sums every map in a fixed order (bit-reproducible maps).
     """
 
     def __init__(self, pix, psi, n_pix, interval_offsets, interval_filter, filter_lags, rcond_excise=0.0,
                  rcond_fp64=0.0, fft_len=0, tiles_per_chunk=0, stream=None, pix_pol=None, n_pix_pol=0,
-                 extra_index=None, n_extra=0, hwp=None, allreduce=None):
+                 extra_index=None, n_extra=0, hwp=None, allreduce=None, deterministic=False):
         torch = _torch()
         self._h = None
         self._reduce = None
@@ -417,6 +418,7 @@ class Plan:
         if allreduce is not None:
             self._reduce = _reduce_callback(allreduce)
             d.allreduce = self._reduce[0]
+        d.deterministic = 1 if deterministic else 0
         self._keep = (off, filt, lags, keep_hwp)
         self.multires = pix_pol is not None
         self._create(d, n_t, stream)

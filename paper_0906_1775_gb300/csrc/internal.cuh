@@ -347,6 +347,14 @@ struct Plan {
   float* bw_r = nullptr;
   void* corr_items = nullptr;
   int n_corr_items = 0;
+  // deterministic plans: the samples of every observed row in ascending order
+  // (rows det_ptr[p] .. det_ptr[p+1]-1 of det_idx), and the timestream buffer
+  // the operator writes before the ordered row sums ([wtod_rhs][n_t], float64 size)
+  bool det = false;
+  int* det_ptr = nullptr;
+  int* det_idx = nullptr;
+  void* wtod = nullptr;
+  int wtod_rhs = 0;
   // sharded solves: sums map-domain buffers across the ranks (NULL: one process)
   madmap_reduce_fn allreduce = nullptr;
   void* allreduce_user = nullptr;
@@ -441,6 +449,9 @@ void build_tiles(const std::vector<long long>& off, const std::vector<int>& filt
 
 // Tile set for n_rhs right-hand sides (cached in the plan).
 madmap_status get_tile_set(Plan* p, int n_rhs, TileSet** out);
+
+// Deterministic plans: a timestream buffer for n_rhs right-hand sides.
+madmap_status ensure_wtod(Plan* p, int n_rhs);
 
 // host FFT (radix 2, float64), used at plan time only
 void host_fft(std::vector<double>& re, std::vector<double>& im, bool inverse);

@@ -465,13 +465,35 @@ __global__ void k_weights(long long n, const float* __restrict__ psi, Real* c, R
   }
 }
 
+// ---------------------------------------------------------------- launch shape
+// Elements per CTA of the operator kernels (log2; float32 and the float64-size
+// types), the float32 column kernels' minimum resident CTAs per SM, and the
+// samples each thread keeps in flight in the gather (polarised map input) and
+// the scatter (map output) phases.
+#ifndef MM_ELOG_F32
+#define MM_ELOG_F32 12
+#endif
+#ifndef MM_MINB_F13
+#define MM_MINB_F13 4
+#endif
+#ifndef MM_U_GATHER
+#define MM_U_GATHER 4
+#endif
+#ifndef MM_U_SCATTER
+#define MM_U_SCATTER 4
+#endif
+template <typename Real>
+__host__ __device__ constexpr int elog() {
+  return sizeof(Real) == 4 ? MM_ELOG_F32 : 11;
+}
+
 // ---------------------------------------------------------------- k_f1
 // LG2 > 0 fixes the column length N2 = 2^LG2 at compile time (and with it the
 // CTA's column count); LG2 = 0 reads the geometry from the arguments.
 template <typename Real, int NS, int IN, int LG2>
-__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a) {
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? MM_MINB_F13 : 2) k_f1(OpArgs a) {
   typedef typename CxT<Real>::type C;
-  constexpr int ELOG = sizeof(Real) == 4 ? 12 : 11;
+  constexpr int ELOG = elog<Real>();
   const int logN2 = LG2 ? LG2 : a.logN2;
   const int logB1 = LG2 ? ELOG - LG2 : a.logB1;
   const int N2 = 1 << logN2, B1 = 1 << logB1;
@@ -495,7 +517,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
   const int n1_0 = blockIdx.x * B1;
   const int total = B1 << logN2;
   constexpr int bd = OP_THREADS;
-  constexpr int U = (IN == IN_MAPX && polarised(NS)) ? 4 : 8;
+  constexpr int U = (IN == IN_MAPX && polarised(NS)) ? MM_U_GATHER : 8;
   for (int e0 = threadIdx.x; e0 < total; e0 += bd * U) {
     int nn[U];
     bool ok[2][U];
@@ -581,7 +603,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f1(OpArgs a)
 template <typename Real, int LG1>
 __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f2(OpArgs a) {
   typedef typename CxT<Real>::type C;
-  constexpr int ELOG = sizeof(Real) == 4 ? 12 : 11;
+  constexpr int ELOG = elog<Real>();
   const int logN1 = LG1 ? LG1 : a.logN1;
   const int N1 = 1 << logN1;
   const int B2 = LG1 ? (1 << (ELOG - LG1)) : a.B2;
@@ -619,9 +641,9 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f2(OpArgs a)
 
 // ---------------------------------------------------------------- k_f3
 template <typename Real, int NS, int OUT, int LG2>
-__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a) {
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? MM_MINB_F13 : 2) k_f3(OpArgs a) {
   typedef typename CxT<Real>::type C;
-  constexpr int ELOG = sizeof(Real) == 4 ? 12 : 11;
+  constexpr int ELOG = elog<Real>();
   const int logN2 = LG2 ? LG2 : a.logN2;
   const int logB1 = LG2 ? ELOG - LG2 : a.logB1;
   const int N2 = 1 << logN2, B1 = 1 << logB1;
@@ -675,7 +697,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
   }
   __syncthreads();
   fft_rows<C, true, SW>(buf, B1, rs, logN2, tw);
-  constexpr int U = OUT == OUT_MAP ? 4 : 8;
+  constexpr int U = OUT == OUT_MAP ? MM_U_SCATTER : 8;
   for (int e0 = threadIdx.x; e0 < total; e0 += bd * U) {
     int nn[U];
     bool ok[2][U];
@@ -698,7 +720,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f3(OpArgs a)
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int l = 0; l < 2; ++l)
-          if (ok[l][u]) static_cast<Real*>(L[l].out)[nn[u]] = val[l][u];  // float and float64 only
+          if (ok[l][u]) static_cast<typename OutT<Real>::type*>(L[l].out)[nn[u]] = to_out(val[l][u]);
     } else if constexpr (std::is_same<Real, df64>::value && polarised(NS)) {
       // double-float: round the value to float64 once and weight it with the
       // float64 (cos, sin) pair (5 float64 operations per sample, not 9)
@@ -867,7 +889,7 @@ __global__ void __launch_bounds__(256) k_diag(OpArgs a, const DiagItem* __restri
       else if (IN == IN_TODF) v = (Real)__ldg(static_cast<const float*>(L.in) + n);
       else v = static_cast<const Real*>(L.in)[n];
       v = v * w0;
-      if (OUT == OUT_TOD) static_cast<Real*>(L.out)[n] = v;   // float and float64 only
+      if (OUT == OUT_TOD) static_cast<typename OutT<Real>::type*>(L.out)[n] = to_out(v);
       else sample_scatter<Real, NS>(a, L, n, v);
     }
   } else {
@@ -910,7 +932,7 @@ __global__ void k_rep_reduce(Out* rep, int n_rep, long long stride, Out* out, lo
 
 template <typename Real>
 inline int elems_per_cta() {
-  return sizeof(Real) == 4 ? 4096 : 2048;
+  return 1 << elog<Real>();
 }
 
 template <typename Real>
@@ -993,10 +1015,121 @@ OpKernels pick_kernels(const Plan* p) {
   return k;
 }
 
+// ---------------------------------------------------------------- ordered sums (deterministic plans)
+// A^T w summed row by row in a fixed order: one warp per observed row walks
+// the row's samples in ascending order (lane k takes samples k, k + 32, ...,
+// then a fixed butterfly adds the lanes), so every application gives the same
+// bits.  w: the weighted timestream N^-1 A x of each right-hand side
+// (blockIdx.y), w_stride apart; the row's sums are added into out.  The
+// weights are formed as the atomic scatter forms them: float32 from psi by
+// sincos_2psi, float64 and double-float from the float64 pair cs64.
+template <typename Real, int NS>
+__global__ void __launch_bounds__(256) k_segsum(const typename OutT<Real>::type* __restrict__ w, long long w_stride,
+                                                const int* __restrict__ ptr, const int* __restrict__ idx, int n_obs,
+                                                const float* __restrict__ psi, const double2* __restrict__ cs64,
+                                                typename OutT<Real>::type* out, long long out_stride, const int* skip,
+                                                int skip_stride) {
+  typedef typename OutT<Real>::type Out;
+  const int r = blockIdx.y;
+  if (skip && (skip_stride == 0 ? *skip != 0 : skip[r * skip_stride] != 0)) return;
+  w += r * w_stride;
+  out += r * out_stride;
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n_obs; p += nw) {
+    const int b = ptr[p], e = ptr[p + 1];
+    Out a0 = Out(0), a1 = Out(0), a2 = Out(0);
+    for (int k = b + lane; k < e; k += 32) {
+      const int t = __ldg(idx + k);
+      const Out v = w[t];
+      if constexpr (NS == 1) {
+        a0 += v;
+      } else {
+        Out c, sn;
+        if constexpr (std::is_same<Real, float>::value) {
+          sincos_2psi(__ldg(psi + t), sn, c);
+        } else {
+          const double2 cs = cs64[t];
+          c = cs.x;
+          sn = cs.y;
+        }
+        a0 += v;
+        a1 += v * c;
+        a2 += v * sn;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      if (NS == 3) {
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+      }
+    }
+    if (lane == 0) {
+      if (NS == 1) {
+        out[p] += a0;
+      } else {
+        Out* q = out + 4LL * p;
+        q[0] += a0;
+        q[1] += a1;
+        q[2] += a2;
+      }
+    }
+  }
+}
+
 template <typename Real, int NS, int IN, int OUT>
 madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride, long long out_stride,
                          int n_rhs, const int* skip, cudaStream_t s, cudaEvent_t* ev = nullptr, int reps = 1,
-                         const TileSet* ts = nullptr, int skip_stride = 0) {
+                         const TileSet* ts = nullptr, int skip_stride = 0);
+
+// Deterministic plans: the operator writes its weighted timestream (no
+// scatter), then k_segsum adds each row's samples in ascending order.
+template <typename Real, int NS, int IN>
+madmap_status launch_det(Plan* p, const void* in, void* out, long long in_stride, long long out_stride, int n_rhs,
+                         const int* skip, cudaStream_t s, cudaEvent_t* ev, int reps, const TileSet* ts,
+                         int skip_stride) {
+  typedef typename OutT<Real>::type Out;
+  constexpr int NSI = IN == IN_MAPX ? NS : 1;   // a timestream input needs no pointing
+  const int nr = ts ? ts->n_rhs : 1;
+  MM_CHECK(p->wtod && p->wtod_rhs >= nr, MADMAP_ERR_INTERNAL, "deterministic plan without a timestream buffer");
+  const int grid_x = (int)std::max(1LL, std::min<long long>(((long long)p->n_obs + 7) / 8, 152LL * 16));
+  if (n_rhs == 0) return launch_all<Real, NSI, IN, OUT_TOD>(p, in, p->wtod, 0, 0, 0, skip, s, nullptr, 1, ts, 0);
+  for (int rep = 0; rep < reps; ++rep) {
+    if (ts) {
+      madmap_status st = launch_all<Real, NSI, IN, OUT_TOD>(p, in, p->wtod, in_stride, p->n_t, 1, skip, s, ev, 1,
+                                                            ts, skip_stride);
+      if (st != MADMAP_OK) return st;
+      k_segsum<Real, NS><<<dim3(grid_x, nr), 256, 0, s>>>(static_cast<const Out*>(p->wtod), p->n_t, p->det_ptr,
+                                                         p->det_idx, p->n_obs, p->psi, p->cs64,
+                                                         static_cast<Out*>(out), out_stride, skip, skip_stride);
+      count_launches(1);
+      continue;
+    }
+    for (int r = 0; r < n_rhs; ++r) {
+      const void* in_r = static_cast<const char*>(in) + (size_t)r * in_stride *
+                                                            (IN == IN_TODF ? sizeof(float) : sizeof(Real));
+      Out* out_r = static_cast<Out*>(out) + (size_t)r * out_stride;
+      madmap_status st = launch_all<Real, NSI, IN, OUT_TOD>(p, in_r, p->wtod, 0, 0, 1, skip, s, ev, 1, nullptr, 0);
+      if (st != MADMAP_OK) return st;
+      k_segsum<Real, NS><<<dim3(grid_x, 1), 256, 0, s>>>(static_cast<const Out*>(p->wtod), 0, p->det_ptr,
+                                                        p->det_idx, p->n_obs, p->psi, p->cs64, out_r, 0, skip, 0);
+      count_launches(1);
+    }
+  }
+  MM_CUDA(cudaGetLastError());
+  return MADMAP_OK;
+}
+
+template <typename Real, int NS, int IN, int OUT>
+madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride, long long out_stride,
+                         int n_rhs, const int* skip, cudaStream_t s, cudaEvent_t* ev, int reps,
+                         const TileSet* ts, int skip_stride) {
+  if constexpr (OUT == OUT_MAP && (NS == 1 || NS == 3)) {
+    if (p->det) return launch_det<Real, NS, IN>(p, in, out, in_stride, out_stride, n_rhs, skip, s, ev, reps, ts,
+                                                skip_stride);
+  }
   OpArgs a;
   a.M = p->M;
   a.N1 = p->N1;

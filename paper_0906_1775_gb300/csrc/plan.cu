@@ -258,6 +258,63 @@ __global__ void k_bits_from_counts(const int* counts, int n_pix, unsigned* bits)
   }
 }
 
+// ---------------------------------------------------------------- deterministic plans
+// The samples of every observed row in ascending order (a compressed row
+// index): counts, an exclusive scan, an unordered fill, then each row sorted.
+__global__ void k_count_rows(const int* pix_obs, long long n, int* counts) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int p = pix_obs[t];
+    if (p >= 0) atomicAdd(counts + p, 1);
+  }
+}
+
+// ptr[i] = counts[0] + ... + counts[i-1] for i = 0 .. n (single block of 1024).
+__global__ void __launch_bounds__(1024) k_scan_rows(const int* counts, int n, int* ptr) {
+  __shared__ long long part[1024];
+  const int tid = threadIdx.x;
+  const int chunk = (n + 1023) / 1024;
+  const int b = min(n, tid * chunk), e = min(n, b + chunk);
+  long long acc = 0;
+  for (int i = b; i < e; ++i) acc += counts[i];
+  part[tid] = acc;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const long long v = tid >= off ? part[tid - off] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  long long run = part[tid] - acc;
+  for (int i = b; i < e; ++i) {
+    ptr[i] = (int)run;
+    run += counts[i];
+  }
+  if (tid == 1023) ptr[n] = (int)part[1023];
+}
+
+__global__ void k_fill_rows(const int* pix_obs, long long n, int* cursor, int* idx) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int p = pix_obs[t];
+    if (p >= 0) idx[atomicAdd(cursor + p, 1)] = (int)t;
+  }
+}
+
+// Insertion sort of each row (the fill leaves rows nearly in order).
+__global__ void k_sort_rows(const int* ptr, int n_rows, int* idx) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_rows; p += gridDim.x * blockDim.x) {
+    const int b = ptr[p], e = ptr[p + 1];
+    for (int i = b + 1; i < e; ++i) {
+      const int v = idx[i];
+      int j = i - 1;
+      while (j >= b && idx[j] > v) {
+        idx[j + 1] = idx[j];
+        --j;
+      }
+      idx[j + 1] = v;
+    }
+  }
+}
+
 __device__ __forceinline__ int rank_of(const unsigned* bits, const int* prefix, int g) {
   const unsigned w = bits[g >> 5];
   return prefix[g >> 5] + __popc(w & ((1u << (g & 31)) - 1u));
@@ -757,7 +814,41 @@ void build_tiles(const std::vector<long long>& off, const std::vector<int>& filt
 // (window, rhs) ordered by filter, window, rhs and paired consecutively, so
 // right-hand sides 2j and 2j+1 of one window share a complex FFT and the
 // pointing loads of the gather and scatter.
+madmap_status ensure_wtod(Plan* p, int n_rhs) {
+  if (!p->det || p->wtod_rhs >= n_rhs) return MADMAP_OK;
+  void* buf = nullptr;
+  madmap_status st = dalloc(p, &buf, sizeof(double) * (size_t)n_rhs * (size_t)std::max(1LL, p->n_t));
+  if (st != MADMAP_OK) return st;
+  p->wtod = buf;  // a smaller buffer stays with the plan until it is destroyed
+  p->wtod_rhs = n_rhs;
+  return MADMAP_OK;
+}
+
+static madmap_status build_det_rows(Plan* p, cudaStream_t s) {
+  const long long n = p->n_t;
+  int* counts = nullptr;
+  madmap_status st = dalloc_t(p, &p->det_ptr, (size_t)p->n_obs + 1);
+  if (st == MADMAP_OK) st = dalloc_t(p, &p->det_idx, (size_t)std::max(1LL, n));
+  if (st != MADMAP_OK) return st;
+  MM_CUDA(cudaMalloc(&counts, sizeof(int) * (size_t)std::max(1, p->n_obs)));
+  cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)std::max(1, p->n_obs), s);
+  if (n > 0) k_count_rows<<<grid_for(n), 256, 0, s>>>(p->pix_obs, n, counts);
+  k_scan_rows<<<1, 1024, 0, s>>>(counts, p->n_obs, p->det_ptr);
+  cudaMemcpyAsync(counts, p->det_ptr, sizeof(int) * (size_t)std::max(1, p->n_obs), cudaMemcpyDeviceToDevice, s);
+  if (n > 0) k_fill_rows<<<grid_for(n), 256, 0, s>>>(p->pix_obs, n, counts, p->det_idx);
+  if (p->n_obs > 0) k_sort_rows<<<grid_for(p->n_obs), 256, 0, s>>>(p->det_ptr, p->n_obs, p->det_idx);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaFree(counts);
+  if (e != cudaSuccess) return cuda_fail(e, "deterministic row index");
+  return ensure_wtod(p, 1);
+}
+
 madmap_status get_tile_set(Plan* p, int n_rhs, TileSet** out) {
+  if (p->det) {
+    madmap_status st = ensure_wtod(p, n_rhs);
+    if (st != MADMAP_OK) return st;
+  }
   for (TileSet* t : p->tile_sets)
     if (t->n_rhs == n_rhs) {
       *out = t;
@@ -1182,6 +1273,11 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
     for (int i = 0; i < d->n_intervals; ++i)
       MM_CHECK(d->interval_hwp_group[i] >= -1 && d->interval_hwp_group[i] < d->n_hwp_groups, MADMAP_ERR_INVALID_ARG,
                "interval_hwp_group out of range");
+  MM_CHECK(!d->deterministic || (!d->boresight && !d->pix_pol && !d->extra_index && !d->hwp_angle &&
+                                  d->n_samples < (1LL << 31) - 1),
+           MADMAP_ERR_INVALID_ARG,
+           "deterministic plans need stored single-resolution pointing without extended pointing and "
+           "n_samples < 2^31");
   MM_CHECK(!d->allreduce || (!d->boresight && !d->pix_pol && !d->extra_index && !d->hwp_angle),
            MADMAP_ERR_INVALID_ARG, "sharded plans (allreduce set) need stored single-resolution pointing");
   MM_CHECK(d->n_intervals >= 0 && d->interval_offsets != nullptr, MADMAP_ERR_INVALID_ARG, "bad intervals");
@@ -1396,6 +1492,10 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
       k_pix_obs<<<grid_for(n), 256, 0, s>>>(d->pix_pol, n, p->n_pix_pol, bits_pol, prefix_pol, p->pix_obs_pol, d->pix);
   }
   MM_TRY(build_preconditioner(p, s));
+  if (d->deterministic) {
+    p->det = true;
+    MM_TRY(build_det_rows(p, s));
+  }
   // FFT geometry and windows
   p->M = d->fft_len ? d->fft_len : choose_fft_len(p->offsets, p->ivl_filter, p->n_filters, p->n_lags);
   if (p->M <= 0) {
@@ -1485,7 +1585,7 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
     }
   }
   MM_TRY(dalloc(p, &p->scratch, (size_t)p->scratch_slots * p->tiles_per_chunk * p->M * sizeof(double2)));
-  if (p->n_obs > 0 && p->n_t >= 1024LL * p->n_obs && (long long)p->n_obs * p->ns_pad <= (1LL << 17)) {
+  if (!p->det && p->n_obs > 0 && p->n_t >= 1024LL * p->n_obs && (long long)p->n_obs * p->ns_pad <= (1LL << 17)) {
     // a small map under more than 1024 samples per row: eight scatter replicas
     p->n_rep = 8;
     const size_t rb = sizeof(double) * (size_t)p->n_rep * p->n_obs * p->ns_pad;
@@ -1532,6 +1632,8 @@ extern "C" madmap_status madmap_plan_get_stats(madmap_plan_t plan, madmap_plan_s
   o->n_hwp_params = 32 * p->n_hwp_groups;
   o->n_excised_hwp = p->n_excised_hwp;
   o->n_map_replicas = p->n_rep;
+  o->deterministic = p->det ? 1 : 0;
+  o->sharded = p->allreduce ? 1 : 0;
   return MADMAP_OK;
 }
 

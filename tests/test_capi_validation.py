@@ -71,14 +71,27 @@ CASES = {
     "boresight_interval_spans_detectors": dict(pix=None, psi=None, boresight=FAKE_DEV, n_bore=300, bore_step=2,
                                                n_det=2, det_pointing=np.zeros((2, 4), np.float32),
                                                grid_width=8, grid_height=8),
+    "deterministic_extended": dict(deterministic=1, extra_index=FAKE_DEV, n_extra=4),
+    "deterministic_multires": dict(deterministic=1, pix_pol=FAKE_DEV, n_pix_pol=16),
+    "sharded_multires": dict(allreduce="reducer", pix_pol=FAKE_DEV, n_pix_pol=16),
+    "sharded_extended": dict(allreduce="reducer", extra_index=FAKE_DEV, n_extra=4),
 }
+
+
+def _reducer(mm, keep):
+    fn = mm._lib.REDUCE_FN(lambda buf, count, dtype, stream, user: 0)
+    keep.append(fn)
+    return fn
 
 
 @pytest.mark.parametrize("case", list(CASES))
 def test_malformed_description_is_rejected_on_the_host(case):
     mm = _lib()
     keep = []
-    d = _desc(mm, keep, **CASES[case])
+    kw = dict(CASES[case])
+    if kw.get("allreduce") == "reducer":
+        kw["allreduce"] = _reducer(mm, keep)
+    d = _desc(mm, keep, **kw)
     h = C.c_void_p()
     st = mm.load().madmap_plan_create(C.byref(d), None, C.byref(h))
     msg = mm.madmap_last_error()
@@ -94,6 +107,8 @@ KEYWORD = {
     "hwp_without_tau": "hwp_tau", "hwp_group_range": "interval_hwp_group", "boresight_with_pix": "must be NULL",
     "boresight_nodes": "n_bore", "boresight_grid": "grid_width", "boresight_det_finite": "det_pointing",
     "boresight_interval_spans_detectors": "spans two detectors",
+    "deterministic_extended": "deterministic", "deterministic_multires": "deterministic",
+    "sharded_multires": "sharded", "sharded_extended": "sharded",
 }
 
 
