@@ -79,6 +79,8 @@ def parse():
                          "0 direct launches (every kernel visible to a profiler)")
     ap.add_argument("--fft-len", type=int, default=0, help="override the plan's FFT length (0 = plan's choice)")
     ap.add_argument("--tpc", type=int, default=0, help="override the plan's tiles per launch chunk (0 = plan's choice)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="plan with the cost model's FFT length instead of the measuring autotuner")
     ap.add_argument("--operator-only", type=int, default=0, metavar="R",
                     help="only build the plan and time R float32 operator applications (profiling runs)")
     return ap.parse_args()
@@ -723,7 +725,7 @@ def run_headline(args, world, rank, local):
     gen_s = time.time() - t0
     t0 = time.time()
     plan = mm.Plan(pix, psi, p.n_pix, p.interval_offsets, p.interval_filter, lib_lags(p), tiles_per_chunk=args.tpc,
-                   fft_len=args.fft_len)
+                   fft_len=args.fft_len, autotune=not args.no_autotune)
     torch.cuda.synchronize()
     plan_s = time.time() - t0
     n_obs = plan.n_obs
@@ -909,7 +911,10 @@ def run_headline(args, world, rank, local):
                            "l2_flush": "inputs larger than L2 (pointing + d = "
                                        f"{p.n_samples * 12 / 1e6:.0f} MB > 129 MB L2)",
                            "replicas": "one independent problem per rank", "generate_s": gen_s,
-                           "plan_create_s": plan_s, "device_bytes": plan.stats["device_bytes"]},
+                           "plan_create_s": plan_s, "device_bytes": plan.stats["device_bytes"],
+                           "tiles_per_chunk": plan.stats["tiles_per_chunk"],
+                           "autotune": [{"fft_len": m, "tiles_per_chunk": t, "fp32_operator_ms": ms}
+                                        for m, t, ms in plan.stats["tuned"]]},
                 "time_to_1e-6_map_error": {
                     "mixed_ms": ms_max / args.steps, "mixed_iters": iters // max(args.steps, 1),
                     "mixed_rel_tol": tol_mixed, "mixed_map_err": err_mixed, "mixed_map_err_IQU": per_mixed,

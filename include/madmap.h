@@ -186,6 +186,16 @@ typedef struct {
    * n_samples < 2^31.  The preconditioner blocks are still summed with atomics
    * at plan creation (plans built twice may differ in their last bits). */
   int32_t deterministic;
+  /* Measuring autotuner (the paper picks n_f by its cost model, Section 5.2;
+   * on a GPU the fastest FFT length and launch batching depend on the
+   * kernels): nonzero times one float32 operator application, with CUDA events
+   * after one warm-up application, for each candidate FFT length (fft_len if
+   * given, else the plan's cost-model choice and the lengths twice and half
+   * it) and tiles per launch chunk (tiles_per_chunk if given, else the default
+   * rule and half and twice it), and keeps the fastest.  The candidates and
+   * their times are in madmap_plan_stats.  Adds a few operator applications
+   * to plan creation; ignored for white-noise plans. */
+  int32_t autotune;
 } madmap_plan_desc;
 
 typedef struct {
@@ -214,6 +224,10 @@ typedef struct {
                               more than 1024 samples per row, else 1) */
   int32_t deterministic;   /* 1 when map sums run in a fixed order (madmap_plan_desc.deterministic) */
   int32_t sharded;         /* 1 for a sharded plan (madmap_plan_desc.allreduce set) */
+  int32_t n_tuned;         /* candidates the autotuner timed (0: not tuned), at most 9 reported */
+  int32_t tuned_fft_len[9];
+  int32_t tuned_tiles_per_chunk[9];
+  float tuned_ms[9];       /* float32 operator application time of each candidate */
 } madmap_plan_stats;
 
 typedef struct {
@@ -276,7 +290,11 @@ typedef struct {
   int32_t outer_iters;     /* MIXED refinement steps (FP64: 1) */
   int32_t best_iter;       /* iteration count at which the returned iterate was produced */
   int32_t fp64_applies;    /* full-precision operator applications (float64, or double-float per
-                              refine_precision), including the right-hand side */
+                              refine_precision), including the right-hand side; MIXED solves of
+                              single-resolution stored pointing form the right-hand side in float32
+                              (it only starts the first inner solve; each refinement residual
+                              b - H x is formed from the data as A^T N^-1 (d - A x) in full precision)
+                              and count it in fp32_applies */
   int32_t fp32_applies;    /* float32 operator applications */
   double final_rel_res;    /* last relative residual ||b - H x_k|| / ||b|| (recursive for FP64) */
   double best_rel_res;     /* relative residual of the returned map */

@@ -144,7 +144,10 @@ def _reduce_callback(fn):
 def madmap_plan_get_stats(h) -> dict:
     s = _lib.madmap_plan_stats()
     check(load().madmap_plan_get_stats(h, C.byref(s)), "madmap_plan_get_stats")
-    return {k: getattr(s, k) for k, _ in s._fields_}
+    out = {k: getattr(s, k) for k, _ in s._fields_ if not k.startswith("tuned_")}
+    out["tuned"] = [(int(s.tuned_fft_len[k]), int(s.tuned_tiles_per_chunk[k]), float(s.tuned_ms[k]))
+                    for k in range(s.n_tuned)]
+    return out
 
 
 def madmap_plan_observed(h, obs2glob_ptr=None, excised_ptr=None, stream=None) -> int:
@@ -361,11 +364,13 @@ class Plan:
     rank's share of the intervals (shard_range); fn sums a device buffer across
     the ranks, e.g. torch_allreduce().  Every rank must make the same calls.
     deterministic = True sums every map in a fixed order (bit-reproducible maps).
+    autotune = True times candidate FFT lengths and launch chunk sizes and keeps the
+    fastest (stats["tuned"] lists them).
     """
 
     def __init__(self, pix, psi, n_pix, interval_offsets, interval_filter, filter_lags, rcond_excise=0.0,
                  rcond_fp64=0.0, fft_len=0, tiles_per_chunk=0, stream=None, pix_pol=None, n_pix_pol=0,
-                 extra_index=None, n_extra=0, hwp=None, allreduce=None, deterministic=False):
+                 extra_index=None, n_extra=0, hwp=None, allreduce=None, deterministic=False, autotune=False):
         torch = _torch()
         self._h = None
         self._reduce = None
@@ -419,6 +424,7 @@ class Plan:
             self._reduce = _reduce_callback(allreduce)
             d.allreduce = self._reduce[0]
         d.deterministic = 1 if deterministic else 0
+        d.autotune = 1 if autotune else 0
         self._keep = (off, filt, lags, keep_hwp)
         self.multires = pix_pol is not None
         self._create(d, n_t, stream)

@@ -48,7 +48,7 @@ class madmap_plan_desc(C.Structure):
                 ("grid_height", C.c_int32), ("extra_index", C.c_void_p), ("n_extra", C.c_int32),
                 ("hwp_angle", C.c_void_p), ("hwp_tau", C.c_void_p), ("interval_hwp_group", C.c_void_p),
                 ("n_hwp_groups", C.c_int32), ("allreduce", REDUCE_FN), ("allreduce_user", C.c_void_p),
-                ("deterministic", C.c_int32)]
+                ("deterministic", C.c_int32), ("autotune", C.c_int32)]
 
 
 class madmap_plan_stats(C.Structure):
@@ -59,7 +59,10 @@ class madmap_plan_stats(C.Structure):
                                                           ("n_extra", C.c_int32), ("n_excised_extra", C.c_int32),
                                                           ("n_hwp_params", C.c_int32), ("n_excised_hwp", C.c_int32),
                                                           ("n_map_replicas", C.c_int32),
-                                                          ("deterministic", C.c_int32), ("sharded", C.c_int32)]
+                                                          ("deterministic", C.c_int32), ("sharded", C.c_int32),
+                                                          ("n_tuned", C.c_int32), ("tuned_fft_len", C.c_int32 * 9),
+                                                          ("tuned_tiles_per_chunk", C.c_int32 * 9),
+                                                          ("tuned_ms", C.c_float * 9)]
 
 
 class madmap_checkpoint(C.Structure):

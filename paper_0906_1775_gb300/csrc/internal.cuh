@@ -355,6 +355,19 @@ struct Plan {
   int* det_idx = nullptr;
   void* wtod = nullptr;
   int wtod_rhs = 0;
+  // buffers that depend on the FFT length (freed and rebuilt by the autotuner)
+  std::vector<void*> win_allocs;
+  size_t win_bytes = 0;
+  // the autotuner's candidates: FFT length, tiles per chunk, float32 operator ms
+  struct Tuned {
+    int M, tpc;
+    float ms;
+  };
+  std::vector<Tuned> tuned;
+  // the data timestream of an IN_RESID operator application (set by the
+  // caller around the launch)
+  const float* resid_d = nullptr;
+  long long resid_stride = 0;
   // sharded solves: sums map-domain buffers across the ranks (NULL: one process)
   madmap_reduce_fn allreduce = nullptr;
   void* allreduce_user = nullptr;
@@ -387,7 +400,9 @@ inline madmap_status dalloc_t(Plan* p, T** ptr, size_t count) {
 // Arithmetic of an operator application: float32, float64, or double-float
 // (float pairs; maps and outputs in float64, the input map pre-split into pairs).
 enum { OPP_F32 = 0, OPP_F64 = 1, OPP_DF64 = 2 };
-enum { IN_MAP = 0, IN_TOD = 1, IN_TOD_REAL = 2 };
+// IN_RESID: the residual timestream d - A x of the map `in` and the float
+// timestream Plan::resid_d (resid_stride floats per right-hand side).
+enum { IN_MAP = 0, IN_TOD = 1, IN_TOD_REAL = 2, IN_RESID = 3 };
 enum { OUT_MAP = 0, OUT_TOD = 1 };
 
 // Runs the three-kernel noise-weighting pipeline over the plan's tiles with

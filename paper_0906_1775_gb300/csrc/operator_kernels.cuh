@@ -37,7 +37,12 @@ namespace mm {
 
 namespace {
 
-enum { IN_MAPX = 0, IN_TODF = 1, IN_TODR = 2 };
+// Input of the noise weighting: a map (gather y = A x), a float timestream, a
+// timestream of the working precision, or the residual timestream d - A x of
+// a float timestream d and a map x (the refinement residual b - H x =
+// A^T N^-1 (d - A x) in one pass).
+enum { IN_MAPX = 0, IN_TODF = 1, IN_TODR = 2, IN_RESX = 3 };
+__host__ __device__ constexpr bool gathers(int in) { return in == IN_MAPX || in == IN_RESX; }
 
 // Stokes layouts of the kernels' NS parameter: 1 = T, 3 = IQU on one
 // pixelisation, NS_MR = IQU with Q and U on a second pixelisation (Section 6;
@@ -92,6 +97,8 @@ struct OpArgs {
   int n_per_det, n_det, grid_w, grid_h;
   const void* in;
   long long in_stride;
+  const float* in2;      // IN_RESX: the timestream d, in2_stride floats per right-hand side
+  long long in2_stride;
   void* out;
   long long out_stride;
   void* scratch;
@@ -303,6 +310,7 @@ struct LaneView {
   const float* hang;
   const float* htau;
   const void* in;
+  const float* in2;  // IN_RESX: d offset by the window start
   void* out;
   int j0;        // on-the-fly pointing: detector sample of window position 0
   float4 dp;     // and the lane's detector offset and orientation
@@ -339,6 +347,7 @@ __device__ __forceinline__ LaneView<Real> lane_view(const OpArgs& a, const Lane&
     v.j0 = 0;
     v.dp = make_float4(0.f, 0.f, 0.f, 0.f);
   }
+  v.in2 = IN == IN_RESX ? a.in2 + g.rhs * a.in2_stride + ws : nullptr;
   if (IN == IN_TODF) v.in = static_cast<const float*>(a.in) + g.rhs * a.in_stride + ws;
   else if (IN == IN_TODR) v.in = static_cast<const Real*>(a.in) + g.rhs * a.in_stride + ws;
   else v.in = static_cast<const Real*>(a.in) + g.rhs * a.in_stride;
@@ -517,7 +526,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? MM_MINB_F13 : 2) k_f1
   const int n1_0 = blockIdx.x * B1;
   const int total = B1 << logN2;
   constexpr int bd = OP_THREADS;
-  constexpr int U = (IN == IN_MAPX && polarised(NS)) ? MM_U_GATHER : 8;
+  constexpr int U = (gathers(IN) && polarised(NS)) ? MM_U_GATHER : 8;
   for (int e0 = threadIdx.x; e0 < total; e0 += bd * U) {
     int nn[U];
     bool ok[2][U];
@@ -529,7 +538,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? MM_MINB_F13 : 2) k_f1
       for (int l = 0; l < 2; ++l) ok[l][u] = e < total && in_range(nn[u], L[l].in_lo, L[l].in_hi);
     }
     Real v[2][U];
-    if (IN != IN_MAPX) {
+    if (!gathers(IN)) {
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -574,6 +583,13 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? MM_MINB_F13 : 2) k_f1
             }
           }
         }
+    }
+    if constexpr (IN == IN_RESX) {   // d - A x (flagged samples: rows of A are zero)
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int l = 0; l < 2; ++l)
+          if (ok[l][u]) v[l][u] = Real(__ldg(L[l].in2 + nn[u])) - v[l][u];
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -886,6 +902,7 @@ __global__ void __launch_bounds__(256) k_diag(OpArgs a, const DiagItem* __restri
     for (int n = threadIdx.x; n < len; n += blockDim.x) {
       Real v;
       if (IN == IN_MAPX) v = sample_gather<Real, NS>(a, L, n);
+      else if (IN == IN_RESX) v = Real(__ldg(L.in2 + n)) - sample_gather<Real, NS>(a, L, n);
       else if (IN == IN_TODF) v = (Real)__ldg(static_cast<const float*>(L.in) + n);
       else v = static_cast<const Real*>(L.in)[n];
       v = v * w0;
@@ -905,6 +922,7 @@ __global__ void __launch_bounds__(256) k_diag(OpArgs a, const DiagItem* __restri
       Real v = Real(0);
       if (in) {
         if (IN == IN_MAPX) v = sample_gather<Real, NS>(a, L, n);
+        else if (IN == IN_RESX) v = Real(__ldg(L.in2 + n)) - sample_gather<Real, NS>(a, L, n);
         else if (IN == IN_TODF) v = (Real)__ldg(static_cast<const float*>(L.in) + n);
         else v = static_cast<const Real*>(L.in)[n];
         v = v * w0;
@@ -1091,7 +1109,7 @@ madmap_status launch_det(Plan* p, const void* in, void* out, long long in_stride
                          const int* skip, cudaStream_t s, cudaEvent_t* ev, int reps, const TileSet* ts,
                          int skip_stride) {
   typedef typename OutT<Real>::type Out;
-  constexpr int NSI = IN == IN_MAPX ? NS : 1;   // a timestream input needs no pointing
+  constexpr int NSI = gathers(IN) ? NS : 1;   // a timestream input needs no pointing
   const int nr = ts ? ts->n_rhs : 1;
   MM_CHECK(p->wtod && p->wtod_rhs >= nr, MADMAP_ERR_INTERNAL, "deterministic plan without a timestream buffer");
   const int grid_x = (int)std::max(1LL, std::min<long long>(((long long)p->n_obs + 7) / 8, 152LL * 16));
@@ -1162,6 +1180,8 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
   a.tw = DF ? (const void*)p->twdf : sizeof(Real) == 8 ? (const void*)p->tw64 : (const void*)p->tw32;
   a.skip = skip;
   a.skip_stride = ts ? skip_stride : 0;
+  a.in2 = p->resid_d;
+  a.in2_stride = p->resid_stride;
   a.n_rep = 1;
   a.rep_stride = 0;
   a.tiles = ts ? ts->tiles : p->tiles;
@@ -1180,6 +1200,7 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
         a.in = static_cast<const char*>(in) + (size_t)r * in_stride * (IN == IN_TODF ? sizeof(float) : sizeof(Real));
         a.out = static_cast<char*>(out) + (size_t)r * out_stride * sizeof(typename OutT<Real>::type);
         a.in_stride = a.out_stride = 0;
+        if (IN == IN_RESX) a.in2 = p->resid_d + (size_t)r * p->resid_stride;
         if (ev) cudaEventRecord(ev[4 * (rep * n_rhs + r)], s);
         if constexpr (extended(NS) && OUT == OUT_MAP) {
           if (p->hwp_base)
@@ -1217,6 +1238,7 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
     for (int r = 0; r < n_rhs; ++r) {
       a.in = static_cast<const char*>(in) + (size_t)r * in_stride *
                                                 (IN == IN_TODF ? sizeof(float) : sizeof(Real));
+      if (IN == IN_RESX && !ts) a.in2 = p->resid_d + (size_t)r * p->resid_stride;
       a.out = static_cast<char*>(out) + (size_t)r * out_stride * sizeof(typename OutT<Real>::type);
       Out* const map_out = static_cast<Out*>(a.out);
       if (use_rep) {
@@ -1277,6 +1299,10 @@ madmap_status dispatch_io(Plan* p, int in_mode, int out_mode, const void* in, vo
     return launch_all<Real, 1, IN_TODR, OUT_TOD>(p, in, out, is, os, n_rhs, skip, s);
   if (in_mode == IN_MAP && out_mode == OUT_TOD)
     return launch_all<Real, NS, IN_MAPX, OUT_TOD>(p, in, out, is, os, n_rhs, skip, s);
+  if constexpr ((NS == 1 || NS == 3) && !std::is_same<Real, float>::value) {
+    if (in_mode == IN_RESID && out_mode == OUT_MAP)
+      return launch_all<Real, NS, IN_RESX, OUT_MAP>(p, in, out, is, os, n_rhs, skip, s);
+  }
   set_error("unsupported operator mode");
   return MADMAP_ERR_INTERNAL;
 }
@@ -1289,6 +1315,10 @@ madmap_status dispatch_df(Plan* p, int in_mode, int out_mode, const void* in, vo
     return launch_all<df64, NS, IN_MAPX, OUT_MAP>(p, in, out, is, os, n_rhs, skip, s);
   if (in_mode == IN_TOD && out_mode == OUT_MAP)
     return launch_all<df64, NS, IN_TODF, OUT_MAP>(p, in, out, is, os, n_rhs, skip, s);
+  if constexpr (NS == 1 || NS == 3) {
+    if (in_mode == IN_RESID && out_mode == OUT_MAP)
+      return launch_all<df64, NS, IN_RESX, OUT_MAP>(p, in, out, is, os, n_rhs, skip, s);
+  }
   set_error("unsupported double-float operator mode");
   return MADMAP_ERR_INTERNAL;
 }
@@ -1354,6 +1384,10 @@ madmap_status dispatch_set(Plan* p, int in_mode, int out_mode, const void* in, v
     return launch_all<Real, NS, IN_MAPX, OUT_MAP>(p, in, out, is, os, 1, skip, s, nullptr, 1, ts, ss);
   if (in_mode == IN_TOD && out_mode == OUT_MAP)
     return launch_all<Real, NS, IN_TODF, OUT_MAP>(p, in, out, is, os, 1, skip, s, nullptr, 1, ts, ss);
+  if constexpr ((NS == 1 || NS == 3) && !std::is_same<Real, float>::value) {
+    if (in_mode == IN_RESID && out_mode == OUT_MAP)
+      return launch_all<Real, NS, IN_RESX, OUT_MAP>(p, in, out, is, os, 1, skip, s, nullptr, 1, ts, ss);
+  }
   set_error("unsupported batched operator mode");
   return MADMAP_ERR_INTERNAL;
 }

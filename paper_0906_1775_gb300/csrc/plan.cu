@@ -54,6 +54,38 @@ madmap_status dalloc(Plan* p, void** ptr, size_t bytes) {
   return MADMAP_OK;
 }
 
+// Device buffers that depend on the FFT length (windows, spectra, twiddles,
+// scratch): kept apart so the autotuner can rebuild them for another length.
+static madmap_status walloc(Plan* p, void** ptr, size_t bytes) {
+  madmap_status st = dalloc(p, ptr, bytes);
+  if (st != MADMAP_OK) return st;
+  p->allocs.pop_back();
+  p->win_allocs.push_back(*ptr);
+  p->win_bytes += bytes == 0 ? 16 : bytes;
+  return MADMAP_OK;
+}
+template <typename T>
+static madmap_status walloc_t(Plan* p, T** ptr, size_t count) {
+  return walloc(p, reinterpret_cast<void**>(ptr), count * sizeof(T));
+}
+
+static void free_windows(Plan* p) {
+  if (p->win_allocs.empty()) return;
+  cudaDeviceSynchronize();
+  for (void* a : p->win_allocs) cudaFree(a);
+  p->win_allocs.clear();
+  p->device_bytes -= p->win_bytes;
+  p->win_bytes = 0;
+  p->tiles = nullptr;
+  p->H64 = nullptr;
+  p->H32 = nullptr;
+  p->Hdf = nullptr;
+  p->tw64 = nullptr;
+  p->tw32 = nullptr;
+  p->twdf = nullptr;
+  p->scratch = nullptr;
+}
+
 void free_solve_buffers(Plan* p);          // solver.cu
 size_t solve_buffer_bytes(const Plan* p);  // solver.cu
 
@@ -68,6 +100,7 @@ Plan::~Plan() {
   }
   if (op_fork) cudaEventDestroy(op_fork);
   for (void* a : allocs) cudaFree(a);
+  for (void* a : win_allocs) cudaFree(a);
 }
 
 // ---------------------------------------------------------------- host FFT
@@ -1200,6 +1233,155 @@ madmap_status reduce_across(Plan* p, void* buf, long long count, int dtype, cuda
   return MADMAP_OK;
 }
 
+// Windows, spectra, twiddles, chunking, streams and scratch for FFT length M
+// (replacing those of an earlier length).  tpc_req > 0 fixes the tiles per
+// launch chunk.
+static madmap_status setup_windows(Plan* p, int M, long long tpc_req, cudaStream_t s) {
+  free_windows(p);
+  p->M = M;
+  {
+    const int lg = ilog2((unsigned)p->M);
+    p->logN2 = (lg + 1) / 2;
+    p->logN1 = lg - p->logN2;
+    p->N1 = 1 << p->logN1;
+    p->N2 = 1 << p->logN2;
+  }
+  std::vector<Seg> segs;
+  make_segments(p->offsets, p->ivl_filter, p->n_lags, p->M, segs);
+  p->host_tiles.clear();
+  pair_tiles(segs, p->n_filters, p->host_tiles);
+  p->n_segments = (int)segs.size();
+  p->n_tiles = (int)p->host_tiles.size();
+  {
+    // Chunk size: launches of many CTA waves let CTAs in different phases
+    // (gather, FFT passes, scatter) overlap on each SM, which beat wave-sized
+    // chunks whose scratch stays in L2.  At most 1 GB of scratch per chunk
+    // (float64 sizing), and at least two chunks when there are 16 tiles or
+    // more: chunks alternate between two streams, so each launch's tail
+    // overlaps the next chunk (4 x 2^22-sample IQU scan: 0.325 ms against 0.341 ms in one launch).
+    long long tpc = tpc_req;
+    if (tpc <= 0) {
+      tpc = std::max(1LL, (1LL << 30) / (16LL * p->M));
+      if (p->n_tiles >= 16) tpc = std::min<long long>(tpc, (p->n_tiles + 1) / 2);
+    }
+    tpc = std::max(1LL, std::min<long long>(tpc, std::max(1, p->n_tiles)));
+    tpc = std::min<long long>(tpc, 65535);
+    p->tiles_per_chunk = (int)tpc;
+  }
+  madmap_status st = walloc_t(p, &p->tiles, std::max(1, p->n_tiles));
+  if (st != MADMAP_OK) return st;
+  if (p->n_tiles)
+    MM_CUDA(cudaMemcpy(p->tiles, p->host_tiles.data(), sizeof(Tile) * p->n_tiles, cudaMemcpyHostToDevice));
+  if ((st = walloc_t(p, &p->H64, (size_t)p->n_filters * p->M)) != MADMAP_OK) return st;
+  if ((st = walloc_t(p, &p->H32, (size_t)p->n_filters * p->M)) != MADMAP_OK) return st;
+  if ((st = walloc_t(p, &p->Hdf, (size_t)p->n_filters * p->M)) != MADMAP_OK) return st;
+  if ((st = build_spectra(p)) != MADMAP_OK) return st;
+  {
+    std::vector<double2> t64(p->M);
+    std::vector<float2> t32(p->M);
+    std::vector<cdf64> tdf(p->M);
+    for (int j = 0; j < p->M; ++j) {
+      const double ang = 2.0 * M_PI * (double)j / (double)p->M;
+      t64[j] = make_double2(cos(ang), -sin(ang));
+      t32[j] = make_float2((float)t64[j].x, (float)t64[j].y);
+      tdf[j].x = df64(t64[j].x);
+      tdf[j].y = df64(t64[j].y);
+    }
+    if ((st = walloc_t(p, &p->tw64, p->M)) != MADMAP_OK) return st;
+    if ((st = walloc_t(p, &p->tw32, p->M)) != MADMAP_OK) return st;
+    if ((st = walloc_t(p, &p->twdf, p->M)) != MADMAP_OK) return st;
+    MM_CUDA(cudaMemcpy(p->tw64, t64.data(), sizeof(double2) * p->M, cudaMemcpyHostToDevice));
+    MM_CUDA(cudaMemcpy(p->tw32, t32.data(), sizeof(float2) * p->M, cudaMemcpyHostToDevice));
+    MM_CUDA(cudaMemcpy(p->twdf, tdf.data(), sizeof(cdf64) * p->M, cudaMemcpyHostToDevice));
+  }
+  {
+    const int n_chunks = p->n_tiles ? (p->n_tiles + p->tiles_per_chunk - 1) / p->tiles_per_chunk : 0;
+    p->scratch_slots = n_chunks > 1 ? 2 : 1;
+    if (n_chunks > 1 && !p->op_stream[0]) {
+      for (int i = 0; i < 2; ++i) {
+        MM_CUDA(cudaStreamCreateWithFlags(&p->op_stream[i], cudaStreamNonBlocking));
+        MM_CUDA(cudaEventCreateWithFlags(&p->op_join[i], cudaEventDisableTiming));
+      }
+      MM_CUDA(cudaEventCreateWithFlags(&p->op_fork, cudaEventDisableTiming));
+    }
+  }
+  return walloc(p, &p->scratch, (size_t)p->scratch_slots * p->tiles_per_chunk * p->M * sizeof(double2));
+}
+
+// Measuring autotuner: time one float32 operator application (CUDA events on
+// `s`, after one warm-up application) for every candidate FFT length (the
+// given one, or the cost model's choice and its neighbours a factor two either
+// way) and tiles per launch chunk (the given number, or the default rule and
+// half and twice it), then keep the fastest.  The candidates' times are
+// reported in the plan's stats.
+static madmap_status autotune_windows(Plan* p, int M_fixed, int M0, long long tpc_fixed, cudaStream_t s) {
+  std::vector<int> Ms;
+  for (int M : {M0 / 2, M0, 2 * M0})
+    if ((M_fixed == 0 || M == M_fixed) && M >= 256 && M <= (1 << 20) && M - 2 * (p->n_lags - 1) >= 1) Ms.push_back(M);
+  const long long nv = (long long)std::max(1, p->n_obs) * p->ns_pad;
+  float *x = nullptr, *y = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(x);
+    cudaFree(y);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  cudaError_t ce = cudaMalloc(&x, sizeof(float) * nv);
+  if (ce == cudaSuccess) ce = cudaMalloc(&y, sizeof(float) * nv);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(x, 0, sizeof(float) * nv, s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(y, 0, sizeof(float) * nv, s);
+  if (ce != cudaSuccess) {
+    cleanup();
+    return cuda_fail(ce, "autotune buffers");
+  }
+  p->tuned.clear();
+  int bestM = M0;
+  long long bestT = tpc_fixed;
+  float best = 3.4e38f;
+  madmap_status st = MADMAP_OK;
+  for (int M : Ms) {
+    std::vector<long long> tpcs;
+    if (tpc_fixed > 0) {
+      tpcs.push_back(tpc_fixed);
+    } else {
+      if ((st = setup_windows(p, M, 0, s)) != MADMAP_OK) break;
+      const long long t0 = p->tiles_per_chunk;
+      for (long long t : {t0 / 2, t0, 2 * t0})
+        if (t >= 1 && (t < 2 * t0 || t <= p->n_tiles) && std::find(tpcs.begin(), tpcs.end(), t) == tpcs.end())
+          tpcs.push_back(t);
+    }
+    for (long long tpc : tpcs) {
+      if ((st = setup_windows(p, M, tpc, s)) != MADMAP_OK) break;
+      if ((st = op_launch(p, OPP_F32, IN_MAP, OUT_MAP, x, y, 0, 0, 1, nullptr, s)) != MADMAP_OK) break;
+      const int reps = 3;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps && st == MADMAP_OK; ++r)
+        st = op_launch(p, OPP_F32, IN_MAP, OUT_MAP, x, y, 0, 0, 1, nullptr, s);
+      cudaEventRecord(e1, s);
+      if (st != MADMAP_OK) break;
+      float ms = 0.f;
+      if ((ce = cudaEventSynchronize(e1)) != cudaSuccess || (ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+        st = cuda_fail(ce, "autotune timing");
+        break;
+      }
+      ms /= reps;
+      p->tuned.push_back({M, (int)p->tiles_per_chunk, ms});
+      if (ms < best) {
+        best = ms;
+        bestM = M;
+        bestT = p->tiles_per_chunk;
+      }
+    }
+    if (st != MADMAP_OK) break;
+  }
+  cleanup();
+  if (st != MADMAP_OK) return st;
+  return setup_windows(p, bestM, bestT, s);
+}
+
 }  // namespace mm
 
 // ---------------------------------------------------------------- C ABI
@@ -1496,41 +1678,6 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
     p->det = true;
     MM_TRY(build_det_rows(p, s));
   }
-  // FFT geometry and windows
-  p->M = d->fft_len ? d->fft_len : choose_fft_len(p->offsets, p->ivl_filter, p->n_filters, p->n_lags);
-  if (p->M <= 0) {
-    delete p;
-    set_error("no FFT length up to 2^20 fits n_lags");
-    return MADMAP_ERR_INVALID_ARG;
-  }
-  {
-    const int lg = ilog2((unsigned)p->M);
-    p->logN2 = (lg + 1) / 2;
-    p->logN1 = lg - p->logN2;
-    p->N1 = 1 << p->logN1;
-    p->N2 = 1 << p->logN2;
-  }
-  std::vector<Seg> segs;
-  make_segments(p->offsets, p->ivl_filter, p->n_lags, p->M, segs);
-  pair_tiles(segs, p->n_filters, p->host_tiles);
-  p->n_segments = (int)segs.size();
-  p->n_tiles = (int)p->host_tiles.size();
-  {
-    // Chunk size: launches of many CTA waves let CTAs in different phases
-    // (gather, FFT passes, scatter) overlap on each SM, which beat wave-sized
-    // chunks whose scratch stays in L2.  At most 1 GB of scratch per chunk
-    // (float64 sizing), and at least two chunks when there are 16 tiles or
-    // more: chunks alternate between two streams, so each launch's tail
-    // overlaps the next chunk (4 x 2^22-sample IQU scan: 0.325 ms against 0.341 ms in one launch).
-    long long tpc = d->tiles_per_chunk;
-    if (tpc <= 0) {
-      tpc = std::max(1LL, (1LL << 30) / (16LL * p->M));
-      if (p->n_tiles >= 16) tpc = std::min<long long>(tpc, (p->n_tiles + 1) / 2);
-    }
-    tpc = std::max(1LL, std::min<long long>(tpc, std::max(1, p->n_tiles)));
-    tpc = std::min<long long>(tpc, 65535);
-    p->tiles_per_chunk = (int)tpc;
-  }
   if (p->n_lags == 1) {
     // white noise: runs of at most 2048 samples within each interval
     std::vector<DiagItem> items;
@@ -1548,43 +1695,20 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
     MM_TRYC(cudaMemcpy(p->f0_64, f0.data(), sizeof(double) * p->n_filters, cudaMemcpyHostToDevice));
     p->diag = true;
   }
-  MM_TRY(dalloc_t(p, &p->tiles, std::max(1, p->n_tiles)));
-  if (p->n_tiles)
-    MM_TRYC(cudaMemcpy(p->tiles, p->host_tiles.data(), sizeof(Tile) * p->n_tiles, cudaMemcpyHostToDevice));
-  MM_TRY(dalloc_t(p, &p->H64, (size_t)p->n_filters * p->M));
-  MM_TRY(dalloc_t(p, &p->H32, (size_t)p->n_filters * p->M));
-  MM_TRY(dalloc_t(p, &p->Hdf, (size_t)p->n_filters * p->M));
-  MM_TRY(build_spectra(p));
+  // FFT geometry and windows: the length and the tiles per launch chunk given
+  // in the description, else chosen by the cost model, or by measurement
   {
-    std::vector<double2> t64(p->M);
-    std::vector<float2> t32(p->M);
-    std::vector<cdf64> tdf(p->M);
-    for (int j = 0; j < p->M; ++j) {
-      const double ang = 2.0 * M_PI * (double)j / (double)p->M;
-      t64[j] = make_double2(cos(ang), -sin(ang));
-      t32[j] = make_float2((float)t64[j].x, (float)t64[j].y);
-      tdf[j].x = df64(t64[j].x);
-      tdf[j].y = df64(t64[j].y);
+    const int M0 = d->fft_len ? d->fft_len : choose_fft_len(p->offsets, p->ivl_filter, p->n_filters, p->n_lags);
+    if (M0 <= 0) {
+      delete p;
+      set_error("no FFT length up to 2^20 fits n_lags");
+      return MADMAP_ERR_INVALID_ARG;
     }
-    MM_TRY(dalloc_t(p, &p->tw64, p->M));
-    MM_TRY(dalloc_t(p, &p->tw32, p->M));
-    MM_TRY(dalloc_t(p, &p->twdf, p->M));
-    MM_TRYC(cudaMemcpy(p->tw64, t64.data(), sizeof(double2) * p->M, cudaMemcpyHostToDevice));
-    MM_TRYC(cudaMemcpy(p->tw32, t32.data(), sizeof(float2) * p->M, cudaMemcpyHostToDevice));
-    MM_TRYC(cudaMemcpy(p->twdf, tdf.data(), sizeof(cdf64) * p->M, cudaMemcpyHostToDevice));
+    if (d->autotune && !p->diag && p->n_t > 0 && p->n_obs > 0)
+      MM_TRY(autotune_windows(p, d->fft_len ? d->fft_len : 0, M0, d->tiles_per_chunk, s));
+    else
+      MM_TRY(setup_windows(p, M0, d->tiles_per_chunk, s));
   }
-  {
-    const int n_chunks = p->n_tiles ? (p->n_tiles + p->tiles_per_chunk - 1) / p->tiles_per_chunk : 0;
-    p->scratch_slots = n_chunks > 1 ? 2 : 1;
-    if (n_chunks > 1) {
-      for (int i = 0; i < 2; ++i) {
-        MM_TRYC(cudaStreamCreateWithFlags(&p->op_stream[i], cudaStreamNonBlocking));
-        MM_TRYC(cudaEventCreateWithFlags(&p->op_join[i], cudaEventDisableTiming));
-      }
-      MM_TRYC(cudaEventCreateWithFlags(&p->op_fork, cudaEventDisableTiming));
-    }
-  }
-  MM_TRY(dalloc(p, &p->scratch, (size_t)p->scratch_slots * p->tiles_per_chunk * p->M * sizeof(double2)));
   if (!p->det && p->n_obs > 0 && p->n_t >= 1024LL * p->n_obs && (long long)p->n_obs * p->ns_pad <= (1LL << 17)) {
     // a small map under more than 1024 samples per row: eight scatter replicas
     p->n_rep = 8;
@@ -1633,6 +1757,13 @@ extern "C" madmap_status madmap_plan_get_stats(madmap_plan_t plan, madmap_plan_s
   o->n_excised_hwp = p->n_excised_hwp;
   o->n_map_replicas = p->n_rep;
   o->deterministic = p->det ? 1 : 0;
+  o->n_tuned = (int32_t)std::min<size_t>(p->tuned.size(), 9);
+  for (int k = 0; k < 9; ++k) {
+    const bool has = k < o->n_tuned;
+    o->tuned_fft_len[k] = has ? p->tuned[k].M : 0;
+    o->tuned_tiles_per_chunk[k] = has ? p->tuned[k].tpc : 0;
+    o->tuned_ms[k] = has ? p->tuned[k].ms : 0.f;
+  }
   o->sharded = p->allreduce ? 1 : 0;
   return MADMAP_OK;
 }

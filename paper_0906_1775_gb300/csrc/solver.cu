@@ -521,6 +521,21 @@ static int refine_prec(const madmap_solve_opts& o) {
   return (o.precision == MADMAP_MIXED && o.refine_precision == MADMAP_DF64) ? OPP_DF64 : OPP_F64;
 }
 
+// Mixed solves of single-resolution stored pointing compute each refinement
+// residual b - H x as A^T N^-1 (d - A x) in one full-precision operator
+// application (the difference taken per sample before the noise weighting),
+// so the right-hand side itself only starts the first float32 inner solve and
+// is formed in float32.
+static bool fused_residual(const Plan* p, const madmap_solve_opts& o) {
+  return o.precision == MADMAP_MIXED && !p->otf && !p->ext && !p->multires;
+}
+
+// y = (double) x
+__global__ void k_widen(const float* x, double* y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+
 // r64 = b64 - t64 and ||r64|| -> st[rhs].res (by the last block of the rhs)
 __global__ void __launch_bounds__(NT) k_residual(const double* b64, const double* t64, double* r64, long long nvec,
                                                  CgState* st, double* partials, const int* inactive) {
@@ -882,9 +897,13 @@ static double ms_since(std::chrono::steady_clock::time_point t) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
 }
 
+// d (device float [n_rhs][n_t], or NULL when b does not come from data, as in
+// the adjoint solve): mixed solves then compute their refinement residuals
+// from d (fused_residual).
 template <int NS>
 static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, const madmap_solve_opts& o,
-                                std::vector<madmap_solve_info>& I, cudaStream_t s, const double** x_pad) {
+                                std::vector<madmap_solve_info>& I, cudaStream_t s, const double** x_pad,
+                                const float* d = nullptr) {
   const int n_rhs = B.n_rhs;
   const long long nv = sb64->nvec;
   const dim3 gv(grid_vec(nv), n_rhs);
@@ -963,13 +982,29 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
       k_split<<<grid_vec(nv * n_rhs), NT, 0, s>>>(sb64->x64, sb64->xdf, nv * n_rhs);
       xin = sb64->xdf;
     }
-    if (B.ts)
-      st = op_launch_set(p, rp, IN_MAP, OUT_MAP, xin, sb64->t64, nv, nv, sb64->flags, 1, B.ts, s);
-    else
-      st = op_launch(p, rp, IN_MAP, OUT_MAP, xin, sb64->t64, 0, 0, 1, nullptr, s);
-    if (st == MADMAP_OK) st = reduce_across(p, sb64->t64, nv * n_rhs, MADMAP_REDUCE_F64, s);
-    if (st != MADMAP_OK) return st;
-    k_residual<<<gv, NT, 0, s>>>(sb64->b64, sb64->t64, sb64->r64, nv, sb64->st, sb64->partials, sb64->flags);
+    if (d && fused_residual(p, o)) {
+      // r = A^T N^-1 (d - A x) in one pass; t64 (zero since k_refine_add) stands in for H x
+      MM_CUDA(cudaMemsetAsync(sb64->r64, 0, sizeof(double) * nv * n_rhs, s));
+      p->resid_d = d;
+      p->resid_stride = p->n_t;
+      if (B.ts)
+        st = op_launch_set(p, rp, IN_RESID, OUT_MAP, xin, sb64->r64, nv, nv, sb64->flags, 1, B.ts, s);
+      else
+        st = op_launch(p, rp, IN_RESID, OUT_MAP, xin, sb64->r64, 0, 0, 1, nullptr, s);
+      p->resid_d = nullptr;
+      p->resid_stride = 0;
+      if (st == MADMAP_OK) st = reduce_across(p, sb64->r64, nv * n_rhs, MADMAP_REDUCE_F64, s);
+      if (st != MADMAP_OK) return st;
+      k_residual<<<gv, NT, 0, s>>>(sb64->r64, sb64->t64, sb64->r64, nv, sb64->st, sb64->partials, sb64->flags);
+    } else {
+      if (B.ts)
+        st = op_launch_set(p, rp, IN_MAP, OUT_MAP, xin, sb64->t64, nv, nv, sb64->flags, 1, B.ts, s);
+      else
+        st = op_launch(p, rp, IN_MAP, OUT_MAP, xin, sb64->t64, 0, 0, 1, nullptr, s);
+      if (st == MADMAP_OK) st = reduce_across(p, sb64->t64, nv * n_rhs, MADMAP_REDUCE_F64, s);
+      if (st != MADMAP_OK) return st;
+      k_residual<<<gv, NT, 0, s>>>(sb64->b64, sb64->t64, sb64->r64, nv, sb64->st, sb64->partials, sb64->flags);
+    }
     MM_CUDA(cudaMemcpyAsync(h.data(), sb64->st, sizeof(CgState) * n_rhs, cudaMemcpyDeviceToHost, s));
     MM_CUDA(cudaStreamSynchronize(s));
     bool any_take = false;
@@ -1045,23 +1080,43 @@ static madmap_status solve_impl(Plan* p, int n_rhs, const float* d, double* m, c
   const int n = p->n_obs;
   std::vector<madmap_solve_info> I(n_rhs);
   for (auto& x : I) memset(&x, 0, sizeof(x));
-  // right-hand sides b = A^T N^-1 d into float64 maps (float64 or double-float arithmetic)
-  MM_CUDA(cudaMemsetAsync(sb64->b64, 0, sizeof(double) * nv * n_rhs, s));
-  if (B.ts)
-    st = op_launch_set(p, refine_prec(o), IN_TOD, OUT_MAP, d, sb64->b64, p->n_t, nv, nullptr, 0, B.ts, s);
-  else
-    st = op_launch(p, refine_prec(o), IN_TOD, OUT_MAP, d, sb64->b64, 0, 0, 1, nullptr, s);
-  if (st == MADMAP_OK) st = reduce_across(p, sb64->b64, nv * n_rhs, MADMAP_REDUCE_F64, s);
-  if (st != MADMAP_OK) return st;
+  const bool fused = fused_residual(p, o);
+  if (fused) {
+    // b in float32: it only starts the first float32 inner solve (every
+    // refinement residual is formed from d in full precision)
+    SolveBuffers* sb32 = nullptr;
+    st = get_buffers(p, false, n_rhs, &sb32);
+    if (st != MADMAP_OK) return st;
+    float* b32 = static_cast<float*>(sb32->q);
+    MM_CUDA(cudaMemsetAsync(b32, 0, sizeof(float) * nv * n_rhs, s));
+    if (B.ts)
+      st = op_launch_set(p, OPP_F32, IN_TOD, OUT_MAP, d, b32, p->n_t, nv, nullptr, 0, B.ts, s);
+    else
+      st = op_launch(p, OPP_F32, IN_TOD, OUT_MAP, d, b32, 0, 0, 1, nullptr, s);
+    if (st == MADMAP_OK) st = reduce_across(p, b32, nv * n_rhs, MADMAP_REDUCE_F32, s);
+    if (st != MADMAP_OK) return st;
+    count_launches(1);
+    k_widen<<<grid_vec(nv * n_rhs), NT, 0, s>>>(b32, sb64->b64, nv * n_rhs);
+  } else {
+    // right-hand sides b = A^T N^-1 d into float64 maps (float64 or double-float arithmetic)
+    MM_CUDA(cudaMemsetAsync(sb64->b64, 0, sizeof(double) * nv * n_rhs, s));
+    if (B.ts)
+      st = op_launch_set(p, refine_prec(o), IN_TOD, OUT_MAP, d, sb64->b64, p->n_t, nv, nullptr, 0, B.ts, s);
+    else
+      st = op_launch(p, refine_prec(o), IN_TOD, OUT_MAP, d, sb64->b64, 0, 0, 1, nullptr, s);
+    if (st == MADMAP_OK) st = reduce_across(p, sb64->b64, nv * n_rhs, MADMAP_REDUCE_F64, s);
+    if (st != MADMAP_OK) return st;
+  }
   MM_CUDA(cudaStreamSynchronize(s));
   const double t_rhs =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   for (auto& x : I) {
-    x.fp64_applies = 1;
+    x.fp64_applies = fused ? 0 : 1;
+    x.fp32_applies = fused ? 1 : 0;
     x.t_rhs_ms = t_rhs;
   }
   const double* xr = nullptr;
-  st = solve_core<NS>(p, B, sb64, o, I, s, &xr);
+  st = solve_core<NS>(p, B, sb64, o, I, s, &xr, d);
   if (st != MADMAP_OK) return st;
   for (int k = 0; k < n_rhs; ++k) {
     count_launches(1);
