@@ -631,6 +631,36 @@ struct PassGeom {
 // forward = small DFT then output twiddles (decimation in frequency, output
 // bit-reversed after all passes); inverse = conjugate twiddles then inverse
 // small DFT, passes in reverse order, returning N times the input.
+// The output twiddles w^k (k = 1 .. 2^R - 1) of a group, w = tw[j] the k = 1
+// entry of its pass table.  Float32 forms them by products of w (w^2 = w w,
+// w^3 = w^2 w, w^4 = w^2 w^2, w^5 = w^4 w, w^6 = w^3 w^3, w^7 = w^4 w^3: at most
+// three roundings past the table entry), so a group reads one table entry
+// instead of 2^R - 1 and the shared-memory pipe, which bounds the operator
+// kernels, carries less; the float64-size types read every power from the
+// table (their products cost more than the loads).
+#ifndef MM_TW_POWERS
+#define MM_TW_POWERS 1
+#endif
+template <typename C, int R>
+__device__ __forceinline__ void pass_twiddles(const C* tw, int logh, int j, C (&w)[1 << R]) {
+  if constexpr (sizeof(C) == 8 && MM_TW_POWERS) {
+    w[1] = tw[j];
+    if (R >= 2) {
+      w[2] = cmul(w[1], w[1]);
+      w[3] = cmul(w[2], w[1]);
+    }
+    if (R >= 3) {
+      w[4] = cmul(w[2], w[2]);
+      w[5] = cmul(w[4], w[1]);
+      w[6] = cmul(w[3], w[3]);
+      w[7] = cmul(w[4], w[3]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 1; k < (1 << R); ++k) w[k] = tw[((k - 1) << logh) + j];
+  }
+}
+
 template <typename C, int R, bool INV, int SW>
 __device__ __forceinline__ void fft_pass(C* buf, int rows, int rs, int logN, int s, const C* tw) {
   const PassGeom G(logN, s, R);
@@ -643,13 +673,15 @@ __device__ __forceinline__ void fft_pass(C* buf, int rows, int rs, int logN, int
     C v[1 << R];
 #pragma unroll
     for (int m = 0; m < (1 << R); ++m) v[m] = rp[swz<SW>(base + m * G.hR)];
+    C w[1 << R];
+    pass_twiddles<C, R>(tw, G.logh, j, w);
     if (!INV) {
       small_dft<C, R, false>(v);
 #pragma unroll
-      for (int m = 1; m < (1 << R); ++m) v[m] = cmul(v[m], tw[((brev_small<R>(m) - 1) << G.logh) + j]);
+      for (int m = 1; m < (1 << R); ++m) v[m] = cmul(v[m], w[brev_small<R>(m)]);
     } else {
 #pragma unroll
-      for (int m = 1; m < (1 << R); ++m) v[m] = cmulc(v[m], tw[((brev_small<R>(m) - 1) << G.logh) + j]);
+      for (int m = 1; m < (1 << R); ++m) v[m] = cmulc(v[m], w[brev_small<R>(m)]);
       small_dft<C, R, true>(v);
     }
 #pragma unroll

@@ -453,6 +453,35 @@ __device__ __forceinline__ C split_twiddle(const C* lo, const C* hi, const C* tw
   else return cmul(hi[m >> logL], lo[m & ((1 << logL) - 1)]);
 }
 __host__ __device__ inline int split_log(int logM) { return (logM + 1) >> 1; }
+
+// The four-step twiddles of one thread's elements in the column kernels'
+// scratch phases.  With 4096 elements per CTA and 256 threads, thread t owns
+// elements t + 256 u (u = 0 .. 15): column n1 = n1_0 + (t mod B1) and row
+// position p0 + (256 / B1) u, p0 = t / B1, whose bit reversal is
+// K0 + brev4(u) (the bits of p0 and of the row step do not overlap).  Its
+// twiddles exp(-2 pi i n1 k2 / M) are therefore A B^v, v = brev4(u), with
+// A = w^(n1 K0) and B = w^(n1) read once from the split tables: p4[a] = A B^(4a)
+// and p1[b] = B^b, so the twiddle of v = 4a + b is p4[a] p1[b] (at most eight
+// roundings; float32 only, replacing two scattered table reads per element).
+template <typename C>
+__device__ __forceinline__ void scratch_twiddles(const C* lo, const C* hi, const C* twM, int n1, int K0, int mask,
+                                                 int logL, C (&p4)[4], C (&p1)[4]) {
+  const C A = split_twiddle(lo, hi, twM, (n1 * K0) & mask, logL);
+  const C B = split_twiddle(lo, hi, twM, n1 & mask, logL);
+  const C B2 = cmul(B, B), B4 = cmul(B2, B2), B8 = cmul(B4, B4);
+  p1[0].x = 1;
+  p1[0].y = 0;
+  p1[1] = B;
+  p1[2] = B2;
+  p1[3] = cmul(B2, B);
+  p4[0] = A;
+  p4[1] = cmul(A, B4);
+  p4[2] = cmul(A, B8);
+  p4[3] = cmul(A, cmul(B8, B4));
+}
+__host__ __device__ constexpr int brev4(int u) {
+  return ((u & 1) << 3) | ((u & 2) << 1) | ((u & 4) >> 1) | ((u & 8) >> 3);
+}
 // Shared entries of the two split tables (none for float64).
 __host__ __device__ inline int split_entries(int esz, int logM) {
   return esz == 8 ? (1 << split_log(logM)) + (1 << (logM - split_log(logM))) : 0;
@@ -606,11 +635,22 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? MM_MINB_F13 : 2) k_f1
   fft_rows<C, false, SW>(buf, B1, rs, logN2, tw);
   C* sc = static_cast<C*>(a.scratch) + (long long)tl * a.M;
   const int mask = a.M - 1;
+  if constexpr (sizeof(C) == 8 && LG2 > 0 && MM_TW_POWERS && ELOG == 12 && OP_THREADS == 256) {
+    const int j = threadIdx.x & (B1 - 1), p0 = threadIdx.x >> logB1;
+    C p4[4], p1[4];
+    scratch_twiddles(tlo, thi, twM, n1_0 + j, brev_n(p0, logN2), mask, logL, p4, p1);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int v = brev4(u), pos = p0 + (u << (8 - logB1));
+      sc[(long long)pos * a.N1 + n1_0 + j] = cmul(buf[j * rs + swz<SW>(pos)], cmul(p4[v >> 2], p1[v & 3]));
+    }
+  } else {
 #pragma unroll 4
-  for (int e = threadIdx.x; e < total; e += bd) {
-    const int j = e & (B1 - 1), pos = e >> logB1;
-    const C w = split_twiddle(tlo, thi, twM, ((n1_0 + j) * brev_n(pos, logN2)) & mask, logL);
-    sc[(long long)pos * a.N1 + n1_0 + j] = cmul(buf[j * rs + swz<SW>(pos)], w);
+    for (int e = threadIdx.x; e < total; e += bd) {
+      const int j = e & (B1 - 1), pos = e >> logB1;
+      const C w = split_twiddle(tlo, thi, twM, ((n1_0 + j) * brev_n(pos, logN2)) & mask, logL);
+      sc[(long long)pos * a.N1 + n1_0 + j] = cmul(buf[j * rs + swz<SW>(pos)], w);
+    }
   }
 }
 
@@ -694,20 +734,37 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? MM_MINB_F13 : 2) k_f3
   constexpr int bd = OP_THREADS;
   const C* sc = static_cast<const C*>(a.scratch) + (long long)tl * a.M;
   const int mask = a.M - 1;
-  for (int e0 = threadIdx.x; e0 < total; e0 += bd * 8) {
-    C v[8];
+  if constexpr (sizeof(C) == 8 && LG2 > 0 && MM_TW_POWERS && ELOG == 12 && OP_THREADS == 256) {
+    const int j = threadIdx.x & (B1 - 1), p0 = threadIdx.x >> logB1;
+    C p4[4], p1[4];
+    scratch_twiddles(tlo, thi, twM, n1_0 + j, brev_n(p0, logN2), mask, logL, p4, p1);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * bd;
-      if (e < total) v[u] = sc[(long long)(e >> logB1) * a.N1 + n1_0 + (e & (B1 - 1))];
+    for (int h = 0; h < 2; ++h) {
+      C v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = sc[(long long)(p0 + ((8 * h + k) << (8 - logB1))) * a.N1 + n1_0 + j];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int u = 8 * h + k, w = brev4(u), pos = p0 + (u << (8 - logB1));
+        buf[j * rs + swz<SW>(pos)] = cmulc(v[k], cmul(p4[w >> 2], p1[w & 3]));
+      }
     }
+  } else {
+    for (int e0 = threadIdx.x; e0 < total; e0 += bd * 8) {
+      C v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * bd;
-      if (e < total) {
-        const int n1 = n1_0 + (e & (B1 - 1)), pos = e >> logB1;
-        const C w = split_twiddle(tlo, thi, twM, (n1 * brev_n(pos, logN2)) & mask, logL);
-        buf[(e & (B1 - 1)) * rs + swz<SW>(pos)] = cmulc(v[u], w);
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * bd;
+        if (e < total) v[u] = sc[(long long)(e >> logB1) * a.N1 + n1_0 + (e & (B1 - 1))];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * bd;
+        if (e < total) {
+          const int n1 = n1_0 + (e & (B1 - 1)), pos = e >> logB1;
+          const C w = split_twiddle(tlo, thi, twM, (n1 * brev_n(pos, logN2)) & mask, logL);
+          buf[(e & (B1 - 1)) * rs + swz<SW>(pos)] = cmulc(v[u], w);
+        }
       }
     }
   }
