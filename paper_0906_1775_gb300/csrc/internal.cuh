@@ -730,21 +730,43 @@ __device__ __forceinline__ void fft_pass_any(C* buf, int rows, int rs, int logN,
 }
 
 // Full FFT of `rows` rows of length N = 2^logN held in shared memory
-// (tw: N entries).
+// (tw: N entries).  s_lo = 3 leaves out the first pass (s = 0) of a forward
+// transform, or the last pass of an inverse one, which the caller does in
+// registers (reg_pass8).
 template <typename C, bool INV, int SW>
-__device__ __forceinline__ void fft_rows(C* buf, int rows, int rs, int logN, const C* tw) {
+__device__ __forceinline__ void fft_rows(C* buf, int rows, int rs, int logN, const C* tw, int s_lo = 0) {
   if (!INV) {
 #pragma unroll
-    for (int s = 0; s < logN; s += 3) {
+    for (int s = s_lo; s < logN; s += 3) {
       fft_pass_any<C, false, SW>(buf, rows, rs, logN, s, tw);
       __syncthreads();
     }
   } else {
 #pragma unroll
-    for (int s = last_pass_start(logN); s >= 0; s -= 3) {
+    for (int s = last_pass_start(logN); s >= s_lo; s -= 3) {
       fft_pass_any<C, true, SW>(buf, rows, rs, logN, s, tw);
       __syncthreads();
     }
+  }
+}
+
+// The first radix-8 pass (s = 0) of a forward transform of length N on one
+// group held in registers: the elements base + m N/8 (m = 0..7) in v, the
+// group's twiddles from the pass table entry tw[base]; or, INV, the last pass
+// of the inverse transform.  The same arithmetic as fft_pass<C, 3, INV> on the
+// group, with no trip through shared memory.
+template <typename C, bool INV>
+__device__ __forceinline__ void reg_pass8(C (&v)[8], const C* tw, int logN, int base) {
+  C w[8];
+  pass_twiddles<C, 3>(tw, logN - 3, base, w);
+  if (!INV) {
+    small_dft<C, 3, false>(v);
+#pragma unroll
+    for (int m = 1; m < 8; ++m) v[m] = cmul(v[m], w[brev_small<3>(m)]);
+  } else {
+#pragma unroll
+    for (int m = 1; m < 8; ++m) v[m] = cmulc(v[m], w[brev_small<3>(m)]);
+    small_dft<C, 3, true>(v);
   }
 }
 
@@ -787,10 +809,11 @@ __device__ __forceinline__ void fused_middle(C* buf, int rows, int rs, int logN,
 }
 
 template <typename C, int SW, typename HF>
-__device__ __forceinline__ void fft_rows_filter(C* buf, int rows, int rs, int logN, const C* tw, HF Hrow) {
+__device__ __forceinline__ void fft_rows_filter(C* buf, int rows, int rs, int logN, const C* tw, HF Hrow,
+                                                int s_lo = 0) {
   const int sl = last_pass_start(logN);
 #pragma unroll
-  for (int s = 0; s < sl; s += 3) {
+  for (int s = s_lo; s < sl; s += 3) {
     fft_pass_any<C, false, SW>(buf, rows, rs, logN, s, tw);
     __syncthreads();
   }
@@ -800,7 +823,7 @@ __device__ __forceinline__ void fft_rows_filter(C* buf, int rows, int rs, int lo
   else fused_middle<C, 1, SW>(buf, rows, rs, logN, sl, Hrow);
   __syncthreads();
 #pragma unroll
-  for (int s = sl - 3; s >= 0; s -= 3) {
+  for (int s = sl - 3; s >= s_lo; s -= 3) {
     fft_pass_any<C, true, SW>(buf, rows, rs, logN, s, tw);
     __syncthreads();
   }

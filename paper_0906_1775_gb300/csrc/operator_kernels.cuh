@@ -520,6 +520,11 @@ __global__ void k_weights(long long n, const float* __restrict__ psi, Real* c, R
 #ifndef MM_U_SCATTER
 #define MM_U_SCATTER 4
 #endif
+// Float32: the outermost radix-8 pass of each transform runs in registers on
+// the way into or out of shared memory (1) or inside it like the others (0).
+#ifndef MM_REG_PASS
+#define MM_REG_PASS 1
+#endif
 template <typename Real>
 __host__ __device__ constexpr int elog() {
   return sizeof(Real) == 4 ? MM_ELOG_F32 : 11;
@@ -556,17 +561,18 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? MM_MINB_F13 : 2) k_f1
   const int total = B1 << logN2;
   constexpr int bd = OP_THREADS;
   constexpr int U = (gathers(IN) && polarised(NS)) ? MM_U_GATHER : 8;
-  for (int e0 = threadIdx.x; e0 < total; e0 += bd * U) {
+  // the input values of elements ee[0 .. U-1] (lane 0, lane 1), all loads of
+  // the batch issued before any is consumed
+  auto gather_batch = [&](const int (&ee)[U], Real (&v)[2][U]) {
     int nn[U];
     bool ok[2][U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * bd;
+      const int e = ee[u];
       nn[u] = n1_0 + (e & (B1 - 1)) + ((e >> logB1) << a.logN1);
 #pragma unroll
       for (int l = 0; l < 2; ++l) ok[l][u] = e < total && in_range(nn[u], L[l].in_lo, L[l].in_hi);
     }
-    Real v[2][U];
     if (!gathers(IN)) {
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -620,19 +626,58 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? MM_MINB_F13 : 2) k_f1
         for (int l = 0; l < 2; ++l)
           if (ok[l][u]) v[l][u] = Real(__ldg(L[l].in2 + nn[u])) - v[l][u];
     }
+  };
+  // float32 with compile-time geometry: thread t's 16 elements t + 256 u are
+  // the two radix-8 groups (bases p0 and p0 + N2/16, stride N2/8) of the first
+  // column pass, which therefore runs in registers before the first store
+  constexpr bool REG1 = sizeof(C) == 8 && LG2 >= 4 && MM_REG_PASS && ELOG == 12 && OP_THREADS == 256 &&
+                        (U == 4 || U == 8);
+  if constexpr (REG1) {
+    constexpr int lgh = LG2 - 3;
+    const int jc = threadIdx.x & (B1 - 1), p0 = threadIdx.x >> logB1;
+    __syncthreads();  // the pass twiddle tables
+#pragma unroll 1
+    for (int G = 0; G < 2; ++G) {
+      C gv[8];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * bd;
-      if (e < total) {
-        C z;
-        z.x = v[0][u];
-        z.y = v[1][u];
-        buf[(e & (B1 - 1)) * rs + swz<SW>(e >> logB1)] = z;
+      for (int b = 0; b < 8 / U; ++b) {
+        int ee[U];
+        Real v[2][U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) ee[k] = threadIdx.x + (2 * (U * b + k) + G) * bd;
+        gather_batch(ee, v);
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          gv[U * b + k].x = v[0][k];
+          gv[U * b + k].y = v[1][k];
+        }
+      }
+      const int base = p0 + (G << (lgh - 1));
+      reg_pass8<C, false>(gv, tw, LG2, base);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) buf[jc * rs + swz<SW>(base + (m << lgh))] = gv[m];
+    }
+  } else {
+    for (int e0 = threadIdx.x; e0 < total; e0 += bd * U) {
+      int ee[U];
+      Real v[2][U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) ee[u] = e0 + u * bd;
+      gather_batch(ee, v);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = ee[u];
+        if (e < total) {
+          C z;
+          z.x = v[0][u];
+          z.y = v[1][u];
+          buf[(e & (B1 - 1)) * rs + swz<SW>(e >> logB1)] = z;
+        }
       }
     }
   }
   __syncthreads();
-  fft_rows<C, false, SW>(buf, B1, rs, logN2, tw);
+  fft_rows<C, false, SW>(buf, B1, rs, logN2, tw, REG1 ? 3 : 0);
   C* sc = static_cast<C*>(a.scratch) + (long long)tl * a.M;
   const int mask = a.M - 1;
   if constexpr (sizeof(C) == 8 && LG2 > 0 && MM_TW_POWERS && ELOG == 12 && OP_THREADS == 256) {
@@ -678,21 +723,53 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) k_f2(OpArgs a)
   C* sc = static_cast<C*>(a.scratch) + (long long)tl * a.M + (long long)pos0 * N1;
   const int total = B2 << logN1;
   constexpr int bd = OP_THREADS;
-  for (int e0 = threadIdx.x; e0 < total; e0 += bd * 8) {
-    C v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (e0 + u * bd < total) v[u] = sc[e0 + u * bd];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * bd;
-      if (e < total) buf[(e >> logN1) * rs + swz<SW>(e & (N1 - 1))] = v[u];
-    }
-  }
-  __syncthreads();
   const Real* H = static_cast<const Real*>(a.H) + (long long)filt * a.M + (long long)pos0 * N1;
-  fft_rows_filter<C, SW>(buf, B2, rs, logN1, tw, [H, N1](int row) { return H + (long long)row * N1; });
-  for (int e = threadIdx.x; e < total; e += bd) sc[e] = buf[(e >> logN1) * rs + swz<SW>(e & (N1 - 1))];
+  auto Hrow = [H, N1](int row) { return H + (long long)row * N1; };
+  if constexpr (sizeof(C) == 8 && LG1 >= 4 && MM_REG_PASS && ELOG == 12 && OP_THREADS == 256) {
+    // float32: the first forward and the last inverse pass in registers,
+    // straight from and to the scratch.  Thread t owns the groups g = t and
+    // t + 256 (row g / (N1/8), elements j + m N1/8, j = g mod N1/8); a warp's
+    // loads and stores of one m cover 32 consecutive elements of one row.
+    constexpr int lgh = LG1 - 3;
+    __syncthreads();  // the pass twiddle tables
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g = threadIdx.x + h * bd, row = g >> lgh, j = g & ((1 << lgh) - 1);
+      C v[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) v[m] = sc[(row << LG1) + j + (m << lgh)];
+      reg_pass8<C, false>(v, tw, LG1, j);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) buf[row * rs + swz<SW>(j + (m << lgh))] = v[m];
+    }
+    __syncthreads();
+    fft_rows_filter<C, SW>(buf, B2, rs, logN1, tw, Hrow, 3);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g = threadIdx.x + h * bd, row = g >> lgh, j = g & ((1 << lgh) - 1);
+      C v[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) v[m] = buf[row * rs + swz<SW>(j + (m << lgh))];
+      reg_pass8<C, true>(v, tw, LG1, j);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) sc[(row << LG1) + j + (m << lgh)] = v[m];
+    }
+  } else {
+    for (int e0 = threadIdx.x; e0 < total; e0 += bd * 8) {
+      C v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (e0 + u * bd < total) v[u] = sc[e0 + u * bd];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * bd;
+        if (e < total) buf[(e >> logN1) * rs + swz<SW>(e & (N1 - 1))] = v[u];
+      }
+    }
+    __syncthreads();
+    fft_rows_filter<C, SW>(buf, B2, rs, logN1, tw, Hrow);
+    for (int e = threadIdx.x; e < total; e += bd) sc[e] = buf[(e >> logN1) * rs + swz<SW>(e & (N1 - 1))];
+  }
 }
 
 // ---------------------------------------------------------------- k_f3
@@ -769,22 +846,15 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? MM_MINB_F13 : 2) k_f3
     }
   }
   __syncthreads();
-  fft_rows<C, true, SW>(buf, B1, rs, logN2, tw);
   constexpr int U = OUT == OUT_MAP ? MM_U_SCATTER : 8;
-  for (int e0 = threadIdx.x; e0 < total; e0 += bd * U) {
+  // the outputs of elements ee[0 .. U-1] with values val (lane 0, lane 1)
+  auto scatter_batch = [&](const int (&eidx)[U], const Real (&val)[2][U]) {
     int nn[U];
     bool ok[2][U];
-    Real val[2][U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * bd;
-      const int j = e & (B1 - 1), n2 = e >> logB1;
-      nn[u] = n1_0 + j + (n2 << a.logN1);
-      C z;
-      z.x = z.y = 0;
-      if (e < total) z = buf[j * rs + swz<SW>(n2)];
-      val[0][u] = z.x;
-      val[1][u] = z.y;
+      const int e = eidx[u];
+      nn[u] = n1_0 + (e & (B1 - 1)) + ((e >> logB1) << a.logN1);
 #pragma unroll
       for (int l = 0; l < 2; ++l) ok[l][u] = e < total && in_range(nn[u], L[l].out_lo, L[l].out_hi);
     }
@@ -870,6 +940,51 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? MM_MINB_F13 : 2) k_f3
             hwp_scatter_warp<Real>(hacc + 32 * l, hgrp + l, L[l].pix, L[l].hb, L[l].hang, L[l].htau, nn[u],
                                    ok[l][u], val[l][u]);
       }
+    }
+  };
+  // float32 with compile-time geometry: the last inverse column pass runs in
+  // registers on each thread's two radix-8 groups (see k_f1) before their outputs
+  constexpr bool REG3 = sizeof(C) == 8 && LG2 >= 4 && MM_REG_PASS && ELOG == 12 && OP_THREADS == 256 &&
+                        (U == 4 || U == 8);
+  fft_rows<C, true, SW>(buf, B1, rs, logN2, tw, REG3 ? 3 : 0);
+  if constexpr (REG3) {
+    constexpr int lgh = LG2 - 3;
+    const int jc = threadIdx.x & (B1 - 1), p0 = threadIdx.x >> logB1;
+#pragma unroll 1
+    for (int G = 0; G < 2; ++G) {
+      const int base = p0 + (G << (lgh - 1));
+      C gv[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) gv[m] = buf[jc * rs + swz<SW>(base + (m << lgh))];
+      reg_pass8<C, true>(gv, tw, LG2, base);
+#pragma unroll
+      for (int b = 0; b < 8 / U; ++b) {
+        int ee[U];
+        Real val[2][U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          ee[k] = threadIdx.x + (2 * (U * b + k) + G) * bd;
+          val[0][k] = gv[U * b + k].x;
+          val[1][k] = gv[U * b + k].y;
+        }
+        scatter_batch(ee, val);
+      }
+    }
+  } else {
+    for (int e0 = threadIdx.x; e0 < total; e0 += bd * U) {
+      int ee[U];
+      Real val[2][U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * bd;
+        ee[u] = e;
+        C z;
+        z.x = z.y = 0;
+        if (e < total) z = buf[(e & (B1 - 1)) * rs + swz<SW>(e >> logB1)];
+        val[0][u] = z.x;
+        val[1][u] = z.y;
+      }
+      scatter_batch(ee, val);
     }
   }
   if constexpr (HWP) {
