@@ -79,6 +79,9 @@ def parse():
                          "0 direct launches (every kernel visible to a profiler)")
     ap.add_argument("--fft-len", type=int, default=0, help="override the plan's FFT length (0 = plan's choice)")
     ap.add_argument("--tpc", type=int, default=0, help="override the plan's tiles per launch chunk (0 = plan's choice)")
+    ap.add_argument("--det", type=int, default=32,
+                    help="detectors of the all-sky workload (profiling captures of a smaller case with the same "
+                         "FFT length and kernels; the headline uses all 32)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plan with the cost model's FFT length instead of the measuring autotuner")
     ap.add_argument("--operator-only", type=int, default=0, metavar="R",
@@ -646,12 +649,12 @@ def run_secondary(args):
 
 
 # ----------------------------------------------------------------------------- headline
-def headline_problem(workload, rank, dev):
+def headline_problem(workload, rank, dev, n_det=32):
     """(problem, pix, psi, d) with pix, psi, d on the device."""
     import torch
     if workload == "config3":
         from synth.allsky import make_allsky_problem
-        p = make_allsky_problem(scale=0, device=dev, seed=3000 + rank)
+        p = make_allsky_problem(scale=0, n_det=n_det, device=dev, seed=3000 + rank)
         return p, p.pix, p.psi, p.d[0]
     from synth import make_config
     p = make_config(2, seed=2000 + rank)
@@ -720,7 +723,7 @@ def run_headline(args, world, rank, local):
 
     # one independent replica per rank (weak scaling, no data-path collective)
     t0 = time.time()
-    p, pix, psi, d = headline_problem(workload, rank, dev)
+    p, pix, psi, d = headline_problem(workload, rank, dev, args.det)
     torch.cuda.synchronize()
     gen_s = time.time() - t0
     t0 = time.time()

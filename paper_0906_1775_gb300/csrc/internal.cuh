@@ -689,7 +689,7 @@ __device__ __forceinline__ void fft_pass(C* buf, int rows, int rs, int logN, int
   }
 }
 
-__host__ __device__ __forceinline__ int last_pass_start(int logN) { return ((logN - 1) / 3) * 3; }
+__host__ __device__ constexpr int last_pass_start(int logN) { return ((logN - 1) / 3) * 3; }
 
 // Offset of pass s's twiddle table: passes before it hold (2^R - 1) N/2^(s'+R)
 // entries each (N - 1 entries in all).
@@ -733,21 +733,34 @@ __device__ __forceinline__ void fft_pass_any(C* buf, int rows, int rs, int logN,
 // (tw: N entries).  s_lo = 3 leaves out the first pass (s = 0) of a forward
 // transform, or the last pass of an inverse one, which the caller does in
 // registers (reg_pass8).
+// s_hi < 0 (the default) runs every pass up to the last; s_hi = the last
+// pass's start leaves it out (forward: the last pass; inverse: the first),
+// for the caller to do it in registers (reg_pass_last).
 template <typename C, bool INV, int SW>
-__device__ __forceinline__ void fft_rows(C* buf, int rows, int rs, int logN, const C* tw, int s_lo = 0) {
+__device__ __forceinline__ void fft_rows(C* buf, int rows, int rs, int logN, const C* tw, int s_lo = 0,
+                                         int s_hi = -1) {
+  const int top = s_hi < 0 ? last_pass_start(logN) + 3 : s_hi;
   if (!INV) {
 #pragma unroll
-    for (int s = s_lo; s < logN; s += 3) {
+    for (int s = s_lo; s < top; s += 3) {
       fft_pass_any<C, false, SW>(buf, rows, rs, logN, s, tw);
       __syncthreads();
     }
   } else {
 #pragma unroll
-    for (int s = last_pass_start(logN); s >= s_lo; s -= 3) {
+    for (int s = top - 3; s >= s_lo; s -= 3) {
       fft_pass_any<C, true, SW>(buf, rows, rs, logN, s, tw);
       __syncthreads();
     }
   }
+}
+
+// The last pass of a forward transform (radix 2^R on 2^R consecutive
+// elements; its twiddles are all 1) on one group held in registers, or, INV,
+// the first pass of the inverse transform.
+template <typename C, int R, bool INV>
+__device__ __forceinline__ void reg_pass_last(C (&v)[1 << R]) {
+  small_dft<C, R, INV>(v);
 }
 
 // The first radix-8 pass (s = 0) of a forward transform of length N on one

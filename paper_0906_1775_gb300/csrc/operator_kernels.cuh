@@ -482,6 +482,35 @@ __device__ __forceinline__ void scratch_twiddles(const C* lo, const C* hi, const
 __host__ __device__ constexpr int brev4(int u) {
   return ((u & 1) << 3) | ((u & 2) << 1) | ((u & 4) >> 1) | ((u & 8) >> 3);
 }
+
+// Four-step twiddles of one group of the last column pass: positions
+// G q + m (G = 2^RL, m < G) of column n1, whose bit reversal over lg bits is
+// brev_RL(m) 2^(lg - RL) + brev_(lg-RL)(q); so the twiddle of element m is
+// tw[m] = A C^brev_RL(m), A = w^(n1 brev(q)), C = w^(n1 2^(lg - RL)), from two
+// split-table reads and products (float32 only).
+template <typename C, int RL>
+__device__ __forceinline__ void last_group_twiddles(const C* lo, const C* hi, const C* twM, int n1, int q, int lg,
+                                                    int mask, int logL, C (&tw)[1 << RL]) {
+  const C A = split_twiddle(lo, hi, twM, (n1 * brev_n(q, lg - RL)) & mask, logL);
+  const C Cw = split_twiddle(lo, hi, twM, (n1 << (lg - RL)) & mask, logL);
+  C p[1 << RL];
+  p[0] = A;
+  p[1] = cmul(A, Cw);
+  if (RL >= 2) {
+    const C C2 = cmul(Cw, Cw);
+    p[2] = cmul(A, C2);
+    p[3] = cmul(p[1], C2);
+    if (RL >= 3) {
+      const C C4 = cmul(C2, C2);
+      p[4] = cmul(A, C4);
+      p[5] = cmul(p[1], C4);
+      p[6] = cmul(p[2], C4);
+      p[7] = cmul(p[3], C4);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < (1 << RL); ++m) tw[m] = p[brev_small<RL>(m)];
+}
 // Shared entries of the two split tables (none for float64).
 __host__ __device__ inline int split_entries(int esz, int logM) {
   return esz == 8 ? (1 << split_log(logM)) + (1 << (logM - split_log(logM))) : 0;
@@ -524,6 +553,11 @@ __global__ void k_weights(long long n, const float* __restrict__ psi, Real* c, R
 // the way into or out of shared memory (1) or inside it like the others (0).
 #ifndef MM_REG_PASS
 #define MM_REG_PASS 1
+#endif
+// Float32 column kernels: the last forward (k_f1) and first inverse (k_f3)
+// column pass in registers at the scratch write or read (1).
+#ifndef MM_REG_LAST
+#define MM_REG_LAST 1
 #endif
 template <typename Real>
 __host__ __device__ constexpr int elog() {
@@ -677,10 +711,28 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? MM_MINB_F13 : 2) k_f1
     }
   }
   __syncthreads();
-  fft_rows<C, false, SW>(buf, B1, rs, logN2, tw, REG1 ? 3 : 0);
+  // float32 with compile-time geometry: the last column pass (radix 4 or 8 on
+  // consecutive elements, no twiddles) runs in registers and feeds the
+  // scratch write directly
+  constexpr int RL = LG2 > 0 ? LG2 - last_pass_start(LG2) : 0;
+  constexpr bool REGL = REG1 && MM_REG_LAST && (RL == 2 || RL == 3) && last_pass_start(LG2) >= 6;
+  fft_rows<C, false, SW>(buf, B1, rs, logN2, tw, REG1 ? 3 : 0, REGL ? last_pass_start(LG2) : -1);
   C* sc = static_cast<C*>(a.scratch) + (long long)tl * a.M;
   const int mask = a.M - 1;
-  if constexpr (sizeof(C) == 8 && LG2 > 0 && MM_TW_POWERS && ELOG == 12 && OP_THREADS == 256) {
+  if constexpr (REGL) {
+    constexpr int G = 1 << RL;
+    const int j = threadIdx.x & (B1 - 1);
+#pragma unroll 1
+    for (int q = threadIdx.x >> logB1; q < (N2 >> RL); q += bd >> logB1) {
+      C v[G], w[G];
+#pragma unroll
+      for (int m = 0; m < G; ++m) v[m] = buf[j * rs + swz<SW>(G * q + m)];
+      reg_pass_last<C, RL, false>(v);
+      last_group_twiddles<C, RL>(tlo, thi, twM, n1_0 + j, q, LG2, mask, logL, w);
+#pragma unroll
+      for (int m = 0; m < G; ++m) sc[(long long)(G * q + m) * a.N1 + n1_0 + j] = cmul(v[m], w[m]);
+    }
+  } else if constexpr (sizeof(C) == 8 && LG2 > 0 && MM_TW_POWERS && ELOG == 12 && OP_THREADS == 256) {
     const int j = threadIdx.x & (B1 - 1), p0 = threadIdx.x >> logB1;
     C p4[4], p1[4];
     scratch_twiddles(tlo, thi, twM, n1_0 + j, brev_n(p0, logN2), mask, logL, p4, p1);
@@ -811,7 +863,28 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? MM_MINB_F13 : 2) k_f3
   constexpr int bd = OP_THREADS;
   const C* sc = static_cast<const C*>(a.scratch) + (long long)tl * a.M;
   const int mask = a.M - 1;
-  if constexpr (sizeof(C) == 8 && LG2 > 0 && MM_TW_POWERS && ELOG == 12 && OP_THREADS == 256) {
+  // float32 with compile-time geometry: the first inverse column pass (radix
+  // 4 or 8 on consecutive elements, no twiddles) runs in registers on the
+  // groups read straight from the scratch (see k_f1)
+  constexpr int RL = LG2 > 0 ? LG2 - last_pass_start(LG2) : 0;
+  constexpr bool REGH = sizeof(C) == 8 && LG2 >= 4 && MM_REG_PASS && MM_REG_LAST && ELOG == 12 &&
+                        OP_THREADS == 256 && (RL == 2 || RL == 3) && last_pass_start(LG2) >= 6;
+  if constexpr (REGH) {
+    constexpr int G = 1 << RL;
+    const int j = threadIdx.x & (B1 - 1);
+#pragma unroll 2
+    for (int q = threadIdx.x >> logB1; q < (N2 >> RL); q += bd >> logB1) {
+      C v[G], w[G];
+#pragma unroll
+      for (int m = 0; m < G; ++m) v[m] = sc[(long long)(G * q + m) * a.N1 + n1_0 + j];
+      last_group_twiddles<C, RL>(tlo, thi, twM, n1_0 + j, q, LG2, mask, logL, w);
+#pragma unroll
+      for (int m = 0; m < G; ++m) v[m] = cmulc(v[m], w[m]);
+      reg_pass_last<C, RL, true>(v);
+#pragma unroll
+      for (int m = 0; m < G; ++m) buf[j * rs + swz<SW>(G * q + m)] = v[m];
+    }
+  } else if constexpr (sizeof(C) == 8 && LG2 > 0 && MM_TW_POWERS && ELOG == 12 && OP_THREADS == 256) {
     const int j = threadIdx.x & (B1 - 1), p0 = threadIdx.x >> logB1;
     C p4[4], p1[4];
     scratch_twiddles(tlo, thi, twM, n1_0 + j, brev_n(p0, logN2), mask, logL, p4, p1);
@@ -946,7 +1019,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? MM_MINB_F13 : 2) k_f3
   // registers on each thread's two radix-8 groups (see k_f1) before their outputs
   constexpr bool REG3 = sizeof(C) == 8 && LG2 >= 4 && MM_REG_PASS && ELOG == 12 && OP_THREADS == 256 &&
                         (U == 4 || U == 8);
-  fft_rows<C, true, SW>(buf, B1, rs, logN2, tw, REG3 ? 3 : 0);
+  fft_rows<C, true, SW>(buf, B1, rs, logN2, tw, REG3 ? 3 : 0, REGH ? last_pass_start(LG2) : -1);
   if constexpr (REG3) {
     constexpr int lgh = LG2 - 3;
     const int jc = threadIdx.x & (B1 - 1), p0 = threadIdx.x >> logB1;
