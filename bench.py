@@ -84,6 +84,8 @@ def parse():
                          "FFT length and kernels; the headline uses all 32)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plan with the cost model's FFT length instead of the measuring autotuner")
+    ap.add_argument("--scatter-runs", type=int, default=0, choices=[-1, 0, 1],
+                    help="the operator scatter's run sums: 0 the plan's rule or the autotuner, 1 on, -1 off")
     ap.add_argument("--operator-only", type=int, default=0, metavar="R",
                     help="only build the plan and time R float32 operator applications (profiling runs)")
     return ap.parse_args()
@@ -728,7 +730,7 @@ def run_headline(args, world, rank, local):
     gen_s = time.time() - t0
     t0 = time.time()
     plan = mm.Plan(pix, psi, p.n_pix, p.interval_offsets, p.interval_filter, lib_lags(p), tiles_per_chunk=args.tpc,
-                   fft_len=args.fft_len, autotune=not args.no_autotune)
+                   fft_len=args.fft_len, autotune=not args.no_autotune, scatter_runs=args.scatter_runs)
     torch.cuda.synchronize()
     plan_s = time.time() - t0
     n_obs = plan.n_obs
@@ -916,8 +918,10 @@ def run_headline(args, world, rank, local):
                            "replicas": "one independent problem per rank", "generate_s": gen_s,
                            "plan_create_s": plan_s, "device_bytes": plan.stats["device_bytes"],
                            "tiles_per_chunk": plan.stats["tiles_per_chunk"],
-                           "autotune": [{"fft_len": m, "tiles_per_chunk": t, "fp32_operator_ms": ms}
-                                        for m, t, ms in plan.stats["tuned"]]},
+                           "scatter_runs": plan.stats["scatter_runs"],
+                           "repeat_frac": round(plan.stats["repeat_frac"], 4),
+                           "autotune": [{"fft_len": m, "tiles_per_chunk": t, "fp32_operator_ms": ms, "runs": r}
+                                        for m, t, ms, r in plan.stats["tuned"]]},
                 "time_to_1e-6_map_error": {
                     "mixed_ms": ms_max / args.steps, "mixed_iters": iters // max(args.steps, 1),
                     "mixed_rel_tol": tol_mixed, "mixed_map_err": err_mixed, "mixed_map_err_IQU": per_mixed,

@@ -42,6 +42,9 @@ extern "C" {
 
 typedef struct madmap_plan_s* madmap_plan_t;
 
+/* autotuner candidates reported in madmap_plan_stats */
+#define MADMAP_MAX_TUNED 12
+
 typedef enum {
   MADMAP_OK = 0,
   MADMAP_WARN_MAXITER = 1,      /* result valid: lowest-residual iterate returned */
@@ -196,6 +199,14 @@ typedef struct {
    * their times are in madmap_plan_stats.  Adds a few operator applications
    * to plan creation; ignored for white-noise plans. */
   int32_t autotune;
+  /* Scatter of the float32 operator (stored T or IQU pointing, one
+   * pixelisation, atomic map sums, FFT lengths 2^13 .. 2^20): lanes holding
+   * consecutive samples that hit one pixel add their sum with one atomic per
+   * run instead of one per sample.  0 (default): on when at least a quarter
+   * of the samples repeat their predecessor's pixel, or as the autotuner
+   * measures; 1: on; -1: off.  The two differ only in the order of the
+   * rounded additions.  Must be -1, 0 or 1. */
+  int32_t scatter_runs;
 } madmap_plan_desc;
 
 typedef struct {
@@ -224,10 +235,14 @@ typedef struct {
                               more than 1024 samples per row, else 1) */
   int32_t deterministic;   /* 1 when map sums run in a fixed order (madmap_plan_desc.deterministic) */
   int32_t sharded;         /* 1 for a sharded plan (madmap_plan_desc.allreduce set) */
-  int32_t n_tuned;         /* candidates the autotuner timed (0: not tuned), at most 9 reported */
-  int32_t tuned_fft_len[9];
-  int32_t tuned_tiles_per_chunk[9];
-  float tuned_ms[9];       /* float32 operator application time of each candidate */
+  int32_t n_tuned;         /* candidates the autotuner timed (0: not tuned), at most MADMAP_MAX_TUNED reported */
+  int32_t tuned_fft_len[MADMAP_MAX_TUNED];
+  int32_t tuned_tiles_per_chunk[MADMAP_MAX_TUNED];
+  float tuned_ms[MADMAP_MAX_TUNED];       /* float32 operator application time of each candidate */
+  int32_t tuned_runs[MADMAP_MAX_TUNED];   /* 1 when the candidate summed runs of one pixel before its atomics */
+  int32_t scatter_runs;    /* 1 when the operator's scatter adds each run of consecutive samples in
+                              one pixel with one atomic (madmap_plan_desc.scatter_runs), else 0 */
+  double repeat_frac;      /* fraction of samples whose successor hits the same observed pixel */
 } madmap_plan_stats;
 
 typedef struct {

@@ -34,6 +34,7 @@ STATUS_NAMES = {0: "OK", 1: "WARN_MAXITER", 2: "STOPPED", -1: "ERR_INVALID_ARG",
 # madmap_reduce_fn: (buf, count, dtype, stream, user) -> 0 on success
 REDUCE_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p)
 MADMAP_REDUCE_F64, MADMAP_REDUCE_F32, MADMAP_REDUCE_I32 = 0, 1, 2
+MADMAP_MAX_TUNED = 12
 
 
 class madmap_plan_desc(C.Structure):
@@ -48,7 +49,7 @@ class madmap_plan_desc(C.Structure):
                 ("grid_height", C.c_int32), ("extra_index", C.c_void_p), ("n_extra", C.c_int32),
                 ("hwp_angle", C.c_void_p), ("hwp_tau", C.c_void_p), ("interval_hwp_group", C.c_void_p),
                 ("n_hwp_groups", C.c_int32), ("allreduce", REDUCE_FN), ("allreduce_user", C.c_void_p),
-                ("deterministic", C.c_int32), ("autotune", C.c_int32)]
+                ("deterministic", C.c_int32), ("autotune", C.c_int32), ("scatter_runs", C.c_int32)]
 
 
 class madmap_plan_stats(C.Structure):
@@ -60,9 +61,12 @@ class madmap_plan_stats(C.Structure):
                                                           ("n_hwp_params", C.c_int32), ("n_excised_hwp", C.c_int32),
                                                           ("n_map_replicas", C.c_int32),
                                                           ("deterministic", C.c_int32), ("sharded", C.c_int32),
-                                                          ("n_tuned", C.c_int32), ("tuned_fft_len", C.c_int32 * 9),
-                                                          ("tuned_tiles_per_chunk", C.c_int32 * 9),
-                                                          ("tuned_ms", C.c_float * 9)]
+                                                          ("n_tuned", C.c_int32), ("tuned_fft_len", C.c_int32 * MADMAP_MAX_TUNED),
+                                                          ("tuned_tiles_per_chunk", C.c_int32 * MADMAP_MAX_TUNED),
+                                                          ("tuned_ms", C.c_float * MADMAP_MAX_TUNED),
+                                                          ("tuned_runs", C.c_int32 * MADMAP_MAX_TUNED),
+                                                          ("scatter_runs", C.c_int32),
+                                                          ("repeat_frac", C.c_double)]
 
 
 class madmap_checkpoint(C.Structure):

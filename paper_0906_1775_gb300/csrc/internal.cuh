@@ -319,6 +319,12 @@ struct Plan {
   // address takes every sample's atomic
   int n_rep = 1;
   void* rep = nullptr;             // n_rep x n_obs x ns_pad (float64 size), zero between applications
+  // samples whose successor hits the same observed pixel (a measure of how
+  // slowly the scan crosses pixels), and whether the column kernels' scatter
+  // sums such runs of lanes before one atomic per run
+  double repeat_frac = 0.0;
+  int runs = 0;
+  bool runs_fixed = false;         // set by the description, not by the autotuner
   // white noise (n_lags == 1): the operator is one diagonal pass over sample runs
   bool diag = false;
   DiagItem* diag_items = nullptr;  // [n_diag_items]
@@ -362,6 +368,7 @@ struct Plan {
   struct Tuned {
     int M, tpc;
     float ms;
+    int runs;
   };
   std::vector<Tuned> tuned;
   // the data timestream of an IN_RESID operator application (set by the

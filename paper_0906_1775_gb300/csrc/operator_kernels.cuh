@@ -105,6 +105,7 @@ struct OpArgs {
   const void* H;
   const void* tw;
   int n_rep;          // > 1: map outputs go to replica (blockIdx.x + blockIdx.y) % n_rep, rep_stride apart
+  int runs;           // scatter runs of consecutive samples that hit one pixel with one atomic (run_*)
   long long rep_stride;
   const int* skip;    // done flag(s): one shared flag, or one per right-hand side
   int skip_stride;    // 0: *skip covers every tile; > 0: skip[rhs * skip_stride] per lane
@@ -564,6 +565,35 @@ __host__ __device__ constexpr int elog() {
   return sizeof(Real) == 4 ? MM_ELOG_F32 : 11;
 }
 
+// ---------------------------------------------------------------- runs of one pixel
+// In the column kernels' output phases the lanes of each group of B
+// consecutive lanes hold B consecutive samples of one window row, and a scan
+// that stays in a pixel for several samples gives runs of lanes with the same
+// map row.  Each run adds its sum with one atomic from its last lane: a
+// segmented inclusive scan over the run (shuffle steps 1, 2, 4, ... < B) instead
+// of one atomic per sample.  Every lane of the warp must take part.  (Stopping
+// the scan at the warp's longest run measured slower: the straight-line scans
+// of a thread's several outputs overlap one another.)
+template <int B>
+__device__ __forceinline__ void run_geometry(int p, int& start, bool& tail) {
+  const int lane = threadIdx.x & 31;
+  const int prev = __shfl_up_sync(0xffffffffu, p, 1);
+  const bool head = (lane & (B - 1)) == 0 || prev != p;
+  const unsigned hm = __ballot_sync(0xffffffffu, head);
+  start = 31 - __clz(hm & ((2u << lane) - 1u));
+  tail = lane == 31 || ((hm >> (lane + 1)) & 1u);
+}
+template <int B, typename T>
+__device__ __forceinline__ T run_sum(T x, int start) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < B; d <<= 1) {
+    const T y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane - d >= start) x += y;
+  }
+  return x;
+}
+
 // ---------------------------------------------------------------- k_f1
 // LG2 > 0 fixes the column length N2 = 2^LG2 at compile time (and with it the
 // CTA's column count); LG2 = 0 reads the geometry from the arguments.
@@ -920,6 +950,8 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? MM_MINB_F13 : 2) k_f3
   }
   __syncthreads();
   constexpr int U = OUT == OUT_MAP ? MM_U_SCATTER : 8;
+  // lanes per group of consecutive samples (compile-time geometry only)
+  constexpr int RUNB = LG2 > 0 ? ((1 << (ELOG - LG2)) < 32 ? (1 << (ELOG - LG2)) : 32) : 0;
   // the outputs of elements ee[0 .. U-1] with values val (lane 0, lane 1)
   auto scatter_batch = [&](const int (&eidx)[U], const Real (&val)[2][U]) {
     int nn[U];
@@ -985,6 +1017,33 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? MM_MINB_F13 : 2) k_f3
             qq[l][u] = (ok[l][u] && qp) ? __ldg(qp + nn[u]) : -1;
           }
         }
+      // float32: one atomic per run of samples in one pixel (in float64 and
+      // double-float the shuffles of the partial sums cost more than the
+      // atomics they save)
+      if constexpr (RUNB > 0 && (NS == 1 || NS == 3) && std::is_same<Real, float>::value) {
+        if (a.runs) {
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+              int start;
+              bool tail;
+              run_geometry<RUNB>(pp[l][u], start, tail);
+              const float v = pp[l][u] >= 0 ? val[l][u] : 0.0f;
+              const float s0 = run_sum<RUNB>(v, start);
+              if constexpr (NS == 1) {
+                if (tail && pp[l][u] >= 0) atomicAdd(static_cast<float*>(L[l].out) + pp[l][u], s0);
+              } else {
+                float c = cc[l][u], sn = ss[l][u];
+                finish_angle<float>(c, sn);
+                const float s1 = run_sum<RUNB>(v * c, start), s2 = run_sum<RUNB>(v * sn, start);
+                if (tail && pp[l][u] >= 0)
+                  atomicAdd(reinterpret_cast<float4*>(L[l].out) + pp[l][u], make_float4(s0, s1, s2, 0.0f));
+              }
+            }
+          return;
+        }
+      }
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -1429,6 +1488,7 @@ madmap_status launch_all(Plan* p, const void* in, void* out, long long in_stride
   a.in2_stride = p->resid_stride;
   a.n_rep = 1;
   a.rep_stride = 0;
+  a.runs = p->runs;
   a.tiles = ts ? ts->tiles : p->tiles;
   const int n_tiles = ts ? ts->n_tiles : p->n_tiles;
   const size_t sm13 = smem_f13<Real>(p), sm2 = smem_f2<Real>(p);

@@ -280,6 +280,24 @@ __global__ void k_count_pix(const int* pix, long long n, int n_pix, int* counts)
   }
 }
 
+// Samples t < n-1 with pix_obs[t] = pix_obs[t+1] >= 0 (block sums, one atomic per block).
+__global__ void __launch_bounds__(256) k_count_repeats(const int* pix_obs, long long n, unsigned long long* count) {
+  __shared__ unsigned long long part[8];
+  unsigned long long c = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t + 1 < n; t += (long long)gridDim.x * blockDim.x) {
+    const int q = pix_obs[t];
+    c += (q >= 0 && q == pix_obs[t + 1]) ? 1ull : 0ull;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += part[w];
+    atomicAdd(count, b);
+  }
+}
+
 // One bit per global pixel observed by some rank (one thread per 32-pixel word).
 __global__ void k_bits_from_counts(const int* counts, int n_pix, unsigned* bits) {
   const int n_words = (n_pix + 31) / 32;
@@ -1314,6 +1332,15 @@ static madmap_status setup_windows(Plan* p, int M, long long tpc_req, cudaStream
 // way) and tiles per launch chunk (the given number, or the default rule and
 // half and twice it), then keep the fastest.  The candidates' times are
 // reported in the plan's stats.
+// Plans whose column kernels can sum runs of one pixel before the scatter's
+// atomics (stored temperature or IQU pointing, one pixelisation, no extra
+// columns, map sums by atomics).
+static bool runs_capable(const Plan* p) {
+  return !p->otf && !p->multires && !p->ext && !p->det && !p->diag && (p->n_stokes == 1 || p->n_stokes == 3);
+}
+// the fraction of repeated samples from which run sums are the default
+static constexpr double kRunsMinFrac = 0.25;
+
 static madmap_status autotune_windows(Plan* p, int M_fixed, int M0, long long tpc_fixed, cudaStream_t s) {
   std::vector<int> Ms;
   for (int M : {M0 / 2, M0, 2 * M0})
@@ -1368,7 +1395,7 @@ static madmap_status autotune_windows(Plan* p, int M_fixed, int M0, long long tp
         break;
       }
       ms /= reps;
-      p->tuned.push_back({M, (int)p->tiles_per_chunk, ms});
+      p->tuned.push_back({M, (int)p->tiles_per_chunk, ms, p->runs});
       if (ms < best) {
         best = ms;
         bestM = M;
@@ -1376,6 +1403,27 @@ static madmap_status autotune_windows(Plan* p, int M_fixed, int M0, long long tp
       }
     }
     if (st != MADMAP_OK) break;
+  }
+  // the other scatter mode at the best geometry
+  if (st == MADMAP_OK && runs_capable(p) && !p->runs_fixed) {
+    const int r0 = p->runs;
+    st = setup_windows(p, bestM, bestT, s);
+    p->runs = 1 - r0;
+    for (int pass = 0; pass < 2 && st == MADMAP_OK; ++pass) {   // a warm-up launch, then three timed
+      if (pass == 1) cudaEventRecord(e0, s);
+      for (int r = 0; r < (pass ? 3 : 1) && st == MADMAP_OK; ++r)
+        st = op_launch(p, OPP_F32, IN_MAP, OUT_MAP, x, y, 0, 0, 1, nullptr, s);
+    }
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (st == MADMAP_OK &&
+        ((ce = cudaEventSynchronize(e1)) != cudaSuccess || (ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess))
+      st = cuda_fail(ce, "autotune timing");
+    if (st == MADMAP_OK) {
+      ms /= 3;
+      p->tuned.push_back({bestM, (int)p->tiles_per_chunk, ms, p->runs});
+      if (!(ms < best)) p->runs = r0;
+    }
   }
   cleanup();
   if (st != MADMAP_OK) return st;
@@ -1460,6 +1508,7 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
            MADMAP_ERR_INVALID_ARG,
            "deterministic plans need stored single-resolution pointing without extended pointing and "
            "n_samples < 2^31");
+  MM_CHECK(d->scatter_runs >= -1 && d->scatter_runs <= 1, MADMAP_ERR_INVALID_ARG, "scatter_runs must be -1, 0 or 1");
   MM_CHECK(!d->allreduce || (!d->boresight && !d->pix_pol && !d->extra_index && !d->hwp_angle),
            MADMAP_ERR_INVALID_ARG, "sharded plans (allreduce set) need stored single-resolution pointing");
   MM_CHECK(d->n_intervals >= 0 && d->interval_offsets != nullptr, MADMAP_ERR_INVALID_ARG, "bad intervals");
@@ -1695,6 +1744,21 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
     MM_TRYC(cudaMemcpy(p->f0_64, f0.data(), sizeof(double) * p->n_filters, cudaMemcpyHostToDevice));
     p->diag = true;
   }
+  // how often consecutive samples stay in one pixel: the scatter sums such
+  // runs within a warp before its atomics when they are common
+  if (p->pix_obs && p->n_t > 1) {
+    unsigned long long* cnt = nullptr;
+    MM_TRY(dalloc_t(p, &cnt, 1));
+    MM_TRYC(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+    k_count_repeats<<<grid_for(p->n_t), 256, 0, s>>>(p->pix_obs, p->n_t, cnt);
+    unsigned long long h = 0;
+    MM_TRYC(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+    MM_TRYC(cudaStreamSynchronize(s));
+    p->repeat_frac = (double)h / (double)p->n_t;
+  }
+  p->runs_fixed = d->scatter_runs != 0;
+  p->runs = runs_capable(p) && (d->scatter_runs == 1 || (d->scatter_runs == 0 && p->repeat_frac >= kRunsMinFrac))
+                ? 1 : 0;
   // FFT geometry and windows: the length and the tiles per launch chunk given
   // in the description, else chosen by the cost model, or by measurement
   {
@@ -1756,13 +1820,16 @@ extern "C" madmap_status madmap_plan_get_stats(madmap_plan_t plan, madmap_plan_s
   o->n_hwp_params = 32 * p->n_hwp_groups;
   o->n_excised_hwp = p->n_excised_hwp;
   o->n_map_replicas = p->n_rep;
+  o->scatter_runs = p->runs;
+  o->repeat_frac = p->repeat_frac;
   o->deterministic = p->det ? 1 : 0;
-  o->n_tuned = (int32_t)std::min<size_t>(p->tuned.size(), 9);
-  for (int k = 0; k < 9; ++k) {
+  o->n_tuned = (int32_t)std::min<size_t>(p->tuned.size(), MADMAP_MAX_TUNED);
+  for (int k = 0; k < MADMAP_MAX_TUNED; ++k) {
     const bool has = k < o->n_tuned;
     o->tuned_fft_len[k] = has ? p->tuned[k].M : 0;
     o->tuned_tiles_per_chunk[k] = has ? p->tuned[k].tpc : 0;
     o->tuned_ms[k] = has ? p->tuned[k].ms : 0.f;
+    o->tuned_runs[k] = has ? p->tuned[k].runs : 0;
   }
   o->sharded = p->allreduce ? 1 : 0;
   return MADMAP_OK;

@@ -75,6 +75,8 @@ CASES = {
     "deterministic_multires": dict(deterministic=1, pix_pol=FAKE_DEV, n_pix_pol=16),
     "sharded_multires": dict(allreduce="reducer", pix_pol=FAKE_DEV, n_pix_pol=16),
     "sharded_extended": dict(allreduce="reducer", extra_index=FAKE_DEV, n_extra=4),
+    "scatter_runs_high": dict(scatter_runs=2),
+    "scatter_runs_low": dict(scatter_runs=-2),
 }
 
 
@@ -109,6 +111,7 @@ KEYWORD = {
     "boresight_interval_spans_detectors": "spans two detectors",
     "deterministic_extended": "deterministic", "deterministic_multires": "deterministic",
     "sharded_multires": "sharded", "sharded_extended": "sharded",
+    "scatter_runs_high": "scatter_runs", "scatter_runs_low": "scatter_runs",
 }
 
 

@@ -28,11 +28,13 @@ def test_autotuned_plan_reports_candidates_and_keeps_the_fastest():
     st = plan.stats
     tuned = st["tuned"]
     assert st["n_tuned"] == len(tuned) >= 3
-    lens = {m for m, _, _ in tuned}
+    lens = {m for m, _, _, _ in tuned}
     assert len(lens) >= 2 and all(m & (m - 1) == 0 and m > 2 * (p.n_lags - 1) for m in lens)
-    assert all(ms > 0 for _, _, ms in tuned)
-    m_best, t_best, _ = min(tuned, key=lambda c: c[2])
-    assert (st["fft_len"], st["tiles_per_chunk"]) == (m_best, t_best)
+    assert all(ms > 0 for _, _, ms, _ in tuned)
+    m_best, t_best, _, r_best = min(tuned, key=lambda c: c[2])
+    assert (st["fft_len"], st["tiles_per_chunk"], st["scatter_runs"]) == (m_best, t_best, r_best)
+    # both scatter modes were timed at the chosen geometry
+    assert {r for m, t, _, r in tuned if (m, t) == (m_best, t_best)} == {0, 1}
 
 
 def test_every_candidate_length_gives_the_exact_product():
@@ -43,7 +45,7 @@ def test_every_candidate_length_gives_the_exact_product():
     lags = lags_for(p)
     y = np.random.default_rng(3).standard_normal(p.n_samples)
     ref = apply_ninv_direct(y, p.interval_offsets, p.interval_filter, lags)
-    for m, tpc, _ in tuned:
+    for m, tpc, _, _ in tuned:
         plan = make_plan(p, fft_len=m, tiles_per_chunk=tpc)
         for prec, tol, dt in (("fp64", 1e-11, torch.float64), ("fp32", 2e-5, torch.float32)):
             w = host(plan.apply_ninv(cuda(y, dt), precision=prec))[0]
