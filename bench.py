@@ -875,7 +875,7 @@ def run_headline(args, world, rank, local):
         try:
             tr = json.load(open(traffic_file))
             if (tr.get("source_sha256") == operator_source_hash() and tr.get("fft_len") == plan.stats["fft_len"]
-                    and tr.get("n_tiles") == plan.stats["n_tiles"]):
+                    and tr.get("n2") == plan.stats["n2"] and tr.get("n_tiles") == plan.stats["n_tiles"]):
                 roofline["traffic"] = tr["dram_bytes_per_application"]
                 roofline["traffic_source"] = tr.get("how")
         except Exception:
@@ -912,7 +912,7 @@ def run_headline(args, world, rank, local):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": HEADLINE[workload], "n_samples": p.n_samples, "unknowns": int(n_obs * 3),
                            "n_obs": n_obs, "n_excised": plan.stats["n_excised"],
-                           "fft_len": plan.stats["fft_len"], "n_tiles": plan.stats["n_tiles"],
+                           "fft_len": plan.stats["fft_len"], "n2": plan.stats["n2"], "n_tiles": plan.stats["n_tiles"],
                            "l2_flush": "inputs larger than L2 (pointing + d = "
                                        f"{p.n_samples * 12 / 1e6:.0f} MB > 129 MB L2)",
                            "replicas": "one independent problem per rank", "generate_s": gen_s,
@@ -920,8 +920,8 @@ def run_headline(args, world, rank, local):
                            "tiles_per_chunk": plan.stats["tiles_per_chunk"],
                            "scatter_runs": plan.stats["scatter_runs"],
                            "repeat_frac": round(plan.stats["repeat_frac"], 4),
-                           "autotune": [{"fft_len": m, "tiles_per_chunk": t, "fp32_operator_ms": ms, "runs": r}
-                                        for m, t, ms, r in plan.stats["tuned"]]},
+                           "autotune": [{"fft_len": m, "n2": n2, "tiles_per_chunk": t, "fp32_operator_ms": ms, "runs": r}
+                                        for m, t, ms, r, n2 in plan.stats["tuned"]]},
                 "time_to_1e-6_map_error": {
                     "mixed_ms": ms_max / args.steps, "mixed_iters": iters // max(args.steps, 1),
                     "mixed_rel_tol": tol_mixed, "mixed_map_err": err_mixed, "mixed_map_err_IQU": per_mixed,

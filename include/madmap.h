@@ -207,6 +207,11 @@ typedef struct {
    * measures; 1: on; -1: off.  The two differ only in the order of the
    * rounded additions.  Must be -1, 0 or 1. */
   int32_t scatter_runs;
+  /* Split of the FFT length into column and row transforms (the four-step
+   * FFT, M = N1 N2): 0 (default) N2 = 2^ceil(log2(M) / 2), or as the
+   * autotuner measures; 1: columns half as long, rows twice (N1 at most
+   * 1024).  Any split gives the same product up to rounding.  Must be 0 or 1. */
+  int32_t fft_split;
 } madmap_plan_desc;
 
 typedef struct {
@@ -240,6 +245,7 @@ typedef struct {
   int32_t tuned_tiles_per_chunk[MADMAP_MAX_TUNED];
   float tuned_ms[MADMAP_MAX_TUNED];       /* float32 operator application time of each candidate */
   int32_t tuned_runs[MADMAP_MAX_TUNED];   /* 1 when the candidate summed runs of one pixel before its atomics */
+  int32_t tuned_n2[MADMAP_MAX_TUNED];     /* the candidate's column transform length N2 (fft_len = n1 n2) */
   int32_t scatter_runs;    /* 1 when the operator's scatter adds each run of consecutive samples in
                               one pixel with one atomic (madmap_plan_desc.scatter_runs), else 0 */
   double repeat_frac;      /* fraction of samples whose successor hits the same observed pixel */

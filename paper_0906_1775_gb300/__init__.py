@@ -146,7 +146,7 @@ def madmap_plan_get_stats(h) -> dict:
     check(load().madmap_plan_get_stats(h, C.byref(s)), "madmap_plan_get_stats")
     out = {k: getattr(s, k) for k, _ in s._fields_ if not k.startswith("tuned_")}
     out["tuned"] = [(int(s.tuned_fft_len[k]), int(s.tuned_tiles_per_chunk[k]), float(s.tuned_ms[k]),
-                     int(s.tuned_runs[k])) for k in range(s.n_tuned)]
+                     int(s.tuned_runs[k]), int(s.tuned_n2[k])) for k in range(s.n_tuned)]
     return out
 
 
@@ -365,15 +365,17 @@ class Plan:
     the ranks, e.g. torch_allreduce().  Every rank must make the same calls.
     deterministic = True sums every map in a fixed order (bit-reproducible maps).
     autotune = True times candidate FFT lengths and launch chunk sizes, then the
-    scatter with and without run sums, and keeps the fastest (stats["tuned"] lists
-    (fft_len, tiles_per_chunk, ms, runs) per candidate).
+    other split of the length into column and row transforms and the scatter with
+    and without run sums, and keeps the fastest (stats["tuned"] lists
+    (fft_len, tiles_per_chunk, ms, runs, n2) per candidate).
     scatter_runs = 1 / -1 forces the scatter's run sums on / off (0: the plan's rule).
+    fft_split = 1 makes the FFT's column transforms half the default length.
     """
 
     def __init__(self, pix, psi, n_pix, interval_offsets, interval_filter, filter_lags, rcond_excise=0.0,
                  rcond_fp64=0.0, fft_len=0, tiles_per_chunk=0, stream=None, pix_pol=None, n_pix_pol=0,
                  extra_index=None, n_extra=0, hwp=None, allreduce=None, deterministic=False, autotune=False,
-                 scatter_runs=0):
+                 scatter_runs=0, fft_split=0):
         torch = _torch()
         self._h = None
         self._reduce = None
@@ -429,6 +431,7 @@ class Plan:
         d.deterministic = 1 if deterministic else 0
         d.autotune = 1 if autotune else 0
         d.scatter_runs = int(scatter_runs)
+        d.fft_split = int(fft_split)
         self._keep = (off, filt, lags, keep_hwp)
         self.multires = pix_pol is not None
         self._create(d, n_t, stream)

@@ -49,7 +49,8 @@ class madmap_plan_desc(C.Structure):
                 ("grid_height", C.c_int32), ("extra_index", C.c_void_p), ("n_extra", C.c_int32),
                 ("hwp_angle", C.c_void_p), ("hwp_tau", C.c_void_p), ("interval_hwp_group", C.c_void_p),
                 ("n_hwp_groups", C.c_int32), ("allreduce", REDUCE_FN), ("allreduce_user", C.c_void_p),
-                ("deterministic", C.c_int32), ("autotune", C.c_int32), ("scatter_runs", C.c_int32)]
+                ("deterministic", C.c_int32), ("autotune", C.c_int32), ("scatter_runs", C.c_int32),
+                ("fft_split", C.c_int32)]
 
 
 class madmap_plan_stats(C.Structure):
@@ -65,6 +66,7 @@ class madmap_plan_stats(C.Structure):
                                                           ("tuned_tiles_per_chunk", C.c_int32 * MADMAP_MAX_TUNED),
                                                           ("tuned_ms", C.c_float * MADMAP_MAX_TUNED),
                                                           ("tuned_runs", C.c_int32 * MADMAP_MAX_TUNED),
+                                                          ("tuned_n2", C.c_int32 * MADMAP_MAX_TUNED),
                                                           ("scatter_runs", C.c_int32),
                                                           ("repeat_frac", C.c_double)]
 

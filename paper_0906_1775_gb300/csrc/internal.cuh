@@ -368,8 +368,10 @@ struct Plan {
   struct Tuned {
     int M, tpc;
     float ms;
-    int runs;
+    int runs, n2;
   };
+  int split_down = 0;              // column transforms of 2^(ceil(log2 M / 2) - split_down) points
+  bool split_fixed = false;        // set by the description, not by the autotuner
   std::vector<Tuned> tuned;
   // the data timestream of an IN_RESID operator application (set by the
   // caller around the launch)

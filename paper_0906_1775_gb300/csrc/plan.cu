@@ -1258,9 +1258,15 @@ static madmap_status setup_windows(Plan* p, int M, long long tpc_req, cudaStream
   free_windows(p);
   p->M = M;
   {
+    // column transforms of 2^ceil(lg/2) points, or half that when the
+    // autotuner found the shorter columns faster
     const int lg = ilog2((unsigned)p->M);
-    p->logN2 = (lg + 1) / 2;
+    p->logN2 = (lg + 1) / 2 - p->split_down;
     p->logN1 = lg - p->logN2;
+    if (p->logN2 < 1 || p->logN1 > 10) {
+      set_error("fft_split: the row transforms would exceed 1024 points");
+      return MADMAP_ERR_INVALID_ARG;
+    }
     p->N1 = 1 << p->logN1;
     p->N2 = 1 << p->logN2;
   }
@@ -1326,12 +1332,6 @@ static madmap_status setup_windows(Plan* p, int M, long long tpc_req, cudaStream
   return walloc(p, &p->scratch, (size_t)p->scratch_slots * p->tiles_per_chunk * p->M * sizeof(double2));
 }
 
-// Measuring autotuner: time one float32 operator application (CUDA events on
-// `s`, after one warm-up application) for every candidate FFT length (the
-// given one, or the cost model's choice and its neighbours a factor two either
-// way) and tiles per launch chunk (the given number, or the default rule and
-// half and twice it), then keep the fastest.  The candidates' times are
-// reported in the plan's stats.
 // Plans whose column kernels can sum runs of one pixel before the scatter's
 // atomics (stored temperature or IQU pointing, one pixelisation, no extra
 // columns, map sums by atomics).
@@ -1341,10 +1341,20 @@ static bool runs_capable(const Plan* p) {
 // the fraction of repeated samples from which run sums are the default
 static constexpr double kRunsMinFrac = 0.25;
 
+// Measuring autotuner: time the float32 operator (CUDA events on `s`, after a
+// warm-up application) for every candidate FFT length (the given one, or the
+// cost model's choice and its neighbours a factor two either way) and tiles
+// per launch chunk (the given number, or the default rule and half and twice
+// it); at the fastest of those, the other split of the length into column and
+// row transforms (columns half as long, rows twice) and then the scatter with
+// and without run sums.  The fastest candidate is kept; all of them are
+// reported in the plan's stats.
 static madmap_status autotune_windows(Plan* p, int M_fixed, int M0, long long tpc_fixed, cudaStream_t s) {
   std::vector<int> Ms;
   for (int M : {M0 / 2, M0, 2 * M0})
-    if ((M_fixed == 0 || M == M_fixed) && M >= 256 && M <= (1 << 20) && M - 2 * (p->n_lags - 1) >= 1) Ms.push_back(M);
+    if ((M_fixed == 0 || M == M_fixed) && M >= 256 && M <= (1 << 20) && M - 2 * (p->n_lags - 1) >= 1 &&
+        ilog2((unsigned)M) - ((ilog2((unsigned)M) + 1) / 2 - p->split_down) <= 10)
+      Ms.push_back(M);
   const long long nv = (long long)std::max(1, p->n_obs) * p->ns_pad;
   float *x = nullptr, *y = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1395,7 +1405,7 @@ static madmap_status autotune_windows(Plan* p, int M_fixed, int M0, long long tp
         break;
       }
       ms /= reps;
-      p->tuned.push_back({M, (int)p->tiles_per_chunk, ms, p->runs});
+      p->tuned.push_back({M, (int)p->tiles_per_chunk, ms, p->runs, p->N2});
       if (ms < best) {
         best = ms;
         bestM = M;
@@ -1404,24 +1414,45 @@ static madmap_status autotune_windows(Plan* p, int M_fixed, int M0, long long tp
     }
     if (st != MADMAP_OK) break;
   }
+  // one more candidate at the best geometry so far: one operator warm-up
+  // application, then the mean of three
+  auto time_current = [&](float* out_ms) -> madmap_status {
+    madmap_status r = MADMAP_OK;
+    for (int pass = 0; pass < 2 && r == MADMAP_OK; ++pass) {
+      if (pass == 1) cudaEventRecord(e0, s);
+      for (int k = 0; k < (pass ? 3 : 1) && r == MADMAP_OK; ++k)
+        r = op_launch(p, OPP_F32, IN_MAP, OUT_MAP, x, y, 0, 0, 1, nullptr, s);
+    }
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (r == MADMAP_OK &&
+        ((ce = cudaEventSynchronize(e1)) != cudaSuccess || (ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess))
+      r = cuda_fail(ce, "autotune timing");
+    *out_ms = ms / 3;
+    return r;
+  };
+  // the other split of the best length: columns of half the length (kept when
+  // both transforms still have compile-time geometry)
+  if (st == MADMAP_OK && !p->split_fixed) {
+    const int lg = ilog2((unsigned)bestM), l2 = (lg + 1) / 2 - 1, l1 = lg - l2;
+    if (l2 >= 7 && l2 <= 10 && l1 >= 6 && l1 <= 10) {
+      p->split_down = 1;
+      float ms = 0.f;
+      if ((st = setup_windows(p, bestM, bestT, s)) == MADMAP_OK && (st = time_current(&ms)) == MADMAP_OK) {
+        p->tuned.push_back({bestM, (int)p->tiles_per_chunk, ms, p->runs, p->N2});
+        if (ms < best) best = ms;
+        else p->split_down = 0;
+      }
+    }
+  }
   // the other scatter mode at the best geometry
   if (st == MADMAP_OK && runs_capable(p) && !p->runs_fixed) {
     const int r0 = p->runs;
     st = setup_windows(p, bestM, bestT, s);
     p->runs = 1 - r0;
-    for (int pass = 0; pass < 2 && st == MADMAP_OK; ++pass) {   // a warm-up launch, then three timed
-      if (pass == 1) cudaEventRecord(e0, s);
-      for (int r = 0; r < (pass ? 3 : 1) && st == MADMAP_OK; ++r)
-        st = op_launch(p, OPP_F32, IN_MAP, OUT_MAP, x, y, 0, 0, 1, nullptr, s);
-    }
-    cudaEventRecord(e1, s);
     float ms = 0.f;
-    if (st == MADMAP_OK &&
-        ((ce = cudaEventSynchronize(e1)) != cudaSuccess || (ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess))
-      st = cuda_fail(ce, "autotune timing");
-    if (st == MADMAP_OK) {
-      ms /= 3;
-      p->tuned.push_back({bestM, (int)p->tiles_per_chunk, ms, p->runs});
+    if (st == MADMAP_OK && (st = time_current(&ms)) == MADMAP_OK) {
+      p->tuned.push_back({bestM, (int)p->tiles_per_chunk, ms, p->runs, p->N2});
       if (!(ms < best)) p->runs = r0;
     }
   }
@@ -1509,6 +1540,7 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
            "deterministic plans need stored single-resolution pointing without extended pointing and "
            "n_samples < 2^31");
   MM_CHECK(d->scatter_runs >= -1 && d->scatter_runs <= 1, MADMAP_ERR_INVALID_ARG, "scatter_runs must be -1, 0 or 1");
+  MM_CHECK(d->fft_split == 0 || d->fft_split == 1, MADMAP_ERR_INVALID_ARG, "fft_split must be 0 or 1");
   MM_CHECK(!d->allreduce || (!d->boresight && !d->pix_pol && !d->extra_index && !d->hwp_angle),
            MADMAP_ERR_INVALID_ARG, "sharded plans (allreduce set) need stored single-resolution pointing");
   MM_CHECK(d->n_intervals >= 0 && d->interval_offsets != nullptr, MADMAP_ERR_INVALID_ARG, "bad intervals");
@@ -1757,6 +1789,8 @@ extern "C" madmap_status madmap_plan_create(const madmap_plan_desc* d, void* str
     p->repeat_frac = (double)h / (double)p->n_t;
   }
   p->runs_fixed = d->scatter_runs != 0;
+  p->split_down = d->fft_split;
+  p->split_fixed = d->fft_split != 0;
   p->runs = runs_capable(p) && (d->scatter_runs == 1 || (d->scatter_runs == 0 && p->repeat_frac >= kRunsMinFrac))
                 ? 1 : 0;
   // FFT geometry and windows: the length and the tiles per launch chunk given
@@ -1830,6 +1864,7 @@ extern "C" madmap_status madmap_plan_get_stats(madmap_plan_t plan, madmap_plan_s
     o->tuned_tiles_per_chunk[k] = has ? p->tuned[k].tpc : 0;
     o->tuned_ms[k] = has ? p->tuned[k].ms : 0.f;
     o->tuned_runs[k] = has ? p->tuned[k].runs : 0;
+    o->tuned_n2[k] = has ? p->tuned[k].n2 : 0;
   }
   o->sharded = p->allreduce ? 1 : 0;
   return MADMAP_OK;
