@@ -38,7 +38,10 @@ def _slow_scan(p, seed):
 def _problems():
     t = _slow_scan(tiny_T(seed=71, n=60000, width=24, n_lags=300, ivls=(11000, 21000, 28000)), 1)
     q = _slow_scan(tiny_IQU(seed=72, n_per_det=12000, width=16, n_lags=300, n_ivl_lo=2000, n_ivl_hi=7000), 2)
-    return {"T": t, "IQU": q}
+    # flagged samples (pixel -1) inside and between the runs
+    f = _slow_scan(tiny_IQU(seed=74, n_per_det=12000, width=16, n_lags=300, n_ivl_lo=2000, n_ivl_hi=7000,
+                            flag_frac=0.05), 3)
+    return {"T": t, "IQU": q, "IQU_flagged": f}
 
 
 @pytest.fixture(scope="module")
@@ -57,7 +60,7 @@ def _repeat_frac(p, S):
 
 # FFT lengths 2^13, 2^16, 2^20: runs of lanes of 32, 16 and 4 samples in the
 # float32 kernels (the window columns each CTA holds)
-@pytest.mark.parametrize("kind", ["T", "IQU"])
+@pytest.mark.parametrize("kind", ["T", "IQU", "IQU_flagged"])
 @pytest.mark.parametrize("runs", [1, -1])
 @pytest.mark.parametrize("fft_len", [1 << 13, 1 << 16, 1 << 20])
 def test_operator_and_rhs_match_oracle_with_and_without_run_sums(problems, kind, runs, fft_len):
@@ -76,6 +79,19 @@ def test_operator_and_rhs_match_oracle_with_and_without_run_sums(problems, kind,
         assert rel_rms(y, ref) < tol, (kind, runs, prec, rel_rms(y, ref))
         b = host(plan.rhs(cuda(p.d), precision=prec))[0]
         assert rel_rms(b, bref) < tol, (kind, runs, prec, rel_rms(b, bref))
+
+
+def test_batched_operator_with_run_sums_matches_oracle(problems):
+    """Three right-hand sides in one application (tile sets whose lanes carry
+    their right-hand side) through the run-summed scatter."""
+    import torch
+    p, S = problems["IQU_flagged"]
+    plan = make_plan(p, fft_len=1 << 13, scatter_runs=1)
+    xs = np.random.default_rng(8).standard_normal((3, S.n_obs, 3))
+    y = host(plan.apply_ATNA(cuda(xs, torch.float32), precision="fp32"))
+    for k in range(3):
+        ref = S.H(xs[k].astype(np.float32).astype(np.float64))
+        assert rel_rms(y[k], ref) < FP32_TOL, (k, rel_rms(y[k], ref))
 
 
 @pytest.mark.parametrize("kind", ["T", "IQU"])
