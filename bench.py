@@ -882,23 +882,40 @@ def run_headline(args, world, rank, local):
             pass
 
     # ---------------- end to end: host d in, host map out, through the public API
+    # Every step uploads its timestream from pinned host memory and reads its
+    # map back.  The uploads run on a copy stream into two device buffers, so
+    # step k+1's upload overlaps step k's solve (a data loader's pattern); the
+    # first upload is not hidden.
     d_host = d.cpu().pin_memory()
     m_host = torch.empty((n_obs, 3), dtype=torch.float64).pin_memory()
+    dbuf = [torch.empty_like(d), torch.empty_like(d)]
+    copy_stream = torch.cuda.Stream(device=dev)
+    up = [torch.cuda.Event(), torch.cuda.Event()]
     barrier(world)
     torch.cuda.synchronize()
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     g0.record()
+    copy_stream.wait_event(g0)
+
+    def upload(k):
+        with torch.cuda.stream(copy_stream):
+            dbuf[k % 2].copy_(d_host, non_blocking=True)
+            up[k % 2].record(copy_stream)
+
     e2e_iters = 0
-    for _ in range(args.steps):
-        d2 = d_host.to(dev, non_blocking=True)
-        m, info = plan.solve(d2, precision="mixed", rel_tol=tol_mixed, max_iter=5000, **mixed_kw)
+    upload(0)
+    for k in range(args.steps):
+        if k + 1 < args.steps:
+            upload(k + 1)   # its buffer's last reader, step k - 1's solve, has returned
+        torch.cuda.current_stream().wait_event(up[k % 2])
+        m, info = plan.solve(dbuf[k % 2], precision="mixed", rel_tol=tol_mixed, max_iter=5000, **mixed_kw)
         m_host.copy_(m, non_blocking=True)
         e2e_iters += info["iters"]
     g1.record()
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(world, g0.elapsed_time(g1), dev)
     e2e_value = sum_over_ranks(world, float(p.n_samples) * e2e_iters, dev) / (ms_e2e / 1e3)
-    del d2, d_host
+    del dbuf, d_host
 
     cpu = None
     if sample is not None:
@@ -933,7 +950,9 @@ def run_headline(args, world, rank, local):
                 "roofline": roofline,
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(p.n_samples * 4),
-                        "d2h_bytes_per_step": int(n_obs * 3 * 8)},
+                        "d2h_bytes_per_step": int(n_obs * 3 * 8),
+                        "copies": "pinned host timestream uploaded every step on a copy stream (step k+1's "
+                                  "upload overlaps step k's solve), map read back every step"},
                 "gpu_launches": int(launches),
                 "clocks": clk}
         print(json.dumps(line), flush=True)
