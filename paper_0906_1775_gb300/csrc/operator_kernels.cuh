@@ -1316,9 +1316,9 @@ struct OpKernels {
 template <typename Real, int NS, int IN, int OUT>
 OpKernels pick_kernels(const Plan* p) {
   OpKernels k;
-  // the multi-resolution and T on-the-fly modes keep only the generic column
+  // the T on-the-fly and extended-pointing modes keep only the generic column
   // kernels (fewer instances to compile)
-  constexpr bool generic_only = NS == NS_MR || NS == NS_OTF_T || extended(NS);
+  constexpr bool generic_only = NS == NS_OTF_T || extended(NS);
   if constexpr (generic_only) {
     k.f1 = k_f1<Real, NS, IN, 0>;
     k.f3 = k_f3<Real, NS, OUT, 0>;
