@@ -257,7 +257,7 @@ typedef struct {
   int32_t precision;       /* madmap_precision: FP64 or MIXED */
   int32_t max_outer;       /* MIXED: refinement steps, default 10 */
   double inner_rel_tol;    /* MIXED: inner float32 PCG stops at this reduction of its residual,
-                              default 1e-4 */
+                              default 1e-4 (and, with inner_restart = 0, not below rel_tol / 2) */
   int32_t use_graph;       /* 2 (default): one CUDA graph runs all iterations on the device (a
                               conditional WHILE node, capped at max_iter + 2 passes); 1: chunks of
                               iters_per_sync iterations replayed as graphs with host checks
@@ -279,14 +279,23 @@ typedef struct {
    * iteration; the paper keeps no record of it).  Host [n_rhs][history_capacity]
    * or NULL.  Entry k is the relative residual ||r_k|| / ||b|| after PCG
    * iteration k (entry 0 = 1): FP64 the recursively updated residual; MIXED
-   * the inner float32 residual scaled by the relative residual of the float64
-   * iterate its refinement step started from (an estimate of ||b - H x|| / ||b||),
-   * inner iterations of all refinement steps in order.  The solve records at
+   * the inner float32 PCG's recursive residual relative to ||b|| (continued
+   * steps: at each refinement step's first entry the refined iterate's
+   * residual that replaced it; restarted steps: scaled by the relative residual
+   * of the float64 iterate the step started from), inner iterations of all
+   * refinement steps in order.  The solve records at
    * most 4096 iterations; madmap_solve_info.history_len tells how many entries
    * were written.  A resumed solve writes NaN for the iterations done before
    * the checkpoint. */
   double* residual_history;
   int32_t history_capacity;
+  /* MIXED (not in the paper): 0 (default) continues the inner float32 PCG
+   * across refinement steps by residual replacement: the refined iterate's
+   * residual replaces the recursive one, the correction restarts from zero and
+   * the search direction is kept, so the Krylov progress of earlier steps is
+   * not lost.  1: each refinement step solves H e = r from e = 0 (classic
+   * iterative refinement). */
+  int32_t inner_restart;
 } madmap_solve_opts;
 
 /* Solver state at a checkpoint, independent of the launch configuration (a

@@ -479,6 +479,72 @@ __global__ void __launch_bounds__(NT) k_cg_direction(const Real* x, const Real* 
   }
 }
 
+// Residual replacement: the float32 PCG continues across a refinement step
+// (the residual replacement of van der Vorst and Ye, 2000; the "reliable
+// updates" of Clark et al., 2010).  The recursive residual is replaced by
+// the true residual r64 of the refined float64 iterate, the correction x
+// restarts from zero and the search direction is kept.  The new direction is
+// made H-conjugate to the last one explicitly, beta = -<z, H p> / <p, H p>
+// (the Hestenes-Stiefel form, equal to <r,z> / <r,z>_old when the recursive
+// residual is exact), from q = H p of the segment's last iteration, which the
+// halted k_cg_direction left in place; k_cg_direction then forms
+// p = z + beta p.  The state continues with tolerance (relative to the first
+// segment's ||b||) max(inner_tol * its new relative residual, floor_tol) and
+// `budget` more iterations.
+template <typename Real, int NS>
+__global__ void __launch_bounds__(NT) k_cg_replace(Real* x, Real* r, Real* z, Real* xb, const Real* p, const Real* q,
+                                                   const double* r64, long long nvec, int n_obs, const double* P64,
+                                                   const float* P32, const unsigned char* f64, CgState* st,
+                                                   double* partials, double inner_tol, double floor_tol, int budget,
+                                                   const int* inactive, double* hist) {
+  if (inactive && inactive[blockIdx.y]) return;
+  st += blockIdx.y;
+  const long long o = blockIdx.y * nvec;
+  x += o; r += o; z += o; xb += o; p += o; q += o; r64 += o;
+  partials += (long long)blockIdx.y * NB * 4;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_obs; i += gridDim.x * blockDim.x) {
+    const V3<double, NS> t = ldv<double, NS>(r64, i);
+    V3<Real, NS> rv;
+    rv.a = (Real)t.a;
+    rv.b = (Real)t.b;
+    rv.c = (Real)t.c;
+    const V3<Real, NS> zv = precond<Real, NS>(rv, i, P64, P32, f64);
+    const V3<Real, NS> pv = ldv<Real, NS>(p, i), qv = ldv<Real, NS>(q, i);
+    const V3<Real, NS> zero = {0, 0, 0};
+    stv<Real, NS>(r, i, rv);
+    stv<Real, NS>(z, i, zv);
+    stv<Real, NS>(x, i, zero);
+    stv<Real, NS>(xb, i, zero);
+    acc[0] += dotv(rv, zv);
+    acc[1] += dotv(rv, rv);
+    acc[2] += dotv(zv, qv);
+    acc[3] += dotv(pv, qv);
+  }
+  if (block_reduce_publish<4>(acc, partials, &st->counter)) {
+    double s[4];
+    final_sums<4>(partials, s);
+    if (threadIdx.x == 0) {
+      st->counter = 0;
+      const int k = st->k;
+      const double res = sqrt(s[1]) / st->bnorm;
+      st->beta = (s[3] > 0.0 && isfinite(s[2] / s[3])) ? -s[2] / s[3] : 0.0;
+      st->rz = s[0];
+      st->res = res;
+      st->best_res = res;
+      st->best_k = k;
+      st->dir_k = k - 1;
+      const double tol = fmax(inner_tol * res, floor_tol);
+      st->tol = tol;
+      st->max_iter = k + (budget > 0 ? budget : 0);
+      st->status = 0;
+      st->done = (res <= tol || budget <= 0 || !(s[0] > 0.0)) ? 1 : 0;
+      st->halt = st->done;
+      if (hist && k < HIST_CAP) hist[(long long)blockIdx.y * HIST_CAP + k] = res;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- layout and refinement kernels
 // user [n][ns] (U) -> padded working layout [n][ns_pad] (Real)
 template <typename U, typename Real>
@@ -958,6 +1024,11 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
   double pcg_ms = 0.0, refine_ms = 0.0;
   MM_CUDA(cudaMemsetAsync(sb64->x64, 0, sizeof(double) * nv * n_rhs, s));
   MM_CUDA(cudaMemsetAsync(sb64->xbest64, 0, sizeof(double) * nv * n_rhs, s));
+  // continued inner PCG (residual replacement, k_cg_replace): iterations so far
+  // of each right-hand side's one float32 PCG, and no step below rel_tol / 2
+  const bool cont = !o.inner_restart;
+  const double floor_tol = cont ? 0.5 * o.rel_tol : 0.0;
+  std::vector<int> kdone(n_rhs, 0), seg(n_rhs, 0);
   int outer = 0;
   while (n_active > 0 && outer < o.max_outer) {
     int budget = 0;
@@ -965,16 +1036,42 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
       if (!inactive[k]) budget = std::max(budget, o.max_iter - total[k]);
     MM_CUDA(cudaMemcpyAsync(sb64->flags, inactive.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, s));
     const auto t_pcg = std::chrono::steady_clock::now();
-    st = run_pcg<float, NS, double>(p, sb32, B, sb64->r64, sb64->flags, o.inner_rel_tol, budget, o.iters_per_sync,
-                                    graph, s, R);
+    if (cont && outer > 0) {
+      const int n = p->n_obs;
+      const dim3 g(grid_vec(n), n_rhs);
+      count_launches(2);
+      k_cg_replace<float, NS><<<g, NT, 0, s>>>((float*)sb32->x, (float*)sb32->r, (float*)sb32->z, (float*)sb32->xb,
+                                               (const float*)sb32->p, (const float*)sb32->q, sb64->r64, sb32->nvec,
+                                               n, p->P64, p->P32, p->fp64flag, sb32->st, sb32->partials,
+                                               o.inner_rel_tol, floor_tol, budget, sb64->flags, sb32->hist);
+      k_cg_direction<float, NS><<<g, NT, 0, s>>>((const float*)sb32->x, (const float*)sb32->z, (float*)sb32->p,
+                                                 (float*)sb32->q, (float*)sb32->xb, sb32->nvec, n, sb32->st);
+      MM_CUDA(cudaGetLastError());
+      st = run_pcg<float, NS, double>(p, sb32, B, sb64->r64, sb64->flags, 0.0, budget, o.iters_per_sync, graph, s,
+                                      R, INT_MAX, false);
+    } else {
+      st = run_pcg<float, NS, double>(p, sb32, B, sb64->r64, sb64->flags, std::max(o.inner_rel_tol, floor_tol),
+                                      budget, o.iters_per_sync, graph, s, R);
+    }
     if (st != MADMAP_OK) return st;
     pcg_ms += ms_since(t_pcg);
     const auto t_ref = std::chrono::steady_clock::now();
-    for (int k = 0; k < n_rhs && want_hist; ++k)
-      if (!inactive[k] && (st = append_hist(sb32, k, 1, R[k].iters, res[k], Hh[k], s)) != MADMAP_OK) return st;
+    for (int k = 0; k < n_rhs; ++k) {
+      if (inactive[k]) continue;
+      seg[k] = R[k].iters - (cont ? kdone[k] : 0);   // this step's inner iterations
+      if (want_hist) {
+        st = cont ? append_hist(sb32, k, kdone[k] + 1, R[k].iters, 1.0, Hh[k], s)
+                  : append_hist(sb32, k, 1, R[k].iters, res[k], Hh[k], s);
+        if (st != MADMAP_OK) return st;
+      }
+      if (cont) kdone[k] = R[k].iters;
+    }
     ++outer;
     count_launches(2);
-    k_refine_add<<<gv, NT, 0, s>>>(sb64->x64, (const float*)sb32->xb, sb64->t64, nv, sb64->flags);
+    // the continued PCG's current iterate carries its residual and direction;
+    // a restarted step's best iterate
+    k_refine_add<<<gv, NT, 0, s>>>(sb64->x64, (const float*)(cont ? sb32->x : sb32->xb), sb64->t64, nv,
+                                   sb64->flags);
     const int rp = refine_prec(o);
     const void* xin = sb64->x64;
     if (rp == OPP_DF64) {
@@ -1011,8 +1108,8 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
     for (int k = 0; k < n_rhs; ++k) {
       take[k] = 0;
       if (inactive[k]) continue;
-      total[k] += R[k].iters;
-      I[k].fp32_applies += R[k].iters;
+      total[k] += seg[k];
+      I[k].fp32_applies += seg[k];
       ++I[k].fp64_applies;
       ++I[k].outer_iters;
       if (R[k].status != 0) inner_status[k] = R[k].status;
@@ -1023,7 +1120,7 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
         take[k] = 1;
         any_take = true;
       }
-      if (res[k] <= o.rel_tol || total[k] >= o.max_iter || R[k].iters == 0) {
+      if (res[k] <= o.rel_tol || total[k] >= o.max_iter || seg[k] == 0) {
         inactive[k] = 1;
         --n_active;
       }
@@ -1535,6 +1632,7 @@ extern "C" void madmap_solve_opts_default(madmap_solve_opts* o) {
   o->checkpoint_user = nullptr;
   o->residual_history = nullptr;
   o->history_capacity = 0;
+  o->inner_restart = 0;
 }
 
 extern "C" madmap_status madmap_solve(madmap_plan_t plan, const float* d, double* m, const madmap_solve_opts* opts,
