@@ -86,6 +86,10 @@ def parse():
                     help="plan with the cost model's FFT length instead of the measuring autotuner")
     ap.add_argument("--scatter-runs", type=int, default=0, choices=[-1, 0, 1],
                     help="the operator scatter's run sums: 0 the plan's rule or the autotuner, 1 on, -1 off")
+    ap.add_argument("--fft-split", type=int, default=0, choices=[0, 1],
+                    help="1: FFT columns half the default length (with --no-autotune; the autotuner times both)")
+    ap.add_argument("--inner-tol", type=float, default=1e-4,
+                    help="inner float32 tolerance of the --profile-step solve")
     ap.add_argument("--operator-only", type=int, default=0, metavar="R",
                     help="only build the plan and time R float32 operator applications (profiling runs)")
     return ap.parse_args()
@@ -730,7 +734,8 @@ def run_headline(args, world, rank, local):
     gen_s = time.time() - t0
     t0 = time.time()
     plan = mm.Plan(pix, psi, p.n_pix, p.interval_offsets, p.interval_filter, lib_lags(p), tiles_per_chunk=args.tpc,
-                   fft_len=args.fft_len, autotune=not args.no_autotune, scatter_runs=args.scatter_runs)
+                   fft_len=args.fft_len, autotune=not args.no_autotune, scatter_runs=args.scatter_runs,
+                   fft_split=args.fft_split)
     torch.cuda.synchronize()
     plan_s = time.time() - t0
     n_obs = plan.n_obs
@@ -750,8 +755,8 @@ def run_headline(args, world, rank, local):
         sample = detector_sample(p, 0, pix, psi, d)
     del pix, psi
     if args.profile_step > 0:
-        _, info = plan.solve(d, precision="mixed", rel_tol=args.profile_step, max_iter=3000, max_outer=20,
-                             use_graph=args.profile_graph, inner_rel_tol=1e-4)
+        _, info = plan.solve(d, precision="mixed", rel_tol=args.profile_step, max_iter=3000, max_outer=30,
+                             use_graph=args.profile_graph, inner_rel_tol=args.inner_tol)
         torch.cuda.synchronize()
         print(json.dumps({"profile_step": info, "launches": mm.madmap_kernel_launch_count()}), flush=True)
         plan.close()
@@ -789,7 +794,7 @@ def run_headline(args, world, rank, local):
     # mixed precision: the inner float32 tolerance is a free parameter of the
     # method; the fastest setting that reaches the map error is timed
     best_mixed = None
-    for inner in (1e-4, 3e-5, 1e-5):
+    for inner in (1e-4, 3e-5, 1e-5, 3e-6):
         kw_i = dict(max_outer=30, inner_rel_tol=inner)
         cand = first_tol(solve_err("mixed", **kw_i))
         if cand[2] > MAP_TARGET:
