@@ -210,10 +210,11 @@ def test_iteration_drivers_agree(prec):
     runs = [plan.solve(d, precision=prec, rel_tol=1e-10, max_iter=200, use_graph=g, iters_per_sync=k)
             for g, k in ((2, 8), (1, 8), (0, 3))]
     for m, info in runs[1:]:
-        assert info["iters"] == runs[0][1]["iters"]
         # dot products reduce in a fixed order, but the scatter's float atomics do
-        # not: float64 maps agree to rounding; mixed maps, whose float32 inner
-        # products carry the atomics' order, agree to the stopping tolerance
+        # not: float64 solves agree to rounding; mixed solves, whose float32 inner
+        # products carry the atomics' order, agree to the stopping tolerance and
+        # may stop one iteration apart when a residual lands at a threshold
+        assert abs(info["iters"] - runs[0][1]["iters"]) <= (0 if prec == "fp64" else 1)
         assert rel_rms(host(m), host(runs[0][0])) < (1e-12 if prec == "fp64" else 1e-9)
 
 
