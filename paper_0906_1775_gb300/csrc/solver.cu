@@ -1126,7 +1126,7 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
       }
     }
     if (any_take) {
-      // the flags buffer is reused for `take`; the next round rewrites it
+      // the flags buffer is reused for `take`; the next refinement step rewrites it
       MM_CUDA(cudaMemcpyAsync(sb64->flags, take.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, s));
       count_launches(1);
       k_take_best<<<gv, NT, 0, s>>>(sb64->x64, sb64->xbest64, nv, sb64->flags);
