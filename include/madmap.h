@@ -296,6 +296,13 @@ typedef struct {
    * not lost.  1: each refinement step solves H e = r from e = 0 (classic
    * iterative refinement). */
   int32_t inner_restart;
+  /* MIXED, continued PCG: 0 (default) a step whose float32 recursive residual
+   * reaches rel_tol, after a full-precision residual has replaced it at least
+   * once, ends the solve without one more full-precision residual (the paper
+   * stops on the recursively updated residual, Section 5; the replacement
+   * bounds its drift); final_rel_res is then that recursive residual.  1:
+   * every stop is confirmed by a full-precision residual. */
+  int32_t final_residual;
 } madmap_solve_opts;
 
 /* Solver state at a checkpoint, independent of the launch configuration (a

@@ -568,13 +568,14 @@ class Plan:
 
     @staticmethod
     def _opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync, refine="df64",
-              inner_restart=False):
+              inner_restart=False, final_residual=False):
         o = _lib.madmap_solve_opts()
         o.max_iter, o.rel_tol, o.precision = int(max_iter), float(rel_tol), _PREC[precision]
         o.max_outer, o.inner_rel_tol = int(max_outer), float(inner_rel_tol)
         o.use_graph, o.iters_per_sync = (2 if use_graph is True else int(use_graph)), int(iters_per_sync)
         o.refine_precision = _PREC[refine]
         o.inner_restart = 1 if inner_restart else 0
+        o.final_residual = 1 if final_residual else 0
         return o
 
     @staticmethod
@@ -597,16 +598,18 @@ class Plan:
 
     def solve_batched(self, d, precision="fp64", max_iter=50, rel_tol=1e-6, max_outer=10, inner_rel_tol=1e-4,
                       use_graph=True, iters_per_sync=8, out=None, stream=None, refine="df64", history=False,
-                      inner_restart=False):
+                      inner_restart=False, final_residual=False):
         """Maps [n_rhs, n_obs, n_stokes] (float64) for d [n_rhs, n_samples], and per-rhs info dicts.
         refine ("df64" or "fp64"): arithmetic of the mixed solve's right-hand side and residuals.
         inner_restart: mixed refinement steps restart the float32 PCG instead of continuing it.
+        final_residual: confirm every mixed stop with a full-precision residual (default: a continued
+        PCG may stop on its recursive residual once a full-precision residual has replaced it).
         history: add each right-hand side's residual history (numpy) as info["history"]."""
         torch = _torch()
         d = d.reshape(-1, self.n_samples)
         n_rhs = d.shape[0]
         o = self._opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync, refine,
-                       inner_restart)
+                       inner_restart, final_residual)
         hist = self._history(o, n_rhs, max_iter, history)
         m = out if out is not None else torch.empty((n_rhs, self.n_obs, self.n_stokes), dtype=torch.float64,
                                                     device="cuda")
@@ -641,16 +644,18 @@ class Plan:
 
     def solve(self, d, precision="fp64", max_iter=50, rel_tol=1e-6, max_outer=10, inner_rel_tol=1e-4,
               use_graph=True, iters_per_sync=8, out=None, stream=None, refine="df64", checkpoint_every=0,
-              on_checkpoint=None, history=False, inner_restart=False):
+              on_checkpoint=None, history=False, inner_restart=False, final_residual=False):
         """Maximum-likelihood map [n_obs, n_stokes] (float64) and the solve info dict.
         refine ("df64" or "fp64"): arithmetic of the mixed solve's right-hand side and residuals.
         checkpoint_every > 0 (float64 solves): every that many iterations the solver state is
         passed to on_checkpoint(state dict); a true return stops the solve (status STOPPED).
         history: add the residual history after every iteration (numpy) as info["history"].
-        inner_restart: mixed refinement steps restart the float32 PCG instead of continuing it."""
+        inner_restart: mixed refinement steps restart the float32 PCG instead of continuing it.
+        final_residual: confirm every mixed stop with a full-precision residual (default: a continued
+        PCG may stop on its recursive residual once a full-precision residual has replaced it)."""
         torch = _torch()
         o = self._opts(precision, max_iter, rel_tol, max_outer, inner_rel_tol, use_graph, iters_per_sync, refine,
-                       inner_restart)
+                       inner_restart, final_residual)
         hist = self._history(o, 1, max_iter, history)
         cb = self._checkpoints(o, checkpoint_every, on_checkpoint)
         m = out if out is not None else torch.empty((self.n_obs, self.n_stokes), dtype=torch.float64,

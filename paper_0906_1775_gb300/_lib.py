@@ -88,7 +88,7 @@ class madmap_solve_opts(C.Structure):
                 ("checkpoint_every", C.c_int32), ("checkpoint", C.POINTER(madmap_checkpoint)),
                 ("on_checkpoint", CHECKPOINT_FN), ("checkpoint_user", C.c_void_p),
                 ("residual_history", C.c_void_p), ("history_capacity", C.c_int32),
-                ("inner_restart", C.c_int32)]
+                ("inner_restart", C.c_int32), ("final_residual", C.c_int32)]
 
 
 class madmap_solve_info(C.Structure):

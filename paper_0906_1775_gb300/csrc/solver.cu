@@ -1066,20 +1066,36 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
       }
       if (cont) kdone[k] = R[k].iters;
     }
-    ++outer;
+    const int step = outer++;
     count_launches(2);
     // the continued PCG's current iterate carries its residual and direction;
     // a restarted step's best iterate
     k_refine_add<<<gv, NT, 0, s>>>(sb64->x64, (const float*)(cont ? sb32->x : sb32->xb), sb64->t64, nv,
                                    sb64->flags);
+    // a continued step that started from a replaced residual and reached
+    // rel_tol stops on its recursive residual (no full-precision residual)
+    std::vector<int> acc(n_rhs, 0);
+    int n_acc = 0;
+    if (cont && !o.final_residual && step >= 1) {
+      std::vector<int> skip(inactive);
+      for (int k = 0; k < n_rhs; ++k)
+        if (!inactive[k] && R[k].status == 0 && seg[k] > 0 && R[k].final_res <= o.rel_tol) {
+          acc[k] = skip[k] = 1;
+          ++n_acc;
+        }
+      if (n_acc) MM_CUDA(cudaMemcpyAsync(sb64->flags, skip.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, s));
+    }
     const int rp = refine_prec(o);
     const void* xin = sb64->x64;
-    if (rp == OPP_DF64) {
+    const bool need_res = n_acc < n_active;
+    if (need_res && rp == OPP_DF64) {
       count_launches(1);
       k_split<<<grid_vec(nv * n_rhs), NT, 0, s>>>(sb64->x64, sb64->xdf, nv * n_rhs);
       xin = sb64->xdf;
     }
-    if (d && fused_residual(p, o)) {
+    if (!need_res) {
+      // every active right-hand side stopped on its recursive residual
+    } else if (d && fused_residual(p, o)) {
       // r = A^T N^-1 (d - A x) in one pass; t64 (zero since k_refine_add) stands in for H x
       MM_CUDA(cudaMemsetAsync(sb64->r64, 0, sizeof(double) * nv * n_rhs, s));
       p->resid_d = d;
@@ -1110,10 +1126,10 @@ static madmap_status solve_core(Plan* p, const Batch& B, SolveBuffers* sb64, con
       if (inactive[k]) continue;
       total[k] += seg[k];
       I[k].fp32_applies += seg[k];
-      ++I[k].fp64_applies;
+      if (!acc[k]) ++I[k].fp64_applies;
       ++I[k].outer_iters;
       if (R[k].status != 0) inner_status[k] = R[k].status;
-      res[k] = h[k].res / bnorm[k];
+      res[k] = acc[k] ? R[k].final_res : h[k].res / bnorm[k];
       if (res[k] < best[k]) {
         best[k] = res[k];
         best_iter[k] = total[k];
@@ -1633,6 +1649,7 @@ extern "C" void madmap_solve_opts_default(madmap_solve_opts* o) {
   o->residual_history = nullptr;
   o->history_capacity = 0;
   o->inner_restart = 0;
+  o->final_residual = 0;
 }
 
 extern "C" madmap_status madmap_solve(madmap_plan_t plan, const float* d, double* m, const madmap_solve_opts* opts,
