@@ -77,6 +77,7 @@ CASES = {
     "sharded_extended": dict(allreduce="reducer", extra_index=FAKE_DEV, n_extra=4),
     "scatter_runs_high": dict(scatter_runs=2),
     "scatter_runs_low": dict(scatter_runs=-2),
+    "fft_split": dict(fft_split=2),
 }
 
 
@@ -111,7 +112,7 @@ KEYWORD = {
     "boresight_interval_spans_detectors": "spans two detectors",
     "deterministic_extended": "deterministic", "deterministic_multires": "deterministic",
     "sharded_multires": "sharded", "sharded_extended": "sharded",
-    "scatter_runs_high": "scatter_runs", "scatter_runs_low": "scatter_runs",
+    "scatter_runs_high": "scatter_runs", "scatter_runs_low": "scatter_runs", "fft_split": "fft_split",
 }
 
 
