@@ -324,16 +324,19 @@ typedef struct madmap_checkpoint_s {
 typedef struct {
   int32_t status;          /* madmap_status of the solve */
   int32_t iters;           /* PCG iterations performed (sum of inner iterations for MIXED) */
-  int32_t outer_iters;     /* MIXED refinement steps (FP64: 1) */
+  int32_t outer_iters;     /* MIXED inner steps, each ended by a refinement (FP64: 1) */
   int32_t best_iter;       /* iteration count at which the returned iterate was produced */
   int32_t fp64_applies;    /* full-precision operator applications (float64, or double-float per
                               refine_precision), including the right-hand side; MIXED solves of
                               single-resolution stored pointing form the right-hand side in float32
                               (it only starts the first inner solve; each refinement residual
                               b - H x is formed from the data as A^T N^-1 (d - A x) in full precision)
-                              and count it in fp32_applies */
+                              and count it in fp32_applies; a continued solve that stops on its
+                              recursive residual (final_residual = 0) forms no residual for its
+                              last step */
   int32_t fp32_applies;    /* float32 operator applications */
-  double final_rel_res;    /* last relative residual ||b - H x_k|| / ||b|| (recursive for FP64) */
+  double final_rel_res;    /* last relative residual ||b - H x_k|| / ||b|| (recursive for FP64, and
+                              for a MIXED solve that stopped on its recursive residual) */
   double best_rel_res;     /* relative residual of the returned map */
   double t_rhs_ms;         /* right-hand side time */
   double t_solve_ms;       /* total call time (right-hand side included) */
