@@ -159,3 +159,17 @@ int main(void) {
     assert int(out[2].split()[1]) == mm.paper_fft_length(1024, 100000)
     assert out[3].startswith("create -1 ") and len(out[3]) > len("create -1 ")
     assert out[4] == "badfilter -1"
+
+
+def test_solve_option_defaults():
+    """madmap_solve_opts_default (host only): the paper's defaults (50 iterations,
+    relative residual 1e-6, Section 5) and the mixed solve's continued refinement."""
+    import ctypes
+    mm = _lib()
+    o = mm._lib.madmap_solve_opts()
+    mm.load().madmap_solve_opts_default(ctypes.byref(o))
+    assert (o.max_iter, o.rel_tol, o.precision) == (50, 1e-6, mm._lib.MADMAP_FP64)
+    assert (o.max_outer, o.inner_rel_tol, o.use_graph, o.iters_per_sync) == (10, 1e-4, 2, 8)
+    assert o.refine_precision == mm._lib.MADMAP_DF64
+    assert (o.checkpoint_every, o.history_capacity) == (0, 0)
+    assert (o.inner_restart, o.final_residual) == (0, 0)
